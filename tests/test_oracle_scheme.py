@@ -1,0 +1,190 @@
+"""Whole-scheme pins for the oracle: analytic solutions the paper's equations fix.
+
+  * P plane wave in a periodic cube: error vs the analytic solution and
+    convergence order N+1 (Sec. 4.1 ADER-DG, homogeneous elastic medium);
+  * normal-incidence P wave on a solid/fluid interface: reflection and
+    transmission coefficients (Z1-Z2)/(Z1+Z2), 2 Z1/(Z1+Z2) (Sec. 4.2);
+  * standing surface-gravity wave in a uniform ocean over a rigid bottom:
+    omega^2 = g m tanh(m H), m^2 = k^2 - omega^2/c^2, obtained from
+    Eqs. (acoustics-pde) and (gravitational-bc) with the right-hand side
+    dropped (Secs. 3, 4.3);
+  * energy does not grow under the upwind flux;
+  * rate-2 LTS: one cluster is bitwise global time stepping, two clusters
+    keep the plane-wave error (Sec. 4.4).
+"""
+
+import numpy as np
+import pytest
+from scipy.optimize import brentq
+
+import synthetic as syn
+from oracle.ader import Oracle
+
+R_P = np.array([-2.0, -1, -1, 0, 0, 0, 1, 0, 0])  # right-going P eigenvector, rho=1, lam=2, mu=1
+
+
+def plane_wave(t, amp=1e-3):
+    # q = amp r sin(k.x - omega t), k = 2 pi e_x, omega = c_p |k| = 4 pi
+    return lambda x: amp * R_P * np.sin(2 * np.pi * x[..., 0:1] - 4 * np.pi * t)
+
+
+def _periodic_oracle(n, N, **kw):
+    m = syn.unit_cube_periodic(n)
+    rho, lam, mu = syn.elastic_uniform(m.nt)
+    return Oracle(m.xyz, m.tets, m.face_tag, m.face_partner, rho, lam, mu, N, **kw)
+
+
+def _run_plane_wave(n, N, T):
+    o = _periodic_oracle(n, N, cfl=0.5)
+    o.Q = o.project(plane_wave(0.0))
+    ns = int(np.ceil(T / o.dtmin))
+    for _ in range(ns):
+        o.step_gts(T / ns)
+    return np.linalg.norm(o.l2_error(plane_wave(o.t)))
+
+
+@pytest.mark.parametrize("N,n", [(2, 4), (3, 2)])
+def test_plane_wave_convergence_order(N, n):
+    e1 = _run_plane_wave(n, N, 0.05)
+    e2 = _run_plane_wave(2 * n, N, 0.05)
+    order = np.log2(e1 / e2)
+    assert order > N + 1 - 0.35, (e1, e2, order)
+
+
+def test_plane_wave_small_config():
+    # 8^3 hexes x 6 tets, N=3, CFL 0.5, 100 steps, amplitude 1e-3
+    o = _periodic_oracle(8, 3, cfl=0.5)
+    assert o.E == 3072
+    o.Q = o.project(plane_wave(0.0))
+    for _ in range(100):
+        o.step_gts()
+    err = np.linalg.norm(o.l2_error(plane_wave(o.t)))
+    ref = np.linalg.norm(o.l2_error(plane_wave(o.t), Q=0 * o.Q))
+    assert 0.18 < o.t < 0.19
+    assert err / ref < 2e-4, err / ref
+
+
+def _interface_exact(t, Rc, Tc, c1=2.0, Z1=2.0, c2=1.0, Z2=1.0, x0=-0.8, w=0.2, amp=1e-3):
+    f = lambda s: amp * np.exp(-((s - x0) / w) ** 2)
+
+    def fn(x):
+        X = x[..., 0]
+        out = np.zeros(x.shape[:-1] + (9,))
+        solid = X < 0
+        vi, vr, vt = f(X - c1 * t), Rc * f(-X - c1 * t), Tc * f(X * c1 / c2 - c1 * t)
+        out[..., 6] = np.where(solid, vi + vr, vt)
+        out[..., 0] = np.where(solid, -Z1 * vi + Z1 * vr, -Z2 * vt)
+        syy = np.where(solid, -(2.0 / c1) * vi + (2.0 / c1) * vr, -Z2 * vt)
+        out[..., 1] = syy
+        out[..., 2] = syy
+        return out
+    return fn
+
+
+def test_solid_fluid_reflection_transmission():
+    xs = np.linspace(-2, 2, 33)
+    yz = np.linspace(0, 0.125, 2)
+    m = syn.kuhn_box(xs, yz, yz, tags={"x-": 3, "x+": 3, "y-": 4, "y+": 4, "z-": 4, "z+": 4})
+    cx = m.centroids()[:, 0]
+    rho = np.ones(m.nt)
+    lam = np.where(cx < 0, 2.0, 1.0)     # solid c_p = 2, Z = 2 | fluid c = 1, Z = 1
+    mu = np.where(cx < 0, 1.0, 0.0)
+    o = Oracle(m.xyz, m.tets, m.face_tag, m.face_partner, rho, lam, mu, 3, cfl=0.5)
+    Z1, Z2 = 2.0, 1.0
+    Rc, Tc = (Z1 - Z2) / (Z1 + Z2), 2 * Z1 / (Z1 + Z2)
+    o.Q = o.project(_interface_exact(0.0, Rc, Tc))
+    T = 0.8
+    ns = int(np.ceil(T / o.dtmin))
+    for _ in range(ns):
+        o.step_gts(T / ns)
+    ref = np.linalg.norm(o.l2_error(_interface_exact(o.t, Rc, Tc), Q=0 * o.Q))
+    err = np.linalg.norm(o.l2_error(_interface_exact(o.t, Rc, Tc))) / ref
+    bad = np.linalg.norm(o.l2_error(_interface_exact(o.t, -Rc, 2 - Tc))) / ref
+    assert err < 1e-2 and bad > 0.5, (err, bad)
+
+
+def _gravity_case(nx=4, nz=2, N=3, g=1.0, H=1.0, c=2.0, rho=1.0, L=2.0, amp=1e-2):
+    k = 2 * np.pi / L
+    om = brentq(lambda w: w * w - g * np.sqrt(k * k - w * w / c / c) * np.tanh(np.sqrt(k * k - w * w / c / c) * H),
+                1e-3, c * k * 0.999)
+    m_ = np.sqrt(k * k - om * om / c / c)
+
+    def exact(t, om=om, m_=m_):
+        def fn(x):
+            X, Zc = x[..., 0], x[..., 2]
+            P = np.cosh(m_ * (Zc + H))
+            out = np.zeros(x.shape[:-1] + (9,))
+            p = amp * P * np.cos(k * X) * np.cos(om * t)
+            out[..., 0] = out[..., 1] = out[..., 2] = -p
+            out[..., 6] = amp * k * P * np.sin(k * X) * np.sin(om * t) / (rho * om)
+            out[..., 8] = -amp * m_ * np.sinh(m_ * (Zc + H)) * np.cos(k * X) * np.sin(om * t) / (rho * om)
+            return out
+        return fn
+
+    xs = np.linspace(0, L, nx + 1)
+    ys = np.linspace(0, L / nx, 2)
+    zs = np.linspace(-H, 0, nz + 1)
+    msh = syn.kuhn_box(xs, ys, zs, tags={"x-": 4, "x+": 4, "y-": 4, "y+": 4, "z-": 6, "z+": 2})
+    o = Oracle(msh.xyz, msh.tets, msh.face_tag, msh.face_partner, np.full(msh.nt, rho),
+               np.full(msh.nt, rho * c * c), np.zeros(msh.nt), N, cfl=0.5, g=g)
+    o.Q = o.project(exact(0.0))
+    for e, f in np.argwhere(o.geo.face_tag == 2):
+        o.eta[e, f] = amp * np.cosh(m_ * H) * np.cos(k * o.face_x[e, f, :, 0]) / (rho * g)
+    return o, exact, om, k
+
+
+def test_surface_gravity_wave_dispersion():
+    o, exact, om, k = _gravity_case()
+    T = np.pi / om  # half a period
+    ns = int(np.ceil(T / o.dtmin))
+    E0 = o.energy()
+    for _ in range(ns):
+        o.step_gts(T / ns)
+    ref = np.linalg.norm(o.l2_error(exact(o.t), Q=0 * o.Q))
+    err = np.linalg.norm(o.l2_error(exact(o.t))) / ref
+    # the same mode with the shallow-water frequency sqrt(gH) k is far off
+    bad = np.linalg.norm(o.l2_error(exact(o.t, om=k * 1.0))) / ref
+    assert err < 1e-2 and bad > 0.1, (err, bad)
+    assert o.energy() <= E0 * (1 + 1e-12)
+
+
+def test_energy_does_not_grow_periodic():
+    o = _periodic_oracle(2, 3, cfl=0.5)
+    rng = np.random.default_rng(3)
+    o.Q = o.project(lambda x: np.sin(2 * np.pi * (x @ rng.standard_normal((3, 9)))))
+    E = [o.energy()]
+    for _ in range(20):
+        o.step_gts()
+        E.append(o.energy())
+    E = np.array(E)
+    assert np.all(E[1:] <= E[:-1] * (1 + 1e-12)), np.diff(E)
+
+
+def _warped_periodic(n, a=0.6):
+    phi = lambda u: u - a * np.sin(2 * np.pi * u) / (2 * np.pi)
+    g = np.linspace(0, 1, n + 1)
+    return syn.kuhn_box(g, g, g, tags={s: 4 for s in syn.mesh.SIDES}, warp=lambda x, ijk: phi(x))
+
+
+def test_lts_one_cluster_is_bitwise_gts_and_two_clusters_keep_accuracy():
+    m = _warped_periodic(4)
+    rho, lam, mu = syn.elastic_uniform(m.nt)
+    mk = lambda mc: Oracle(m.xyz, m.tets, m.face_tag, m.face_partner, rho, lam, mu, 3, cfl=0.5,
+                           max_clusters=mc)
+    g1 = mk(1)
+    g1.Q = g1.project(plane_wave(0.0))
+    l1 = mk(1)
+    l1.Q = g1.Q.copy()
+    for _ in range(8):
+        g1.step_gts()
+        l1.advance_macro()
+    assert np.array_equal(g1.Q, l1.Q)
+    l2 = mk(2)
+    assert np.bincount(l2.cluster).size == 2 and np.all(np.bincount(l2.cluster) > 0)
+    l2.Q = l2.project(plane_wave(0.0))
+    for _ in range(4):
+        l2.advance_macro()
+    assert np.isclose(l2.t, g1.t)
+    e_gts = np.linalg.norm(g1.l2_error(plane_wave(g1.t)))
+    e_lts = np.linalg.norm(l2.l2_error(plane_wave(l2.t)))
+    assert e_lts < 1.5 * e_gts, (e_lts, e_gts)
