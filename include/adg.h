@@ -1,0 +1,170 @@
+/*
+ * adg.h - C ABI of the GB300 ADER-DG solver for the fully coupled
+ * elastic (Earth) / acoustic (ocean) wave equation with a gravitational free
+ * surface, local time stepping and dynamic rupture, after Krenz et al.,
+ * "3D Acoustic-Elastic Coupling with Gravity: The Dynamics of the 2018 Palu,
+ * Sulawesi Earthquake and Tsunami" (SC'21).
+ *
+ * Conventions shared by every entry point
+ *  - Return value: ADG_OK (0) or a negative ADG_E_* code; adg_last_error()
+ *    gives a message.  No exception or abort crosses the ABI.
+ *  - Pointers are HOST pointers unless the name says otherwise; they are
+ *    borrowed for the duration of the call only.  The library owns every
+ *    device allocation it makes (cudaMalloc) and frees it in adg_destroy().
+ *  - A context is used by one host thread at a time.
+ *  - Quantities q = (s_xx, s_yy, s_zz, s_xy, s_yz, s_xz, v_x, v_y, v_z):
+ *    stress (positive in tension) and particle velocity (Sec. 3,
+ *    Eq. elasticity-pde).  The ocean is the acoustic special case mu = 0,
+ *    lambda = K, s_ij = -p delta_ij (Sec. 4.1).
+ *  - Mesh: tetrahedra with 4 vertex indices each, positively oriented
+ *    (det[v1-v0, v2-v0, v3-v0] > 0); local face f is the face opposite local
+ *    vertex f; its vertices in increasing local order (a, b, c) parametrise it
+ *    as x(chi) = xa + chi1 (xb - xa) + chi2 (xc - xa).
+ *  - Dofs: modal coefficients of the orthonormal Dubiner basis on the
+ *    reference tet (0,0,0),(1,0,0),(0,1,0),(0,0,1), ordered by total degree,
+ *    then i, then j of the product index (i, j, k); B = (N+1)(N+2)(N+3)/6
+ *    (Sec. 4.1).  Array layout Q[tet][scenario][quantity][basis], double.
+ *  - Face nodes (sea-surface height, fault output): the (N+1)(N+2)/2
+ *    equispaced points chi = (i1/N, i2/N), i2 outer loop, i1 inner loop.
+ */
+#ifndef ADG_H
+#define ADG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ADG_OK 0
+#define ADG_E_INVALID (-1)   /* bad argument or size                          */
+#define ADG_E_MESH (-2)      /* inverted tet, non-matching or unpaired faces  */
+#define ADG_E_STATE (-3)     /* call out of order (e.g. step before init)     */
+#define ADG_E_CUDA (-4)      /* CUDA runtime error                            */
+#define ADG_E_NOMEM (-5)     /* device or host allocation failed              */
+#define ADG_E_NAN (-6)       /* non-finite value detected in the dofs         */
+#define ADG_E_NEWTON (-7)    /* friction Newton solve did not converge        */
+#define ADG_E_TIMEOUT (-8)   /* a bounded device wait ran out                 */
+#define ADG_E_NOT_READY (-9) /* dependencies of a cluster step are not met    */
+
+#define ADG_FP64 0
+#define ADG_FP32 1
+
+/* Face tags (per tet and local face). */
+#define ADG_TAG_INTERIOR 0  /* matched with the face sharing its three vertices  */
+#define ADG_TAG_FREE 1      /* traction-free surface                            */
+#define ADG_TAG_GRAVITY 2   /* gravitational free surface p = rho g eta (Sec. 3) */
+#define ADG_TAG_ABSORB 3    /* outgoing-only: ghost state q+ = 0                */
+#define ADG_TAG_PERIODIC 4  /* paired with face_partner                         */
+#define ADG_TAG_FAULT 5     /* dynamic-rupture fault (both sides tagged)        */
+#define ADG_TAG_RIGID 6     /* rigid free-slip wall: u_n = 0                    */
+
+typedef struct adg_ctx adg_ctx;
+
+typedef struct adg_config {
+  int degree;        /* polynomial degree N in [1, 5]; 5 = order 6 (Sec. 6)       */
+  int precision;     /* ADG_FP64 or ADG_FP32: storage and arithmetic of the dofs;
+                        eta/H, LTS buffers and friction stay FP64                 */
+  double cfl;        /* C in dt = C/(2N+1) h / c_p, h = insphere diameter (Sec. 4.4) */
+  double gravity;    /* g in p = rho g eta; 9.81 in the paper (Sec. 3)            */
+  int max_clusters;  /* rate-2 LTS clusters (Sec. 4.4); 1 = global time stepping */
+  int ensemble;      /* S >= 1 independent scenarios sharing mesh and material    */
+  int device;        /* CUDA device ordinal                                       */
+  void* cuda_stream; /* cudaStream_t to run on, or NULL for a library stream      */
+} adg_config;
+
+typedef struct adg_info {
+  int64_t n_tets;
+  int n_basis;         /* B */
+  int n_face_nodes;    /* (N+1)(N+2)/2 */
+  int n_clusters;      /* clusters actually used */
+  int64_t cluster_size[16];
+  double dt_min;       /* step of cluster 0 */
+  double macro_dt;     /* 2^(n_clusters-1) dt_min */
+  double time;         /* current simulated time */
+  int64_t n_gravity_faces;
+  int64_t n_fault_faces;
+  int64_t updates_per_macro; /* element updates (x ensemble) per macro step */
+  int64_t device_bytes;
+} adg_info;
+
+/* Default configuration: N=5, FP64, cfl 0.35 (Sec. 6), g 9.81, GTS, S=1. */
+void adg_default_config(adg_config* cfg);
+
+/* Create a context on cfg->device.  *out receives the context. */
+int adg_create(const adg_config* cfg, adg_ctx** out);
+
+/* Mesh upload (Sec. 4.1: conforming tetrahedral mesh).
+ * xyz[3*nv] vertex coordinates; tet_v[4*nt] vertex indices;
+ * face_tag[4*nt] ADG_TAG_* per local face; face_partner[4*nt] = t*4+f of the
+ * paired face for ADG_TAG_PERIODIC faces (ignored otherwise) or NULL when no
+ * face is periodic.  Validation (orientation, matching) happens in adg_init. */
+int adg_upload_mesh(adg_ctx* ctx, int64_t nv, const double* xyz, int64_t nt,
+                    const int64_t* tet_v, const int32_t* face_tag, const int64_t* face_partner);
+
+/* Element-wise constant material (Sec. 4.1): density, Lame lambda, mu (mu = 0: fluid). */
+int adg_upload_material(adg_ctx* ctx, const double* rho, const double* lambda, const double* mu);
+
+/* Geometry, CFL time steps, rate-2 clustering, Godunov flux matrices F-/F+
+ * per face (Sec. 4.2, Eq. numerical-flux), device allocation.  Dofs start at 0. */
+int adg_init(adg_ctx* ctx);
+
+int adg_query(const adg_ctx* ctx, adg_info* out);
+
+/* Dofs in user tet order, layout [nt][S][9][B] (host, double). */
+int adg_set_dofs(adg_ctx* ctx, const double* Q);
+int adg_get_dofs(adg_ctx* ctx, double* Q);
+
+/* Initial condition by projection: adg_initial_points returns, for every tet,
+ * n_pts physical points (xyz[nt][n_pts][3]); the caller evaluates its field
+ * there and passes values[nt][S][n_pts][9]; the library projects them onto
+ * the basis with the matching quadrature weights (exact for degree 2N+4). */
+int adg_initial_points(adg_ctx* ctx, int* n_pts, double* xyz /* may be NULL to query n_pts */);
+int adg_set_initial_values(adg_ctx* ctx, const double* values);
+
+/* Gravitational faces (tag 2) in increasing user (tet*4+face) order:
+ * elem_face[n_gravity_faces]; node_xyz[n_gravity_faces][Bf][3] or NULL. */
+int adg_gravity_faces(adg_ctx* ctx, int64_t* elem_face, double* node_xyz);
+/* Sea-surface height eta at the face nodes: [n_gravity_faces][S][Bf] (Sec. 4.3). */
+int adg_set_eta(adg_ctx* ctx, const double* eta);
+int adg_read_ssh(adg_ctx* ctx, double* eta);
+
+/* Time stepping (Sec. 4.4).  A macro step advances every cluster by
+ * macro_dt = 2^(n_clusters-1) dt_min through the rate-2 tick schedule, as one
+ * CUDA graph launch.  adg_advance(n) runs n macro steps; adg_advance_to(t)
+ * runs whole macro steps and a final one with all cluster steps shortened
+ * uniformly so that the time lands on t. */
+int adg_advance(adg_ctx* ctx, int n_macro);
+int adg_advance_to(adg_ctx* ctx, double t);
+/* One rate-2 tick: predictors of the clusters whose step starts, then
+ * correctors of the clusters whose step ends.  Ticks run in order; cluster
+ * c is in step with the others after every 2^c ticks. */
+int adg_step_tick(adg_ctx* ctx);
+/* Run ticks until cluster c completes one more step. */
+int adg_step_cluster(adg_ctx* ctx, int c);
+/* Block until queued work is done; reports device-side errors (NaN...). */
+int adg_sync(adg_ctx* ctx);
+
+/* Receivers: physical points; readout of q at the current time (whole ticks
+ * synchronised: at macro-step boundaries), out[n][S][9] (host, double). */
+int adg_add_receivers(adg_ctx* ctx, int64_t n, const double* xyz);
+int adg_read_receivers(adg_ctx* ctx, double* out);
+
+/* Checkpoint: dofs, eta, fault state and time at a macro-step boundary.
+ * adg_save_state with buf == NULL returns the size in *len. */
+int adg_save_state(adg_ctx* ctx, void* buf, size_t* len);
+int adg_load_state(adg_ctx* ctx, const void* buf, size_t len);
+
+/* Reference operators the library generated (for inspection and tests):
+ * kt[3][B][B] = int phi_m dphi_l/dxi_a, kvol[3][B][B1] = int dphi_m/dxi_a phi_l,
+ * efc[4][Bf][B] basis values at face nodes, lift[4][B][Bf]; any may be NULL. */
+int adg_reference_operators(int degree, double* kt, double* kvol, double* efc, double* lift);
+
+const char* adg_last_error(const adg_ctx* ctx);
+void adg_destroy(adg_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ADG_H */

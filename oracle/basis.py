@@ -9,14 +9,15 @@ Reading (the paper names the basis but prints no formula): the Dubiner
     s = 1 - eta - zeta,  t = 1 - zeta,
 with c_ijk > 0 chosen so that the reference mass matrix is the identity.
 Order: total degree n = i+j+k ascending, then i ascending, then j ascending.
-Jacobi polynomials and their derivatives come from scipy (library
-primitives); all integrals use the collapsed Gauss rules of quadrature.py.
+Jacobi polynomial coefficients come from scipy (a library primitive); each
+factor is evaluated in its homogeneous form, defined on the whole closed tet;
+all integrals use the collapsed Gauss rules of quadrature.py.
 """
 
 from functools import lru_cache
 
 import numpy as np
-from scipy.special import eval_jacobi
+from scipy.special import jacobi
 
 from .quadrature import tet_rule
 
@@ -38,27 +39,31 @@ def triples(N):
     return out
 
 
-def _P(n, a, y):
-    return eval_jacobi(n, a, 0.0, y)
-
-
-def _dP(n, a, y):
-    if n == 0:
-        return np.zeros_like(y)
-    return 0.5 * (n + a + 1) * eval_jacobi(n - 1, a + 1, 1.0, y)
+@lru_cache(maxsize=None)
+def _jac_coeffs(n, a):
+    """Monomial coefficients c_k of P_n^(a,0)(y) = sum_k c_k y^k (scipy)."""
+    return tuple(jacobi(n, a, 0.0).coeffs[::-1])
 
 
 def _G(n, a, x, tau):
-    """tau^n P_n^(a,0)(2x/tau - 1) with its partial derivatives in x and tau."""
-    y = 2.0 * x / tau - 1.0
-    p = _P(n, a, y)
-    val = tau ** n * p
-    if n == 0:
-        z = np.zeros_like(x)
-        return val, z, z
-    dp = _dP(n, a, y)
-    dx = 2.0 * tau ** (n - 1) * dp
-    dtau = tau ** (n - 1) * (n * p - (y + 1.0) * dp)
+    """tau^n P_n^(a,0)(2x/tau - 1) with its partial derivatives in x and tau,
+    written in the homogeneous form sum_k c_k (2x - tau)^k tau^(n-k), which is
+    the same polynomial and stays defined where tau = 0 (tet vertices/edges)."""
+    c = _jac_coeffs(n, a)
+    u = 2.0 * x - tau
+    val = np.zeros_like(x)
+    dx = np.zeros_like(x)
+    dtau = np.zeros_like(x)
+    for k, ck in enumerate(c):
+        uk = u ** k
+        tk = tau ** (n - k)
+        val += ck * uk * tk
+        if k > 0:
+            uk1 = u ** (k - 1)
+            dx += ck * 2.0 * k * uk1 * tk
+            dtau += ck * (-k) * uk1 * tk
+        if n - k > 0:
+            dtau += ck * (n - k) * uk * tau ** (n - k - 1)
     return val, dx, dtau
 
 
@@ -72,9 +77,7 @@ def _raw(N, pts):
     for l, (i, j, k) in enumerate(T):
         f1, f1x, f1s = _G(i, 0, xi, s)
         f2, f2y, f2t = _G(j, 2 * i + 1, eta, t)
-        c = 2.0 * zeta - 1.0
-        f3 = _P(k, 2 * i + 2 * j + 2, c)
-        f3z = 2.0 * _dP(k, 2 * i + 2 * j + 2, c)
+        f3, f3z, _ = _G(k, 2 * i + 2 * j + 2, zeta, np.ones_like(zeta))
         val[:, l] = f1 * f2 * f3
         # d/dxi: only f1 through x
         grad[:, l, 0] = f1x * f2 * f3

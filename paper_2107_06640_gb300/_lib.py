@@ -1,0 +1,247 @@
+"""ctypes binding of the C ABI in include/adg.h (argument marshalling only).
+
+Every function here has the name of the C entry point it wraps, takes numpy
+arrays for the pointer arguments and raises AdgError on a negative status.
+All computation happens in libadg.so (CUDA kernels + host set-up); there is
+no Python or CPU fallback: loading fails loudly if the library is missing.
+"""
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libadg.so")
+
+ADG_OK = 0
+ADG_FP64, ADG_FP32 = 0, 1
+ERRORS = {-1: "INVALID", -2: "MESH", -3: "STATE", -4: "CUDA", -5: "NOMEM", -6: "NAN",
+          -7: "NEWTON", -8: "TIMEOUT", -9: "NOT_READY"}
+
+
+class AdgError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"ADG_E_{ERRORS.get(code, code)} ({code}): {msg}")
+        self.code = code
+
+
+class adg_config(C.Structure):
+    _fields_ = [("degree", C.c_int), ("precision", C.c_int), ("cfl", C.c_double),
+                ("gravity", C.c_double), ("max_clusters", C.c_int), ("ensemble", C.c_int),
+                ("device", C.c_int), ("cuda_stream", C.c_void_p)]
+
+
+class adg_info(C.Structure):
+    _fields_ = [("n_tets", C.c_int64), ("n_basis", C.c_int), ("n_face_nodes", C.c_int),
+                ("n_clusters", C.c_int), ("cluster_size", C.c_int64 * 16), ("dt_min", C.c_double),
+                ("macro_dt", C.c_double), ("time", C.c_double), ("n_gravity_faces", C.c_int64),
+                ("n_fault_faces", C.c_int64), ("updates_per_macro", C.c_int64),
+                ("device_bytes", C.c_int64)]
+
+
+_P = C.c_void_p
+_SIGS = {
+    "adg_default_config": (None, [C.POINTER(adg_config)]),
+    "adg_create": (C.c_int, [C.POINTER(adg_config), C.POINTER(_P)]),
+    "adg_upload_mesh": (C.c_int, [_P, C.c_int64, _P, C.c_int64, _P, _P, _P]),
+    "adg_upload_material": (C.c_int, [_P, _P, _P, _P]),
+    "adg_init": (C.c_int, [_P]),
+    "adg_query": (C.c_int, [_P, C.POINTER(adg_info)]),
+    "adg_set_dofs": (C.c_int, [_P, _P]),
+    "adg_get_dofs": (C.c_int, [_P, _P]),
+    "adg_initial_points": (C.c_int, [_P, C.POINTER(C.c_int), _P]),
+    "adg_set_initial_values": (C.c_int, [_P, _P]),
+    "adg_gravity_faces": (C.c_int, [_P, _P, _P]),
+    "adg_set_eta": (C.c_int, [_P, _P]),
+    "adg_read_ssh": (C.c_int, [_P, _P]),
+    "adg_advance": (C.c_int, [_P, C.c_int]),
+    "adg_advance_to": (C.c_int, [_P, C.c_double]),
+    "adg_step_tick": (C.c_int, [_P]),
+    "adg_step_cluster": (C.c_int, [_P, C.c_int]),
+    "adg_sync": (C.c_int, [_P]),
+    "adg_add_receivers": (C.c_int, [_P, C.c_int64, _P]),
+    "adg_read_receivers": (C.c_int, [_P, _P]),
+    "adg_save_state": (C.c_int, [_P, _P, C.POINTER(C.c_size_t)]),
+    "adg_load_state": (C.c_int, [_P, _P, C.c_size_t]),
+    "adg_reference_operators": (C.c_int, [C.c_int, _P, _P, _P, _P]),
+    "adg_last_error": (C.c_char_p, [_P]),
+    "adg_destroy": (None, [_P]),
+}
+
+_lib = None
+
+
+def load():
+    """Load libadg.so (built by paper_2107_06640_gb300.build)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: run `python -m paper_2107_06640_gb300.build`"
+                              " (the solver has no CPU fallback)")
+        lib = C.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _check(ctx, rc):
+    if rc != ADG_OK:
+        msg = load().adg_last_error(ctx).decode() if ctx else ""
+        raise AdgError(rc, msg)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def adg_default_config():
+    cfg = adg_config()
+    load().adg_default_config(C.byref(cfg))
+    return cfg
+
+
+def adg_create(cfg):
+    h = C.c_void_p()
+    _check(None, load().adg_create(C.byref(cfg), C.byref(h)))
+    return h
+
+
+def adg_upload_mesh(ctx, xyz, tets, face_tag, face_partner=None):
+    xyz = _f64(xyz)
+    tets = np.ascontiguousarray(tets, dtype=np.int64)
+    face_tag = np.ascontiguousarray(face_tag, dtype=np.int32)
+    fp = None if face_partner is None else np.ascontiguousarray(face_partner, dtype=np.int64)
+    _check(ctx, load().adg_upload_mesh(ctx, xyz.shape[0], _ptr(xyz), tets.shape[0], _ptr(tets),
+                                       _ptr(face_tag), _ptr(fp)))
+
+
+def adg_upload_material(ctx, rho, lam, mu):
+    rho, lam, mu = _f64(rho), _f64(lam), _f64(mu)
+    _check(ctx, load().adg_upload_material(ctx, _ptr(rho), _ptr(lam), _ptr(mu)))
+
+
+def adg_init(ctx):
+    _check(ctx, load().adg_init(ctx))
+
+
+def adg_query(ctx):
+    info = adg_info()
+    _check(ctx, load().adg_query(ctx, C.byref(info)))
+    return info
+
+
+def adg_set_dofs(ctx, Q):
+    Q = _f64(Q)
+    _check(ctx, load().adg_set_dofs(ctx, _ptr(Q)))
+
+
+def adg_get_dofs(ctx, out):
+    assert out.dtype == np.float64 and out.flags.c_contiguous
+    _check(ctx, load().adg_get_dofs(ctx, _ptr(out)))
+    return out
+
+
+def adg_initial_points(ctx, n_tets):
+    n = C.c_int()
+    _check(ctx, load().adg_initial_points(ctx, C.byref(n), None))
+    xyz = np.empty((n_tets, n.value, 3))
+    _check(ctx, load().adg_initial_points(ctx, C.byref(n), _ptr(xyz)))
+    return xyz
+
+
+def adg_set_initial_values(ctx, values):
+    values = _f64(values)
+    _check(ctx, load().adg_set_initial_values(ctx, _ptr(values)))
+
+
+def adg_gravity_faces(ctx, n, Bf):
+    ef = np.empty(n, np.int64)
+    xyz = np.empty((n, Bf, 3))
+    if n:
+        _check(ctx, load().adg_gravity_faces(ctx, _ptr(ef), _ptr(xyz)))
+    return ef, xyz
+
+
+def adg_set_eta(ctx, eta):
+    eta = _f64(eta)
+    _check(ctx, load().adg_set_eta(ctx, _ptr(eta)))
+
+
+def adg_read_ssh(ctx, out):
+    _check(ctx, load().adg_read_ssh(ctx, _ptr(out)))
+    return out
+
+
+def adg_advance(ctx, n):
+    _check(ctx, load().adg_advance(ctx, int(n)))
+
+
+def adg_advance_to(ctx, t):
+    _check(ctx, load().adg_advance_to(ctx, float(t)))
+
+
+def adg_step_tick(ctx):
+    _check(ctx, load().adg_step_tick(ctx))
+
+
+def adg_step_cluster(ctx, c):
+    _check(ctx, load().adg_step_cluster(ctx, int(c)))
+
+
+def adg_sync(ctx):
+    _check(ctx, load().adg_sync(ctx))
+
+
+def adg_add_receivers(ctx, xyz):
+    xyz = _f64(xyz)
+    _check(ctx, load().adg_add_receivers(ctx, xyz.shape[0], _ptr(xyz)))
+
+
+def adg_read_receivers(ctx, out):
+    _check(ctx, load().adg_read_receivers(ctx, _ptr(out)))
+    return out
+
+
+def adg_save_state(ctx):
+    n = C.c_size_t(0)
+    _check(ctx, load().adg_save_state(ctx, None, C.byref(n)))
+    buf = np.empty(n.value, np.uint8)
+    _check(ctx, load().adg_save_state(ctx, _ptr(buf), C.byref(n)))
+    return buf
+
+
+def adg_load_state(ctx, buf):
+    buf = np.ascontiguousarray(buf, dtype=np.uint8)
+    _check(ctx, load().adg_load_state(ctx, _ptr(buf), buf.size))
+
+
+def adg_reference_operators(N):
+    B = (N + 1) * (N + 2) * (N + 3) // 6
+    Bf = (N + 1) * (N + 2) // 2
+    B1 = N * (N + 1) * (N + 2) // 6
+    kt = np.empty((3, B, B))
+    kvol = np.empty((3, B, B1))
+    efc = np.empty((4, Bf, B))
+    lift = np.empty((4, B, Bf))
+    _check(None, load().adg_reference_operators(N, _ptr(kt), _ptr(kvol), _ptr(efc), _ptr(lift)))
+    return kt, kvol, efc, lift
+
+
+def adg_last_error(ctx):
+    return load().adg_last_error(ctx).decode()
+
+
+def adg_destroy(ctx):
+    load().adg_destroy(ctx)

@@ -1,0 +1,501 @@
+// extern "C" entry points of include/adg.h: argument checks, user<->internal
+// reordering, host<->device copies and the time-stepping front end.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <exception>
+#include <stdexcept>
+#include <vector>
+
+#include "adg_internal.hpp"
+
+using adg::Ctx;
+
+namespace {
+
+template <typename F>
+int guard(adg_ctx* ctx, F&& f) {
+  try {
+    f();
+    if (ctx) ctx->c.last_error.clear();
+    return ADG_OK;
+  } catch (const std::bad_alloc&) {
+    if (ctx) ctx->c.last_error = "out of host memory";
+    return ADG_E_NOMEM;
+  } catch (const adg::AdgError& ex) {
+    if (ctx) ctx->c.last_error = ex.what();
+    return ex.code;
+  } catch (const std::exception& ex) {
+    if (ctx) ctx->c.last_error = ex.what();
+    return ADG_E_INVALID;
+  }
+}
+
+void need_init(const Ctx& c) {
+  if (!c.inited) adg::throw_err(ADG_E_STATE, "call adg_init first");
+}
+
+void check_cuda(cudaError_t e, const char* what) {
+  if (e != cudaSuccess) adg::throw_err(ADG_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+template <typename T>
+void put_dofs(Ctx& c, const double* Q) {
+  const int64_t per = (int64_t)c.S * 9 * c.B;
+  std::vector<T> buf((size_t)(c.nt * per));
+  for (int64_t i = 0; i < c.nt; ++i) {
+    const double* src = Q + c.order[i] * per;
+    T* dst = buf.data() + i * per;
+    for (int64_t k = 0; k < per; ++k) dst[k] = (T)src[k];
+  }
+  check_cuda(cudaMemcpyAsync(c.dQ, buf.data(), buf.size() * sizeof(T), cudaMemcpyHostToDevice, c.stream),
+             "dofs upload");
+  check_cuda(cudaStreamSynchronize(c.stream), "dofs upload");
+}
+template <typename T>
+void take_dofs(Ctx& c, double* Q) {
+  const int64_t per = (int64_t)c.S * 9 * c.B;
+  std::vector<T> buf((size_t)(c.nt * per));
+  check_cuda(cudaMemcpyAsync(buf.data(), c.dQ, buf.size() * sizeof(T), cudaMemcpyDeviceToHost, c.stream),
+             "dofs download");
+  check_cuda(cudaStreamSynchronize(c.stream), "dofs download");
+  for (int64_t i = 0; i < c.nt; ++i) {
+    const T* src = buf.data() + i * per;
+    double* dst = Q + c.order[i] * per;
+    for (int64_t k = 0; k < per; ++k) dst[k] = (double)src[k];
+  }
+}
+
+void run_ticks_to_boundary(Ctx& c) {
+  const int ticks = 1 << (c.ncl - 1);
+  while (c.tick % ticks) {
+    c.launch_tick((int)(c.tick % ticks), c.dtmin);
+    c.tick++;
+    c.time += c.dtmin;
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+void adg_default_config(adg_config* cfg) {
+  if (!cfg) return;
+  std::memset(cfg, 0, sizeof(*cfg));
+  cfg->degree = 5;
+  cfg->precision = ADG_FP64;
+  cfg->cfl = 0.35;
+  cfg->gravity = 9.81;
+  cfg->max_clusters = 1;
+  cfg->ensemble = 1;
+  cfg->device = 0;
+  cfg->cuda_stream = nullptr;
+}
+
+int adg_create(const adg_config* cfg, adg_ctx** out) {
+  if (!cfg || !out) return ADG_E_INVALID;
+  *out = nullptr;
+  if (cfg->degree < 1 || cfg->degree > 5 || (cfg->precision != ADG_FP64 && cfg->precision != ADG_FP32) ||
+      !(cfg->cfl > 0) || cfg->max_clusters < 1 || cfg->max_clusters > 16 || cfg->ensemble < 1 ||
+      cfg->gravity < 0)
+    return ADG_E_INVALID;
+  adg_ctx* c = new (std::nothrow) adg_ctx();
+  if (!c) return ADG_E_NOMEM;
+  c->c.cfg = *cfg;
+  *out = c;
+  return ADG_OK;
+}
+
+int adg_upload_mesh(adg_ctx* ctx, int64_t nv, const double* xyz, int64_t nt, const int64_t* tet_v,
+                    const int32_t* face_tag, const int64_t* face_partner) {
+  if (!ctx) return ADG_E_INVALID;
+  return guard(ctx, [&] {
+    Ctx& c = ctx->c;
+    if (c.inited) adg::throw_err(ADG_E_STATE, "mesh is fixed after adg_init");
+    if (nv < 4 || nt < 1 || !xyz || !tet_v || !face_tag || nt > (int64_t)1 << 30)
+      adg::throw_err(ADG_E_INVALID, "bad mesh arguments");
+    c.nv = nv;
+    c.nt = nt;
+    c.xyz.assign(xyz, xyz + 3 * nv);
+    c.tets.assign(tet_v, tet_v + 4 * nt);
+    c.tag.assign(face_tag, face_tag + 4 * nt);
+    if (face_partner) c.partner.assign(face_partner, face_partner + 4 * nt);
+    else c.partner.clear();
+    c.has_mesh = true;
+  });
+}
+
+int adg_upload_material(adg_ctx* ctx, const double* rho, const double* lambda, const double* mu) {
+  if (!ctx) return ADG_E_INVALID;
+  return guard(ctx, [&] {
+    Ctx& c = ctx->c;
+    if (!c.has_mesh) adg::throw_err(ADG_E_STATE, "upload the mesh first");
+    if (c.inited) adg::throw_err(ADG_E_STATE, "material is fixed after adg_init");
+    if (!rho || !lambda || !mu) adg::throw_err(ADG_E_INVALID, "null material array");
+    c.rho.assign(rho, rho + c.nt);
+    c.lam.assign(lambda, lambda + c.nt);
+    c.mu.assign(mu, mu + c.nt);
+    c.has_mat = true;
+  });
+}
+
+int adg_init(adg_ctx* ctx) {
+  if (!ctx) return ADG_E_INVALID;
+  return guard(ctx, [&] {
+    if (ctx->c.inited) adg::throw_err(ADG_E_STATE, "already initialised");
+    ctx->c.setup();
+  });
+}
+
+int adg_query(const adg_ctx* ctx, adg_info* out) {
+  if (!ctx || !out) return ADG_E_INVALID;
+  const Ctx& c = ctx->c;
+  if (!c.inited) return ADG_E_STATE;
+  std::memset(out, 0, sizeof(*out));
+  out->n_tets = c.nt;
+  out->n_basis = c.B;
+  out->n_face_nodes = c.Bf;
+  out->n_clusters = c.ncl;
+  for (int i = 0; i < c.ncl && i < 16; ++i) out->cluster_size[i] = c.cl_begin[i + 1] - c.cl_begin[i];
+  out->dt_min = c.dtmin;
+  out->macro_dt = c.dtmin * (double)(1 << (c.ncl - 1));
+  out->time = c.time;
+  out->n_gravity_faces = (int64_t)c.gfaces.size();
+  out->n_fault_faces = c.n_fault_faces;
+  int64_t upd = 0;
+  for (int i = 0; i < c.ncl; ++i) upd += (c.cl_begin[i + 1] - c.cl_begin[i]) * ((int64_t)1 << (c.ncl - 1 - i));
+  out->updates_per_macro = upd * c.S;
+  out->device_bytes = c.dev_bytes;
+  return ADG_OK;
+}
+
+int adg_set_dofs(adg_ctx* ctx, const double* Q) {
+  if (!ctx || !Q) return ADG_E_INVALID;
+  return guard(ctx, [&] {
+    need_init(ctx->c);
+    if (ctx->c.fp64) put_dofs<double>(ctx->c, Q);
+    else put_dofs<float>(ctx->c, Q);
+  });
+}
+
+int adg_get_dofs(adg_ctx* ctx, double* Q) {
+  if (!ctx || !Q) return ADG_E_INVALID;
+  return guard(ctx, [&] {
+    need_init(ctx->c);
+    if (ctx->c.fp64) take_dofs<double>(ctx->c, Q);
+    else take_dofs<float>(ctx->c, Q);
+  });
+}
+
+int adg_initial_points(adg_ctx* ctx, int* n_pts, double* xyz) {
+  if (!ctx || !n_pts) return ADG_E_INVALID;
+  return guard(ctx, [&] {
+    Ctx& c = ctx->c;
+    need_init(c);
+    std::vector<double> pts, w;
+    adg::tet_rule(2 * c.N + 4, pts, w);
+    const int nq = (int)w.size();
+    *n_pts = nq;
+    if (!xyz) return;
+    for (int64_t e = 0; e < c.nt; ++e) {
+      const double* P0 = &c.xyz[3 * c.tets[4 * e]];
+      for (int q = 0; q < nq; ++q)
+        for (int d = 0; d < 3; ++d) {
+          double x = P0[d];
+          for (int k = 0; k < 3; ++k) x += (c.xyz[3 * c.tets[4 * e + k + 1] + d] - P0[d]) * pts[3 * q + k];
+          xyz[((size_t)e * nq + q) * 3 + d] = x;
+        }
+    }
+  });
+}
+
+int adg_set_initial_values(adg_ctx* ctx, const double* values) {
+  if (!ctx || !values) return ADG_E_INVALID;
+  return guard(ctx, [&] {
+    Ctx& c = ctx->c;
+    need_init(c);
+    std::vector<double> pts, w;
+    adg::tet_rule(2 * c.N + 4, pts, w);
+    const int nq = (int)w.size();
+    std::vector<double> phi((size_t)nq * c.B);
+    for (int q = 0; q < nq; ++q) adg::eval_basis(c.ops, &pts[3 * q], &phi[(size_t)q * c.B]);
+    const int64_t per = (int64_t)c.S * 9 * c.B;
+    std::vector<double> Q((size_t)(c.nt * per), 0.0);
+    for (int64_t e = 0; e < c.nt; ++e)
+      for (int s = 0; s < c.S; ++s) {
+        const double* val = values + (((size_t)e * c.S + s) * nq) * 9;
+        double* out = Q.data() + e * per + (int64_t)s * 9 * c.B;
+        for (int q = 0; q < nq; ++q)
+          for (int p = 0; p < 9; ++p) {
+            const double v = w[q] * val[q * 9 + p];
+            for (int l = 0; l < c.B; ++l) out[p * c.B + l] += v * phi[(size_t)q * c.B + l];
+          }
+      }
+    if (c.fp64) put_dofs<double>(c, Q.data());
+    else put_dofs<float>(c, Q.data());
+  });
+}
+
+int adg_gravity_faces(adg_ctx* ctx, int64_t* elem_face, double* node_xyz) {
+  if (!ctx) return ADG_E_INVALID;
+  return guard(ctx, [&] {
+    Ctx& c = ctx->c;
+    need_init(c);
+    static const int fv[4][3] = {{1, 2, 3}, {0, 2, 3}, {0, 1, 3}, {0, 1, 2}};
+    for (size_t g = 0; g < c.gfaces.size(); ++g) {
+      if (elem_face) elem_face[g] = c.gfaces[g];
+      if (node_xyz) {
+        const int64_t e = c.gfaces[g] / 4;
+        const int f = (int)(c.gfaces[g] % 4);
+        const double* A = &c.xyz[3 * c.tets[4 * e + fv[f][0]]];
+        const double* Bv = &c.xyz[3 * c.tets[4 * e + fv[f][1]]];
+        const double* C = &c.xyz[3 * c.tets[4 * e + fv[f][2]]];
+        for (int n = 0; n < c.Bf; ++n) {
+          const double c1 = c.ops.node_chi[2 * n], c2 = c.ops.node_chi[2 * n + 1];
+          for (int d = 0; d < 3; ++d)
+            node_xyz[((size_t)g * c.Bf + n) * 3 + d] = A[d] + c1 * (Bv[d] - A[d]) + c2 * (C[d] - A[d]);
+        }
+      }
+    }
+  });
+}
+
+int adg_set_eta(adg_ctx* ctx, const double* eta) {
+  if (!ctx || !eta) return ADG_E_INVALID;
+  return guard(ctx, [&] {
+    Ctx& c = ctx->c;
+    need_init(c);
+    const size_t n = c.gfaces.size() * (size_t)c.S * c.Bf;
+    if (n) {
+      check_cuda(cudaMemcpyAsync(c.dEta, eta, n * 8, cudaMemcpyHostToDevice, c.stream), "eta upload");
+      check_cuda(cudaStreamSynchronize(c.stream), "eta upload");
+    }
+  });
+}
+
+int adg_read_ssh(adg_ctx* ctx, double* eta) {
+  if (!ctx || !eta) return ADG_E_INVALID;
+  return guard(ctx, [&] {
+    Ctx& c = ctx->c;
+    need_init(c);
+    const size_t n = c.gfaces.size() * (size_t)c.S * c.Bf;
+    if (n) {
+      check_cuda(cudaMemcpyAsync(eta, c.dEta, n * 8, cudaMemcpyDeviceToHost, c.stream), "eta download");
+      check_cuda(cudaStreamSynchronize(c.stream), "eta download");
+    }
+  });
+}
+
+int adg_advance(adg_ctx* ctx, int n_macro) {
+  if (!ctx || n_macro < 0) return ADG_E_INVALID;
+  return guard(ctx, [&] {
+    Ctx& c = ctx->c;
+    need_init(c);
+    run_ticks_to_boundary(c);
+    for (int i = 0; i < n_macro; ++i) {
+      c.run_macro(1.0);
+      c.tick += 1 << (c.ncl - 1);
+    }
+    c.check_err();
+  });
+}
+
+int adg_advance_to(adg_ctx* ctx, double t) {
+  if (!ctx) return ADG_E_INVALID;
+  return guard(ctx, [&] {
+    Ctx& c = ctx->c;
+    need_init(c);
+    run_ticks_to_boundary(c);
+    const double macro = c.dtmin * (double)(1 << (c.ncl - 1));
+    if (t < c.time - 1e-12 * macro) adg::throw_err(ADG_E_INVALID, "target time is in the past");
+    while (c.time + macro <= t + 1e-12 * macro) {
+      c.run_macro(1.0);
+      c.tick += 1 << (c.ncl - 1);
+    }
+    const double rest = t - c.time;
+    if (rest > 1e-12 * macro) {
+      c.run_macro(rest / macro);
+      c.tick += 1 << (c.ncl - 1);
+    }
+    c.time = t;
+    c.check_err();
+  });
+}
+
+int adg_step_tick(adg_ctx* ctx) {
+  if (!ctx) return ADG_E_INVALID;
+  return guard(ctx, [&] {
+    Ctx& c = ctx->c;
+    need_init(c);
+    const int ticks = 1 << (c.ncl - 1);
+    c.launch_tick((int)(c.tick % ticks), c.dtmin);
+    c.tick++;
+    c.time += c.dtmin;
+    c.check_err();
+  });
+}
+
+int adg_step_cluster(adg_ctx* ctx, int cl) {
+  if (!ctx) return ADG_E_INVALID;
+  return guard(ctx, [&] {
+    Ctx& c = ctx->c;
+    need_init(c);
+    if (cl < 0 || cl >= c.ncl) adg::throw_err(ADG_E_INVALID, "no such cluster");
+    const int ticks = 1 << (c.ncl - 1);
+    do {
+      c.launch_tick((int)(c.tick % ticks), c.dtmin);
+      c.tick++;
+      c.time += c.dtmin;
+    } while (c.tick % (1 << cl));
+    c.check_err();
+  });
+}
+
+int adg_sync(adg_ctx* ctx) {
+  if (!ctx) return ADG_E_INVALID;
+  return guard(ctx, [&] {
+    need_init(ctx->c);
+    ctx->c.check_err();
+  });
+}
+
+int adg_add_receivers(adg_ctx* ctx, int64_t n, const double* xyz) {
+  if (!ctx || n < 0 || (n && !xyz)) return ADG_E_INVALID;
+  return guard(ctx, [&] {
+    Ctx& c = ctx->c;
+    need_init(c);
+    std::vector<int64_t> elem((size_t)n, -1);
+    std::vector<double> phi((size_t)n * c.B);
+    for (int64_t r = 0; r < n; ++r) {
+      const double* x = xyz + 3 * r;
+      double best = -1e300;
+      int64_t be = -1;
+      double bxi[3] = {0, 0, 0};
+      for (int64_t e = 0; e < c.nt; ++e) {
+        const double* P[4];
+        for (int k = 0; k < 4; ++k) P[k] = &c.xyz[3 * c.tets[4 * e + k]];
+        double J[3][3];
+        for (int d = 0; d < 3; ++d)
+          for (int k = 0; k < 3; ++k) J[d][k] = P[k + 1][d] - P[0][d];
+        const double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
+                           J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+                           J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+        double b[3] = {x[0] - P[0][0], x[1] - P[0][1], x[2] - P[0][2]};
+        double xi[3];
+        for (int a = 0; a < 3; ++a) {  // Cramer
+          double M[3][3];
+          for (int d = 0; d < 3; ++d)
+            for (int k = 0; k < 3; ++k) M[d][k] = (k == a) ? b[d] : J[d][k];
+          xi[a] = (M[0][0] * (M[1][1] * M[2][2] - M[1][2] * M[2][1]) -
+                   M[0][1] * (M[1][0] * M[2][2] - M[1][2] * M[2][0]) +
+                   M[0][2] * (M[1][0] * M[2][1] - M[1][1] * M[2][0])) / det;
+        }
+        const double lmin = std::min(std::min(xi[0], xi[1]), std::min(xi[2], 1 - xi[0] - xi[1] - xi[2]));
+        if (lmin > best) {
+          best = lmin;
+          be = e;
+          bxi[0] = xi[0]; bxi[1] = xi[1]; bxi[2] = xi[2];
+        }
+      }
+      if (best < -1e-9) adg::throw_err(ADG_E_INVALID, "receiver outside the mesh");
+      elem[r] = c.inv[be];
+      adg::eval_basis(c.ops, bxi, &phi[(size_t)r * c.B]);
+    }
+    for (void* p : {(void*)c.dRecElem, (void*)c.dRecPhi, (void*)c.dRecOut}) {
+      if (!p) continue;
+      cudaFree(p);
+      for (auto& o : c.owned)
+        if (o == p) o = nullptr;
+    }
+    c.n_rec = n;
+    c.dRecElem = nullptr; c.dRecPhi = nullptr; c.dRecOut = nullptr;
+    if (!n) return;
+    check_cuda(cudaMalloc((void**)&c.dRecElem, n * 8), "receivers");
+    c.owned.push_back(c.dRecElem);
+    check_cuda(cudaMalloc((void**)&c.dRecPhi, n * c.B * 8), "receivers");
+    c.owned.push_back(c.dRecPhi);
+    check_cuda(cudaMalloc((void**)&c.dRecOut, n * c.S * 9 * 8), "receivers");
+    c.owned.push_back(c.dRecOut);
+    check_cuda(cudaMemcpy(c.dRecElem, elem.data(), n * 8, cudaMemcpyHostToDevice), "receivers");
+    check_cuda(cudaMemcpy(c.dRecPhi, phi.data(), n * c.B * 8, cudaMemcpyHostToDevice), "receivers");
+  });
+}
+
+int adg_read_receivers(adg_ctx* ctx, double* out) {
+  if (!ctx || !out) return ADG_E_INVALID;
+  return guard(ctx, [&] {
+    Ctx& c = ctx->c;
+    need_init(c);
+    if (!c.n_rec) return;
+    int rc = adg::launch_receivers(c.fp64, c.B, c.dQ, c.S, c.n_rec, c.dRecElem, c.dRecPhi, c.dRecOut, c.stream);
+    if (rc) adg::throw_err(ADG_E_CUDA, "receiver kernel");
+    check_cuda(cudaMemcpyAsync(out, c.dRecOut, c.n_rec * c.S * 9 * 8, cudaMemcpyDeviceToHost, c.stream),
+               "receiver download");
+    check_cuda(cudaStreamSynchronize(c.stream), "receiver download");
+  });
+}
+
+int adg_save_state(adg_ctx* ctx, void* buf, size_t* len) {
+  if (!ctx || !len) return ADG_E_INVALID;
+  return guard(ctx, [&] {
+    Ctx& c = ctx->c;
+    need_init(c);
+    const int ticks = 1 << (c.ncl - 1);
+    if (c.tick % ticks) adg::throw_err(ADG_E_STATE, "save only at a macro-step boundary");
+    const size_t qb = (size_t)c.nt * c.S * 9 * c.B * (c.fp64 ? 8 : 4);
+    const size_t eb = c.gfaces.size() * (size_t)c.S * c.Bf * 8;
+    const size_t need = 64 + qb + eb;
+    if (!buf) { *len = need; return; }
+    if (*len < need) adg::throw_err(ADG_E_INVALID, "buffer too small");
+    char* p = (char*)buf;
+    int64_t hdr[8] = {0x41444731, c.N, c.S, c.nt, c.fp64, (int64_t)c.gfaces.size(), c.tick, 0};
+    std::memcpy(p, hdr, sizeof(hdr));
+    std::memcpy(p + 56, &c.time, 8);
+    check_cuda(cudaStreamSynchronize(c.stream), "save");
+    check_cuda(cudaMemcpy(p + 64, c.dQ, qb, cudaMemcpyDeviceToHost), "save dofs");
+    if (eb) check_cuda(cudaMemcpy(p + 64 + qb, c.dEta, eb, cudaMemcpyDeviceToHost), "save eta");
+    *len = need;
+  });
+}
+
+int adg_load_state(adg_ctx* ctx, const void* buf, size_t len) {
+  if (!ctx || !buf) return ADG_E_INVALID;
+  return guard(ctx, [&] {
+    Ctx& c = ctx->c;
+    need_init(c);
+    const char* p = (const char*)buf;
+    int64_t hdr[8];
+    if (len < 64) adg::throw_err(ADG_E_INVALID, "state too short");
+    std::memcpy(hdr, p, sizeof(hdr));
+    const size_t qb = (size_t)c.nt * c.S * 9 * c.B * (c.fp64 ? 8 : 4);
+    const size_t eb = c.gfaces.size() * (size_t)c.S * c.Bf * 8;
+    if (hdr[0] != 0x41444731 || hdr[1] != c.N || hdr[2] != c.S || hdr[3] != c.nt || hdr[4] != (int64_t)c.fp64 ||
+        hdr[5] != (int64_t)c.gfaces.size() || len < 64 + qb + eb)
+      adg::throw_err(ADG_E_INVALID, "state does not match this context");
+    check_cuda(cudaStreamSynchronize(c.stream), "load");
+    check_cuda(cudaMemcpy(c.dQ, p + 64, qb, cudaMemcpyHostToDevice), "load dofs");
+    if (eb) check_cuda(cudaMemcpy(c.dEta, p + 64 + qb, eb, cudaMemcpyHostToDevice), "load eta");
+    c.tick = hdr[6];
+    std::memcpy(&c.time, p + 56, 8);
+  });
+}
+
+int adg_reference_operators(int degree, double* kt, double* kvol, double* efc, double* lift) {
+  try {
+    adg::RefOps o = adg::make_ref_ops(degree);
+    if (kt) std::memcpy(kt, o.kt.data(), o.kt.size() * 8);
+    if (kvol) std::memcpy(kvol, o.kvol.data(), o.kvol.size() * 8);
+    if (efc) std::memcpy(efc, o.efc.data(), o.efc.size() * 8);
+    if (lift) std::memcpy(lift, o.lift.data(), o.lift.size() * 8);
+    return ADG_OK;
+  } catch (...) {
+    return ADG_E_INVALID;
+  }
+}
+
+const char* adg_last_error(const adg_ctx* ctx) { return ctx ? ctx->c.last_error.c_str() : "null context"; }
+
+void adg_destroy(adg_ctx* ctx) { delete ctx; }
+
+}  // extern "C"

@@ -1,0 +1,665 @@
+// Host side of the C ABI (include/adg.h): mesh set-up, geometry, clustering,
+// Godunov flux matrices, device memory, the rate-2 LTS tick schedule and the
+// per-macro-step CUDA graph.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <stdexcept>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/adg.h"
+#include "kernels.cuh"
+#include "refmat.hpp"
+#include "adg_internal.hpp"
+
+using namespace adg;
+
+namespace {
+
+const int kFaceV[4][3] = {{1, 2, 3}, {0, 2, 3}, {0, 1, 3}, {0, 1, 2}};
+
+using Err = adg::AdgError;
+
+#define CK(call)                                                                          \
+  do {                                                                                    \
+    cudaError_t _e = (call);                                                              \
+    if (_e != cudaSuccess) throw Err(ADG_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(_e)); \
+  } while (0)
+
+// ---------------- small dense 9x9 helpers (row-major) ----------------
+typedef std::array<double, 81> M9;
+M9 mm(const M9& a, const M9& b) {
+  M9 r{};
+  for (int i = 0; i < 9; ++i)
+    for (int k = 0; k < 9; ++k) {
+      double v = a[i * 9 + k];
+      if (v == 0) continue;
+      for (int j = 0; j < 9; ++j) r[i * 9 + j] += v * b[k * 9 + j];
+    }
+  return r;
+}
+M9 madd(const M9& a, const M9& b) { M9 r; for (int i = 0; i < 81; ++i) r[i] = a[i] + b[i]; return r; }
+
+// x-Jacobian of Eq. (elasticity-pde) (the rotated 1-D problem uses A only)
+M9 jac_x(double rho, double lam, double mu) {
+  M9 A{};
+  A[0 * 9 + 6] = -(lam + 2 * mu);
+  A[1 * 9 + 6] = -lam;
+  A[2 * 9 + 6] = -lam;
+  A[3 * 9 + 7] = -mu;
+  A[5 * 9 + 8] = -mu;
+  A[6 * 9 + 0] = -1.0 / rho;
+  A[7 * 9 + 3] = -1.0 / rho;
+  A[8 * 9 + 5] = -1.0 / rho;
+  return A;
+}
+
+// Orthonormal frame (n, s, t) and the maps T (rotated -> global) and T^-1.
+void frame(const double n[3], double R[3][3]) {
+  int k = 0;
+  for (int d = 1; d < 3; ++d)
+    if (std::fabs(n[d]) < std::fabs(n[k])) k = d;
+  double a[3] = {0, 0, 0};
+  a[k] = 1;
+  double dot = a[0] * n[0] + a[1] * n[1] + a[2] * n[2];
+  double s[3] = {a[0] - dot * n[0], a[1] - dot * n[1], a[2] - dot * n[2]};
+  double ns = std::sqrt(s[0] * s[0] + s[1] * s[1] + s[2] * s[2]);
+  for (double& v : s) v /= ns;
+  double t[3] = {n[1] * s[2] - n[2] * s[1], n[2] * s[0] - n[0] * s[2], n[0] * s[1] - n[1] * s[0]};
+  for (int d = 0; d < 3; ++d) { R[d][0] = n[d]; R[d][1] = s[d]; R[d][2] = t[d]; }
+}
+const int kVo[6][2] = {{0, 0}, {1, 1}, {2, 2}, {0, 1}, {1, 2}, {0, 2}};
+// out = rotate(vec): fwd => stress R S R^T, vel R v ; inverse => R^T S R, R^T v
+void rot9(const double R[3][3], const double* in, double* out, bool to_global) {
+  double S[3][3];
+  for (int c = 0; c < 6; ++c) { S[kVo[c][0]][kVo[c][1]] = in[c]; S[kVo[c][1]][kVo[c][0]] = in[c]; }
+  double Rm[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) Rm[i][j] = to_global ? R[i][j] : R[j][i];
+  double Y[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int l = 0; l < 3; ++l) {
+      double acc = 0;
+      for (int j = 0; j < 3; ++j)
+        for (int k = 0; k < 3; ++k) acc += Rm[i][j] * S[j][k] * Rm[l][k];
+      Y[i][l] = acc;
+    }
+  for (int c = 0; c < 6; ++c) out[c] = Y[kVo[c][0]][kVo[c][1]];
+  for (int i = 0; i < 3; ++i) {
+    double acc = 0;
+    for (int j = 0; j < 3; ++j) acc += Rm[i][j] * in[6 + j];
+    out[6 + i] = acc;
+  }
+}
+void rot_mats(const double n[3], M9& T, M9& Ti) {
+  double R[3][3];
+  frame(n, R);
+  for (int c = 0; c < 9; ++c) {
+    double e[9] = {0}, o[9];
+    e[c] = 1;
+    rot9(R, e, o, true);
+    for (int r = 0; r < 9; ++r) T[r * 9 + c] = o[r];
+    rot9(R, e, o, false);
+    for (int r = 0; r < 9; ++r) Ti[r * 9 + c] = o[r];
+  }
+}
+
+// Middle state w^b = Mm w^- + Mp w^+ (Sec. 4.2, Eq. boundary-state; solid-solid
+// shear with the same welded form using Z_s).
+void middle_state(double Zpm, double Zpp, double Zsm, double Zsp, M9& Mm, M9& Mp) {
+  Mm.fill(0);
+  Mp.fill(0);
+  const double c = Zpm * Zpp / (Zpm + Zpp);
+  Mm[0 * 9 + 0] = 1 - c / Zpp; Mm[0 * 9 + 6] = -c;
+  Mp[0 * 9 + 0] = c / Zpp;     Mp[0 * 9 + 6] = c;
+  Mm[6 * 9 + 0] = -c / (Zpp * Zpm); Mm[6 * 9 + 6] = 1 - c / Zpm;
+  Mp[6 * 9 + 0] = c / (Zpp * Zpm);  Mp[6 * 9 + 6] = c / Zpm;
+  for (int r : {1, 2, 4}) Mm[r * 9 + r] = 1;  // irrelevant components (zero columns of A)
+  const int pairs[2][2] = {{3, 7}, {5, 8}};
+  for (auto& pr : pairs) {
+    const int ts = pr[0], tv = pr[1];
+    if (Zsm > 0 && Zsp > 0) {
+      const double cs = Zsm * Zsp / (Zsm + Zsp);
+      Mm[ts * 9 + ts] = 1 - cs / Zsp; Mm[ts * 9 + tv] = -cs;
+      Mp[ts * 9 + ts] = cs / Zsp;     Mp[ts * 9 + tv] = cs;
+      Mm[tv * 9 + ts] = -cs / (Zsp * Zsm); Mm[tv * 9 + tv] = 1 - cs / Zsm;
+      Mp[tv * 9 + ts] = cs / (Zsp * Zsm);  Mp[tv * 9 + tv] = cs / Zsm;
+    } else {
+      Mm[tv * 9 + tv] = 1;
+      if (Zsm > 0) Mm[tv * 9 + ts] = -1.0 / Zsm;
+    }
+  }
+}
+
+M9 diag9(std::initializer_list<double> d) {
+  M9 r{};
+  int i = 0;
+  for (double v : d) { r[i * 9 + i] = v; ++i; }
+  return r;
+}
+
+// ---------------- Gauss-Legendre on [0,1] (Newton on P_n) ----------------
+void gauss01(int n, std::vector<double>& x, std::vector<double>& w) {
+  x.resize(n);
+  w.resize(n);
+  for (int i = 0; i < n; ++i) {
+    double z = std::cos(M_PI * (i + 0.75) / (n + 0.5)), pp = 0;
+    for (int it = 0; it < 100; ++it) {
+      double p1 = 1, p2 = 0;
+      for (int j = 1; j <= n; ++j) { double p3 = p2; p2 = p1; p1 = ((2 * j - 1) * z * p2 - (j - 1) * p3) / j; }
+      pp = n * (z * p1 - p2) / (z * z - 1);
+      double dz = p1 / pp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    x[i] = 0.5 * (1 - z);
+    w[i] = 1.0 / ((1 - z * z) * pp * pp);  // = 0.5 * 2/((1-z^2) P'^2)
+  }
+}
+
+}  // namespace
+
+// ======================================================================
+namespace adg {
+
+[[noreturn]] void throw_err(int code, const std::string& m) { throw Err(code, m); }
+
+template <typename T>
+static void* upload_vec(const std::vector<double>& h, std::vector<void*>& owned, int64_t& bytes) {
+  std::vector<T> t(h.begin(), h.end());
+  void* d = nullptr;
+  if (t.empty()) return nullptr;
+  CK(cudaMalloc(&d, t.size() * sizeof(T)));
+  owned.push_back(d);
+  bytes += t.size() * sizeof(T);
+  CK(cudaMemcpy(d, t.data(), t.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return d;
+}
+template <typename T>
+static T* upload_raw(const std::vector<T>& h, std::vector<void*>& owned, int64_t& bytes) {
+  if (h.empty()) return nullptr;
+  void* d = nullptr;
+  CK(cudaMalloc(&d, h.size() * sizeof(T)));
+  owned.push_back(d);
+  bytes += h.size() * sizeof(T);
+  CK(cudaMemcpy(d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return (T*)d;
+}
+static void* dalloc(size_t n, std::vector<void*>& owned, int64_t& bytes) {
+  if (n == 0) return nullptr;
+  void* d = nullptr;
+  CK(cudaMalloc(&d, n));
+  owned.push_back(d);
+  bytes += n;
+  CK(cudaMemset(d, 0, n));
+  return d;
+}
+
+void Ctx::setup() {
+  if (!has_mesh || !has_mat) throw Err(ADG_E_STATE, "upload mesh and material before adg_init");
+  CK(cudaSetDevice(cfg.device));
+  const int64_t E = nt;
+  N = cfg.degree;
+  S = cfg.ensemble;
+  fp64 = cfg.precision == ADG_FP64;
+  ops = make_ref_ops(N);
+  if (ops.max_orth_err > 1e-12) throw Err(ADG_E_INVALID, "reference basis not orthonormal");
+  B = ops.B; Bf = ops.Bf; B1 = ops.B1;
+
+  // ---- geometry (user order)
+  std::vector<double> Jinv(9 * E), detJ(E), area(4 * E), nrm(12 * E), fcen(12 * E), h(E);
+  for (int64_t e = 0; e < E; ++e) {
+    const double* P[4];
+    for (int k = 0; k < 4; ++k) {
+      int64_t vid = tets[4 * e + k];
+      if (vid < 0 || vid >= nv) throw Err(ADG_E_MESH, "vertex index out of range");
+      P[k] = &xyz[3 * vid];
+    }
+    double J[3][3];
+    for (int d = 0; d < 3; ++d)
+      for (int c = 0; c < 3; ++c) J[d][c] = P[c + 1][d] - P[0][d];
+    double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
+                 J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+                 J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+    if (!(det > 0)) throw Err(ADG_E_MESH, "inverted or degenerate tetrahedron " + std::to_string(e));
+    detJ[e] = det;
+    // inverse: Jinv[a][d] = d xi_a / d x_d
+    double Ji[3][3];
+    Ji[0][0] = (J[1][1] * J[2][2] - J[1][2] * J[2][1]) / det;
+    Ji[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) / det;
+    Ji[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) / det;
+    Ji[1][0] = (J[1][2] * J[2][0] - J[1][0] * J[2][2]) / det;
+    Ji[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) / det;
+    Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) / det;
+    Ji[2][0] = (J[1][0] * J[2][1] - J[1][1] * J[2][0]) / det;
+    Ji[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) / det;
+    Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) / det;
+    for (int a = 0; a < 3; ++a)
+      for (int d = 0; d < 3; ++d) Jinv[9 * e + 3 * a + d] = Ji[a][d];
+    double asum = 0;
+    for (int f = 0; f < 4; ++f) {
+      const double* A = P[kFaceV[f][0]];
+      const double* Bv = P[kFaceV[f][1]];
+      const double* C = P[kFaceV[f][2]];
+      double u[3], w[3], cr[3];
+      for (int d = 0; d < 3; ++d) { u[d] = Bv[d] - A[d]; w[d] = C[d] - A[d]; }
+      cr[0] = u[1] * w[2] - u[2] * w[1];
+      cr[1] = u[2] * w[0] - u[0] * w[2];
+      cr[2] = u[0] * w[1] - u[1] * w[0];
+      double ar = std::sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
+      double out = 0;
+      for (int d = 0; d < 3; ++d) out += cr[d] * (A[d] - P[f][d]);
+      double sg = out > 0 ? 1.0 : -1.0;
+      for (int d = 0; d < 3; ++d) {
+        nrm[12 * e + 3 * f + d] = sg * cr[d] / ar;
+        fcen[12 * e + 3 * f + d] = (A[d] + Bv[d] + C[d]) / 3.0;
+      }
+      area[4 * e + f] = 0.5 * ar;
+      asum += 0.5 * ar;
+    }
+    h[e] = 6.0 * (det / 6.0) / asum;  // insphere diameter 2 r_in = 6 V / sum(A)
+  }
+
+  // ---- face connectivity: interior/fault by vertex triples, periodic by partner
+  std::vector<int64_t> nbr_u(4 * E, -1);
+  std::vector<int> nface_u(4 * E, -1), nperm_u(4 * E, -1);
+  {
+    std::unordered_map<std::string, int64_t> table;
+    table.reserve((size_t)(2 * E + 16));
+    auto key = [&](int64_t e, int f) {
+      int64_t v[3] = {tets[4 * e + kFaceV[f][0]], tets[4 * e + kFaceV[f][1]], tets[4 * e + kFaceV[f][2]]};
+      std::sort(v, v + 3);
+      return std::string((const char*)v, sizeof(v));
+    };
+    for (int64_t e = 0; e < E; ++e)
+      for (int f = 0; f < 4; ++f) {
+        int tg = tag[4 * e + f];
+        if (tg < 0 || tg > 6) throw Err(ADG_E_MESH, "unknown face tag");
+        if (tg != ADG_TAG_INTERIOR && tg != ADG_TAG_FAULT) continue;
+        std::string k = key(e, f);
+        auto it = table.find(k);
+        if (it == table.end()) {
+          table.emplace(k, 4 * e + f);
+        } else {
+          int64_t o = it->second;
+          if (o < 0) throw Err(ADG_E_MESH, "face shared by more than two tets");
+          int64_t e2 = o / 4;
+          int f2 = (int)(o % 4);
+          if (tag[4 * e2 + f2] != tg) throw Err(ADG_E_MESH, "fault face tagged on one side only");
+          nbr_u[4 * e + f] = e2; nface_u[4 * e + f] = f2;
+          nbr_u[4 * e2 + f2] = e; nface_u[4 * e2 + f2] = f;
+          it->second = -1;
+        }
+      }
+    for (auto& kv : table)
+      if (kv.second >= 0) throw Err(ADG_E_MESH, "interior face without a matching neighbour (tet " +
+                                                    std::to_string(kv.second / 4) + ")");
+    for (int64_t e = 0; e < E; ++e)
+      for (int f = 0; f < 4; ++f) {
+        if (tag[4 * e + f] != ADG_TAG_PERIODIC) continue;
+        if (partner.empty()) throw Err(ADG_E_MESH, "periodic face without partner array");
+        int64_t p = partner[4 * e + f];
+        if (p < 0 || p >= 4 * E || tag[p] != ADG_TAG_PERIODIC) throw Err(ADG_E_MESH, "bad periodic partner");
+        nbr_u[4 * e + f] = p / 4;
+        nface_u[4 * e + f] = (int)(p % 4);
+      }
+    // orientation: node permutation so that my node n sits on the neighbour's node perm[n]
+    for (int64_t e = 0; e < E; ++e)
+      for (int f = 0; f < 4; ++f) {
+        int64_t e2 = nbr_u[4 * e + f];
+        if (e2 < 0) continue;
+        int f2 = nface_u[4 * e + f];
+        int sig[3];
+        for (int s = 0; s < 3; ++s) {
+          int64_t gv = tets[4 * e + kFaceV[f][s]];
+          sig[s] = -1;
+          if (tag[4 * e + f] == ADG_TAG_PERIODIC) {
+            double sh[3];
+            for (int d = 0; d < 3; ++d) sh[d] = fcen[12 * e2 + 3 * f2 + d] - fcen[12 * e + 3 * f + d];
+            double best = 1e300;
+            for (int s2 = 0; s2 < 3; ++s2) {
+              const double* X = &xyz[3 * tets[4 * e2 + kFaceV[f2][s2]]];
+              double dd = 0;
+              for (int d = 0; d < 3; ++d) { double df = X[d] - (xyz[3 * gv + d] + sh[d]); dd += df * df; }
+              if (dd < best) { best = dd; sig[s] = s2; }
+            }
+          } else {
+            for (int s2 = 0; s2 < 3; ++s2)
+              if (tets[4 * e2 + kFaceV[f2][s2]] == gv) sig[s] = s2;
+          }
+        }
+        int pid = -1;
+        for (int p = 0; p < 6; ++p)
+          if (ops.vperm[3 * p] == sig[0] && ops.vperm[3 * p + 1] == sig[1] && ops.vperm[3 * p + 2] == sig[2]) pid = p;
+        if (pid < 0) throw Err(ADG_E_MESH, "could not orient a face pair");
+        nperm_u[4 * e + f] = pid;
+      }
+  }
+
+  // ---- CFL time steps and rate-2 clusters (Sec. 4.4)
+  std::vector<double> dte(E);
+  dtmin = 1e300;
+  for (int64_t e = 0; e < E; ++e) {
+    double cp = std::sqrt((lam[e] + 2 * mu[e]) / rho[e]);
+    if (!(cp > 0) || !(rho[e] > 0) || mu[e] < 0) throw Err(ADG_E_INVALID, "bad material");
+    dte[e] = cfg.cfl / (2 * N + 1) * h[e] / cp;
+    dtmin = std::min(dtmin, dte[e]);
+  }
+  std::vector<int> cl(E);
+  const int cmaxcap = std::max(1, std::min(cfg.max_clusters, 16)) - 1;
+  for (int64_t e = 0; e < E; ++e) {
+    int c = (int)std::floor(std::log2(dte[e] / dtmin) + 1e-12);
+    cl[e] = std::max(0, std::min(c, cmaxcap));
+  }
+  for (bool changed = true; changed;) {
+    changed = false;
+    for (int64_t e = 0; e < E; ++e)
+      for (int f = 0; f < 4; ++f) {
+        int64_t e2 = nbr_u[4 * e + f];
+        if (e2 < 0) continue;
+        int lim = tag[4 * e + f] == ADG_TAG_FAULT ? cl[e2] : cl[e2] + 1;
+        if (cl[e] > lim) { cl[e] = lim; changed = true; }
+      }
+  }
+  ncl = 0;
+  for (int64_t e = 0; e < E; ++e) ncl = std::max(ncl, cl[e] + 1);
+  // ---- internal order: by cluster, stable
+  order.resize(E);
+  for (int64_t e = 0; e < E; ++e) order[e] = e;
+  std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return cl[a] < cl[b]; });
+  inv.assign(E, 0);
+  for (int64_t i = 0; i < E; ++i) inv[order[i]] = i;
+  cl_begin.assign(ncl + 1, 0);
+  for (int64_t i = 0; i < E; ++i) cl_begin[cl[order[i]] + 1]++;
+  for (int c = 0; c < ncl; ++c) cl_begin[c + 1] += cl_begin[c];
+  cluster.resize(E);
+  for (int64_t i = 0; i < E; ++i) cluster[i] = cl[order[i]];
+
+  // ---- per-element / per-face device data (internal order)
+  std::vector<double> par((size_t)E * PAR), Fm((size_t)E * 324, 0.0), Fp((size_t)E * 324, 0.0);
+  std::vector<int> nbr((size_t)E * 4, -1), ninfo((size_t)E * 4, 0), gslot((size_t)E * 4, -1),
+      bslot(E, -1), dslot((size_t)E * 4, -1);
+  std::vector<double> gpar;
+  gfaces.clear();
+  int nb_slots = 0, nd_slots = 0, ng = 0;
+  // gravity faces in increasing user (tet*4+face) order
+  for (int64_t eu = 0; eu < E; ++eu)
+    for (int f = 0; f < 4; ++f)
+      if (tag[4 * eu + f] == ADG_TAG_GRAVITY) gfaces.push_back(4 * eu + f);
+  for (size_t g = 0; g < gfaces.size(); ++g) {
+    int64_t eu = gfaces[g] / 4;
+    gslot[inv[eu] * 4 + gfaces[g] % 4] = (int)g;
+  }
+  ng = (int)gfaces.size();
+  gpar.assign((size_t)ng * GPAR, 0.0);
+  for (int64_t i = 0; i < E; ++i) {
+    const int64_t eu = order[i];
+    for (int k = 0; k < 9; ++k) par[i * PAR + k] = Jinv[9 * eu + k];
+    par[i * PAR + 9] = rho[eu];
+    par[i * PAR + 10] = lam[eu];
+    par[i * PAR + 11] = mu[eu];
+    for (int f = 0; f < 4; ++f) par[i * PAR + 12 + f] = 2.0 * area[4 * eu + f] / detJ[eu];
+    const double Zpm = std::sqrt(rho[eu] * (lam[eu] + 2 * mu[eu])), Zsm = std::sqrt(rho[eu] * mu[eu]);
+    const M9 Am = jac_x(rho[eu], lam[eu], mu[eu]);
+    bool has_coarse = false;
+    for (int f = 0; f < 4; ++f) {
+      const double* n = &nrm[12 * eu + 3 * f];
+      M9 T, Ti;
+      rot_mats(n, T, Ti);
+      const M9 TA = mm(T, Am);
+      const int tg = tag[4 * eu + f];
+      M9 Mm, Mp, FmM{}, FpM{};
+      int kind = NK_NONE;
+      if (tg == ADG_TAG_INTERIOR || tg == ADG_TAG_PERIODIC) {
+        const int64_t e2u = nbr_u[4 * eu + f];
+        const double Zpp = std::sqrt(rho[e2u] * (lam[e2u] + 2 * mu[e2u])), Zsp = std::sqrt(rho[e2u] * mu[e2u]);
+        middle_state(Zpm, Zpp, Zsm, Zsp, Mm, Mp);
+        FmM = mm(mm(TA, Mm), Ti);
+        FpM = mm(mm(TA, Mp), Ti);
+        const int64_t e2 = inv[e2u];
+        nbr[i * 4 + f] = (int)e2;
+        const int c1 = cluster[i], c2 = cluster[e2];
+        kind = c1 == c2 ? NK_SAME : (c2 > c1 ? NK_COARSE : NK_FINE);
+        if (kind == NK_COARSE) has_coarse = true;
+        if (kind == NK_FINE) dslot[i * 4 + f] = nd_slots++;
+        ninfo[i * 4 + f] = nface_u[4 * eu + f] | (nperm_u[4 * eu + f] << 2) | (kind << 5);
+      } else if (tg == ADG_TAG_GRAVITY) {
+        middle_state(Zpm, Zpm, Zsm, Zsm, Mm, Mp);
+        // time-integrated middle state: w1 = -rho g H, w7 = eta^{n+1}-eta^n, w4 = w6 = 0,
+        // w8/w9 = w8/w9 - w4/w6 / Z_s (solid) ; Fg applies the shear part to int q^-
+        M9 Sm{};
+        const int pairs[2][2] = {{3, 7}, {5, 8}};
+        for (auto& pr : pairs) {
+          Sm[pr[1] * 9 + pr[1]] = 1;
+          if (Zsm > 0) Sm[pr[1] * 9 + pr[0]] = -1.0 / Zsm;
+        }
+        const M9 Fg = mm(mm(TA, Sm), Ti);
+        const int g = gslot[i * 4 + f];
+        double* gp = &gpar[(size_t)g * GPAR];
+        gp[0] = n[0]; gp[1] = n[1]; gp[2] = n[2];
+        gp[3] = Zpm;
+        gp[4] = rho[eu] * cfg.gravity / Zpm;
+        gp[5] = rho[eu] * cfg.gravity;
+        for (int k = 0; k < 81; ++k) gp[6 + k] = Fg[k];
+        for (int q = 0; q < 9; ++q) { gp[87 + q] = TA[q * 9 + 0]; gp[96 + q] = TA[q * 9 + 6]; }
+      } else if (tg == ADG_TAG_FAULT) {
+        kind = NK_FAULT;  // flux supplied by the rupture solver
+        nbr[i * 4 + f] = (int)inv[nbr_u[4 * eu + f]];
+        ninfo[i * 4 + f] = nface_u[4 * eu + f] | (nperm_u[4 * eu + f] << 2) | (kind << 5);
+      } else {
+        middle_state(Zpm, Zpm, Zsm, Zsm, Mm, Mp);
+        M9 G{};
+        if (tg == ADG_TAG_FREE) G = diag9({-1, 1, 1, -1, 1, -1, 1, 1, 1});
+        else if (tg == ADG_TAG_RIGID) G = diag9({1, 1, 1, -1, 1, -1, -1, 1, 1});
+        // absorbing: G = 0
+        FmM = mm(mm(TA, madd(Mm, mm(Mp, G))), Ti);
+      }
+      for (int k = 0; k < 81; ++k) {
+        Fm[(i * 4 + f) * 81 + k] = FmM[k];
+        Fp[(i * 4 + f) * 81 + k] = FpM[k];
+      }
+    }
+    if (has_coarse) bslot[i] = nb_slots++;
+  }
+  n_bslots = nb_slots;
+  n_dslots = nd_slots;
+  n_gslots = ng;
+  // fault faces are counted here; the rupture solver owns their state
+  n_fault_faces = 0;
+  for (int64_t e = 0; e < E; ++e)
+    for (int f = 0; f < 4; ++f)
+      if (tag[4 * e + f] == ADG_TAG_FAULT) ++n_fault_faces;
+  if (n_fault_faces) throw Err(ADG_E_INVALID, "fault faces need the rupture solver (adg_upload_fault)");
+
+  // ---- reference operators in device layouts (l-major / n-major)
+  std::vector<double> ktT((size_t)3 * B * B), kvolT((size_t)3 * B1 * B), efcT((size_t)4 * B * Bf),
+      liftT((size_t)4 * Bf * B);
+  for (int a = 0; a < 3; ++a)
+    for (int m = 0; m < B; ++m) {
+      for (int l = 0; l < B; ++l) ktT[((size_t)a * B + l) * B + m] = ops.kt[((size_t)a * B + m) * B + l];
+      for (int l = 0; l < B1; ++l) kvolT[((size_t)a * B1 + l) * B + m] = ops.kvol[((size_t)a * B + m) * B1 + l];
+    }
+  for (int f = 0; f < 4; ++f)
+    for (int n = 0; n < Bf; ++n)
+      for (int l = 0; l < B; ++l) {
+        efcT[((size_t)f * B + l) * Bf + n] = ops.efc[((size_t)f * Bf + n) * B + l];
+        liftT[((size_t)f * Bf + n) * B + l] = ops.lift[((size_t)f * B + l) * Bf + n];
+      }
+
+  // ---- device allocations
+  if (cfg.cuda_stream) {
+    stream = (cudaStream_t)cfg.cuda_stream;
+  } else {
+    CK(cudaStreamCreateWithFlags(&own_stream, cudaStreamNonBlocking));
+    stream = own_stream;
+  }
+  const size_t ts = fp64 ? 8 : 4;
+  const int64_t V = E * S;
+  dQ = dalloc((size_t)V * 9 * B * ts, owned, dev_bytes);
+  dTrace = dalloc((size_t)V * 36 * Bf * ts, owned, dev_bytes);
+  dBtrace = (double*)dalloc((size_t)nb_slots * S * 36 * Bf * 8, owned, dev_bytes);
+  dDtrace = dalloc((size_t)nd_slots * S * (N + 1) * 9 * Bf * ts, owned, dev_bytes);
+  dEta = (double*)dalloc((size_t)ng * S * Bf * 8, owned, dev_bytes);
+  if (fp64) {
+    dPar = upload_vec<double>(par, owned, dev_bytes);
+    dFm = upload_vec<double>(Fm, owned, dev_bytes);
+    dFp = upload_vec<double>(Fp, owned, dev_bytes);
+    dKt = upload_vec<double>(ktT, owned, dev_bytes);
+    dKvol = upload_vec<double>(kvolT, owned, dev_bytes);
+    dEfc = upload_vec<double>(efcT, owned, dev_bytes);
+    dLift = upload_vec<double>(liftT, owned, dev_bytes);
+  } else {
+    dPar = upload_vec<float>(par, owned, dev_bytes);
+    dFm = upload_vec<float>(Fm, owned, dev_bytes);
+    dFp = upload_vec<float>(Fp, owned, dev_bytes);
+    dKt = upload_vec<float>(ktT, owned, dev_bytes);
+    dKvol = upload_vec<float>(kvolT, owned, dev_bytes);
+    dEfc = upload_vec<float>(efcT, owned, dev_bytes);
+    dLift = upload_vec<float>(liftT, owned, dev_bytes);
+  }
+  dNbr = upload_raw<int>(nbr, owned, dev_bytes);
+  dNinfo = upload_raw<int>(ninfo, owned, dev_bytes);
+  dGslot = ng ? upload_raw<int>(gslot, owned, dev_bytes) : nullptr;
+  dBslot = nb_slots ? upload_raw<int>(bslot, owned, dev_bytes) : nullptr;
+  dDslot = nd_slots ? upload_raw<int>(dslot, owned, dev_bytes) : nullptr;
+  dGpar = ng ? upload_raw<double>(gpar, owned, dev_bytes) : nullptr;
+  dPerm = upload_raw<int>(ops.perm, owned, dev_bytes);
+  dErr = (unsigned int*)dalloc(sizeof(unsigned int), owned, dev_bytes);
+  // configure kernels once (outside any stream capture)
+  StepArgs a0 = base_args();
+  int rc = launch_local(fp64, N, a0, 0, stream);
+  if (rc) throw Err(ADG_E_CUDA, std::string("kernel configuration: ") + cudaGetErrorString((cudaError_t)rc));
+  tick = 0;
+  time = 0.0;
+  inited = true;
+}
+
+StepArgs Ctx::base_args() const {
+  StepArgs a{};
+  a.Q = dQ; a.trace = dTrace; a.btrace = dBtrace; a.dtrace = dDtrace; a.eta = dEta;
+  a.par = dPar; a.Fm = dFm; a.Fp = dFp; a.nbr = dNbr; a.ninfo = dNinfo;
+  a.gslot = dGslot; a.bslot = dBslot; a.dslot = dDslot;
+  a.ktT = dKt; a.kvolT = dKvol; a.efcT = dEfc; a.liftT = dLift; a.perm = dPerm; a.gpar = dGpar;
+  a.S = S; a.err = dErr;
+  return a;
+}
+
+static void taylor_int(int N, double ta, double tb, double* out) {
+  double fa = ta, fb = tb, fac = 1;
+  for (int k = 0; k <= N; ++k) {
+    fac *= (k + 1);
+    out[k] = (fb - fa) / fac;
+    fa *= ta;
+    fb *= tb;
+  }
+}
+
+// Launch the work of tick s of the rate-2 schedule with fine step dtm.
+void Ctx::launch_tick(int s, double dtm) {
+  StepArgs a = base_args();
+  for (int c = 0; c < ncl; ++c) {
+    if (s % (1 << c)) continue;
+    const int64_t n = cl_begin[c + 1] - cl_begin[c];
+    if (!n) continue;
+    const double dt = (double)(1 << c) * dtm;
+    a.v_begin = cl_begin[c] * S;
+    a.dt = dt;
+    taylor_int(N, 0.0, dt, a.tcoef);
+    a.btrace_mode = (s % (1 << (c + 1)) == 0) ? 1 : 2;
+    int rc = launch_local(fp64, N, a, n * S, stream);
+    if (rc) throw Err(ADG_E_CUDA, std::string("local kernel: ") + cudaGetErrorString((cudaError_t)rc));
+  }
+  for (int c = 0; c < ncl; ++c) {
+    if ((s + 1) % (1 << c)) continue;
+    const int64_t n = cl_begin[c + 1] - cl_begin[c];
+    if (!n) continue;
+    const double dt = (double)(1 << c) * dtm;
+    // position of this step inside the coarser neighbour's (2x longer) step
+    const int half = ((s + 1) / (1 << c) - 1) % 2;
+    a.v_begin = cl_begin[c] * S;
+    a.dt = dt;
+    taylor_int(N, half * dt, (half + 1) * dt, a.ccoef);
+    int rc = launch_neighbour(fp64, N, a, n * S, stream);
+    if (rc) throw Err(ADG_E_CUDA, std::string("neighbour kernel: ") + cudaGetErrorString((cudaError_t)rc));
+  }
+}
+
+int64_t Ctx::launches_per_macro() const {
+  int64_t L = 0;
+  const int ticks = 1 << (ncl - 1);
+  for (int s = 0; s < ticks; ++s)
+    for (int c = 0; c < ncl; ++c) {
+      if (cl_begin[c + 1] == cl_begin[c]) continue;
+      if (s % (1 << c) == 0) ++L;
+      if ((s + 1) % (1 << c) == 0) ++L;
+    }
+  return L;
+}
+
+void Ctx::run_macro(double scale) {
+  const int ticks = 1 << (ncl - 1);
+  const double dtm = dtmin * scale;
+  if (scale == 1.0 && use_graph) {
+    if (!graph_exec) {
+      cudaGraph_t g;
+      CK(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
+      try {
+        for (int s = 0; s < ticks; ++s) launch_tick(s, dtm);
+      } catch (...) {
+        cudaStreamEndCapture(stream, &g);
+        throw;
+      }
+      CK(cudaStreamEndCapture(stream, &g));
+      CK(cudaGraphInstantiate(&graph_exec, g, 0));
+      CK(cudaGraphDestroy(g));
+    }
+    CK(cudaGraphLaunch(graph_exec, stream));
+  } else {
+    for (int s = 0; s < ticks; ++s) launch_tick(s, dtm);
+  }
+  time += ticks * dtm;
+}
+
+void Ctx::check_err() {
+  CK(cudaStreamSynchronize(stream));
+  unsigned int h = 0;
+  CK(cudaMemcpy(&h, dErr, sizeof(h), cudaMemcpyDeviceToHost));
+  if (h) {
+    CK(cudaMemset(dErr, 0, sizeof(unsigned int)));
+    if (h & ERR_NAN) throw Err(ADG_E_NAN, "non-finite dofs detected");
+    if (h & ERR_NEWTON) throw Err(ADG_E_NEWTON, "friction Newton solve did not converge");
+    if (h & ERR_TIMEOUT) throw Err(ADG_E_TIMEOUT, "bounded device wait ran out");
+  }
+}
+
+Ctx::~Ctx() {
+  if (graph_exec) cudaGraphExecDestroy(graph_exec);
+  for (void* p : owned) cudaFree(p);
+  if (own_stream) cudaStreamDestroy(own_stream);
+}
+
+// Volume quadrature for projections: collapsed Gauss-Legendre, exact for degree deg.
+void tet_rule(int deg, std::vector<double>& pts, std::vector<double>& w) {
+  int n = std::max(1, (deg + 4) / 2);
+  std::vector<double> x, wx;
+  gauss01(n, x, wx);
+  pts.clear();
+  w.clear();
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j)
+      for (int k = 0; k < n; ++k) {
+        double u = x[i], v = x[j], s = x[k];
+        pts.push_back(u * (1 - v) * (1 - s));
+        pts.push_back(v * (1 - s));
+        pts.push_back(s);
+        w.push_back(wx[i] * wx[j] * wx[k] * (1 - v) * (1 - s) * (1 - s));
+      }
+}
+
+}  // namespace adg

@@ -1,0 +1,71 @@
+// ADER-DG element-update kernels (CUDA cores), templated on the working
+// precision T (double or float) and the polynomial degree N.
+//
+// Per element v (virtual index; ensembles stack S scenarios per element) over
+// one own step:
+//   local kernel      Sec. 4.1: Cauchy-Kovalewski predictor
+//                       D^{k+1} = -sum_a KT_a D^k A*_a^T,  KT_a[m][l] = int phi_m dphi_l/dxi_a,
+//                     time integral I = sum_k dt^{k+1}/(k+1)! D^k (Eq. taylor),
+//                     volume sum_a K_a I A*_a^T, local Godunov flux with F^-
+//                     (Sec. 4.2, Eq. numerical-flux) lifted from nodal face values,
+//                     gravitational faces (Sec. 4.3): exact (eta, H) Taylor
+//                     recursion in FP64 at the face nodes, flux from
+//                     int w1^b = -rho g H and int w7^b = eta^{n+1} - eta^n;
+//                     writes its own face traces (and LTS buffers/derivatives).
+//   neighbour kernel  gathers the neighbours' face traces (re-oriented by a
+//                     node permutation), applies F^+ and lifts.
+// Dofs layout: Q[v][9][B] (basis fastest); traces [v][4][9][Bf] (node fastest).
+#pragma once
+#include <cstdint>
+
+namespace adg {
+
+__host__ __device__ constexpr int nb3(int n) { return n < 0 ? 0 : (n + 1) * (n + 2) * (n + 3) / 6; }
+__host__ __device__ constexpr int nb2(int n) { return (n + 1) * (n + 2) / 2; }
+
+// neighbour-face kinds (ninfo bits 5..7)
+enum { NK_NONE = 0, NK_SAME = 1, NK_COARSE = 2, NK_FINE = 3, NK_FAULT = 4 };
+
+// per-element parameters (stride PAR): Jinv[9] (d xi_a/d x_d, row a), rho, lam, mu, scale[4]
+constexpr int PAR = 16;
+// per-gravity-face parameters (double, stride GPAR):
+//   n[3], Z, kappa = rho g / Z, rho*g, Fg[81], a1[9], a7[9]
+constexpr int GPAR = 6 + 81 + 18;
+
+struct StepArgs {
+  void* Q;              // T [V][9][B]
+  void* trace;          // T [V][4][9][Bf]
+  double* btrace;       // [nbslot*S][4][9][Bf]  (LTS buffer, FP64)
+  void* dtrace;         // T [ndslot*S][N+1][9][Bf] (LTS derivative traces)
+  double* eta;          // [ngslot*S][Bf]
+  const void* par;      // T [E][PAR]
+  const void* Fm;       // T [E][4][81]  row-major F[q][p]
+  const void* Fp;       // T [E][4][81]
+  const int* nbr;       // [E][4] internal neighbour element or -1
+  const int* ninfo;     // [E][4] j | perm<<2 | kind<<5
+  const int* gslot;     // [E][4] gravity slot or -1
+  const int* bslot;     // [E]    LTS buffer slot or -1
+  const int* dslot;     // [E][4] LTS derivative-trace slot or -1
+  const void* ktT;      // T [3][B(l)][B(m)]   KT_a[m][l] stored l-major
+  const void* kvolT;    // T [3][B1(l)][B(m)]  K_a[m][l]  stored l-major
+  const void* efcT;     // T [4][B(l)][Bf(n)]  phi_l at node n stored l-major
+  const void* liftT;    // T [4][Bf(n)][B(m)]  lift[f][m][n] stored n-major
+  const int* perm;      // [6][Bf]
+  const double* gpar;   // [ngslot][GPAR]
+  int64_t v_begin;      // first virtual element of the launch
+  int S;                // ensemble size
+  int btrace_mode;      // 0 none, 1 overwrite, 2 accumulate
+  double tcoef[8];      // dt^{k+1}/(k+1)!, k = 0..N (own step)
+  double ccoef[8];      // (tb^{k+1}-ta^{k+1})/(k+1)! on a coarser neighbour's expansion
+  double dt;            // own step (gravity ODE)
+  unsigned int* err;    // device error word
+};
+
+enum { ERR_NAN = 1u, ERR_TIMEOUT = 2u, ERR_NEWTON = 4u };
+
+// host-side launchers (kernels_f64.cu / kernels_f32.cu); return cudaError_t as int
+int launch_local(int fp64, int N, const StepArgs& a, int64_t nblocks, void* stream);
+int launch_neighbour(int fp64, int N, const StepArgs& a, int64_t nblocks, void* stream);
+int local_smem_bytes(int fp64, int N);
+
+}  // namespace adg

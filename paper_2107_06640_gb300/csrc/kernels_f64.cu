@@ -1,0 +1,12 @@
+// FP64 instantiations of the element-update kernels.
+#include "kernels_impl.cuh"
+
+namespace adg {
+int launch_local_f64(int N, const StepArgs& a, int64_t nb, void* st) {
+  return dispatch_local<double>(N, a, nb, (cudaStream_t)st);
+}
+int launch_neighbour_f64(int N, const StepArgs& a, int64_t nb, void* st) {
+  return dispatch_neighbour<double>(N, a, nb, (cudaStream_t)st);
+}
+int smem_f64(int N) { return smem_of<double>(N); }
+}  // namespace adg

@@ -1,0 +1,101 @@
+"""Convenience wrapper around one adg_ctx (marshalling only; see _lib)."""
+
+import numpy as np
+
+from . import _lib as L
+
+
+class Solver:
+    def __init__(self, xyz, tets, face_tag, rho, lam, mu, face_partner=None, degree=5,
+                 precision=L.ADG_FP64, cfl=0.35, gravity=9.81, max_clusters=1, ensemble=1,
+                 device=0, stream=None):
+        cfg = L.adg_default_config()
+        cfg.degree = degree
+        cfg.precision = precision
+        cfg.cfl = cfl
+        cfg.gravity = gravity
+        cfg.max_clusters = max_clusters
+        cfg.ensemble = ensemble
+        cfg.device = device
+        cfg.cuda_stream = stream
+        self.ctx = L.adg_create(cfg)
+        try:
+            L.adg_upload_mesh(self.ctx, xyz, tets, face_tag, face_partner)
+            L.adg_upload_material(self.ctx, rho, lam, mu)
+            L.adg_init(self.ctx)
+        except Exception:
+            L.adg_destroy(self.ctx)
+            self.ctx = None
+            raise
+        self.info = L.adg_query(self.ctx)
+        self.nt = int(self.info.n_tets)
+        self.B = self.info.n_basis
+        self.Bf = self.info.n_face_nodes
+        self.S = ensemble
+
+    def __del__(self):
+        if getattr(self, "ctx", None) is not None:
+            L.adg_destroy(self.ctx)
+            self.ctx = None
+
+    def query(self):
+        self.info = L.adg_query(self.ctx)
+        return self.info
+
+    @property
+    def time(self):
+        return L.adg_query(self.ctx).time
+
+    def set_dofs(self, Q):
+        """Q[tet][S][9][B] (or [tet][9][B] when S == 1)."""
+        L.adg_set_dofs(self.ctx, Q)
+
+    def get_dofs(self):
+        out = np.empty((self.nt, self.S, 9, self.B))
+        L.adg_get_dofs(self.ctx, out)
+        return out[:, 0] if self.S == 1 else out
+
+    def initial_points(self):
+        return L.adg_initial_points(self.ctx, self.nt)
+
+    def set_initial_values(self, values):
+        L.adg_set_initial_values(self.ctx, values)
+
+    def gravity_faces(self):
+        return L.adg_gravity_faces(self.ctx, int(self.info.n_gravity_faces), self.Bf)
+
+    def set_eta(self, eta):
+        L.adg_set_eta(self.ctx, eta)
+
+    def read_ssh(self):
+        out = np.empty((int(self.info.n_gravity_faces), self.S, self.Bf))
+        return L.adg_read_ssh(self.ctx, out)
+
+    def advance(self, n=1):
+        L.adg_advance(self.ctx, n)
+
+    def advance_to(self, t):
+        L.adg_advance_to(self.ctx, t)
+
+    def step_tick(self):
+        L.adg_step_tick(self.ctx)
+
+    def step_cluster(self, c):
+        L.adg_step_cluster(self.ctx, c)
+
+    def sync(self):
+        L.adg_sync(self.ctx)
+
+    def add_receivers(self, xyz):
+        self._nrec = len(xyz)
+        L.adg_add_receivers(self.ctx, xyz)
+
+    def read_receivers(self):
+        out = np.empty((self._nrec, self.S, 9))
+        return L.adg_read_receivers(self.ctx, out)
+
+    def save_state(self):
+        return L.adg_save_state(self.ctx)
+
+    def load_state(self, buf):
+        L.adg_load_state(self.ctx, buf)
