@@ -1,0 +1,333 @@
+"""Benchmark: ADER-DG element-updates/s at order 6 (degree N=5).
+
+Workload: the coupled ocean-crust box, 100 x 100 x 40 km, 80 x 80 hex columns
+x 39 layers (2 km water in 4 layers over 35 crust layers), 1,497,600 tets,
+gravitational free surface on top, absorbing elsewhere, seafloor v_z pulse
+(sigma 5 km horizontally, 1 km vertically) plus seeded higher-mode noise.  One
+step = one global time step of the whole element update (CK predictor,
+volume, local flux with the gravity-face ODE, neighbour flux) for every tet,
+i.e. one macro step of the C ABI, replayed as a CUDA graph.
+
+`value` is the FP32 path (the fast form); the FP64 path is measured in the
+same run (`fp64`).  Dofs (3 GB FP32 / 6 GB FP64) are far larger than L2
+(129 MB), so no flush is needed between steps.  With --gpus N (torchrun),
+every rank runs an independent replica with its own source position (weak
+scaling, no collective on the data path).
+
+--impl reference times the FP64 oracle (test infrastructure) as it stands on
+the host cores, one bounded sample of the workload per step.
+"""
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_DEG = 5
+METRIC = "ADER-DG element-updates/s at order 6, FP32/batched vs FP64; % of roofline"
+UNIT = "element-updates/s"
+WORKLOAD = "coupled ocean-crust box 100x100x40 km, 1,497,600 tets, degree 5, gravitational surface"
+
+
+def flops_per_update(N):
+    """Algorithmic flop count per element update (fixed counting convention)."""
+    nb = lambda n: (n + 1) * (n + 2) * (n + 3) // 6 if n >= 0 else 0
+    B, Bf = nb(N), (N + 1) * (N + 2) // 2
+    pred = sum(54 * nb(N - k - 1) * nb(N - k) + 486 * nb(N - k - 1) for k in range(N)) + 18 * sum(
+        nb(N - k) for k in range(N + 1))
+    vol = 3 * (18 * B * nb(N - 1) + 162 * B)
+    loc = 4 * (36 * Bf * B + 162 * Bf)
+    nbf = loc + 72 * Bf * Bf
+    return {"pred": pred, "vol": vol, "loc": loc, "nb": nbf, "local_kernel": pred + vol + loc,
+            "neighbour_kernel": nbf, "total": pred + vol + loc + nbf}
+
+
+def bytes_per_update(N, w):
+    """Algorithmic HBM bytes per element update and kernel: each kernel reads and
+    writes the dofs once and writes (local) or reads (neighbour) 4 face traces."""
+    B, Bf = (N + 1) * (N + 2) * (N + 3) // 6, (N + 1) * (N + 2) // 2
+    per_kernel = (2 * 9 * B + 4 * 9 * Bf) * w
+    return {"local_kernel": per_kernel, "neighbour_kernel": per_kernel}
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def alu_peak_tflops(fp64, sm_mhz):
+    """CUDA-core peak: 152 SMs x 128 FP32 lanes x 2 flop/FMA x clock; FP64 from
+    the 1.25 TFLOP/s nominal at the 2070 MHz maximum, scaled to the clock."""
+    if fp64:
+        return 1.25 * sm_mhz / 2070.0
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+class ClockSampler:
+    def __init__(self, path):
+        self.path = path
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,"
+                 "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+                 "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except Exception:
+                self.p.kill()
+            self.f.close()
+
+    def summary(self, device):
+        if self.p is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9 or f[0] != str(device):
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def make_workload(seed):
+    import numpy as np
+    from synthetic.workloads import coupled_box, random_dofs, seafloor_pulse
+    m, mat = coupled_box()
+    rng = np.random.default_rng(seed)
+    x0, y0 = rng.uniform(30e3, 70e3, 2)
+    pulse = seafloor_pulse(x0, y0, m.extra["seafloor"])
+    B = (N_DEG + 1) * (N_DEG + 2) * (N_DEG + 3) // 6
+    # constant mode of the orthonormal basis is phi_0 = sqrt(6): the projection of
+    # the pulse sampled at the centroid, plus small seeded noise in all modes
+    Q = random_dofs((m.nt, 9, B), seed, decay=1.0, N=N_DEG) * 1e-4
+    Q[:, :, 0] += pulse(m.centroids()) / np.sqrt(6.0)
+    return m, mat, Q
+
+
+def cpu_sample_run(seconds, steps=None):
+    """Time the oracle on a bounded sample of the workload (in-process)."""
+    import numpy as np
+    from oracle.ader import Oracle
+    from synthetic.workloads import coupled_box, random_dofs
+    # a 6 x 6 hex-column piece of the same box: same spacing, materials, faces
+    m, mat = coupled_box(nxy=6, n_water=4, n_crust=3, L=100e3 * 6 / 80, depth=2e3 + 3 * 38e3 / 35,
+                         water=2e3)
+    o = Oracle(m.xyz, m.tets, m.face_tag, m.face_partner, *mat, N_DEG, cfl=0.35)
+    o.Q = random_dofs((m.nt, o.B, 9), 0, N=N_DEG) * 1e-3
+    n = 0
+    t0 = time.perf_counter()
+    while True:
+        o.step_gts()
+        n += 1
+        el = time.perf_counter() - t0
+        if (steps is not None and n >= steps) or (steps is None and el >= seconds):
+            break
+    return m.nt * n / el, m.nt, n, el
+
+
+def cpu_baseline(seconds=12.0):
+    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = ("import sys, json; sys.path.insert(0, %r); import bench; v, nt, n, el = bench.cpu_sample_run(%f); "
+            "print(json.dumps([v, nt, n, el]))" % (ROOT, seconds))
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=600)
+    v, nt, n, el = json.loads(r.stdout.strip().splitlines()[-1])
+    return {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{nt}-tet 6x6-column piece of the same box (N=5, FP64, numpy), {n} global steps in {el:.1f} s, single thread"}
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    steps, warm = args.steps, args.warmup
+    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = ("import sys, json; sys.path.insert(0, %r); import bench; "
+            "bench.cpu_sample_run(0, steps=%d); v, nt, n, el = bench.cpu_sample_run(0, steps=%d); "
+            "print(json.dumps([v, nt, n, el]))" % (ROOT, max(1, warm), steps))
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
+    v, nt, n, el = json.loads(r.stdout.strip().splitlines()[-1])
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": steps, "warmup": warm, "ms_per_step": 1e3 * el / n, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD + " (oracle: bounded sample per step)", "degree": N_DEG},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{nt}-tet piece of the box per step, single thread"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0:
+        import __graft_entry__
+        __graft_entry__.build()
+    if world > 1:
+        dist.barrier()
+    import paper_2107_06640_gb300 as pkg
+    from paper_2107_06640_gb300 import Solver
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    m, (rho, lam, mu), Q0 = make_workload(seed=rank)
+    stream = torch.cuda.current_stream()
+    res = {}
+    for prec, steps, warm in ((pkg.ADG_FP32, args.steps, args.warmup), (pkg.ADG_FP64, args.fp64_steps, 1)):
+        s = Solver(m.xyz, m.tets, m.face_tag, rho, lam, mu, degree=N_DEG, precision=prec, cfl=0.35,
+                   device=local, stream=stream.cuda_stream)
+        s.set_dofs(Q0)
+        s.set_eta(np.zeros((int(s.info.n_gravity_faces), 1, s.Bf)))
+        upd = int(s.info.updates_per_macro)
+        s.advance(warm)
+        barrier()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else "_work",
+                                       f"clocks_r{rank}_{prec}.csv")) as cs:
+            ev0.record(stream)
+            s.advance(steps)
+            ev1.record(stream)
+            barrier()
+        ms = max_over_ranks(ev0.elapsed_time(ev1))
+        # per-kernel durations (CUDA events on the library stream)
+        kms, kcnt = pkg._lib.adg_profile(s.ctx, 2)
+        res[prec] = dict(solver=s, ms=ms, steps=steps, upd=upd, kms=kms, kcnt=kcnt,
+                         clocks=cs.summary(local), launches=int(kcnt.sum() // 2))
+        if prec == pkg.ADG_FP64:
+            del s
+            res[prec]["solver"] = None
+    r32 = res[pkg.ADG_FP32]
+    upd = r32["upd"]
+    value = upd * world * r32["steps"] / (r32["ms"] * 1e-3)
+    ms_step = r32["ms"] / r32["steps"]
+    r64 = res[pkg.ADG_FP64]
+    value64 = upd * world * r64["steps"] / (r64["ms"] * 1e-3)
+
+    # e2e through the public API with host buffers: upload dofs, one step, download
+    s = r32["solver"]
+    Qh = np.ascontiguousarray(Q0)
+    out = np.empty((s.nt, 1, 9, s.B))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        s.set_dofs(Qh)
+        s.advance(1)
+        pkg._lib.adg_get_dofs(s.ctx, out)
+    barrier()
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    e2e_val = upd * world * args.e2e_steps / e2e_s
+    bytes_q = s.nt * 9 * s.B * 4
+
+    peaks, src = load_peaks()
+    fl = flops_per_update(N_DEG)
+    by = bytes_per_update(N_DEG, 4)
+    kms = r32["kms"]
+    dom = 0 if kms[0] >= kms[1] else 1
+    kname = ["local_kernel", "neighbour_kernel"][dom]
+    clk = r32["clocks"]
+    sm_mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    alu_peak = alu_peak_tflops(False, peaks.get("sm_max_mhz", 2070.0))
+    achieved_flops = fl[kname] * s.nt / (kms[dom] * 1e-3) / 1e12
+    achieved_bytes = by[kname] * s.nt / (kms[dom] * 1e-3) / 1e9
+    frac_alu = achieved_flops / alu_peak
+    frac_hbm = achieved_bytes / peaks["hbm_gbs"]
+    if frac_alu >= frac_hbm:
+        roof = {"bound": "alu", "achieved": achieved_flops, "peak": alu_peak, "unit": "TFLOP/s",
+                "frac": frac_alu, "traffic": None}
+    else:
+        roof = {"bound": "hbm", "achieved": achieved_bytes, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": frac_hbm, "traffic": None}
+    roof.update({"kernel": kname, "peak_source": src if roof["bound"] == "hbm" else
+                 "derived: 152 SM x 128 FP32 lanes x 2 x 2070 MHz", "ms_per_launch": kms[dom],
+                 "hbm_frac": frac_hbm, "alu_frac": frac_alu,
+                 "kernel_ms": {"local": kms[0], "neighbour": kms[1]}})
+    r64k = r64["kms"]
+    fp64_alu = fl["local_kernel"] * s.nt / (r64k[0] * 1e-3) / 1e12
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": r32["steps"],
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_tets": s.nt, "degree": N_DEG, "time_stepping": "global (1 cluster)",
+                   "parallelism": f"replicas x{world}", "l2": "inputs larger than L2 (3 GB FP32 dofs)"},
+        "gflops": value * fl["total"] / 1e9,
+        "fp64": {"value": value64, "unit": UNIT, "steps": r64["steps"], "ms_per_step": r64["ms"] / r64["steps"],
+                 "local_kernel_tflops": fp64_alu, "fp64_peak_tflops_nominal": 1.25,
+                 "kernel_ms": {"local": r64k[0], "neighbour": r64k[1]}, "clocks": r64["clocks"]},
+        "roofline": roof,
+        "clocks": clk,
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": bytes_q, "d2h_bytes_per_step": bytes_q,
+                "steps": args.e2e_steps, "note": "adg_set_dofs + adg_advance(1) + adg_get_dofs, host double arrays"},
+        "gpu_launches": r32["launches"] * r32["steps"],
+    }
+    if rank == 0 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

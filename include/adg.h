@@ -146,6 +146,13 @@ int adg_step_cluster(adg_ctx* ctx, int c);
 /* Block until queued work is done; reports device-side errors (NaN...). */
 int adg_sync(adg_ctx* ctx);
 
+/* Per-kernel timing for roofline reports: runs n_macro macro steps with
+ * eager (non-graph) launches and a CUDA event pair around every kernel on the
+ * library stream.  ms[k] = mean duration of one launch of kernel kind k,
+ * launches[k] = number of launches, k = 0 local (predictor, volume, local
+ * flux), 1 neighbour flux.  Advances the simulation like adg_advance. */
+int adg_profile(adg_ctx* ctx, int n_macro, double* ms, int64_t* launches);
+
 /* Receivers: physical points; readout of q at the current time (whole ticks
  * synchronised: at macro-step boundaries), out[n][S][9] (host, double). */
 int adg_add_receivers(adg_ctx* ctx, int64_t n, const double* xyz);

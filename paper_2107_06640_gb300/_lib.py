@@ -60,6 +60,7 @@ _SIGS = {
     "adg_step_tick": (C.c_int, [_P]),
     "adg_step_cluster": (C.c_int, [_P, C.c_int]),
     "adg_sync": (C.c_int, [_P]),
+    "adg_profile": (C.c_int, [_P, C.c_int, _P, _P]),
     "adg_add_receivers": (C.c_int, [_P, C.c_int64, _P]),
     "adg_read_receivers": (C.c_int, [_P, _P]),
     "adg_save_state": (C.c_int, [_P, _P, C.POINTER(C.c_size_t)]),
@@ -202,6 +203,13 @@ def adg_step_cluster(ctx, c):
 
 def adg_sync(ctx):
     _check(ctx, load().adg_sync(ctx))
+
+
+def adg_profile(ctx, n_macro):
+    ms = np.zeros(2)
+    cnt = np.zeros(2, np.int64)
+    _check(ctx, load().adg_profile(ctx, int(n_macro), _ptr(ms), _ptr(cnt)))
+    return ms, cnt
 
 
 def adg_add_receivers(ctx, xyz):

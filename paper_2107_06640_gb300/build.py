@@ -58,7 +58,8 @@ def build(force=False, verbose=False):
         jobs.append([nvcc, *ARCH, "-lineinfo", *common, "-c", os.path.join(CSRC, f), "-o",
                      os.path.join(obj, f + ".o")])
     for f in cpp:
-        jobs.append([nvcc, *common, "-c", os.path.join(CSRC, f), "-o", os.path.join(obj, f + ".o")])
+        jobs.append([nvcc, *common, "-Xcompiler", "-fopenmp", "-c", os.path.join(CSRC, f), "-o",
+                     os.path.join(obj, f + ".o")])
 
     def run(cmd):
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -72,7 +73,8 @@ def build(force=False, verbose=False):
                 print(r.stdout + r.stderr)
     objs = [os.path.join(obj, f + ".o") for f in cu + cpp]
     tmp = LIB + ".tmp"
-    r = subprocess.run([nvcc, *ARCH, "-shared", "-o", tmp, *objs], capture_output=True, text=True)
+    r = subprocess.run([nvcc, *ARCH, "-shared", "-Xcompiler", "-fopenmp", "-o", tmp, *objs],
+                       capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n" + r.stdout + r.stderr)
     os.replace(tmp, LIB)

@@ -44,6 +44,7 @@ template <typename T>
 void put_dofs(Ctx& c, const double* Q) {
   const int64_t per = (int64_t)c.S * 9 * c.B;
   std::vector<T> buf((size_t)(c.nt * per));
+#pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < c.nt; ++i) {
     const double* src = Q + c.order[i] * per;
     T* dst = buf.data() + i * per;
@@ -60,6 +61,7 @@ void take_dofs(Ctx& c, double* Q) {
   check_cuda(cudaMemcpyAsync(buf.data(), c.dQ, buf.size() * sizeof(T), cudaMemcpyDeviceToHost, c.stream),
              "dofs download");
   check_cuda(cudaStreamSynchronize(c.stream), "dofs download");
+#pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < c.nt; ++i) {
     const T* src = buf.data() + i * per;
     double* dst = Q + c.order[i] * per;
@@ -350,6 +352,49 @@ int adg_step_cluster(adg_ctx* ctx, int cl) {
     } while (c.tick % (1 << cl));
     c.check_err();
   });
+}
+
+int adg_profile(adg_ctx* ctx, int n_macro, double* ms, int64_t* launches) {
+  if (!ctx || n_macro < 1 || !ms || !launches) return ADG_E_INVALID;
+  std::vector<Ctx::ProfEv> evs;
+  int rc = guard(ctx, [&] {
+    Ctx& c = ctx->c;
+    need_init(c);
+    run_ticks_to_boundary(c);
+    const int ticks = 1 << (c.ncl - 1);
+    c.prof = &evs;
+    try {
+      for (int i = 0; i < n_macro; ++i)
+        for (int s = 0; s < ticks; ++s) {
+          c.launch_tick(s, c.dtmin);
+          c.tick++;
+          c.time += c.dtmin;
+        }
+    } catch (...) {
+      c.prof = nullptr;
+      throw;
+    }
+    c.prof = nullptr;
+    check_cuda(cudaStreamSynchronize(c.stream), "profile");
+    double tot[2] = {0, 0};
+    int64_t cnt[2] = {0, 0};
+    for (auto& e : evs) {
+      float t = 0;
+      check_cuda(cudaEventElapsedTime(&t, e.a, e.b), "profile events");
+      tot[e.kind] += t;
+      cnt[e.kind] += 1;
+    }
+    for (int k = 0; k < 2; ++k) {
+      ms[k] = cnt[k] ? tot[k] / cnt[k] : 0.0;
+      launches[k] = cnt[k];
+    }
+    c.check_err();
+  });
+  for (auto& e : evs) {
+    cudaEventDestroy(e.a);
+    cudaEventDestroy(e.b);
+  }
+  return rc;
 }
 
 int adg_sync(adg_ctx* ctx) {

@@ -572,7 +572,14 @@ void Ctx::launch_tick(int s, double dtm) {
     a.dt = dt;
     taylor_int(N, 0.0, dt, a.tcoef);
     a.btrace_mode = (s % (1 << (c + 1)) == 0) ? 1 : 2;
+    ProfEv ev{0, nullptr, nullptr};
+    if (prof) {
+      CK(cudaEventCreate(&ev.a));
+      CK(cudaEventCreate(&ev.b));
+      CK(cudaEventRecord(ev.a, stream));
+    }
     int rc = launch_local(fp64, N, a, n * S, stream);
+    if (prof) { CK(cudaEventRecord(ev.b, stream)); prof->push_back(ev); }
     if (rc) throw Err(ADG_E_CUDA, std::string("local kernel: ") + cudaGetErrorString((cudaError_t)rc));
   }
   for (int c = 0; c < ncl; ++c) {
@@ -585,7 +592,14 @@ void Ctx::launch_tick(int s, double dtm) {
     a.v_begin = cl_begin[c] * S;
     a.dt = dt;
     taylor_int(N, half * dt, (half + 1) * dt, a.ccoef);
+    ProfEv ev{1, nullptr, nullptr};
+    if (prof) {
+      CK(cudaEventCreate(&ev.a));
+      CK(cudaEventCreate(&ev.b));
+      CK(cudaEventRecord(ev.a, stream));
+    }
     int rc = launch_neighbour(fp64, N, a, n * S, stream);
+    if (prof) { CK(cudaEventRecord(ev.b, stream)); prof->push_back(ev); }
     if (rc) throw Err(ADG_E_CUDA, std::string("neighbour kernel: ") + cudaGetErrorString((cudaError_t)rc));
   }
 }

@@ -59,6 +59,9 @@ struct Ctx {
   unsigned int* dErr = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
   bool use_graph = true;
+  // per-kernel profiling (adg_profile)
+  struct ProfEv { int kind; cudaEvent_t a, b; };
+  std::vector<ProfEv>* prof = nullptr;
   // receivers
   int64_t n_rec = 0;
   int64_t* dRecElem = nullptr;

@@ -1,0 +1,243 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle on the
+same seeded inputs.  Bar: relative L2 <= 1e-10 for the FP64 path (dofs and
+sea-surface height); FP32 within the tolerance stated in each test."""
+
+import numpy as np
+import pytest
+
+import synthetic as syn
+from synthetic.workloads import plane_wave_case, plane_wave_field, random_dofs
+from tests._cases import (eta_poly, make_pair, node_chi, oracle_eta_at_nodes, rel_l2, small_coupled,
+                          submesh, to_gpu_layout, to_oracle_layout)
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-10
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2107_06640_gb300 import build
+    build.build()
+
+
+def test_plane_wave_small_config_fp64():
+    # 8^3 hexes x 6 tets periodic, rho=1 lambda=2 mu=1, N=3, CFL 0.5, 100 steps
+    m, mat = plane_wave_case(8)
+    o, s = make_pair(m, mat, 3, cfl=0.5)
+    assert s.nt == 3072 and np.isclose(s.info.dt_min, o.dtmin, rtol=1e-14)
+    o.Q = o.project(plane_wave_field(0.0))
+    s.set_dofs(to_gpu_layout(o.Q))
+    for _ in range(100):
+        o.step_gts()
+    s.advance(100)
+    Qg = to_oracle_layout(s.get_dofs())
+    assert rel_l2(Qg, o.Q) <= FP64_TOL, rel_l2(Qg, o.Q)
+    ref = np.linalg.norm(o.l2_error(plane_wave_field(o.t), Q=0 * o.Q))
+    assert np.linalg.norm(o.l2_error(plane_wave_field(o.t), Q=Qg)) / ref < 2e-4
+    assert np.isclose(s.time, o.t, rtol=1e-13)
+
+
+def _coupled_run(N, precision, steps=3, seed=1):
+    m, mat = small_coupled()
+    o, s = make_pair(m, mat, N, precision=precision, cfl=0.5)
+    Q0 = random_dofs((m.nt, s.B, 9), seed, N=N) * 1e-3
+    o.Q = Q0.copy()
+    s.set_dofs(to_gpu_layout(Q0))
+    ef, nxyz = s.gravity_faces()
+    assert len(ef) == int(np.sum(m.face_tag == syn.TAG_GRAVITY)) > 0
+    s.set_eta(eta_poly(nxyz[..., 0], nxyz[..., 1])[:, None, :])
+    for e, f in np.argwhere(m.face_tag == syn.TAG_GRAVITY):
+        o.eta[e, f] = eta_poly(o.face_x[e, f, :, 0], o.face_x[e, f, :, 1])
+    for _ in range(steps):
+        o.step_gts()
+    s.advance(steps)
+    Qg = to_oracle_layout(s.get_dofs())
+    eta_g = s.read_ssh()[:, 0, :]
+    eta_o = oracle_eta_at_nodes(o, ef, node_chi(N), N)
+    return rel_l2(Qg, o.Q), rel_l2(eta_g, eta_o)
+
+
+@pytest.mark.parametrize("N", [2, 3, 4, 5])
+def test_coupled_random_dofs_fp64(N):
+    # ocean over crust: solid-fluid interface, gravitational top, absorbing sides
+    eq, ee = _coupled_run(N, 0)
+    assert eq <= FP64_TOL and ee <= FP64_TOL, (eq, ee)
+
+
+def test_coupled_random_dofs_fp32():
+    # FP32 dofs/operators (FP64 eta): per-output tolerance after 3 steps at N=5
+    eq, ee = _coupled_run(5, 1)
+    assert eq <= 2e-5 and ee <= 1e-6, (eq, ee)
+
+
+def test_free_surface_and_rigid_wall_fp64():
+    m, mat = small_coupled(rigid_bottom=True)
+    m.face_tag[m.face_tag == syn.TAG_GRAVITY] = syn.TAG_FREE
+    o, s = make_pair(m, mat, 4, cfl=0.5)
+    Q0 = random_dofs((m.nt, s.B, 9), 7, N=4)
+    o.Q = Q0.copy()
+    s.set_dofs(to_gpu_layout(Q0))
+    for _ in range(2):
+        o.step_gts()
+    s.advance(2)
+    assert rel_l2(to_oracle_layout(s.get_dofs()), o.Q) <= FP64_TOL
+
+
+def _warped_periodic(n, a=0.6):
+    phi = lambda u: u - a * np.sin(2 * np.pi * u) / (2 * np.pi)
+    g = np.linspace(0, 1, n + 1)
+    return syn.kuhn_box(g, g, g, tags={sd: syn.TAG_PERIODIC for sd in syn.mesh.SIDES},
+                        warp=lambda x, ijk: phi(x))
+
+
+def test_lts_two_clusters_fp64():
+    m = _warped_periodic(4)
+    mat = syn.elastic_uniform(m.nt)
+    o, s = make_pair(m, mat, 3, cfl=0.5, max_clusters=3)
+    assert s.info.n_clusters == int(o.cluster.max()) + 1 >= 2
+    sizes = np.bincount(o.cluster)
+    assert list(s.info.cluster_size[: s.info.n_clusters]) == list(sizes)
+    o.Q = o.project(plane_wave_field(0.0))
+    s.set_dofs(to_gpu_layout(o.Q))
+    for _ in range(3):
+        o.advance_macro()
+    s.advance(3)
+    assert rel_l2(to_oracle_layout(s.get_dofs()), o.Q) <= FP64_TOL
+
+
+def test_lts_coupled_graded_fp64():
+    m, mat = syn.workloads.coupled_box(nxy=4, n_water=2, n_crust=2, L=8e3, depth=4e3, water=1e3,
+                                       grading=4.0)
+    o, s = make_pair(m, mat, 3, cfl=0.5, max_clusters=4)
+    assert s.info.n_clusters >= 2
+    Q0 = random_dofs((m.nt, s.B, 9), 3, N=3)
+    o.Q = Q0.copy()
+    s.set_dofs(to_gpu_layout(Q0))
+    o.advance_macro()
+    s.advance(1)
+    assert rel_l2(to_oracle_layout(s.get_dofs()), o.Q) <= FP64_TOL
+
+
+def test_ensemble_equals_independent_runs():
+    m, mat = small_coupled()
+    S = 3
+    from paper_2107_06640_gb300 import Solver
+    rho, lam, mu = mat
+    ens = Solver(m.xyz, m.tets, m.face_tag, rho, lam, mu, degree=3, cfl=0.5, ensemble=S)
+    Qs = np.stack([to_gpu_layout(random_dofs((m.nt, ens.B, 9), 10 + k, N=3)) for k in range(S)], axis=1)
+    ens.set_dofs(Qs)
+    ens.advance(2)
+    out = ens.get_dofs()
+    for k in range(S):
+        one = Solver(m.xyz, m.tets, m.face_tag, rho, lam, mu, degree=3, cfl=0.5)
+        one.set_dofs(Qs[:, k])
+        one.advance(2)
+        assert np.array_equal(one.get_dofs(), out[:, k])
+
+
+def test_receivers_checkpoint_and_advance_to():
+    m, mat = small_coupled()
+    o, s = make_pair(m, mat, 3, cfl=0.5)
+    Q0 = random_dofs((m.nt, s.B, 9), 5, N=3)
+    o.Q = Q0.copy()
+    s.set_dofs(to_gpu_layout(Q0))
+    # checkpoint at t=0, run, restore, run again: bitwise identical
+    buf = s.save_state()
+    s.advance(2)
+    first = s.get_dofs()
+    s.load_state(buf)
+    assert s.time == 0.0
+    s.advance(2)
+    assert np.array_equal(s.get_dofs(), first)
+    # advance_to with a shortened final step
+    s.load_state(buf)
+    T = 2.37 * s.info.dt_min
+    s.advance_to(T)
+    o.step_gts()
+    o.step_gts()
+    o.step_gts(0.37 * o.dtmin)
+    assert np.isclose(s.time, T)
+    assert rel_l2(to_oracle_layout(s.get_dofs()), o.Q) <= FP64_TOL
+    # receivers
+    rng = np.random.default_rng(0)
+    c = m.centroids()
+    pts = c[rng.choice(m.nt, 7, replace=False)] + 10.0
+    s.add_receivers(pts)
+    got = s.read_receivers()[:, 0, :]
+    from oracle.geometry import Geometry
+    inside = []
+    for p in pts:
+        lam_ = np.einsum("ead,ed->ea", o.geo.Jinv, p[None] - o.geo.x0)
+        bary = np.concatenate([lam_, 1 - lam_.sum(1, keepdims=True)], axis=1)
+        inside.append(int(np.argmax(bary.min(1))))
+    want = o.evaluate(np.array(inside), pts)
+    assert rel_l2(got, want) <= FP64_TOL
+
+
+def test_nan_is_reported():
+    from paper_2107_06640_gb300 import AdgError
+    m, mat = small_coupled()
+    o, s = make_pair(m, mat, 2, cfl=0.5)
+    Q = np.zeros((m.nt, 9, s.B))
+    Q[5, 2, 1] = np.nan
+    s.set_dofs(Q)
+    with pytest.raises(AdgError) as ei:
+        s.advance(1)
+    assert ei.value.code == -6
+
+
+def test_full_size_coupled_box_sampled_fp64():
+    """The 1.5 M-tet coupled ocean-crust box at N=5 in FP64 (the benchmark
+    workload): one global step from a projected seafloor pulse plus seeded
+    noise; 60 sampled elements (interior, interface, surface, boundary)
+    recomputed by the oracle on their neighbourhood."""
+    from synthetic.workloads import coupled_box, seafloor_pulse
+    m, mat = coupled_box()
+    assert m.nt == 1497600
+    from paper_2107_06640_gb300 import Solver
+    rho, lam, mu = mat
+    s = Solver(m.xyz, m.tets, m.face_tag, rho, lam, mu, degree=5, cfl=0.35)
+    rng = np.random.default_rng(11)
+    Q0 = rng.standard_normal((m.nt, 9, s.B)) * 1e-3
+    s.set_dofs(Q0)
+    ef, nxyz = s.gravity_faces()
+    eta0 = 0.5 * np.sin(nxyz[..., 0] / 7e3)[:, None, :]
+    s.set_eta(eta0)
+    s.advance(1)
+    Q1 = s.get_dofs()
+    eta1 = s.read_ssh()[:, 0]
+    # sample: 20 random, 20 at the sea surface, 20 at the sea floor
+    wet = m.hex_index[:, 2] >= 35
+    top = np.nonzero(np.any(m.face_tag == syn.TAG_GRAVITY, axis=1))[0]
+    floor = np.nonzero(wet & (m.hex_index[:, 2] == 35))[0]
+    side = np.nonzero(np.any(m.face_tag == syn.TAG_ABSORB, axis=1))[0]
+    pick = np.concatenate([rng.choice(m.nt, 15, replace=False), rng.choice(top, 15, replace=False),
+                           rng.choice(floor, 15, replace=False), rng.choice(side, 15, replace=False)])
+    sub, smat, keep, pos = submesh(m, mat, pick)
+    from oracle.ader import Oracle
+    o = Oracle(sub.xyz, sub.tets, sub.face_tag, sub.face_partner, *smat, 5, cfl=0.35, dt=s.info.dt_min)
+    o.Q = to_oracle_layout(Q0[keep])
+    gmap = {int(v): g for g, v in enumerate(ef)}
+    for i, e in enumerate(keep):
+        for f in range(4):
+            if sub.face_tag[i, f] == syn.TAG_GRAVITY:
+                # eta0 = 0.5 sin(x/7e3) is not a polynomial: hand the oracle the
+                # library's nodal values through their P_N interpolant
+                g = gmap[int(e) * 4 + f]
+                mono = [(a, b) for a in range(6) for b in range(6 - a)]
+                Vn = np.array([[x ** a * y ** b for (a, b) in mono] for x, y in node_chi(5)])
+                Vq = np.array([[x ** a * y ** b for (a, b) in mono] for x, y in o.chi])
+                o.eta[i, f] = Vq @ np.linalg.solve(Vn, eta0[g, 0])
+    o.step_gts()
+    sel = pos[pick]
+    got = to_oracle_layout(Q1[pick])
+    assert rel_l2(got, o.Q[sel]) <= FP64_TOL, rel_l2(got, o.Q[sel])
+    for i, e in enumerate(keep):
+        if pos[e] not in set(sel):
+            continue
+        for f in range(4):
+            if sub.face_tag[i, f] == syn.TAG_GRAVITY:
+                g = gmap[int(e) * 4 + f]
+                want = oracle_eta_at_nodes(o, [i * 4 + f], node_chi(5), 5)[0]
+                assert rel_l2(eta1[g], want) <= FP64_TOL
