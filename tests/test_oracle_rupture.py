@@ -87,15 +87,15 @@ def test_locked_fault_is_the_welded_interface():
     wm, wp = ph.rotate_in(qm, R), ph.rotate_in(qp, R)
     Zpm, Zsm = ph.impedances(*matm)
     Zpp, Zsp = ph.impedances(*matp)
-    wb = ph.middle_state(wm, wp, Zpm[:, None] * 0 + Zpm[0], Zpp[0], Zsm[0], Zsp[0])
-    F = ph.rotate_out(ph.flux_rotated(wb, matm[0][0], matm[1][0], matm[2][0]), R)
+    wb = ph.middle_state(wm, wp, Zpm, Zpp, Zsm, Zsp)
+    F = ph.rotate_out(ph.flux_rotated(wb, *matm), R)
     assert np.allclose(Fm, F, rtol=1e-10, atol=1e-12 * np.abs(F).max())
     # the plus side sees the same interface from the other side
     Fp = -ru.ahat_apply(n, t_b, vc, *matp)
     Rn = ph.frame(-n)
     wm2, wp2 = ph.rotate_in(qp, Rn), ph.rotate_in(qm, Rn)
-    wb2 = ph.middle_state(wm2, wp2, Zpp[0], Zpm[0], Zsp[0], Zsm[0])
-    F2 = ph.rotate_out(ph.flux_rotated(wb2, matp[0][0], matp[1][0], matp[2][0]), Rn)
+    wb2 = ph.middle_state(wm2, wp2, Zpp, Zpm, Zsp, Zsm)
+    F2 = ph.rotate_out(ph.flux_rotated(wb2, *matp), Rn)
     assert np.allclose(Fp, F2, rtol=1e-10, atol=1e-12 * np.abs(F2).max())
 
 
