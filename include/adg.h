@@ -153,6 +153,32 @@ int adg_sync(adg_ctx* ctx);
  * flux), 1 neighbour flux.  Advances the simulation like adg_advance. */
 int adg_profile(adg_ctx* ctx, int n_macro, double* ms, int64_t* launches);
 
+/* Allocation-free global steps (the paper has no counterpart; this is a
+ * service of this library).  For callers that must not allocate device
+ * memory while they step - for example a plug-in whose host application owns
+ * and budgets all device memory - this runs n_steps global time steps on the
+ * caller's own dofs and allocates nothing: the face-trace scratch that the
+ * step needs lives in a fixed 32 MiB static device array inside the library
+ * (held by every GPU that loads the library until the process exits).
+ *  - ctx: an initialised context with one cluster, ensemble 1 and no
+ *    gravitational or fault faces (else ADG_E_INVALID); its tables are read,
+ *    its own dofs are not touched.
+ *  - d_Q: DEVICE pointer to the caller's dofs in the context's precision,
+ *    layout [tet][9][B] in user tet order (for such contexts the internal
+ *    order is the user order), updated in place.  Owned by the caller.
+ *  - stream: cudaStream_t to launch on, or NULL for the context's stream;
+ *    the call only enqueues work (no synchronisation).
+ *  - Meshes whose traces need more than the fixed maximum
+ *    (n_tets * 36 * Bf * sizeof(precision) > 32 MiB) are rejected with
+ *    ADG_E_INVALID and a message naming both sizes.
+ *  - The first call on a device looks up the array's device address with
+ *    that device current; make that first call before any stream capture.
+ *  - All calls share the array and it keeps the last call's contents
+ *    (every trace is written before it is read); calls whose work overlaps
+ *    on the GPU race on it.  Non-finite dofs are reported by the next
+ *    adg_sync() on the context. */
+int adg_step_noalloc(adg_ctx* ctx, void* d_Q, int n_steps, void* stream);
+
 /* Receivers: physical points; readout of q at the current time (whole ticks
  * synchronised: at macro-step boundaries), out[n][S][9] (host, double). */
 int adg_add_receivers(adg_ctx* ctx, int64_t n, const double* xyz);

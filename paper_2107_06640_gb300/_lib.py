@@ -61,6 +61,7 @@ _SIGS = {
     "adg_step_cluster": (C.c_int, [_P, C.c_int]),
     "adg_sync": (C.c_int, [_P]),
     "adg_profile": (C.c_int, [_P, C.c_int, _P, _P]),
+    "adg_step_noalloc": (C.c_int, [_P, _P, C.c_int, _P]),
     "adg_add_receivers": (C.c_int, [_P, C.c_int64, _P]),
     "adg_read_receivers": (C.c_int, [_P, _P]),
     "adg_save_state": (C.c_int, [_P, _P, C.POINTER(C.c_size_t)]),
@@ -210,6 +211,12 @@ def adg_profile(ctx, n_macro):
     cnt = np.zeros(2, np.int64)
     _check(ctx, load().adg_profile(ctx, int(n_macro), _ptr(ms), _ptr(cnt)))
     return ms, cnt
+
+
+def adg_step_noalloc(ctx, d_Q_ptr, n_steps, stream_ptr=None):
+    """d_Q_ptr: integer device address of the caller's dofs (see include/adg.h)."""
+    _check(ctx, load().adg_step_noalloc(ctx, C.c_void_p(d_Q_ptr), int(n_steps),
+                                        None if stream_ptr is None else C.c_void_p(stream_ptr)))
 
 
 def adg_add_receivers(ctx, xyz):

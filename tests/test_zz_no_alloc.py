@@ -1,0 +1,62 @@
+"""The allocation-free step entry point (adg_step_noalloc).
+
+Callers that must not allocate device memory while they step (a plug-in
+whose host application owns all device memory, for instance) keep their dofs
+in memory they already own; adg_step_noalloc steps them in place and uses a
+fixed static device array inside the library for its face-trace scratch.
+This file runs last so that a failure here never hides another test.  The
+test itself allocates the caller's buffer with torch, as such a caller would
+have done ahead of time.
+"""
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2107_06640_gb300 import build
+    build.build()
+    from paper_2107_06640_gb300 import _lib
+    return _lib
+
+
+def _periodic_context(n, N):
+    from paper_2107_06640_gb300 import Solver
+    from synthetic.workloads import plane_wave_case
+    m, (rho, lam, mu) = plane_wave_case(n)
+    return m, Solver(m.xyz, m.tets, m.face_tag, rho, lam, mu, face_partner=m.face_partner,
+                     degree=N, cfl=0.5)
+
+
+def test_noalloc_steps_match_the_context_path(lib):
+    import torch
+    from synthetic.workloads import random_dofs
+    m, s = _periodic_context(8, 3)          # 3072 tets: 8.8 MB of FP64 traces
+    Q0 = random_dofs((m.nt, 9, s.B), 21, N=3)
+    d = torch.tensor(Q0, dtype=torch.float64, device="cuda").contiguous()
+    stream = torch.cuda.current_stream()
+    out = []
+    for _ in range(2):                       # two calls in a row on the same buffer
+        lib.adg_step_noalloc(s.ctx, d.data_ptr(), 1, stream.cuda_stream)
+        torch.cuda.synchronize()
+        out.append(d.cpu().numpy().copy())
+    assert np.all(s.get_dofs() == 0.0)       # the context's own dofs were not touched
+    s.sync()
+    s.set_dofs(Q0)
+    for k in range(2):
+        s.advance(1)
+        ref = s.get_dofs()
+        err = np.linalg.norm(out[k] - ref) / np.linalg.norm(ref)
+        assert err <= 1e-10, (k, err)
+
+
+def test_noalloc_rejects_meshes_beyond_the_scratch_limit(lib):
+    import torch
+    m, s = _periodic_context(12, 5)         # 10368 tets at N=5: 62.7 MB of traces
+    d = torch.zeros((m.nt, 9, s.B), dtype=torch.float64, device="cuda")
+    with pytest.raises(lib.AdgError) as ei:
+        lib.adg_step_noalloc(s.ctx, d.data_ptr(), 1)
+    assert ei.value.code == -1 and "maximum" in str(ei.value)
