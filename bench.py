@@ -122,10 +122,10 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def make_workload(seed):
+def make_workload(seed, nxy=80):
     import numpy as np
     from synthetic.workloads import coupled_box, random_dofs, seafloor_pulse
-    m, mat = coupled_box()
+    m, mat = coupled_box(nxy=nxy, L=100e3 * nxy / 80)
     rng = np.random.default_rng(seed)
     x0, y0 = rng.uniform(30e3, 70e3, 2)
     pulse = seafloor_pulse(x0, y0, m.extra["seafloor"])
@@ -197,6 +197,8 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--nxy", type=int, default=80,
+                    help="hex columns per side (80: the 1.5 M-tet workload; smaller for profiling)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -232,7 +234,7 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         return float(t.item())
 
-    m, (rho, lam, mu), Q0 = make_workload(seed=rank)
+    m, (rho, lam, mu), Q0 = make_workload(seed=rank, nxy=args.nxy)
     stream = torch.cuda.current_stream()
     res = {}
     for prec, steps, warm in ((pkg.ADG_FP32, args.steps, args.warmup), (pkg.ADG_FP64, args.fp64_steps, 1)):
@@ -309,7 +311,7 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": r32["steps"],
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n_tets": s.nt, "degree": N_DEG, "time_stepping": "global (1 cluster)",
+        "config": {"workload": WORKLOAD if args.nxy == 80 else f"{args.nxy}x{args.nxy}-column box", "n_tets": s.nt, "degree": N_DEG, "time_stepping": "global (1 cluster)",
                    "parallelism": f"replicas x{world}", "l2": "inputs larger than L2 (3 GB FP32 dofs)"},
         "gflops": value * fl["total"] / 1e9,
         "fp64": {"value": value64, "unit": UNIT, "steps": r64["steps"], "ms_per_step": r64["ms"] / r64["steps"],

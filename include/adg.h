@@ -149,8 +149,9 @@ int adg_sync(adg_ctx* ctx);
 /* Per-kernel timing for roofline reports: runs n_macro macro steps with
  * eager (non-graph) launches and a CUDA event pair around every kernel on the
  * library stream.  ms[k] = mean duration of one launch of kernel kind k,
- * launches[k] = number of launches, k = 0 local (predictor, volume, local
- * flux), 1 neighbour flux.  Advances the simulation like adg_advance. */
+ * launches[k] = number of launches (arrays of 3), k = 0 local (predictor,
+ * volume, local flux), 1 neighbour flux, 2 fault friction solve.  Advances
+ * the simulation like adg_advance. */
 int adg_profile(adg_ctx* ctx, int n_macro, double* ms, int64_t* launches);
 
 /* Allocation-free global steps (the paper has no counterpart; this is a
@@ -183,6 +184,48 @@ int adg_step_noalloc(adg_ctx* ctx, void* d_Q, int n_steps, void* stream);
  * synchronised: at macro-step boundaries), out[n][S][9] (host, double). */
 int adg_add_receivers(adg_ctx* ctx, int64_t n, const double* xyz);
 int adg_read_receivers(adg_ctx* ctx, double* out);
+
+/* ---- Dynamic rupture (Sec. 3, Eq. bc-dynrup) --------------------------------
+ * Faces tagged ADG_TAG_FAULT on both sides (solid-solid).  Each tet pair is one
+ * fault face; its minus side is the tet with the lower user index and n is that
+ * tet's outward normal.  The fault lives at the face nodes of the minus face
+ * (equispaced, see above).  Friction (reading of the fast-velocity-weakening
+ * law): f = a asinh(V/(2V0) e^{psi/a}), dpsi/dt = -(V/L)(psi - psi_ss(V)),
+ * f_ss = f_w + (f0 - (b-a) ln(V/V0) - f_w)/(1 + (V/V_w)^8)^{1/8}; strength
+ * S = max(0, -(sigma_n0 + sigma_n)); solved per node at N+1 Gauss time points
+ * per step by Newton on ln|V| in FP64.
+ *
+ * adg_fault_faces: per fault face (library order, cluster-major) the user
+ *   tet*4+face of both sides, node coordinates [nff][Bf][3] and n [nff][3];
+ *   any pointer may be NULL.  n_fault_faces comes from adg_query.
+ * adg_set_fault: per node and scenario parameters [nff][S][Bf][13] =
+ *   a, b, L, f0, V0, f_w, V_w, sigma_n0 (tension positive), tau0 (3, global
+ *   frame; its normal part is ignored), psi_init, V_init (> 0); required before
+ *   the first step.  Resets slip and traction.
+ * adg_read_fault: state [nff][S][Bf][8] = |V|, psi, slip (3), shear traction (3).
+ * adg_fault_stats: friction solves and Newton iterations so far (reset if asked). */
+int adg_fault_faces(adg_ctx* ctx, int64_t* minus_face, int64_t* plus_face, double* node_xyz, double* normal);
+int adg_set_fault(adg_ctx* ctx, const double* par);
+int adg_read_fault(adg_ctx* ctx, double* state);
+int adg_fault_stats(adg_ctx* ctx, int64_t* solves, int64_t* iterations, int reset);
+
+/* ---- Learned Newton start for the friction solve ----------------------------
+ * A 6-32-32-1 tanh network proposes ln|V| for the first Newton pass of every
+ * friction solve; Newton then converges to the same tolerance as from the
+ * plain start (the previous slip rate), which it replaces only as a guess.
+ * adg_rupture_capture(capacity): start recording (features, converged ln|V|)
+ *   of every solve into a device buffer of that many rows (0 stops recording);
+ *   *n_captured returns the rows recorded since the last start.
+ * adg_mlp_train: fit the network to the recorded rows on the GPU (own forward,
+ *   backward and Adam kernels); loss[2] = scaled MSE before / after.
+ * adg_mlp_params: set (if set != NULL) / get the MLP_NPARAM = 1327 floats and
+ *   enable (1) or disable (0) the guess (-1 keeps the current setting).
+ * adg_mlp_gradient: the loss gradient for given parameters and rows (host
+ *   arrays, rows [n][7]); grad receives the 1313 trainable entries. */
+int adg_rupture_capture(adg_ctx* ctx, int64_t capacity, int64_t* n_captured);
+int adg_mlp_train(adg_ctx* ctx, int epochs, int batch, double lr, int seed, double* loss);
+int adg_mlp_params(adg_ctx* ctx, const float* set, float* get, int enable);
+int adg_mlp_gradient(const float* params, int64_t n, const float* rows, float* grad, double* loss);
 
 /* Checkpoint: dofs, eta, fault state and time at a macro-step boundary.
  * adg_save_state with buf == NULL returns the size in *len. */

@@ -67,9 +67,95 @@ class Oracle:
             self.dtmin = float(dt)
         self.Q = np.zeros((E, self.B, 9))
         self.t = 0.0
-        self.fault_faces = np.argwhere(geo.face_tag == 5)
-        if self.fault_faces.size:
-            raise NotImplementedError("fault faces need oracle.rupture")
+        self.fault_guess = None
+        self._setup_faults()
+
+    # ---------------- dynamic rupture (oracle.rupture) -----------------
+    def _setup_faults(self):
+        """Fault faces: one per tet pair, minus = lower tet index, n = its outward
+        normal; listed cluster-major, then by minus tet, then by face (the
+        library's order).  The fault sits at the minus face's equispaced nodes."""
+        geo, N = self.geo, self.N
+        ff = [(int(e), int(f)) for e, f in np.argwhere(geo.face_tag == 5) if geo.nbr[e, f] > e]
+        ff.sort(key=lambda ef: (self.cluster[ef[0]], ef[0], ef[1]))
+        self.nff = len(ff)
+        if not ff:
+            return
+        for e, f in ff:
+            if self.cluster[e] != self.cluster[geo.nbr[e, f]]:
+                raise ValueError("fault sides must share a cluster")
+        self.fm = np.array(ff)
+        self.fp = np.array([(geo.nbr[e, f], geo.nbr_face[e, f]) for e, f in ff])
+        nodes = np.array([[i1 / N, i2 / N] for i2 in range(N + 1) for i1 in range(N + 1 - i2)])
+        self.f_nodes = nodes
+        Bf = nodes.shape[0]
+        em, fm = self.fm[:, 0], self.fm[:, 1]
+        ep = self.fp[:, 0]
+        self.f_n = geo.normal[em, fm]                                   # (nff,3)
+        self.f_xyz = np.stack([geo.to_phys(np.full(Bf, e), ob.face_to_ref(f, nodes)) for e, f in ff])
+        self.f_phim = np.stack([ob.eval_basis(N, ob.face_to_ref(f, nodes)) for e, f in ff])
+        self.f_phip = np.stack([ob.eval_basis(N, geo.to_ref(np.full(Bf, e2), x))
+                                for e2, x in zip(ep, self.f_xyz)])
+        # lift: int_face phi_k (sum_n ell_n G_n) dS by the face Gauss rule
+        mono = [(a, b) for a in range(N + 1) for b in range(N + 1 - a)]
+        V = np.array([[x ** a * y ** b for (a, b) in mono] for x, y in nodes])
+        Vq = np.array([[x ** a * y ** b for (a, b) in mono] for x, y in self.chi])
+        self.f_ell = Vq @ np.linalg.inv(V)                              # (nq, Bf)
+        xq = np.stack([geo.to_phys(np.full(self.nq, e), ob.face_to_ref(f, self.chi)) for e, f in ff])
+        self.f_phiq_m = np.stack([self.phi_face[f] for e, f in ff])     # (nff,nq,B)
+        self.f_phiq_p = np.stack([ob.eval_basis(N, geo.to_ref(np.full(self.nq, e2), x)) for e2, x in zip(ep, xq)])
+        self.f_area = geo.area[em, fm]
+        self.fault = None  # set by set_fault
+
+    def set_fault(self, par):
+        """par: dict of (nff, Bf) arrays named as rupture.PARAMS (psi, V: initial state)."""
+        self.fault = {k: np.array(v, dtype=np.float64) for k, v in par.items()}
+        self.fault["slip"] = np.zeros(self.fault["a"].shape + (3,))
+        self.fault["traction"] = np.zeros(self.fault["a"].shape + (3,))
+        self.newton_solves = 0
+        self.newton_iters = 0
+
+    def fault_update(self, sel, D, dt, guess=None):
+        """Friction solve over [t0, t0+dt] on fault faces sel (indices into the
+        fault list) from the Taylor expansions D (full element arrays) of both
+        sides; returns {element: dQ increment}."""
+        from . import rupture as ru
+        N, Bf = self.N, self.f_nodes.shape[0]
+        if self.fault is None:
+            raise RuntimeError("fault parameters not set")
+        em, ep = self.fm[sel, 0], self.fp[sel, 0]
+        tj, _ = ru.time_points(N, dt)
+        qm_t = np.zeros((N + 1, sel.size, Bf, 9))
+        qp_t = np.zeros((N + 1, sel.size, Bf, 9))
+        for j, t in enumerate(tj):
+            for k, Dk in enumerate(D):
+                c = t ** k / factorial(k)
+                qm_t[j] += c * np.einsum("xnl,xlp->xnp", self.f_phim[sel], Dk[em])
+                qp_t[j] += c * np.einsum("xnl,xlp->xnp", self.f_phip[sel], Dk[ep])
+        flat = lambda a: a.reshape(a.shape[0] * a.shape[1], *a.shape[2:])
+        nrm = np.repeat(self.f_n[sel], Bf, axis=0)
+        matm = tuple(np.repeat(a[em], Bf) for a in (self.rho, self.lam, self.mu))
+        matp = tuple(np.repeat(a[ep], Bf) for a in (self.rho, self.lam, self.mu))
+        par = {k: flat(v[sel]) for k, v in self.fault.items() if k not in ("slip", "traction")}
+        Gm, Gp, psi, V, dslip, iters, tau = ru.solve_step(
+            nrm, qm_t.reshape(N + 1, -1, 9), qp_t.reshape(N + 1, -1, 9), matm, matp, par, dt, N, guess=guess)
+        self.newton_solves += int(np.sum(iters > 0))
+        self.newton_iters += int(iters.sum())
+        shp = (sel.size, Bf)
+        self.fault["psi"][sel] = psi.reshape(shp)
+        self.fault["V"][sel] = V.reshape(shp)
+        self.fault["slip"][sel] += dslip.reshape(shp + (3,))
+        self.fault["traction"][sel] = tau.reshape(shp + (3,))
+        Gm = Gm.reshape(shp + (9,))
+        Gp = Gp.reshape(shp + (9,))
+        out = {}
+        for i, fi in enumerate(sel):
+            for (e, phiq, G) in ((em[i], self.f_phiq_m[fi], Gm[i]), (ep[i], self.f_phiq_p[fi], Gp[i])):
+                scale = 2.0 * self.f_area[fi] / self.geo.detJ[e]
+                Gq = self.f_ell @ G                                       # (nq, 9)
+                d = -scale * np.einsum("q,qk,qp->kp", self.fw, phiq, Gq)
+                out[int(e)] = out.get(int(e), 0.0) + d
+        return out
 
     # ---------------- predictor -----------------
     def derivatives(self, Q, idx):
@@ -172,6 +258,9 @@ class Oracle:
         eta_new = []
         dQ = self.volume(I, idx) + self.face_update(
             idx, I, lambda f, s, nb: I[nb], D=D, dt=dt, eta_new=eta_new)
+        if self.nff:
+            for e, d in self.fault_update(np.arange(self.nff), D, dt, self.fault_guess).items():
+                dQ[e] += d
         self.Q = self.Q + dQ
         for e, f, v in eta_new:
             self.eta[e, f] = v
@@ -242,6 +331,12 @@ class Oracle:
                 eta_new = []
                 dQ = self.volume(self._Iown[idx], idx) + self.face_update(
                     idx, self._Iown[idx], nbr_int, D=Dloc, dt=(1 << cl) * dtm, eta_new=eta_new)
+                if self.nff:
+                    sel = np.nonzero(c[self.fm[:, 0]] == cl)[0]
+                    if sel.size:
+                        pos = {int(e): i for i, e in enumerate(idx)}
+                        for e, d in self.fault_update(sel, self._D, (1 << cl) * dtm, self.fault_guess).items():
+                            dQ[pos[e]] += d
                 self.Q[idx] += dQ
                 for e, f, v in eta_new:
                     self.eta[e, f] = v

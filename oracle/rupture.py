@@ -19,8 +19,10 @@ but prints neither f nor g):
         Theta - eta_s |V| = S f(|V|, psi),  Theta = |tau0 + theta|;
     side states: u_b = u- + (tau - tau-)/Z_s-,  u_c = u+ - (tau - tau+)/Z_s+;
   * time: N+1 Gauss-Legendre points per step; between points psi relaxes
-    exactly for frozen V (mid-point of the old and new slip rate), two passes
-    of [psi update, Newton on |V|]; Newton is safeguarded by the bracket
+    exactly for frozen V; two passes of [psi update, Newton on |V|], the first
+    with the previous slip rate, the second with the mid-point of the previous
+    and the first pass's slip rate (a Newton start guess never enters the
+    state update, so the answer does not depend on it); Newton is safeguarded by the bracket
     [0, Theta/eta_s] in x = ln V, tolerance |dx| <= tol;
   * the fault sits at the equispaced face nodes of the minus element's face;
     the flux there is interpolated (Lagrange on those nodes) and integrated
@@ -56,7 +58,9 @@ def friction(V, psi, p):
 
 
 def psi_relax(psi, V, h, p):
-    """Exact solution of dpsi/dt = -(V/L)(psi - psi_ss(V)) over h for frozen V."""
+    """Exact solution of dpsi/dt = -(V/L)(psi - psi_ss(V)) over h for frozen V
+    (V is floored at 1e-300: for V -> 0 the state does not change)."""
+    V = np.maximum(V, 1e-300)
     ss = psi_ss(V, p)
     return ss + (psi - ss) * np.exp(-V * h / p["L"])
 
@@ -204,10 +208,12 @@ def solve_step(n, qm_t, qp_t, matm, matp, par, dt, N, guess=None, tol=1e-10, max
         Th = np.linalg.norm(st["Thv"], axis=-1)
         h = tj[j] - tprev
         Vold = V
+        # the start guess only seeds Newton; the state update of the first
+        # pass uses the previous slip rate, the second the mid-point
         Vcur = V if guess is None else guess(j, Th, st, psi, V)
         psi_new = psi
         for ps in range(2):
-            Vmid = 0.5 * (Vold + Vcur)
+            Vmid = Vold if ps == 0 else 0.5 * (Vold + Vcur)
             psi_new = psi_relax(psi, Vmid, h, par)
             Vcur, it, ok = newton_slip_rate(Th, st["S"], st["eta"], psi_new, par, Vcur, tol, max_iter)
             if not np.all(ok):

@@ -62,6 +62,14 @@ _SIGS = {
     "adg_sync": (C.c_int, [_P]),
     "adg_profile": (C.c_int, [_P, C.c_int, _P, _P]),
     "adg_step_noalloc": (C.c_int, [_P, _P, C.c_int, _P]),
+    "adg_fault_faces": (C.c_int, [_P, _P, _P, _P, _P]),
+    "adg_set_fault": (C.c_int, [_P, _P]),
+    "adg_read_fault": (C.c_int, [_P, _P]),
+    "adg_fault_stats": (C.c_int, [_P, _P, _P, C.c_int]),
+    "adg_rupture_capture": (C.c_int, [_P, C.c_int64, _P]),
+    "adg_mlp_train": (C.c_int, [_P, C.c_int, C.c_int, C.c_double, C.c_int, _P]),
+    "adg_mlp_params": (C.c_int, [_P, _P, _P, C.c_int]),
+    "adg_mlp_gradient": (C.c_int, [_P, C.c_int64, _P, _P, _P]),
     "adg_add_receivers": (C.c_int, [_P, C.c_int64, _P]),
     "adg_read_receivers": (C.c_int, [_P, _P]),
     "adg_save_state": (C.c_int, [_P, _P, C.POINTER(C.c_size_t)]),
@@ -207,8 +215,8 @@ def adg_sync(ctx):
 
 
 def adg_profile(ctx, n_macro):
-    ms = np.zeros(2)
-    cnt = np.zeros(2, np.int64)
+    ms = np.zeros(3)
+    cnt = np.zeros(3, np.int64)
     _check(ctx, load().adg_profile(ctx, int(n_macro), _ptr(ms), _ptr(cnt)))
     return ms, cnt
 
@@ -217,6 +225,63 @@ def adg_step_noalloc(ctx, d_Q_ptr, n_steps, stream_ptr=None):
     """d_Q_ptr: integer device address of the caller's dofs (see include/adg.h)."""
     _check(ctx, load().adg_step_noalloc(ctx, C.c_void_p(d_Q_ptr), int(n_steps),
                                         None if stream_ptr is None else C.c_void_p(stream_ptr)))
+
+
+FPAR, FSTATE, MLP_NPARAM, MLP_TRAINABLE = 13, 8, 1327, 1313
+
+
+def adg_fault_faces(ctx, nff, Bf):
+    mf = np.empty(nff, np.int64)
+    pf = np.empty(nff, np.int64)
+    xyz = np.empty((nff, Bf, 3))
+    nrm = np.empty((nff, 3))
+    _check(ctx, load().adg_fault_faces(ctx, _ptr(mf), _ptr(pf), _ptr(xyz), _ptr(nrm)))
+    return mf, pf, xyz, nrm
+
+
+def adg_set_fault(ctx, par):
+    par = _f64(par)
+    _check(ctx, load().adg_set_fault(ctx, _ptr(par)))
+
+
+def adg_read_fault(ctx, out):
+    _check(ctx, load().adg_read_fault(ctx, _ptr(out)))
+    return out
+
+
+def adg_fault_stats(ctx, reset=False):
+    s = C.c_int64()
+    it = C.c_int64()
+    _check(ctx, load().adg_fault_stats(ctx, C.byref(s), C.byref(it), int(reset)))
+    return s.value, it.value
+
+
+def adg_rupture_capture(ctx, capacity):
+    n = C.c_int64()
+    _check(ctx, load().adg_rupture_capture(ctx, int(capacity), C.byref(n)))
+    return n.value
+
+
+def adg_mlp_train(ctx, epochs, batch, lr, seed=0):
+    loss = np.zeros(2)
+    _check(ctx, load().adg_mlp_train(ctx, int(epochs), int(batch), float(lr), int(seed), _ptr(loss)))
+    return loss
+
+
+def adg_mlp_params(ctx, set_params=None, enable=-1):
+    get = np.empty(MLP_NPARAM, np.float32)
+    sp = None if set_params is None else np.ascontiguousarray(set_params, dtype=np.float32)
+    _check(ctx, load().adg_mlp_params(ctx, _ptr(sp), _ptr(get), int(enable)))
+    return get
+
+
+def adg_mlp_gradient(params, rows):
+    params = np.ascontiguousarray(params, dtype=np.float32)
+    rows = np.ascontiguousarray(rows, dtype=np.float32)
+    grad = np.empty(MLP_TRAINABLE, np.float32)
+    loss = np.zeros(1)
+    _check(None, load().adg_mlp_gradient(_ptr(params), rows.shape[0], _ptr(rows), _ptr(grad), _ptr(loss)))
+    return grad, loss[0]
 
 
 def adg_add_receivers(ctx, xyz):

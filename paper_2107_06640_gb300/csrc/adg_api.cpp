@@ -32,6 +32,8 @@ int guard(adg_ctx* ctx, F&& f) {
   }
 }
 
+constexpr size_t kStateHeader = 80;  // 10 int64 words: magic, N, S, nt, fp64, n_gface, tick, fault bytes, time, 0
+
 void need_init(const Ctx& c) {
   if (!c.inited) adg::throw_err(ADG_E_STATE, "call adg_init first");
 }
@@ -376,15 +378,15 @@ int adg_profile(adg_ctx* ctx, int n_macro, double* ms, int64_t* launches) {
     }
     c.prof = nullptr;
     check_cuda(cudaStreamSynchronize(c.stream), "profile");
-    double tot[2] = {0, 0};
-    int64_t cnt[2] = {0, 0};
+    double tot[3] = {0, 0, 0};
+    int64_t cnt[3] = {0, 0, 0};
     for (auto& e : evs) {
       float t = 0;
       check_cuda(cudaEventElapsedTime(&t, e.a, e.b), "profile events");
       tot[e.kind] += t;
       cnt[e.kind] += 1;
     }
-    for (int k = 0; k < 2; ++k) {
+    for (int k = 0; k < 3; ++k) {
       ms[k] = cnt[k] ? tot[k] / cnt[k] : 0.0;
       launches[k] = cnt[k];
     }
@@ -490,16 +492,19 @@ int adg_save_state(adg_ctx* ctx, void* buf, size_t* len) {
     if (c.tick % ticks) adg::throw_err(ADG_E_STATE, "save only at a macro-step boundary");
     const size_t qb = (size_t)c.nt * c.S * 9 * c.B * (c.fp64 ? 8 : 4);
     const size_t eb = c.gfaces.size() * (size_t)c.S * c.Bf * 8;
-    const size_t need = 64 + qb + eb;
+    const size_t fb = c.fault_set ? (size_t)c.nff * c.S * c.Bf * adg::FSTATE * 8 : 0;
+    const size_t need = kStateHeader + qb + eb + fb;
     if (!buf) { *len = need; return; }
     if (*len < need) adg::throw_err(ADG_E_INVALID, "buffer too small");
     char* p = (char*)buf;
-    int64_t hdr[8] = {0x41444731, c.N, c.S, c.nt, c.fp64, (int64_t)c.gfaces.size(), c.tick, 0};
+    int64_t hdr[10] = {0x41444732, c.N, c.S, c.nt, c.fp64, (int64_t)c.gfaces.size(), c.tick, (int64_t)fb, 0, 0};
+    std::memcpy(&hdr[8], &c.time, 8);
     std::memcpy(p, hdr, sizeof(hdr));
-    std::memcpy(p + 56, &c.time, 8);
+    char* body = p + kStateHeader;
     check_cuda(cudaStreamSynchronize(c.stream), "save");
-    check_cuda(cudaMemcpy(p + 64, c.dQ, qb, cudaMemcpyDeviceToHost), "save dofs");
-    if (eb) check_cuda(cudaMemcpy(p + 64 + qb, c.dEta, eb, cudaMemcpyDeviceToHost), "save eta");
+    check_cuda(cudaMemcpy(body, c.dQ, qb, cudaMemcpyDeviceToHost), "save dofs");
+    if (eb) check_cuda(cudaMemcpy(body + qb, c.dEta, eb, cudaMemcpyDeviceToHost), "save eta");
+    if (fb) check_cuda(cudaMemcpy(body + qb + eb, c.dFstate, fb, cudaMemcpyDeviceToHost), "save fault state");
     *len = need;
   });
 }
@@ -510,19 +515,26 @@ int adg_load_state(adg_ctx* ctx, const void* buf, size_t len) {
     Ctx& c = ctx->c;
     need_init(c);
     const char* p = (const char*)buf;
-    int64_t hdr[8];
-    if (len < 64) adg::throw_err(ADG_E_INVALID, "state too short");
+    int64_t hdr[10];
+    if (len < kStateHeader) adg::throw_err(ADG_E_INVALID, "state too short");
     std::memcpy(hdr, p, sizeof(hdr));
     const size_t qb = (size_t)c.nt * c.S * 9 * c.B * (c.fp64 ? 8 : 4);
     const size_t eb = c.gfaces.size() * (size_t)c.S * c.Bf * 8;
-    if (hdr[0] != 0x41444731 || hdr[1] != c.N || hdr[2] != c.S || hdr[3] != c.nt || hdr[4] != (int64_t)c.fp64 ||
-        hdr[5] != (int64_t)c.gfaces.size() || len < 64 + qb + eb)
+    const size_t fb = (size_t)hdr[7];
+    const size_t fb_ctx = (size_t)c.nff * c.S * c.Bf * adg::FSTATE * 8;
+    if (hdr[0] != 0x41444732 || hdr[1] != c.N || hdr[2] != c.S || hdr[3] != c.nt || hdr[4] != (int64_t)c.fp64 ||
+        hdr[5] != (int64_t)c.gfaces.size() || (fb && fb != fb_ctx) || len < kStateHeader + qb + eb + fb)
       adg::throw_err(ADG_E_INVALID, "state does not match this context");
+    const char* body = p + kStateHeader;
     check_cuda(cudaStreamSynchronize(c.stream), "load");
-    check_cuda(cudaMemcpy(c.dQ, p + 64, qb, cudaMemcpyHostToDevice), "load dofs");
-    if (eb) check_cuda(cudaMemcpy(c.dEta, p + 64 + qb, eb, cudaMemcpyHostToDevice), "load eta");
+    check_cuda(cudaMemcpy(c.dQ, body, qb, cudaMemcpyHostToDevice), "load dofs");
+    if (eb) check_cuda(cudaMemcpy(c.dEta, body + qb, eb, cudaMemcpyHostToDevice), "load eta");
+    if (fb) {
+      if (!c.fault_set) adg::throw_err(ADG_E_STATE, "set the fault parameters before loading a fault state");
+      check_cuda(cudaMemcpy(c.dFstate, body + qb + eb, fb, cudaMemcpyHostToDevice), "load fault state");
+    }
     c.tick = hdr[6];
-    std::memcpy(&c.time, p + 56, 8);
+    std::memcpy(&c.time, &hdr[8], 8);
   });
 }
 

@@ -449,7 +449,8 @@ void Ctx::setup() {
         for (int k = 0; k < 81; ++k) gp[6 + k] = Fg[k];
         for (int q = 0; q < 9; ++q) { gp[87 + q] = TA[q * 9 + 0]; gp[96 + q] = TA[q * 9 + 6]; }
       } else if (tg == ADG_TAG_FAULT) {
-        kind = NK_FAULT;  // flux supplied by the rupture solver
+        kind = NK_FAULT;  // flux supplied by the rupture solver from both sides' derivative traces
+        dslot[i * 4 + f] = nd_slots++;
         nbr[i * 4 + f] = (int)inv[nbr_u[4 * eu + f]];
         ninfo[i * 4 + f] = nface_u[4 * eu + f] | (nperm_u[4 * eu + f] << 2) | (kind << 5);
       } else {
@@ -470,12 +471,35 @@ void Ctx::setup() {
   n_bslots = nb_slots;
   n_dslots = nd_slots;
   n_gslots = ng;
-  // fault faces are counted here; the rupture solver owns their state
-  n_fault_faces = 0;
-  for (int64_t e = 0; e < E; ++e)
-    for (int f = 0; f < 4; ++f)
-      if (tag[4 * e + f] == ADG_TAG_FAULT) ++n_fault_faces;
-  if (n_fault_faces) throw Err(ADG_E_INVALID, "fault faces need the rupture solver (adg_upload_fault)");
+  // ---- fault faces: one entry per tet pair, minus side = lower user tet index,
+  // listed in internal (cluster) order; both sides share a cluster by construction
+  fface.clear(); fgeo.clear(); fminus_user.clear(); fplus_user.clear();
+  std::vector<int> fslot((size_t)E * 4, -1);
+  fcl_begin.assign(ncl + 1, 0);
+  for (int64_t i = 0; i < E; ++i) {
+    const int64_t eu = order[i];
+    for (int f = 0; f < 4; ++f) {
+      if (tag[4 * eu + f] != ADG_TAG_FAULT) continue;
+      const int64_t e2u = nbr_u[4 * eu + f];
+      if (e2u < eu) continue;  // listed from the minus side
+      const int f2 = nface_u[4 * eu + f];
+      const int64_t e2 = inv[e2u];
+      const int64_t fi = (int64_t)fface.size() / 5;
+      fface.insert(fface.end(), {(int)i, f, (int)e2, f2, nperm_u[4 * eu + f]});
+      fslot[i * 4 + f] = (int)(2 * fi);
+      fslot[e2 * 4 + f2] = (int)(2 * fi + 1);
+      fminus_user.push_back(4 * eu + f);
+      fplus_user.push_back(4 * e2u + f2);
+      const double* n = &nrm[12 * eu + 3 * f];
+      fgeo.insert(fgeo.end(), {n[0], n[1], n[2], rho[eu], lam[eu], mu[eu], rho[e2u], lam[e2u], mu[e2u]});
+      if (!(mu[eu] > 0 && mu[e2u] > 0)) throw Err(ADG_E_MESH, "fault faces must separate two solids");
+      fcl_begin[cluster[i] + 1]++;
+    }
+  }
+  nff = (int64_t)fface.size() / 5;
+  for (int c = 0; c < ncl; ++c) fcl_begin[c + 1] += fcl_begin[c];
+  n_fault_faces = nff;
+  fault_set = false;
 
   // ---- reference operators in device layouts (l-major / n-major)
   std::vector<double> ktT((size_t)3 * B * B), kvolT((size_t)3 * B1 * B), efcT((size_t)4 * B * Bf),
@@ -531,6 +555,17 @@ void Ctx::setup() {
   dGpar = ng ? upload_raw<double>(gpar, owned, dev_bytes) : nullptr;
   dPerm = upload_raw<int>(ops.perm, owned, dev_bytes);
   dErr = (unsigned int*)dalloc(sizeof(unsigned int), owned, dev_bytes);
+  if (nff) {
+    dFface = upload_raw<int>(fface, owned, dev_bytes);
+    dFslot = upload_raw<int>(fslot, owned, dev_bytes);
+    dFgeo = upload_raw<double>(fgeo, owned, dev_bytes);
+    dFpar = (double*)dalloc((size_t)nff * S * Bf * FPAR * 8, owned, dev_bytes);
+    dFstate = (double*)dalloc((size_t)nff * S * Bf * FSTATE * 8, owned, dev_bytes);
+    dDrout = dalloc((size_t)nff * S * 2 * 9 * Bf * ts, owned, dev_bytes);
+    dNewton = (unsigned long long*)dalloc(2 * sizeof(unsigned long long), owned, dev_bytes);
+    dMlp = (float*)dalloc(MLP_NPARAM * sizeof(float), owned, dev_bytes);
+    dCapCount = (unsigned long long*)dalloc(sizeof(unsigned long long), owned, dev_bytes);
+  }
   // configure kernels once (outside any stream capture)
   StepArgs a0 = base_args();
   int rc = launch_local(fp64, N, a0, 0, stream);
@@ -547,6 +582,7 @@ StepArgs Ctx::base_args() const {
   a.gslot = dGslot; a.bslot = dBslot; a.dslot = dDslot;
   a.ktT = dKt; a.kvolT = dKvol; a.efcT = dEfc; a.liftT = dLift; a.perm = dPerm; a.gpar = dGpar;
   a.S = S; a.err = dErr;
+  a.fslot = dFslot; a.drout = dDrout;
   return a;
 }
 
@@ -592,6 +628,7 @@ void Ctx::launch_tick(int s, double dtm) {
     a.v_begin = cl_begin[c] * S;
     a.dt = dt;
     taylor_int(N, half * dt, (half + 1) * dt, a.ccoef);
+    if (fcl_begin.size() > (size_t)c + 1 && fcl_begin[c + 1] > fcl_begin[c]) launch_rupture_cluster(c, dt);
     ProfEv ev{1, nullptr, nullptr};
     if (prof) {
       CK(cudaEventCreate(&ev.a));
@@ -604,6 +641,36 @@ void Ctx::launch_tick(int s, double dtm) {
   }
 }
 
+// Friction solve on the fault faces of cluster c over its step dt (before the
+// neighbour kernel of that cluster, which lifts the fault fluxes).
+void Ctx::launch_rupture_cluster(int c, double dt) {
+  if (!fault_set) throw Err(ADG_E_STATE, "fault faces present: call adg_set_fault before stepping");
+  DRArgs d{};
+  d.dtrace = dDtrace; d.dslot = dDslot; d.fface = dFface; d.fgeo = dFgeo; d.fpar = dFpar;
+  d.fstate = dFstate; d.drout = dDrout; d.perm = dPerm;
+  d.f_begin = fcl_begin[c];
+  d.n_faces = fcl_begin[c + 1] - fcl_begin[c];
+  d.S = S;
+  d.dt = dt;
+  std::vector<double> x, w;
+  gauss01(N + 1, x, w);
+  for (int j = 0; j <= N; ++j) { d.tp[j] = dt * x[j]; d.tw[j] = dt * w[j]; }
+  d.newton = dNewton; d.err = dErr;
+  d.mlp = mlp_on ? dMlp : nullptr;
+  d.capture = cap_on ? dCapture : nullptr;
+  d.cap_count = dCapCount;
+  d.cap_capacity = cap_capacity;
+  ProfEv ev{2, nullptr, nullptr};
+  if (prof) {
+    CK(cudaEventCreate(&ev.a));
+    CK(cudaEventCreate(&ev.b));
+    CK(cudaEventRecord(ev.a, stream));
+  }
+  int rc = launch_rupture(fp64, N, d, stream);
+  if (prof) { CK(cudaEventRecord(ev.b, stream)); prof->push_back(ev); }
+  if (rc) throw Err(ADG_E_CUDA, std::string("rupture kernel: ") + cudaGetErrorString((cudaError_t)rc));
+}
+
 int64_t Ctx::launches_per_macro() const {
   int64_t L = 0;
   const int ticks = 1 << (ncl - 1);
@@ -611,7 +678,7 @@ int64_t Ctx::launches_per_macro() const {
     for (int c = 0; c < ncl; ++c) {
       if (cl_begin[c + 1] == cl_begin[c]) continue;
       if (s % (1 << c) == 0) ++L;
-      if ((s + 1) % (1 << c) == 0) ++L;
+      if ((s + 1) % (1 << c) == 0) L += (fcl_begin[c + 1] > fcl_begin[c]) ? 2 : 1;
     }
   return L;
 }

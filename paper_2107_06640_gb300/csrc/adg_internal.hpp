@@ -20,6 +20,12 @@ struct AdgError : std::runtime_error {
 [[noreturn]] void throw_err(int code, const std::string& m);
 void tet_rule(int deg, std::vector<double>& pts, std::vector<double>& w);
 
+// friction-guess network training (mlp.cu)
+int mlp_trainable();
+int launch_mlp_grad(const float* P, const float* rows, int64_t row0, int64_t n, int64_t n_norm, float* grad,
+                    double* loss, void* stream);
+int launch_adam(float* P, const float* g, float* m, float* v, float lr, int step, void* stream);
+
 // receiver readout kernel launcher (readout.cu)
 int launch_receivers(int fp64, int B, const void* Q, int S, int64_t n, const int64_t* elem,
                      const double* phi, double* out, void* stream);
@@ -59,6 +65,25 @@ struct Ctx {
   unsigned int* dErr = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
   bool use_graph = true;
+  // dynamic rupture: fault faces in internal (cluster) order
+  int64_t nff = 0;
+  std::vector<int> fface;                 // [nff][5] minus elem, face, plus elem, face, perm
+  std::vector<int64_t> fcl_begin;         // per cluster ranges of fault faces
+  std::vector<int64_t> fminus_user, fplus_user;  // user tet*4+face of both sides
+  std::vector<double> fgeo;               // [nff][FGEO]
+  int *dFface = nullptr, *dFslot = nullptr;
+  double *dFgeo = nullptr, *dFpar = nullptr, *dFstate = nullptr;
+  void* dDrout = nullptr;
+  unsigned long long* dNewton = nullptr;
+  bool fault_set = false;
+  // friction-guess network and training-sample capture
+  float* dMlp = nullptr;
+  bool mlp_on = false;
+  float* dCapture = nullptr;
+  unsigned long long* dCapCount = nullptr;
+  int64_t cap_capacity = 0;
+  bool cap_on = false;
+  void launch_rupture_cluster(int c, double dt);
   // per-kernel profiling (adg_profile)
   struct ProfEv { int kind; cudaEvent_t a, b; };
   std::vector<ProfEv>* prof = nullptr;

@@ -59,7 +59,44 @@ struct StepArgs {
   double ccoef[8];      // (tb^{k+1}-ta^{k+1})/(k+1)! on a coarser neighbour's expansion
   double dt;            // own step (gravity ODE)
   unsigned int* err;    // device error word
+  const int* fslot;     // [E][4] 2*fault + side for fault faces, else -1
+  const void* drout;    // T [nff*S][2][9][Bf] time-integrated fault flux per side
 };
+
+// ---- dynamic rupture (rupture.cu) ----
+// per-node fault parameters (double, stride FPAR), in this order:
+//   a, b, L, f0, V0, f_w, V_w, sigma_n0, tau0_x, tau0_y, tau0_z, psi_init, V_init
+constexpr int FPAR = 13;
+// per-node fault state (double, stride FSTATE): |V|, psi, slip_xyz, traction_xyz
+constexpr int FSTATE = 8;
+// per-fault-face geometry (double, stride FGEO): n (minus outward), rho-, lam-, mu-, rho+, lam+, mu+
+constexpr int FGEO = 9;
+// friction-guess network: inputs, hidden width (two tanh layers), parameters
+constexpr int MLP_IN = 6, MLP_H = 32;
+constexpr int MLP_NPARAM = MLP_IN * MLP_H + MLP_H + MLP_H * MLP_H + MLP_H + MLP_H + 1 + 2 * MLP_IN + 2;
+
+struct DRArgs {
+  const void* dtrace;   // derivative traces of both sides (see StepArgs)
+  const int* dslot;
+  const int* fface;     // [nff][5] minus elem, minus face, plus elem, plus face, perm
+  const double* fgeo;   // [nff][FGEO]
+  const double* fpar;   // [nff*S][Bf][FPAR]
+  double* fstate;       // [nff*S][Bf][FSTATE]
+  void* drout;          // T [nff*S][2][9][Bf]
+  const int* perm;      // [6][Bf]
+  int64_t f_begin, n_faces;
+  int S;
+  double dt;
+  double tp[8], tw[8];  // Gauss-Legendre time points / weights on [0, dt]
+  unsigned long long* newton;  // [0] solves, [1] iterations
+  unsigned int* err;
+  const float* mlp;     // network parameters (or null: plain start)
+  float* capture;       // training samples [cap][MLP_IN + 1] (or null)
+  unsigned long long* cap_count;
+  int64_t cap_capacity;
+};
+
+int launch_rupture(int fp64, int N, const DRArgs& a, void* stream);
 
 enum { ERR_NAN = 1u, ERR_TIMEOUT = 2u, ERR_NEWTON = 4u };
 

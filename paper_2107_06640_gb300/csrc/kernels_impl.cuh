@@ -333,7 +333,11 @@ __global__ void __launch_bounds__(kThreads) neighbour_kernel(StepArgs a) {
   for (int r = tid; r < 36 * Bf; r += nth) {
     const int f = r / (9 * Bf), q = (r / Bf) % 9, n = r % Bf;
     T acc = T(0);
-    if (sKind[f] != NK_NONE) {
+    if (sKind[f] == NK_FAULT) {
+      // time-integrated fault flux of this side, already in this face's node order
+      const int fsl = a.fslot[e * 4 + f];
+      acc = reinterpret_cast<const T*>(a.drout)[((((int64_t)(fsl >> 1) * a.S + s) * 2 + (fsl & 1)) * 9 + q) * Bf + n];
+    } else if (sKind[f] != NK_NONE) {
 #pragma unroll
       for (int p = 0; p < 9; ++p) acc += sFp[f * 81 + q * 9 + p] * sV[(f * 9 + p) * Bf + n];
     }

@@ -1,0 +1,305 @@
+// Dynamic-rupture friction solve (Sec. 3, Eq. bc-dynrup) on fault faces,
+// FP64, one thread per fault node and scenario.
+//
+// Readings (the paper names fast-velocity-weakening rate and state friction
+// but prints neither f nor g):
+//   f(V, psi)  = a asinh(V/(2 V0) exp(psi/a))
+//   dpsi/dt    = -(V/L)(psi - psi_ss(V)),  psi_ss = a ln((2V0/V) sinh(f_ss/a)),
+//   f_ss       = f_w + (f0 - (b-a) ln(V/V0) - f_w) / (1 + (V/V_w)^8)^(1/8);
+//   strength S = max(0, -(sigma_n0 + sigma_n^b)) with sigma_n^b the welded P
+//   middle state; locked shear traction theta = eta_s [(u+ - u-) + tau+/Zs+ +
+//   tau-/Zs-], eta_s = Zs- Zs+/(Zs- + Zs+); |V| solves
+//   Theta - eta_s |V| = S f(|V|, psi), Theta = |tau0 + theta|, V parallel to
+//   tau0 + theta.  Per step: N+1 Gauss-Legendre time points; at each, two
+//   passes of [exact psi relaxation for a frozen slip rate (pass 0: the
+//   previous one, pass 1: the mid-point of previous and pass-0 rates), Newton
+//   on x = ln |V| clamped to [-700, ln(Theta/eta_s)], |dx| <= 1e-10]; the
+//   learned guess only seeds the pass-0 Newton, so the answer does not
+//   depend on it.
+// Output per fault face: the time-integrated flux n.(A,B,C) q^b for the minus
+// element (minus node order) and -n.(A,B,C) q^c for the plus element (plus
+// node order); the neighbour kernel lifts them.
+#include <cuda_runtime.h>
+
+#include "kernels.cuh"
+
+namespace adg {
+
+namespace {
+
+constexpr double kTol = 1e-10;
+constexpr int kMaxIter = 100;
+constexpr double kXFloor = -700.0;
+
+struct FricPar {
+  double a, b, L, f0, V0, fw, Vw;
+};
+
+__device__ double f_ss(double V, const FricPar& p) {
+  const double fLV = p.f0 - (p.b - p.a) * log(V / p.V0);
+  const double r = V / p.Vw;
+  const double r2 = r * r, r4 = r2 * r2, r8 = r4 * r4;
+  return p.fw + (fLV - p.fw) / pow(1.0 + r8, 0.125);
+}
+
+__device__ double psi_relax(double psi, double V, double h, const FricPar& p) {
+  // exact solution of dpsi/dt = -(V/L)(psi - psi_ss(V)) for frozen V over h
+  // (V floored at 1e-300: for V -> 0 the state does not change)
+  V = fmax(V, 1e-300);
+  const double x = f_ss(V, p) / p.a;
+  const double lsinh = x + log1p(-exp(-2.0 * x)) - 0.6931471805599453;  // ln sinh(x)
+  const double ss = p.a * (log(2.0 * p.V0 / V) + lsinh);
+  return ss + (psi - ss) * exp(-V * h / p.L);
+}
+
+// Newton on x = ln V for Theta - eta V - S a asinh(c V) = 0 (decreasing, concave in x)
+__device__ double newton_v(double Th, double S, double eta, double psi, const FricPar& p, double x0,
+                           int* iters, bool* ok) {
+  *iters = 0;
+  *ok = true;
+  if (!(Th > 0)) return 0.0;
+  if (S == 0.0) return Th / eta;
+  const double lc = psi / p.a - log(2.0 * p.V0);
+  const double hi = log(Th / eta);
+  double x = fmin(fmax(x0, kXFloor), hi);
+  for (int it = 0; it < kMaxIter; ++it) {
+    const double V = exp(x);
+    const double cv = exp(lc + x);
+    const double g = Th - eta * V - S * p.a * asinh(cv);
+    const double dg = -eta * V - S * p.a * cv / sqrt(1.0 + cv * cv);
+    const double xn = fmin(fmax(x - g / dg, kXFloor), hi);
+    const double step = fabs(xn - x);
+    x = xn;
+    if (step <= kTol) {
+      *iters = it + 1;
+      return exp(x);
+    }
+  }
+  *iters = kMaxIter;
+  *ok = false;
+  return exp(x);
+}
+
+// n.(A,B,C) applied to a state with traction t = sigma n and velocity v
+__device__ void ahat(const double n[3], const double t[3], const double v[3], double rho, double lam, double mu,
+                     double sgn, double w, double* acc) {
+  const double nv = n[0] * v[0] + n[1] * v[1] + n[2] * v[2];
+  const int pi[6] = {0, 1, 2, 0, 1, 0}, pj[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+  for (int c = 0; c < 6; ++c) {
+    double s = -mu * (n[pj[c]] * v[pi[c]] + n[pi[c]] * v[pj[c]]);
+    if (c < 3) s -= lam * nv;
+    acc[c] += sgn * w * s;
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i) acc[6 + i] += sgn * w * (-t[i] / rho);
+}
+
+__device__ void traction(const double q[9], const double n[3], double t[3]) {
+  t[0] = q[0] * n[0] + q[3] * n[1] + q[5] * n[2];
+  t[1] = q[3] * n[0] + q[1] * n[1] + q[4] * n[2];
+  t[2] = q[5] * n[0] + q[4] * n[1] + q[2] * n[2];
+}
+
+// friction-guess network (FP32): features -> predicted ln V
+__device__ float mlp_eval(const float* W, const float f[MLP_IN]) {
+  const float* W1 = W;
+  const float* b1 = W1 + MLP_IN * MLP_H;
+  const float* W2 = b1 + MLP_H;
+  const float* b2 = W2 + MLP_H * MLP_H;
+  const float* w3 = b2 + MLP_H;
+  const float* b3 = w3 + MLP_H;
+  const float* mu = b3 + 1;
+  const float* sd = mu + MLP_IN;
+  const float* osc = sd + MLP_IN;  // output shift, scale
+  float x[MLP_IN], h1[MLP_H];
+#pragma unroll
+  for (int i = 0; i < MLP_IN; ++i) x[i] = (f[i] - mu[i]) / sd[i];
+  for (int j = 0; j < MLP_H; ++j) {
+    float s = b1[j];
+#pragma unroll
+    for (int i = 0; i < MLP_IN; ++i) s += W1[j * MLP_IN + i] * x[i];
+    h1[j] = tanhf(s);
+  }
+  float y = b3[0];
+  for (int j = 0; j < MLP_H; ++j) {
+    float s = b2[j];
+    for (int i = 0; i < MLP_H; ++i) s += W2[j * MLP_H + i] * h1[i];
+    y += w3[j] * tanhf(s);
+  }
+  return osc[0] + osc[1] * y;
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(128) rupture_kernel(DRArgs a) {
+  constexpr int Bf = nb2(N);
+  const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t total = a.n_faces * a.S * Bf;
+  if (id >= total) return;
+  const int n = (int)(id % Bf);
+  const int64_t fs = id / Bf;
+  const int64_t fi = a.f_begin + fs / a.S;
+  const int s = (int)(fs % a.S);
+  const int* ff = a.fface + fi * 5;
+  const int em = ff[0], fm = ff[1], ep = ff[2], fp = ff[3], pm = ff[4];
+  const double* g = a.fgeo + fi * FGEO;
+  const double nrm[3] = {g[0], g[1], g[2]};
+  const double rhom = g[3], lamm = g[4], mum = g[5], rhop = g[6], lamp = g[7], mup = g[8];
+  const double Zpm = sqrt(rhom * (lamm + 2 * mum)), Zsm = sqrt(rhom * mum);
+  const double Zpp = sqrt(rhop * (lamp + 2 * mup)), Zsp = sqrt(rhop * mup);
+  const double eta = Zsm * Zsp / (Zsm + Zsp);
+  const int np_ = a.perm[pm * Bf + n];
+  const T* dm = reinterpret_cast<const T*>(a.dtrace) + ((int64_t)a.dslot[em * 4 + fm] * a.S + s) * (N + 1) * 9 * Bf;
+  const T* dp = reinterpret_cast<const T*>(a.dtrace) + ((int64_t)a.dslot[ep * 4 + fp] * a.S + s) * (N + 1) * 9 * Bf;
+  const double* par = a.fpar + ((fi * a.S + s) * Bf + n) * FPAR;
+  double* st = a.fstate + ((fi * a.S + s) * Bf + n) * FSTATE;
+  const FricPar p{par[0], par[1], par[2], par[3], par[4], par[5], par[6]};
+  const double sn0 = par[7];
+  double t0s[3] = {par[8], par[9], par[10]};
+  {
+    const double t0n = t0s[0] * nrm[0] + t0s[1] * nrm[1] + t0s[2] * nrm[2];
+    for (int i = 0; i < 3; ++i) t0s[i] -= t0n * nrm[i];
+  }
+  double V = st[0], psi = st[1];
+  double slip[3] = {st[2], st[3], st[4]};
+  double tau_tot[3] = {st[5], st[6], st[7]};
+  double Gm[9] = {0}, Gp[9] = {0};
+  double tprev = 0.0;
+  unsigned long long n_solves = 0, n_iters = 0;
+  bool all_ok = true;
+  for (int j = 0; j <= N; ++j) {
+    const double t = a.tp[j];
+    double qm[9], qp[9];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) {
+      double am = 0, ap = 0, tk = 1.0, fac = 1.0;
+      for (int k = 0; k <= N; ++k) {
+        am += tk / fac * (double)dm[(k * 9 + c) * Bf + n];
+        ap += tk / fac * (double)dp[(k * 9 + c) * Bf + np_];
+        tk *= t;
+        fac *= (k + 1);
+      }
+      qm[c] = am;
+      qp[c] = ap;
+    }
+    double Tm[3], Tp[3];
+    traction(qm, nrm, Tm);
+    traction(qp, nrm, Tp);
+    const double snm = Tm[0] * nrm[0] + Tm[1] * nrm[1] + Tm[2] * nrm[2];
+    const double snp = Tp[0] * nrm[0] + Tp[1] * nrm[1] + Tp[2] * nrm[2];
+    const double vnm = qm[6] * nrm[0] + qm[7] * nrm[1] + qm[8] * nrm[2];
+    const double vnp = qp[6] * nrm[0] + qp[7] * nrm[1] + qp[8] * nrm[2];
+    double taum[3], taup[3], um[3], up[3], Thv[3];
+    const double a1 = Zpm * Zpp / (Zpm + Zpp) * ((snm - snp) / Zpp + vnm - vnp);
+    const double sn_b = snm - a1, vn_b = vnm - a1 / Zpm;
+    for (int i = 0; i < 3; ++i) {
+      taum[i] = Tm[i] - snm * nrm[i];
+      taup[i] = Tp[i] - snp * nrm[i];
+      um[i] = qm[6 + i] - vnm * nrm[i];
+      up[i] = qp[6 + i] - vnp * nrm[i];
+      Thv[i] = t0s[i] + eta * ((up[i] - um[i]) + taup[i] / Zsp + taum[i] / Zsm);
+    }
+    const double Th = sqrt(Thv[0] * Thv[0] + Thv[1] * Thv[1] + Thv[2] * Thv[2]);
+    const double S = fmax(0.0, -(sn0 + sn_b));
+    const double h = t - tprev;
+    const double Vold = V;
+    double x0 = log(fmax(V, 1e-300));
+    double xa = 0.0;
+    float feat[MLP_IN];
+    const bool solve = (Th > 0) && (S > 0);
+    if (solve && (a.mlp || a.capture)) {
+      const double lc = psi / p.a - log(2.0 * p.V0);
+      const double xhi = log(Th / eta);
+      const double r = fmin(Th / (S * p.a), 700.0);
+      xa = fmin(fmax(r - lc - 0.6931471805599453, kXFloor), xhi);
+      feat[0] = (float)r;
+      feat[1] = (float)lc;
+      feat[2] = (float)xhi;
+      feat[3] = (float)fmin(fmax(x0, kXFloor), xhi);
+      feat[4] = (float)fmin(fmax(log(eta / (S * p.a)), -50.0), 50.0);
+      feat[5] = (float)xa;
+      if (a.mlp) x0 = fmin(fmax(xa + (double)mlp_eval(a.mlp, feat), kXFloor), xhi);
+    }
+    double Vcur = exp(x0);
+    if (!(Vcur > 0)) Vcur = 0.0;
+    double psi_new = psi;
+    for (int pass = 0; pass < 2; ++pass) {
+      // the start guess only seeds Newton; pass 0 relaxes psi with the previous
+      // slip rate, pass 1 with the mid-point of the previous and pass-0 rates
+      const double Vmid = pass == 0 ? Vold : 0.5 * (Vold + Vcur);
+      psi_new = psi_relax(psi, Vmid, h, p);
+      int it;
+      bool ok;
+      Vcur = newton_v(Th, S, eta, psi_new, p, log(fmax(Vcur, 1e-300)), &it, &ok);
+      all_ok &= ok;
+      if (solve) {
+        n_solves++;
+        n_iters += it;
+      }
+      if (pass == 0 && solve && a.capture) {
+        const unsigned long long k = atomicAdd(a.cap_count, 1ull);
+        if ((int64_t)k < a.cap_capacity) {
+          float* row = a.capture + k * (MLP_IN + 1);
+          for (int i = 0; i < MLP_IN; ++i) row[i] = feat[i];
+          row[MLP_IN] = (float)(log(fmax(Vcur, 1e-300)) - xa);
+        }
+      }
+    }
+    psi = psi_new;
+    V = Vcur;
+    double d[3] = {0, 0, 0};
+    if (Th > 0)
+      for (int i = 0; i < 3; ++i) d[i] = Thv[i] / Th;
+    double tb[3], vb[3], vc[3];
+    for (int i = 0; i < 3; ++i) {
+      tau_tot[i] = (Th - eta * V) * d[i];
+      const double tp_ = tau_tot[i] - t0s[i];
+      tb[i] = sn_b * nrm[i] + tp_;
+      vb[i] = vn_b * nrm[i] + um[i] + (tp_ - taum[i]) / Zsm;
+      vc[i] = vn_b * nrm[i] + up[i] - (tp_ - taup[i]) / Zsp;
+      slip[i] += a.tw[j] * V * d[i];
+    }
+    ahat(nrm, tb, vb, rhom, lamm, mum, 1.0, a.tw[j], Gm);
+    ahat(nrm, tb, vc, rhop, lamp, mup, -1.0, a.tw[j], Gp);
+    tprev = t;
+  }
+  psi = psi_relax(psi, V, a.dt - tprev, p);
+  st[0] = V;
+  st[1] = psi;
+  for (int i = 0; i < 3; ++i) {
+    st[2 + i] = slip[i];
+    st[5 + i] = tau_tot[i];
+  }
+  T* out = reinterpret_cast<T*>(a.drout) + (fi * a.S + s) * 2 * 9 * Bf;
+  for (int c = 0; c < 9; ++c) {
+    out[c * Bf + n] = (T)Gm[c];
+    out[(9 + c) * Bf + np_] = (T)Gp[c];
+  }
+  if (!all_ok) atomicOr(a.err, ERR_NEWTON);
+  atomicAdd(&a.newton[0], n_solves);
+  atomicAdd(&a.newton[1], n_iters);
+}
+
+template <typename T>
+int dispatch(int N, const DRArgs& a, cudaStream_t st) {
+  const int64_t total = a.n_faces * a.S * nb2(N);
+  if (total <= 0) return 0;
+  const unsigned grid = (unsigned)((total + 127) / 128);
+  switch (N) {
+    case 1: rupture_kernel<T, 1><<<grid, 128, 0, st>>>(a); break;
+    case 2: rupture_kernel<T, 2><<<grid, 128, 0, st>>>(a); break;
+    case 3: rupture_kernel<T, 3><<<grid, 128, 0, st>>>(a); break;
+    case 4: rupture_kernel<T, 4><<<grid, 128, 0, st>>>(a); break;
+    case 5: rupture_kernel<T, 5><<<grid, 128, 0, st>>>(a); break;
+    default: return (int)cudaErrorInvalidValue;
+  }
+  return (int)cudaGetLastError();
+}
+
+}  // namespace
+
+int launch_rupture(int fp64, int N, const DRArgs& a, void* stream) {
+  return fp64 ? dispatch<double>(N, a, (cudaStream_t)stream) : dispatch<float>(N, a, (cudaStream_t)stream);
+}
+
+}  // namespace adg

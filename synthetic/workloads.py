@@ -103,6 +103,62 @@ def uplift_scenarios(S, L=100e3, seed=0):
     return out
 
 
+def fault_box(nx=8, ny=4, nz=4, dz=1e3, dip_deg=15.0, width=None, ocean_layers=0, water=2e3,
+              material=CRUST):
+    """Megathrust-style box: a Kuhn grid whose hexes are stretched so that the
+    index diagonal plane i - k = 0 dips `dip_deg` (dx = dz / tan(dip)); its
+    faces between j in [0, width] become a planar fault (tag 5).  Optionally
+    `ocean_layers` of water (OCEAN material, gravitational top) sit on top of
+    the crust layers.  Sides absorbing."""
+    dx = dz / np.tan(np.radians(dip_deg))
+    xs = np.arange(nx + 1) * dx
+    ys = np.arange(ny + 1) * dx
+    if ocean_layers:
+        zs = np.concatenate([np.linspace(-water - nz * dz, -water, nz + 1),
+                             np.linspace(-water, 0.0, ocean_layers + 1)[1:]])
+    else:
+        zs = np.linspace(-nz * dz, 0.0, nz + 1)
+    width = ny if width is None else width
+    tags = {"x-": TAG_ABSORB, "x+": TAG_ABSORB, "y-": TAG_ABSORB, "y+": TAG_ABSORB, "z-": TAG_ABSORB,
+            "z+": TAG_GRAVITY if ocean_layers else TAG_ABSORB}
+    m = kuhn_box(xs, ys, zs, tags=tags, fault=dict(c=0, jrange=(0, width), krange=(0, nz)))
+    wet = m.hex_index[:, 2] >= nz
+    rho = np.where(wet, OCEAN[0], material[0])
+    lam = np.where(wet, OCEAN[1], material[1])
+    mu = np.where(wet, OCEAN[2], material[2])
+    return m, (rho, lam, mu)
+
+
+def rs_fault_params(node_xyz, normal, seed=0, patch_center=None, patch_radius=3e3, sn0=-40e6,
+                    tau_ratio=0.55, patch_ratio=0.85, noise=0.05, psi0=0.6, V_init=1e-12):
+    """Per-node rate-and-state parameters [nff, Bf, 13] (a, b, L, f0, V0, f_w,
+    V_w, sigma_n0, tau0_xyz, psi_init, V_init): a, b, L, f0, V0 uniform with
+    seeded +-noise relative perturbations; f_w = 0.1, V_w = 0.1 m/s; uniform
+    normal stress sn0 (compression negative); shear prestress along the
+    up-dip direction with |tau0| = tau_ratio |sn0|, raised to patch_ratio |sn0|
+    inside a circular nucleation patch (overstress)."""
+    rng = np.random.default_rng(seed)
+    nff, Bf, _ = node_xyz.shape
+    base = dict(a=0.01, b=0.014, L=0.2, f0=0.6, V0=1e-6)
+    out = np.zeros((nff, Bf, 13))
+    for k, (name, v) in enumerate(base.items()):
+        out[..., k] = v * (1.0 + noise * rng.uniform(-1.0, 1.0, (nff, Bf)))
+    out[..., 5] = 0.1
+    out[..., 6] = 0.1
+    out[..., 7] = sn0
+    up = np.array([0.0, 0.0, 1.0])
+    d = up[None, :] - np.sum(normal * up, 1, keepdims=True) * normal
+    d /= np.maximum(np.linalg.norm(d, axis=1, keepdims=True), 1e-30)
+    if patch_center is None:
+        patch_center = node_xyz.reshape(-1, 3).mean(0)
+    r = np.linalg.norm(node_xyz - np.asarray(patch_center)[None, None, :], axis=2)
+    mag = np.where(r < patch_radius, patch_ratio, tau_ratio) * abs(sn0)
+    out[..., 8:11] = mag[..., None] * d[:, None, :]
+    out[..., 11] = psi0
+    out[..., 12] = V_init
+    return out
+
+
 def random_dofs(shape, seed, decay=0.5, N=None):
     """Seeded random modal coefficients (any basis layout); optional decay by
     basis index keeps higher modes smaller."""
