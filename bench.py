@@ -188,6 +188,110 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
+def _timed_advance(s, steps, warm, stream, torch, tag):
+    import numpy as np  # noqa: F401
+    s.advance(warm)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else "_work",
+                                   f"clocks_{tag}.csv")) as cs:
+        ev0.record(stream)
+        s.advance(steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    return ev0.elapsed_time(ev1), cs.summary(torch.cuda.current_device())
+
+
+def run_other_workload(args):
+    """LTS, rupture and ensemble workloads: one JSON line each (single GPU)."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2107_06640_gb300 as pkg
+    from paper_2107_06640_gb300 import Solver, _lib
+    from synthetic.workloads import coupled_box, fault_box, rs_fault_params, uplift_scenarios
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    steps, warm = args.steps, args.warmup
+    line = {"metric": METRIC, "unit": UNIT, "n_gpus": 1, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "data": "synthetic", "warmup": warm}
+    t_setup = time.perf_counter()
+    if args.workload == "lts":
+        L = 100e3
+        bathy = lambda x, y: -2000.0 + 500.0 * np.sin(2 * np.pi * x / L) * np.sin(2 * np.pi * y / L)
+        m, (rho, lam, mu) = coupled_box(nxy=200, bathy=bathy, grading=32.0)
+        s = Solver(m.xyz, m.tets, m.face_tag, rho, lam, mu, degree=N_DEG, precision=pkg.ADG_FP32, cfl=0.35,
+                   max_clusters=6, stream=stream.cuda_stream)
+        ef, nxyz = s.gravity_faces()
+        s.set_eta(np.exp(-((nxyz[..., 0] - L / 2) ** 2 + (nxyz[..., 1] - L / 2) ** 2) / (2 * 8e3 ** 2))[:, None, :])
+        info = s.info
+        hist = [int(info.cluster_size[c]) for c in range(info.n_clusters)]
+        upd = int(info.updates_per_macro)
+        gts_upd = s.nt * (1 << (info.n_clusters - 1))
+        line["config"] = {"workload": f"LTS-graded coupled box, sin bathymetry +-500 m, x/y grading 32x, "
+                                      f"{s.nt} tets, degree 5", "n_tets": s.nt, "clusters": hist,
+                          "lts_update_reduction": gts_upd / upd, "macro_dt": info.macro_dt}
+        line["dtype"] = "f32"
+    elif args.workload == "rupture":
+        r = 3
+        m, (rho, lam, mu) = fault_box(nx=32 * r, ny=40 * r, nz=16 * r, dz=1e3 / r, dip_deg=15.0,
+                                      ocean_layers=2 * r, water=2e3)
+        s = Solver(m.xyz, m.tets, m.face_tag, rho, lam, mu, degree=4, precision=pkg.ADG_FP32, cfl=0.35,
+                   max_clusters=1, stream=stream.cuda_stream)
+        nff = int(s.info.n_fault_faces)
+        mf, pf, fxyz, fn = _lib.adg_fault_faces(s.ctx, nff, s.Bf)
+        c = fxyz.reshape(-1, 3).mean(0)
+        par = rs_fault_params(fxyz, fn, seed=0, patch_center=c, patch_radius=8e3)
+        _lib.adg_set_fault(s.ctx, par[:, None])
+        upd = int(s.info.updates_per_macro)
+        line["config"] = {"workload": f"15-degree planar megathrust 150 x 60 km under 2 km ocean with gravity, "
+                                      f"rate-and-state fast-velocity-weakening friction, {s.nt} tets, degree 4",
+                          "n_tets": s.nt, "fault_faces": nff, "fault_nodes": nff * s.Bf}
+        line["dtype"] = "f32 (friction f64)"
+    else:
+        S = 32
+        m, (rho, lam, mu) = coupled_box(nxy=66)
+        s = Solver(m.xyz, m.tets, m.face_tag, rho, lam, mu, degree=N_DEG, precision=pkg.ADG_FP32, cfl=0.35,
+                   ensemble=S, stream=stream.cuda_stream)
+        ef, nxyz = s.gravity_faces()
+        eta0 = np.stack([f(nxyz[..., 0], nxyz[..., 1]) for f in uplift_scenarios(S, seed=0)], axis=1)
+        s.set_eta(eta0)
+        upd = int(s.info.updates_per_macro)
+        line["config"] = {"workload": f"ensemble of {S} seafloor-uplift scenarios (8 Gaussian bumps, 0.1-2 m) "
+                                      f"on a {s.nt}-tet coupled box, degree 5; 64 scenarios = 2 passes of {S}",
+                          "n_tets": s.nt, "ensemble": S}
+        line["dtype"] = "f32"
+    t_setup = time.perf_counter() - t_setup
+    ms, clk = _timed_advance(s, steps, warm, stream, torch, args.workload)
+    line.update({"value": upd * steps / (ms * 1e-3), "steps": steps, "ms_per_step": ms / steps, "clocks": clk,
+                 "setup_s": t_setup})
+    kms, kcnt = _lib.adg_profile(s.ctx, 1)
+    line["kernel_ms"] = {"local": kms[0], "neighbour": kms[1], "rupture": kms[2],
+                         "launches_per_macro": [int(x) for x in kcnt]}
+    line["gpu_launches"] = int(kcnt.sum()) * steps
+    if args.workload == "rupture":
+        solves, iters = _lib.adg_fault_stats(s.ctx, reset=True)
+        # learned Newton start: capture, train on the GPU, rerun the same steps
+        state = s.save_state()
+        _lib.adg_rupture_capture(s.ctx, 1 << 22)
+        s.advance(steps)
+        ncap = _lib.adg_rupture_capture(s.ctx, 0)
+        s0, i0 = _lib.adg_fault_stats(s.ctx, reset=True)
+        loss = _lib.adg_mlp_train(s.ctx, epochs=30, batch=4096, lr=3e-3, seed=0)
+        s.load_state(state)
+        _lib.adg_mlp_params(s.ctx, enable=1)
+        t0 = time.perf_counter()
+        s.advance(steps)
+        torch.cuda.synchronize()
+        s1, i1 = _lib.adg_fault_stats(s.ctx, reset=True)
+        line["rupture"] = {"newton_iters_per_solve_plain": i0 / max(s0, 1),
+                           "newton_iters_per_solve_learned": i1 / max(s1, 1), "training_solves": ncap,
+                           "train_loss": [float(loss[0]), float(loss[1])], "solves_per_step": s0 / steps,
+                           "friction_kernel_ms": kms[2]}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -199,7 +303,12 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--nxy", type=int, default=80,
                     help="hex columns per side (80: the 1.5 M-tet workload; smaller for profiling)")
+    ap.add_argument("--workload", default="coupled", choices=["coupled", "lts", "rupture", "ensemble"],
+                    help="coupled: the headline line; lts / rupture / ensemble: the other workloads")
     args = ap.parse_args()
+    if args.workload != "coupled":
+        run_other_workload(args)
+        return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))

@@ -270,36 +270,41 @@ void Ctx::setup() {
   std::vector<int64_t> nbr_u(4 * E, -1);
   std::vector<int> nface_u(4 * E, -1), nperm_u(4 * E, -1);
   {
-    std::unordered_map<std::string, int64_t> table;
-    table.reserve((size_t)(2 * E + 16));
-    auto key = [&](int64_t e, int f) {
-      int64_t v[3] = {tets[4 * e + kFaceV[f][0]], tets[4 * e + kFaceV[f][1]], tets[4 * e + kFaceV[f][2]]};
-      std::sort(v, v + 3);
-      return std::string((const char*)v, sizeof(v));
+    // match interior/fault faces by their sorted vertex triples: sort all
+    // triples, then equal neighbours in the sorted list are the two sides
+    struct FK {
+      int64_t v0, v1, v2, id;
     };
+    std::vector<FK> keys;
+    keys.reserve((size_t)(4 * E));
     for (int64_t e = 0; e < E; ++e)
       for (int f = 0; f < 4; ++f) {
         int tg = tag[4 * e + f];
         if (tg < 0 || tg > 6) throw Err(ADG_E_MESH, "unknown face tag");
         if (tg != ADG_TAG_INTERIOR && tg != ADG_TAG_FAULT) continue;
-        std::string k = key(e, f);
-        auto it = table.find(k);
-        if (it == table.end()) {
-          table.emplace(k, 4 * e + f);
-        } else {
-          int64_t o = it->second;
-          if (o < 0) throw Err(ADG_E_MESH, "face shared by more than two tets");
-          int64_t e2 = o / 4;
-          int f2 = (int)(o % 4);
-          if (tag[4 * e2 + f2] != tg) throw Err(ADG_E_MESH, "fault face tagged on one side only");
-          nbr_u[4 * e + f] = e2; nface_u[4 * e + f] = f2;
-          nbr_u[4 * e2 + f2] = e; nface_u[4 * e2 + f2] = f;
-          it->second = -1;
-        }
+        int64_t v[3] = {tets[4 * e + kFaceV[f][0]], tets[4 * e + kFaceV[f][1]], tets[4 * e + kFaceV[f][2]]};
+        std::sort(v, v + 3);
+        keys.push_back({v[0], v[1], v[2], 4 * e + f});
       }
-    for (auto& kv : table)
-      if (kv.second >= 0) throw Err(ADG_E_MESH, "interior face without a matching neighbour (tet " +
-                                                    std::to_string(kv.second / 4) + ")");
+    auto less = [](const FK& a, const FK& b) {
+      if (a.v0 != b.v0) return a.v0 < b.v0;
+      if (a.v1 != b.v1) return a.v1 < b.v1;
+      if (a.v2 != b.v2) return a.v2 < b.v2;
+      return a.id < b.id;
+    };
+    std::sort(keys.begin(), keys.end(), less);
+    auto same = [](const FK& a, const FK& b) { return a.v0 == b.v0 && a.v1 == b.v1 && a.v2 == b.v2; };
+    for (size_t k = 0; k < keys.size();) {
+      if (k + 1 >= keys.size() || !same(keys[k], keys[k + 1]))
+        throw Err(ADG_E_MESH, "interior face without a matching neighbour (tet " + std::to_string(keys[k].id / 4) + ")");
+      if (k + 2 < keys.size() && same(keys[k], keys[k + 2])) throw Err(ADG_E_MESH, "face shared by more than two tets");
+      const int64_t e = keys[k].id / 4, e2 = keys[k + 1].id / 4;
+      const int f = (int)(keys[k].id % 4), f2 = (int)(keys[k + 1].id % 4);
+      if (tag[4 * e2 + f2] != tag[4 * e + f]) throw Err(ADG_E_MESH, "fault face tagged on one side only");
+      nbr_u[4 * e + f] = e2; nface_u[4 * e + f] = f2;
+      nbr_u[4 * e2 + f2] = e; nface_u[4 * e2 + f2] = f;
+      k += 2;
+    }
     for (int64_t e = 0; e < E; ++e)
       for (int f = 0; f < 4; ++f) {
         if (tag[4 * e + f] != ADG_TAG_PERIODIC) continue;
@@ -398,6 +403,9 @@ void Ctx::setup() {
   }
   ng = (int)gfaces.size();
   gpar.assign((size_t)ng * GPAR, 0.0);
+  // per element in parallel; LTS/fault slots are flagged here and numbered in
+  // element order afterwards
+#pragma omp parallel for schedule(dynamic, 4096)
   for (int64_t i = 0; i < E; ++i) {
     const int64_t eu = order[i];
     for (int k = 0; k < 9; ++k) par[i * PAR + k] = Jinv[9 * eu + k];
@@ -427,7 +435,7 @@ void Ctx::setup() {
         const int c1 = cluster[i], c2 = cluster[e2];
         kind = c1 == c2 ? NK_SAME : (c2 > c1 ? NK_COARSE : NK_FINE);
         if (kind == NK_COARSE) has_coarse = true;
-        if (kind == NK_FINE) dslot[i * 4 + f] = nd_slots++;
+        if (kind == NK_FINE) dslot[i * 4 + f] = 1;
         ninfo[i * 4 + f] = nface_u[4 * eu + f] | (nperm_u[4 * eu + f] << 2) | (kind << 5);
       } else if (tg == ADG_TAG_GRAVITY) {
         middle_state(Zpm, Zpm, Zsm, Zsm, Mm, Mp);
@@ -450,7 +458,7 @@ void Ctx::setup() {
         for (int q = 0; q < 9; ++q) { gp[87 + q] = TA[q * 9 + 0]; gp[96 + q] = TA[q * 9 + 6]; }
       } else if (tg == ADG_TAG_FAULT) {
         kind = NK_FAULT;  // flux supplied by the rupture solver from both sides' derivative traces
-        dslot[i * 4 + f] = nd_slots++;
+        dslot[i * 4 + f] = 1;
         nbr[i * 4 + f] = (int)inv[nbr_u[4 * eu + f]];
         ninfo[i * 4 + f] = nface_u[4 * eu + f] | (nperm_u[4 * eu + f] << 2) | (kind << 5);
       } else {
@@ -466,7 +474,12 @@ void Ctx::setup() {
         Fp[(i * 4 + f) * 81 + k] = FpM[k];
       }
     }
-    if (has_coarse) bslot[i] = nb_slots++;
+    if (has_coarse) bslot[i] = 1;
+  }
+  for (int64_t i = 0; i < E; ++i) {
+    if (bslot[i] == 1) bslot[i] = nb_slots++;
+    for (int f = 0; f < 4; ++f)
+      if (dslot[i * 4 + f] == 1) dslot[i * 4 + f] = nd_slots++;
   }
   n_bslots = nb_slots;
   n_dslots = nd_slots;

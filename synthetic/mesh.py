@@ -94,7 +94,7 @@ def kuhn_box(xs, ys, zs, tags=None, warp=None, fault=None):
 
     I, J, K = np.meshgrid(np.arange(nx + 1), np.arange(ny + 1), np.arange(nz + 1), indexing="ij")
     I, J, K = (a.transpose(2, 1, 0).ravel() for a in (I, J, K))  # i fastest
-    ijk = np.stack([I, J, K], axis=1).astype(np.int64)
+    ijk = np.stack([I, J, K], axis=1).astype(np.int32)
     xyz = np.stack([xs[I], ys[J], zs[K]], axis=1)
     if warp is not None:
         xyz = np.asarray(warp(xyz.copy(), ijk), dtype=np.float64)
