@@ -50,6 +50,10 @@ extern "C" {
 
 #define ADG_FP64 0
 #define ADG_FP32 1
+/* FP32 dofs; at degree 5 the reference-matrix products run on the tensor
+ * cores (tcgen05) as 3xTF32 split products with FP32 accumulation; other
+ * degrees behave as ADG_FP32. */
+#define ADG_3XTF32 2
 
 /* Face tags (per tet and local face). */
 #define ADG_TAG_INTERIOR 0  /* matched with the face sharing its three vertices  */

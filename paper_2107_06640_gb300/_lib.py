@@ -15,7 +15,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "lib", "libadg.so")
 
 ADG_OK = 0
-ADG_FP64, ADG_FP32 = 0, 1
+ADG_FP64, ADG_FP32, ADG_3XTF32 = 0, 1, 2
 ERRORS = {-1: "INVALID", -2: "MESH", -3: "STATE", -4: "CUDA", -5: "NOMEM", -6: "NAN",
           -7: "NEWTON", -8: "TIMEOUT", -9: "NOT_READY"}
 

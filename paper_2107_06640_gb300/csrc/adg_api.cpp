@@ -100,7 +100,8 @@ void adg_default_config(adg_config* cfg) {
 int adg_create(const adg_config* cfg, adg_ctx** out) {
   if (!cfg || !out) return ADG_E_INVALID;
   *out = nullptr;
-  if (cfg->degree < 1 || cfg->degree > 5 || (cfg->precision != ADG_FP64 && cfg->precision != ADG_FP32) ||
+  if (cfg->degree < 1 || cfg->degree > 5 ||
+      (cfg->precision != ADG_FP64 && cfg->precision != ADG_FP32 && cfg->precision != ADG_3XTF32) ||
       !(cfg->cfl > 0) || cfg->max_clusters < 1 || cfg->max_clusters > 16 || cfg->ensemble < 1 ||
       cfg->gravity < 0)
     return ADG_E_INVALID;

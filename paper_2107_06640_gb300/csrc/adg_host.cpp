@@ -208,6 +208,7 @@ void Ctx::setup() {
   N = cfg.degree;
   S = cfg.ensemble;
   fp64 = cfg.precision == ADG_FP64;
+  tc = cfg.precision == ADG_3XTF32 && cfg.degree == 5;
   ops = make_ref_ops(N);
   if (ops.max_orth_err > 1e-12) throw Err(ADG_E_INVALID, "reference basis not orthonormal");
   B = ops.B; Bf = ops.Bf; B1 = ops.B1;
@@ -543,6 +544,7 @@ void Ctx::setup() {
   dBtrace = (double*)dalloc((size_t)nb_slots * S * 36 * Bf * 8, owned, dev_bytes);
   dDtrace = dalloc((size_t)nd_slots * S * (N + 1) * 9 * Bf * ts, owned, dev_bytes);
   dEta = (double*)dalloc((size_t)ng * S * Bf * 8, owned, dev_bytes);
+  dGflux = dalloc((size_t)ng * S * 9 * Bf * ts, owned, dev_bytes);
   if (fp64) {
     dPar = upload_vec<double>(par, owned, dev_bytes);
     dFm = upload_vec<double>(Fm, owned, dev_bytes);
@@ -567,6 +569,12 @@ void Ctx::setup() {
   dDslot = nd_slots ? upload_raw<int>(dslot, owned, dev_bytes) : nullptr;
   dGpar = ng ? upload_raw<double>(gpar, owned, dev_bytes) : nullptr;
   dPerm = upload_raw<int>(ops.perm, owned, dev_bytes);
+  CK(cudaDeviceGetAttribute(&n_sms, cudaDevAttrMultiProcessorCount, cfg.device));
+  if (tc) {
+    std::vector<float> tl(TC_LIFT_FLOATS);
+    pack_lift_tc(ops.lift.data(), tl.data());
+    dTcLift = upload_raw<float>(tl, owned, dev_bytes);
+  }
   dErr = (unsigned int*)dalloc(sizeof(unsigned int), owned, dev_bytes);
   if (nff) {
     dFface = upload_raw<int>(fface, owned, dev_bytes);
@@ -582,6 +590,7 @@ void Ctx::setup() {
   // configure kernels once (outside any stream capture)
   StepArgs a0 = base_args();
   int rc = launch_local(fp64, N, a0, 0, stream);
+  if (!rc && tc) rc = launch_neighbour_tc(a0, 0, n_sms, stream);
   if (rc) throw Err(ADG_E_CUDA, std::string("kernel configuration: ") + cudaGetErrorString((cudaError_t)rc));
   tick = 0;
   time = 0.0;
@@ -595,7 +604,7 @@ StepArgs Ctx::base_args() const {
   a.gslot = dGslot; a.bslot = dBslot; a.dslot = dDslot;
   a.ktT = dKt; a.kvolT = dKvol; a.efcT = dEfc; a.liftT = dLift; a.perm = dPerm; a.gpar = dGpar;
   a.S = S; a.err = dErr;
-  a.fslot = dFslot; a.drout = dDrout;
+  a.fslot = dFslot; a.drout = dDrout; a.gflux = dGflux; a.tc_lift = dTcLift;
   return a;
 }
 
@@ -648,7 +657,7 @@ void Ctx::launch_tick(int s, double dtm) {
       CK(cudaEventCreate(&ev.b));
       CK(cudaEventRecord(ev.a, stream));
     }
-    int rc = launch_neighbour(fp64, N, a, n * S, stream);
+    int rc = tc ? launch_neighbour_tc(a, n * S, n_sms, stream) : launch_neighbour(fp64, N, a, n * S, stream);
     if (prof) { CK(cudaEventRecord(ev.b, stream)); prof->push_back(ev); }
     if (rc) throw Err(ADG_E_CUDA, std::string("neighbour kernel: ") + cudaGetErrorString((cudaError_t)rc));
   }

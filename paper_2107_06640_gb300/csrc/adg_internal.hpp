@@ -43,6 +43,9 @@ struct Ctx {
   // discretisation
   int N = 0, B = 0, Bf = 0, B1 = 0, S = 1;
   bool fp64 = true;
+  bool tc = false;          // tensor-core (3xTF32) kernels in use
+  int n_sms = 1;
+  float* dTcLift = nullptr;
   RefOps ops;
   int ncl = 1;
   std::vector<int64_t> order, inv, cl_begin;
@@ -56,7 +59,7 @@ struct Ctx {
   cudaStream_t stream = nullptr, own_stream = nullptr;
   std::vector<void*> owned;
   int64_t dev_bytes = 0;
-  void *dQ = nullptr, *dTrace = nullptr, *dDtrace = nullptr;
+  void *dQ = nullptr, *dTrace = nullptr, *dDtrace = nullptr, *dGflux = nullptr;
   double *dBtrace = nullptr, *dEta = nullptr, *dGpar = nullptr;
   void *dPar = nullptr, *dFm = nullptr, *dFp = nullptr;
   void *dKt = nullptr, *dKvol = nullptr, *dEfc = nullptr, *dLift = nullptr;

@@ -61,7 +61,14 @@ struct StepArgs {
   unsigned int* err;    // device error word
   const int* fslot;     // [E][4] 2*fault + side for fault faces, else -1
   const void* drout;    // T [nff*S][2][9][Bf] time-integrated fault flux per side
+  void* gflux;          // T [ngslot*S][9][Bf] time-integrated flux of gravitational faces
+  const float* tc_lift; // tensor-core lift operand (hi/lo, canonical layout), degree 5 only
 };
+
+// tensor-core (tcgen05, 3xTF32) neighbour kernel, degree 5, FP32 dofs (neighbour_tc.cu)
+int launch_neighbour_tc(const StepArgs& a, int64_t n_virtual, int n_sms, void* stream);
+void pack_lift_tc(const double* lift, float* out);
+constexpr int TC_LIFT_FLOATS = 2 * 64 * 88;
 
 // ---- dynamic rupture (rupture.cu) ----
 // per-node fault parameters (double, stride FPAR), in this order:

@@ -203,16 +203,10 @@ __global__ void __launch_bounds__(kThreads) local_kernel(StepArgs a) {
     }
     sdQ[r] = acc;
   }
-  // ---- local flux G[f][q][n] = sum_p F^-[q][p] V[f][p][n]
-  const T* Fm = reinterpret_cast<const T*>(a.Fm) + e * 4 * 81;
-  for (int r = tid; r < 36 * Bf; r += nth) {
-    const int f = r / (9 * Bf), q = (r / Bf) % 9, n = r % Bf;
-    T acc = T(0);
-#pragma unroll
-    for (int p = 0; p < 9; ++p) acc += Fm[f * 81 + q * 9 + p] * sV[(f * 9 + p) * Bf + n];
-    sG[r] = acc;
-  }
-  // ---- gravitational faces: (eta, H) ODE per node in FP64, then the flux
+  // ---- the local flux F^- V of ordinary faces is applied, together with the
+  // neighbour flux, by the neighbour kernel (one lift per step); here only the
+  // gravitational faces need the own derivatives:
+  // (eta, H) ODE per node in FP64, then that face's flux into gflux
   if (a.gslot) {
 #pragma unroll 1
     for (int f = 0; f < 4; ++f) {
@@ -260,39 +254,31 @@ __global__ void __launch_bounds__(kThreads) local_kernel(StepArgs a) {
         const double* Fg = gp + 6;
         const double* a1 = gp + 87;
         const double* a7 = gp + 96;
+        T* gfl = reinterpret_cast<T*>(a.gflux) + ((int64_t)gs * a.S + s) * 9 * Bf;
         for (int q = 0; q < 9; ++q) {
           double acc = a1[q] * (-rg * H) + a7[q] * (e1 - eta0);
           for (int p = 0; p < 9; ++p) acc += Fg[q * 9 + p] * (double)sV[(f * 9 + p) * Bf + n];
-          sG[(f * 9 + q) * Bf + n] = (T)acc;
+          gfl[q * Bf + n] = (T)acc;
         }
       }
     }
   }
   __syncthreads();
-  // ---- lift: dQ[q][m] -= sum_f scale_f sum_n lift[f][m][n] G[f][q][n]; Q += dQ
-  for (int r = tid; r < 9 * B; r += nth) {
-    const int q = r / B, m = r % B;
-    T acc = T(0);
-#pragma unroll
-    for (int f = 0; f < 4; ++f) {
-      T af = T(0);
-      const T* lf = liftT + (size_t)f * Bf * B + m;
-      const T* g = sG + (f * 9 + q) * Bf;
-      for (int n = 0; n < Bf; ++n) af += lf[(size_t)n * B] * g[n];
-      acc += sP[12 + f] * af;
-    }
-    Q[r] = sD[r] + (sdQ[r] - acc);
-  }
+  // ---- Q += volume term (the face terms follow in the neighbour kernel)
+  for (int r = tid; r < 9 * B; r += nth) Q[r] = sD[r] + sdQ[r];
 }
 
 template <typename T, int N>
 __global__ void __launch_bounds__(kThreads) neighbour_kernel(StepArgs a) {
   constexpr int B = nb3(N), Bf = nb2(N);
-  __shared__ T sV[36 * Bf];
+  __shared__ T sV[36 * Bf];   // neighbours' time-integrated traces (this face's node order)
+  __shared__ T sVo[36 * Bf];  // own time-integrated traces
   __shared__ T sG[36 * Bf];
   __shared__ T sFp[4 * 81];
+  __shared__ T sFm[4 * 81];
   __shared__ T sScale[4];
   __shared__ int sKind[4];
+  __shared__ int sGrav[4];
   const int tid = threadIdx.x, nth = blockDim.x;
   const int64_t v = a.v_begin + blockIdx.x;
   const int64_t e = v / a.S;
@@ -301,8 +287,13 @@ __global__ void __launch_bounds__(kThreads) neighbour_kernel(StepArgs a) {
   if (tid < 4) {
     sScale[tid] = reinterpret_cast<const T*>(a.par)[e * PAR + 12 + tid];
     sKind[tid] = (a.ninfo[e * 4 + tid] >> 5) & 7;
+    sGrav[tid] = a.gslot ? a.gslot[e * 4 + tid] : -1;
   }
-  for (int r = tid; r < 4 * 81; r += nth) sFp[r] = reinterpret_cast<const T*>(a.Fp)[e * 4 * 81 + r];
+  for (int r = tid; r < 4 * 81; r += nth) {
+    sFp[r] = reinterpret_cast<const T*>(a.Fp)[e * 4 * 81 + r];
+    sFm[r] = reinterpret_cast<const T*>(a.Fm)[e * 4 * 81 + r];
+  }
+  for (int r = tid; r < 36 * Bf; r += nth) sVo[r] = reinterpret_cast<const T*>(a.trace)[v * 36 * Bf + r];
   __syncthreads();
   for (int r = tid; r < 36 * Bf; r += nth) {
     const int f = r / (9 * Bf), p = (r / Bf) % 9, n = r % Bf;
@@ -330,6 +321,9 @@ __global__ void __launch_bounds__(kThreads) neighbour_kernel(StepArgs a) {
     sV[r] = val;
   }
   __syncthreads();
+  // face fluxes G[f][q][n]: F^- (own) + F^+ (neighbour) on interior faces,
+  // F^- with the ghost folded in on linear boundaries, the precomputed fluxes on
+  // gravitational (local kernel) and fault faces (rupture kernel)
   for (int r = tid; r < 36 * Bf; r += nth) {
     const int f = r / (9 * Bf), q = (r / Bf) % 9, n = r % Bf;
     T acc = T(0);
@@ -337,9 +331,15 @@ __global__ void __launch_bounds__(kThreads) neighbour_kernel(StepArgs a) {
       // time-integrated fault flux of this side, already in this face's node order
       const int fsl = a.fslot[e * 4 + f];
       acc = reinterpret_cast<const T*>(a.drout)[((((int64_t)(fsl >> 1) * a.S + s) * 2 + (fsl & 1)) * 9 + q) * Bf + n];
-    } else if (sKind[f] != NK_NONE) {
+    } else if (sGrav[f] >= 0) {
+      acc = reinterpret_cast<const T*>(a.gflux)[((int64_t)sGrav[f] * a.S + s) * 9 * Bf + q * Bf + n];
+    } else {
 #pragma unroll
-      for (int p = 0; p < 9; ++p) acc += sFp[f * 81 + q * 9 + p] * sV[(f * 9 + p) * Bf + n];
+      for (int p = 0; p < 9; ++p) acc += sFm[f * 81 + q * 9 + p] * sVo[(f * 9 + p) * Bf + n];
+      if (sKind[f] != NK_NONE) {
+#pragma unroll
+        for (int p = 0; p < 9; ++p) acc += sFp[f * 81 + q * 9 + p] * sV[(f * 9 + p) * Bf + n];
+      }
     }
     sG[r] = acc;
   }
@@ -351,7 +351,6 @@ __global__ void __launch_bounds__(kThreads) neighbour_kernel(StepArgs a) {
     T acc = T(0);
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
-      if (sKind[f] == NK_NONE) continue;
       T af = T(0);
       const T* lf = liftT + (size_t)f * Bf * B + m;
       const T* g = sG + (f * 9 + q) * Bf;
