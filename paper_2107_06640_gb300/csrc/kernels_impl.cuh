@@ -1,4 +1,11 @@
 // Template bodies of the element-update kernels (see kernels.cuh).
+//
+// Shared-memory working arrays keep the 9 quantities of one basis function
+// (or face node) contiguous, padded to P values so that a row is read with
+// vector loads; inside a warp the threads usually read the same row, so one
+// broadcast load feeds 9 FMAs per thread.  Star products use the Jacobian
+// form  sum_a A*_a Y_a = sum_d A_d X_d,  X_d = sum_a (dxi_a/dx_d) Y_a,  with
+// the sparse A_d of Eq. (elasticity-pde) written out (material in registers).
 #pragma once
 #include <cuda_runtime.h>
 
@@ -8,58 +15,91 @@ namespace adg {
 
 constexpr int kThreads = 128;
 
-__host__ __device__ constexpr int doff(int k, int N) {
+__host__ __device__ constexpr int doff_rows(int k, int N) {  // first row of D^k in the derivative stack
   int s = 0;
-  for (int j = 0; j < k; ++j) s += 9 * nb3(N - j);
+  for (int j = 0; j < k; ++j) s += nb3(N - j);
   return s;
 }
 
-// Entry (q, p) of the Jacobian A_d of Eq. (elasticity-pde) for material (rho, lam, mu).
 template <typename T>
-__device__ __forceinline__ T jac_entry(int d, int q, int p, T rho, T lam, T mu) {
-  if (q < 3) {
-    if (p != 6 + d) return T(0);
-    return -lam - (q == d ? T(2) * mu : T(0));
+struct Pad;
+template <>
+struct Pad<float> {
+  static constexpr int P = 12;  // 3 x float4
+};
+template <>
+struct Pad<double> {
+  static constexpr int P = 10;  // 5 x double2
+};
+
+__device__ __forceinline__ void load9(const float* p, float o[9]) {
+  const float4 a = *reinterpret_cast<const float4*>(p);
+  const float4 b = *reinterpret_cast<const float4*>(p + 4);
+  o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w;
+  o[4] = b.x; o[5] = b.y; o[6] = b.z; o[7] = b.w;
+  o[8] = p[8];
+}
+__device__ __forceinline__ void load9(const double* p, double o[9]) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const double2 a = *reinterpret_cast<const double2*>(p + 2 * i);
+    o[2 * i] = a.x;
+    o[2 * i + 1] = a.y;
   }
-  if (q < 6) {
-    const int i = (q == 4) ? 1 : 0;
-    const int j = (q == 3) ? 1 : 2;
-    T r = T(0);
-    if (d == j && p == 6 + i) r -= mu;
-    if (d == i && p == 6 + j) r -= mu;
-    return r;
-  }
-  const int i = q - 6;
-  // Voigt index of s_{i d}
-  int s;
-  if (i == d) s = i;
-  else if ((i == 0 && d == 1) || (i == 1 && d == 0)) s = 3;
-  else if ((i == 1 && d == 2) || (i == 2 && d == 1)) s = 4;
-  else s = 5;
-  return p == s ? -T(1) / rho : T(0);
+  o[8] = p[8];
+}
+__device__ __forceinline__ void store9(float* p, const float o[9]) {
+  *reinterpret_cast<float4*>(p) = make_float4(o[0], o[1], o[2], o[3]);
+  *reinterpret_cast<float4*>(p + 4) = make_float4(o[4], o[5], o[6], o[7]);
+  p[8] = o[8];
+}
+__device__ __forceinline__ void store9(double* p, const double o[9]) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i) *reinterpret_cast<double2*>(p + 2 * i) = make_double2(o[2 * i], o[2 * i + 1]);
+  p[8] = o[8];
 }
 
-// star[a][q][p] = sum_d Jinv[a][d] A_d[q][p]
+// out = sum_d A_d X_d for the Jacobians of Eq. (elasticity-pde)
 template <typename T>
-__device__ __forceinline__ void build_star(const T* par, T* star) {
-  const T rho = par[9], lam = par[10], mu = par[11];
-  for (int r = threadIdx.x; r < 243; r += blockDim.x) {
-    const int a = r / 81, q = (r / 9) % 9, p = r % 9;
-    T s = T(0);
+__device__ __forceinline__ void jac_sum(const T X0[9], const T X1[9], const T X2[9], T lam, T mu, T irho, T out[9]) {
+  const T l2m = lam + T(2) * mu;
+  out[0] = -(l2m * X0[6] + lam * X1[7] + lam * X2[8]);
+  out[1] = -(lam * X0[6] + l2m * X1[7] + lam * X2[8]);
+  out[2] = -(lam * X0[6] + lam * X1[7] + l2m * X2[8]);
+  out[3] = -mu * (X1[6] + X0[7]);
+  out[4] = -mu * (X2[7] + X1[8]);
+  out[5] = -mu * (X2[6] + X0[8]);
+  out[6] = -irho * (X0[0] + X1[3] + X2[5]);
+  out[7] = -irho * (X0[3] + X1[1] + X2[4]);
+  out[8] = -irho * (X0[5] + X1[4] + X2[2]);
+}
+// out = A_d x for one direction d
+template <typename T>
+__device__ __forceinline__ void jac_dir(int d, const T x[9], T lam, T mu, T irho, T out[9]) {
+  const T vd = x[6 + d];
 #pragma unroll
-    for (int d = 0; d < 3; ++d) s += par[a * 3 + d] * jac_entry<T>(d, q, p, rho, lam, mu);
-    star[r] = s;
-  }
+  for (int i = 0; i < 3; ++i) out[i] = -lam * vd;
+  out[d] -= T(2) * mu * vd;
+  out[3] = -mu * ((d == 1 ? x[6] : T(0)) + (d == 0 ? x[7] : T(0)));
+  out[4] = -mu * ((d == 2 ? x[7] : T(0)) + (d == 1 ? x[8] : T(0)));
+  out[5] = -mu * ((d == 2 ? x[6] : T(0)) + (d == 0 ? x[8] : T(0)));
+  // velocity rows: -(1/rho) s_{i d}
+  const int s0 = d == 0 ? 0 : (d == 1 ? 3 : 5);  // s_{x d}
+  const int s1 = d == 0 ? 3 : (d == 1 ? 1 : 4);  // s_{y d}
+  const int s2 = d == 0 ? 5 : (d == 1 ? 4 : 2);  // s_{z d}
+  out[6] = -irho * x[s0];
+  out[7] = -irho * x[s1];
+  out[8] = -irho * x[s2];
 }
 
 template <typename T, int N>
 struct Smem {
+  static constexpr int P = Pad<T>::P;
   static constexpr int B = nb3(N), Bf = nb2(N), B1 = nb3(N - 1);
-  static constexpr int nD = doff(N + 1, N);
-  static constexpr int nY = 27 * B1;
-  // D | I | Y | dQ | star | V | G | par | gravity scratch (double)
-  static constexpr int oD = 0, oI = oD + nD, oY = oI + 9 * B, odQ = oY + nY, oS = odQ + 9 * B,
-                       oV = oS + 243, oG = oV + 36 * Bf, oP = oG + 36 * Bf, oEnd = oP + PAR;
+  static constexpr int nDrows = doff_rows(N + 1, N);
+  // derivative stack | time integral | Y / Z scratch (3 x B1 rows) | face traces | dQ partials | params
+  static constexpr int oD = 0, oI = oD + nDrows * P, oY = oI + B * P, oV = oY + 3 * B1 * P,
+                       oQ = oV + 4 * Bf * P, oP = oQ + 3 * B * P, oEnd = oP + PAR;
   static constexpr int nGrav = (N + 1) * Bf;  // doubles
   static constexpr int bytes = ((oEnd * (int)sizeof(T) + 15) / 16) * 16 + nGrav * 8;
 };
@@ -67,16 +107,14 @@ struct Smem {
 template <typename T, int N>
 __global__ void __launch_bounds__(kThreads) local_kernel(StepArgs a) {
   using S = Smem<T, N>;
-  constexpr int B = S::B, Bf = S::Bf, B1 = S::B1;
+  constexpr int P = S::P, B = S::B, Bf = S::Bf, B1 = S::B1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
   T* sD = sm + S::oD;
   T* sI = sm + S::oI;
   T* sY = sm + S::oY;
-  T* sdQ = sm + S::odQ;
-  T* sStar = sm + S::oS;
   T* sV = sm + S::oV;
-  T* sG = sm + S::oG;
+  T* sQp = sm + S::oQ;
   T* sP = sm + S::oP;
   double* sF = reinterpret_cast<double*>(smem_raw + ((S::oEnd * (int)sizeof(T) + 15) / 16) * 16);
 
@@ -88,20 +126,24 @@ __global__ void __launch_bounds__(kThreads) local_kernel(StepArgs a) {
   const T* ktT = reinterpret_cast<const T*>(a.ktT);
   const T* kvolT = reinterpret_cast<const T*>(a.kvolT);
   const T* efcT = reinterpret_cast<const T*>(a.efcT);
-  const T* liftT = reinterpret_cast<const T*>(a.liftT);
 
   if (tid < PAR) sP[tid] = reinterpret_cast<const T*>(a.par)[e * PAR + tid];
-  for (int r = tid; r < 9 * B; r += nth) sD[r] = Q[r];
+  for (int r = tid; r < 9 * B; r += nth) {  // Q[p][l] -> D^0[l][p]
+    const int p = r / B, l = r % B;
+    sD[l * P + p] = Q[r];
+  }
   __syncthreads();
-  build_star<T>(sP, sStar);
-  __syncthreads();
+  T g[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) g[i] = sP[i];  // g[a*3+d] = d xi_a / d x_d
+  const T lam = sP[10], mu = sP[11], irho = T(1) / sP[9];
 
-  // ---- Cauchy-Kovalewski: D^{k+1} = -sum_a KT_a D^k A*_a^T, truncated to B_{N-k-1} rows
+  // ---- Cauchy-Kovalewski: Y_a = KT_a D^k (rows < B_{N-k-1}), D^{k+1} = -sum_d A_d X_d
 #pragma unroll 1
   for (int k = 0; k < N; ++k) {
     const int Bl = nb3(N - k), Bm = nb3(N - k - 1);
-    const T* Dk = sD + doff(k, N);
-    T* Dn = sD + doff(k + 1, N);
+    const T* Dk = sD + doff_rows(k, N) * P;
+    T* Dn = sD + doff_rows(k + 1, N) * P;
     for (int r = tid; r < 3 * Bm; r += nth) {
       const int ax = r / Bm, m = r % Bm;
       T acc[9];
@@ -110,103 +152,148 @@ __global__ void __launch_bounds__(kThreads) local_kernel(StepArgs a) {
       const T* kk = ktT + (size_t)ax * B * B + m;
       for (int l = 0; l < Bl; ++l) {
         const T w = kk[(size_t)l * B];
+        T d9[9];
+        load9(Dk + l * P, d9);
 #pragma unroll
-        for (int p = 0; p < 9; ++p) acc[p] += w * Dk[p * Bl + l];
+        for (int p = 0; p < 9; ++p) acc[p] += w * d9[p];
       }
-#pragma unroll
-      for (int p = 0; p < 9; ++p) sY[(ax * 9 + p) * Bm + m] = acc[p];
+      store9(sY + (ax * B1 + m) * P, acc);
     }
     __syncthreads();
-    for (int r = tid; r < 9 * Bm; r += nth) {
-      const int q = r / Bm, m = r % Bm;
-      T acc = T(0);
+    for (int m = tid; m < Bm; m += nth) {
+      T y0[9], y1[9], y2[9], X0[9], X1[9], X2[9], o[9];
+      load9(sY + (0 * B1 + m) * P, y0);
+      load9(sY + (1 * B1 + m) * P, y1);
+      load9(sY + (2 * B1 + m) * P, y2);
 #pragma unroll
-      for (int ax = 0; ax < 3; ++ax)
+      for (int p = 0; p < 9; ++p) {
+        X0[p] = g[0] * y0[p] + g[3] * y1[p] + g[6] * y2[p];
+        X1[p] = g[1] * y0[p] + g[4] * y1[p] + g[7] * y2[p];
+        X2[p] = g[2] * y0[p] + g[5] * y1[p] + g[8] * y2[p];
+      }
+      jac_sum(X0, X1, X2, lam, mu, irho, o);
 #pragma unroll
-        for (int p = 0; p < 9; ++p) {
-          const T st = sStar[(ax * 9 + q) * 9 + p];
-          if (st != T(0)) acc += st * sY[(ax * 9 + p) * Bm + m];
-        }
-      Dn[q * Bm + m] = -acc;
+      for (int p = 0; p < 9; ++p) o[p] = -o[p];
+      store9(Dn + m * P, o);
     }
     __syncthreads();
   }
 
   // ---- time integral over the own step
-  for (int r = tid; r < 9 * B; r += nth) {
-    const int p = r / B, l = r % B;
-    T acc = T(0);
+  for (int l = tid; l < B; l += nth) {
+    T acc[9];
+#pragma unroll
+    for (int p = 0; p < 9; ++p) acc[p] = T(0);
 #pragma unroll
     for (int k = 0; k <= N; ++k) {
-      const int Bk = nb3(N - k);
-      if (l < Bk) acc += T(a.tcoef[k]) * sD[doff(k, N) + p * Bk + l];
+      if (l < nb3(N - k)) {
+        T d9[9];
+        load9(sD + (doff_rows(k, N) + l) * P, d9);
+        const T c = T(a.tcoef[k]);
+#pragma unroll
+        for (int p = 0; p < 9; ++p) acc[p] += c * d9[p];
+      }
     }
-    sI[r] = acc;
+    store9(sI + l * P, acc);
   }
-  // ---- LTS: derivative traces for finer neighbours
+  // ---- LTS: derivative traces E_f D^k for faces with a finer neighbour or a fault
   if (a.dslot) {
 #pragma unroll 1
     for (int f = 0; f < 4; ++f) {
-      const int ds = a.dslot[e * 4 + f];
+      const int ds = a.dslot[e * 4 + f];  // block-uniform
       if (ds < 0) continue;
       T* out = reinterpret_cast<T*>(a.dtrace) + ((int64_t)ds * a.S + s) * (N + 1) * 9 * Bf;
-      for (int r = tid; r < (N + 1) * 9 * Bf; r += nth) {
-        const int k = r / (9 * Bf), p = (r / Bf) % 9, n = r % Bf;
+      for (int r = tid; r < (N + 1) * Bf; r += nth) {
+        const int k = r / Bf, n = r % Bf;
         const int Bk = nb3(N - k);
-        const T* Dk = sD + doff(k, N) + p * Bk;
-        T acc = T(0);
-        for (int l = 0; l < Bk; ++l) acc += efcT[((size_t)f * B + l) * Bf + n] * Dk[l];
-        out[r] = acc;
+        const T* Dk = sD + doff_rows(k, N) * P;
+        T acc[9];
+#pragma unroll
+        for (int p = 0; p < 9; ++p) acc[p] = T(0);
+        for (int l = 0; l < Bk; ++l) {
+          const T w = efcT[((size_t)f * B + l) * Bf + n];
+          T d9[9];
+          load9(Dk + l * P, d9);
+#pragma unroll
+          for (int p = 0; p < 9; ++p) acc[p] += w * d9[p];
+        }
+#pragma unroll
+        for (int p = 0; p < 9; ++p) out[(k * 9 + p) * Bf + n] = acc[p];
       }
     }
   }
   __syncthreads();
 
-  // ---- volume: dQ = sum_a K_a (I A*_a^T)
-  for (int r = tid; r < 27 * B1; r += nth) {
-    const int ax = r / (9 * B1), q = (r / B1) % 9, l = r % B1;
-    T acc = T(0);
+  // ---- volume operand Z_a[l] = A*_a I[l] (l < B_{N-1}) and face traces V = E_f I
+  for (int l = tid; l < B1; l += nth) {
+    T x[9], u0[9], u1[9], u2[9];
+    load9(sI + l * P, x);
+    jac_dir(0, x, lam, mu, irho, u0);
+    jac_dir(1, x, lam, mu, irho, u1);
+    jac_dir(2, x, lam, mu, irho, u2);
 #pragma unroll
-    for (int p = 0; p < 9; ++p) {
-      const T st = sStar[(ax * 9 + q) * 9 + p];
-      if (st != T(0)) acc += st * sI[p * B + l];
+    for (int ax = 0; ax < 3; ++ax) {
+      T z[9];
+#pragma unroll
+      for (int p = 0; p < 9; ++p) z[p] = g[ax * 3 + 0] * u0[p] + g[ax * 3 + 1] * u1[p] + g[ax * 3 + 2] * u2[p];
+      store9(sY + (ax * B1 + l) * P, z);
     }
-    sY[r] = acc;  // Z[a][q][l]
   }
-  // ---- own face traces V[f][p][n] = sum_l E_f[n][l] I[p][l]
   T* trace = reinterpret_cast<T*>(a.trace) + v * 36 * Bf;
-  for (int r = tid; r < 36 * Bf; r += nth) {
-    const int f = r / (9 * Bf), p = (r / Bf) % 9, n = r % Bf;
-    T acc = T(0);
-    const T* ee = efcT + (size_t)f * B * Bf + n;
-    for (int l = 0; l < B; ++l) acc += ee[(size_t)l * Bf] * sI[p * B + l];
-    sV[r] = acc;
-    trace[r] = acc;
-  }
+  double* bt = nullptr;
   if (a.btrace_mode && a.bslot) {
     const int bs = a.bslot[e];
-    if (bs >= 0) {
-      __syncthreads();
-      double* bt = a.btrace + ((int64_t)bs * a.S + s) * 36 * Bf;
-      for (int r = tid; r < 36 * Bf; r += nth) bt[r] = (a.btrace_mode == 1 ? 0.0 : bt[r]) + (double)sV[r];
+    if (bs >= 0) bt = a.btrace + ((int64_t)bs * a.S + s) * 36 * Bf;
+  }
+  for (int r = tid; r < 4 * Bf; r += nth) {
+    const int f = r / Bf, n = r % Bf;
+    T acc[9];
+#pragma unroll
+    for (int p = 0; p < 9; ++p) acc[p] = T(0);
+    const T* ee = efcT + (size_t)f * B * Bf + n;
+    for (int l = 0; l < B; ++l) {
+      const T w = ee[(size_t)l * Bf];
+      T d9[9];
+      load9(sI + l * P, d9);
+#pragma unroll
+      for (int p = 0; p < 9; ++p) acc[p] += w * d9[p];
+    }
+    store9(sV + r * P, acc);
+#pragma unroll
+    for (int p = 0; p < 9; ++p) trace[(f * 9 + p) * Bf + n] = acc[p];
+    if (bt) {
+#pragma unroll
+      for (int p = 0; p < 9; ++p) {
+        double* b = bt + (f * 9 + p) * Bf + n;
+        *b = (a.btrace_mode == 1 ? 0.0 : *b) + (double)acc[p];
+      }
     }
   }
   __syncthreads();
-  for (int r = tid; r < 9 * B; r += nth) {
-    const int q = r / B, m = r % B;
-    T acc = T(0);
+  // ---- volume: dQ[m] = sum_a sum_l K_a[m][l] Z_a[l]   (three partial sums, one per a)
+  for (int r = tid; r < 3 * B; r += nth) {
+    const int ax = r / B, m = r % B;
+    T acc[9];
 #pragma unroll
-    for (int ax = 0; ax < 3; ++ax) {
-      const T* kv = kvolT + (size_t)ax * B1 * B + m;
-      const T* z = sY + (ax * 9 + q) * B1;
-      for (int l = 0; l < B1; ++l) acc += kv[(size_t)l * B] * z[l];
+    for (int p = 0; p < 9; ++p) acc[p] = T(0);
+    const T* kv = kvolT + (size_t)ax * B1 * B + m;
+    const T* z = sY + ax * B1 * P;
+    for (int l = 0; l < B1; ++l) {
+      const T w = kv[(size_t)l * B];
+      T z9[9];
+      load9(z + l * P, z9);
+#pragma unroll
+      for (int p = 0; p < 9; ++p) acc[p] += w * z9[p];
     }
-    sdQ[r] = acc;
+    store9(sQp + (ax * B + m) * P, acc);
   }
-  // ---- the local flux F^- V of ordinary faces is applied, together with the
-  // neighbour flux, by the neighbour kernel (one lift per step); here only the
-  // gravitational faces need the own derivatives:
-  // (eta, H) ODE per node in FP64, then that face's flux into gflux
+  __syncthreads();
+  // ---- Q += volume term (face terms follow in the neighbour kernel)
+  for (int r = tid; r < 9 * B; r += nth) {
+    const int p = r / B, m = r % B;
+    Q[r] = sD[m * P + p] + ((sQp[m * P + p] + sQp[(B + m) * P + p]) + sQp[(2 * B + m) * P + p]);
+  }
+  // ---- gravitational faces: (eta, H) ODE per node in FP64, then that face's flux
   if (a.gslot) {
 #pragma unroll 1
     for (int f = 0; f < 4; ++f) {
@@ -218,14 +305,20 @@ __global__ void __launch_bounds__(kThreads) local_kernel(StepArgs a) {
       for (int r = tid; r < (N + 1) * Bf; r += nth) {
         const int m = r / Bf, n = r % Bf;
         const int Bk = nb3(N - m);
-        const T* Dm = sD + doff(m, N);
+        const T* Dm = sD + doff_rows(m, N) * P;
+        T acc[9];
+#pragma unroll
+        for (int p = 0; p < 9; ++p) acc[p] = T(0);
+        for (int l = 0; l < Bk; ++l) {
+          const T w = efcT[((size_t)f * B + l) * Bf + n];
+          T d9[9];
+          load9(Dm + l * P, d9);
+#pragma unroll
+          for (int p = 0; p < 9; ++p) acc[p] += w * d9[p];
+        }
         double val[9];
 #pragma unroll
-        for (int p = 0; p < 9; ++p) {
-          T acc = T(0);
-          for (int l = 0; l < Bk; ++l) acc += efcT[((size_t)f * B + l) * Bf + n] * Dm[p * Bk + l];
-          val[p] = (double)acc;
-        }
+        for (int p = 0; p < 9; ++p) val[p] = (double)acc[p];
         const double nx = gp[0], ny = gp[1], nz = gp[2], Z = gp[3];
         const double snn = nx * nx * val[0] + ny * ny * val[1] + nz * nz * val[2] +
                            2.0 * (nx * ny * val[3] + ny * nz * val[4] + nx * nz * val[5]);
@@ -257,25 +350,28 @@ __global__ void __launch_bounds__(kThreads) local_kernel(StepArgs a) {
         T* gfl = reinterpret_cast<T*>(a.gflux) + ((int64_t)gs * a.S + s) * 9 * Bf;
         for (int q = 0; q < 9; ++q) {
           double acc = a1[q] * (-rg * H) + a7[q] * (e1 - eta0);
-          for (int p = 0; p < 9; ++p) acc += Fg[q * 9 + p] * (double)sV[(f * 9 + p) * Bf + n];
+          for (int p = 0; p < 9; ++p) acc += Fg[q * 9 + p] * (double)sV[(f * Bf + n) * P + p];
           gfl[q * Bf + n] = (T)acc;
         }
       }
     }
   }
-  __syncthreads();
-  // ---- Q += volume term (the face terms follow in the neighbour kernel)
-  for (int r = tid; r < 9 * B; r += nth) Q[r] = sD[r] + sdQ[r];
 }
 
 template <typename T, int N>
+struct SmemN {
+  static constexpr int P = Pad<T>::P;
+  static constexpr int B = nb3(N), Bf = nb2(N);
+};
+
+template <typename T, int N>
 __global__ void __launch_bounds__(kThreads) neighbour_kernel(StepArgs a) {
-  constexpr int B = nb3(N), Bf = nb2(N);
-  __shared__ T sV[36 * Bf];   // neighbours' time-integrated traces (this face's node order)
-  __shared__ T sVo[36 * Bf];  // own time-integrated traces
-  __shared__ T sG[36 * Bf];
-  __shared__ T sFp[4 * 81];
-  __shared__ T sFm[4 * 81];
+  constexpr int P = Pad<T>::P, B = nb3(N), Bf = nb2(N);
+  __shared__ __align__(16) T sVo[4 * Bf * P];  // own traces [f][n][p]
+  __shared__ __align__(16) T sVn[4 * Bf * P];  // neighbours' traces in this face's node order
+  __shared__ __align__(16) T sG[4 * Bf * P];   // scaled face fluxes
+  __shared__ __align__(16) T sPart[2 * B * P];
+  __shared__ T sF[4 * 162];                    // per face: F- (81) then F+ (81)
   __shared__ T sScale[4];
   __shared__ int sKind[4];
   __shared__ int sGrav[4];
@@ -290,17 +386,22 @@ __global__ void __launch_bounds__(kThreads) neighbour_kernel(StepArgs a) {
     sGrav[tid] = a.gslot ? a.gslot[e * 4 + tid] : -1;
   }
   for (int r = tid; r < 4 * 81; r += nth) {
-    sFp[r] = reinterpret_cast<const T*>(a.Fp)[e * 4 * 81 + r];
-    sFm[r] = reinterpret_cast<const T*>(a.Fm)[e * 4 * 81 + r];
+    const int f = r / 81, k = r % 81;
+    sF[f * 162 + k] = reinterpret_cast<const T*>(a.Fm)[e * 4 * 81 + r];
+    sF[f * 162 + 81 + k] = reinterpret_cast<const T*>(a.Fp)[e * 4 * 81 + r];
   }
-  for (int r = tid; r < 36 * Bf; r += nth) sVo[r] = reinterpret_cast<const T*>(a.trace)[v * 36 * Bf + r];
+  const T* own = reinterpret_cast<const T*>(a.trace) + v * 36 * Bf;
+  for (int r = tid; r < 36 * Bf; r += nth) {  // [f][p][n] -> [f][n][p]
+    const int f = r / (9 * Bf), p = (r / Bf) % 9, n = r % Bf;
+    sVo[(f * Bf + n) * P + p] = own[r];
+  }
   __syncthreads();
   for (int r = tid; r < 36 * Bf; r += nth) {
     const int f = r / (9 * Bf), p = (r / Bf) % 9, n = r % Bf;
-    const int info = a.ninfo[e * 4 + f];
-    const int kind = (info >> 5) & 7;
+    const int kind = sKind[f];
     T val = T(0);
-    if (kind != NK_NONE && kind != NK_FAULT) {
+    if (kind == NK_SAME || kind == NK_FINE || kind == NK_COARSE) {
+      const int info = a.ninfo[e * 4 + f];
       const int64_t nb = a.nbr[e * 4 + f];
       const int j = info & 3, pm = (info >> 2) & 7;
       const int src = a.perm[pm * Bf + n];
@@ -318,46 +419,74 @@ __global__ void __launch_bounds__(kThreads) neighbour_kernel(StepArgs a) {
         val = acc;
       }
     }
-    sV[r] = val;
+    sVn[(f * Bf + n) * P + p] = val;
   }
   __syncthreads();
-  // face fluxes G[f][q][n]: F^- (own) + F^+ (neighbour) on interior faces,
-  // F^- with the ghost folded in on linear boundaries, the precomputed fluxes on
-  // gravitational (local kernel) and fault faces (rupture kernel)
-  for (int r = tid; r < 36 * Bf; r += nth) {
-    const int f = r / (9 * Bf), q = (r / Bf) % 9, n = r % Bf;
-    T acc = T(0);
+  // face fluxes: F- (own) + F+ (neighbour) on interior faces, F- with the ghost
+  // folded in on linear boundaries, stored fluxes on gravitational / fault faces
+  for (int r = tid; r < 4 * Bf; r += nth) {
+    const int f = r / Bf, n = r % Bf;
+    T gq[9];
     if (sKind[f] == NK_FAULT) {
-      // time-integrated fault flux of this side, already in this face's node order
       const int fsl = a.fslot[e * 4 + f];
-      acc = reinterpret_cast<const T*>(a.drout)[((((int64_t)(fsl >> 1) * a.S + s) * 2 + (fsl & 1)) * 9 + q) * Bf + n];
+      const T* src = reinterpret_cast<const T*>(a.drout) + (((int64_t)(fsl >> 1) * a.S + s) * 2 + (fsl & 1)) * 9 * Bf;
+#pragma unroll
+      for (int q = 0; q < 9; ++q) gq[q] = src[q * Bf + n];
     } else if (sGrav[f] >= 0) {
-      acc = reinterpret_cast<const T*>(a.gflux)[((int64_t)sGrav[f] * a.S + s) * 9 * Bf + q * Bf + n];
+      const T* src = reinterpret_cast<const T*>(a.gflux) + ((int64_t)sGrav[f] * a.S + s) * 9 * Bf;
+#pragma unroll
+      for (int q = 0; q < 9; ++q) gq[q] = src[q * Bf + n];
     } else {
+      T vo[9];
+      load9(sVo + r * P, vo);
+      const T* Fm = sF + f * 162;
 #pragma unroll
-      for (int p = 0; p < 9; ++p) acc += sFm[f * 81 + q * 9 + p] * sVo[(f * 9 + p) * Bf + n];
+      for (int q = 0; q < 9; ++q) {
+        T acc = T(0);
+#pragma unroll
+        for (int p = 0; p < 9; ++p) acc += Fm[q * 9 + p] * vo[p];
+        gq[q] = acc;
+      }
       if (sKind[f] != NK_NONE) {
+        T vn[9];
+        load9(sVn + r * P, vn);
+        const T* Fp = sF + f * 162 + 81;
 #pragma unroll
-        for (int p = 0; p < 9; ++p) acc += sFp[f * 81 + q * 9 + p] * sV[(f * 9 + p) * Bf + n];
+        for (int q = 0; q < 9; ++q) {
+          T acc = T(0);
+#pragma unroll
+          for (int p = 0; p < 9; ++p) acc += Fp[q * 9 + p] * vn[p];
+          gq[q] += acc;
+        }
       }
     }
-    sG[r] = acc;
+    const T sc = sScale[f];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) gq[q] *= sc;
+    store9(sG + r * P, gq);
+  }
+  __syncthreads();
+  // lift: two partial sums per basis function (faces 0-1 and 2-3)
+  for (int r = tid; r < 2 * B; r += nth) {
+    const int half = r / B, m = r % B;
+    T acc[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) acc[q] = T(0);
+    for (int fn = half * 2 * Bf; fn < (half + 1) * 2 * Bf; ++fn) {  // fn = f*Bf + n
+      const T w = liftT[(size_t)fn * B + m];
+      T g9[9];
+      load9(sG + fn * P, g9);
+#pragma unroll
+      for (int q = 0; q < 9; ++q) acc[q] += w * g9[q];
+    }
+    store9(sPart + r * P, acc);
   }
   __syncthreads();
   T* Q = reinterpret_cast<T*>(a.Q) + v * 9 * B;
   bool bad = false;
   for (int r = tid; r < 9 * B; r += nth) {
     const int q = r / B, m = r % B;
-    T acc = T(0);
-#pragma unroll
-    for (int f = 0; f < 4; ++f) {
-      T af = T(0);
-      const T* lf = liftT + (size_t)f * Bf * B + m;
-      const T* g = sG + (f * 9 + q) * Bf;
-      for (int n = 0; n < Bf; ++n) af += lf[(size_t)n * B] * g[n];
-      acc += sScale[f] * af;
-    }
-    const T nq = Q[r] - acc;
+    const T nq = Q[r] - (sPart[m * P + q] + sPart[(B + m) * P + q]);
     Q[r] = nq;
     bad |= !isfinite((double)nq);
   }
