@@ -307,6 +307,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--nxy", type=int, default=80,
                     help="hex columns per side (80: the 1.5 M-tet workload; smaller for profiling)")
+    ap.add_argument("--only", default=None, choices=["fp64", "fp32", "3xtf32"],
+                    help="profiling aid: run one precision of the coupled workload, print no JSON line")
     ap.add_argument("--workload", default="coupled", choices=["coupled", "lts", "rupture", "ensemble"],
                     help="coupled: the headline line; lts / rupture / ensemble: the other workloads")
     args = ap.parse_args()
@@ -353,6 +355,16 @@ def main():
     HEAD = pkg.ADG_FP32
     runs = ((pkg.ADG_FP64, args.fp64_steps, 1), (pkg.ADG_3XTF32, args.steps, args.warmup),
             (pkg.ADG_FP32, args.steps, args.warmup))
+    if args.only:
+        # profiling aid: one precision, a short run, no JSON line
+        prec = {"fp64": pkg.ADG_FP64, "fp32": pkg.ADG_FP32, "3xtf32": pkg.ADG_3XTF32}[args.only]
+        s = Solver(m.xyz, m.tets, m.face_tag, rho, lam, mu, degree=N_DEG, precision=prec, cfl=0.35,
+                   device=local, stream=stream.cuda_stream)
+        s.set_dofs(Q0)
+        s.advance(args.warmup + args.steps)
+        s.sync()
+        print(f"profiling run: {args.only}, {args.warmup + args.steps} steps", flush=True)
+        return
     for prec, steps, warm in runs:
         s = Solver(m.xyz, m.tets, m.face_tag, rho, lam, mu, degree=N_DEG, precision=prec, cfl=0.35,
                    device=local, stream=stream.cuda_stream)
