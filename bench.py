@@ -285,14 +285,14 @@ def run_other_workload(args):
         loss = _lib.adg_mlp_train(s.ctx, epochs=30, batch=4096, lr=3e-3, seed=0)
         s.load_state(state)
         _lib.adg_mlp_params(s.ctx, enable=1)
-        t0 = time.perf_counter()
         s.advance(steps)
         torch.cuda.synchronize()
         s1, i1 = _lib.adg_fault_stats(s.ctx, reset=True)
+        kms_l, _ = _lib.adg_profile(s.ctx, 1)
         line["rupture"] = {"newton_iters_per_solve_plain": i0 / max(s0, 1),
                            "newton_iters_per_solve_learned": i1 / max(s1, 1), "training_solves": ncap,
                            "train_loss": [float(loss[0]), float(loss[1])], "solves_per_step": s0 / steps,
-                           "friction_kernel_ms": kms[2]}
+                           "friction_kernel_ms": kms[2], "friction_kernel_ms_learned": kms_l[2]}
     print(json.dumps(line), flush=True)
 
 

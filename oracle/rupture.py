@@ -210,14 +210,23 @@ def solve_step(n, qm_t, qp_t, matm, matp, par, dt, N, guess=None, tol=1e-10, max
         Vold = V
         # the start guess only seeds Newton; the state update of the first
         # pass uses the previous slip rate, the second the mid-point
-        Vcur = V if guess is None else guess(j, Th, st, psi, V)
+        Vcur = V if guess is None else guess(j, Th, st, psi, V, par)
         psi_new = psi
         for ps in range(2):
             Vmid = Vold if ps == 0 else 0.5 * (Vold + Vcur)
             psi_new = psi_relax(psi, Vmid, h, par)
             Vcur, it, ok = newton_slip_rate(Th, st["S"], st["eta"], psi_new, par, Vcur, tol, max_iter)
+            if ps == 0 and guess is not None and not np.all(ok):
+                # fallback: rerun the failed points from the warm start
+                Vw, itw, okw = newton_slip_rate(Th, st["S"], st["eta"], psi_new, par, V, tol, max_iter)
+                bad = ~ok
+                Vcur = np.where(bad, Vw, Vcur)
+                it = np.where(bad, it + itw, it)
+                ok = np.where(bad, okw, ok)
             if not np.all(ok):
                 raise RuntimeError("friction Newton did not converge")
+            if ps == 0 and hasattr(guess, "solved"):
+                guess.solved(j, Vcur)
             iters[j, ps] = it
         psi, V = psi_new, Vcur
         t_b, vb, vc, Vvec, tau_tot = middle_traction_velocity(st, V, n)

@@ -16,6 +16,11 @@
 //   on x = ln |V| clamped to [-700, ln(Theta/eta_s)], |dx| <= 1e-10]; the
 //   learned guess only seeds the pass-0 Newton, so the answer does not
 //   depend on it.
+// Learned start (the paper has none): the network predicts ln V* - x_a, x_a
+// the large-argument asymptote of asinh; at time points j >= 1 the pass-0
+// Newton starts from the warm start plus the change of the predicted ln V*
+// since point j-1 (exact where nothing changes), at j = 0 from the warm
+// start; a start that fails falls back to the warm start.
 // Output per fault face: the time-integrated flux n.(A,B,C) q^b for the minus
 // element (minus node order) and -n.(A,B,C) q^c for the plus element (plus
 // node order); the neighbour kernel lifts them.
@@ -101,7 +106,7 @@ __device__ void traction(const double q[9], const double n[3], double t[3]) {
   t[2] = q[5] * n[0] + q[4] * n[1] + q[2] * n[2];
 }
 
-// friction-guess network (FP32): features -> predicted ln V
+// friction-guess network (FP32): features -> predicted ln V* - x_a
 __device__ float mlp_eval(const float* W, const float f[MLP_IN]) {
   const float* W1 = W;
   const float* b1 = W1 + MLP_IN * MLP_H;
@@ -165,6 +170,8 @@ __global__ void __launch_bounds__(128) rupture_kernel(DRArgs a) {
   double tau_tot[3] = {st[5], st[6], st[7]};
   double Gm[9] = {0}, Gp[9] = {0};
   double tprev = 0.0;
+  double xhat_prev = 0.0;  // the network's ln V* at the previous time point
+  bool have_prev = false;
   unsigned long long n_solves = 0, n_iters = 0;
   bool all_ok = true;
   for (int j = 0; j <= N; ++j) {
@@ -203,22 +210,37 @@ __global__ void __launch_bounds__(128) rupture_kernel(DRArgs a) {
     const double S = fmax(0.0, -(sn0 + sn_b));
     const double h = t - tprev;
     const double Vold = V;
-    double x0 = log(fmax(V, 1e-300));
-    double xa = 0.0;
+    const double xw = log(fmax(V, 1e-300));  // warm start: the previous ln|V|
+    double x0 = xw;
+    double xa = 0.0;  // asinh asymptote: the base of the network's prediction
     float feat[MLP_IN];
     const bool solve = (Th > 0) && (S > 0);
+    bool learned = false;
     if (solve && (a.mlp || a.capture)) {
       const double lc = psi / p.a - log(2.0 * p.V0);
       const double xhi = log(Th / eta);
       const double r = fmin(Th / (S * p.a), 700.0);
+      const double xwc = fmin(fmax(xw, kXFloor), xhi);
       xa = fmin(fmax(r - lc - 0.6931471805599453, kXFloor), xhi);
       feat[0] = (float)r;
       feat[1] = (float)lc;
       feat[2] = (float)xhi;
-      feat[3] = (float)fmin(fmax(x0, kXFloor), xhi);
+      feat[3] = (float)xwc;
       feat[4] = (float)fmin(fmax(log(eta / (S * p.a)), -50.0), 50.0);
       feat[5] = (float)xa;
-      if (a.mlp) x0 = fmin(fmax(xa + (double)mlp_eval(a.mlp, feat), kXFloor), xhi);
+      if (a.mlp) {
+        // predicted ln V* = x_a + network; from the second time point on, the
+        // start is the warm start moved by the change of that prediction
+        const double xhat = xa + (double)mlp_eval(a.mlp, feat);
+        if (have_prev) {
+          x0 = fmin(fmax(xwc + (xhat - xhat_prev), kXFloor), xhi);
+          learned = true;
+        }
+        xhat_prev = xhat;
+        have_prev = true;
+      }
+    } else {
+      have_prev = false;
     }
     double Vcur = exp(x0);
     if (!(Vcur > 0)) Vcur = 0.0;
@@ -231,6 +253,12 @@ __global__ void __launch_bounds__(128) rupture_kernel(DRArgs a) {
       int it;
       bool ok;
       Vcur = newton_v(Th, S, eta, psi_new, p, log(fmax(Vcur, 1e-300)), &it, &ok);
+      if (pass == 0 && learned && !ok) {
+        // fallback: rerun from the warm start
+        int it_w;
+        Vcur = newton_v(Th, S, eta, psi_new, p, xw, &it_w, &ok);
+        it += it_w;
+      }
       all_ok &= ok;
       if (solve) {
         n_solves++;
