@@ -50,9 +50,11 @@ extern "C" {
 
 #define ADG_FP64 0
 #define ADG_FP32 1
-/* FP32 dofs; at degree 5 the reference-matrix products run on the tensor
- * cores (tcgen05) as 3xTF32 split products with FP32 accumulation; other
- * degrees behave as ADG_FP32. */
+/* FP32 dofs; at degree 5 the predictor, face traces and volume term of the
+ * elements without gravitational face, fault face or neighbour in another LTS
+ * cluster run on the tensor cores (tcgen05) as 3xTF32 split products with
+ * FP32 accumulation, everything else as in ADG_FP32; other degrees behave as
+ * ADG_FP32. */
 #define ADG_3XTF32 2
 
 /* Face tags (per tet and local face). */
@@ -151,11 +153,12 @@ int adg_step_cluster(adg_ctx* ctx, int c);
 int adg_sync(adg_ctx* ctx);
 
 /* Per-kernel timing for roofline reports: runs n_macro macro steps with
- * eager (non-graph) launches and a CUDA event pair around every kernel on the
- * library stream.  ms[k] = mean duration of one launch of kernel kind k,
- * launches[k] = number of launches (arrays of 3), k = 0 local (predictor,
- * volume, local flux), 1 neighbour flux, 2 fault friction solve.  Advances
- * the simulation like adg_advance. */
+ * eager (non-graph) launches and a CUDA event pair around the work of every
+ * kernel kind of a cluster on the library stream.  ms[k] = mean duration of
+ * one such phase of kind k, launches[k] = number of kernel launches (arrays
+ * of 3), k = 0 local (predictor, volume, traces; with ADG_3XTF32 at degree 5
+ * one tensor-core and one CUDA-core launch per cluster), 1 neighbour flux,
+ * 2 fault friction solve.  Advances the simulation like adg_advance. */
 int adg_profile(adg_ctx* ctx, int n_macro, double* ms, int64_t* launches);
 
 /* Allocation-free global steps (the paper has no counterpart; this is a
@@ -214,11 +217,16 @@ int adg_read_fault(adg_ctx* ctx, double* state);
 int adg_fault_stats(adg_ctx* ctx, int64_t* solves, int64_t* iterations, int reset);
 
 /* ---- Learned Newton start for the friction solve ----------------------------
- * A 6-32-32-1 tanh network proposes ln|V| for the first Newton pass of every
- * friction solve; Newton then converges to the same tolerance as from the
- * plain start (the previous slip rate), which it replaces only as a guess.
- * adg_rupture_capture(capacity): start recording (features, converged ln|V|)
- *   of every solve into a device buffer of that many rows (0 stops recording);
+ * A 6-32-32-1 tanh network predicts the first-pass solution ln|V*| of every
+ * friction solve as x_a + network, x_a the large-argument asymptote of asinh.
+ * At the second and later time points of a step the first Newton pass starts
+ * from the warm start ln|V_prev| moved by the change of that prediction since
+ * the previous time point; at the first it starts from the warm start, and a
+ * start that fails falls back to it.  Newton then converges to the same
+ * tolerance as from the plain start, so only the iteration count changes.
+ * adg_rupture_capture(capacity): start recording rows (6 features,
+ *   ln|V*| - x_a) of every first-pass solve into a device buffer of that many
+ *   rows (0 stops recording);
  *   *n_captured returns the rows recorded since the last start.
  * adg_mlp_train: fit the network to the recorded rows on the GPU (own forward,
  *   backward and Adam kernels); loss[2] = scaled MSE before / after.

@@ -42,30 +42,53 @@ void check_cuda(cudaError_t e, const char* what) {
   if (e != cudaSuccess) adg::throw_err(ADG_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
+// Pinned staging buffer sized for the dofs in device precision: conversion to
+// or from the caller's double array runs in parallel on the host, the copy over
+// the host link runs from pinned memory.  Chunks of elements are converted and
+// copied in a pipeline (the copy of chunk k overlaps the conversion of k+1).
+template <typename T>
+T* staging(Ctx& c) {
+  const size_t bytes = (size_t)c.nt * c.S * 9 * c.B * sizeof(T);
+  if (c.hstage_bytes < bytes) {
+    if (c.hstage) cudaFreeHost(c.hstage);
+    c.hstage = nullptr;
+    c.hstage_bytes = 0;
+    check_cuda(cudaHostAlloc(&c.hstage, bytes, cudaHostAllocDefault), "pinned staging buffer");
+    c.hstage_bytes = bytes;
+  }
+  return (T*)c.hstage;
+}
+
+constexpr int64_t kChunks = 8;
+
 template <typename T>
 void put_dofs(Ctx& c, const double* Q) {
   const int64_t per = (int64_t)c.S * 9 * c.B;
-  std::vector<T> buf((size_t)(c.nt * per));
+  T* buf = staging<T>(c);
+  for (int64_t ch = 0; ch < kChunks; ++ch) {
+    const int64_t i0 = c.nt * ch / kChunks, i1 = c.nt * (ch + 1) / kChunks;
 #pragma omp parallel for schedule(static)
-  for (int64_t i = 0; i < c.nt; ++i) {
-    const double* src = Q + c.order[i] * per;
-    T* dst = buf.data() + i * per;
-    for (int64_t k = 0; k < per; ++k) dst[k] = (T)src[k];
+    for (int64_t i = i0; i < i1; ++i) {
+      const double* src = Q + c.order[i] * per;
+      T* dst = buf + i * per;
+      for (int64_t k = 0; k < per; ++k) dst[k] = (T)src[k];
+    }
+    check_cuda(cudaMemcpyAsync((T*)c.dQ + i0 * per, buf + i0 * per, (size_t)(i1 - i0) * per * sizeof(T),
+                               cudaMemcpyHostToDevice, c.stream),
+               "dofs upload");
   }
-  check_cuda(cudaMemcpyAsync(c.dQ, buf.data(), buf.size() * sizeof(T), cudaMemcpyHostToDevice, c.stream),
-             "dofs upload");
   check_cuda(cudaStreamSynchronize(c.stream), "dofs upload");
 }
 template <typename T>
 void take_dofs(Ctx& c, double* Q) {
   const int64_t per = (int64_t)c.S * 9 * c.B;
-  std::vector<T> buf((size_t)(c.nt * per));
-  check_cuda(cudaMemcpyAsync(buf.data(), c.dQ, buf.size() * sizeof(T), cudaMemcpyDeviceToHost, c.stream),
+  T* buf = staging<T>(c);
+  check_cuda(cudaMemcpyAsync(buf, c.dQ, (size_t)c.nt * per * sizeof(T), cudaMemcpyDeviceToHost, c.stream),
              "dofs download");
   check_cuda(cudaStreamSynchronize(c.stream), "dofs download");
 #pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < c.nt; ++i) {
-    const T* src = buf.data() + i * per;
+    const T* src = buf + i * per;
     double* dst = Q + c.order[i] * per;
     for (int64_t k = 0; k < per; ++k) dst[k] = (double)src[k];
   }
@@ -380,16 +403,17 @@ int adg_profile(adg_ctx* ctx, int n_macro, double* ms, int64_t* launches) {
     c.prof = nullptr;
     check_cuda(cudaStreamSynchronize(c.stream), "profile");
     double tot[3] = {0, 0, 0};
-    int64_t cnt[3] = {0, 0, 0};
+    int64_t cnt[3] = {0, 0, 0}, nl[3] = {0, 0, 0};
     for (auto& e : evs) {
       float t = 0;
       check_cuda(cudaEventElapsedTime(&t, e.a, e.b), "profile events");
       tot[e.kind] += t;
       cnt[e.kind] += 1;
+      nl[e.kind] += e.launches;
     }
     for (int k = 0; k < 3; ++k) {
       ms[k] = cnt[k] ? tot[k] / cnt[k] : 0.0;
-      launches[k] = cnt[k];
+      launches[k] = nl[k];
     }
     c.check_err();
   });

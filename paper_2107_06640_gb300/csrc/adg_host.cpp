@@ -375,14 +375,30 @@ void Ctx::setup() {
   }
   ncl = 0;
   for (int64_t e = 0; e < E; ++e) ncl = std::max(ncl, cl[e] + 1);
-  // ---- internal order: by cluster, stable
+  // ---- internal order: by cluster, stable; with the tensor-core local
+  // kernel, the elements of a cluster without gravitational face, fault face
+  // or neighbour in another cluster come first
+  std::vector<char> special(E, 0);
+  if (tc)
+    for (int64_t e = 0; e < E; ++e)
+      for (int f = 0; f < 4; ++f) {
+        const int tg = tag[4 * e + f];
+        const int64_t e2 = nbr_u[4 * e + f];
+        if (tg == ADG_TAG_GRAVITY || tg == ADG_TAG_FAULT || (e2 >= 0 && cl[e2] != cl[e])) special[e] = 1;
+      }
   order.resize(E);
   for (int64_t e = 0; e < E; ++e) order[e] = e;
-  std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return cl[a] < cl[b]; });
+  std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) {
+    return cl[a] != cl[b] ? cl[a] < cl[b] : special[a] < special[b];
+  });
   inv.assign(E, 0);
   for (int64_t i = 0; i < E; ++i) inv[order[i]] = i;
   cl_begin.assign(ncl + 1, 0);
-  for (int64_t i = 0; i < E; ++i) cl_begin[cl[order[i]] + 1]++;
+  cl_plain.assign(ncl, 0);
+  for (int64_t i = 0; i < E; ++i) {
+    cl_begin[cl[order[i]] + 1]++;
+    if (tc && !special[order[i]]) cl_plain[cl[order[i]]]++;
+  }
   for (int c = 0; c < ncl; ++c) cl_begin[c + 1] += cl_begin[c];
   cluster.resize(E);
   for (int64_t i = 0; i < E; ++i) cluster[i] = cl[order[i]];
@@ -571,9 +587,9 @@ void Ctx::setup() {
   dPerm = upload_raw<int>(ops.perm, owned, dev_bytes);
   CK(cudaDeviceGetAttribute(&n_sms, cudaDevAttrMultiProcessorCount, cfg.device));
   if (tc) {
-    std::vector<float> tl(TC_LIFT_FLOATS);
-    pack_lift_tc(ops.lift.data(), tl.data());
-    dTcLift = upload_raw<float>(tl, owned, dev_bytes);
+    std::vector<float> tl(local_tc_floats());
+    pack_local_tc(ops.kt.data(), ops.kvol.data(), ops.efc.data(), tl.data());
+    dTcLocal = upload_raw<float>(tl, owned, dev_bytes);
   }
   dErr = (unsigned int*)dalloc(sizeof(unsigned int), owned, dev_bytes);
   if (nff) {
@@ -590,7 +606,7 @@ void Ctx::setup() {
   // configure kernels once (outside any stream capture)
   StepArgs a0 = base_args();
   int rc = launch_local(fp64, N, a0, 0, stream);
-  if (!rc && tc) rc = launch_neighbour_tc(a0, 0, n_sms, stream);
+  if (!rc && tc) rc = launch_local_tc(a0, 0, n_sms, stream);
   if (rc) throw Err(ADG_E_CUDA, std::string("kernel configuration: ") + cudaGetErrorString((cudaError_t)rc));
   tick = 0;
   time = 0.0;
@@ -604,7 +620,7 @@ StepArgs Ctx::base_args() const {
   a.gslot = dGslot; a.bslot = dBslot; a.dslot = dDslot;
   a.ktT = dKt; a.kvolT = dKvol; a.efcT = dEfc; a.liftT = dLift; a.perm = dPerm; a.gpar = dGpar;
   a.S = S; a.err = dErr;
-  a.fslot = dFslot; a.drout = dDrout; a.gflux = dGflux; a.tc_lift = dTcLift;
+  a.fslot = dFslot; a.drout = dDrout; a.gflux = dGflux; a.tc_local = dTcLocal;
   return a;
 }
 
@@ -630,13 +646,23 @@ void Ctx::launch_tick(int s, double dtm) {
     a.dt = dt;
     taylor_int(N, 0.0, dt, a.tcoef);
     a.btrace_mode = (s % (1 << (c + 1)) == 0) ? 1 : 2;
-    ProfEv ev{0, nullptr, nullptr};
+    ProfEv ev{0, nullptr, nullptr, 1};
     if (prof) {
       CK(cudaEventCreate(&ev.a));
       CK(cudaEventCreate(&ev.b));
       CK(cudaEventRecord(ev.a, stream));
     }
-    int rc = launch_local(fp64, N, a, n * S, stream);
+    int rc = 0;
+    if (tc) {
+      // plain elements on the tensor cores, the rest on the CUDA cores
+      const int64_t np = cl_plain[c];
+      ev.launches = (np > 0) + (n > np);
+      if (np > 0) rc = launch_local_tc(a, np * S, n_sms, stream);
+      a.v_begin = (cl_begin[c] + np) * S;
+      if (!rc && n > np) rc = launch_local(fp64, N, a, (n - np) * S, stream);
+    } else {
+      rc = launch_local(fp64, N, a, n * S, stream);
+    }
     if (prof) { CK(cudaEventRecord(ev.b, stream)); prof->push_back(ev); }
     if (rc) throw Err(ADG_E_CUDA, std::string("local kernel: ") + cudaGetErrorString((cudaError_t)rc));
   }
@@ -651,13 +677,13 @@ void Ctx::launch_tick(int s, double dtm) {
     a.dt = dt;
     taylor_int(N, half * dt, (half + 1) * dt, a.ccoef);
     if (fcl_begin.size() > (size_t)c + 1 && fcl_begin[c + 1] > fcl_begin[c]) launch_rupture_cluster(c, dt);
-    ProfEv ev{1, nullptr, nullptr};
+    ProfEv ev{1, nullptr, nullptr, 1};
     if (prof) {
       CK(cudaEventCreate(&ev.a));
       CK(cudaEventCreate(&ev.b));
       CK(cudaEventRecord(ev.a, stream));
     }
-    int rc = tc ? launch_neighbour_tc(a, n * S, n_sms, stream) : launch_neighbour(fp64, N, a, n * S, stream);
+    int rc = launch_neighbour(fp64, N, a, n * S, stream);
     if (prof) { CK(cudaEventRecord(ev.b, stream)); prof->push_back(ev); }
     if (rc) throw Err(ADG_E_CUDA, std::string("neighbour kernel: ") + cudaGetErrorString((cudaError_t)rc));
   }
@@ -682,7 +708,7 @@ void Ctx::launch_rupture_cluster(int c, double dt) {
   d.capture = cap_on ? dCapture : nullptr;
   d.cap_count = dCapCount;
   d.cap_capacity = cap_capacity;
-  ProfEv ev{2, nullptr, nullptr};
+  ProfEv ev{2, nullptr, nullptr, 1};
   if (prof) {
     CK(cudaEventCreate(&ev.a));
     CK(cudaEventCreate(&ev.b));
@@ -699,7 +725,10 @@ int64_t Ctx::launches_per_macro() const {
   for (int s = 0; s < ticks; ++s)
     for (int c = 0; c < ncl; ++c) {
       if (cl_begin[c + 1] == cl_begin[c]) continue;
-      if (s % (1 << c) == 0) ++L;
+      if (s % (1 << c) == 0) {
+        const int64_t n = cl_begin[c + 1] - cl_begin[c];
+        L += tc ? (cl_plain[c] > 0) + (n > cl_plain[c]) : 1;
+      }
       if ((s + 1) % (1 << c) == 0) L += (fcl_begin[c + 1] > fcl_begin[c]) ? 2 : 1;
     }
   return L;
@@ -744,6 +773,7 @@ void Ctx::check_err() {
 Ctx::~Ctx() {
   if (graph_exec) cudaGraphExecDestroy(graph_exec);
   for (void* p : owned) cudaFree(p);
+  if (hstage) cudaFreeHost(hstage);
   if (own_stream) cudaStreamDestroy(own_stream);
 }
 

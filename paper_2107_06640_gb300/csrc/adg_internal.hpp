@@ -43,12 +43,15 @@ struct Ctx {
   // discretisation
   int N = 0, B = 0, Bf = 0, B1 = 0, S = 1;
   bool fp64 = true;
-  bool tc = false;          // tensor-core (3xTF32) kernels in use
+  bool tc = false;          // tensor-core (3xTF32) local kernel in use
   int n_sms = 1;
-  float* dTcLift = nullptr;
+  float* dTcLocal = nullptr;
   RefOps ops;
   int ncl = 1;
   std::vector<int64_t> order, inv, cl_begin;
+  // elements [cl_begin[c], cl_begin[c] + cl_plain[c]) of cluster c have no
+  // gravitational face, fault face or LTS buffer (tensor-core local kernel)
+  std::vector<int64_t> cl_plain;
   std::vector<int> cluster;
   double dtmin = 0, time = 0;
   int64_t tick = 0;
@@ -88,8 +91,11 @@ struct Ctx {
   bool cap_on = false;
   void launch_rupture_cluster(int c, double dt);
   // per-kernel profiling (adg_profile)
-  struct ProfEv { int kind; cudaEvent_t a, b; };
+  struct ProfEv { int kind; cudaEvent_t a, b; int launches; };
   std::vector<ProfEv>* prof = nullptr;
+  // pinned host staging buffer for dofs upload / download (allocated on first use)
+  void* hstage = nullptr;
+  size_t hstage_bytes = 0;
   // receivers
   int64_t n_rec = 0;
   int64_t* dRecElem = nullptr;

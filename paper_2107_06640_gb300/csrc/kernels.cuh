@@ -62,13 +62,14 @@ struct StepArgs {
   const int* fslot;     // [E][4] 2*fault + side for fault faces, else -1
   const void* drout;    // T [nff*S][2][9][Bf] time-integrated fault flux per side
   void* gflux;          // T [ngslot*S][9][Bf] time-integrated flux of gravitational faces
-  const float* tc_lift; // tensor-core lift operand (hi/lo, canonical layout), degree 5 only
+  const float* tc_local; // tensor-core operands of the local kernel (hi/lo, canonical layout), degree 5
 };
 
-// tensor-core (tcgen05, 3xTF32) neighbour kernel, degree 5, FP32 dofs (neighbour_tc.cu)
-int launch_neighbour_tc(const StepArgs& a, int64_t n_virtual, int n_sms, void* stream);
-void pack_lift_tc(const double* lift, float* out);
-constexpr int TC_LIFT_FLOATS = 2 * 64 * 88;
+// tensor-core (tcgen05, 3xTF32) local kernel, degree 5, FP32 dofs (local_tc.cu),
+// for elements without gravitational faces, fault faces or LTS buffers
+int launch_local_tc(const StepArgs& a, int64_t n_virtual, int n_sms, void* stream);
+void pack_local_tc(const double* kt, const double* kvol, const double* efc, float* out);
+int local_tc_floats();
 
 // ---- dynamic rupture (rupture.cu) ----
 // per-node fault parameters (double, stride FPAR), in this order:

@@ -1,0 +1,495 @@
+// Local element kernel on the tensor cores (tcgen05, 3xTF32), degree 5,
+// FP32 dofs: Cauchy-Kovalewski predictor, time integral, face traces and
+// volume term of Sec. 4.1 for elements without gravitational faces, fault
+// faces or LTS buffers (those take the CUDA-core kernel).
+//
+// A tile is 12 (virtual) elements x 9 quantities = the 128 rows of the MMAs,
+// one row per TMEM lane: warp w of a warpgroup holds elements 3w..3w+2, the
+// j-th of them in lanes 9j..9j+8 (lane 9j+p = quantity p); lanes 27..31 are
+// zero padding.  Every product with a reference matrix is then
+//   rows(element, quantity) x reference matrix^T
+// with the element data as the A operand in TMEM (split into tf32 hi + lo by
+// the threads that own the rows) and the reference matrices as B operands,
+// resident in shared memory in the canonical K-major layout (hi and lo);
+// A_hi B_hi + A_hi B_lo + A_lo B_hi accumulate in fp32 in TMEM.  Per tile:
+//   levels k = 0, 1, 2:  Y = D^k [KT_0; KT_1; KT_2]^T on the tensor cores,
+//     then X_d = sum_a (dxi_a/dx_d) Y_a and D^{k+1} = -sum_d A_d X_d on the CUDA
+//     cores (Jacobian form of the star product; the quantities of an element
+//     are exchanged with warp shuffles);
+//   levels 3, 4 (4 and 1 rows) on the CUDA cores from registers;
+//   I = sum_k dt^{k+1}/(k+1)! D^k in registers (Eq. taylor);
+//   traces V_f = E_f I on the tensor cores, written to the trace array;
+//   volume: Z_a = A*_a I (shuffles), Q += sum_a K_a Z_a on the tensor cores.
+// The two warpgroups of a CTA work on two tiles at a time (TMEM columns
+// [0, 256) and [256, 512)); one thread per warpgroup issues its MMAs and
+// waits for their completion with a bounded mbarrier wait.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "kernels.cuh"
+#include "tc_common.cuh"
+
+namespace adg {
+
+namespace {
+
+constexpr int B = 56, B1 = 35, BF = 21;
+constexpr int TE = 12;          // elements per tile
+constexpr int kThreadsL = 256;  // two warpgroups
+constexpr int kWaitIters = 1 << 24;
+
+// tensor-core predictor levels: K (rows of D^k, padded to 8), rows of D^{k+1}
+// per axis (padded to 8), N = 3 axes (padded to 16)
+constexpr int kK0 = 56, kM0 = 35, kM0p = 40, kN0 = 128;
+constexpr int kK1 = 40, kM1 = 20, kM1p = 24, kN1 = 80;
+constexpr int kK2 = 24, kM2 = 10, kM2p = 16, kN2 = 48;
+constexpr int kNT = 96;  // traces: 4 faces x 21 nodes, padded
+constexpr int kNV = 64;  // volume: 56 basis functions, padded; K per axis = 40
+
+// shared-memory image of the operands (floats), hi block then lo block each
+struct LImg {
+  static constexpr int oP0 = 0, sP0 = kN0 * kK0;
+  static constexpr int oP1 = oP0 + 2 * sP0, sP1 = kN1 * kK1;
+  static constexpr int oP2 = oP1 + 2 * sP1, sP2 = kN2 * kK2;
+  static constexpr int oV = oP2 + 2 * sP2, sV = kNV * 40;  // per axis
+  static constexpr int oT = oV + 6 * sV, sT = kNT * kK0;
+  static constexpr int oK3 = oT + 2 * sT;                  // kt[a][m][l], m < 4, l < 10
+  static constexpr int oK4 = oK3 + 120;                    // kt[a][0][l], l < 4
+  static constexpr int floats = ((oK4 + 12 + 3) / 4) * 4;
+  static constexpr int bytes = floats * 4;
+};
+static_assert(LImg::bytes + 64 <= 232448, "operands exceed the shared memory of one CTA");
+
+// per-warpgroup TMEM columns: A hi [0, 64), A lo [64, 128), accumulators [128, 256)
+constexpr uint32_t cAh = 0, cAl = 64, cAcc = 128;
+
+__device__ __forceinline__ void mma_ts(uint32_t d, uint32_t a, uint64_t db, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d),
+      "r"(a), "l"(db), "r"(idesc), "r"(acc));
+}
+
+// 3xTF32 product into d: A (TMEM, hi at ah, lo at al) x B^T (shared, canonical
+// K-major N x K, hi at bh, lo at bl), K / 8 steps
+__device__ __forceinline__ void issue(uint32_t d, uint32_t ah, uint32_t al, uint32_t bh, uint32_t bl, int N, int K,
+                                      bool acc_first) {
+  const uint32_t idesc = tc::idesc_tf32(128, N);
+  const uint32_t lbo = (uint32_t)(N / 8) * 128;
+  for (int kk = 0; kk < K / 8; ++kk) {
+    const uint32_t off = kk * 2 * lbo;
+    const uint64_t dbh = tc::sdesc(bh + off, lbo, 128), dbl = tc::sdesc(bl + off, lbo, 128);
+    mma_ts(d, ah + 8 * kk, dbh, idesc, (kk > 0 || acc_first) ? 1u : 0u);
+    mma_ts(d, ah + 8 * kk, dbl, idesc, 1u);
+    mma_ts(d, al + 8 * kk, dbh, idesc, 1u);
+  }
+}
+
+// three groups of 8 consecutive fp32 columns of this warp's lanes (one wait)
+__device__ __forceinline__ void ld3x8(uint32_t t0, uint32_t t1, uint32_t t2, float o[24]) {
+  uint32_t r[24];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%24];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8,%9,%10,%11,%12,%13,%14,%15}, [%25];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%16,%17,%18,%19,%20,%21,%22,%23}, [%26];\n"
+      "tcgen05.wait::ld.sync.aligned;\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23])
+      : "r"(t0), "r"(t1), "r"(t2));
+#pragma unroll
+  for (int j = 0; j < 24; ++j) o[j] = __uint_as_float(r[j]);
+}
+
+__device__ __forceinline__ void ld8(uint32_t t, float o[8]) {
+  uint32_t r[8];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+      "tcgen05.wait::ld.sync.aligned;\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+      : "r"(t));
+#pragma unroll
+  for (int j = 0; j < 8; ++j) o[j] = __uint_as_float(r[j]);
+}
+
+// 8 values of this lane's row -> tf32 hi at column th, lo at column tl
+__device__ __forceinline__ void st_split8(uint32_t th, uint32_t tl, const float x[8]) {
+  uint32_t h[8], l[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const float hh = tc::tf32_trunc(x[j]);
+    h[j] = __float_as_uint(hh);
+    l[j] = __float_as_uint(x[j] - hh);
+  }
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(th), "r"(h[0]),
+               "r"(h[1]), "r"(h[2]), "r"(h[3]), "r"(h[4]), "r"(h[5]), "r"(h[6]), "r"(h[7]));
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(tl), "r"(l[0]),
+               "r"(l[1]), "r"(l[2]), "r"(l[3]), "r"(l[4]), "r"(l[5]), "r"(l[6]), "r"(l[7]));
+}
+
+__device__ __forceinline__ void wg_bar(int wg) { asm volatile("bar.sync %0, 128;" ::"r"(wg + 1)); }
+
+// Per-thread star-product data: the quantity p of this lane's row, the lanes
+// of the quantities each output reads and their material coefficients.
+// D^{k+1}[p] = sum_d c_d X_d[src_d] with X_d = sum_a (dxi_a/dx_d) Y_a, the
+// Jacobian form of -sum_a A*_a Y_a (Eq. elasticity-pde); the volume operand
+// is Z_a[p] = -sum_d (dxi_a/dx_d) c_d I[src_d].
+struct Star {
+  float g[9];    // g[a*3+d] = d xi_a / d x_d
+  float c[3];    // coefficients of the three directions
+  int src[3];    // source lanes
+};
+
+__device__ __forceinline__ void star_setup(int lane, bool valid, const float* par, Star& s) {
+  const int j = lane / 9, p = lane - 9 * (lane / 9);
+  const int base = 9 * j;
+  float lam = 0.f, mu = 0.f, irho = 0.f;
+  if (valid) {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) s.g[k] = par[k];
+    irho = 1.f / par[9];
+    lam = par[10];
+    mu = par[11];
+  } else {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) s.g[k] = 0.f;
+  }
+  const float l2m = lam + 2.f * mu;
+  // (source quantity, coefficient) per direction d for output quantity p
+  int q0 = p, q1 = p, q2 = p;
+  float c0 = 0.f, c1 = 0.f, c2 = 0.f;
+  switch (p) {
+    case 0: q0 = 6; c0 = l2m; q1 = 7; c1 = lam; q2 = 8; c2 = lam; break;
+    case 1: q0 = 6; c0 = lam; q1 = 7; c1 = l2m; q2 = 8; c2 = lam; break;
+    case 2: q0 = 6; c0 = lam; q1 = 7; c1 = lam; q2 = 8; c2 = l2m; break;
+    case 3: q0 = 7; c0 = mu; q1 = 6; c1 = mu; break;
+    case 4: q1 = 8; c1 = mu; q2 = 7; c2 = mu; break;
+    case 5: q0 = 8; c0 = mu; q2 = 6; c2 = mu; break;
+    case 6: q0 = 0; c0 = irho; q1 = 3; c1 = irho; q2 = 5; c2 = irho; break;
+    case 7: q0 = 3; c0 = irho; q1 = 1; c1 = irho; q2 = 4; c2 = irho; break;
+    default: q0 = 5; c0 = irho; q1 = 4; c1 = irho; q2 = 2; c2 = irho; break;
+  }
+  if (lane >= 27) { q0 = q1 = q2 = 0; c0 = c1 = c2 = 0.f; }
+  s.c[0] = c0; s.c[1] = c1; s.c[2] = c2;
+  s.src[0] = (lane >= 27 ? lane : base + q0);
+  s.src[1] = (lane >= 27 ? lane : base + q1);
+  s.src[2] = (lane >= 27 ? lane : base + q2);
+}
+
+// one output of the star product from the three axis values of this lane
+__device__ __forceinline__ float star_apply(const Star& s, float y0, float y1, float y2) {
+  const float X0 = s.g[0] * y0 + s.g[3] * y1 + s.g[6] * y2;
+  const float X1 = s.g[1] * y0 + s.g[4] * y1 + s.g[7] * y2;
+  const float X2 = s.g[2] * y0 + s.g[5] * y1 + s.g[8] * y2;
+  const float a0 = __shfl_sync(0xffffffffu, X0, s.src[0]);
+  const float a1 = __shfl_sync(0xffffffffu, X1, s.src[1]);
+  const float a2 = __shfl_sync(0xffffffffu, X2, s.src[2]);
+  return s.c[0] * a0 + s.c[1] * a1 + s.c[2] * a2;
+}
+
+// Epilogue of a tensor-core predictor level: Y (3 axes x MP columns at tacc)
+// -> D^{k+1} (M rows), I += ck * D^{k+1}; D^{k+1} goes to the A columns of the
+// next level (TO_A) or to registers dn.
+template <int M, int MP, bool TO_A>
+__device__ __forceinline__ void level_epilogue(uint32_t tacc, uint32_t tah, uint32_t tal, const Star& s, float ck,
+                                               float (&I)[B], float* dn) {
+#pragma unroll
+  for (int mc = 0; mc < MP / 8; ++mc) {
+    float y[24];
+    ld3x8(tacc + 8 * mc, tacc + MP + 8 * mc, tacc + 2 * MP + 8 * mc, y);
+    float d[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int m = 8 * mc + j;
+      if (m < M) {
+        d[j] = star_apply(s, y[j], y[8 + j], y[16 + j]);
+        I[m] += ck * d[j];
+        if (!TO_A) dn[m] = d[j];
+      } else {
+        d[j] = 0.f;
+      }
+    }
+    if (TO_A) st_split8(tah + 8 * mc, tal + 8 * mc, d);
+  }
+}
+
+__global__ void __launch_bounds__(kThreadsL, 1) local_tc_kernel(StepArgs a, int64_t n_virtual) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  float* sm = reinterpret_cast<float*>(smem_raw);
+  __shared__ uint32_t tmem_base;
+  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ int s_abort[2];
+
+  const int tid = threadIdx.x, wg = tid >> 7, t = tid & 127, w = t >> 5, lane = tid & 31;
+  {
+    const float4* src = reinterpret_cast<const float4*>(a.tc_local);
+    float4* dst = reinterpret_cast<float4*>(sm);
+    for (int r = tid; r < LImg::floats / 4; r += kThreadsL) dst[r] = src[r];
+  }
+  if (tid < 2) {
+    tc::mbar_init(&mbar[tid], 1);
+    s_abort[tid] = 0;
+  }
+  if (tid < 32) tc::tmem_alloc<512>(&tmem_base);
+  tc::fence_async_smem();
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+
+  const uint32_t tbase = tmem_base + (uint32_t)wg * 256u;            // this warpgroup's columns
+  const uint32_t trow = tbase + ((uint32_t)(32 * w) << 16);           // this warp's lanes
+  const uint32_t sbase = tc::smem_u32(sm);
+  const float* k3 = sm + LImg::oK3;
+  const float* k4 = sm + LImg::oK4;
+  const int jj = lane / 9, p = lane - 9 * (lane / 9);
+  const int64_t ntiles = (n_virtual + TE - 1) / TE;
+  uint32_t phase = 0;
+  const float tc0 = (float)a.tcoef[0], tc1 = (float)a.tcoef[1], tc2 = (float)a.tcoef[2];
+  const float tc3 = (float)a.tcoef[3], tc4 = (float)a.tcoef[4], tc5 = (float)a.tcoef[5];
+
+  // one tensor-core round of this warpgroup: make the A stores visible, issue
+  // (thread 0 of the warpgroup), wait for completion; false on timeout
+  auto round = [&](auto&& issue_fn) -> bool {
+    asm volatile("tcgen05.wait::st.sync.aligned;");
+    tc::fence_before();
+    wg_bar(wg);
+    tc::fence_after();
+    if (t == 0) {
+      issue_fn();
+      tc::commit(&mbar[wg]);
+      if (!tc::mbar_wait(&mbar[wg], phase, kWaitIters)) {
+        atomicOr(a.err, ERR_TIMEOUT);
+        s_abort[wg] = 1;
+      }
+    }
+    wg_bar(wg);
+    const bool ok = !s_abort[wg];
+    if (ok) tc::mbar_wait(&mbar[wg], phase, 1 << 20);  // observe the completed phase in every thread
+    phase ^= 1u;
+    tc::fence_after();
+    return ok;
+  };
+
+  for (int64_t tile = (int64_t)blockIdx.x * 2 + wg; tile < ntiles; tile += (int64_t)gridDim.x * 2) {
+    const int64_t v0 = a.v_begin + tile * TE;
+    const int64_t nrem = n_virtual - tile * TE;
+    const int nE = (int)(nrem < TE ? nrem : TE);
+    const int i = 3 * w + jj;
+    const bool valid = lane < 27 && i < nE;
+    const int64_t v = v0 + (valid ? i : 0);
+    const int64_t e = v / a.S;
+    Star st;
+    star_setup(lane, valid, reinterpret_cast<const float*>(a.par) + e * PAR, st);
+
+    // ---- D^0 = Q row: I = dt Q, A = Q
+    float* Qrow = reinterpret_cast<float*>(a.Q) + (v * 9 + p) * B;
+    float q[B], I[B];
+#pragma unroll
+    for (int c = 0; c < B / 4; ++c) {
+      float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (valid) x = *reinterpret_cast<const float4*>(Qrow + 4 * c);
+      q[4 * c] = x.x; q[4 * c + 1] = x.y; q[4 * c + 2] = x.z; q[4 * c + 3] = x.w;
+    }
+#pragma unroll
+    for (int m = 0; m < B; ++m) I[m] = tc0 * q[m];
+#pragma unroll
+    for (int c = 0; c < kK0 / 8; ++c) st_split8(trow + cAh + 8 * c, trow + cAl + 8 * c, q + 8 * c);
+
+    // ---- level 0: Y = D^0 KT^T (N = 3 x 40)
+    if (!round([&] {
+          issue(tbase + cAcc, tbase + cAh, tbase + cAl, sbase + 4 * LImg::oP0, sbase + 4 * (LImg::oP0 + LImg::sP0), kN0,
+                kK0, false);
+        }))
+      break;
+    level_epilogue<kM0, kM0p, true>(trow + cAcc, trow + cAh, trow + cAl, st, tc1, I, nullptr);
+    // ---- level 1
+    if (!round([&] {
+          issue(tbase + cAcc, tbase + cAh, tbase + cAl, sbase + 4 * LImg::oP1, sbase + 4 * (LImg::oP1 + LImg::sP1), kN1,
+                kK1, false);
+        }))
+      break;
+    level_epilogue<kM1, kM1p, true>(trow + cAcc, trow + cAh, trow + cAl, st, tc2, I, nullptr);
+    // ---- level 2 (D^3 to registers)
+    if (!round([&] {
+          issue(tbase + cAcc, tbase + cAh, tbase + cAl, sbase + 4 * LImg::oP2, sbase + 4 * (LImg::oP2 + LImg::sP2), kN2,
+                kK2, false);
+        }))
+      break;
+    float d3[kM2];
+    level_epilogue<kM2, kM2p, false>(trow + cAcc, trow + cAh, trow + cAl, st, tc3, I, d3);
+    // ---- levels 3 and 4 on the CUDA cores
+    float d4[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      float y0 = 0.f, y1 = 0.f, y2 = 0.f;
+#pragma unroll
+      for (int l = 0; l < kM2; ++l) {
+        y0 += k3[(0 * 4 + m) * 10 + l] * d3[l];
+        y1 += k3[(1 * 4 + m) * 10 + l] * d3[l];
+        y2 += k3[(2 * 4 + m) * 10 + l] * d3[l];
+      }
+      d4[m] = star_apply(st, y0, y1, y2);
+      I[m] += tc4 * d4[m];
+    }
+    {
+      float y0 = 0.f, y1 = 0.f, y2 = 0.f;
+#pragma unroll
+      for (int l = 0; l < 4; ++l) {
+        y0 += k4[0 * 4 + l] * d4[l];
+        y1 += k4[1 * 4 + l] * d4[l];
+        y2 += k4[2 * 4 + l] * d4[l];
+      }
+      I[0] += tc5 * star_apply(st, y0, y1, y2);
+    }
+
+    // ---- face traces: T = I E^T (N = 4 x 21)
+#pragma unroll
+    for (int c = 0; c < kK0 / 8; ++c) st_split8(trow + cAh + 8 * c, trow + cAl + 8 * c, I + 8 * c);
+    if (!round([&] {
+          issue(tbase + cAcc, tbase + cAh, tbase + cAl, sbase + 4 * LImg::oT, sbase + 4 * (LImg::oT + LImg::sT), kNT,
+                kK0, false);
+        }))
+      break;
+    {
+      float* tr = reinterpret_cast<float*>(a.trace) + v * 36 * BF + p * BF;
+#pragma unroll
+      for (int c = 0; c < 11; ++c) {
+        float x[8];
+        ld8(trow + cAcc + 8 * c, x);
+        if (valid) {
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int col = 8 * c + j;
+            if (col < 4 * BF) tr[(col / BF) * 9 * BF + col % BF] = x[j];
+          }
+        }
+      }
+    }
+
+    // ---- volume: Z_a = A*_a I (l < 35); axes 0 and 1 at A columns [0, 160), then axis 2
+    float z2[kM0];
+    {
+      const float w00 = -st.g[0] * st.c[0], w01 = -st.g[1] * st.c[1], w02 = -st.g[2] * st.c[2];
+      const float w10 = -st.g[3] * st.c[0], w11 = -st.g[4] * st.c[1], w12 = -st.g[5] * st.c[2];
+      const float w20 = -st.g[6] * st.c[0], w21 = -st.g[7] * st.c[1], w22 = -st.g[8] * st.c[2];
+#pragma unroll
+      for (int lc = 0; lc < 5; ++lc) {
+        float z0[8], z1[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int l = 8 * lc + j;
+          if (l < kM0) {
+            const float s0 = __shfl_sync(0xffffffffu, I[l], st.src[0]);
+            const float s1 = __shfl_sync(0xffffffffu, I[l], st.src[1]);
+            const float s2 = __shfl_sync(0xffffffffu, I[l], st.src[2]);
+            z0[j] = w00 * s0 + w01 * s1 + w02 * s2;
+            z1[j] = w10 * s0 + w11 * s1 + w12 * s2;
+            z2[l] = w20 * s0 + w21 * s1 + w22 * s2;
+          } else {
+            z0[j] = 0.f;
+            z1[j] = 0.f;
+          }
+        }
+        st_split8(trow + 8 * lc, trow + 40 + 8 * lc, z0);
+        st_split8(trow + 80 + 8 * lc, trow + 120 + 8 * lc, z1);
+      }
+    }
+    constexpr uint32_t cV = 192;  // volume accumulator columns [192, 256)
+    if (!round([&] {
+          issue(tbase + cV, tbase + 0, tbase + 40, sbase + 4 * LImg::oV, sbase + 4 * (LImg::oV + LImg::sV), kNV, 40,
+                false);
+          issue(tbase + cV, tbase + 80, tbase + 120, sbase + 4 * (LImg::oV + 2 * LImg::sV),
+                sbase + 4 * (LImg::oV + 3 * LImg::sV), kNV, 40, true);
+        }))
+      break;
+#pragma unroll
+    for (int lc = 0; lc < 5; ++lc) {
+      float z[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) z[j] = (8 * lc + j < kM0) ? z2[8 * lc + j] : 0.f;
+      st_split8(trow + 8 * lc, trow + 40 + 8 * lc, z);
+    }
+    if (!round([&] {
+          issue(tbase + cV, tbase + 0, tbase + 40, sbase + 4 * (LImg::oV + 4 * LImg::sV),
+                sbase + 4 * (LImg::oV + 5 * LImg::sV), kNV, 40, true);
+        }))
+      break;
+    // ---- Q += volume term (face terms follow in the neighbour kernel)
+#pragma unroll
+    for (int c = 0; c < B / 8; ++c) {
+      float x[8];
+      ld8(trow + cV + 8 * c, x);
+      if (valid) {
+        float4* dst = reinterpret_cast<float4*>(Qrow + 8 * c);
+        dst[0] = make_float4(q[8 * c] + x[0], q[8 * c + 1] + x[1], q[8 * c + 2] + x[2], q[8 * c + 3] + x[3]);
+        dst[1] = make_float4(q[8 * c + 4] + x[4], q[8 * c + 5] + x[5], q[8 * c + 6] + x[6], q[8 * c + 7] + x[7]);
+      }
+    }
+    // the next tile's first MMA overwrites these columns only after the
+    // barrier at the start of its round
+    tc::fence_before();
+  }
+  // after a timed-out wait, give this warpgroup's MMAs in flight a bounded
+  // chance to finish before the columns are freed
+  if (t == 0 && s_abort[wg]) tc::mbar_wait(&mbar[wg], phase ^ 1u, kWaitIters);
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  if (tid < 32) tc::tmem_dealloc<512>(tmem_base);
+}
+
+}  // namespace
+
+int launch_local_tc(const StepArgs& a, int64_t n_virtual, int n_sms, void* stream) {
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t ce = cudaFuncSetAttribute(local_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, LImg::bytes);
+    if (ce != cudaSuccess) return (int)ce;
+    configured = true;
+  }
+  if (n_virtual <= 0) return 0;
+  const int64_t ntiles = (n_virtual + TE - 1) / TE;
+  const int64_t want = (ntiles + 1) / 2;
+  const unsigned grid = (unsigned)(want < n_sms ? want : n_sms);
+  local_tc_kernel<<<grid, kThreadsL, LImg::bytes, (cudaStream_t)stream>>>(a, n_virtual);
+  return (int)cudaGetLastError();
+}
+
+// Host-side image of the operands: kt[a][m][l], kvol[a][m][l] (l < 35) and
+// efc[f][n][l] of the degree-5 basis, split into tf32 hi / lo and laid out as
+// the canonical K-major B operands of local_tc_kernel.
+void pack_local_tc(const double* kt, const double* kvol, const double* efc, float* out) {
+  for (int i = 0; i < LImg::floats; ++i) out[i] = 0.f;
+  auto put = [&](int off, int size, int R, int n, int k, double x) {
+    const float xf = (float)x;
+    const float hi = tc::tf32_trunc(xf);
+    const int o = tc::canon(n, k, R);
+    out[off + o] = hi;
+    out[off + size + o] = xf - hi;
+  };
+  const int Mk[3] = {kM0, kM1, kM2}, Mp[3] = {kM0p, kM1p, kM2p}, Kk[3] = {B, B1, 20};
+  const int offk[3] = {LImg::oP0, LImg::oP1, LImg::oP2}, sizek[3] = {LImg::sP0, LImg::sP1, LImg::sP2};
+  const int Nk[3] = {kN0, kN1, kN2};
+  for (int lev = 0; lev < 3; ++lev)
+    for (int ax = 0; ax < 3; ++ax)
+      for (int m = 0; m < Mk[lev]; ++m)
+        for (int l = 0; l < Kk[lev]; ++l)
+          put(offk[lev], sizek[lev], Nk[lev], ax * Mp[lev] + m, l, kt[((size_t)ax * B + m) * B + l]);
+  for (int ax = 0; ax < 3; ++ax)
+    for (int m = 0; m < B; ++m)
+      for (int l = 0; l < B1; ++l)
+        put(LImg::oV + 2 * ax * LImg::sV, LImg::sV, kNV, m, l, kvol[((size_t)ax * B + m) * B1 + l]);
+  for (int f = 0; f < 4; ++f)
+    for (int n = 0; n < BF; ++n)
+      for (int l = 0; l < B; ++l) put(LImg::oT, LImg::sT, kNT, f * BF + n, l, efc[((size_t)f * BF + n) * B + l]);
+  for (int ax = 0; ax < 3; ++ax)
+    for (int m = 0; m < 4; ++m)
+      for (int l = 0; l < 10; ++l) out[LImg::oK3 + (ax * 4 + m) * 10 + l] = (float)kt[((size_t)ax * B + m) * B + l];
+  for (int ax = 0; ax < 3; ++ax)
+    for (int l = 0; l < 4; ++l) out[LImg::oK4 + ax * 4 + l] = (float)kt[((size_t)ax * B + 0) * B + l];
+}
+
+int local_tc_floats() { return LImg::floats; }
+
+}  // namespace adg

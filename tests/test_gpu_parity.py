@@ -86,6 +86,50 @@ def test_lts_coupled_graded_3xtf32():
     assert rel_l2(to_oracle_layout(s.get_dofs()), o.Q) <= 2e-5
 
 
+def test_periodic_cube_tensor_core_local_kernel():
+    """Every element of a periodic cube takes the tensor-core local kernel
+    (no gravitational, fault or LTS-boundary faces); 384 elements = 32 tiles
+    of 12, ragged against the 2 x 152 tiles in flight."""
+    m, mat = syn.unit_cube_periodic(4), syn.materials.elastic_uniform(384)
+    o, s = make_pair(m, mat, 5, precision=2, cfl=0.5)
+    from paper_2107_06640_gb300 import _lib
+    Q0 = random_dofs((m.nt, s.B, 9), 5, N=5)
+    o.Q = Q0.copy()
+    s.set_dofs(to_gpu_layout(Q0))
+    for _ in range(3):
+        o.step_gts()
+    s.advance(3)
+    assert rel_l2(to_oracle_layout(s.get_dofs()), o.Q) <= 2e-5
+    _, launches = _lib.adg_profile(s.ctx, 1)
+    assert launches[0] == 1  # one tensor-core launch, no CUDA-core remainder
+
+
+def test_coupled_box_uses_both_local_kernels_3xtf32():
+    m, mat = small_coupled()
+    from paper_2107_06640_gb300 import _lib
+    s = make_pair(m, mat, 5, precision=2, cfl=0.5)[1]
+    _, launches = _lib.adg_profile(s.ctx, 1)
+    assert launches[0] == 2  # tensor cores for the interior, CUDA cores for the gravity-face layer
+
+
+def test_ensemble_equals_independent_runs_3xtf32():
+    m, mat = small_coupled(nxy=2)
+    S = 5
+    from paper_2107_06640_gb300 import ADG_3XTF32, Solver
+    rho, lam, mu = mat
+    kw = dict(degree=5, cfl=0.5, precision=ADG_3XTF32)
+    ens = Solver(m.xyz, m.tets, m.face_tag, rho, lam, mu, ensemble=S, **kw)
+    Qs = np.stack([to_gpu_layout(random_dofs((m.nt, ens.B, 9), 20 + k, N=5)) for k in range(S)], axis=1)
+    ens.set_dofs(Qs.astype(np.float32))
+    ens.advance(2)
+    out = ens.get_dofs()
+    for k in range(S):
+        one = Solver(m.xyz, m.tets, m.face_tag, rho, lam, mu, **kw)
+        one.set_dofs(Qs[:, k].astype(np.float32))
+        one.advance(2)
+        assert np.array_equal(one.get_dofs(), out[:, k])
+
+
 def test_free_surface_and_rigid_wall_fp64():
     m, mat = small_coupled(rigid_bottom=True)
     m.face_tag[m.face_tag == syn.TAG_GRAVITY] = syn.TAG_FREE
