@@ -590,6 +590,9 @@ void Ctx::setup() {
     std::vector<float> tl(local_tc_floats());
     pack_local_tc(ops.kt.data(), ops.kvol.data(), ops.efc.data(), tl.data());
     dTcLocal = upload_raw<float>(tl, owned, dev_bytes);
+    std::vector<float> tf(lift_tc_floats());
+    pack_lift_tc(ops.lift.data(), tf.data());
+    dTcLift = upload_raw<float>(tf, owned, dev_bytes);
   }
   dErr = (unsigned int*)dalloc(sizeof(unsigned int), owned, dev_bytes);
   if (nff) {
@@ -607,6 +610,7 @@ void Ctx::setup() {
   StepArgs a0 = base_args();
   int rc = launch_local(fp64, N, a0, 0, stream);
   if (!rc && tc) rc = launch_local_tc(a0, 0, n_sms, stream);
+  if (!rc && tc) rc = launch_neighbour_tc(a0, 0, n_sms, stream);
   if (rc) throw Err(ADG_E_CUDA, std::string("kernel configuration: ") + cudaGetErrorString((cudaError_t)rc));
   tick = 0;
   time = 0.0;
@@ -620,7 +624,7 @@ StepArgs Ctx::base_args() const {
   a.gslot = dGslot; a.bslot = dBslot; a.dslot = dDslot;
   a.ktT = dKt; a.kvolT = dKvol; a.efcT = dEfc; a.liftT = dLift; a.perm = dPerm; a.gpar = dGpar;
   a.S = S; a.err = dErr;
-  a.fslot = dFslot; a.drout = dDrout; a.gflux = dGflux; a.tc_local = dTcLocal;
+  a.fslot = dFslot; a.drout = dDrout; a.gflux = dGflux; a.tc_local = dTcLocal; a.tc_lift = dTcLift;
   return a;
 }
 
@@ -683,7 +687,16 @@ void Ctx::launch_tick(int s, double dtm) {
       CK(cudaEventCreate(&ev.b));
       CK(cudaEventRecord(ev.a, stream));
     }
-    int rc = launch_neighbour(fp64, N, a, n * S, stream);
+    int rc = 0;
+    if (tc) {
+      const int64_t np = cl_plain[c];
+      ev.launches = (np > 0) + (n > np);
+      if (np > 0) rc = launch_neighbour_tc(a, np * S, n_sms, stream);
+      a.v_begin = (cl_begin[c] + np) * S;
+      if (!rc && n > np) rc = launch_neighbour(fp64, N, a, (n - np) * S, stream);
+    } else {
+      rc = launch_neighbour(fp64, N, a, n * S, stream);
+    }
     if (prof) { CK(cudaEventRecord(ev.b, stream)); prof->push_back(ev); }
     if (rc) throw Err(ADG_E_CUDA, std::string("neighbour kernel: ") + cudaGetErrorString((cudaError_t)rc));
   }
@@ -729,7 +742,11 @@ int64_t Ctx::launches_per_macro() const {
         const int64_t n = cl_begin[c + 1] - cl_begin[c];
         L += tc ? (cl_plain[c] > 0) + (n > cl_plain[c]) : 1;
       }
-      if ((s + 1) % (1 << c) == 0) L += (fcl_begin[c + 1] > fcl_begin[c]) ? 2 : 1;
+      if ((s + 1) % (1 << c) == 0) {
+        const int64_t n = cl_begin[c + 1] - cl_begin[c];
+        L += (fcl_begin[c + 1] > fcl_begin[c]) ? 1 : 0;
+        L += tc ? (cl_plain[c] > 0) + (n > cl_plain[c]) : 1;
+      }
     }
   return L;
 }

@@ -46,6 +46,7 @@ struct Ctx {
   bool tc = false;          // tensor-core (3xTF32) local kernel in use
   int n_sms = 1;
   float* dTcLocal = nullptr;
+  float* dTcLift = nullptr;
   RefOps ops;
   int ncl = 1;
   std::vector<int64_t> order, inv, cl_begin;

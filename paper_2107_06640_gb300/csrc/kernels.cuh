@@ -63,6 +63,7 @@ struct StepArgs {
   const void* drout;    // T [nff*S][2][9][Bf] time-integrated fault flux per side
   void* gflux;          // T [ngslot*S][9][Bf] time-integrated flux of gravitational faces
   const float* tc_local; // tensor-core operands of the local kernel (hi/lo, canonical layout), degree 5
+  const float* tc_lift;  // tensor-core lift operand of the neighbour kernel (hi/lo, canonical layout), degree 5
 };
 
 // tensor-core (tcgen05, 3xTF32) local kernel, degree 5, FP32 dofs (local_tc.cu),
@@ -70,6 +71,11 @@ struct StepArgs {
 int launch_local_tc(const StepArgs& a, int64_t n_virtual, int n_sms, void* stream);
 void pack_local_tc(const double* kt, const double* kvol, const double* efc, float* out);
 int local_tc_floats();
+// tensor-core (tcgen05, 3xTF32) neighbour kernel, degree 5, FP32 dofs
+// (neighbour_tc.cu), for the same elements
+int launch_neighbour_tc(const StepArgs& a, int64_t n_virtual, int n_sms, void* stream);
+void pack_lift_tc(const double* lift, float* out);
+int lift_tc_floats();
 
 // ---- dynamic rupture (rupture.cu) ----
 // per-node fault parameters (double, stride FPAR), in this order:

@@ -1,0 +1,332 @@
+// Neighbour kernel on the tensor cores (tcgen05, 3xTF32), degree 5, FP32
+// dofs: face fluxes of Sec. 4.2 (Eq. numerical-flux) and their lift for
+// elements whose faces are all interior faces inside their LTS cluster,
+// periodic faces or linear boundaries (the others take the CUDA-core kernel).
+//
+// Same tile as the local tensor-core kernel: 12 (virtual) elements x 9
+// quantities = 128 TMEM lanes (warp w: elements 3w..3w+2, lane 9j+p = element
+// 3w+j, quantity p; lanes 27..31 zero).  Per tile and face f, the own and the
+// neighbours' time-integrated traces are staged in shared memory as rows of
+// the 9 quantities of one face node (padded to 12 floats, read as float4);
+// the thread of row (element, p) forms
+//   G[p][n] = s_f (sum_q F-[p][q] V_own[q][n] + sum_q F+[p][q] V_nbr[q][n])
+// for the 21 nodes n (s_f = 2|S_f|/|J|) and writes it, split into tf32 hi + lo,
+// to TMEM columns 24 f + n.  One MMA chain then lifts all four faces:
+//   Q[(element, p)][m] -= sum_{f,n} G[p][24 f + n] lift_f[m][n],
+// A = G in TMEM (K = 96), B = the lift matrices resident in shared memory.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "kernels.cuh"
+#include "tc_common.cuh"
+
+namespace adg {
+
+namespace {
+
+constexpr int B = 56, BF = 21;
+constexpr int TE = 12;
+constexpr int kThreadsN = 256;  // two warpgroups, one tile each
+constexpr int kWaitIters = 1 << 24;
+constexpr int kK = 96;          // 4 faces x 24 columns (21 nodes + 3 zero)
+constexpr int kN = 64;          // 56 basis functions, padded
+constexpr int kRow = 12;        // staged floats per face node (9 quantities + 3 zero)
+constexpr int kStage = TE * BF * kRow;  // floats per staged face array
+
+struct NImg {
+  static constexpr int oL = 0, sL = kN * kK;                  // lift hi, lo
+  static constexpr int oPerm = oL + 2 * sL;                   // 6 x 21 ints
+  static constexpr int oMeta = oPerm + 128;                   // per warpgroup: [face][element] int64 + int
+  static constexpr int sMeta = 4 * TE * 3;
+  static constexpr int oStage = oMeta + 2 * sMeta;            // per warpgroup: 2 buffers x (own, nbr)
+  static constexpr int floats = oStage + 2 * 4 * kStage;
+  static constexpr int bytes = floats * 4;
+};
+
+// per-warpgroup TMEM columns: G hi [0, 96), G lo [96, 192), accumulator [192, 256)
+constexpr uint32_t cGh = 0, cGl = 96, cAcc = 192;
+
+__device__ __forceinline__ void mma_ts(uint32_t d, uint32_t a, uint64_t db, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d),
+      "r"(a), "l"(db), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void ld8(uint32_t t, float o[8]) {
+  uint32_t r[8];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+      "tcgen05.wait::ld.sync.aligned;\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+      : "r"(t));
+#pragma unroll
+  for (int j = 0; j < 8; ++j) o[j] = __uint_as_float(r[j]);
+}
+
+__device__ __forceinline__ void st_split8(uint32_t th, uint32_t tl, const float x[8]) {
+  uint32_t h[8], l[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const float hh = tc::tf32_trunc(x[j]);
+    h[j] = __float_as_uint(hh);
+    l[j] = __float_as_uint(x[j] - hh);
+  }
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(th), "r"(h[0]),
+               "r"(h[1]), "r"(h[2]), "r"(h[3]), "r"(h[4]), "r"(h[5]), "r"(h[6]), "r"(h[7]));
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(tl), "r"(l[0]),
+               "r"(l[1]), "r"(l[2]), "r"(l[3]), "r"(l[4]), "r"(l[5]), "r"(l[6]), "r"(l[7]));
+}
+
+__device__ __forceinline__ void wg_bar(int wg) { asm volatile("bar.sync %0, 128;" ::"r"(wg + 1)); }
+
+// asynchronous 4-byte copy global -> shared; zero fill when !valid
+__device__ __forceinline__ void cp4(float* dst, const float* src, bool valid) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(tc::smem_u32(dst)), "l"(src),
+               "r"(valid ? 4 : 0));
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;"); }
+template <int NPEND>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(NPEND)); }
+
+// Stage face f of a tile: own traces and the neighbours' traces (through the
+// node permutation) as [element][node][quantity (12)] rows.
+__device__ __forceinline__ void stage_face(int f, int t, int64_t v0, int nE, const float* trace,
+                                           const long long* nbase, const int* npm, const int* sPerm, float* so,
+                                           float* sn) {
+#pragma unroll
+  for (int it = 0; it < (TE * 9 * BF + 127) / 128; ++it) {
+    const int r = t + 128 * it;
+    if (r < TE * 9 * BF) {
+      const int ei = r / (9 * BF), rem = r - ei * (9 * BF);
+      const int qq = rem / BF, n = rem - qq * BF;
+      const bool ok = ei < nE;
+      const float* src_o = trace + ((v0 + (ok ? ei : 0)) * 4 + f) * 9 * BF + rem;
+      const long long nb = nbase[f * TE + ei];
+      const bool okn = ok && nb >= 0;
+      const float* src_n = trace + (okn ? nb + qq * BF + sPerm[npm[f * TE + ei] * BF + n] : 0);
+      cp4(so + (ei * BF + n) * kRow + qq, src_o, ok);
+      cp4(sn + (ei * BF + n) * kRow + qq, src_n, okn);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, int64_t n_virtual) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  float* sm = reinterpret_cast<float*>(smem_raw);
+  int* sPerm = reinterpret_cast<int*>(sm + NImg::oPerm);
+  __shared__ uint32_t tmem_base;
+  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ int s_abort[2];
+
+  const int tid = threadIdx.x, wg = tid >> 7, t = tid & 127, w = t >> 5, lane = tid & 31;
+  {
+    const float4* src = reinterpret_cast<const float4*>(a.tc_lift);
+    float4* dst = reinterpret_cast<float4*>(sm + NImg::oL);
+    for (int r = tid; r < 2 * NImg::sL / 4; r += kThreadsN) dst[r] = src[r];
+    for (int r = tid; r < 6 * BF; r += kThreadsN) sPerm[r] = a.perm[r];
+  }
+  if (tid < 2) {
+    tc::mbar_init(&mbar[tid], 1);
+    s_abort[tid] = 0;
+  }
+  if (tid < 32) tc::tmem_alloc<512>(&tmem_base);
+  tc::fence_async_smem();
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+
+  const uint32_t tbase = tmem_base + (uint32_t)wg * 256u;
+  const uint32_t trow = tbase + ((uint32_t)(32 * w) << 16);
+  const uint32_t sL = tc::smem_u32(sm + NImg::oL);
+  float* sStage = sm + NImg::oStage + wg * 4 * kStage;  // buffer b: own at 2b, nbr at 2b + 1
+  long long* sNb = reinterpret_cast<long long*>(sm + NImg::oMeta + wg * NImg::sMeta);
+  int* sPm = reinterpret_cast<int*>(sNb + 4 * TE);
+  const float* trace = reinterpret_cast<const float*>(a.trace);
+  const int jj = lane / 9, p = lane - 9 * (lane / 9);
+  const int64_t ntiles = (n_virtual + TE - 1) / TE;
+  uint32_t phase = 0;
+  bool bad = false;
+
+  for (int64_t tile = (int64_t)blockIdx.x * 2 + wg; tile < ntiles; tile += (int64_t)gridDim.x * 2) {
+    const int64_t v0 = a.v_begin + tile * TE;
+    const int64_t nrem = n_virtual - tile * TE;
+    const int nE = (int)(nrem < TE ? nrem : TE);
+    const int i = 3 * w + jj;
+    const bool valid = lane < 27 && i < nE;
+    const int64_t v = v0 + (valid ? i : 0);
+    const int64_t e = v / a.S;
+    // the dofs row is needed only at the end: load it first
+    float* Qrow = reinterpret_cast<float*>(a.Q) + (v * 9 + p) * B;
+    float q[B];
+#pragma unroll
+    for (int c = 0; c < B / 4; ++c) {
+      float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (valid) x = *reinterpret_cast<const float4*>(Qrow + 4 * c);
+      q[4 * c] = x.x; q[4 * c + 1] = x.y; q[4 * c + 2] = x.z; q[4 * c + 3] = x.w;
+    }
+    // ---- neighbour trace blocks of the tile's faces (NK_SAME; -1 for boundaries)
+    if (t < 4 * TE) {
+      const int f = t / TE, ei = t - f * TE;
+      long long nb = -1;
+      int pm = 0;
+      if (ei < nE) {
+        const int64_t ve = v0 + ei, ee = ve / a.S;
+        const int info = a.ninfo[ee * 4 + f];
+        if (((info >> 5) & 7) == NK_SAME) {
+          const int64_t vn_e = (int64_t)a.nbr[ee * 4 + f] * a.S + (ve - ee * a.S);
+          nb = (vn_e * 4 + (info & 3)) * 9 * BF;
+          pm = (info >> 2) & 7;
+        }
+      }
+      sNb[t] = nb;
+      sPm[t] = pm;
+    }
+    wg_bar(wg);
+    stage_face(0, t, v0, nE, trace, sNb, sPm, sPerm, sStage, sStage + kStage);
+    cp_commit();
+#pragma unroll 1
+    for (int f = 0; f < 4; ++f) {
+      // ---- stage face f + 1 while face f is used
+      if (f < 3) {
+        float* nb_buf = sStage + ((f + 1) & 1) * 2 * kStage;
+        stage_face(f + 1, t, v0, nE, trace, sNb, sPm, sPerm, nb_buf, nb_buf + kStage);
+        cp_commit();
+        cp_wait<1>();
+      } else {
+        cp_wait<0>();
+      }
+      wg_bar(wg);
+      const float* sVo = sStage + (f & 1) * 2 * kStage;
+      const float* sVn = sVo + kStage;
+      // ---- this row's scaled flux at the 21 nodes of face f
+      float fm[9], fp[9], sc = 0.f;
+      if (valid) {
+        const float* Fm = reinterpret_cast<const float*>(a.Fm) + (e * 4 + f) * 81 + p * 9;
+        const float* Fp = reinterpret_cast<const float*>(a.Fp) + (e * 4 + f) * 81 + p * 9;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+          fm[k] = Fm[k];
+          fp[k] = Fp[k];
+        }
+        sc = reinterpret_cast<const float*>(a.par)[e * PAR + 12 + f];
+      } else {
+#pragma unroll
+        for (int k = 0; k < 9; ++k) fm[k] = fp[k] = 0.f;
+      }
+      const float* vo_row = sVo + (i < TE ? i : 0) * BF * kRow;
+      const float* vn_row = sVn + (i < TE ? i : 0) * BF * kRow;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        float g[8];
+#pragma unroll
+        for (int jn = 0; jn < 8; ++jn) {
+          const int n = 8 * c + jn;
+          if (n < BF) {
+            const float4* o4 = reinterpret_cast<const float4*>(vo_row + n * kRow);
+            const float4* n4 = reinterpret_cast<const float4*>(vn_row + n * kRow);
+            const float4 o0 = o4[0], o1 = o4[1], o2 = o4[2];
+            const float4 n0 = n4[0], n1 = n4[1], n2 = n4[2];
+            float acc = fm[0] * o0.x + fm[1] * o0.y + fm[2] * o0.z + fm[3] * o0.w + fm[4] * o1.x + fm[5] * o1.y +
+                        fm[6] * o1.z + fm[7] * o1.w + fm[8] * o2.x;
+            acc += fp[0] * n0.x + fp[1] * n0.y + fp[2] * n0.z + fp[3] * n0.w + fp[4] * n1.x + fp[5] * n1.y +
+                   fp[6] * n1.z + fp[7] * n1.w + fp[8] * n2.x;
+            g[jn] = valid ? sc * acc : 0.f;
+          } else {
+            g[jn] = 0.f;
+          }
+        }
+        st_split8(trow + cGh + 24 * f + 8 * c, trow + cGl + 24 * f + 8 * c, g);
+      }
+      wg_bar(wg);  // the staging buffers are refilled for the next face
+    }
+    // ---- lift on the tensor cores
+    asm volatile("tcgen05.wait::st.sync.aligned;");
+    tc::fence_before();
+    wg_bar(wg);
+    tc::fence_after();
+    if (t == 0) {
+      const uint32_t idesc = tc::idesc_tf32(128, kN);
+      constexpr uint32_t lbo = (kN / 8) * 128;
+      for (int kk = 0; kk < kK / 8; ++kk) {
+        const uint32_t off = kk * 2 * lbo;
+        const uint64_t dbh = tc::sdesc(sL + off, lbo, 128), dbl = tc::sdesc(sL + 4 * NImg::sL + off, lbo, 128);
+        mma_ts(tbase + cAcc, tbase + cGh + 8 * kk, dbh, idesc, kk > 0 ? 1u : 0u);
+        mma_ts(tbase + cAcc, tbase + cGh + 8 * kk, dbl, idesc, 1u);
+        mma_ts(tbase + cAcc, tbase + cGl + 8 * kk, dbh, idesc, 1u);
+      }
+      tc::commit(&mbar[wg]);
+      if (!tc::mbar_wait(&mbar[wg], phase, kWaitIters)) {
+        atomicOr(a.err, ERR_TIMEOUT);
+        s_abort[wg] = 1;
+      }
+    }
+    wg_bar(wg);
+    if (s_abort[wg]) break;
+    tc::mbar_wait(&mbar[wg], phase, 1 << 20);
+    phase ^= 1u;
+    tc::fence_after();
+    // ---- Q -= lift
+#pragma unroll
+    for (int c = 0; c < B / 8; ++c) {
+      float x[8];
+      ld8(trow + cAcc + 8 * c, x);
+      if (valid) {
+        float nq[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          nq[j] = q[8 * c + j] - x[j];
+          bad |= !isfinite(nq[j]);
+        }
+        float4* dst = reinterpret_cast<float4*>(Qrow + 8 * c);
+        dst[0] = make_float4(nq[0], nq[1], nq[2], nq[3]);
+        dst[1] = make_float4(nq[4], nq[5], nq[6], nq[7]);
+      }
+    }
+    tc::fence_before();
+  }
+  if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(a.err, ERR_NAN);
+  if (t == 0 && s_abort[wg]) tc::mbar_wait(&mbar[wg], phase ^ 1u, kWaitIters);
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  if (tid < 32) tc::tmem_dealloc<512>(tmem_base);
+}
+
+}  // namespace
+
+int launch_neighbour_tc(const StepArgs& a, int64_t n_virtual, int n_sms, void* stream) {
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t ce =
+        cudaFuncSetAttribute(neighbour_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, NImg::bytes);
+    if (ce != cudaSuccess) return (int)ce;
+    configured = true;
+  }
+  if (n_virtual <= 0) return 0;
+  const int64_t ntiles = (n_virtual + TE - 1) / TE;
+  const int64_t want = (ntiles + 1) / 2;
+  const unsigned grid = (unsigned)(want < n_sms ? want : n_sms);
+  neighbour_tc_kernel<<<grid, kThreadsN, NImg::bytes, (cudaStream_t)stream>>>(a, n_virtual);
+  return (int)cudaGetLastError();
+}
+
+// Host-side B operand of the lift: lift[f][m][n] of the degree-5 basis at
+// row m, column 24 f + n, split into tf32 hi / lo, canonical K-major layout.
+void pack_lift_tc(const double* lift, float* out) {
+  for (int i = 0; i < 2 * NImg::sL; ++i) out[i] = 0.f;
+  for (int f = 0; f < 4; ++f)
+    for (int m = 0; m < B; ++m)
+      for (int n = 0; n < BF; ++n) {
+        const float xf = (float)lift[((size_t)f * B + m) * BF + n];
+        const float hi = tc::tf32_trunc(xf);
+        const int o = tc::canon(m, 24 * f + n, kN);
+        out[o] = hi;
+        out[NImg::sL + o] = xf - hi;
+      }
+}
+
+int lift_tc_floats() { return 2 * NImg::sL; }
+
+}  // namespace adg

@@ -101,15 +101,16 @@ def test_periodic_cube_tensor_core_local_kernel():
     s.advance(3)
     assert rel_l2(to_oracle_layout(s.get_dofs()), o.Q) <= 2e-5
     _, launches = _lib.adg_profile(s.ctx, 1)
-    assert launches[0] == 1  # one tensor-core launch, no CUDA-core remainder
+    assert launches[0] == 1 and launches[1] == 1  # tensor-core launches only, no CUDA-core remainder
 
 
-def test_coupled_box_uses_both_local_kernels_3xtf32():
+def test_coupled_box_uses_both_kernel_forms_3xtf32():
     m, mat = small_coupled()
     from paper_2107_06640_gb300 import _lib
     s = make_pair(m, mat, 5, precision=2, cfl=0.5)[1]
     _, launches = _lib.adg_profile(s.ctx, 1)
-    assert launches[0] == 2  # tensor cores for the interior, CUDA cores for the gravity-face layer
+    # tensor cores for the interior, CUDA cores for the gravity-face layer
+    assert launches[0] == 2 and launches[1] == 2
 
 
 def test_ensemble_equals_independent_runs_3xtf32():
