@@ -5,15 +5,21 @@
 //
 // Same tile as the local tensor-core kernel: 12 (virtual) elements x 9
 // quantities = 128 TMEM lanes (warp w: elements 3w..3w+2, lane 9j+p = element
-// 3w+j, quantity p; lanes 27..31 zero).  Per tile and face f, the own and the
-// neighbours' time-integrated traces are staged in shared memory as rows of
-// the 9 quantities of one face node (padded to 12 floats, read as float4);
-// the thread of row (element, p) forms
-//   G[p][n] = s_f (sum_q F-[p][q] V_own[q][n] + sum_q F+[p][q] V_nbr[q][n])
-// for the 21 nodes n (s_f = 2|S_f|/|J|) and writes it, split into tf32 hi + lo,
-// to TMEM columns 24 f + n.  One MMA chain then lifts all four faces:
+// 3w+j, quantity p; lanes 27..31 zero).  Per tile and face f:
+//   1. the own and the neighbours' time-integrated traces of face f are
+//      copied asynchronously (cp.async, double-buffered over the faces) into
+//      shared memory as they are stored, [element][quantity][node];
+//   2. work item (element, node triplet) forms, for its three nodes,
+//        G[p][n] = s_f (sum_q F-[p][q] V_own[q][n] + sum_q F+[p][q] V_nbr[q][perm n])
+//      (s_f = 2|S_f|/|J|, F rows broadcast from the staged F-/F+ of the tile)
+//      and writes the 9 values to a transposition buffer [element][p][24];
+//   3. the thread of row (element, p) takes its 24 columns, splits them into
+//      tf32 hi + lo and writes them to TMEM columns 24 f + n.
+// One MMA chain then lifts all four faces:
 //   Q[(element, p)][m] -= sum_{f,n} G[p][24 f + n] lift_f[m][n],
 // A = G in TMEM (K = 96), B = the lift matrices resident in shared memory.
+// The next tile's F matrices, parameters and face 0 are requested before
+// this tile's lift.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -31,8 +37,12 @@ constexpr int kThreadsN = 256;  // two warpgroups, one tile each
 constexpr int kWaitIters = 1 << 24;
 constexpr int kK = 96;          // 4 faces x 24 columns (21 nodes + 3 zero)
 constexpr int kN = 64;          // 56 basis functions, padded
-constexpr int kRow = 12;        // staged floats per face node (9 quantities + 3 zero)
-constexpr int kStage = TE * BF * kRow;  // floats per staged face array
+constexpr int kFace = 9 * BF;         // floats of one face's traces (189)
+constexpr int kStage = TE * kFace;    // floats per staged face array
+constexpr int kGrow = 24;             // transposed flux row: 21 nodes + 3 zero
+constexpr int kG = TE * 9 * kGrow;    // floats per transposition buffer
+constexpr int kTrip = 7;              // node triplets (n, n + 7, n + 14) per element face
+constexpr int kItems = TE * kTrip;    // work items per face (84 <= 128 threads)
 
 struct NImg {
   static constexpr int oL = 0, sL = kN * kK;                  // lift hi, lo
@@ -40,9 +50,15 @@ struct NImg {
   static constexpr int oMeta = oPerm + 128;                   // per warpgroup: [face][element] int64 + int
   static constexpr int sMeta = 4 * TE * 3;
   static constexpr int oStage = oMeta + 2 * sMeta;            // per warpgroup: 2 buffers x (own, nbr)
-  static constexpr int floats = oStage + 2 * 4 * kStage;
+  static constexpr int oF = oStage + 2 * 4 * kStage;          // per warpgroup: F- then F+ of the tile
+  static constexpr int sF = 2 * TE * 324;
+  static constexpr int oPar = oF + 2 * sF;                    // per warpgroup: element parameters
+  static constexpr int sPar = TE * PAR;
+  static constexpr int oG = oPar + 2 * sPar;                  // per warpgroup: 2 transposition buffers
+  static constexpr int floats = oG + 2 * 2 * kG;
   static constexpr int bytes = floats * 4;
 };
+static_assert(NImg::bytes + 64 <= 232448, "neighbour tensor-core kernel exceeds the shared memory of one CTA");
 
 // per-warpgroup TMEM columns: G hi [0, 96), G lo [96, 192), accumulator [192, 256)
 constexpr uint32_t cGh = 0, cGl = 96, cAcc = 192;
@@ -86,28 +102,29 @@ __device__ __forceinline__ void cp4(float* dst, const float* src, bool valid) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(tc::smem_u32(dst)), "l"(src),
                "r"(valid ? 4 : 0));
 }
+__device__ __forceinline__ void cp16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(tc::smem_u32(dst)), "l"(src));
+}
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;"); }
 template <int NPEND>
 __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(NPEND)); }
 
-// Stage face f of a tile: own traces and the neighbours' traces (through the
-// node permutation) as [element][node][quantity (12)] rows.
+// Stage face f of a tile: own traces and the neighbours' traces of that face,
+// both as stored ([element][quantity][node]); the neighbour's node order is
+// applied when the values are read.
 __device__ __forceinline__ void stage_face(int f, int t, int64_t v0, int nE, const float* trace,
-                                           const long long* nbase, const int* npm, const int* sPerm, float* so,
-                                           float* sn) {
+                                           const long long* nbase, float* so, float* sn) {
 #pragma unroll
-  for (int it = 0; it < (TE * 9 * BF + 127) / 128; ++it) {
+  for (int it = 0; it < (kStage + 127) / 128; ++it) {
     const int r = t + 128 * it;
-    if (r < TE * 9 * BF) {
-      const int ei = r / (9 * BF), rem = r - ei * (9 * BF);
-      const int qq = rem / BF, n = rem - qq * BF;
+    if (r < kStage) {
+      const int ei = r / kFace, rem = r - ei * kFace;
       const bool ok = ei < nE;
-      const float* src_o = trace + ((v0 + (ok ? ei : 0)) * 4 + f) * 9 * BF + rem;
+      const float* src_o = trace + ((v0 + (ok ? ei : 0)) * 4 + f) * kFace + rem;
       const long long nb = nbase[f * TE + ei];
       const bool okn = ok && nb >= 0;
-      const float* src_n = trace + (okn ? nb + qq * BF + sPerm[npm[f * TE + ei] * BF + n] : 0);
-      cp4(so + (ei * BF + n) * kRow + qq, src_o, ok);
-      cp4(sn + (ei * BF + n) * kRow + qq, src_n, okn);
+      cp4(so + r, src_o, ok);
+      cp4(sn + r, trace + (okn ? nb + rem : 0), okn);
     }
   }
 }
@@ -144,35 +161,26 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
   long long* sNb = reinterpret_cast<long long*>(sm + NImg::oMeta + wg * NImg::sMeta);
   int* sPm = reinterpret_cast<int*>(sNb + 4 * TE);
   const float* trace = reinterpret_cast<const float*>(a.trace);
+  float* sFm = sm + NImg::oF + wg * NImg::sF;  // [element - e0][face][81], F+ at + TE * 324
+  float* sPr = sm + NImg::oPar + wg * NImg::sPar;
+  float* sG = sm + NImg::oG + wg * 2 * kG;     // [buffer][element][p][24]
+  for (int r = t; r < 2 * kG; r += 128) sG[r] = 0.f;  // columns 21..23 stay zero
   const int jj = lane / 9, p = lane - 9 * (lane / 9);
   const int64_t ntiles = (n_virtual + TE - 1) / TE;
   uint32_t phase = 0;
   bool bad = false;
 
-  for (int64_t tile = (int64_t)blockIdx.x * 2 + wg; tile < ntiles; tile += (int64_t)gridDim.x * 2) {
-    const int64_t v0 = a.v_begin + tile * TE;
-    const int64_t nrem = n_virtual - tile * TE;
-    const int nE = (int)(nrem < TE ? nrem : TE);
-    const int i = 3 * w + jj;
-    const bool valid = lane < 27 && i < nE;
-    const int64_t v = v0 + (valid ? i : 0);
-    const int64_t e = v / a.S;
-    // the dofs row is needed only at the end: load it first
-    float* Qrow = reinterpret_cast<float*>(a.Q) + (v * 9 + p) * B;
-    float q[B];
-#pragma unroll
-    for (int c = 0; c < B / 4; ++c) {
-      float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (valid) x = *reinterpret_cast<const float4*>(Qrow + 4 * c);
-      q[4 * c] = x.x; q[4 * c + 1] = x.y; q[4 * c + 2] = x.z; q[4 * c + 3] = x.w;
-    }
-    // ---- neighbour trace blocks of the tile's faces (NK_SAME; -1 for boundaries)
+  // Neighbour trace blocks of a tile's faces, then one cp.async group with the
+  // tile's F-/F+ matrices, element parameters and face 0 (staging buffer 0).
+  auto prefetch = [&](int64_t tl) {
+    const int64_t pv0 = a.v_begin + tl * TE, prem = n_virtual - tl * TE;
+    const int pnE = (int)(prem < TE ? prem : TE);
     if (t < 4 * TE) {
       const int f = t / TE, ei = t - f * TE;
       long long nb = -1;
       int pm = 0;
-      if (ei < nE) {
-        const int64_t ve = v0 + ei, ee = ve / a.S;
+      if (ei < pnE) {
+        const int64_t ve = pv0 + ei, ee = ve / a.S;
         const int info = a.ninfo[ee * 4 + f];
         if (((info >> 5) & 7) == NK_SAME) {
           const int64_t vn_e = (int64_t)a.nbr[ee * 4 + f] * a.S + (ve - ee * a.S);
@@ -184,14 +192,44 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
       sPm[t] = pm;
     }
     wg_bar(wg);
-    stage_face(0, t, v0, nE, trace, sNb, sPm, sPerm, sStage, sStage + kStage);
+    const int64_t e0 = pv0 / a.S;
+    const int ne = (int)((pv0 + pnE - 1) / a.S - e0 + 1);
+    // F-, F+ rows of elements e0 .. e0 + ne - 1: ne x 1296 bytes each, 16-byte aligned
+    for (int c = t; c < 2 * ne * 81; c += 128) {
+      const int m = c / (ne * 81), cc = c - m * (ne * 81);
+      const float* src = reinterpret_cast<const float*>(m ? a.Fp : a.Fm) + e0 * 324 + 4 * cc;
+      cp16(sFm + m * TE * 324 + 4 * cc, src);
+    }
+    for (int c = t; c < ne * (PAR / 4); c += 128)
+      cp16(sPr + 4 * c, reinterpret_cast<const float*>(a.par) + e0 * PAR + 4 * c);
+    stage_face(0, t, pv0, pnE, trace, sNb, sStage, sStage + kStage);
     cp_commit();
+  };
+
+  int64_t tile = (int64_t)blockIdx.x * 2 + wg;
+  if (tile < ntiles) prefetch(tile);
+  for (; tile < ntiles; tile += (int64_t)gridDim.x * 2) {
+    const int64_t v0 = a.v_begin + tile * TE;
+    const int64_t nrem = n_virtual - tile * TE;
+    const int nE = (int)(nrem < TE ? nrem : TE);
+    const int i = 3 * w + jj;
+    const bool valid = lane < 27 && i < nE;
+    const int64_t v = v0 + (valid ? i : 0);
+    // the dofs row is needed only at the end: load it first
+    float* Qrow = reinterpret_cast<float*>(a.Q) + (v * 9 + p) * B;
+    float q[B];
+#pragma unroll
+    for (int c = 0; c < B / 4; ++c) {
+      float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (valid) x = *reinterpret_cast<const float4*>(Qrow + 4 * c);
+      q[4 * c] = x.x; q[4 * c + 1] = x.y; q[4 * c + 2] = x.z; q[4 * c + 3] = x.w;
+    }
 #pragma unroll 1
     for (int f = 0; f < 4; ++f) {
       // ---- stage face f + 1 while face f is used
       if (f < 3) {
         float* nb_buf = sStage + ((f + 1) & 1) * 2 * kStage;
-        stage_face(f + 1, t, v0, nE, trace, sNb, sPm, sPerm, nb_buf, nb_buf + kStage);
+        stage_face(f + 1, t, v0, nE, trace, sNb, nb_buf, nb_buf + kStage);
         cp_commit();
         cp_wait<1>();
       } else {
@@ -200,47 +238,65 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
       wg_bar(wg);
       const float* sVo = sStage + (f & 1) * 2 * kStage;
       const float* sVn = sVo + kStage;
-      // ---- this row's scaled flux at the 21 nodes of face f
-      float fm[9], fp[9], sc = 0.f;
-      if (valid) {
-        const float* Fm = reinterpret_cast<const float*>(a.Fm) + (e * 4 + f) * 81 + p * 9;
-        const float* Fp = reinterpret_cast<const float*>(a.Fp) + (e * 4 + f) * 81 + p * 9;
+      float* gbuf = sG + (f & 1) * kG;
+      // ---- work items (element, node triplet): scaled flux of the three nodes
+      if (t < kItems) {
+        const int ei = t / kTrip, k = t - ei * kTrip;
+        const int el = (int)((v0 + ei) / a.S - v0 / a.S);
+        const float* Fm = sFm + (el * 4 + f) * 81;
+        const float* Fp = Fm + TE * 324;
+        const float sc = ei < nE ? sPr[el * PAR + 12 + f] : 0.f;
+        const int* perm = sPerm + sPm[f * TE + ei] * BF;
+        int nd[3], pn[3];
 #pragma unroll
-        for (int k = 0; k < 9; ++k) {
-          fm[k] = Fm[k];
-          fp[k] = Fp[k];
+        for (int u = 0; u < 3; ++u) {
+          nd[u] = k + kTrip * u;
+          pn[u] = perm[nd[u]];
         }
-        sc = reinterpret_cast<const float*>(a.par)[e * PAR + 12 + f];
-      } else {
+        float vo[3][9], vn[3][9];
 #pragma unroll
-        for (int k = 0; k < 9; ++k) fm[k] = fp[k] = 0.f;
-      }
-      const float* vo_row = sVo + (i < TE ? i : 0) * BF * kRow;
-      const float* vn_row = sVn + (i < TE ? i : 0) * BF * kRow;
+        for (int qq = 0; qq < 9; ++qq) {
+          const float* o = sVo + ei * kFace + qq * BF;
+          const float* nn = sVn + ei * kFace + qq * BF;
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        float g[8];
-#pragma unroll
-        for (int jn = 0; jn < 8; ++jn) {
-          const int n = 8 * c + jn;
-          if (n < BF) {
-            const float4* o4 = reinterpret_cast<const float4*>(vo_row + n * kRow);
-            const float4* n4 = reinterpret_cast<const float4*>(vn_row + n * kRow);
-            const float4 o0 = o4[0], o1 = o4[1], o2 = o4[2];
-            const float4 n0 = n4[0], n1 = n4[1], n2 = n4[2];
-            float acc = fm[0] * o0.x + fm[1] * o0.y + fm[2] * o0.z + fm[3] * o0.w + fm[4] * o1.x + fm[5] * o1.y +
-                        fm[6] * o1.z + fm[7] * o1.w + fm[8] * o2.x;
-            acc += fp[0] * n0.x + fp[1] * n0.y + fp[2] * n0.z + fp[3] * n0.w + fp[4] * n1.x + fp[5] * n1.y +
-                   fp[6] * n1.z + fp[7] * n1.w + fp[8] * n2.x;
-            g[jn] = valid ? sc * acc : 0.f;
-          } else {
-            g[jn] = 0.f;
+          for (int u = 0; u < 3; ++u) {
+            vo[u][qq] = o[nd[u]];
+            vn[u][qq] = nn[pn[u]];
           }
         }
-        st_split8(trow + cGh + 24 * f + 8 * c, trow + cGl + 24 * f + 8 * c, g);
+        float* gout = gbuf + ei * 9 * kGrow;
+#pragma unroll
+        for (int pp = 0; pp < 9; ++pp) {
+          float g[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+          for (int qq = 0; qq < 9; ++qq) {
+            const float fm = Fm[pp * 9 + qq], fp = Fp[pp * 9 + qq];
+#pragma unroll
+            for (int u = 0; u < 3; ++u) g[u] += fm * vo[u][qq] + fp * vn[u][qq];
+          }
+#pragma unroll
+          for (int u = 0; u < 3; ++u) gout[pp * kGrow + nd[u]] = sc * g[u];
+        }
       }
-      wg_bar(wg);  // the staging buffers are refilled for the next face
+      wg_bar(wg);
+      // ---- this row's 24 columns of face f -> TMEM (hi, lo)
+      {
+        const float4* g4 = reinterpret_cast<const float4*>(gbuf + ((i < TE ? i : 0) * 9 + p) * kGrow);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const float4 x0 = g4[2 * c], x1 = g4[2 * c + 1];
+          float g[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+          if (!valid) {
+#pragma unroll
+            for (int jn = 0; jn < 8; ++jn) g[jn] = 0.f;
+          }
+          st_split8(trow + cGh + 24 * f + 8 * c, trow + cGl + 24 * f + 8 * c, g);
+        }
+      }
     }
+    // ---- the next tile's loads overlap this tile's lift and dofs update
+    const int64_t next = tile + (int64_t)gridDim.x * 2;
+    if (next < ntiles) prefetch(next);
     // ---- lift on the tensor cores
     asm volatile("tcgen05.wait::st.sync.aligned;");
     tc::fence_before();
