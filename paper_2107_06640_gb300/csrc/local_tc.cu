@@ -20,9 +20,10 @@
 //   I = sum_k dt^{k+1}/(k+1)! D^k in registers (Eq. taylor);
 //   traces V_f = E_f I on the tensor cores, written to the trace array;
 //   volume: Z_a = A*_a I (shuffles), Q += sum_a K_a Z_a on the tensor cores.
-// The two warpgroups of a CTA work on two tiles at a time (TMEM columns
-// [0, 256) and [256, 512)); one thread per warpgroup issues its MMAs and
-// waits for their completion with a bounded mbarrier wait.
+// A CTA keeps two tiles in flight (TMEM columns [0, 256) and [256, 512)), each
+// worked on by two warpgroups that split every stage by 8-column chunks (even
+// chunks: first half, odd chunks: second half); one thread per tile issues
+// its MMAs and waits for their completion with a bounded mbarrier wait.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -36,7 +37,7 @@ namespace {
 
 constexpr int B = 56, B1 = 35, BF = 21;
 constexpr int TE = 12;          // elements per tile
-constexpr int kThreadsL = 256;  // two warpgroups
+constexpr int kThreadsL = 512;  // two tiles in flight, two warpgroups (halves) per tile
 constexpr int kWaitIters = 1 << 24;
 
 // tensor-core predictor levels: K (rows of D^k, padded to 8), rows of D^{k+1}
@@ -59,7 +60,8 @@ struct LImg {
   static constexpr int floats = ((oK4 + 12 + 3) / 4) * 4;
   static constexpr int bytes = floats * 4;
 };
-static_assert(LImg::bytes + 64 <= 232448, "operands exceed the shared memory of one CTA");
+static_assert(LImg::bytes + 2 * (2 * 128 + TE * 9 * BF) * 4 + 64 <= 232448,
+              "operands exceed the shared memory of one CTA");
 
 // per-warpgroup TMEM columns: A hi [0, 64), A lo [64, 128), accumulators [128, 256)
 constexpr uint32_t cAh = 0, cAl = 64, cAcc = 128;
@@ -128,8 +130,6 @@ __device__ __forceinline__ void st_split8(uint32_t th, uint32_t tl, const float 
                "r"(l[1]), "r"(l[2]), "r"(l[3]), "r"(l[4]), "r"(l[5]), "r"(l[6]), "r"(l[7]));
 }
 
-__device__ __forceinline__ void wg_bar(int wg) { asm volatile("bar.sync %0, 128;" ::"r"(wg + 1)); }
-
 // Per-thread star-product data: the quantity p of this lane's row, the lanes
 // of the quantities each output reads and their material coefficients.
 // D^{k+1}[p] = sum_d c_d X_d[src_d] with X_d = sum_a (dxi_a/dx_d) Y_a, the
@@ -188,14 +188,15 @@ __device__ __forceinline__ float star_apply(const Star& s, float y0, float y1, f
   return s.c[0] * a0 + s.c[1] * a1 + s.c[2] * a2;
 }
 
-// Epilogue of a tensor-core predictor level: Y (3 axes x MP columns at tacc)
-// -> D^{k+1} (M rows), I += ck * D^{k+1}; D^{k+1} goes to the A columns of the
-// next level (TO_A) or to registers dn.
-template <int M, int MP, bool TO_A>
+// Epilogue of a tensor-core predictor level for the 8-column chunks mc with
+// mc % 2 == H: Y (3 axes x MP columns at tacc) -> D^{k+1} (M rows),
+// I += ck * D^{k+1}; D^{k+1} goes to the A columns of the next level (TO_A)
+// or to registers dn.
+template <int H, int M, int MP, bool TO_A>
 __device__ __forceinline__ void level_epilogue(uint32_t tacc, uint32_t tah, uint32_t tal, const Star& s, float ck,
                                                float (&I)[B], float* dn) {
 #pragma unroll
-  for (int mc = 0; mc < MP / 8; ++mc) {
+  for (int mc = H; mc < MP / 8; mc += 2) {
     float y[24];
     ld3x8(tacc + 8 * mc, tacc + MP + 8 * mc, tacc + 2 * MP + 8 * mc, y);
     float d[8];
@@ -214,14 +215,265 @@ __device__ __forceinline__ void level_epilogue(uint32_t tacc, uint32_t tah, uint
   }
 }
 
+__device__ __forceinline__ void pair_bar(int slot) { asm volatile("bar.sync %0, 256;" ::"r"(slot + 1)); }
+
+// Everything one thread needs to work on the tiles of its slot.
+struct Lane {
+  float* Q;
+  float* trace;
+  const float* par;
+  unsigned int* err;
+  int64_t v_begin, n_virtual;
+  int S;
+  float tcf[6];       // dt^{k+1}/(k+1)!, k = 0..5
+  int slot, t, w, lane;
+  uint32_t tbase, trow, sbase;
+  const float* k3;
+  const float* k4;
+  float* sX;          // [128][2] rows 8, 9 of D^3 handed from half 1 to half 0
+  float* sT;          // [12][9][21] one face of the tile's traces, as stored in memory
+  uint64_t* mbar;     // this slot's barrier
+  int* abort;         // this slot's abort flag
+  uint32_t phase;
+};
+
+// One tensor-core round of a slot: both halves' A stores made visible, MMAs
+// issued by thread 0 of half 0, bounded wait for their completion.
+template <int H, class F>
+__device__ __forceinline__ bool pair_round(Lane& L, F&& issue_fn) {
+  asm volatile("tcgen05.wait::st.sync.aligned;");
+  tc::fence_before();
+  pair_bar(L.slot);
+  tc::fence_after();
+  if (H == 0 && L.t == 0) {
+    issue_fn();
+    tc::commit(L.mbar);
+    if (!tc::mbar_wait(L.mbar, L.phase, kWaitIters)) {
+      atomicOr(L.err, ERR_TIMEOUT);
+      *L.abort = 1;
+    }
+  }
+  pair_bar(L.slot);
+  const bool ok = !*(volatile int*)L.abort;
+  if (ok) tc::mbar_wait(L.mbar, L.phase, 1 << 20);  // observe the completed phase in every thread
+  L.phase ^= 1u;
+  tc::fence_after();
+  return ok;
+}
+
+// One tile, the share of half H (8-column chunks c with c % 2 == H); false
+// after a timed-out wait.
+template <int H>
+__device__ __forceinline__ bool local_tile(Lane& L, int64_t tile) {
+  const int64_t v0 = L.v_begin + tile * TE;
+  const int64_t nrem = L.n_virtual - tile * TE;
+  const int nE = (int)(nrem < TE ? nrem : TE);
+  const int jj = L.lane / 9, p = L.lane - 9 * (L.lane / 9);
+  const int i = 3 * L.w + jj;
+  const bool valid = L.lane < 27 && i < nE;
+  const int64_t v = v0 + (valid ? i : 0);
+  const int64_t e = v / L.S;
+  Star st;
+  star_setup(L.lane, valid, L.par + e * PAR, st);
+  const uint32_t trow = L.trow, tbase = L.tbase, sbase = L.sbase;
+
+  // ---- D^0 = Q row: I = dt Q, A = Q
+  float* Qrow = L.Q + (v * 9 + p) * B;
+  float I[B];
+#pragma unroll
+  for (int c = H; c < B / 8; c += 2) {
+    float x[8];
+    float4 x0 = make_float4(0.f, 0.f, 0.f, 0.f), x1 = x0;
+    if (valid) {
+      x0 = *reinterpret_cast<const float4*>(Qrow + 8 * c);
+      x1 = *reinterpret_cast<const float4*>(Qrow + 8 * c + 4);
+    }
+    x[0] = x0.x; x[1] = x0.y; x[2] = x0.z; x[3] = x0.w;
+    x[4] = x1.x; x[5] = x1.y; x[6] = x1.z; x[7] = x1.w;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) I[8 * c + j] = L.tcf[0] * x[j];
+    st_split8(trow + cAh + 8 * c, trow + cAl + 8 * c, x);
+  }
+  // ---- levels 0, 1, 2 on the tensor cores
+  if (!pair_round<H>(L, [&] {
+        issue(tbase + cAcc, tbase + cAh, tbase + cAl, sbase + 4 * LImg::oP0, sbase + 4 * (LImg::oP0 + LImg::sP0), kN0,
+              kK0, false);
+      }))
+    return false;
+  level_epilogue<H, kM0, kM0p, true>(trow + cAcc, trow + cAh, trow + cAl, st, L.tcf[1], I, nullptr);
+  if (!pair_round<H>(L, [&] {
+        issue(tbase + cAcc, tbase + cAh, tbase + cAl, sbase + 4 * LImg::oP1, sbase + 4 * (LImg::oP1 + LImg::sP1), kN1,
+              kK1, false);
+      }))
+    return false;
+  level_epilogue<H, kM1, kM1p, true>(trow + cAcc, trow + cAh, trow + cAl, st, L.tcf[2], I, nullptr);
+  if (!pair_round<H>(L, [&] {
+        issue(tbase + cAcc, tbase + cAh, tbase + cAl, sbase + 4 * LImg::oP2, sbase + 4 * (LImg::oP2 + LImg::sP2), kN2,
+              kK2, false);
+      }))
+    return false;
+  float d3[kM2p];
+  level_epilogue<H, kM2, kM2p, false>(trow + cAcc, trow + cAh, trow + cAl, st, L.tcf[3], I, d3);
+  // ---- levels 3 and 4 (half 0, with rows 8 and 9 of D^3 from half 1)
+  if (H == 1) {
+    L.sX[2 * L.t] = d3[8];
+    L.sX[2 * L.t + 1] = d3[9];
+  }
+  pair_bar(L.slot);
+  if (H == 0) {
+    d3[8] = L.sX[2 * L.t];
+    d3[9] = L.sX[2 * L.t + 1];
+    const float* k3 = L.k3;
+    const float* k4 = L.k4;
+    float d4[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      float y0 = 0.f, y1 = 0.f, y2 = 0.f;
+#pragma unroll
+      for (int l = 0; l < kM2; ++l) {
+        y0 += k3[(0 * 4 + m) * 10 + l] * d3[l];
+        y1 += k3[(1 * 4 + m) * 10 + l] * d3[l];
+        y2 += k3[(2 * 4 + m) * 10 + l] * d3[l];
+      }
+      d4[m] = star_apply(st, y0, y1, y2);
+      I[m] += L.tcf[4] * d4[m];
+    }
+    float y0 = 0.f, y1 = 0.f, y2 = 0.f;
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+      y0 += k4[0 * 4 + l] * d4[l];
+      y1 += k4[1 * 4 + l] * d4[l];
+      y2 += k4[2 * 4 + l] * d4[l];
+    }
+    I[0] += L.tcf[5] * star_apply(st, y0, y1, y2);
+  }
+
+  // ---- face traces: T = I E^T (N = 4 x 21)
+#pragma unroll
+  for (int c = H; c < B / 8; c += 2) st_split8(trow + cAh + 8 * c, trow + cAl + 8 * c, I + 8 * c);
+  if (!pair_round<H>(L, [&] {
+        issue(tbase + cAcc, tbase + cAh, tbase + cAl, sbase + 4 * LImg::oT, sbase + 4 * (LImg::oT + LImg::sT), kNT,
+              kK0, false);
+      }))
+    return false;
+  // traces leave face by face through shared memory, so that the stores of
+  // every element's contiguous face block are coalesced
+#pragma unroll
+  for (int f = 0; f < 4; ++f) {
+#pragma unroll
+    for (int c = H; c < 11; c += 2) {
+      if (8 * c + 7 < BF * f || 8 * c >= BF * (f + 1)) continue;  // chunk outside face f
+      float x[8];
+      ld8(trow + cAcc + 8 * c, x);
+      if (valid) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int col = 8 * c + j;
+          if (col >= BF * f && col < BF * (f + 1)) L.sT[(i * 9 + p) * BF + col - BF * f] = x[j];
+        }
+      }
+    }
+    pair_bar(L.slot);
+    for (int r = H * 128 + L.t; r < nE * 9 * BF; r += 256) {
+      const int ei = r / (9 * BF);
+      L.trace[((v0 + ei) * 4 + f) * 9 * BF + (r - ei * 9 * BF)] = L.sT[r];
+    }
+    pair_bar(L.slot);
+  }
+
+  // ---- volume: Z_a = A*_a I (l < 35); axes 0 and 1 at A columns [0, 160), then axis 2
+  const float w00 = -st.g[0] * st.c[0], w01 = -st.g[1] * st.c[1], w02 = -st.g[2] * st.c[2];
+  const float w10 = -st.g[3] * st.c[0], w11 = -st.g[4] * st.c[1], w12 = -st.g[5] * st.c[2];
+  const float w20 = -st.g[6] * st.c[0], w21 = -st.g[7] * st.c[1], w22 = -st.g[8] * st.c[2];
+#pragma unroll
+  for (int lc = H; lc < 5; lc += 2) {
+    float z0[8], z1[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int l = 8 * lc + j;
+      if (l < kM0) {
+        const float s0 = __shfl_sync(0xffffffffu, I[l], st.src[0]);
+        const float s1 = __shfl_sync(0xffffffffu, I[l], st.src[1]);
+        const float s2 = __shfl_sync(0xffffffffu, I[l], st.src[2]);
+        z0[j] = w00 * s0 + w01 * s1 + w02 * s2;
+        z1[j] = w10 * s0 + w11 * s1 + w12 * s2;
+      } else {
+        z0[j] = 0.f;
+        z1[j] = 0.f;
+      }
+    }
+    st_split8(trow + 8 * lc, trow + 40 + 8 * lc, z0);
+    st_split8(trow + 80 + 8 * lc, trow + 120 + 8 * lc, z1);
+  }
+  constexpr uint32_t cV = 192;  // volume accumulator columns [192, 256)
+  if (!pair_round<H>(L, [&] {
+        issue(tbase + cV, tbase + 0, tbase + 40, sbase + 4 * LImg::oV, sbase + 4 * (LImg::oV + LImg::sV), kNV, 40,
+              false);
+        issue(tbase + cV, tbase + 80, tbase + 120, sbase + 4 * (LImg::oV + 2 * LImg::sV),
+              sbase + 4 * (LImg::oV + 3 * LImg::sV), kNV, 40, true);
+      }))
+    return false;
+#pragma unroll
+  for (int lc = H; lc < 5; lc += 2) {
+    float z2[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int l = 8 * lc + j;
+      if (l < kM0) {
+        const float s0 = __shfl_sync(0xffffffffu, I[l], st.src[0]);
+        const float s1 = __shfl_sync(0xffffffffu, I[l], st.src[1]);
+        const float s2 = __shfl_sync(0xffffffffu, I[l], st.src[2]);
+        z2[j] = w20 * s0 + w21 * s1 + w22 * s2;
+      } else {
+        z2[j] = 0.f;
+      }
+    }
+    st_split8(trow + 8 * lc, trow + 40 + 8 * lc, z2);
+  }
+  // the dofs rows for the update are requested before the last round
+  float4 qv[8];
+#pragma unroll
+  for (int c = H; c < B / 8; c += 2) {
+    qv[c - H] = make_float4(0.f, 0.f, 0.f, 0.f);
+    qv[c - H + 1] = qv[c - H];
+    if (valid) {
+      qv[c - H] = reinterpret_cast<const float4*>(Qrow + 8 * c)[0];
+      qv[c - H + 1] = reinterpret_cast<const float4*>(Qrow + 8 * c)[1];
+    }
+  }
+  if (!pair_round<H>(L, [&] {
+        issue(tbase + cV, tbase + 0, tbase + 40, sbase + 4 * (LImg::oV + 4 * LImg::sV),
+              sbase + 4 * (LImg::oV + 5 * LImg::sV), kNV, 40, true);
+      }))
+    return false;
+  // ---- Q += volume term (face terms follow in the neighbour kernel)
+#pragma unroll
+  for (int c = H; c < B / 8; c += 2) {
+    float x[8];
+    ld8(trow + cV + 8 * c, x);
+    if (valid) {
+      float4* dst = reinterpret_cast<float4*>(Qrow + 8 * c);
+      const float4 q0 = qv[c - H], q1 = qv[c - H + 1];
+      dst[0] = make_float4(q0.x + x[0], q0.y + x[1], q0.z + x[2], q0.w + x[3]);
+      dst[1] = make_float4(q1.x + x[4], q1.y + x[5], q1.z + x[6], q1.w + x[7]);
+    }
+  }
+  // the next tile's first MMA overwrites these columns only after the
+  // barrier at the start of its round
+  tc::fence_before();
+  return true;
+}
+
 __global__ void __launch_bounds__(kThreadsL, 1) local_tc_kernel(StepArgs a, int64_t n_virtual) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   float* sm = reinterpret_cast<float*>(smem_raw);
   __shared__ uint32_t tmem_base;
   __shared__ __align__(8) uint64_t mbar[2];
   __shared__ int s_abort[2];
+  __shared__ float sX[2][2 * 128];
+  __shared__ __align__(16) float sT[2][TE * 9 * BF];
 
-  const int tid = threadIdx.x, wg = tid >> 7, t = tid & 127, w = t >> 5, lane = tid & 31;
+  const int tid = threadIdx.x, slot = tid >> 8, half = (tid >> 7) & 1;
   {
     const float4* src = reinterpret_cast<const float4*>(a.tc_local);
     float4* dst = reinterpret_cast<float4*>(sm);
@@ -237,202 +489,38 @@ __global__ void __launch_bounds__(kThreadsL, 1) local_tc_kernel(StepArgs a, int6
   __syncthreads();
   tc::fence_after();
 
-  const uint32_t tbase = tmem_base + (uint32_t)wg * 256u;            // this warpgroup's columns
-  const uint32_t trow = tbase + ((uint32_t)(32 * w) << 16);           // this warp's lanes
-  const uint32_t sbase = tc::smem_u32(sm);
-  const float* k3 = sm + LImg::oK3;
-  const float* k4 = sm + LImg::oK4;
-  const int jj = lane / 9, p = lane - 9 * (lane / 9);
+  Lane L;
+  L.Q = reinterpret_cast<float*>(a.Q);
+  L.trace = reinterpret_cast<float*>(a.trace);
+  L.par = reinterpret_cast<const float*>(a.par);
+  L.err = a.err;
+  L.v_begin = a.v_begin;
+  L.S = a.S;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) L.tcf[k] = (float)a.tcoef[k];
+  L.n_virtual = n_virtual;
+  L.slot = slot;
+  L.t = tid & 127;
+  L.w = L.t >> 5;
+  L.lane = tid & 31;
+  L.tbase = tmem_base + (uint32_t)slot * 256u;
+  L.trow = L.tbase + ((uint32_t)(32 * L.w) << 16);
+  L.sbase = tc::smem_u32(sm);
+  L.k3 = sm + LImg::oK3;
+  L.k4 = sm + LImg::oK4;
+  L.sX = sX[slot];
+  L.sT = sT[slot];
+  L.mbar = &mbar[slot];
+  L.abort = &s_abort[slot];
+  L.phase = 0;
   const int64_t ntiles = (n_virtual + TE - 1) / TE;
-  uint32_t phase = 0;
-  const float tc0 = (float)a.tcoef[0], tc1 = (float)a.tcoef[1], tc2 = (float)a.tcoef[2];
-  const float tc3 = (float)a.tcoef[3], tc4 = (float)a.tcoef[4], tc5 = (float)a.tcoef[5];
-
-  // one tensor-core round of this warpgroup: make the A stores visible, issue
-  // (thread 0 of the warpgroup), wait for completion; false on timeout
-  auto round = [&](auto&& issue_fn) -> bool {
-    asm volatile("tcgen05.wait::st.sync.aligned;");
-    tc::fence_before();
-    wg_bar(wg);
-    tc::fence_after();
-    if (t == 0) {
-      issue_fn();
-      tc::commit(&mbar[wg]);
-      if (!tc::mbar_wait(&mbar[wg], phase, kWaitIters)) {
-        atomicOr(a.err, ERR_TIMEOUT);
-        s_abort[wg] = 1;
-      }
-    }
-    wg_bar(wg);
-    const bool ok = !s_abort[wg];
-    if (ok) tc::mbar_wait(&mbar[wg], phase, 1 << 20);  // observe the completed phase in every thread
-    phase ^= 1u;
-    tc::fence_after();
-    return ok;
-  };
-
-  for (int64_t tile = (int64_t)blockIdx.x * 2 + wg; tile < ntiles; tile += (int64_t)gridDim.x * 2) {
-    const int64_t v0 = a.v_begin + tile * TE;
-    const int64_t nrem = n_virtual - tile * TE;
-    const int nE = (int)(nrem < TE ? nrem : TE);
-    const int i = 3 * w + jj;
-    const bool valid = lane < 27 && i < nE;
-    const int64_t v = v0 + (valid ? i : 0);
-    const int64_t e = v / a.S;
-    Star st;
-    star_setup(lane, valid, reinterpret_cast<const float*>(a.par) + e * PAR, st);
-
-    // ---- D^0 = Q row: I = dt Q, A = Q
-    float* Qrow = reinterpret_cast<float*>(a.Q) + (v * 9 + p) * B;
-    float q[B], I[B];
-#pragma unroll
-    for (int c = 0; c < B / 4; ++c) {
-      float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (valid) x = *reinterpret_cast<const float4*>(Qrow + 4 * c);
-      q[4 * c] = x.x; q[4 * c + 1] = x.y; q[4 * c + 2] = x.z; q[4 * c + 3] = x.w;
-    }
-#pragma unroll
-    for (int m = 0; m < B; ++m) I[m] = tc0 * q[m];
-#pragma unroll
-    for (int c = 0; c < kK0 / 8; ++c) st_split8(trow + cAh + 8 * c, trow + cAl + 8 * c, q + 8 * c);
-
-    // ---- level 0: Y = D^0 KT^T (N = 3 x 40)
-    if (!round([&] {
-          issue(tbase + cAcc, tbase + cAh, tbase + cAl, sbase + 4 * LImg::oP0, sbase + 4 * (LImg::oP0 + LImg::sP0), kN0,
-                kK0, false);
-        }))
-      break;
-    level_epilogue<kM0, kM0p, true>(trow + cAcc, trow + cAh, trow + cAl, st, tc1, I, nullptr);
-    // ---- level 1
-    if (!round([&] {
-          issue(tbase + cAcc, tbase + cAh, tbase + cAl, sbase + 4 * LImg::oP1, sbase + 4 * (LImg::oP1 + LImg::sP1), kN1,
-                kK1, false);
-        }))
-      break;
-    level_epilogue<kM1, kM1p, true>(trow + cAcc, trow + cAh, trow + cAl, st, tc2, I, nullptr);
-    // ---- level 2 (D^3 to registers)
-    if (!round([&] {
-          issue(tbase + cAcc, tbase + cAh, tbase + cAl, sbase + 4 * LImg::oP2, sbase + 4 * (LImg::oP2 + LImg::sP2), kN2,
-                kK2, false);
-        }))
-      break;
-    float d3[kM2];
-    level_epilogue<kM2, kM2p, false>(trow + cAcc, trow + cAh, trow + cAl, st, tc3, I, d3);
-    // ---- levels 3 and 4 on the CUDA cores
-    float d4[4];
-#pragma unroll
-    for (int m = 0; m < 4; ++m) {
-      float y0 = 0.f, y1 = 0.f, y2 = 0.f;
-#pragma unroll
-      for (int l = 0; l < kM2; ++l) {
-        y0 += k3[(0 * 4 + m) * 10 + l] * d3[l];
-        y1 += k3[(1 * 4 + m) * 10 + l] * d3[l];
-        y2 += k3[(2 * 4 + m) * 10 + l] * d3[l];
-      }
-      d4[m] = star_apply(st, y0, y1, y2);
-      I[m] += tc4 * d4[m];
-    }
-    {
-      float y0 = 0.f, y1 = 0.f, y2 = 0.f;
-#pragma unroll
-      for (int l = 0; l < 4; ++l) {
-        y0 += k4[0 * 4 + l] * d4[l];
-        y1 += k4[1 * 4 + l] * d4[l];
-        y2 += k4[2 * 4 + l] * d4[l];
-      }
-      I[0] += tc5 * star_apply(st, y0, y1, y2);
-    }
-
-    // ---- face traces: T = I E^T (N = 4 x 21)
-#pragma unroll
-    for (int c = 0; c < kK0 / 8; ++c) st_split8(trow + cAh + 8 * c, trow + cAl + 8 * c, I + 8 * c);
-    if (!round([&] {
-          issue(tbase + cAcc, tbase + cAh, tbase + cAl, sbase + 4 * LImg::oT, sbase + 4 * (LImg::oT + LImg::sT), kNT,
-                kK0, false);
-        }))
-      break;
-    {
-      float* tr = reinterpret_cast<float*>(a.trace) + v * 36 * BF + p * BF;
-#pragma unroll
-      for (int c = 0; c < 11; ++c) {
-        float x[8];
-        ld8(trow + cAcc + 8 * c, x);
-        if (valid) {
-#pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            const int col = 8 * c + j;
-            if (col < 4 * BF) tr[(col / BF) * 9 * BF + col % BF] = x[j];
-          }
-        }
-      }
-    }
-
-    // ---- volume: Z_a = A*_a I (l < 35); axes 0 and 1 at A columns [0, 160), then axis 2
-    float z2[kM0];
-    {
-      const float w00 = -st.g[0] * st.c[0], w01 = -st.g[1] * st.c[1], w02 = -st.g[2] * st.c[2];
-      const float w10 = -st.g[3] * st.c[0], w11 = -st.g[4] * st.c[1], w12 = -st.g[5] * st.c[2];
-      const float w20 = -st.g[6] * st.c[0], w21 = -st.g[7] * st.c[1], w22 = -st.g[8] * st.c[2];
-#pragma unroll
-      for (int lc = 0; lc < 5; ++lc) {
-        float z0[8], z1[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const int l = 8 * lc + j;
-          if (l < kM0) {
-            const float s0 = __shfl_sync(0xffffffffu, I[l], st.src[0]);
-            const float s1 = __shfl_sync(0xffffffffu, I[l], st.src[1]);
-            const float s2 = __shfl_sync(0xffffffffu, I[l], st.src[2]);
-            z0[j] = w00 * s0 + w01 * s1 + w02 * s2;
-            z1[j] = w10 * s0 + w11 * s1 + w12 * s2;
-            z2[l] = w20 * s0 + w21 * s1 + w22 * s2;
-          } else {
-            z0[j] = 0.f;
-            z1[j] = 0.f;
-          }
-        }
-        st_split8(trow + 8 * lc, trow + 40 + 8 * lc, z0);
-        st_split8(trow + 80 + 8 * lc, trow + 120 + 8 * lc, z1);
-      }
-    }
-    constexpr uint32_t cV = 192;  // volume accumulator columns [192, 256)
-    if (!round([&] {
-          issue(tbase + cV, tbase + 0, tbase + 40, sbase + 4 * LImg::oV, sbase + 4 * (LImg::oV + LImg::sV), kNV, 40,
-                false);
-          issue(tbase + cV, tbase + 80, tbase + 120, sbase + 4 * (LImg::oV + 2 * LImg::sV),
-                sbase + 4 * (LImg::oV + 3 * LImg::sV), kNV, 40, true);
-        }))
-      break;
-#pragma unroll
-    for (int lc = 0; lc < 5; ++lc) {
-      float z[8];
-#pragma unroll
-      for (int j = 0; j < 8; ++j) z[j] = (8 * lc + j < kM0) ? z2[8 * lc + j] : 0.f;
-      st_split8(trow + 8 * lc, trow + 40 + 8 * lc, z);
-    }
-    if (!round([&] {
-          issue(tbase + cV, tbase + 0, tbase + 40, sbase + 4 * (LImg::oV + 4 * LImg::sV),
-                sbase + 4 * (LImg::oV + 5 * LImg::sV), kNV, 40, true);
-        }))
-      break;
-    // ---- Q += volume term (face terms follow in the neighbour kernel)
-#pragma unroll
-    for (int c = 0; c < B / 8; ++c) {
-      float x[8];
-      ld8(trow + cV + 8 * c, x);
-      if (valid) {
-        float4* dst = reinterpret_cast<float4*>(Qrow + 8 * c);
-        dst[0] = make_float4(q[8 * c] + x[0], q[8 * c + 1] + x[1], q[8 * c + 2] + x[2], q[8 * c + 3] + x[3]);
-        dst[1] = make_float4(q[8 * c + 4] + x[4], q[8 * c + 5] + x[5], q[8 * c + 6] + x[6], q[8 * c + 7] + x[7]);
-      }
-    }
-    // the next tile's first MMA overwrites these columns only after the
-    // barrier at the start of its round
-    tc::fence_before();
+  for (int64_t tile = (int64_t)blockIdx.x * 2 + slot; tile < ntiles; tile += (int64_t)gridDim.x * 2) {
+    const bool ok = half == 0 ? local_tile<0>(L, tile) : local_tile<1>(L, tile);
+    if (!ok) break;
   }
-  // after a timed-out wait, give this warpgroup's MMAs in flight a bounded
-  // chance to finish before the columns are freed
-  if (t == 0 && s_abort[wg]) tc::mbar_wait(&mbar[wg], phase ^ 1u, kWaitIters);
+  // after a timed-out wait, give this slot's MMAs in flight a bounded chance
+  // to finish before the columns are freed
+  if (half == 0 && L.t == 0 && s_abort[slot]) tc::mbar_wait(&mbar[slot], L.phase ^ 1u, kWaitIters);
   tc::fence_before();
   __syncthreads();
   tc::fence_after();
