@@ -216,6 +216,10 @@ __device__ __forceinline__ void level_epilogue(uint32_t tacc, uint32_t tah, uint
 }
 
 __device__ __forceinline__ void pair_bar(int slot) { asm volatile("bar.sync %0, 256;" ::"r"(slot + 1)); }
+// the two warps (one per half) of a slot that hold the same 32 rows
+__device__ __forceinline__ void warp_pair_bar(int slot, int w) {
+  asm volatile("bar.sync %0, 64;" ::"r"(3 + 4 * slot + w));
+}
 
 // Everything one thread needs to work on the tiles of its slot.
 struct Lane {
@@ -231,7 +235,7 @@ struct Lane {
   const float* k3;
   const float* k4;
   float* sX;          // [128][2] rows 8, 9 of D^3 handed from half 1 to half 0
-  float* sT;          // [12][9][21] one face of the tile's traces, as stored in memory
+  float* sT;          // [3][9][21] one face of this warp's three elements' traces, as stored in memory
   uint64_t* mbar;     // this slot's barrier
   int* abort;         // this slot's abort flag
   uint32_t phase;
@@ -277,6 +281,14 @@ __device__ __forceinline__ bool local_tile(Lane& L, int64_t tile) {
   star_setup(L.lane, valid, L.par + e * PAR, st);
   const uint32_t trow = L.trow, tbase = L.tbase, sbase = L.sbase;
 
+  // the next tile of this slot into L2 while this one is worked on
+  if (H == 0 && L.t == 0) {
+    const int64_t nt = tile + (int64_t)gridDim.x * 2;
+    if (nt * TE < L.n_virtual) {
+      const int64_t nrem2 = L.n_virtual - nt * TE;
+      tc::prefetch_l2(L.Q + (L.v_begin + nt * TE) * 9 * B, (uint32_t)((nrem2 < TE ? nrem2 : TE) * 9 * B * 4));
+    }
+  }
   // ---- D^0 = Q row: I = dt Q, A = Q
   float* Qrow = L.Q + (v * 9 + p) * B;
   float I[B];
@@ -357,28 +369,32 @@ __device__ __forceinline__ bool local_tile(Lane& L, int64_t tile) {
       }))
     return false;
   // traces leave face by face through shared memory, so that the stores of
-  // every element's contiguous face block are coalesced
+  // every element's contiguous face block are coalesced; the two warps (one
+  // per half) that hold the rows of three elements share a buffer
+  {
+    const int nmine = nE - 3 * L.w < 3 ? nE - 3 * L.w : 3;  // elements of this warp (may be <= 0)
 #pragma unroll
-  for (int f = 0; f < 4; ++f) {
+    for (int f = 0; f < 4; ++f) {
 #pragma unroll
-    for (int c = H; c < 11; c += 2) {
-      if (8 * c + 7 < BF * f || 8 * c >= BF * (f + 1)) continue;  // chunk outside face f
-      float x[8];
-      ld8(trow + cAcc + 8 * c, x);
-      if (valid) {
+      for (int c = H; c < 11; c += 2) {
+        if (8 * c + 7 < BF * f || 8 * c >= BF * (f + 1)) continue;  // chunk outside face f
+        float x[8];
+        ld8(trow + cAcc + 8 * c, x);
+        if (valid) {
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const int col = 8 * c + j;
-          if (col >= BF * f && col < BF * (f + 1)) L.sT[(i * 9 + p) * BF + col - BF * f] = x[j];
+          for (int j = 0; j < 8; ++j) {
+            const int col = 8 * c + j;
+            if (col >= BF * f && col < BF * (f + 1)) L.sT[(jj * 9 + p) * BF + col - BF * f] = x[j];
+          }
         }
       }
+      warp_pair_bar(L.slot, L.w);
+      for (int r = H * 32 + L.lane; r < nmine * 9 * BF; r += 64) {
+        const int ej = r / (9 * BF);
+        L.trace[((v0 + 3 * L.w + ej) * 4 + f) * 9 * BF + (r - ej * 9 * BF)] = L.sT[r];
+      }
+      warp_pair_bar(L.slot, L.w);
     }
-    pair_bar(L.slot);
-    for (int r = H * 128 + L.t; r < nE * 9 * BF; r += 256) {
-      const int ei = r / (9 * BF);
-      L.trace[((v0 + ei) * 4 + f) * 9 * BF + (r - ei * 9 * BF)] = L.sT[r];
-    }
-    pair_bar(L.slot);
   }
 
   // ---- volume: Z_a = A*_a I (l < 35); axes 0 and 1 at A columns [0, 160), then axis 2
@@ -471,7 +487,7 @@ __global__ void __launch_bounds__(kThreadsL, 1) local_tc_kernel(StepArgs a, int6
   __shared__ __align__(8) uint64_t mbar[2];
   __shared__ int s_abort[2];
   __shared__ float sX[2][2 * 128];
-  __shared__ __align__(16) float sT[2][TE * 9 * BF];
+  __shared__ __align__(16) float sT[2][4][3 * 9 * BF];
 
   const int tid = threadIdx.x, slot = tid >> 8, half = (tid >> 7) & 1;
   {
@@ -509,7 +525,7 @@ __global__ void __launch_bounds__(kThreadsL, 1) local_tc_kernel(StepArgs a, int6
   L.k3 = sm + LImg::oK3;
   L.k4 = sm + LImg::oK4;
   L.sX = sX[slot];
-  L.sT = sT[slot];
+  L.sT = sT[slot][(tid & 127) >> 5];
   L.mbar = &mbar[slot];
   L.abort = &s_abort[slot];
   L.phase = 0;

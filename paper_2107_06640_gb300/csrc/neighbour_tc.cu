@@ -195,10 +195,9 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
     const int64_t e0 = pv0 / a.S;
     const int ne = (int)((pv0 + pnE - 1) / a.S - e0 + 1);
     // F-, F+ rows of elements e0 .. e0 + ne - 1: ne x 1296 bytes each, 16-byte aligned
-    for (int c = t; c < 2 * ne * 81; c += 128) {
-      const int m = c / (ne * 81), cc = c - m * (ne * 81);
-      const float* src = reinterpret_cast<const float*>(m ? a.Fp : a.Fm) + e0 * 324 + 4 * cc;
-      cp16(sFm + m * TE * 324 + 4 * cc, src);
+    for (int cc = t; cc < ne * 81; cc += 128) {
+      cp16(sFm + 4 * cc, reinterpret_cast<const float*>(a.Fm) + e0 * 324 + 4 * cc);
+      cp16(sFm + TE * 324 + 4 * cc, reinterpret_cast<const float*>(a.Fp) + e0 * 324 + 4 * cc);
     }
     for (int c = t; c < ne * (PAR / 4); c += 128)
       cp16(sPr + 4 * c, reinterpret_cast<const float*>(a.par) + e0 * PAR + 4 * c);
@@ -297,6 +296,17 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
     // ---- the next tile's loads overlap this tile's lift and dofs update
     const int64_t next = tile + (int64_t)gridDim.x * 2;
     if (next < ntiles) prefetch(next);
+    // and the tile after it into L2
+    const int64_t next2 = next + (int64_t)gridDim.x * 2;
+    if (t == 0 && next2 < ntiles) {
+      const int64_t q0 = a.v_begin + next2 * TE, rem2 = n_virtual - next2 * TE;
+      const uint32_t n2 = (uint32_t)(rem2 < TE ? rem2 : TE);
+      tc::prefetch_l2(reinterpret_cast<const float*>(a.Q) + q0 * 9 * B, n2 * 9 * B * 4);
+      tc::prefetch_l2(trace + q0 * 4 * 9 * BF, n2 * 4 * 9 * BF * 4);
+      const int64_t e0 = q0 / a.S, ne = (q0 + n2 - 1) / a.S - e0 + 1;
+      tc::prefetch_l2(reinterpret_cast<const float*>(a.Fm) + e0 * 324, (uint32_t)(ne * 324 * 4));
+      tc::prefetch_l2(reinterpret_cast<const float*>(a.Fp) + e0 * 324, (uint32_t)(ne * 324 * 4));
+    }
     // ---- lift on the tensor cores
     asm volatile("tcgen05.wait::st.sync.aligned;");
     tc::fence_before();
