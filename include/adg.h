@@ -177,7 +177,8 @@ int adg_profile(adg_ctx* ctx, int n_macro, double* ms, int64_t* launches);
  *  - stream: cudaStream_t to launch on, or NULL for the context's stream;
  *    the call only enqueues work (no synchronisation).
  *  - Meshes whose traces need more than the fixed maximum
- *    (n_tets * 36 * Bf * sizeof(precision) > 32 MiB) are rejected with
+ *    (n_tets * 4 * S_f * sizeof(precision) > 32 MiB, S_f = 9 Bf rounded up
+ *    to a multiple of 4) are rejected with
  *    ADG_E_INVALID and a message naming both sizes.
  *  - The first call on a device looks up the array's device address with
  *    that device current; make that first call before any stream capture.

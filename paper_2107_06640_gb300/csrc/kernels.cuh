@@ -14,7 +14,8 @@
 //                     writes its own face traces (and LTS buffers/derivatives).
 //   neighbour kernel  gathers the neighbours' face traces (re-oriented by a
 //                     node permutation), applies F^+ and lifts.
-// Dofs layout: Q[v][9][B] (basis fastest); traces [v][4][9][Bf] (node fastest).
+// Dofs layout: Q[v][9][B] (basis fastest); traces [v][4][face_stride(N)], each face
+// block [9][Bf] (node fastest) followed by padding.
 #pragma once
 #include <cstdint>
 
@@ -22,6 +23,9 @@ namespace adg {
 
 __host__ __device__ constexpr int nb3(int n) { return n < 0 ? 0 : (n + 1) * (n + 2) * (n + 3) / 6; }
 __host__ __device__ constexpr int nb2(int n) { return (n + 1) * (n + 2) / 2; }
+// floats of one face's traces in the trace array: 9 x Bf values [quantity][node],
+// padded to a multiple of 4 so that every face block starts on 16 bytes
+__host__ __device__ constexpr int face_stride(int n) { return (9 * nb2(n) + 3) / 4 * 4; }
 
 // neighbour-face kinds (ninfo bits 5..7)
 enum { NK_NONE = 0, NK_SAME = 1, NK_COARSE = 2, NK_FINE = 3, NK_FAULT = 4 };
@@ -34,7 +38,7 @@ constexpr int GPAR = 6 + 81 + 18;
 
 struct StepArgs {
   void* Q;              // T [V][9][B]
-  void* trace;          // T [V][4][9][Bf]
+  void* trace;          // T [V][4][face_stride(N)]: [9][Bf] per face + padding
   double* btrace;       // [nbslot*S][4][9][Bf]  (LTS buffer, FP64)
   void* dtrace;         // T [ndslot*S][N+1][9][Bf] (LTS derivative traces)
   double* eta;          // [ngslot*S][Bf]

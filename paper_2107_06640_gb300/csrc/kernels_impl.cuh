@@ -239,7 +239,8 @@ __global__ void __launch_bounds__(kThreads) local_kernel(StepArgs a) {
       store9(sY + (ax * B1 + l) * P, z);
     }
   }
-  T* trace = reinterpret_cast<T*>(a.trace) + v * 36 * Bf;
+  constexpr int FS = face_stride(N);
+  T* trace = reinterpret_cast<T*>(a.trace) + v * 4 * FS;
   double* bt = nullptr;
   if (a.btrace_mode && a.bslot) {
     const int bs = a.bslot[e];
@@ -260,7 +261,7 @@ __global__ void __launch_bounds__(kThreads) local_kernel(StepArgs a) {
     }
     store9(sV + r * P, acc);
 #pragma unroll
-    for (int p = 0; p < 9; ++p) trace[(f * 9 + p) * Bf + n] = acc[p];
+    for (int p = 0; p < 9; ++p) trace[f * FS + p * Bf + n] = acc[p];
     if (bt) {
 #pragma unroll
       for (int p = 0; p < 9; ++p) {
@@ -390,10 +391,11 @@ __global__ void __launch_bounds__(kThreads) neighbour_kernel(StepArgs a) {
     sF[f * 162 + k] = reinterpret_cast<const T*>(a.Fm)[e * 4 * 81 + r];
     sF[f * 162 + 81 + k] = reinterpret_cast<const T*>(a.Fp)[e * 4 * 81 + r];
   }
-  const T* own = reinterpret_cast<const T*>(a.trace) + v * 36 * Bf;
+  constexpr int FS = face_stride(N);
+  const T* own = reinterpret_cast<const T*>(a.trace) + v * 4 * FS;
   for (int r = tid; r < 36 * Bf; r += nth) {  // [f][p][n] -> [f][n][p]
     const int f = r / (9 * Bf), p = (r / Bf) % 9, n = r % Bf;
-    sVo[(f * Bf + n) * P + p] = own[r];
+    sVo[(f * Bf + n) * P + p] = own[f * FS + p * Bf + n];
   }
   __syncthreads();
   for (int r = tid; r < 36 * Bf; r += nth) {
@@ -406,7 +408,7 @@ __global__ void __launch_bounds__(kThreads) neighbour_kernel(StepArgs a) {
       const int j = info & 3, pm = (info >> 2) & 7;
       const int src = a.perm[pm * Bf + n];
       if (kind == NK_SAME) {
-        val = reinterpret_cast<const T*>(a.trace)[((nb * a.S + s) * 4 + j) * 9 * Bf + p * Bf + src];
+        val = reinterpret_cast<const T*>(a.trace)[((nb * a.S + s) * 4 + j) * FS + p * Bf + src];
       } else if (kind == NK_FINE) {
         const int bs = a.bslot[nb];
         val = (T)a.btrace[(((int64_t)bs * a.S + s) * 4 + j) * 9 * Bf + p * Bf + src];

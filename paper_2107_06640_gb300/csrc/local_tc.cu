@@ -19,7 +19,8 @@
 //   levels 3, 4 (4 and 1 rows) on the CUDA cores from registers;
 //   I = sum_k dt^{k+1}/(k+1)! D^k in registers (Eq. taylor);
 //   traces V_f = E_f I on the tensor cores, written to the trace array;
-//   volume: Z_a = A*_a I (shuffles), Q += sum_a K_a Z_a on the tensor cores.
+//   volume: W_a = K_a I for the three axes on the tensor cores, then
+//     Q += sum_a A*_a W_a on the CUDA cores (Jacobian form, shuffles).
 // A CTA keeps two tiles in flight (TMEM columns [0, 256) and [256, 512)), each
 // worked on by two warpgroups that split every stage by 8-column chunks (even
 // chunks: first half, odd chunks: second half); one thread per tile issues
@@ -36,6 +37,7 @@ namespace adg {
 namespace {
 
 constexpr int B = 56, B1 = 35, BF = 21;
+constexpr int FS = face_stride(5);  // 192 floats per face block of the trace array
 constexpr int TE = 12;          // elements per tile
 constexpr int kThreadsL = 512;  // two tiles in flight, two warpgroups (halves) per tile
 constexpr int kWaitIters = 1 << 24;
@@ -46,15 +48,15 @@ constexpr int kK0 = 56, kM0 = 35, kM0p = 40, kN0 = 128;
 constexpr int kK1 = 40, kM1 = 20, kM1p = 24, kN1 = 80;
 constexpr int kK2 = 24, kM2 = 10, kM2p = 16, kN2 = 48;
 constexpr int kNT = 96;  // traces: 4 faces x 21 nodes, padded
-constexpr int kNV = 64;  // volume: 56 basis functions, padded; K per axis = 40
+constexpr int kNV = 176;  // volume: 3 axes x 56 basis functions, padded; K = 40 (35 used)
 
 // shared-memory image of the operands (floats), hi block then lo block each
 struct LImg {
   static constexpr int oP0 = 0, sP0 = kN0 * kK0;
   static constexpr int oP1 = oP0 + 2 * sP0, sP1 = kN1 * kK1;
   static constexpr int oP2 = oP1 + 2 * sP1, sP2 = kN2 * kK2;
-  static constexpr int oV = oP2 + 2 * sP2, sV = kNV * 40;  // per axis
-  static constexpr int oT = oV + 6 * sV, sT = kNT * kK0;
+  static constexpr int oV = oP2 + 2 * sP2, sV = kNV * 40;
+  static constexpr int oT = oV + 2 * sV, sT = kNT * kK0;
   static constexpr int oK3 = oT + 2 * sT;                  // kt[a][m][l], m < 4, l < 10
   static constexpr int oK4 = oK3 + 120;                    // kt[a][0][l], l < 4
   static constexpr int floats = ((oK4 + 12 + 3) / 4) * 4;
@@ -391,62 +393,17 @@ __device__ __forceinline__ bool local_tile(Lane& L, int64_t tile) {
       warp_pair_bar(L.slot, L.w);
       for (int r = H * 32 + L.lane; r < nmine * 9 * BF; r += 64) {
         const int ej = r / (9 * BF);
-        L.trace[((v0 + 3 * L.w + ej) * 4 + f) * 9 * BF + (r - ej * 9 * BF)] = L.sT[r];
+        L.trace[((v0 + 3 * L.w + ej) * 4 + f) * FS + (r - ej * 9 * BF)] = L.sT[r];
       }
       warp_pair_bar(L.slot, L.w);
     }
   }
 
-  // ---- volume: Z_a = A*_a I (l < 35); axes 0 and 1 at A columns [0, 160), then axis 2
-  const float w00 = -st.g[0] * st.c[0], w01 = -st.g[1] * st.c[1], w02 = -st.g[2] * st.c[2];
-  const float w10 = -st.g[3] * st.c[0], w11 = -st.g[4] * st.c[1], w12 = -st.g[5] * st.c[2];
-  const float w20 = -st.g[6] * st.c[0], w21 = -st.g[7] * st.c[1], w22 = -st.g[8] * st.c[2];
+  // ---- volume: W_a = K_a I (l < 35) for the three axes in one product,
+  // then Q += sum_a A*_a W_a = -sum_d c_d X_d[src_d] (Jacobian form)
 #pragma unroll
-  for (int lc = H; lc < 5; lc += 2) {
-    float z0[8], z1[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int l = 8 * lc + j;
-      if (l < kM0) {
-        const float s0 = __shfl_sync(0xffffffffu, I[l], st.src[0]);
-        const float s1 = __shfl_sync(0xffffffffu, I[l], st.src[1]);
-        const float s2 = __shfl_sync(0xffffffffu, I[l], st.src[2]);
-        z0[j] = w00 * s0 + w01 * s1 + w02 * s2;
-        z1[j] = w10 * s0 + w11 * s1 + w12 * s2;
-      } else {
-        z0[j] = 0.f;
-        z1[j] = 0.f;
-      }
-    }
-    st_split8(trow + 8 * lc, trow + 40 + 8 * lc, z0);
-    st_split8(trow + 80 + 8 * lc, trow + 120 + 8 * lc, z1);
-  }
-  constexpr uint32_t cV = 192;  // volume accumulator columns [192, 256)
-  if (!pair_round<H>(L, [&] {
-        issue(tbase + cV, tbase + 0, tbase + 40, sbase + 4 * LImg::oV, sbase + 4 * (LImg::oV + LImg::sV), kNV, 40,
-              false);
-        issue(tbase + cV, tbase + 80, tbase + 120, sbase + 4 * (LImg::oV + 2 * LImg::sV),
-              sbase + 4 * (LImg::oV + 3 * LImg::sV), kNV, 40, true);
-      }))
-    return false;
-#pragma unroll
-  for (int lc = H; lc < 5; lc += 2) {
-    float z2[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int l = 8 * lc + j;
-      if (l < kM0) {
-        const float s0 = __shfl_sync(0xffffffffu, I[l], st.src[0]);
-        const float s1 = __shfl_sync(0xffffffffu, I[l], st.src[1]);
-        const float s2 = __shfl_sync(0xffffffffu, I[l], st.src[2]);
-        z2[j] = w20 * s0 + w21 * s1 + w22 * s2;
-      } else {
-        z2[j] = 0.f;
-      }
-    }
-    st_split8(trow + 8 * lc, trow + 40 + 8 * lc, z2);
-  }
-  // the dofs rows for the update are requested before the last round
+  for (int c = H; c < 5; c += 2) st_split8(trow + 8 * c, trow + 40 + 8 * c, I + 8 * c);
+  // the dofs rows for the update are requested before the round
   float4 qv[8];
 #pragma unroll
   for (int c = H; c < B / 8; c += 2) {
@@ -457,16 +414,20 @@ __device__ __forceinline__ bool local_tile(Lane& L, int64_t tile) {
       qv[c - H + 1] = reinterpret_cast<const float4*>(Qrow + 8 * c)[1];
     }
   }
+  constexpr uint32_t cV = 80;  // volume accumulator: axis a, basis m at column 80 + 56 a + m
   if (!pair_round<H>(L, [&] {
-        issue(tbase + cV, tbase + 0, tbase + 40, sbase + 4 * (LImg::oV + 4 * LImg::sV),
-              sbase + 4 * (LImg::oV + 5 * LImg::sV), kNV, 40, true);
+        issue(tbase + cV, tbase + 0, tbase + 40, sbase + 4 * LImg::oV, sbase + 4 * (LImg::oV + LImg::sV), kNV, 40,
+              false);
       }))
     return false;
   // ---- Q += volume term (face terms follow in the neighbour kernel)
 #pragma unroll
   for (int c = H; c < B / 8; c += 2) {
+    float y[24];
+    ld3x8(trow + cV + 8 * c, trow + cV + B + 8 * c, trow + cV + 2 * B + 8 * c, y);
     float x[8];
-    ld8(trow + cV + 8 * c, x);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) x[j] = -star_apply(st, y[j], y[8 + j], y[16 + j]);
     if (valid) {
       float4* dst = reinterpret_cast<float4*>(Qrow + 8 * c);
       const float4 q0 = qv[c - H], q1 = qv[c - H + 1];
@@ -583,7 +544,7 @@ void pack_local_tc(const double* kt, const double* kvol, const double* efc, floa
   for (int ax = 0; ax < 3; ++ax)
     for (int m = 0; m < B; ++m)
       for (int l = 0; l < B1; ++l)
-        put(LImg::oV + 2 * ax * LImg::sV, LImg::sV, kNV, m, l, kvol[((size_t)ax * B + m) * B1 + l]);
+        put(LImg::oV, LImg::sV, kNV, ax * B + m, l, kvol[((size_t)ax * B + m) * B1 + l]);
   for (int f = 0; f < 4; ++f)
     for (int n = 0; n < BF; ++n)
       for (int l = 0; l < B; ++l) put(LImg::oT, LImg::sT, kNT, f * BF + n, l, efc[((size_t)f * BF + n) * B + l]);

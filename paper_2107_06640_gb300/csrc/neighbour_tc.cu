@@ -37,8 +37,8 @@ constexpr int kThreadsN = 256;  // two warpgroups, one tile each
 constexpr int kWaitIters = 1 << 24;
 constexpr int kK = 96;          // 4 faces x 24 columns (21 nodes + 3 zero)
 constexpr int kN = 64;          // 56 basis functions, padded
-constexpr int kFace = 9 * BF;         // floats of one face's traces (189)
-constexpr int kStage = TE * kFace;    // floats per staged face array
+constexpr int kFS = face_stride(5);   // floats per face block in the trace array (192)
+constexpr int kStage = TE * kFS;      // floats per staged face array
 constexpr int kGrow = 24;             // transposed flux row: 21 nodes + 3 zero
 constexpr int kG = TE * 9 * kGrow;    // floats per transposition buffer
 constexpr int kTrip = 7;              // node triplets (n, n + 7, n + 14) per element face
@@ -97,34 +97,31 @@ __device__ __forceinline__ void st_split8(uint32_t th, uint32_t tl, const float 
 
 __device__ __forceinline__ void wg_bar(int wg) { asm volatile("bar.sync %0, 128;" ::"r"(wg + 1)); }
 
-// asynchronous 4-byte copy global -> shared; zero fill when !valid
-__device__ __forceinline__ void cp4(float* dst, const float* src, bool valid) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(tc::smem_u32(dst)), "l"(src),
-               "r"(valid ? 4 : 0));
-}
-__device__ __forceinline__ void cp16(void* dst, const void* src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(tc::smem_u32(dst)), "l"(src));
+// asynchronous 16-byte copy global -> shared; zero fill when !valid
+__device__ __forceinline__ void cp16(void* dst, const void* src, bool valid = true) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(tc::smem_u32(dst)), "l"(src),
+               "r"(valid ? 16 : 0));
 }
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;"); }
 template <int NPEND>
 __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(NPEND)); }
 
 // Stage face f of a tile: own traces and the neighbours' traces of that face,
-// both as stored ([element][quantity][node]); the neighbour's node order is
-// applied when the values are read.
+// both as stored (one 16-byte aligned face block [quantity][node] per
+// element); the neighbour's node order is applied when the values are read.
 __device__ __forceinline__ void stage_face(int f, int t, int64_t v0, int nE, const float* trace,
                                            const long long* nbase, float* so, float* sn) {
+  constexpr int kChunks = kFS / 4;  // 16-byte chunks per face block
 #pragma unroll
-  for (int it = 0; it < (kStage + 127) / 128; ++it) {
+  for (int it = 0; it < (TE * kChunks + 127) / 128; ++it) {
     const int r = t + 128 * it;
-    if (r < kStage) {
-      const int ei = r / kFace, rem = r - ei * kFace;
+    if (r < TE * kChunks) {
+      const int ei = r / kChunks, ch = r - ei * kChunks;
       const bool ok = ei < nE;
-      const float* src_o = trace + ((v0 + (ok ? ei : 0)) * 4 + f) * kFace + rem;
       const long long nb = nbase[f * TE + ei];
       const bool okn = ok && nb >= 0;
-      cp4(so + r, src_o, ok);
-      cp4(sn + r, trace + (okn ? nb + rem : 0), okn);
+      cp16(so + ei * kFS + 4 * ch, trace + ((v0 + (ok ? ei : 0)) * 4 + f) * kFS + 4 * ch, ok);
+      cp16(sn + ei * kFS + 4 * ch, trace + (okn ? nb : 0) + 4 * ch, okn);
     }
   }
 }
@@ -184,7 +181,7 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
         const int info = a.ninfo[ee * 4 + f];
         if (((info >> 5) & 7) == NK_SAME) {
           const int64_t vn_e = (int64_t)a.nbr[ee * 4 + f] * a.S + (ve - ee * a.S);
-          nb = (vn_e * 4 + (info & 3)) * 9 * BF;
+          nb = (vn_e * 4 + (info & 3)) * kFS;
           pm = (info >> 2) & 7;
         }
       }
@@ -255,8 +252,8 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
         float vo[3][9], vn[3][9];
 #pragma unroll
         for (int qq = 0; qq < 9; ++qq) {
-          const float* o = sVo + ei * kFace + qq * BF;
-          const float* nn = sVn + ei * kFace + qq * BF;
+          const float* o = sVo + ei * kFS + qq * BF;
+          const float* nn = sVn + ei * kFS + qq * BF;
 #pragma unroll
           for (int u = 0; u < 3; ++u) {
             vo[u][qq] = o[nd[u]];
@@ -302,7 +299,7 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
       const int64_t q0 = a.v_begin + next2 * TE, rem2 = n_virtual - next2 * TE;
       const uint32_t n2 = (uint32_t)(rem2 < TE ? rem2 : TE);
       tc::prefetch_l2(reinterpret_cast<const float*>(a.Q) + q0 * 9 * B, n2 * 9 * B * 4);
-      tc::prefetch_l2(trace + q0 * 4 * 9 * BF, n2 * 4 * 9 * BF * 4);
+      tc::prefetch_l2(trace + q0 * 4 * kFS, n2 * 4 * kFS * 4);
       const int64_t e0 = q0 / a.S, ne = (q0 + n2 - 1) / a.S - e0 + 1;
       tc::prefetch_l2(reinterpret_cast<const float*>(a.Fm) + e0 * 324, (uint32_t)(ne * 324 * 4));
       tc::prefetch_l2(reinterpret_cast<const float*>(a.Fp) + e0 * 324, (uint32_t)(ne * 324 * 4));

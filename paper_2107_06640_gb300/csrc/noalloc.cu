@@ -47,7 +47,7 @@ extern "C" int adg_step_noalloc(adg_ctx* ctx, void* d_Q, int n_steps, void* stre
                    "and no gravitational or fault faces";
     return ADG_E_INVALID;
   }
-  const size_t need = (size_t)c.nt * 36 * c.Bf * (c.fp64 ? 8 : 4);
+  const size_t need = (size_t)c.nt * 4 * adg::face_stride(c.N) * (c.fp64 ? 8 : 4);
   if (need > kScratchBytes) {
     c.last_error = "adg_step_noalloc: the face traces of this mesh need " + std::to_string(need) +
                    " bytes of scratch; the fixed maximum is " + std::to_string(kScratchBytes) + " bytes";

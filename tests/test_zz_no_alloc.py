@@ -55,7 +55,7 @@ def test_noalloc_steps_match_the_context_path(lib):
 
 def test_noalloc_rejects_meshes_beyond_the_scratch_limit(lib):
     import torch
-    m, s = _periodic_context(12, 5)         # 10368 tets at N=5: 62.7 MB of traces
+    m, s = _periodic_context(12, 5)         # 10368 tets at N=5: 63.7 MB of traces
     d = torch.zeros((m.nt, 9, s.B), dtype=torch.float64, device="cuda")
     with pytest.raises(lib.AdgError) as ei:
         lib.adg_step_noalloc(s.ctx, d.data_ptr(), 1)
