@@ -68,6 +68,12 @@ def bytes_per_update(N, w):
             "neighbour_tc_kernel": (2 * 9 * B + 8 * FS + 2 * 4 * 81 + 16) * w}
 
 
+# DRAM bytes (read + write) per element of the tensor-core kernels, from the
+# full ncu capture of the 374,400-tet box (profiles/tensor_core_kernels_box40.md);
+# a launch's traffic is scaled from it by the number of elements
+TC_DRAM_BYTES_PER_ELEMENT = {"local_tc_kernel": 7250.0, "neighbour_tc_kernel": 10450.0}
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -463,6 +469,9 @@ def main():
     else:
         roof = {"bound": "hbm", "achieved": achieved_bytes, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": frac_hbm, "traffic": None, "kernel": kname, "peak_source": src}
+    if kname in TC_DRAM_BYTES_PER_ELEMENT:
+        roof["traffic"] = TC_DRAM_BYTES_PER_ELEMENT[kname] * s.nt
+        roof["traffic_note"] = "DRAM bytes per launch, ncu on the 374,400-tet box scaled by elements"
     roof.update({"ms_per_launch": kms[dom], "hbm_frac": frac_hbm, "alu_frac": frac_alu,
                  "kernel_ms": {"local": kms[0], "neighbour": kms[1]},
                  "local_tc_tensor_frac": achieved_tc / tc_peak,
