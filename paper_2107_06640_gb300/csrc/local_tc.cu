@@ -68,28 +68,6 @@ static_assert(LImg::bytes + 2 * (2 * 128 + TE * 9 * BF) * 4 + 64 <= 232448,
 // per-warpgroup TMEM columns: A hi [0, 64), A lo [64, 128), accumulators [128, 256)
 constexpr uint32_t cAh = 0, cAl = 64, cAcc = 128;
 
-__device__ __forceinline__ void mma_ts(uint32_t d, uint32_t a, uint64_t db, uint32_t idesc, uint32_t acc) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d),
-      "r"(a), "l"(db), "r"(idesc), "r"(acc));
-}
-
-// 3xTF32 product into d: A (TMEM, hi at ah, lo at al) x B^T (shared, canonical
-// K-major N x K, hi at bh, lo at bl), K / 8 steps
-__device__ __forceinline__ void issue(uint32_t d, uint32_t ah, uint32_t al, uint32_t bh, uint32_t bl, int N, int K,
-                                      bool acc_first) {
-  const uint32_t idesc = tc::idesc_tf32(128, N);
-  const uint32_t lbo = (uint32_t)(N / 8) * 128;
-  for (int kk = 0; kk < K / 8; ++kk) {
-    const uint32_t off = kk * 2 * lbo;
-    const uint64_t dbh = tc::sdesc(bh + off, lbo, 128), dbl = tc::sdesc(bl + off, lbo, 128);
-    mma_ts(d, ah + 8 * kk, dbh, idesc, (kk > 0 || acc_first) ? 1u : 0u);
-    mma_ts(d, ah + 8 * kk, dbl, idesc, 1u);
-    mma_ts(d, al + 8 * kk, dbh, idesc, 1u);
-  }
-}
-
 // three groups of 8 consecutive fp32 columns of this warp's lanes (one wait)
 __device__ __forceinline__ void ld3x8(uint32_t t0, uint32_t t1, uint32_t t2, float o[24]) {
   uint32_t r[24];
@@ -310,20 +288,20 @@ __device__ __forceinline__ bool local_tile(Lane& L, int64_t tile) {
   }
   // ---- levels 0, 1, 2 on the tensor cores
   if (!pair_round<H>(L, [&] {
-        issue(tbase + cAcc, tbase + cAh, tbase + cAl, sbase + 4 * LImg::oP0, sbase + 4 * (LImg::oP0 + LImg::sP0), kN0,
-              kK0, false);
+        tc::mma3_ts<kN0, kK0>(tbase + cAcc, tbase + cAh, tbase + cAl, sbase + 4 * LImg::oP0,
+                              sbase + 4 * (LImg::oP0 + LImg::sP0), false);
       }))
     return false;
   level_epilogue<H, kM0, kM0p, true>(trow + cAcc, trow + cAh, trow + cAl, st, L.tcf[1], I, nullptr);
   if (!pair_round<H>(L, [&] {
-        issue(tbase + cAcc, tbase + cAh, tbase + cAl, sbase + 4 * LImg::oP1, sbase + 4 * (LImg::oP1 + LImg::sP1), kN1,
-              kK1, false);
+        tc::mma3_ts<kN1, kK1>(tbase + cAcc, tbase + cAh, tbase + cAl, sbase + 4 * LImg::oP1,
+                              sbase + 4 * (LImg::oP1 + LImg::sP1), false);
       }))
     return false;
   level_epilogue<H, kM1, kM1p, true>(trow + cAcc, trow + cAh, trow + cAl, st, L.tcf[2], I, nullptr);
   if (!pair_round<H>(L, [&] {
-        issue(tbase + cAcc, tbase + cAh, tbase + cAl, sbase + 4 * LImg::oP2, sbase + 4 * (LImg::oP2 + LImg::sP2), kN2,
-              kK2, false);
+        tc::mma3_ts<kN2, kK2>(tbase + cAcc, tbase + cAh, tbase + cAl, sbase + 4 * LImg::oP2,
+                              sbase + 4 * (LImg::oP2 + LImg::sP2), false);
       }))
     return false;
   float d3[kM2p];
@@ -366,8 +344,8 @@ __device__ __forceinline__ bool local_tile(Lane& L, int64_t tile) {
 #pragma unroll
   for (int c = H; c < B / 8; c += 2) st_split8(trow + cAh + 8 * c, trow + cAl + 8 * c, I + 8 * c);
   if (!pair_round<H>(L, [&] {
-        issue(tbase + cAcc, tbase + cAh, tbase + cAl, sbase + 4 * LImg::oT, sbase + 4 * (LImg::oT + LImg::sT), kNT,
-              kK0, false);
+        tc::mma3_ts<kNT, kK0>(tbase + cAcc, tbase + cAh, tbase + cAl, sbase + 4 * LImg::oT,
+                              sbase + 4 * (LImg::oT + LImg::sT), false);
       }))
     return false;
   // traces leave face by face through shared memory, so that the stores of
@@ -416,8 +394,8 @@ __device__ __forceinline__ bool local_tile(Lane& L, int64_t tile) {
   }
   constexpr uint32_t cV = 80;  // volume accumulator: axis a, basis m at column 80 + 56 a + m
   if (!pair_round<H>(L, [&] {
-        issue(tbase + cV, tbase + 0, tbase + 40, sbase + 4 * LImg::oV, sbase + 4 * (LImg::oV + LImg::sV), kNV, 40,
-              false);
+        tc::mma3_ts<kNV, 40>(tbase + cV, tbase + 0, tbase + 40, sbase + 4 * LImg::oV,
+                             sbase + 4 * (LImg::oV + LImg::sV), false);
       }))
     return false;
   // ---- Q += volume term (face terms follow in the neighbour kernel)

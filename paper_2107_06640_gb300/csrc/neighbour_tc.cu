@@ -63,13 +63,6 @@ static_assert(NImg::bytes + 64 <= 232448, "neighbour tensor-core kernel exceeds 
 // per-warpgroup TMEM columns: G hi [0, 96), G lo [96, 192), accumulator [192, 256)
 constexpr uint32_t cGh = 0, cGl = 96, cAcc = 192;
 
-__device__ __forceinline__ void mma_ts(uint32_t d, uint32_t a, uint64_t db, uint32_t idesc, uint32_t acc) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d),
-      "r"(a), "l"(db), "r"(idesc), "r"(acc));
-}
-
 __device__ __forceinline__ void ld8(uint32_t t, float o[8]) {
   uint32_t r[8];
   asm volatile(
@@ -310,15 +303,7 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
     wg_bar(wg);
     tc::fence_after();
     if (t == 0) {
-      const uint32_t idesc = tc::idesc_tf32(128, kN);
-      constexpr uint32_t lbo = (kN / 8) * 128;
-      for (int kk = 0; kk < kK / 8; ++kk) {
-        const uint32_t off = kk * 2 * lbo;
-        const uint64_t dbh = tc::sdesc(sL + off, lbo, 128), dbl = tc::sdesc(sL + 4 * NImg::sL + off, lbo, 128);
-        mma_ts(tbase + cAcc, tbase + cGh + 8 * kk, dbh, idesc, kk > 0 ? 1u : 0u);
-        mma_ts(tbase + cAcc, tbase + cGh + 8 * kk, dbl, idesc, 1u);
-        mma_ts(tbase + cAcc, tbase + cGl + 8 * kk, dbh, idesc, 1u);
-      }
+      tc::mma3_ts<kN, kK>(tbase + cAcc, tbase + cGh, tbase + cGl, sL, sL + 4 * NImg::sL, false);
       tc::commit(&mbar[wg]);
       if (!tc::mbar_wait(&mbar[wg], phase, kWaitIters)) {
         atomicOr(a.err, ERR_TIMEOUT);

@@ -57,6 +57,33 @@ __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t da, uint64_t 
       "l"(da), "l"(db), "r"(idesc), "r"(acc));
 }
 
+// MMA with the A operand in TMEM (lane = row, one tf32 per column)
+__device__ __forceinline__ void mma_ts(uint32_t d, uint32_t a, uint64_t db, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d),
+      "r"(a), "l"(db), "r"(idesc), "r"(acc));
+}
+
+// 3xTF32 product chain into d (M = 128): A in TMEM (hi at column ah, lo at
+// al) times B^T, B canonical K-major N x K in shared memory (hi at byte
+// address bh, lo at bl); K / 8 steps of A_hi B_hi + A_hi B_lo + A_lo B_hi.
+// The descriptors are built once; a step advances their start address.
+template <int N, int K>
+__device__ __forceinline__ void mma3_ts(uint32_t d, uint32_t ah, uint32_t al, uint32_t bh, uint32_t bl,
+                                        bool acc_first) {
+  constexpr uint32_t idesc = idesc_tf32(128, N);
+  constexpr uint32_t lbo = (N / 8) * 128;
+  const uint64_t dh0 = sdesc(bh, lbo, 128), dl0 = sdesc(bl, lbo, 128);
+#pragma unroll
+  for (int kk = 0; kk < K / 8; ++kk) {
+    const uint64_t step = (uint64_t)((kk * 2 * lbo) >> 4);
+    mma_ts(d, ah + 8 * kk, dh0 + step, idesc, (kk > 0 || acc_first) ? 1u : 0u);
+    mma_ts(d, ah + 8 * kk, dl0 + step, idesc, 1u);
+    mma_ts(d, al + 8 * kk, dh0 + step, idesc, 1u);
+  }
+}
+
 __device__ __forceinline__ void commit(uint64_t* mbar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(mbar)));
 }
