@@ -83,15 +83,32 @@ template <typename T>
 void take_dofs(Ctx& c, double* Q) {
   const int64_t per = (int64_t)c.S * 9 * c.B;
   T* buf = staging<T>(c);
-  check_cuda(cudaMemcpyAsync(buf, c.dQ, (size_t)c.nt * per * sizeof(T), cudaMemcpyDeviceToHost, c.stream),
-             "dofs download");
-  check_cuda(cudaStreamSynchronize(c.stream), "dofs download");
-#pragma omp parallel for schedule(static)
-  for (int64_t i = 0; i < c.nt; ++i) {
-    const T* src = buf + i * per;
-    double* dst = Q + c.order[i] * per;
-    for (int64_t k = 0; k < per; ++k) dst[k] = (double)src[k];
+  // all chunk copies are queued at once; chunk k is converted as soon as its
+  // copy has completed, while the later chunks are still in flight
+  cudaEvent_t done[kChunks];
+  for (int64_t ch = 0; ch < kChunks; ++ch) {
+    const int64_t i0 = c.nt * ch / kChunks, i1 = c.nt * (ch + 1) / kChunks;
+    check_cuda(cudaEventCreateWithFlags(&done[ch], cudaEventDisableTiming), "dofs download");
+    check_cuda(cudaMemcpyAsync(buf + i0 * per, (const T*)c.dQ + i0 * per, (size_t)(i1 - i0) * per * sizeof(T),
+                               cudaMemcpyDeviceToHost, c.stream),
+               "dofs download");
+    check_cuda(cudaEventRecord(done[ch], c.stream), "dofs download");
   }
+  cudaError_t err = cudaSuccess;
+  for (int64_t ch = 0; ch < kChunks; ++ch) {
+    const int64_t i0 = c.nt * ch / kChunks, i1 = c.nt * (ch + 1) / kChunks;
+    if (err == cudaSuccess) err = cudaEventSynchronize(done[ch]);
+    if (err == cudaSuccess) {
+#pragma omp parallel for schedule(static)
+      for (int64_t i = i0; i < i1; ++i) {
+        const T* src = buf + i * per;
+        double* dst = Q + c.order[i] * per;
+        for (int64_t k = 0; k < per; ++k) dst[k] = (double)src[k];
+      }
+    }
+  }
+  for (int64_t ch = 0; ch < kChunks; ++ch) cudaEventDestroy(done[ch]);
+  check_cuda(err, "dofs download");
 }
 
 void run_ticks_to_boundary(Ctx& c) {

@@ -68,48 +68,6 @@ static_assert(LImg::bytes + 2 * (2 * 128 + TE * 9 * BF) * 4 + 64 <= 232448,
 // per-warpgroup TMEM columns: A hi [0, 64), A lo [64, 128), accumulators [128, 256)
 constexpr uint32_t cAh = 0, cAl = 64, cAcc = 128;
 
-// three groups of 8 consecutive fp32 columns of this warp's lanes (one wait)
-__device__ __forceinline__ void ld3x8(uint32_t t0, uint32_t t1, uint32_t t2, float o[24]) {
-  uint32_t r[24];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%24];\n"
-      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8,%9,%10,%11,%12,%13,%14,%15}, [%25];\n"
-      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%16,%17,%18,%19,%20,%21,%22,%23}, [%26];\n"
-      "tcgen05.wait::ld.sync.aligned;\n"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23])
-      : "r"(t0), "r"(t1), "r"(t2));
-#pragma unroll
-  for (int j = 0; j < 24; ++j) o[j] = __uint_as_float(r[j]);
-}
-
-__device__ __forceinline__ void ld8(uint32_t t, float o[8]) {
-  uint32_t r[8];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
-      "tcgen05.wait::ld.sync.aligned;\n"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-      : "r"(t));
-#pragma unroll
-  for (int j = 0; j < 8; ++j) o[j] = __uint_as_float(r[j]);
-}
-
-// 8 values of this lane's row -> tf32 hi at column th, lo at column tl
-__device__ __forceinline__ void st_split8(uint32_t th, uint32_t tl, const float x[8]) {
-  uint32_t h[8], l[8];
-#pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    const float hh = tc::tf32_trunc(x[j]);
-    h[j] = __float_as_uint(hh);
-    l[j] = __float_as_uint(x[j] - hh);
-  }
-  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(th), "r"(h[0]),
-               "r"(h[1]), "r"(h[2]), "r"(h[3]), "r"(h[4]), "r"(h[5]), "r"(h[6]), "r"(h[7]));
-  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(tl), "r"(l[0]),
-               "r"(l[1]), "r"(l[2]), "r"(l[3]), "r"(l[4]), "r"(l[5]), "r"(l[6]), "r"(l[7]));
-}
-
 // Per-thread star-product data: the quantity p of this lane's row, the lanes
 // of the quantities each output reads and their material coefficients.
 // D^{k+1}[p] = sum_d c_d X_d[src_d] with X_d = sum_a (dxi_a/dx_d) Y_a, the
@@ -178,7 +136,7 @@ __device__ __forceinline__ void level_epilogue(uint32_t tacc, uint32_t tah, uint
 #pragma unroll
   for (int mc = H; mc < MP / 8; mc += 2) {
     float y[24];
-    ld3x8(tacc + 8 * mc, tacc + MP + 8 * mc, tacc + 2 * MP + 8 * mc, y);
+    tc::ld3x8(tacc + 8 * mc, tacc + MP + 8 * mc, tacc + 2 * MP + 8 * mc, y);
     float d[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
@@ -191,7 +149,7 @@ __device__ __forceinline__ void level_epilogue(uint32_t tacc, uint32_t tah, uint
         d[j] = 0.f;
       }
     }
-    if (TO_A) st_split8(tah + 8 * mc, tal + 8 * mc, d);
+    if (TO_A) tc::st_split8(tah + 8 * mc, tal + 8 * mc, d);
   }
 }
 
@@ -284,7 +242,7 @@ __device__ __forceinline__ bool local_tile(Lane& L, int64_t tile) {
     x[4] = x1.x; x[5] = x1.y; x[6] = x1.z; x[7] = x1.w;
 #pragma unroll
     for (int j = 0; j < 8; ++j) I[8 * c + j] = L.tcf[0] * x[j];
-    st_split8(trow + cAh + 8 * c, trow + cAl + 8 * c, x);
+    tc::st_split8(trow + cAh + 8 * c, trow + cAl + 8 * c, x);
   }
   // ---- levels 0, 1, 2 on the tensor cores
   if (!pair_round<H>(L, [&] {
@@ -342,7 +300,7 @@ __device__ __forceinline__ bool local_tile(Lane& L, int64_t tile) {
 
   // ---- face traces: T = I E^T (N = 4 x 21)
 #pragma unroll
-  for (int c = H; c < B / 8; c += 2) st_split8(trow + cAh + 8 * c, trow + cAl + 8 * c, I + 8 * c);
+  for (int c = H; c < B / 8; c += 2) tc::st_split8(trow + cAh + 8 * c, trow + cAl + 8 * c, I + 8 * c);
   if (!pair_round<H>(L, [&] {
         tc::mma3_ts<kNT, kK0>(tbase + cAcc, tbase + cAh, tbase + cAl, sbase + 4 * LImg::oT,
                               sbase + 4 * (LImg::oT + LImg::sT), false);
@@ -353,18 +311,21 @@ __device__ __forceinline__ bool local_tile(Lane& L, int64_t tile) {
   // per half) that hold the rows of three elements share a buffer
   {
     const int nmine = nE - 3 * L.w < 3 ? nE - 3 * L.w : 3;  // elements of this warp (may be <= 0)
+    // this half's chunks c = H, H + 2, ... of the 88 trace columns, read once
+    float tv[48];
+    tc::ld3x8(trow + cAcc + 8 * H, trow + cAcc + 8 * (H + 2), trow + cAcc + 8 * (H + 4), tv);
+    tc::ld3x8(trow + cAcc + 8 * (H + 6), trow + cAcc + 8 * (H + 8), trow + cAcc + 8 * (H == 0 ? 10 : 9), tv + 24);
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
 #pragma unroll
-      for (int c = H; c < 11; c += 2) {
+      for (int cj = 0; cj < (H == 0 ? 6 : 5); ++cj) {
+        const int c = H + 2 * cj;
         if (8 * c + 7 < BF * f || 8 * c >= BF * (f + 1)) continue;  // chunk outside face f
-        float x[8];
-        ld8(trow + cAcc + 8 * c, x);
         if (valid) {
 #pragma unroll
           for (int j = 0; j < 8; ++j) {
             const int col = 8 * c + j;
-            if (col >= BF * f && col < BF * (f + 1)) L.sT[(jj * 9 + p) * BF + col - BF * f] = x[j];
+            if (col >= BF * f && col < BF * (f + 1)) L.sT[(jj * 9 + p) * BF + col - BF * f] = tv[8 * cj + j];
           }
         }
       }
@@ -380,7 +341,7 @@ __device__ __forceinline__ bool local_tile(Lane& L, int64_t tile) {
   // ---- volume: W_a = K_a I (l < 35) for the three axes in one product,
   // then Q += sum_a A*_a W_a = -sum_d c_d X_d[src_d] (Jacobian form)
 #pragma unroll
-  for (int c = H; c < 5; c += 2) st_split8(trow + 8 * c, trow + 40 + 8 * c, I + 8 * c);
+  for (int c = H; c < 5; c += 2) tc::st_split8(trow + 8 * c, trow + 40 + 8 * c, I + 8 * c);
   // the dofs rows for the update are requested before the round
   float4 qv[8];
 #pragma unroll
@@ -402,7 +363,7 @@ __device__ __forceinline__ bool local_tile(Lane& L, int64_t tile) {
 #pragma unroll
   for (int c = H; c < B / 8; c += 2) {
     float y[24];
-    ld3x8(trow + cV + 8 * c, trow + cV + B + 8 * c, trow + cV + 2 * B + 8 * c, y);
+    tc::ld3x8(trow + cV + 8 * c, trow + cV + B + 8 * c, trow + cV + 2 * B + 8 * c, y);
     float x[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) x[j] = -star_apply(st, y[j], y[8 + j], y[16 + j]);

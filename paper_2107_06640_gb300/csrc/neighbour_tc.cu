@@ -9,7 +9,8 @@
 //   1. the own and the neighbours' time-integrated traces of face f are
 //      copied asynchronously (cp.async, double-buffered over the faces) into
 //      shared memory as they are stored, [element][quantity][node];
-//   2. work item (element, node triplet) forms, for its three nodes,
+//   2. work item (element, node triplet, group of 3 output rows p) forms, for its
+//      three nodes and rows,
 //        G[p][n] = s_f (sum_q F-[p][q] V_own[q][n] + sum_q F+[p][q] V_nbr[q][perm n])
 //      (s_f = 2|S_f|/|J|, F rows broadcast from the staged F-/F+ of the tile)
 //      and writes the 9 values to a transposition buffer [element][p][24];
@@ -42,7 +43,7 @@ constexpr int kStage = TE * kFS;      // floats per staged face array
 constexpr int kGrow = 24;             // transposed flux row: 21 nodes + 3 zero
 constexpr int kG = TE * 9 * kGrow;    // floats per transposition buffer
 constexpr int kTrip = 7;              // node triplets (n, n + 7, n + 14) per element face
-constexpr int kItems = TE * kTrip;    // work items per face (84 <= 128 threads)
+constexpr int kItems = TE * kTrip * 3;  // work items per face: element x node triplet x 3 output rows
 
 struct NImg {
   static constexpr int oL = 0, sL = kN * kK;                  // lift hi, lo
@@ -62,31 +63,6 @@ static_assert(NImg::bytes + 64 <= 232448, "neighbour tensor-core kernel exceeds 
 
 // per-warpgroup TMEM columns: G hi [0, 96), G lo [96, 192), accumulator [192, 256)
 constexpr uint32_t cGh = 0, cGl = 96, cAcc = 192;
-
-__device__ __forceinline__ void ld8(uint32_t t, float o[8]) {
-  uint32_t r[8];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
-      "tcgen05.wait::ld.sync.aligned;\n"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-      : "r"(t));
-#pragma unroll
-  for (int j = 0; j < 8; ++j) o[j] = __uint_as_float(r[j]);
-}
-
-__device__ __forceinline__ void st_split8(uint32_t th, uint32_t tl, const float x[8]) {
-  uint32_t h[8], l[8];
-#pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    const float hh = tc::tf32_trunc(x[j]);
-    h[j] = __float_as_uint(hh);
-    l[j] = __float_as_uint(x[j] - hh);
-  }
-  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(th), "r"(h[0]),
-               "r"(h[1]), "r"(h[2]), "r"(h[3]), "r"(h[4]), "r"(h[5]), "r"(h[6]), "r"(h[7]));
-  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(tl), "r"(l[0]),
-               "r"(l[1]), "r"(l[2]), "r"(l[3]), "r"(l[4]), "r"(l[5]), "r"(l[6]), "r"(l[7]));
-}
 
 __device__ __forceinline__ void wg_bar(int wg) { asm volatile("bar.sync %0, 128;" ::"r"(wg + 1)); }
 
@@ -228,11 +204,13 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
       const float* sVo = sStage + (f & 1) * 2 * kStage;
       const float* sVn = sVo + kStage;
       float* gbuf = sG + (f & 1) * kG;
-      // ---- work items (element, node triplet): scaled flux of the three nodes
-      if (t < kItems) {
-        const int ei = t / kTrip, k = t - ei * kTrip;
+      // ---- work items (element, node triplet, three output rows): scaled flux
+#pragma unroll 1
+      for (int item = t; item < kItems; item += 128) {
+        const int ei = item / (3 * kTrip), rem = item - ei * (3 * kTrip);
+        const int k = rem / 3, pg = rem - 3 * k;  // node triplet, group of output rows
         const int el = (int)((v0 + ei) / a.S - v0 / a.S);
-        const float* Fm = sFm + (el * 4 + f) * 81;
+        const float* Fm = sFm + (el * 4 + f) * 81 + 27 * pg;
         const float* Fp = Fm + TE * 324;
         const float sc = ei < nE ? sPr[el * PAR + 12 + f] : 0.f;
         const int* perm = sPerm + sPm[f * TE + ei] * BF;
@@ -253,9 +231,9 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
             vn[u][qq] = nn[pn[u]];
           }
         }
-        float* gout = gbuf + ei * 9 * kGrow;
+        float* gout = gbuf + (ei * 9 + 3 * pg) * kGrow;
 #pragma unroll
-        for (int pp = 0; pp < 9; ++pp) {
+        for (int pp = 0; pp < 3; ++pp) {
           float g[3] = {0.f, 0.f, 0.f};
 #pragma unroll
           for (int qq = 0; qq < 9; ++qq) {
@@ -279,7 +257,7 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
 #pragma unroll
             for (int jn = 0; jn < 8; ++jn) g[jn] = 0.f;
           }
-          st_split8(trow + cGh + 24 * f + 8 * c, trow + cGl + 24 * f + 8 * c, g);
+          tc::st_split8(trow + cGh + 24 * f + 8 * c, trow + cGl + 24 * f + 8 * c, g);
         }
       }
     }
@@ -317,19 +295,23 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
     tc::fence_after();
     // ---- Q -= lift
 #pragma unroll
-    for (int c = 0; c < B / 8; ++c) {
-      float x[8];
-      ld8(trow + cAcc + 8 * c, x);
-      if (valid) {
-        float nq[8];
+    for (int c3 = 0; c3 < 3; ++c3) {  // chunks 3 c3 .. 3 c3 + 2 (the last group repeats chunk 6)
+      float x3[24];
+      tc::ld3x8(trow + cAcc + 24 * c3, trow + cAcc + 24 * c3 + 8, trow + cAcc + (c3 < 2 ? 24 * c3 + 16 : 48), x3);
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          nq[j] = q[8 * c + j] - x[j];
-          bad |= !isfinite(nq[j]);
+      for (int cc = 0; cc < 3; ++cc) {
+        const int c = 3 * c3 + cc;
+        if (c < B / 8 && valid) {
+          float nq[8];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            nq[j] = q[8 * c + j] - x3[8 * cc + j];
+            bad |= !isfinite(nq[j]);
+          }
+          float4* dst = reinterpret_cast<float4*>(Qrow + 8 * c);
+          dst[0] = make_float4(nq[0], nq[1], nq[2], nq[3]);
+          dst[1] = make_float4(nq[4], nq[5], nq[6], nq[7]);
         }
-        float4* dst = reinterpret_cast<float4*>(Qrow + 8 * c);
-        dst[0] = make_float4(nq[0], nq[1], nq[2], nq[3]);
-        dst[1] = make_float4(nq[4], nq[5], nq[6], nq[7]);
       }
     }
     tc::fence_before();
