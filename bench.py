@@ -184,14 +184,28 @@ def cpu_sample_run(seconds, steps=None):
     return m.nt * n / el, m.nt, n, el
 
 
-def cpu_baseline(seconds=12.0):
-    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+def _oracle_sample(seconds, threads):
+    t = str(threads)
+    env = dict(os.environ, OPENBLAS_NUM_THREADS=t, OMP_NUM_THREADS=t, MKL_NUM_THREADS=t)
     code = ("import sys, json; sys.path.insert(0, %r); import bench; v, nt, n, el = bench.cpu_sample_run(%f); "
             "print(json.dumps([v, nt, n, el]))" % (ROOT, seconds))
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=600)
-    v, nt, n, el = json.loads(r.stdout.strip().splitlines()[-1])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline(seconds=12.0):
+    """The oracle on the host: one thread, and the same sample with the BLAS
+    threads on all cores (the element loops of the oracle are numpy batched
+    products, so the threads split the elements)."""
+    v, nt, n, el = _oracle_sample(seconds, 1)
+    ncores = os.cpu_count() or 1
+    va, _, na, ela = _oracle_sample(seconds, ncores)
     return {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{nt}-tet 6x6-column piece of the same box (N=5, FP64, numpy), {n} global steps in {el:.1f} s, single thread"}
+            "sample": f"{nt}-tet 6x6-column piece of the same box (N=5, FP64, numpy), {n} global steps in {el:.1f} s, single thread",
+            "all_cores": {"value": va, "unit": UNIT, "cores": ncores,
+                          "sample": f"same piece, {na} global steps in {ela:.1f} s, BLAS threads = {ncores}",
+                          "note": "the oracle's batched 56 x 56 products gain nothing from BLAS threads; it has "
+                                  "no element-parallel loop of its own"}}
 
 
 def run_reference(args, rank):
@@ -406,8 +420,9 @@ def main():
         # per-kernel durations (CUDA events on the library stream)
         kms, kcnt = pkg._lib.adg_profile(s.ctx, 2)
         res[prec] = dict(solver=s, ms=ms, steps=steps, upd=upd, kms=kms, kcnt=kcnt,
-                         clocks=cs.summary(local), launches=int(kcnt.sum() // 2))
-        if prec != HEAD:
+                         clocks=cs.summary(local), launches=int(kcnt.sum() // 2),
+                         advanced=warm + steps + 2)
+        if prec not in (HEAD, pkg.ADG_FP64):
             del s
             res[prec]["solver"] = None
     r32 = res[HEAD]                # headline: FP32 dofs, reference-matrix products on the tensor cores
@@ -418,6 +433,22 @@ def main():
     value64 = upd * world * r64["steps"] / (r64["ms"] * 1e-3)
     rcc = res[pkg.ADG_FP32]
     value_cc = upd * world * rcc["steps"] / (rcc["ms"] * 1e-3)
+
+    # accuracy of the headline form against FP64 after the same steps from the same input
+    s64 = res[pkg.ADG_FP64]["solver"]
+    n64 = res[pkg.ADG_FP64]["advanced"]
+    sa = Solver(m.xyz, m.tets, m.face_tag, rho, lam, mu, degree=N_DEG, precision=HEAD, cfl=0.35,
+                device=local, stream=stream.cuda_stream)
+    sa.set_dofs(Q0)
+    sa.set_eta(np.zeros((int(sa.info.n_gravity_faces), 1, sa.Bf)))
+    sa.advance(n64)
+    q64, qa = s64.get_dofs(), sa.get_dofs()
+    h64, ha = s64.read_ssh(), sa.read_ssh()
+    accuracy = {"steps": n64, "against": "ADG_FP64 on the same input",
+                "dofs_rel_l2": float(np.linalg.norm(qa - q64) / np.linalg.norm(q64)),
+                "ssh_rel_l2": float(np.linalg.norm(ha - h64) / max(np.linalg.norm(h64), 1e-300))}
+    del q64, qa, sa, s64
+    res[pkg.ADG_FP64]["solver"] = None
 
     # e2e through the public API with host buffers: upload dofs, one step, download
     s = r32["solver"]
@@ -495,6 +526,7 @@ def main():
                  "local_kernel_tflops": fp64_alu, "fp64_peak_tflops_nominal": 1.25,
                  "kernel_ms": {"local": r64k[0], "neighbour": r64k[1]}, "clocks": r64["clocks"]},
         "roofline": roof,
+        "accuracy": accuracy,
         "clocks": clk,
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": bytes_q, "d2h_bytes_per_step": bytes_q,
                 "steps": args.e2e_steps, "note": "adg_set_dofs + adg_advance(1) + adg_get_dofs, host double arrays"},

@@ -501,6 +501,18 @@ void Ctx::setup() {
   n_bslots = nb_slots;
   n_dslots = nd_slots;
   n_gslots = ng;
+  // the tensor-core kernels handle only same-cluster neighbours and linear
+  // boundaries: check that the ordering gave them nothing else
+  if (tc)
+    for (int c = 0; c < ncl; ++c)
+      for (int64_t i = cl_begin[c]; i < cl_begin[c] + cl_plain[c]; ++i) {
+        bool ok = bslot[i] < 0;
+        for (int f = 0; f < 4; ++f) {
+          const int kind = (ninfo[i * 4 + f] >> 5) & 7;
+          ok = ok && gslot[i * 4 + f] < 0 && dslot[i * 4 + f] < 0 && (kind == NK_SAME || kind == NK_NONE);
+        }
+        if (!ok) throw Err(ADG_E_STATE, "internal: element order for the tensor-core kernels is inconsistent");
+      }
   // ---- fault faces: one entry per tet pair, minus side = lower user tet index,
   // listed in internal (cluster) order; both sides share a cluster by construction
   fface.clear(); fgeo.clear(); fminus_user.clear(); fplus_user.clear();

@@ -138,21 +138,34 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
 
   // Neighbour trace blocks of a tile's faces, then one cp.async group with the
   // tile's F-/F+ matrices, element parameters and face 0 (staging buffer 0).
-  auto prefetch = [&](int64_t tl) {
+  // Thread t < 48 owns (face t / 12, element t % 12) of a tile: its neighbour
+  // information, loaded early (meta_load) and made the tile's trace-block
+  // table later (prefetch).
+  auto meta_load = [&](int64_t tl, int& info, int& nbe) {
+    info = 0;
+    nbe = 0;
+    const int64_t pv0 = a.v_begin + tl * TE, prem = n_virtual - tl * TE;
+    if (t < 4 * TE) {
+      const int f = t / TE, ei = t - f * TE;
+      if (ei < prem) {
+        const int64_t ee = (pv0 + ei) / a.S;
+        info = a.ninfo[ee * 4 + f];
+        nbe = a.nbr[ee * 4 + f];
+      }
+    }
+  };
+  auto prefetch = [&](int64_t tl, int info, int nbe) {
     const int64_t pv0 = a.v_begin + tl * TE, prem = n_virtual - tl * TE;
     const int pnE = (int)(prem < TE ? prem : TE);
     if (t < 4 * TE) {
-      const int f = t / TE, ei = t - f * TE;
+      const int ei = t - (t / TE) * TE;
       long long nb = -1;
       int pm = 0;
-      if (ei < pnE) {
+      if (ei < pnE && ((info >> 5) & 7) == NK_SAME) {
         const int64_t ve = pv0 + ei, ee = ve / a.S;
-        const int info = a.ninfo[ee * 4 + f];
-        if (((info >> 5) & 7) == NK_SAME) {
-          const int64_t vn_e = (int64_t)a.nbr[ee * 4 + f] * a.S + (ve - ee * a.S);
-          nb = (vn_e * 4 + (info & 3)) * kFS;
-          pm = (info >> 2) & 7;
-        }
+        const int64_t vn_e = (int64_t)nbe * a.S + (ve - ee * a.S);
+        nb = (vn_e * 4 + (info & 3)) * kFS;
+        pm = (info >> 2) & 7;
       }
       sNb[t] = nb;
       sPm[t] = pm;
@@ -172,8 +185,15 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
   };
 
   int64_t tile = (int64_t)blockIdx.x * 2 + wg;
-  if (tile < ntiles) prefetch(tile);
+  if (tile < ntiles) {
+    int info0, nbe0;
+    meta_load(tile, info0, nbe0);
+    prefetch(tile, info0, nbe0);
+  }
   for (; tile < ntiles; tile += (int64_t)gridDim.x * 2) {
+    const int64_t next = tile + (int64_t)gridDim.x * 2;
+    int info_n = 0, nbe_n = 0;  // the next tile's neighbour information, needed after the faces
+    if (next < ntiles) meta_load(next, info_n, nbe_n);
     const int64_t v0 = a.v_begin + tile * TE;
     const int64_t nrem = n_virtual - tile * TE;
     const int nE = (int)(nrem < TE ? nrem : TE);
@@ -200,7 +220,15 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
       } else {
         cp_wait<0>();
       }
+      if (f == 2) {  // the rows of faces 0 and 1 are in TMEM: their lift starts now
+        asm volatile("tcgen05.wait::st.sync.aligned;");
+        tc::fence_before();
+      }
       wg_bar(wg);
+      if (f == 2 && t == 0) {
+        tc::fence_after();
+        tc::mma3_ts<kN, 48>(tbase + cAcc, tbase + cGh, tbase + cGl, sL, sL + 4 * NImg::sL, false);
+      }
       const float* sVo = sStage + (f & 1) * 2 * kStage;
       const float* sVn = sVo + kStage;
       float* gbuf = sG + (f & 1) * kG;
@@ -262,8 +290,7 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
       }
     }
     // ---- the next tile's loads overlap this tile's lift and dofs update
-    const int64_t next = tile + (int64_t)gridDim.x * 2;
-    if (next < ntiles) prefetch(next);
+    if (next < ntiles) prefetch(next, info_n, nbe_n);
     // and the tile after it into L2
     const int64_t next2 = next + (int64_t)gridDim.x * 2;
     if (t == 0 && next2 < ntiles) {
@@ -275,13 +302,13 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
       tc::prefetch_l2(reinterpret_cast<const float*>(a.Fm) + e0 * 324, (uint32_t)(ne * 324 * 4));
       tc::prefetch_l2(reinterpret_cast<const float*>(a.Fp) + e0 * 324, (uint32_t)(ne * 324 * 4));
     }
-    // ---- lift on the tensor cores
+    // ---- lift of faces 2 and 3 on the tensor cores (faces 0 and 1 were issued above)
     asm volatile("tcgen05.wait::st.sync.aligned;");
     tc::fence_before();
     wg_bar(wg);
     tc::fence_after();
     if (t == 0) {
-      tc::mma3_ts<kN, kK>(tbase + cAcc, tbase + cGh, tbase + cGl, sL, sL + 4 * NImg::sL, false);
+      tc::mma3_ts<kN, kK, 48>(tbase + cAcc, tbase + cGh, tbase + cGl, sL, sL + 4 * NImg::sL, true);
       tc::commit(&mbar[wg]);
       if (!tc::mbar_wait(&mbar[wg], phase, kWaitIters)) {
         atomicOr(a.err, ERR_TIMEOUT);

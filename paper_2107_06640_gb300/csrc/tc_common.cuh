@@ -69,16 +69,17 @@ __device__ __forceinline__ void mma_ts(uint32_t d, uint32_t a, uint64_t db, uint
 // al) times B^T, B canonical K-major N x K in shared memory (hi at byte
 // address bh, lo at bl); K / 8 steps of A_hi B_hi + A_hi B_lo + A_lo B_hi.
 // The descriptors are built once; a step advances their start address.
-template <int N, int K>
+// K0 (a multiple of 8) starts the chain part-way through K.
+template <int N, int K, int K0 = 0>
 __device__ __forceinline__ void mma3_ts(uint32_t d, uint32_t ah, uint32_t al, uint32_t bh, uint32_t bl,
                                         bool acc_first) {
   constexpr uint32_t idesc = idesc_tf32(128, N);
   constexpr uint32_t lbo = (N / 8) * 128;
   const uint64_t dh0 = sdesc(bh, lbo, 128), dl0 = sdesc(bl, lbo, 128);
 #pragma unroll
-  for (int kk = 0; kk < K / 8; ++kk) {
+  for (int kk = K0 / 8; kk < K / 8; ++kk) {
     const uint64_t step = (uint64_t)((kk * 2 * lbo) >> 4);
-    mma_ts(d, ah + 8 * kk, dh0 + step, idesc, (kk > 0 || acc_first) ? 1u : 0u);
+    mma_ts(d, ah + 8 * kk, dh0 + step, idesc, (kk > K0 / 8 || acc_first) ? 1u : 0u);
     mma_ts(d, ah + 8 * kk, dl0 + step, idesc, 1u);
     mma_ts(d, al + 8 * kk, dh0 + step, idesc, 1u);
   }
