@@ -8,7 +8,8 @@
 // 3w+j, quantity p; lanes 27..31 zero).  Per tile and face f:
 //   1. the own and the neighbours' time-integrated traces of face f are
 //      copied asynchronously (cp.async, double-buffered over the faces) into
-//      shared memory as they are stored, [element][quantity][node];
+//      shared memory as they are stored, [element][quantity][node] (element
+//      stride padded against bank conflicts);
 //   2. work item (element, node triplet, group of 3 output rows p) forms, for its
 //      three nodes and rows,
 //        G[p][n] = s_f (sum_q F-[p][q] V_own[q][n] + sum_q F+[p][q] V_nbr[q][perm n])
@@ -39,7 +40,9 @@ constexpr int kWaitIters = 1 << 24;
 constexpr int kK = 96;          // 4 faces x 24 columns (21 nodes + 3 zero)
 constexpr int kN = 64;          // 56 basis functions, padded
 constexpr int kFS = face_stride(5);   // floats per face block in the trace array (192)
-constexpr int kStage = TE * kFS;      // floats per staged face array
+constexpr int kSS = kFS + 8;          // staged floats per element face: the 8 extra put the two
+                                      // elements a warp's work items span on different banks
+constexpr int kStage = TE * kSS;      // floats per staged face array
 constexpr int kGrow = 24;             // transposed flux row: 21 nodes + 3 zero
 constexpr int kG = TE * 9 * kGrow;    // floats per transposition buffer
 constexpr int kTrip = 7;              // node triplets (n, n + 7, n + 14) per element face
@@ -55,8 +58,8 @@ struct NImg {
   static constexpr int sF = 2 * TE * 324;
   static constexpr int oPar = oF + 2 * sF;                    // per warpgroup: element parameters
   static constexpr int sPar = TE * PAR;
-  static constexpr int oG = oPar + 2 * sPar;                  // per warpgroup: 2 transposition buffers
-  static constexpr int floats = oG + 2 * 2 * kG;
+  static constexpr int oG = oPar + 2 * sPar;                  // per warpgroup: transposition buffer
+  static constexpr int floats = oG + 2 * kG;
   static constexpr int bytes = floats * 4;
 };
 static_assert(NImg::bytes + 64 <= 232448, "neighbour tensor-core kernel exceeds the shared memory of one CTA");
@@ -89,8 +92,8 @@ __device__ __forceinline__ void stage_face(int f, int t, int64_t v0, int nE, con
       const bool ok = ei < nE;
       const long long nb = nbase[f * TE + ei];
       const bool okn = ok && nb >= 0;
-      cp16(so + ei * kFS + 4 * ch, trace + ((v0 + (ok ? ei : 0)) * 4 + f) * kFS + 4 * ch, ok);
-      cp16(sn + ei * kFS + 4 * ch, trace + (okn ? nb : 0) + 4 * ch, okn);
+      cp16(so + ei * kSS + 4 * ch, trace + ((v0 + (ok ? ei : 0)) * 4 + f) * kFS + 4 * ch, ok);
+      cp16(sn + ei * kSS + 4 * ch, trace + (okn ? nb : 0) + 4 * ch, okn);
     }
   }
 }
@@ -129,8 +132,10 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
   const float* trace = reinterpret_cast<const float*>(a.trace);
   float* sFm = sm + NImg::oF + wg * NImg::sF;  // [element - e0][face][81], F+ at + TE * 324
   float* sPr = sm + NImg::oPar + wg * NImg::sPar;
-  float* sG = sm + NImg::oG + wg * 2 * kG;     // [buffer][element][p][24]
-  for (int r = t; r < 2 * kG; r += 128) sG[r] = 0.f;  // columns 21..23 stay zero
+  // [element][p][24]; one buffer: face f + 1's items start after the barrier
+  // that every thread reaches only when its rows of face f are done
+  float* sG = sm + NImg::oG + wg * kG;
+  for (int r = t; r < kG; r += 128) sG[r] = 0.f;  // columns 21..23 stay zero
   const int jj = lane / 9, p = lane - 9 * (lane / 9);
   const int64_t ntiles = (n_virtual + TE - 1) / TE;
   uint32_t phase = 0;
@@ -231,7 +236,7 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
       }
       const float* sVo = sStage + (f & 1) * 2 * kStage;
       const float* sVn = sVo + kStage;
-      float* gbuf = sG + (f & 1) * kG;
+      float* gbuf = sG;
       // ---- work items (element, node triplet, three output rows): scaled flux
 #pragma unroll 1
       for (int item = t; item < kItems; item += 128) {
@@ -251,8 +256,8 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
         float vo[3][9], vn[3][9];
 #pragma unroll
         for (int qq = 0; qq < 9; ++qq) {
-          const float* o = sVo + ei * kFS + qq * BF;
-          const float* nn = sVn + ei * kFS + qq * BF;
+          const float* o = sVo + ei * kSS + qq * BF;
+          const float* nn = sVn + ei * kSS + qq * BF;
 #pragma unroll
           for (int u = 0; u < 3; ++u) {
             vo[u][qq] = o[nd[u]];
