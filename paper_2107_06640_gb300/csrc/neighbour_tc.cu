@@ -14,7 +14,7 @@
 //      three nodes and rows,
 //        G[p][n] = s_f (sum_q F-[p][q] V_own[q][n] + sum_q F+[p][q] V_nbr[q][perm n])
 //      (s_f = 2|S_f|/|J|, F rows broadcast from the staged F-/F+ of the tile)
-//      and writes the 9 values to a transposition buffer [element][p][24];
+//      and writes the 9 values to a transposition buffer [element][p][28];
 //   3. the thread of row (element, p) takes its 24 columns, splits them into
 //      tf32 hi + lo and writes them to TMEM columns 24 f + n.
 // One MMA chain then lifts all four faces:
@@ -43,7 +43,8 @@ constexpr int kFS = face_stride(5);   // floats per face block in the trace arra
 constexpr int kSS = kFS + 8;          // staged floats per element face: the 8 extra put the two
                                       // elements a warp's work items span on different banks
 constexpr int kStage = TE * kSS;      // floats per staged face array
-constexpr int kGrow = 24;             // transposed flux row: 21 nodes + 3 zero
+constexpr int kGrow = 28;             // transposed flux row: 21 nodes + 7 zero; 28 floats put the 8
+                                      // rows of a quarter warp's 16-byte reads on distinct banks
 constexpr int kG = TE * 9 * kGrow;    // floats per transposition buffer
 constexpr int kTrip = 7;              // node triplets (n, n + 7, n + 14) per element face
 constexpr int kItems = TE * kTrip * 3;  // work items per face: element x node triplet x 3 output rows
@@ -132,10 +133,10 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
   const float* trace = reinterpret_cast<const float*>(a.trace);
   float* sFm = sm + NImg::oF + wg * NImg::sF;  // [element - e0][face][81], F+ at + TE * 324
   float* sPr = sm + NImg::oPar + wg * NImg::sPar;
-  // [element][p][24]; one buffer: face f + 1's items start after the barrier
+  // [element][p][28]; one buffer: face f + 1's items start after the barrier
   // that every thread reaches only when its rows of face f are done
   float* sG = sm + NImg::oG + wg * kG;
-  for (int r = t; r < kG; r += 128) sG[r] = 0.f;  // columns 21..23 stay zero
+  for (int r = t; r < kG; r += 128) sG[r] = 0.f;  // columns 21..27 stay zero
   const int jj = lane / 9, p = lane - 9 * (lane / 9);
   const int64_t ntiles = (n_virtual + TE - 1) / TE;
   uint32_t phase = 0;
