@@ -221,7 +221,7 @@ __device__ __forceinline__ bool local_tile(Lane& L, int64_t tile) {
 
   // the next tile of this slot into L2 while this one is worked on
   if (H == 0 && L.t == 0) {
-    const int64_t nt = tile + (int64_t)gridDim.x * 2;
+    const int64_t nt = tile + (int64_t)gridDim.x * 4;
     if (nt * TE < L.n_virtual) {
       const int64_t nrem2 = L.n_virtual - nt * TE;
       tc::prefetch_l2(L.Q + (L.v_begin + nt * TE) * 9 * B, (uint32_t)((nrem2 < TE ? nrem2 : TE) * 9 * B * 4));
