@@ -71,7 +71,7 @@ def bytes_per_update(N, w):
 # DRAM bytes (read + write) per element of the tensor-core kernels, from the
 # full ncu capture of the 374,400-tet box (profiles/tensor_core_kernels_box40.md);
 # a launch's traffic is scaled from it by the number of elements
-TC_DRAM_BYTES_PER_ELEMENT = {"local_tc_kernel": 7250.0, "neighbour_tc_kernel": 10450.0}
+TC_DRAM_BYTES_PER_ELEMENT = {"local_tc_kernel": 7253.0, "neighbour_tc_kernel": 10510.0}
 
 
 def load_peaks():
@@ -503,7 +503,9 @@ def main():
     if kname in TC_DRAM_BYTES_PER_ELEMENT:
         roof["traffic"] = TC_DRAM_BYTES_PER_ELEMENT[kname] * s.nt
         roof["traffic_note"] = "DRAM bytes per launch, ncu on the 374,400-tet box scaled by elements"
-    roof.update({"ms_per_launch": kms[dom], "hbm_frac": frac_hbm, "alu_frac": frac_alu,
+    roof.update({"ms_per_launch": kms[dom], "hbm_frac": frac_hbm,
+                 # the CUDA-core ALU fraction of a tensor-core kernel's whole flop count means nothing
+                 "alu_frac": None if kname.endswith("_tc_kernel") else frac_alu,
                  "kernel_ms": {"local": kms[0], "neighbour": kms[1]},
                  "local_tc_tensor_frac": achieved_tc / tc_peak,
                  "local_hbm_frac": by["local_tc_kernel"] * s.nt / (kms[0] * 1e-3) / 1e9 / peaks["hbm_gbs"],
