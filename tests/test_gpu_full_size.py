@@ -1,0 +1,127 @@
+"""GPU parity at the full sizes the benchmark runs, on sampled outputs the
+oracle recomputes one by one: after one step, the update of an element only
+reads its own and its face neighbours' state, so the oracle steps a small mesh
+made of the sampled elements and their neighbours (tests._cases.submesh)."""
+
+import numpy as np
+import pytest
+
+import synthetic as syn
+from tests._cases import node_chi, oracle_eta_at_nodes, rel_l2, submesh, to_oracle_layout
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2107_06640_gb300 import build
+    build.build()
+
+
+def _eta_to_oracle(o, sub, keep, gmap, eta_nodes, N):
+    """Hand the oracle the library's nodal sea-surface values through their
+    P_N interpolant on every gravitational face of the small mesh."""
+    mono = [(a, b) for a in range(N + 1) for b in range(N + 1 - a)]
+    Vn = np.array([[x ** a * y ** b for (a, b) in mono] for x, y in node_chi(N)])
+    Vq = np.array([[x ** a * y ** b for (a, b) in mono] for x, y in o.chi])
+    for i, e in enumerate(keep):
+        for f in range(4):
+            if sub.face_tag[i, f] == syn.TAG_GRAVITY:
+                o.eta[i, f] = Vq @ np.linalg.solve(Vn, eta_nodes[gmap[int(e) * 4 + f]])
+
+
+def test_full_size_ensemble_sampled():
+    """The ensemble workload's mesh (1,019,304-tet coupled box, N = 5) in the
+    tensor-core 3xTF32 form with 4 scenarios, each with its own seeded dofs and
+    sea-surface uplift (8 Gaussian bumps): one step, then 30 sampled elements
+    (random, at the sea surface, at the sea floor) of every scenario against the
+    oracle.  Tolerance as for the 1.5 M-tet box in this form (1e-5)."""
+    from oracle.ader import Oracle
+    from paper_2107_06640_gb300 import ADG_3XTF32, Solver
+    from synthetic.workloads import coupled_box, uplift_scenarios
+    m, mat = coupled_box(nxy=66)
+    assert m.nt == 1019304
+    S = 4
+    rho, lam, mu = mat
+    s = Solver(m.xyz, m.tets, m.face_tag, rho, lam, mu, degree=5, cfl=0.35, precision=ADG_3XTF32, ensemble=S)
+    rng = np.random.default_rng(21)
+    Q0 = rng.standard_normal((m.nt, S, 9, s.B)) * 1e-3
+    s.set_dofs(Q0)
+    ef, nxyz = s.gravity_faces()
+    eta0 = np.stack([f(nxyz[..., 0], nxyz[..., 1]) for f in uplift_scenarios(S, seed=3)], axis=1)
+    s.set_eta(eta0)
+    s.advance(1)
+    Q1 = s.get_dofs()
+    eta1 = s.read_ssh()
+    wet = m.hex_index[:, 2] >= 35
+    top = np.nonzero(np.any(m.face_tag == syn.TAG_GRAVITY, axis=1))[0]
+    floor = np.nonzero(wet & (m.hex_index[:, 2] == 35))[0]
+    pick = np.concatenate([rng.choice(m.nt, 10, replace=False), rng.choice(top, 10, replace=False),
+                           rng.choice(floor, 10, replace=False)])
+    sub, smat, keep, pos = submesh(m, mat, pick)
+    o = Oracle(sub.xyz, sub.tets, sub.face_tag, sub.face_partner, *smat, 5, cfl=0.35, dt=s.info.dt_min)
+    gmap = {int(v): g for g, v in enumerate(ef)}
+    sel = pos[pick]
+    for k in range(S):
+        o.Q = np.ascontiguousarray(np.transpose(Q0[keep, k], (0, 2, 1)))
+        o.eta[:] = 0.0
+        _eta_to_oracle(o, sub, keep, gmap, eta0[:, k], 5)
+        o.t = 0.0
+        o.step_gts()
+        got = to_oracle_layout(Q1[pick, k])
+        assert rel_l2(got, o.Q[sel]) <= 1e-5, (k, rel_l2(got, o.Q[sel]))
+        for i, e in enumerate(keep):
+            if pos[e] not in set(sel):
+                continue
+            for f in range(4):
+                if sub.face_tag[i, f] == syn.TAG_GRAVITY:
+                    want = oracle_eta_at_nodes(o, [i * 4 + f], node_chi(5), 5)[0]
+                    assert rel_l2(eta1[gmap[int(e) * 4 + f], k], want) <= 1e-6
+
+
+def test_full_size_megathrust_sampled():
+    """The megathrust workload at its benchmark size (3,732,480 tets, N = 4,
+    15-degree fault under a 2 km ocean with gravity, rate-and-state friction) in
+    the form the benchmark runs (FP32 dofs, FP64 friction): one step from seeded
+    dofs, then 25 sampled elements on both sides of the fault and 5 elsewhere
+    against the oracle, and the fault state (slip rate, state, slip) of every
+    fault face whose two sides are in the small mesh.  Tolerances: FP32 dofs
+    and traces, one step (2e-5 dofs, 1e-4 fault state, relative L2)."""
+    from oracle import rupture as ru
+    from oracle.ader import Oracle
+    from paper_2107_06640_gb300 import ADG_FP32, Solver, _lib
+    from synthetic.workloads import fault_box, rs_fault_params
+    r = 3
+    m, mat = fault_box(nx=32 * r, ny=40 * r, nz=16 * r, dz=1e3 / r, dip_deg=15.0, ocean_layers=2 * r, water=2e3)
+    assert m.nt == 3732480
+    rho, lam, mu = mat
+    s = Solver(m.xyz, m.tets, m.face_tag, rho, lam, mu, degree=4, cfl=0.35, precision=ADG_FP32)
+    nff = int(s.info.n_fault_faces)
+    mf, pf, fxyz, fn = _lib.adg_fault_faces(s.ctx, nff, s.Bf)
+    par = rs_fault_params(fxyz, fn, seed=0, patch_center=fxyz.reshape(-1, 3).mean(0), patch_radius=8e3)
+    _lib.adg_set_fault(s.ctx, par[:, None])
+    rng = np.random.default_rng(31)
+    Q0 = rng.standard_normal((m.nt, 9, s.B)) * np.array([1e5] * 6 + [1e-2] * 3)[None, :, None]
+    s.set_dofs(Q0)
+    ef, _ = s.gravity_faces()
+    s.set_eta(np.zeros((len(ef), 1, s.Bf)))
+    s.advance(1)
+    Q1 = s.get_dofs()
+    st = np.empty((nff, 1, s.Bf, 8))
+    st = _lib.adg_read_fault(s.ctx, st)[:, 0]
+    faces = rng.choice(nff, 25, replace=False)
+    pick = np.unique(np.concatenate([mf[faces[:15]] // 4, pf[faces[15:]] // 4, rng.choice(m.nt, 5, replace=False)]))
+    sub, smat, keep, pos = submesh(m, mat, pick)
+    o = Oracle(sub.xyz, sub.tets, sub.face_tag, sub.face_partner, *smat, 4, cfl=0.35, dt=s.info.dt_min)
+    lib_face = {int(v): k for k, v in enumerate(mf)}
+    idx = np.array([lib_face[int(keep[e]) * 4 + int(f)] for e, f in o.fm])
+    assert np.allclose(o.f_xyz, fxyz[idx], rtol=0, atol=1e-6)
+    o.set_fault({k: par[idx, :, i] for i, k in enumerate(ru.PARAMS)})
+    o.Q = to_oracle_layout(Q0[keep])
+    o.step_gts()
+    sel = pos[pick]
+    got = to_oracle_layout(Q1[pick])
+    assert rel_l2(got, o.Q[sel]) <= 2e-5, rel_l2(got, o.Q[sel])
+    assert rel_l2(st[idx, :, 0], o.fault["V"]) <= 1e-4
+    assert rel_l2(st[idx, :, 1], o.fault["psi"]) <= 1e-4
+    assert rel_l2(st[idx, :, 2:5], o.fault["slip"]) <= 1e-4
