@@ -22,6 +22,7 @@ import argparse
 import json
 import os
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -95,6 +96,10 @@ def alu_peak_tflops(fp64, sm_mhz):
     if fp64:
         return 1.25 * sm_mhz / 2070.0
     return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+# where the nvidia-smi clock samples of each timed region are written (--clock-dir)
+CLOCK_DIR = [tempfile.gettempdir()]
 
 
 class ClockSampler:
@@ -239,8 +244,7 @@ def _timed_advance(s, steps, warm, stream, torch, tag):
     s.advance(warm)
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else "_work",
-                                   f"clocks_{tag}.csv")) as cs:
+    with ClockSampler(os.path.join(CLOCK_DIR[0], f"clocks_{tag}.csv")) as cs:
         ev0.record(stream)
         s.advance(steps)
         ev1.record(stream)
@@ -353,7 +357,12 @@ def main():
                     help="profiling aid: run one precision of the coupled workload, print no JSON line")
     ap.add_argument("--workload", default="coupled", choices=["coupled", "lts", "rupture", "ensemble"],
                     help="coupled: the headline line; lts / rupture / ensemble: the other workloads")
+    ap.add_argument("--clock-dir", default=None,
+                    help="directory for the nvidia-smi clock samples of each timed region (default: the temp dir)")
     args = ap.parse_args()
+    if args.clock_dir:
+        os.makedirs(args.clock_dir, exist_ok=True)
+        CLOCK_DIR[0] = args.clock_dir
     if args.workload != "coupled":
         run_other_workload(args)
         return
@@ -416,8 +425,7 @@ def main():
         s.advance(warm)
         barrier()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        with ClockSampler(os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else "_work",
-                                       f"clocks_r{rank}_{prec}.csv")) as cs:
+        with ClockSampler(os.path.join(CLOCK_DIR[0], f"clocks_r{rank}_{prec}.csv")) as cs:
             ev0.record(stream)
             s.advance(steps)
             ev1.record(stream)
