@@ -18,7 +18,8 @@
 //     are exchanged with warp shuffles);
 //   levels 3, 4 (4 and 1 rows) on the CUDA cores from registers;
 //   I = sum_k dt^{k+1}/(k+1)! D^k in registers (Eq. taylor);
-//   traces V_f = E_f I on the tensor cores, written to the trace array;
+//   traces V_f = E_f I on the tensor cores, staged per face in shared memory
+//     and written to the trace array with bulk copies (cp.async.bulk);
 //   volume: W_a = K_a I for the three axes on the tensor cores, then
 //     Q += sum_a A*_a W_a on the CUDA cores (Jacobian form, shuffles).
 // A CTA keeps two tiles in flight (TMEM columns [0, 256) and [256, 512)), each
@@ -41,6 +42,11 @@ constexpr int FS = face_stride(5);  // 192 floats per face block of the trace ar
 constexpr int TE = 12;          // elements per tile
 constexpr int kThreadsL = 512;  // two tiles in flight, two warpgroups (halves) per tile
 constexpr int kWaitIters = 1 << 24;
+// trace staging: one face of a warp pair's three elements, element blocks of
+// kTS floats (16-byte aligned, the face block's 189 values then zeros); two
+// buffers alternate over the faces
+constexpr int kTS = 196;
+constexpr int kTB = 3 * kTS;
 
 // tensor-core predictor levels: K (rows of D^k, padded to 8), rows of D^{k+1}
 // per axis (padded to 8), N = 3 axes (padded to 16)
@@ -62,7 +68,7 @@ struct LImg {
   static constexpr int floats = ((oK4 + 12 + 3) / 4) * 4;
   static constexpr int bytes = floats * 4;
 };
-static_assert(LImg::bytes + 2 * (2 * 128 + TE * 9 * BF) * 4 + 64 <= 232448,
+static_assert(LImg::bytes + 2 * (2 * 128 + 4 * 2 * kTB) * 4 + 64 <= 232448,
               "operands exceed the shared memory of one CTA");
 
 // per-warpgroup TMEM columns: A hi [0, 64), A lo [64, 128), accumulators [128, 256)
@@ -173,7 +179,7 @@ struct Lane {
   const float* k3;
   const float* k4;
   float* sX;          // [128][2] rows 8, 9 of D^3 handed from half 1 to half 0
-  float* sT;          // [3][9][21] one face of this warp's three elements' traces, as stored in memory
+  float* sT;          // [2][3][kTS] two buffers: one face of this warp's three elements' traces
   uint64_t* mbar;     // this slot's barrier
   int* abort;         // this slot's abort flag
   uint32_t phase;
@@ -306,17 +312,20 @@ __device__ __forceinline__ bool local_tile(Lane& L, int64_t tile) {
                               sbase + 4 * (LImg::oT + LImg::sT), false);
       }))
     return false;
-  // traces leave face by face through shared memory, so that the stores of
-  // every element's contiguous face block are coalesced; the two warps (one
-  // per half) that hold the rows of three elements share a buffer
+  // traces leave face by face: the rows go to a shared buffer laid out like
+  // the element's face block in memory, then one thread of the warp pair
+  // copies each element's block with a bulk copy; two buffers alternate, the
+  // copier waits until the copy before the last has read its buffer
   {
     const int nmine = nE - 3 * L.w < 3 ? nE - 3 * L.w : 3;  // elements of this warp (may be <= 0)
+    const bool copier = H == 0 && L.lane == 0;
     // this half's chunks c = H, H + 2, ... of the 88 trace columns, read once
     float tv[48];
     tc::ld3x8(trow + cAcc + 8 * H, trow + cAcc + 8 * (H + 2), trow + cAcc + 8 * (H + 4), tv);
     tc::ld3x8(trow + cAcc + 8 * (H + 6), trow + cAcc + 8 * (H + 8), trow + cAcc + 8 * (H == 0 ? 10 : 9), tv + 24);
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
+      float* sTf = L.sT + (f & 1) * kTB;
 #pragma unroll
       for (int cj = 0; cj < (H == 0 ? 6 : 5); ++cj) {
         const int c = H + 2 * cj;
@@ -325,16 +334,18 @@ __device__ __forceinline__ bool local_tile(Lane& L, int64_t tile) {
 #pragma unroll
           for (int j = 0; j < 8; ++j) {
             const int col = 8 * c + j;
-            if (col >= BF * f && col < BF * (f + 1)) L.sT[(jj * 9 + p) * BF + col - BF * f] = tv[8 * cj + j];
+            if (col >= BF * f && col < BF * (f + 1)) sTf[jj * kTS + p * BF + col - BF * f] = tv[8 * cj + j];
           }
         }
       }
+      tc::fence_async_smem();
+      if (copier) tc::bulk_wait_read();  // the other buffer is free for face f + 1
       warp_pair_bar(L.slot, L.w);
-      for (int r = H * 32 + L.lane; r < nmine * 9 * BF; r += 64) {
-        const int ej = r / (9 * BF);
-        L.trace[((v0 + 3 * L.w + ej) * 4 + f) * FS + (r - ej * 9 * BF)] = L.sT[r];
+      if (copier) {
+        for (int ej = 0; ej < nmine; ++ej)
+          tc::bulk_store(L.trace + ((v0 + 3 * L.w + ej) * 4 + f) * FS, sTf + ej * kTS, FS * 4);
+        tc::bulk_commit();
       }
-      warp_pair_bar(L.slot, L.w);
     }
   }
 
@@ -387,7 +398,7 @@ __global__ void __launch_bounds__(kThreadsL, 1) local_tc_kernel(StepArgs a, int6
   __shared__ __align__(8) uint64_t mbar[2];
   __shared__ int s_abort[2];
   __shared__ float sX[2][2 * 128];
-  __shared__ __align__(16) float sT[2][4][3 * 9 * BF];
+  __shared__ __align__(16) float sT[2][4][2 * kTB];
 
   const int tid = threadIdx.x, slot = tid >> 8, half = (tid >> 7) & 1;
   {
@@ -395,6 +406,7 @@ __global__ void __launch_bounds__(kThreadsL, 1) local_tc_kernel(StepArgs a, int6
     float4* dst = reinterpret_cast<float4*>(sm);
     for (int r = tid; r < LImg::floats / 4; r += kThreadsL) dst[r] = src[r];
   }
+  for (int r = tid; r < 2 * 4 * 2 * kTB; r += kThreadsL) (&sT[0][0][0])[r] = 0.f;
   if (tid < 2) {
     tc::mbar_init(&mbar[tid], 1);
     s_abort[tid] = 0;
@@ -437,6 +449,7 @@ __global__ void __launch_bounds__(kThreadsL, 1) local_tc_kernel(StepArgs a, int6
   // after a timed-out wait, give this slot's MMAs in flight a bounded chance
   // to finish before the columns are freed
   if (half == 0 && L.t == 0 && s_abort[slot]) tc::mbar_wait(&mbar[slot], L.phase ^ 1u, kWaitIters);
+  if (half == 0 && L.lane == 0) tc::bulk_wait();  // trace copies complete before shared memory is released
   tc::fence_before();
   __syncthreads();
   tc::fence_after();

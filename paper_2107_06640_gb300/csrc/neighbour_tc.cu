@@ -206,15 +206,6 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
     const int i = 3 * w + jj;
     const bool valid = lane < 27 && i < nE;
     const int64_t v = v0 + (valid ? i : 0);
-    // the dofs row is needed only at the end: load it first
-    float* Qrow = reinterpret_cast<float*>(a.Q) + (v * 9 + p) * B;
-    float q[B];
-#pragma unroll
-    for (int c = 0; c < B / 4; ++c) {
-      float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (valid) x = *reinterpret_cast<const float4*>(Qrow + 4 * c);
-      q[4 * c] = x.x; q[4 * c + 1] = x.y; q[4 * c + 2] = x.z; q[4 * c + 3] = x.w;
-    }
 #pragma unroll 1
     for (int f = 0; f < 4; ++f) {
       // ---- stage face f + 1 while face f is used
@@ -294,6 +285,16 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
           tc::st_split8(trow + cGh + 24 * f + 8 * c, trow + cGl + 24 * f + 8 * c, g);
         }
       }
+    }
+    // the dofs row (in L2 from the prefetch two tiles back) is loaded while
+    // the next tile's copies are issued and the lift runs
+    float* Qrow = reinterpret_cast<float*>(a.Q) + (v * 9 + p) * B;
+    float q[B];
+#pragma unroll
+    for (int c = 0; c < B / 4; ++c) {
+      float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (valid) x = *reinterpret_cast<const float4*>(Qrow + 4 * c);
+      q[4 * c] = x.x; q[4 * c + 1] = x.y; q[4 * c + 2] = x.z; q[4 * c + 3] = x.w;
     }
     // ---- the next tile's loads overlap this tile's lift and dofs update
     if (next < ntiles) prefetch(next, info_n, nbe_n);
