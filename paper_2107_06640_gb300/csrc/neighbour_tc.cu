@@ -140,7 +140,7 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
   const int jj = lane / 9, p = lane - 9 * (lane / 9);
   const int64_t ntiles = (n_virtual + TE - 1) / TE;
   uint32_t phase = 0;
-  bool bad = false;
+  float bad = 0.f;  // stays 0 while every updated dof is finite (x * 0 is NaN for x = inf, NaN)
 
   // Neighbour trace blocks of a tile's faces, then one cp.async group with the
   // tile's F-/F+ matrices, element parameters and face 0 (staging buffer 0).
@@ -340,7 +340,7 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
 #pragma unroll
           for (int j = 0; j < 8; ++j) {
             nq[j] = q[8 * c + j] - x3[8 * cc + j];
-            bad |= !isfinite(nq[j]);
+            bad = fmaf(nq[j], 0.f, bad);
           }
           float4* dst = reinterpret_cast<float4*>(Qrow + 8 * c);
           dst[0] = make_float4(nq[0], nq[1], nq[2], nq[3]);
@@ -350,7 +350,7 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
     }
     tc::fence_before();
   }
-  if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(a.err, ERR_NAN);
+  if (__any_sync(0xffffffffu, bad != 0.f) && lane == 0) atomicOr(a.err, ERR_NAN);
   if (t == 0 && s_abort[wg]) tc::mbar_wait(&mbar[wg], phase ^ 1u, kWaitIters);
   tc::fence_before();
   __syncthreads();

@@ -247,6 +247,22 @@ def test_nan_is_reported():
     assert ei.value.code == -6
 
 
+
+def test_nan_is_reported_by_the_tensor_core_kernels():
+    """A NaN in one dof of a periodic cube (every element on the tensor-core
+    kernels) is reported after the step, in the first tile and in the last."""
+    from paper_2107_06640_gb300 import AdgError, Solver, ADG_3XTF32
+    m, mat = syn.unit_cube_periodic(4), syn.materials.elastic_uniform(384)
+    for e in (5, 383):
+        s = Solver(m.xyz, m.tets, m.face_tag, *mat, face_partner=m.face_partner, degree=5, cfl=0.5,
+                   precision=ADG_3XTF32)
+        Q = np.zeros((m.nt, 9, s.B))
+        Q[e, 4, 17] = np.nan
+        s.set_dofs(Q)
+        with pytest.raises(AdgError) as ei:
+            s.advance(1)
+        assert ei.value.code == -6
+
 @pytest.mark.parametrize("precision,tol", [(0, FP64_TOL), (2, 1e-5)])
 def test_full_size_coupled_box_sampled(precision, tol):
     """The 1.5 M-tet coupled ocean-crust box at N=5 (the benchmark workload),
