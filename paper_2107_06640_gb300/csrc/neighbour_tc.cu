@@ -99,6 +99,9 @@ __device__ __forceinline__ void stage_face(int f, int t, int64_t v0, int nE, con
   }
 }
 
+// kOne: one scenario (S = 1), where a virtual element is its element and the
+// 64-bit divisions by S drop out
+template <bool kOne>
 __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, int64_t n_virtual) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   float* sm = reinterpret_cast<float*>(smem_raw);
@@ -138,6 +141,8 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
   float* sG = sm + NImg::oG + wg * kG;
   for (int r = t; r < kG; r += 128) sG[r] = 0.f;  // columns 21..27 stay zero
   const int jj = lane / 9, p = lane - 9 * (lane / 9);
+  const int S = kOne ? 1 : a.S;
+  auto elem = [&](int64_t vv) -> int64_t { return kOne ? vv : vv / S; };  // element of a virtual element
   const int64_t ntiles = (n_virtual + TE - 1) / TE;
   uint32_t phase = 0;
   float bad = 0.f;  // stays 0 while every updated dof is finite (x * 0 is NaN for x = inf, NaN)
@@ -154,7 +159,7 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
     if (t < 4 * TE) {
       const int f = t / TE, ei = t - f * TE;
       if (ei < prem) {
-        const int64_t ee = (pv0 + ei) / a.S;
+        const int64_t ee = elem(pv0 + ei);
         info = a.ninfo[ee * 4 + f];
         nbe = a.nbr[ee * 4 + f];
       }
@@ -168,8 +173,8 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
       long long nb = -1;
       int pm = 0;
       if (ei < pnE && ((info >> 5) & 7) == NK_SAME) {
-        const int64_t ve = pv0 + ei, ee = ve / a.S;
-        const int64_t vn_e = (int64_t)nbe * a.S + (ve - ee * a.S);
+        const int64_t ve = pv0 + ei, ee = elem(ve);
+        const int64_t vn_e = (int64_t)nbe * S + (ve - ee * S);
         nb = (vn_e * 4 + (info & 3)) * kFS;
         pm = (info >> 2) & 7;
       }
@@ -177,8 +182,8 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
       sPm[t] = pm;
     }
     wg_bar(wg);
-    const int64_t e0 = pv0 / a.S;
-    const int ne = (int)((pv0 + pnE - 1) / a.S - e0 + 1);
+    const int64_t e0 = elem(pv0);
+    const int ne = (int)(elem(pv0 + pnE - 1) - e0 + 1);
     // F-, F+ rows of elements e0 .. e0 + ne - 1: ne x 1296 bytes each, 16-byte aligned
     for (int cc = t; cc < ne * 81; cc += 128) {
       cp16(sFm + 4 * cc, reinterpret_cast<const float*>(a.Fm) + e0 * 324 + 4 * cc);
@@ -206,6 +211,7 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
     const int i = 3 * w + jj;
     const bool valid = lane < 27 && i < nE;
     const int64_t v = v0 + (valid ? i : 0);
+    const int r0 = kOne ? 0 : (int)(v0 - elem(v0) * S);  // scenario of the tile's first virtual element
 #pragma unroll 1
     for (int f = 0; f < 4; ++f) {
       // ---- stage face f + 1 while face f is used
@@ -234,7 +240,7 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
       for (int item = t; item < kItems; item += 128) {
         const int ei = item / (3 * kTrip), rem = item - ei * (3 * kTrip);
         const int k = rem / 3, pg = rem - 3 * k;  // node triplet, group of output rows
-        const int el = (int)((v0 + ei) / a.S - v0 / a.S);
+        const int el = kOne ? ei : (r0 + ei) / S;  // element of item's virtual element, from the tile's first
         const float* Fm = sFm + (el * 4 + f) * 81 + 27 * pg;
         const float* Fp = Fm + TE * 324;
         const float sc = ei < nE ? sPr[el * PAR + 12 + f] : 0.f;
@@ -305,7 +311,7 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
       const uint32_t n2 = (uint32_t)(rem2 < TE ? rem2 : TE);
       tc::prefetch_l2(reinterpret_cast<const float*>(a.Q) + q0 * 9 * B, n2 * 9 * B * 4);
       tc::prefetch_l2(trace + q0 * 4 * kFS, n2 * 4 * kFS * 4);
-      const int64_t e0 = q0 / a.S, ne = (q0 + n2 - 1) / a.S - e0 + 1;
+      const int64_t e0 = elem(q0), ne = elem(q0 + n2 - 1) - e0 + 1;
       tc::prefetch_l2(reinterpret_cast<const float*>(a.Fm) + e0 * 324, (uint32_t)(ne * 324 * 4));
       tc::prefetch_l2(reinterpret_cast<const float*>(a.Fp) + e0 * 324, (uint32_t)(ne * 324 * 4));
     }
@@ -364,7 +370,10 @@ int launch_neighbour_tc(const StepArgs& a, int64_t n_virtual, int n_sms, void* s
   static bool configured = false;
   if (!configured) {
     cudaError_t ce =
-        cudaFuncSetAttribute(neighbour_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, NImg::bytes);
+        cudaFuncSetAttribute(neighbour_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, NImg::bytes);
+    if (ce == cudaSuccess)
+      ce = cudaFuncSetAttribute(neighbour_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                NImg::bytes);
     if (ce != cudaSuccess) return (int)ce;
     configured = true;
   }
@@ -372,7 +381,10 @@ int launch_neighbour_tc(const StepArgs& a, int64_t n_virtual, int n_sms, void* s
   const int64_t ntiles = (n_virtual + TE - 1) / TE;
   const int64_t want = (ntiles + 1) / 2;
   const unsigned grid = (unsigned)(want < n_sms ? want : n_sms);
-  neighbour_tc_kernel<<<grid, kThreadsN, NImg::bytes, (cudaStream_t)stream>>>(a, n_virtual);
+  if (a.S == 1)
+    neighbour_tc_kernel<true><<<grid, kThreadsN, NImg::bytes, (cudaStream_t)stream>>>(a, n_virtual);
+  else
+    neighbour_tc_kernel<false><<<grid, kThreadsN, NImg::bytes, (cudaStream_t)stream>>>(a, n_virtual);
   return (int)cudaGetLastError();
 }
 
