@@ -5,13 +5,14 @@
 //
 // Same tile as the local tensor-core kernel: 12 (virtual) elements x 9
 // quantities = 128 TMEM lanes (warp w: elements 3w..3w+2, lane 9j+p = element
-// 3w+j, quantity p; lanes 27..31 zero).  Per tile and face f:
+// 3w+j, quantity p; lanes 27..31 zero).  A CTA keeps two tiles in flight, each
+// worked on by two warpgroups (256 threads).  Per tile and face f:
 //   1. the own and the neighbours' time-integrated traces of face f are
 //      copied asynchronously (cp.async, double-buffered over the faces) into
 //      shared memory as they are stored, [element][quantity][node] (element
 //      stride padded against bank conflicts);
-//   2. work item (element, node triplet, group of 3 output rows p) forms, for its
-//      three nodes and rows,
+//   2. work item (element, node triplet, group of 3 output rows p), one per
+//      thread of the tile, forms for its three nodes and rows
 //        G[p][n] = s_f (sum_q F-[p][q] V_own[q][n] + sum_q F+[p][q] V_nbr[q][perm n])
 //      (s_f = 2|S_f|/|J|, F rows broadcast from the staged F-/F+ of the tile)
 //      and writes the 9 values to a transposition buffer [element][p][28];
@@ -35,7 +36,7 @@ namespace {
 
 constexpr int B = 56, BF = 21;
 constexpr int TE = 12;
-constexpr int kThreadsN = 256;  // two warpgroups, one tile each
+constexpr int kThreadsN = 512;  // two tiles in flight, two warpgroups (halves) per tile
 constexpr int kWaitIters = 1 << 24;
 constexpr int kK = 96;          // 4 faces x 24 columns (21 nodes + 3 zero)
 constexpr int kN = 64;          // 56 basis functions, padded
@@ -52,23 +53,24 @@ constexpr int kItems = TE * kTrip * 3;  // work items per face: element x node t
 struct NImg {
   static constexpr int oL = 0, sL = kN * kK;                  // lift hi, lo
   static constexpr int oPerm = oL + 2 * sL;                   // 6 x 21 ints
-  static constexpr int oMeta = oPerm + 128;                   // per warpgroup: [face][element] int64 + int
+  static constexpr int oMeta = oPerm + 128;                   // per tile slot: [face][element] int64 + int
   static constexpr int sMeta = 4 * TE * 3;
-  static constexpr int oStage = oMeta + 2 * sMeta;            // per warpgroup: 2 buffers x (own, nbr)
-  static constexpr int oF = oStage + 2 * 4 * kStage;          // per warpgroup: F- then F+ of the tile
+  static constexpr int oStage = oMeta + 2 * sMeta;            // per tile slot: 2 buffers x (own, nbr)
+  static constexpr int oF = oStage + 2 * 4 * kStage;          // per tile slot: F- then F+ of the tile
   static constexpr int sF = 2 * TE * 324;
-  static constexpr int oPar = oF + 2 * sF;                    // per warpgroup: element parameters
+  static constexpr int oPar = oF + 2 * sF;                    // per tile slot: element parameters
   static constexpr int sPar = TE * PAR;
-  static constexpr int oG = oPar + 2 * sPar;                  // per warpgroup: transposition buffer
+  static constexpr int oG = oPar + 2 * sPar;                  // per tile slot: transposition buffer
   static constexpr int floats = oG + 2 * kG;
   static constexpr int bytes = floats * 4;
 };
 static_assert(NImg::bytes + 64 <= 232448, "neighbour tensor-core kernel exceeds the shared memory of one CTA");
 
-// per-warpgroup TMEM columns: G hi [0, 96), G lo [96, 192), accumulator [192, 256)
+// per-slot TMEM columns: G hi [0, 96), G lo [96, 192), accumulator [192, 256)
 constexpr uint32_t cGh = 0, cGl = 96, cAcc = 192;
 
-__device__ __forceinline__ void wg_bar(int wg) { asm volatile("bar.sync %0, 128;" ::"r"(wg + 1)); }
+// the 256 threads (two warpgroups) of a tile slot
+__device__ __forceinline__ void slot_bar(int slot) { asm volatile("bar.sync %0, 256;" ::"r"(slot + 1)); }
 
 // asynchronous 16-byte copy global -> shared; zero fill when !valid
 __device__ __forceinline__ void cp16(void* dst, const void* src, bool valid = true) {
@@ -79,15 +81,16 @@ __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_grou
 template <int NPEND>
 __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(NPEND)); }
 
-// Stage face f of a tile: own traces and the neighbours' traces of that face,
-// both as stored (one 16-byte aligned face block [quantity][node] per
-// element); the neighbour's node order is applied when the values are read.
-__device__ __forceinline__ void stage_face(int f, int t, int64_t v0, int nE, const float* trace,
+// Stage face f of a tile (thread u of the slot's 256): own traces and the
+// neighbours' traces of that face, both as stored (one 16-byte aligned face
+// block [quantity][node] per element); the neighbour's node order is applied
+// when the values are read.
+__device__ __forceinline__ void stage_face(int f, int u, int64_t v0, int nE, const float* trace,
                                            const long long* nbase, float* so, float* sn) {
   constexpr int kChunks = kFS / 4;  // 16-byte chunks per face block
 #pragma unroll
-  for (int it = 0; it < (TE * kChunks + 127) / 128; ++it) {
-    const int r = t + 128 * it;
+  for (int it = 0; it < (TE * kChunks + 255) / 256; ++it) {
+    const int r = u + 256 * it;
     if (r < TE * kChunks) {
       const int ei = r / kChunks, ch = r - ei * kChunks;
       const bool ok = ei < nE;
@@ -110,7 +113,9 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
   __shared__ __align__(8) uint64_t mbar[2];
   __shared__ int s_abort[2];
 
-  const int tid = threadIdx.x, wg = tid >> 7, t = tid & 127, w = t >> 5, lane = tid & 31;
+  // slot: tile in flight; half: warpgroup within the slot; u: thread within the slot
+  const int tid = threadIdx.x, slot = tid >> 8, half = (tid >> 7) & 1;
+  const int u = tid & 255, t = tid & 127, w = t >> 5, lane = tid & 31;
   {
     const float4* src = reinterpret_cast<const float4*>(a.tc_lift);
     float4* dst = reinterpret_cast<float4*>(sm + NImg::oL);
@@ -127,19 +132,19 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
   __syncthreads();
   tc::fence_after();
 
-  const uint32_t tbase = tmem_base + (uint32_t)wg * 256u;
+  const uint32_t tbase = tmem_base + (uint32_t)slot * 256u;
   const uint32_t trow = tbase + ((uint32_t)(32 * w) << 16);
   const uint32_t sL = tc::smem_u32(sm + NImg::oL);
-  float* sStage = sm + NImg::oStage + wg * 4 * kStage;  // buffer b: own at 2b, nbr at 2b + 1
-  long long* sNb = reinterpret_cast<long long*>(sm + NImg::oMeta + wg * NImg::sMeta);
+  float* sStage = sm + NImg::oStage + slot * 4 * kStage;  // buffer b: own at 2b, nbr at 2b + 1
+  long long* sNb = reinterpret_cast<long long*>(sm + NImg::oMeta + slot * NImg::sMeta);
   int* sPm = reinterpret_cast<int*>(sNb + 4 * TE);
   const float* trace = reinterpret_cast<const float*>(a.trace);
-  float* sFm = sm + NImg::oF + wg * NImg::sF;  // [element - e0][face][81], F+ at + TE * 324
-  float* sPr = sm + NImg::oPar + wg * NImg::sPar;
+  float* sFm = sm + NImg::oF + slot * NImg::sF;  // [element - e0][face][81], F+ at + TE * 324
+  float* sPr = sm + NImg::oPar + slot * NImg::sPar;
   // [element][p][28]; one buffer: face f + 1's items start after the barrier
   // that every thread reaches only when its rows of face f are done
-  float* sG = sm + NImg::oG + wg * kG;
-  for (int r = t; r < kG; r += 128) sG[r] = 0.f;  // columns 21..27 stay zero
+  float* sG = sm + NImg::oG + slot * kG;
+  for (int r = u; r < kG; r += 256) sG[r] = 0.f;  // columns 21..27 stay zero
   const int jj = lane / 9, p = lane - 9 * (lane / 9);
   const int S = kOne ? 1 : a.S;
   auto elem = [&](int64_t vv) -> int64_t { return kOne ? vv : vv / S; };  // element of a virtual element
@@ -147,17 +152,17 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
   uint32_t phase = 0;
   float bad = 0.f;  // stays 0 while every updated dof is finite (x * 0 is NaN for x = inf, NaN)
 
-  // Neighbour trace blocks of a tile's faces, then one cp.async group with the
-  // tile's F-/F+ matrices, element parameters and face 0 (staging buffer 0).
-  // Thread t < 48 owns (face t / 12, element t % 12) of a tile: its neighbour
-  // information, loaded early (meta_load) and made the tile's trace-block
-  // table later (prefetch).
+  // Neighbour trace blocks of a tile's faces, then one cp.async group per
+  // thread with the tile's F-/F+ matrices, element parameters and face 0
+  // (staging buffer 0).  Thread u < 48 owns (face u / 12, element u % 12) of
+  // a tile: its neighbour information, loaded early (meta_load) and made the
+  // tile's trace-block table later (prefetch).
   auto meta_load = [&](int64_t tl, int& info, int& nbe) {
     info = 0;
     nbe = 0;
     const int64_t pv0 = a.v_begin + tl * TE, prem = n_virtual - tl * TE;
-    if (t < 4 * TE) {
-      const int f = t / TE, ei = t - f * TE;
+    if (u < 4 * TE) {
+      const int f = u / TE, ei = u - f * TE;
       if (ei < prem) {
         const int64_t ee = elem(pv0 + ei);
         info = a.ninfo[ee * 4 + f];
@@ -168,8 +173,8 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
   auto prefetch = [&](int64_t tl, int info, int nbe) {
     const int64_t pv0 = a.v_begin + tl * TE, prem = n_virtual - tl * TE;
     const int pnE = (int)(prem < TE ? prem : TE);
-    if (t < 4 * TE) {
-      const int ei = t - (t / TE) * TE;
+    if (u < 4 * TE) {
+      const int ei = u - (u / TE) * TE;
       long long nb = -1;
       int pm = 0;
       if (ei < pnE && ((info >> 5) & 7) == NK_SAME) {
@@ -178,24 +183,24 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
         nb = (vn_e * 4 + (info & 3)) * kFS;
         pm = (info >> 2) & 7;
       }
-      sNb[t] = nb;
-      sPm[t] = pm;
+      sNb[u] = nb;
+      sPm[u] = pm;
     }
-    wg_bar(wg);
+    slot_bar(slot);
     const int64_t e0 = elem(pv0);
     const int ne = (int)(elem(pv0 + pnE - 1) - e0 + 1);
     // F-, F+ rows of elements e0 .. e0 + ne - 1: ne x 1296 bytes each, 16-byte aligned
-    for (int cc = t; cc < ne * 81; cc += 128) {
+    for (int cc = u; cc < ne * 81; cc += 256) {
       cp16(sFm + 4 * cc, reinterpret_cast<const float*>(a.Fm) + e0 * 324 + 4 * cc);
       cp16(sFm + TE * 324 + 4 * cc, reinterpret_cast<const float*>(a.Fp) + e0 * 324 + 4 * cc);
     }
-    for (int c = t; c < ne * (PAR / 4); c += 128)
+    for (int c = u; c < ne * (PAR / 4); c += 256)
       cp16(sPr + 4 * c, reinterpret_cast<const float*>(a.par) + e0 * PAR + 4 * c);
-    stage_face(0, t, pv0, pnE, trace, sNb, sStage, sStage + kStage);
+    stage_face(0, u, pv0, pnE, trace, sNb, sStage, sStage + kStage);
     cp_commit();
   };
 
-  int64_t tile = (int64_t)blockIdx.x * 2 + wg;
+  int64_t tile = (int64_t)blockIdx.x * 2 + slot;
   if (tile < ntiles) {
     int info0, nbe0;
     meta_load(tile, info0, nbe0);
@@ -217,7 +222,7 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
       // ---- stage face f + 1 while face f is used
       if (f < 3) {
         float* nb_buf = sStage + ((f + 1) & 1) * 2 * kStage;
-        stage_face(f + 1, t, v0, nE, trace, sNb, nb_buf, nb_buf + kStage);
+        stage_face(f + 1, u, v0, nE, trace, sNb, nb_buf, nb_buf + kStage);
         cp_commit();
         cp_wait<1>();
       } else {
@@ -227,17 +232,16 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
         asm volatile("tcgen05.wait::st.sync.aligned;");
         tc::fence_before();
       }
-      wg_bar(wg);
-      if (f == 2 && t == 0) {
+      slot_bar(slot);
+      if (f == 2 && u == 0) {
         tc::fence_after();
         tc::mma3_ts<kN, 48>(tbase + cAcc, tbase + cGh, tbase + cGl, sL, sL + 4 * NImg::sL, false);
       }
       const float* sVo = sStage + (f & 1) * 2 * kStage;
       const float* sVn = sVo + kStage;
-      float* gbuf = sG;
-      // ---- work items (element, node triplet, three output rows): scaled flux
-#pragma unroll 1
-      for (int item = t; item < kItems; item += 128) {
+      // ---- work item (element, node triplet, three output rows) of thread u: scaled flux
+      if (u < kItems) {
+        const int item = u;
         const int ei = item / (3 * kTrip), rem = item - ei * (3 * kTrip);
         const int k = rem / 3, pg = rem - 3 * k;  // node triplet, group of output rows
         const int el = kOne ? ei : (r0 + ei) / S;  // element of item's virtual element, from the tile's first
@@ -247,9 +251,9 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
         const int* perm = sPerm + sPm[f * TE + ei] * BF;
         int nd[3], pn[3];
 #pragma unroll
-        for (int u = 0; u < 3; ++u) {
-          nd[u] = k + kTrip * u;
-          pn[u] = perm[nd[u]];
+        for (int uu = 0; uu < 3; ++uu) {
+          nd[uu] = k + kTrip * uu;
+          pn[uu] = perm[nd[uu]];
         }
         float vo[3][9], vn[3][9];
 #pragma unroll
@@ -257,12 +261,12 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
           const float* o = sVo + ei * kSS + qq * BF;
           const float* nn = sVn + ei * kSS + qq * BF;
 #pragma unroll
-          for (int u = 0; u < 3; ++u) {
-            vo[u][qq] = o[nd[u]];
-            vn[u][qq] = nn[pn[u]];
+          for (int uu = 0; uu < 3; ++uu) {
+            vo[uu][qq] = o[nd[uu]];
+            vn[uu][qq] = nn[pn[uu]];
           }
         }
-        float* gout = gbuf + (ei * 9 + 3 * pg) * kGrow;
+        float* gout = sG + (ei * 9 + 3 * pg) * kGrow;
 #pragma unroll
         for (int pp = 0; pp < 3; ++pp) {
           float g[3] = {0.f, 0.f, 0.f};
@@ -270,18 +274,20 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
           for (int qq = 0; qq < 9; ++qq) {
             const float fm = Fm[pp * 9 + qq], fp = Fp[pp * 9 + qq];
 #pragma unroll
-            for (int u = 0; u < 3; ++u) g[u] += fm * vo[u][qq] + fp * vn[u][qq];
+            for (int uu = 0; uu < 3; ++uu) g[uu] += fm * vo[uu][qq] + fp * vn[uu][qq];
           }
 #pragma unroll
-          for (int u = 0; u < 3; ++u) gout[pp * kGrow + nd[u]] = sc * g[u];
+          for (int uu = 0; uu < 3; ++uu) gout[pp * kGrow + nd[uu]] = sc * g[uu];
         }
       }
-      wg_bar(wg);
-      // ---- this row's 24 columns of face f -> TMEM (hi, lo)
+      slot_bar(slot);
+      // ---- this row's 24 columns of face f -> TMEM (hi, lo): 8-column chunk c
+      // by the half (c + f) % 2
       {
-        const float4* g4 = reinterpret_cast<const float4*>(gbuf + ((i < TE ? i : 0) * 9 + p) * kGrow);
+        const float4* g4 = reinterpret_cast<const float4*>(sG + ((i < TE ? i : 0) * 9 + p) * kGrow);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
+          if (((c + f) & 1) != half) continue;
           const float4 x0 = g4[2 * c], x1 = g4[2 * c + 1];
           float g[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
           if (!valid) {
@@ -292,21 +298,27 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
         }
       }
     }
-    // the dofs row (in L2 from the prefetch two tiles back) is loaded while
-    // the next tile's copies are issued and the lift runs
+    // this half's chunks (c % 2 == half) of the dofs row (in L2 from the
+    // prefetch two tiles back), loaded while the next tile's copies are issued
+    // and the lift runs
     float* Qrow = reinterpret_cast<float*>(a.Q) + (v * 9 + p) * B;
-    float q[B];
+    float q[32];
 #pragma unroll
-    for (int c = 0; c < B / 4; ++c) {
-      float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (valid) x = *reinterpret_cast<const float4*>(Qrow + 4 * c);
-      q[4 * c] = x.x; q[4 * c + 1] = x.y; q[4 * c + 2] = x.z; q[4 * c + 3] = x.w;
+    for (int cj = 0; cj < 4; ++cj) {
+      const int c = half + 2 * cj;
+      float4 x0 = make_float4(0.f, 0.f, 0.f, 0.f), x1 = x0;
+      if (c < B / 8 && valid) {
+        x0 = reinterpret_cast<const float4*>(Qrow + 8 * c)[0];
+        x1 = reinterpret_cast<const float4*>(Qrow + 8 * c)[1];
+      }
+      q[8 * cj] = x0.x; q[8 * cj + 1] = x0.y; q[8 * cj + 2] = x0.z; q[8 * cj + 3] = x0.w;
+      q[8 * cj + 4] = x1.x; q[8 * cj + 5] = x1.y; q[8 * cj + 6] = x1.z; q[8 * cj + 7] = x1.w;
     }
     // ---- the next tile's loads overlap this tile's lift and dofs update
     if (next < ntiles) prefetch(next, info_n, nbe_n);
     // and the tile after it into L2
     const int64_t next2 = next + (int64_t)gridDim.x * 2;
-    if (t == 0 && next2 < ntiles) {
+    if (u == 0 && next2 < ntiles) {
       const int64_t q0 = a.v_begin + next2 * TE, rem2 = n_virtual - next2 * TE;
       const uint32_t n2 = (uint32_t)(rem2 < TE ? rem2 : TE);
       tc::prefetch_l2(reinterpret_cast<const float*>(a.Q) + q0 * 9 * B, n2 * 9 * B * 4);
@@ -318,34 +330,34 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
     // ---- lift of faces 2 and 3 on the tensor cores (faces 0 and 1 were issued above)
     asm volatile("tcgen05.wait::st.sync.aligned;");
     tc::fence_before();
-    wg_bar(wg);
+    slot_bar(slot);
     tc::fence_after();
-    if (t == 0) {
+    if (u == 0) {
       tc::mma3_ts<kN, kK, 48>(tbase + cAcc, tbase + cGh, tbase + cGl, sL, sL + 4 * NImg::sL, true);
-      tc::commit(&mbar[wg]);
-      if (!tc::mbar_wait(&mbar[wg], phase, kWaitIters)) {
+      tc::commit(&mbar[slot]);
+      if (!tc::mbar_wait(&mbar[slot], phase, kWaitIters)) {
         atomicOr(a.err, ERR_TIMEOUT);
-        s_abort[wg] = 1;
+        s_abort[slot] = 1;
       }
     }
-    wg_bar(wg);
-    if (s_abort[wg]) break;
-    tc::mbar_wait(&mbar[wg], phase, 1 << 20);
+    slot_bar(slot);
+    if (s_abort[slot]) break;
+    tc::mbar_wait(&mbar[slot], phase, 1 << 20);
     phase ^= 1u;
     tc::fence_after();
-    // ---- Q -= lift
+    // ---- Q -= lift, this half's chunks
+    {
+      float x[32];
+      tc::ld3x8(trow + cAcc + 8 * half, trow + cAcc + 8 * (half + 2), trow + cAcc + 8 * (half + 4), x);
+      if (half == 0) tc::ld8(trow + cAcc + 48, x + 24);
 #pragma unroll
-    for (int c3 = 0; c3 < 3; ++c3) {  // chunks 3 c3 .. 3 c3 + 2 (the last group repeats chunk 6)
-      float x3[24];
-      tc::ld3x8(trow + cAcc + 24 * c3, trow + cAcc + 24 * c3 + 8, trow + cAcc + (c3 < 2 ? 24 * c3 + 16 : 48), x3);
-#pragma unroll
-      for (int cc = 0; cc < 3; ++cc) {
-        const int c = 3 * c3 + cc;
+      for (int cj = 0; cj < 4; ++cj) {
+        const int c = half + 2 * cj;
         if (c < B / 8 && valid) {
           float nq[8];
 #pragma unroll
           for (int j = 0; j < 8; ++j) {
-            nq[j] = q[8 * c + j] - x3[8 * cc + j];
+            nq[j] = q[8 * cj + j] - x[8 * cj + j];
             bad = fmaf(nq[j], 0.f, bad);
           }
           float4* dst = reinterpret_cast<float4*>(Qrow + 8 * c);
@@ -357,7 +369,7 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
     tc::fence_before();
   }
   if (__any_sync(0xffffffffu, bad != 0.f) && lane == 0) atomicOr(a.err, ERR_NAN);
-  if (t == 0 && s_abort[wg]) tc::mbar_wait(&mbar[wg], phase ^ 1u, kWaitIters);
+  if (u == 0 && s_abort[slot]) tc::mbar_wait(&mbar[slot], phase ^ 1u, kWaitIters);
   tc::fence_before();
   __syncthreads();
   tc::fence_after();
