@@ -72,7 +72,7 @@ def bytes_per_update(N, w):
 # DRAM bytes (read + write) per element of the tensor-core kernels, from the
 # full ncu capture of the 374,400-tet box (profiles/tensor_core_kernels_box40.md);
 # a launch's traffic is scaled from it by the number of elements
-TC_DRAM_BYTES_PER_ELEMENT = {"local_tc_kernel": 7253.0, "neighbour_tc_kernel": 10510.0}
+TC_DRAM_BYTES_PER_ELEMENT = {"local_tc_kernel": 7135.7, "neighbour_tc_kernel": 10723.0}
 
 
 def load_peaks():
@@ -318,8 +318,8 @@ def run_other_workload(args):
                  "setup_s": t_setup})
     kms, kcnt = _lib.adg_profile(s.ctx, 1)
     line["kernel_ms"] = {"local": kms[0], "neighbour": kms[1], "rupture": kms[2],
-                         "launches_per_macro": [int(x) for x in kcnt]}
-    line["gpu_launches"] = int(kcnt.sum()) * steps
+                         "launches_per_macro": [int(x) for x in kcnt[:3]]}
+    line["gpu_launches"] = int(kcnt[:3].sum()) * steps
     if args.workload == "rupture":
         solves, iters = _lib.adg_fault_stats(s.ctx, reset=True)
         # learned Newton start: capture, train on the GPU, rerun the same steps
@@ -434,7 +434,7 @@ def main():
         # per-kernel durations (CUDA events on the library stream)
         kms, kcnt = pkg._lib.adg_profile(s.ctx, 2)
         res[prec] = dict(solver=s, ms=ms, steps=steps, upd=upd, kms=kms, kcnt=kcnt,
-                         clocks=cs.summary(local), launches=int(kcnt.sum() // 2),
+                         clocks=cs.summary(local), launches=int(kcnt[:3].sum() // 2),
                          advanced=warm + steps + 2)
         if prec not in (HEAD, pkg.ADG_FP64):
             del s
@@ -483,19 +483,23 @@ def main():
     fl = flops_per_update(N_DEG)
     by = bytes_per_update(N_DEG, 4)
     kms = r32["kms"]
-    dom = 0 if kms[0] >= kms[1] else 1
-    kname = ["local_kernel", "neighbour_kernel"][dom]
-    if HEAD == pkg.ADG_3XTF32:
-        kname = ["local_tc_kernel", "neighbour_tc_kernel"][dom]
+    # elements of one launch of the dominant kernel and that launch's own duration:
+    # with the tensor-core form the tensor-core launches are timed alone (kms[3], kms[4])
+    n_tc = int(s.info.tensor_core_updates_per_macro)
+    tc_form = HEAD == pkg.ADG_3XTF32 and n_tc > 0
+    t_k = [kms[3], kms[4]] if tc_form else [kms[0], kms[1]]
+    n_k = n_tc if tc_form else s.nt
+    dom = 0 if t_k[0] >= t_k[1] else 1
+    kname = ["local_tc_kernel", "neighbour_tc_kernel"][dom] if tc_form else ["local_kernel", "neighbour_kernel"][dom]
     clk = r32["clocks"]
     sm_mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
     alu_peak = alu_peak_tflops(False, peaks.get("sm_max_mhz", 2070.0))
-    achieved_flops = fl[kname.replace("_tc", "")] * s.nt / (kms[dom] * 1e-3) / 1e12
-    achieved_bytes = by[kname] * s.nt / (kms[dom] * 1e-3) / 1e9
+    achieved_flops = fl[kname.replace("_tc", "")] * n_k / (t_k[dom] * 1e-3) / 1e12
+    achieved_bytes = by[kname] * n_k / (t_k[dom] * 1e-3) / 1e9
     frac_alu = achieved_flops / alu_peak
     frac_hbm = achieved_bytes / peaks["hbm_gbs"]
     tc_peak = tf32x3_peak_tflops(peaks)
-    achieved_tc = fl["local_tensor"] * s.nt / (kms[0] * 1e-3) / 1e12
+    achieved_tc = fl["local_tensor"] * n_k / (t_k[0] * 1e-3) / 1e12 if tc_form else None
     if kname == "local_tc_kernel":
         roof = {"bound": "tensor", "achieved": achieved_tc, "peak": tc_peak, "unit": "TFLOP/s",
                 "frac": achieved_tc / tc_peak, "traffic": None, "kernel": kname,
@@ -515,15 +519,18 @@ def main():
         roof = {"bound": "hbm", "achieved": achieved_bytes, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": frac_hbm, "traffic": None, "kernel": kname, "peak_source": src}
     if kname in TC_DRAM_BYTES_PER_ELEMENT:
-        roof["traffic"] = TC_DRAM_BYTES_PER_ELEMENT[kname] * s.nt
+        roof["traffic"] = TC_DRAM_BYTES_PER_ELEMENT[kname] * n_k
         roof["traffic_note"] = "DRAM bytes per launch, ncu on the 374,400-tet box scaled by elements"
-    roof.update({"ms_per_launch": kms[dom], "hbm_frac": frac_hbm,
+    roof.update({"ms_per_launch": t_k[dom], "elements_per_launch": n_k, "hbm_frac": frac_hbm,
                  # the CUDA-core ALU fraction of a tensor-core kernel's whole flop count means nothing
                  "alu_frac": None if kname.endswith("_tc_kernel") else frac_alu,
-                 "kernel_ms": {"local": kms[0], "neighbour": kms[1]},
-                 "local_tc_tensor_frac": achieved_tc / tc_peak,
-                 "local_hbm_frac": by["local_tc_kernel"] * s.nt / (kms[0] * 1e-3) / 1e9 / peaks["hbm_gbs"],
-                 "neighbour_hbm_frac": by["neighbour_tc_kernel"] * s.nt / (kms[1] * 1e-3) / 1e9 / peaks["hbm_gbs"]})
+                 "kernel_ms": {"local": kms[0], "neighbour": kms[1]}})
+    if tc_form:
+        roof.update({"tc_kernel_ms": {"local_tc": kms[3], "neighbour_tc": kms[4]},
+                     "local_tc_tensor_frac": achieved_tc / tc_peak,
+                     "local_tc_hbm_frac": by["local_tc_kernel"] * n_k / (kms[3] * 1e-3) / 1e9 / peaks["hbm_gbs"],
+                     "neighbour_tc_hbm_frac": by["neighbour_tc_kernel"] * n_k / (kms[4] * 1e-3) / 1e9
+                     / peaks["hbm_gbs"]})
     r64k = r64["kms"]
     fp64_alu = fl["local_kernel"] * s.nt / (r64k[0] * 1e-3) / 1e12
     line = {

@@ -93,6 +93,7 @@ typedef struct adg_info {
   int64_t n_fault_faces;
   int64_t updates_per_macro; /* element updates (x ensemble) per macro step */
   int64_t device_bytes;
+  int64_t tensor_core_updates_per_macro; /* of those, by the tensor-core kernels (ADG_3XTF32, degree 5) */
 } adg_info;
 
 /* Default configuration: N=5, FP64, cfl 0.35 (Sec. 6), g 9.81, GTS, S=1. */
@@ -156,9 +157,11 @@ int adg_sync(adg_ctx* ctx);
  * eager (non-graph) launches and a CUDA event pair around the work of every
  * kernel kind of a cluster on the library stream.  ms[k] = mean duration of
  * one such phase of kind k, launches[k] = number of kernel launches (arrays
- * of 3), k = 0 local (predictor, volume, traces; with ADG_3XTF32 at degree 5
+ * of 5), k = 0 local (predictor, volume, traces; with ADG_3XTF32 at degree 5
  * one tensor-core and one CUDA-core launch per cluster), 1 neighbour flux,
- * 2 fault friction solve.  Advances the simulation like adg_advance. */
+ * 2 fault friction solve, 3 and 4 the tensor-core launch of the local and
+ * of the neighbour phase alone (0 without one).  Advances the simulation
+ * like adg_advance. */
 int adg_profile(adg_ctx* ctx, int n_macro, double* ms, int64_t* launches);
 
 /* Allocation-free global steps (the paper has no counterpart; this is a

@@ -37,7 +37,7 @@ class adg_info(C.Structure):
                 ("n_clusters", C.c_int), ("cluster_size", C.c_int64 * 16), ("dt_min", C.c_double),
                 ("macro_dt", C.c_double), ("time", C.c_double), ("n_gravity_faces", C.c_int64),
                 ("n_fault_faces", C.c_int64), ("updates_per_macro", C.c_int64),
-                ("device_bytes", C.c_int64)]
+                ("device_bytes", C.c_int64), ("tensor_core_updates_per_macro", C.c_int64)]
 
 
 _P = C.c_void_p
@@ -215,8 +215,8 @@ def adg_sync(ctx):
 
 
 def adg_profile(ctx, n_macro):
-    ms = np.zeros(3)
-    cnt = np.zeros(3, np.int64)
+    ms = np.zeros(5)
+    cnt = np.zeros(5, np.int64)
     _check(ctx, load().adg_profile(ctx, int(n_macro), _ptr(ms), _ptr(cnt)))
     return ms, cnt
 

@@ -212,6 +212,9 @@ int adg_query(const adg_ctx* ctx, adg_info* out) {
   for (int i = 0; i < c.ncl; ++i) upd += (c.cl_begin[i + 1] - c.cl_begin[i]) * ((int64_t)1 << (c.ncl - 1 - i));
   out->updates_per_macro = upd * c.S;
   out->device_bytes = c.dev_bytes;
+  int64_t utc = 0;
+  for (int i = 0; i < c.ncl && i < (int)c.cl_plain.size(); ++i) utc += c.cl_plain[i] * ((int64_t)1 << (c.ncl - 1 - i));
+  out->tensor_core_updates_per_macro = utc * c.S;
   return ADG_OK;
 }
 
@@ -419,16 +422,22 @@ int adg_profile(adg_ctx* ctx, int n_macro, double* ms, int64_t* launches) {
     }
     c.prof = nullptr;
     check_cuda(cudaStreamSynchronize(c.stream), "profile");
-    double tot[3] = {0, 0, 0};
-    int64_t cnt[3] = {0, 0, 0}, nl[3] = {0, 0, 0};
+    double tot[5] = {0, 0, 0, 0, 0};
+    int64_t cnt[5] = {0, 0, 0, 0, 0}, nl[5] = {0, 0, 0, 0, 0};
     for (auto& e : evs) {
       float t = 0;
       check_cuda(cudaEventElapsedTime(&t, e.a, e.b), "profile events");
       tot[e.kind] += t;
       cnt[e.kind] += 1;
       nl[e.kind] += e.launches;
+      if (e.m) {  // tensor-core launch of the phase, timed alone
+        check_cuda(cudaEventElapsedTime(&t, e.a, e.m), "profile events");
+        tot[3 + e.kind] += t;
+        cnt[3 + e.kind] += 1;
+        nl[3 + e.kind] += 1;
+      }
     }
-    for (int k = 0; k < 3; ++k) {
+    for (int k = 0; k < 5; ++k) {
       ms[k] = cnt[k] ? tot[k] / cnt[k] : 0.0;
       launches[k] = nl[k];
     }
@@ -437,6 +446,7 @@ int adg_profile(adg_ctx* ctx, int n_macro, double* ms, int64_t* launches) {
   for (auto& e : evs) {
     cudaEventDestroy(e.a);
     cudaEventDestroy(e.b);
+    if (e.m) cudaEventDestroy(e.m);
   }
   return rc;
 }

@@ -674,6 +674,10 @@ void Ctx::launch_tick(int s, double dtm) {
       const int64_t np = cl_plain[c];
       ev.launches = (np > 0) + (n > np);
       if (np > 0) rc = launch_local_tc(a, np * S, n_sms, stream);
+      if (prof && np > 0) {  // the tensor-core launch alone
+        CK(cudaEventCreate(&ev.m));
+        CK(cudaEventRecord(ev.m, stream));
+      }
       a.v_begin = (cl_begin[c] + np) * S;
       if (!rc && n > np) rc = launch_local(fp64, N, a, (n - np) * S, stream);
     } else {
@@ -704,6 +708,10 @@ void Ctx::launch_tick(int s, double dtm) {
       const int64_t np = cl_plain[c];
       ev.launches = (np > 0) + (n > np);
       if (np > 0) rc = launch_neighbour_tc(a, np * S, n_sms, stream);
+      if (prof && np > 0) {
+        CK(cudaEventCreate(&ev.m));
+        CK(cudaEventRecord(ev.m, stream));
+      }
       a.v_begin = (cl_begin[c] + np) * S;
       if (!rc && n > np) rc = launch_neighbour(fp64, N, a, (n - np) * S, stream);
     } else {

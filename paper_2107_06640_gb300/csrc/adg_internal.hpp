@@ -92,7 +92,7 @@ struct Ctx {
   bool cap_on = false;
   void launch_rupture_cluster(int c, double dt);
   // per-kernel profiling (adg_profile)
-  struct ProfEv { int kind; cudaEvent_t a, b; int launches; };
+  struct ProfEv { int kind; cudaEvent_t a, b; int launches; cudaEvent_t m = nullptr; };  // m: after the tensor-core launch
   std::vector<ProfEv>* prof = nullptr;
   // pinned host staging buffer for dofs upload / download (allocated on first use)
   void* hstage = nullptr;

@@ -102,15 +102,20 @@ def test_periodic_cube_tensor_core_local_kernel():
     assert rel_l2(to_oracle_layout(s.get_dofs()), o.Q) <= 2e-5
     _, launches = _lib.adg_profile(s.ctx, 1)
     assert launches[0] == 1 and launches[1] == 1  # tensor-core launches only, no CUDA-core remainder
+    assert int(s.info.tensor_core_updates_per_macro) == m.nt
 
 
 def test_coupled_box_uses_both_kernel_forms_3xtf32():
     m, mat = small_coupled()
     from paper_2107_06640_gb300 import _lib
     s = make_pair(m, mat, 5, precision=2, cfl=0.5)[1]
-    _, launches = _lib.adg_profile(s.ctx, 1)
+    ms, launches = _lib.adg_profile(s.ctx, 1)
     # tensor cores for the interior, CUDA cores for the gravity-face layer
     assert launches[0] == 2 and launches[1] == 2
+    assert launches[3] == 1 and launches[4] == 1
+    assert 0 < ms[3] <= ms[0] and 0 < ms[4] <= ms[1]  # the tensor-core launches timed alone
+    plain = int(np.sum(~np.any(m.face_tag == syn.TAG_GRAVITY, axis=1)))
+    assert int(s.info.tensor_core_updates_per_macro) == plain < m.nt
 
 
 def test_ensemble_equals_independent_runs_3xtf32():
