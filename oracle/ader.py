@@ -107,11 +107,13 @@ class Oracle:
         self.f_area = geo.area[em, fm]
         self.fault = None  # set by set_fault
 
-    def set_fault(self, par):
-        """par: dict of (nff, Bf) arrays named as rupture.PARAMS (psi, V: initial state)."""
+    def set_fault(self, par, law="rs"):
+        """par: dict of (nff, Bf) arrays named as rupture.PARAMS, or rupture.LSW_PARAMS
+        for law = "lsw" (linear slip weakening); psi, V: initial state."""
         self.fault = {k: np.array(v, dtype=np.float64) for k, v in par.items()}
-        self.fault["slip"] = np.zeros(self.fault["a"].shape + (3,))
-        self.fault["traction"] = np.zeros(self.fault["a"].shape + (3,))
+        self.fault_law = law
+        self.fault["slip"] = np.zeros(self.fault["psi"].shape + (3,))
+        self.fault["traction"] = np.zeros(self.fault["psi"].shape + (3,))
         self.newton_solves = 0
         self.newton_iters = 0
 
@@ -138,7 +140,8 @@ class Oracle:
         matp = tuple(np.repeat(a[ep], Bf) for a in (self.rho, self.lam, self.mu))
         par = {k: flat(v[sel]) for k, v in self.fault.items() if k not in ("slip", "traction")}
         Gm, Gp, psi, V, dslip, iters, tau = ru.solve_step(
-            nrm, qm_t.reshape(N + 1, -1, 9), qp_t.reshape(N + 1, -1, 9), matm, matp, par, dt, N, guess=guess)
+            nrm, qm_t.reshape(N + 1, -1, 9), qp_t.reshape(N + 1, -1, 9), matm, matp, par, dt, N, guess=guess,
+            law=self.fault_law)
         self.newton_solves += int(np.sum(iters > 0))
         self.newton_iters += int(iters.sum())
         shp = (sel.size, Bf)

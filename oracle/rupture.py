@@ -27,13 +27,25 @@ but prints neither f nor g):
   * the fault sits at the equispaced face nodes of the minus element's face;
     the flux there is interpolated (Lagrange on those nodes) and integrated
     against the basis; minus = the lower user tet index of the pair.
+
+Linear slip weakening (Sec. 5, the Scenario-A fault; law of Andrews 1976),
+the same Eq. (bc-dynrup) with the state psi = slip path length:
+  * f(psi) = mu_s - (mu_s - mu_d) min(psi / D_c, 1),  dpsi/dt = |V|;
+  * strength tau_S = C + f(psi) S (cohesion C >= 0, S as above);
+  * |V| = max(0, Theta - tau_S) / eta_s: the locked traction if it is below the
+    strength, else the strength with the slip rate that the Godunov states
+    give (Theta - eta_s |V| = tau_S);
+  * time: the same points and two passes as above, the state advancing exactly
+    for a frozen slip rate, psi + |V| h.
 """
 
 import numpy as np
 from numpy.polynomial.legendre import leggauss
 
-# parameter slots per fault node
+# parameter slots per fault node (rate and state; linear slip weakening uses
+# the first four for its own parameters, slots 4..6 unused)
 PARAMS = ("a", "b", "L", "f0", "V0", "fw", "Vw", "sn0", "t0x", "t0y", "t0z", "psi", "V")
+LSW_PARAMS = ("mu_s", "mu_d", "Dc", "C", "u4", "u5", "u6", "sn0", "t0x", "t0y", "t0z", "psi", "V")
 NPAR = len(PARAMS)
 
 
@@ -181,17 +193,30 @@ def ahat_apply(n, t, v, rho, lam, mu):
     return out
 
 
+def lsw_friction(psi, p):
+    """Linear slip weakening: mu_s at psi = 0, mu_d from psi = D_c on."""
+    return p["mu_s"] - (p["mu_s"] - p["mu_d"]) * np.minimum(psi / p["Dc"], 1.0)
+
+
+def lsw_slip_rate(Theta, S, eta, psi, p):
+    """|V| = max(0, Theta - tau_S) / eta_s with tau_S = C + f(psi) S."""
+    return np.maximum(0.0, Theta - (p["C"] + lsw_friction(psi, p) * S)) / eta
+
+
 def time_points(N, dt):
     x, w = leggauss(N + 1)
     return 0.5 * dt * (x + 1.0), 0.5 * dt * w
 
 
-def solve_step(n, qm_t, qp_t, matm, matp, par, dt, N, guess=None, tol=1e-10, max_iter=100):
+def solve_step(n, qm_t, qp_t, matm, matp, par, dt, N, guess=None, tol=1e-10, max_iter=100, law="rs"):
     """One step at all fault points.
     qm_t, qp_t: (N+1, npts, 9) states of both sides at the Gauss time points.
-    par: dict of per-point parameter arrays (PARAMS), psi and V are the state
-    at the step start.  Returns (G_minus, G_plus, new psi, new |V|, slip
-    increment (npts,3), iteration counts (N+1, 2, npts), final traction)."""
+    par: dict of per-point parameter arrays (PARAMS, or LSW_PARAMS for
+    law = "lsw"), psi and V are the state at the step start.  Returns
+    (G_minus, G_plus, new psi, new |V|, slip increment (npts,3), iteration
+    counts (N+1, 2, npts; zero for the closed-form law), final traction)."""
+    if law not in ("rs", "lsw"):
+        raise ValueError("law: 'rs' or 'lsw'")
     tj, wj = time_points(N, dt)
     psi = par["psi"].copy()
     V = par["V"].copy()
@@ -208,6 +233,21 @@ def solve_step(n, qm_t, qp_t, matm, matp, par, dt, N, guess=None, tol=1e-10, max
         Th = np.linalg.norm(st["Thv"], axis=-1)
         h = tj[j] - tprev
         Vold = V
+        if law == "lsw":
+            # pass 0 advances the state with the previous slip rate, pass 1
+            # with the mid-point of the previous and pass-0 rates
+            Vcur = V
+            for ps in range(2):
+                Vmid = Vold if ps == 0 else 0.5 * (Vold + Vcur)
+                psi_new = psi + Vmid * h
+                Vcur = lsw_slip_rate(Th, st["S"], st["eta"], psi_new, par)
+            psi, V = psi_new, Vcur
+            t_b, vb, vc, Vvec, tau_tot = middle_traction_velocity(st, V, n)
+            Gm += wj[j] * ahat_apply(n, t_b, vb, *matm)
+            Gp += wj[j] * (-ahat_apply(n, t_b, vc, *matp))
+            slip += wj[j] * Vvec
+            tprev = tj[j]
+            continue
         # the start guess only seeds Newton; the state update of the first
         # pass uses the previous slip rate, the second the mid-point
         Vcur = V if guess is None else guess(j, Th, st, psi, V, par)
@@ -234,5 +274,5 @@ def solve_step(n, qm_t, qp_t, matm, matp, par, dt, N, guess=None, tol=1e-10, max
         Gp += wj[j] * (-ahat_apply(n, t_b, vc, *matp))
         slip += wj[j] * Vvec
         tprev = tj[j]
-    psi = psi_relax(psi, V, dt - tprev, par)
+    psi = psi + V * (dt - tprev) if law == "lsw" else psi_relax(psi, V, dt - tprev, par)
     return Gm, Gp, psi, V, slip, iters, tau_tot

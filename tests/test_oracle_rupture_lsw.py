@@ -1,0 +1,113 @@
+"""Pins of the oracle's linear slip-weakening friction (Sec. 5, Scenario-A
+fault; Eq. bc-dynrup with the slip path length as state) against closed
+forms: the friction coefficient, a fault that stays locked, and a fault under
+constant load, whose state obeys dpsi/dt = A + B psi until psi = D_c and
+slides at a constant rate after."""
+
+import numpy as np
+import pytest
+
+from oracle import rupture as ru
+
+RHO, LAM, MU = 3000.0, 3.0e10, 3.0e10
+ETA = np.sqrt(RHO * MU) / 2.0  # both sides alike: Zs- Zs+ / (Zs- + Zs+)
+
+
+def _par(npts, mu_s=0.6, mu_d=0.4, Dc=0.5, C=2e6, sn0=-40e6, tau=20e6, psi=0.0, V=0.0):
+    """Parameters of npts points with the shear prestress along x on a fault
+    with normal z (its normal part zero)."""
+    p = {k: np.zeros(npts) for k in ru.LSW_PARAMS}
+    p.update(mu_s=np.full(npts, mu_s), mu_d=np.full(npts, mu_d), Dc=np.full(npts, Dc), C=np.full(npts, C),
+             sn0=np.full(npts, sn0), t0x=np.full(npts, tau), psi=np.full(npts, psi), V=np.full(npts, V))
+    return p
+
+
+def _run(par, dt, steps, N=3):
+    """Both sides at rest (zero perturbation), so Theta = |tau0| and S = -sn0
+    at every time point; returns psi, |V|, slip, traction after each step."""
+    npts = par["psi"].size
+    n = np.tile([0.0, 0.0, 1.0], (npts, 1))
+    q = np.zeros((N + 1, npts, 9))
+    mat = tuple(np.full(npts, v) for v in (RHO, LAM, MU))
+    hist = []
+    slip = np.zeros((npts, 3))
+    for _ in range(steps):
+        Gm, Gp, psi, V, dslip, iters, tau = ru.solve_step(n, q, q, mat, mat, par, dt, N, law="lsw")
+        assert not iters.any()
+        par = dict(par, psi=psi, V=V)
+        slip = slip + dslip
+        hist.append((psi.copy(), V.copy(), slip.copy(), tau.copy()))
+    return hist
+
+
+def test_friction_coefficient_is_linear_in_slip_then_constant():
+    p = dict(mu_s=0.6, mu_d=0.4, Dc=0.5)
+    psi = np.array([0.0, 0.125, 0.25, 0.5, 0.9, 7.0])
+    assert np.allclose(ru.lsw_friction(psi, p), [0.6, 0.55, 0.5, 0.4, 0.4, 0.4], rtol=0, atol=1e-15)
+
+
+def test_fault_below_strength_stays_locked():
+    # |tau0| = 20 MPa < C + mu_s S = 2 + 0.6 * 40 = 26 MPa
+    hist = _run(_par(4, tau=20e6), dt=1e-3, steps=5)
+    psi, V, slip, tau = hist[-1]
+    assert np.all(V == 0) and np.all(psi == 0) and np.all(slip == 0)
+    assert np.allclose(tau, [[20e6, 0, 0]] * 4, rtol=1e-15)
+
+
+def _closed_form(t, Th, S, C, mu_s, mu_d, Dc, eta, psi0=0.0):
+    """Slip path length under constant Theta and S: dpsi/dt = A + B psi with
+    A = (Th - C - mu_s S)/eta, B = (mu_s - mu_d) S / (Dc eta) until psi = Dc,
+    then constant V_d = (Th - C - mu_d S)/eta."""
+    A = (Th - C - mu_s * S) / eta
+    B = (mu_s - mu_d) * S / (Dc * eta)
+    tc = np.log((Dc + A / B) / (psi0 + A / B)) / B
+    return np.where(t <= tc, (psi0 + A / B) * np.exp(B * t) - A / B, Dc + (Th - C - mu_d * S) / eta * (t - tc))
+
+
+@pytest.mark.parametrize("N", [2, 3])
+def test_overloaded_fault_follows_the_closed_form(N):
+    """Theta = 27 MPa above the static strength 26 MPa: the slip path
+    length grows as the exponential closed form until it reaches D_c, then
+    the fault slides at (Theta - C - mu_d S)/eta; the scheme converges at
+    first order in dt (each step's tail, after the last time point, advances
+    the state with the frozen last rate), and while sliding the traction
+    equals the strength."""
+    Th, S, C, mu_s, mu_d, Dc = 27e6, 40e6, 2e6, 0.6, 0.4, 0.5
+    A = (Th - C - mu_s * S) / ETA
+    T = 1.0
+    errs = []
+    for steps in (40, 80, 160):
+        dt = T / steps
+        hist = _run(_par(1, mu_s=mu_s, mu_d=mu_d, Dc=Dc, C=C, sn0=-S, tau=Th, V=A), dt, steps, N=N)
+        t = dt * np.arange(1, steps + 1)
+        psi = np.array([h[0][0] for h in hist])
+        want = _closed_form(t, Th, S, C, mu_s, mu_d, Dc, ETA)
+        errs.append(np.max(np.abs(psi - want)))
+        assert want[-1] > 2 * Dc  # the run covers both regimes
+        # slip runs along the prestress; its Gauss-weighted integral of |V|
+        # approximates the same path length
+        slip = np.array([h[2][0] for h in hist])
+        assert np.all(slip[:, 1:] == 0)
+        assert np.max(np.abs(slip[:, 0] - want)) < 2e-3 * want[-1]
+        # once weakened: constant rate and the traction at the dynamic strength
+        psi_end, V_end, _, tau_end = hist[-1]
+        assert psi_end[0] > Dc
+        assert V_end[0] == pytest.approx((Th - C - mu_d * S) / ETA, rel=1e-13)
+        assert np.linalg.norm(tau_end[0]) == pytest.approx(C + mu_d * S, rel=1e-13)
+    assert errs[0] < 2e-3 * want[-1]
+    assert errs[0] / errs[1] > 1.8 and errs[1] / errs[2] > 1.8
+
+
+def test_traction_is_the_strength_while_weakening():
+    """Mid-weakening (psi < D_c) the fault traction is C + f(psi) S with the
+    state at the last time point, and theta - eta |V| gives it."""
+    Th, S, C = 27e6, 40e6, 2e6
+    hist = _run(_par(1, C=C, sn0=-S, tau=Th, V=(Th - C - 0.6 * S) / ETA), dt=2e-3, steps=3, N=3)
+    psi, V, _, tau = hist[-1]
+    assert 0 < psi[0] < 0.5
+    # the last time point's state is psi advanced by the rest of the step
+    tj, _ = ru.time_points(3, 2e-3)
+    psi_last = psi[0] - V[0] * (2e-3 - tj[-1])
+    want = C + ru.lsw_friction(np.array([psi_last]), dict(mu_s=0.6, mu_d=0.4, Dc=0.5))[0] * S
+    assert np.linalg.norm(tau[0]) == pytest.approx(want, rel=1e-12)
+    assert Th - ETA * V[0] == pytest.approx(want, rel=1e-12)
