@@ -72,7 +72,7 @@ def bytes_per_update(N, w):
 # DRAM bytes (read + write) per element of the tensor-core kernels, from the
 # full ncu capture of the 374,400-tet box (profiles/tensor_core_kernels_box40.md);
 # a launch's traffic is scaled from it by the number of elements
-TC_DRAM_BYTES_PER_ELEMENT = {"local_tc_kernel": 7135.7, "neighbour_tc_kernel": 10723.0}
+TC_DRAM_BYTES_PER_ELEMENT = {"local_tc_kernel": 7012.7, "neighbour_tc_kernel": 10538.1}
 
 
 def load_peaks():
@@ -260,7 +260,7 @@ def run_other_workload(args):
     __graft_entry__.build()
     import paper_2107_06640_gb300 as pkg
     from paper_2107_06640_gb300 import Solver, _lib
-    from synthetic.workloads import coupled_box, fault_box, rs_fault_params, uplift_scenarios
+    from synthetic.workloads import coupled_box, fault_box, lsw_fault_params, rs_fault_params, uplift_scenarios
     torch.cuda.set_device(0)
     stream = torch.cuda.current_stream()
     steps, warm = args.steps, args.warmup
@@ -283,7 +283,7 @@ def run_other_workload(args):
                                       f"{s.nt} tets, degree 5", "n_tets": s.nt, "clusters": hist,
                           "lts_update_reduction": gts_upd / upd, "macro_dt": info.macro_dt}
         line["dtype"] = "f32 (3xTF32 tensor-core products)"
-    elif args.workload == "rupture":
+    elif args.workload in ("rupture", "rupture-lsw"):
         r = 3
         m, (rho, lam, mu) = fault_box(nx=32 * r, ny=40 * r, nz=16 * r, dz=1e3 / r, dip_deg=15.0,
                                       ocean_layers=2 * r, water=2e3)
@@ -292,11 +292,17 @@ def run_other_workload(args):
         nff = int(s.info.n_fault_faces)
         mf, pf, fxyz, fn = _lib.adg_fault_faces(s.ctx, nff, s.Bf)
         c = fxyz.reshape(-1, 3).mean(0)
-        par = rs_fault_params(fxyz, fn, seed=0, patch_center=c, patch_radius=8e3)
+        if args.workload == "rupture-lsw":
+            _lib.adg_set_friction_law(s.ctx, _lib.ADG_FRICTION_LSW)
+            par = lsw_fault_params(fxyz, fn, seed=0, patch_center=c, patch_radius=8e3, taper=10e3)
+            law = "linear slip-weakening friction (cohesion rising toward the seafloor)"
+        else:
+            par = rs_fault_params(fxyz, fn, seed=0, patch_center=c, patch_radius=8e3)
+            law = "rate-and-state fast-velocity-weakening friction"
         _lib.adg_set_fault(s.ctx, par[:, None])
         upd = int(s.info.updates_per_macro)
         line["config"] = {"workload": f"15-degree planar megathrust 150 x 60 km under 2 km ocean with gravity, "
-                                      f"rate-and-state fast-velocity-weakening friction, {s.nt} tets, degree 4",
+                                      f"{law}, {s.nt} tets, degree 4",
                           "n_tets": s.nt, "fault_faces": nff, "fault_nodes": nff * s.Bf}
         line["dtype"] = "f32 (friction f64)"
     else:
@@ -320,6 +326,11 @@ def run_other_workload(args):
     line["kernel_ms"] = {"local": kms[0], "neighbour": kms[1], "rupture": kms[2],
                          "launches_per_macro": [int(x) for x in kcnt[:3]]}
     line["gpu_launches"] = int(kcnt[:3].sum()) * steps
+    if args.workload == "rupture-lsw":
+        st = _lib.adg_read_fault(s.ctx, np.empty((nff, 1, s.Bf, 8)))
+        line["rupture"] = {"slipping_node_fraction": float(np.mean(st[..., 0] > 1e-3)),
+                           "max_slip_rate": float(st[..., 0].max()), "max_slip_path": float(st[..., 1].max()),
+                           "friction_kernel_ms": kms[2]}
     if args.workload == "rupture":
         solves, iters = _lib.adg_fault_stats(s.ctx, reset=True)
         # learned Newton start: capture, train on the GPU, rerun the same steps
@@ -355,8 +366,8 @@ def main():
                     help="hex columns per side (80: the 1.5 M-tet workload; smaller for profiling)")
     ap.add_argument("--only", default=None, choices=["fp64", "fp32", "3xtf32"],
                     help="profiling aid: run one precision of the coupled workload, print no JSON line")
-    ap.add_argument("--workload", default="coupled", choices=["coupled", "lts", "rupture", "ensemble"],
-                    help="coupled: the headline line; lts / rupture / ensemble: the other workloads")
+    ap.add_argument("--workload", default="coupled", choices=["coupled", "lts", "rupture", "rupture-lsw", "ensemble"],
+                    help="coupled: the headline line; lts / rupture / rupture-lsw / ensemble: the other workloads")
     ap.add_argument("--clock-dir", default=None,
                     help="directory for the nvidia-smi clock samples of each timed region (default: the temp dir)")
     args = ap.parse_args()

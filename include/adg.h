@@ -217,6 +217,20 @@ int adg_read_receivers(adg_ctx* ctx, double* out);
  * adg_fault_stats: friction solves and Newton iterations so far (reset if asked). */
 int adg_fault_faces(adg_ctx* ctx, int64_t* minus_face, int64_t* plus_face, double* node_xyz, double* normal);
 int adg_set_fault(adg_ctx* ctx, const double* par);
+
+/* Friction law of the fault faces: ADG_FRICTION_RS (default, above) or
+ * ADG_FRICTION_LSW, linear slip weakening (the Scenario-A fault of Sec. 5,
+ * law of Andrews 1976): psi = slip path length, dpsi/dt = |V|,
+ * f = mu_s - (mu_s - mu_d) min(psi/D_c, 1), strength tau_S = C + f S, and at
+ * each time point |V| = max(0, Theta - tau_S)/eta_s in closed form (the same
+ * time points and two passes as for rate and state; no Newton, no learned
+ * start).  Its adg_set_fault parameters [13] are mu_s, mu_d, D_c (> 0),
+ * cohesion C (>= 0), three unused slots, sigma_n0, tau0 (3), psi_init (>= 0),
+ * V_init (>= 0), with mu_s >= mu_d >= 0.  Requires fault faces; clears the
+ * parameters, so adg_set_fault follows it.  ADG_E_INVALID for another law. */
+#define ADG_FRICTION_RS 0
+#define ADG_FRICTION_LSW 1
+int adg_set_friction_law(adg_ctx* ctx, int law);
 int adg_read_fault(adg_ctx* ctx, double* state);
 int adg_fault_stats(adg_ctx* ctx, int64_t* solves, int64_t* iterations, int reset);
 

@@ -16,6 +16,7 @@ LIB_PATH = os.path.join(_HERE, "lib", "libadg.so")
 
 ADG_OK = 0
 ADG_FP64, ADG_FP32, ADG_3XTF32 = 0, 1, 2
+ADG_FRICTION_RS, ADG_FRICTION_LSW = 0, 1
 ERRORS = {-1: "INVALID", -2: "MESH", -3: "STATE", -4: "CUDA", -5: "NOMEM", -6: "NAN",
           -7: "NEWTON", -8: "TIMEOUT", -9: "NOT_READY"}
 
@@ -64,6 +65,7 @@ _SIGS = {
     "adg_step_noalloc": (C.c_int, [_P, _P, C.c_int, _P]),
     "adg_fault_faces": (C.c_int, [_P, _P, _P, _P, _P]),
     "adg_set_fault": (C.c_int, [_P, _P]),
+    "adg_set_friction_law": (C.c_int, [_P, C.c_int]),
     "adg_read_fault": (C.c_int, [_P, _P]),
     "adg_fault_stats": (C.c_int, [_P, _P, _P, C.c_int]),
     "adg_rupture_capture": (C.c_int, [_P, C.c_int64, _P]),
@@ -242,6 +244,10 @@ def adg_fault_faces(ctx, nff, Bf):
 def adg_set_fault(ctx, par):
     par = _f64(par)
     _check(ctx, load().adg_set_fault(ctx, _ptr(par)))
+
+
+def adg_set_friction_law(ctx, law):
+    _check(ctx, load().adg_set_friction_law(ctx, int(law)))
 
 
 def adg_read_fault(ctx, out):

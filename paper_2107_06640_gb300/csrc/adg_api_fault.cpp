@@ -84,14 +84,30 @@ int adg_set_fault(adg_ctx* ctx, const double* par) {
     std::vector<double> st(npts * adg::FSTATE, 0.0);
     for (size_t k = 0; k < npts; ++k) {
       const double* p = par + k * adg::FPAR;
-      if (!(p[0] > 0) || !(p[2] > 0) || !(p[4] > 0) || !(p[6] > 0) || !(p[12] > 0))
+      if (c.fric_law == ADG_FRICTION_LSW) {
+        if (!(p[1] >= 0) || !(p[0] >= p[1]) || !(p[2] > 0) || !(p[3] >= 0) || !(p[11] >= 0) || !(p[12] >= 0))
+          adg::throw_err(ADG_E_INVALID,
+                         "slip-weakening parameters: need mu_s >= mu_d >= 0, D_c > 0, cohesion >= 0, "
+                         "initial slip path and slip rate >= 0");
+      } else if (!(p[0] > 0) || !(p[2] > 0) || !(p[4] > 0) || !(p[6] > 0) || !(p[12] > 0)) {
         adg::throw_err(ADG_E_INVALID, "fault parameters: a, L, V0, V_w and the initial slip rate must be positive");
+      }
       st[k * adg::FSTATE + 0] = p[12];
       st[k * adg::FSTATE + 1] = p[11];
     }
     cuda_ok(cudaMemcpy(c.dFpar, par, npts * adg::FPAR * 8, cudaMemcpyHostToDevice), "fault parameters");
     cuda_ok(cudaMemcpy(c.dFstate, st.data(), st.size() * 8, cudaMemcpyHostToDevice), "fault state");
     c.fault_set = true;
+  });
+}
+
+int adg_set_friction_law(adg_ctx* ctx, int law) {
+  if (!ctx || (law != ADG_FRICTION_RS && law != ADG_FRICTION_LSW)) return ADG_E_INVALID;
+  return guard(ctx, [&] {
+    Ctx& c = ctx->c;
+    need_faults(c);
+    c.fric_law = law;
+    c.fault_set = false;  // the parameters mean other things under the other law
   });
 }
 

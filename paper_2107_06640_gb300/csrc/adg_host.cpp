@@ -741,6 +741,7 @@ void Ctx::launch_rupture_cluster(int c, double dt) {
   d.capture = cap_on ? dCapture : nullptr;
   d.cap_count = dCapCount;
   d.cap_capacity = cap_capacity;
+  d.law = fric_law;
   ProfEv ev{2, nullptr, nullptr, 1};
   if (prof) {
     CK(cudaEventCreate(&ev.a));

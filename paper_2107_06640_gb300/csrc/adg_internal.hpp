@@ -86,6 +86,7 @@ struct Ctx {
   // friction-guess network and training-sample capture
   float* dMlp = nullptr;
   bool mlp_on = false;
+  int fric_law = 0;  // ADG_FRICTION_RS / ADG_FRICTION_LSW
   float* dCapture = nullptr;
   unsigned long long* dCapCount = nullptr;
   int64_t cap_capacity = 0;

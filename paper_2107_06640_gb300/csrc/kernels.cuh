@@ -112,7 +112,10 @@ struct DRArgs {
   float* capture;       // training samples [cap][MLP_IN + 1] (or null)
   unsigned long long* cap_count;
   int64_t cap_capacity;
+  int law;              // FRIC_RS or FRIC_LSW
 };
+
+enum { FRIC_RS = 0, FRIC_LSW = 1 };  // the ADG_FRICTION_* values of adg.h
 
 int launch_rupture(int fp64, int N, const DRArgs& a, void* stream);
 

@@ -21,6 +21,12 @@
 // Newton starts from the warm start plus the change of the predicted ln V*
 // since point j-1 (exact where nothing changes), at j = 0 from the warm
 // start; a start that fails falls back to the warm start.
+// Linear slip weakening (law FRIC_LSW; the Scenario-A fault of Sec. 5, law of
+// Andrews 1976): the parameter slots a, b, L, f0 hold mu_s, mu_d, D_c and the
+// cohesion C; psi is the slip path length, dpsi/dt = |V|,
+// f = mu_s - (mu_s - mu_d) min(psi/D_c, 1), strength tau_S = C + f S and
+// |V| = max(0, Theta - tau_S)/eta_s in closed form, with the same time points
+// and two passes (psi advanced exactly for a frozen slip rate: psi + |V| h).
 // Output per fault face: the time-integrated flux n.(A,B,C) q^b for the minus
 // element (minus node order) and -n.(A,B,C) q^c for the plus element (plus
 // node order); the neighbour kernel lifts them.
@@ -214,7 +220,8 @@ __global__ void __launch_bounds__(128) rupture_kernel(DRArgs a) {
     double x0 = xw;
     double xa = 0.0;  // asinh asymptote: the base of the network's prediction
     float feat[MLP_IN];
-    const bool solve = (Th > 0) && (S > 0);
+    const bool lsw = a.law == FRIC_LSW;
+    const bool solve = (Th > 0) && (S > 0) && !lsw;
     bool learned = false;
     if (solve && (a.mlp || a.capture)) {
       const double lc = psi / p.a - log(2.0 * p.V0);
@@ -245,7 +252,17 @@ __global__ void __launch_bounds__(128) rupture_kernel(DRArgs a) {
     double Vcur = exp(x0);
     if (!(Vcur > 0)) Vcur = 0.0;
     double psi_new = psi;
-    for (int pass = 0; pass < 2; ++pass) {
+    if (lsw) {
+      // mu_s, mu_d, D_c, C in the slots a, b, L, f0
+      Vcur = V;
+      for (int pass = 0; pass < 2; ++pass) {
+        const double Vmid = pass == 0 ? Vold : 0.5 * (Vold + Vcur);
+        psi_new = psi + Vmid * h;
+        const double f = p.a - (p.a - p.b) * fmin(psi_new / p.L, 1.0);
+        Vcur = fmax(0.0, Th - (p.f0 + f * S)) / eta;
+      }
+    }
+    for (int pass = 0; pass < (lsw ? 0 : 2); ++pass) {
       // the start guess only seeds Newton; pass 0 relaxes psi with the previous
       // slip rate, pass 1 with the mid-point of the previous and pass-0 rates
       const double Vmid = pass == 0 ? Vold : 0.5 * (Vold + Vcur);
@@ -291,7 +308,7 @@ __global__ void __launch_bounds__(128) rupture_kernel(DRArgs a) {
     ahat(nrm, tb, vc, rhop, lamp, mup, -1.0, a.tw[j], Gp);
     tprev = t;
   }
-  psi = psi_relax(psi, V, a.dt - tprev, p);
+  psi = a.law == FRIC_LSW ? psi + V * (a.dt - tprev) : psi_relax(psi, V, a.dt - tprev, p);
   st[0] = V;
   st[1] = psi;
   for (int i = 0; i < 3; ++i) {

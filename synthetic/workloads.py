@@ -159,6 +159,37 @@ def rs_fault_params(node_xyz, normal, seed=0, patch_center=None, patch_radius=3e
     return out
 
 
+def lsw_fault_params(node_xyz, normal, seed=0, patch_center=None, patch_radius=3e3, sn0=-40e6, mu_s=0.6,
+                     mu_d=0.4, Dc=0.5, tau_ratio=0.48, patch_ratio=0.62, noise=0.05, C_top=2e6, taper=2e3):
+    """Per-node linear slip-weakening parameters [nff, Bf, 13] (mu_s, mu_d,
+    D_c, cohesion C, three unused, sigma_n0, tau0_xyz, psi_init = 0,
+    V_init = 0): mu_s, mu_d, D_c with seeded +-noise relative perturbations
+    (mu_d kept <= mu_s); uniform normal stress sn0 (compression negative);
+    shear prestress along the up-dip direction with |tau0| = tau_ratio |sn0|,
+    between the dynamic and static strengths, raised to patch_ratio |sn0|
+    (above the static strength) in a circular nucleation patch; cohesion
+    rising linearly from 0 at depth `taper` below the fault's top edge to C_top
+    there, so the fault is stronger toward the seafloor (Sec. 5, Scenario A)."""
+    rng = np.random.default_rng(seed)
+    nff, Bf, _ = node_xyz.shape
+    out = np.zeros((nff, Bf, 13))
+    for k, v in enumerate((mu_s, mu_d, Dc)):
+        out[..., k] = v * (1.0 + noise * rng.uniform(-1.0, 1.0, (nff, Bf)))
+    out[..., 1] = np.minimum(out[..., 1], out[..., 0])
+    z = node_xyz[..., 2]
+    out[..., 3] = C_top * np.clip(1.0 - (z.max() - z) / taper, 0.0, 1.0)
+    out[..., 7] = sn0
+    up = np.array([0.0, 0.0, 1.0])
+    d = up[None, :] - np.sum(normal * up, 1, keepdims=True) * normal
+    d /= np.maximum(np.linalg.norm(d, axis=1, keepdims=True), 1e-30)
+    if patch_center is None:
+        patch_center = node_xyz.reshape(-1, 3).mean(0)
+    r = np.linalg.norm(node_xyz - np.asarray(patch_center)[None, None, :], axis=2)
+    mag = np.where(r < patch_radius, patch_ratio, tau_ratio) * abs(sn0)
+    out[..., 8:11] = mag[..., None] * d[:, None, :]
+    return out
+
+
 def random_dofs(shape, seed, decay=0.5, N=None):
     """Seeded random modal coefficients (any basis layout); optional decay by
     basis index keeps higher modes smaller."""

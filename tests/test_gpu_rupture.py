@@ -6,7 +6,7 @@ import pytest
 
 from oracle import mlp as omlp
 from oracle import rupture as ru
-from synthetic.workloads import fault_box, random_dofs, rs_fault_params
+from synthetic.workloads import fault_box, lsw_fault_params, random_dofs, rs_fault_params
 from tests._cases import make_pair, rel_l2, to_gpu_layout, to_oracle_layout
 
 pytestmark = pytest.mark.gpu
@@ -19,7 +19,7 @@ def built():
     build.build()
 
 
-def _fault_pair(N=3, ocean_layers=0, max_clusters=1, precision=0, **kw):
+def _fault_pair(N=3, ocean_layers=0, max_clusters=1, precision=0, law="rs", **kw):
     m, mat = fault_box(nx=4, ny=2, nz=4, dz=1e3, ocean_layers=ocean_layers, **kw)
     o, s = make_pair(m, mat, N, precision=precision, cfl=0.5, max_clusters=max_clusters)
     nff = int(s.info.n_fault_faces)
@@ -29,9 +29,15 @@ def _fault_pair(N=3, ocean_layers=0, max_clusters=1, precision=0, **kw):
     assert np.array_equal(mf, o.fm[:, 0] * 4 + o.fm[:, 1])
     assert np.array_equal(pf, o.fp[:, 0] * 4 + o.fp[:, 1])
     assert np.allclose(xyz, o.f_xyz, rtol=0, atol=1e-9) and np.allclose(nrm, o.f_n, atol=1e-14)
-    par = rs_fault_params(xyz, nrm, seed=1, patch_radius=2e3)
+    if law == "lsw":
+        par = lsw_fault_params(xyz, nrm, seed=1, patch_radius=2e3)
+        _lib.adg_set_friction_law(s.ctx, _lib.ADG_FRICTION_LSW)
+        names = ru.LSW_PARAMS
+    else:
+        par = rs_fault_params(xyz, nrm, seed=1, patch_radius=2e3)
+        names = ru.PARAMS
     _lib.adg_set_fault(s.ctx, par[:, None, :, :])
-    o.set_fault({k: par[..., i] for i, k in enumerate(ru.PARAMS)})
+    o.set_fault({k: par[..., i] for i, k in enumerate(names)}, law=law)
     return m, o, s, nff
 
 
@@ -72,6 +78,43 @@ def test_rupture_under_ocean_with_lts_fp64():
         o.advance_macro()
     s.advance(2)
     _compare(o, s, nff)
+
+
+def test_slip_weakening_parity_fp64():
+    """Linear slip weakening (closed-form slip rate): dofs, slip rate, slip
+    path, slip and traction against the oracle after 5 steps; the nucleation
+    patch ruptures and no Newton solve runs."""
+    m, o, s, nff = _fault_pair(law="lsw")
+    Q0 = random_dofs((m.nt, s.B, 9), 4, N=3) * 1e3
+    o.Q = Q0.copy()
+    s.set_dofs(to_gpu_layout(Q0))
+    for _ in range(5):
+        o.step_gts()
+    s.advance(5)
+    st = _compare(o, s, nff)
+    assert st[..., 0].max() > 0.1 and st[..., 1].max() > 0
+    assert np.all(st[..., 0] >= 0) and np.all(st[..., 1] >= 0)
+    from paper_2107_06640_gb300 import _lib
+    solves, iters = _lib.adg_fault_stats(s.ctx)
+    assert solves == 0 and iters == 0
+
+
+def test_slip_weakening_under_ocean_with_lts_fp64():
+    m, o, s, nff = _fault_pair(N=2, ocean_layers=1, max_clusters=3, law="lsw")
+    for _ in range(2):
+        o.advance_macro()
+    s.advance(2)
+    _compare(o, s, nff)
+
+
+def test_friction_law_switch_needs_new_parameters():
+    from paper_2107_06640_gb300 import AdgError, _lib
+    m, o, s, nff = _fault_pair(law="lsw")
+    _lib.adg_set_friction_law(s.ctx, _lib.ADG_FRICTION_RS)
+    with pytest.raises(AdgError):
+        s.advance(1)  # parameters cleared by the switch
+    with pytest.raises(AdgError):
+        _lib.adg_set_friction_law(s.ctx, 7)
 
 
 def test_mlp_gradient_matches_oracle():
