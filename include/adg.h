@@ -122,6 +122,15 @@ int adg_query(const adg_ctx* ctx, adg_info* out);
 /* Dofs in user tet order, layout [nt][S][9][B] (host, double). */
 int adg_set_dofs(adg_ctx* ctx, const double* Q);
 int adg_get_dofs(adg_ctx* ctx, double* Q);
+/* The same in FP32 host arrays, [nt][S][9][B] floats: one copy over the host
+ * link (at full speed from pinned memory: cudaHostAlloc, cudaHostRegister or
+ * a pinned torch tensor), the reordering to the library's element order and
+ * the conversion to the dofs precision run on the device.  The trace array is
+ * the device scratch, so these calls need a macro-step boundary (always the
+ * case after adg_advance / adg_advance_to); ADG_E_STATE otherwise.  The host
+ * array is borrowed for the call; both calls return after their copy. */
+int adg_set_dofs_f32(adg_ctx* ctx, const float* Q);
+int adg_get_dofs_f32(adg_ctx* ctx, float* Q);
 
 /* Initial condition by projection: adg_initial_points returns, for every tet,
  * n_pts physical points (xyz[nt][n_pts][3]); the caller evaluates its field

@@ -51,6 +51,8 @@ _SIGS = {
     "adg_query": (C.c_int, [_P, C.POINTER(adg_info)]),
     "adg_set_dofs": (C.c_int, [_P, _P]),
     "adg_get_dofs": (C.c_int, [_P, _P]),
+    "adg_set_dofs_f32": (C.c_int, [_P, _P]),
+    "adg_get_dofs_f32": (C.c_int, [_P, _P]),
     "adg_initial_points": (C.c_int, [_P, C.POINTER(C.c_int), _P]),
     "adg_set_initial_values": (C.c_int, [_P, _P]),
     "adg_gravity_faces": (C.c_int, [_P, _P, _P]),
@@ -162,6 +164,18 @@ def adg_set_dofs(ctx, Q):
 def adg_get_dofs(ctx, out):
     assert out.dtype == np.float64 and out.flags.c_contiguous
     _check(ctx, load().adg_get_dofs(ctx, _ptr(out)))
+    return out
+
+
+def adg_set_dofs_f32(ctx, Q):
+    """Q: float32 [tet][S][9][B] (pinned host memory for full speed)."""
+    Q = np.ascontiguousarray(Q, dtype=np.float32)
+    _check(ctx, load().adg_set_dofs_f32(ctx, _ptr(Q)))
+
+
+def adg_get_dofs_f32(ctx, out):
+    assert out.dtype == np.float32 and out.flags.c_contiguous
+    _check(ctx, load().adg_get_dofs_f32(ctx, _ptr(out)))
     return out
 
 

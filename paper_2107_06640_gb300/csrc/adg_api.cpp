@@ -111,6 +111,18 @@ void take_dofs(Ctx& c, double* Q) {
   check_cuda(err, "dofs download");
 }
 
+// FP32 dofs to or from the caller go through the trace array as device
+// scratch: between macro steps no trace is pending, and 4 S_f >= 9 B for every
+// supported degree.
+float* dofs_scratch(Ctx& c) {
+  if (c.tick % (1 << (c.ncl - 1)))
+    adg::throw_err(ADG_E_STATE, "FP32 dofs transfer: only at a macro-step boundary");
+  const size_t need = (size_t)c.nt * c.S * 9 * c.B * sizeof(float);
+  const size_t have = (size_t)c.nt * c.S * 4 * adg::face_stride(c.N) * (c.fp64 ? 8 : 4);
+  if (need > have) adg::throw_err(ADG_E_INVALID, "FP32 dofs transfer: scratch too small");
+  return static_cast<float*>(c.dTrace);
+}
+
 void run_ticks_to_boundary(Ctx& c) {
   const int ticks = 1 << (c.ncl - 1);
   while (c.tick % ticks) {
@@ -233,6 +245,38 @@ int adg_get_dofs(adg_ctx* ctx, double* Q) {
     need_init(ctx->c);
     if (ctx->c.fp64) take_dofs<double>(ctx->c, Q);
     else take_dofs<float>(ctx->c, Q);
+  });
+}
+
+int adg_set_dofs_f32(adg_ctx* ctx, const float* Q) {
+  if (!ctx || !Q) return ADG_E_INVALID;
+  return guard(ctx, [&] {
+    Ctx& c = ctx->c;
+    need_init(c);
+    float* scratch = dofs_scratch(c);
+    const int per = c.S * 9 * c.B;
+    check_cuda(cudaMemcpyAsync(scratch, Q, (size_t)c.nt * per * sizeof(float), cudaMemcpyHostToDevice, c.stream),
+               "dofs upload");
+    check_cuda((cudaError_t)adg::launch_permute_dofs(c.fp64, 1, scratch, c.dQ, c.dOrder, c.nt, per, c.n_sms,
+                                                      c.stream),
+               "dofs upload");
+    check_cuda(cudaStreamSynchronize(c.stream), "dofs upload");
+  });
+}
+
+int adg_get_dofs_f32(adg_ctx* ctx, float* Q) {
+  if (!ctx || !Q) return ADG_E_INVALID;
+  return guard(ctx, [&] {
+    Ctx& c = ctx->c;
+    need_init(c);
+    float* scratch = dofs_scratch(c);
+    const int per = c.S * 9 * c.B;
+    check_cuda((cudaError_t)adg::launch_permute_dofs(c.fp64, 0, c.dQ, scratch, c.dOrder, c.nt, per, c.n_sms,
+                                                      c.stream),
+               "dofs download");
+    check_cuda(cudaMemcpyAsync(Q, scratch, (size_t)c.nt * per * sizeof(float), cudaMemcpyDeviceToHost, c.stream),
+               "dofs download");
+    check_cuda(cudaStreamSynchronize(c.stream), "dofs download");
   });
 }
 

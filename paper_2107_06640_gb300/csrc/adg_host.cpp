@@ -569,6 +569,7 @@ void Ctx::setup() {
   const int64_t V = E * S;
   dQ = dalloc((size_t)V * 9 * B * ts, owned, dev_bytes);
   dTrace = dalloc((size_t)V * 4 * face_stride(N) * ts, owned, dev_bytes);
+  dOrder = upload_raw(order, owned, dev_bytes);
   dBtrace = (double*)dalloc((size_t)nb_slots * S * 36 * Bf * 8, owned, dev_bytes);
   dDtrace = dalloc((size_t)nd_slots * S * (N + 1) * 9 * Bf * ts, owned, dev_bytes);
   dEta = (double*)dalloc((size_t)ng * S * Bf * 8, owned, dev_bytes);

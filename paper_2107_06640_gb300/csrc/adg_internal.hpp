@@ -27,6 +27,8 @@ int launch_mlp_grad(const float* P, const float* rows, int64_t row0, int64_t n, 
 int launch_adam(float* P, const float* g, float* m, float* v, float lr, int step, void* stream);
 
 // receiver readout kernel launcher (readout.cu)
+int launch_permute_dofs(int fp64, int up, const void* in, void* out, const int64_t* order, int64_t nt, int per,
+                        int n_sms, void* stream);
 int launch_receivers(int fp64, int B, const void* Q, int S, int64_t n, const int64_t* elem,
                      const double* phi, double* out, void* stream);
 
@@ -64,6 +66,7 @@ struct Ctx {
   std::vector<void*> owned;
   int64_t dev_bytes = 0;
   void *dQ = nullptr, *dTrace = nullptr, *dDtrace = nullptr, *dGflux = nullptr;
+  int64_t* dOrder = nullptr;  // order on the device: the caller's element of library element i
   double *dBtrace = nullptr, *dEta = nullptr, *dGpar = nullptr;
   void *dPar = nullptr, *dFm = nullptr, *dFp = nullptr;
   void *dKt = nullptr, *dKvol = nullptr, *dEfc = nullptr, *dLift = nullptr;

@@ -55,6 +55,17 @@ class Solver:
         L.adg_get_dofs(self.ctx, out)
         return out[:, 0] if self.S == 1 else out
 
+    def set_dofs_f32(self, Q):
+        """Q: float32 [tet][S][9][B] (or [tet][9][B] when S == 1); at a macro-step boundary."""
+        L.adg_set_dofs_f32(self.ctx, Q)
+
+    def get_dofs_f32(self, out=None):
+        """Into out (float32 [tet][S][9][B], e.g. pinned) or a new array; at a macro-step boundary."""
+        if out is None:
+            out = np.empty((self.nt, self.S, 9, self.B), np.float32)
+        L.adg_get_dofs_f32(self.ctx, out)
+        return out
+
     def initial_points(self):
         return L.adg_initial_points(self.ctx, self.nt)
 

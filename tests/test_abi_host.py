@@ -23,7 +23,7 @@ def lib():
 
 def test_exports_every_declared_symbol(lib, root):
     hdr = open(os.path.join(root, "include", "adg.h")).read()
-    declared = set(re.findall(r"\b(adg_[a-z_]+)\s*\(", hdr))
+    declared = set(re.findall(r"\b(adg_[a-z0-9_]+)\s*\(", hdr))
     declared -= {"adg_ctx"}
     L = lib.load()
     for name in declared:

@@ -171,6 +171,40 @@ def test_lts_two_clusters_fp64():
     assert rel_l2(to_oracle_layout(s.get_dofs()), o.Q) <= FP64_TOL
 
 
+
+@pytest.mark.parametrize("N", [3, 4])
+def test_f32_dofs_transfer(N):
+    """adg_set_dofs_f32 / adg_get_dofs_f32 (device-side reordering; rows of
+    S 9 B = 360 values at N = 3 move in 16-byte chunks, 630 at N = 4 one by
+    one): the caller's order survives bit for bit in both dofs precisions, the
+    double API sees the same values, a step from an FP32 upload equals the step
+    from the same values through the double API, and a call inside an LTS macro
+    step is refused."""
+    from paper_2107_06640_gb300 import ADG_FP32, ADG_FP64, AdgError, Solver
+    m, (rho, lam, mu) = small_coupled()
+    rng = np.random.default_rng(5)
+    for prec in (ADG_FP32, ADG_FP64):
+        kw = dict(degree=N, cfl=0.5, precision=prec, ensemble=2)
+        a = Solver(m.xyz, m.tets, m.face_tag, rho, lam, mu, **kw)
+        b = Solver(m.xyz, m.tets, m.face_tag, rho, lam, mu, **kw)
+        Q32 = (rng.standard_normal((m.nt, 2, 9, a.B)) * 1e-2).astype(np.float32)
+        a.set_dofs_f32(Q32)
+        assert np.array_equal(a.get_dofs_f32(), Q32)
+        assert np.array_equal(a.get_dofs(), Q32.astype(np.float64))
+        b.set_dofs(Q32.astype(np.float64))
+        a.advance(1)
+        b.advance(1)
+        assert np.array_equal(a.get_dofs(), b.get_dofs())
+        assert np.array_equal(a.get_dofs_f32(), b.get_dofs().astype(np.float32))
+    w = _warped_periodic(4)
+    s = Solver(w.xyz, w.tets, w.face_tag, *syn.elastic_uniform(w.nt), face_partner=w.face_partner, degree=3,
+               cfl=0.5, max_clusters=3)
+    assert s.info.n_clusters >= 2
+    s.step_tick()
+    with pytest.raises(AdgError) as ei:
+        s.set_dofs_f32(np.zeros((w.nt, 9, s.B), np.float32))
+    assert ei.value.code == -3
+
 def test_lts_coupled_graded_fp64():
     m, mat = syn.workloads.coupled_box(nxy=4, n_water=2, n_crust=2, L=8e3, depth=4e3, water=1e3,
                                        grading=4.0)
