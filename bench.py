@@ -305,6 +305,18 @@ def run_other_workload(args):
                                       f"{law}, {s.nt} tets, degree 4",
                           "n_tets": s.nt, "fault_faces": nff, "fault_nodes": nff * s.Bf}
         line["dtype"] = "f32 (friction f64)"
+    elif args.workload == "record":
+        m, (rho, lam, mu), Q0 = make_workload(seed=0, nxy=args.nxy)
+        s = Solver(m.xyz, m.tets, m.face_tag, rho, lam, mu, degree=N_DEG, precision=pkg.ADG_3XTF32, cfl=0.35,
+                   stream=stream.cuda_stream)
+        s.set_dofs(Q0)
+        s.set_eta(np.zeros((int(s.info.n_gravity_faces), 1, s.Bf)))
+        pick = np.random.default_rng(0).choice(m.nt, 1000, replace=False)
+        s.add_receivers(m.xyz[m.tets[pick]].mean(1))
+        upd = int(s.info.updates_per_macro)
+        line["config"] = {"workload": f"coupled ocean-crust box, {s.nt} tets, degree 5, recording 1000 receivers "
+                                      f"and the sea surface every macro step", "n_tets": s.nt}
+        line["dtype"] = "f32 (3xTF32 tensor-core products)"
     else:
         S = 32
         m, (rho, lam, mu) = coupled_box(nxy=66)
@@ -326,6 +338,22 @@ def run_other_workload(args):
     line["kernel_ms"] = {"local": kms[0], "neighbour": kms[1], "rupture": kms[2],
                          "launches_per_macro": [int(x) for x in kcnt[:3]]}
     line["gpu_launches"] = int(kcnt[:3].sum()) * steps
+    if args.workload == "record":
+        # the same steps again while both kinds are recorded every macro step
+        R, H = _lib.ADG_RECORD_RECEIVERS, _lib.ADG_RECORD_SSH
+        s.record(R, 1, steps + warm)
+        s.record(H, 1, steps + warm)
+        ms_r, clk_r = _timed_advance(s, steps, warm, stream, torch, "record_on")
+        tr, _, dr = s.read_record(R)
+        th, _, dh = s.read_record(H)
+        n_ssh = int(s.info.n_gravity_faces) * s.Bf
+        line["recording"] = {"receivers": 1000, "ssh_values": n_ssh, "every_macro_steps": 1,
+                             "bytes_per_step": (1000 * 9 + n_ssh) * 8,
+                             "ms_per_step_without": ms / steps, "ms_per_step_with": ms_r / steps,
+                             "overhead": ms_r / ms - 1.0, "samples": [len(tr), len(th)], "dropped": [dr, dh],
+                             "clocks_with": clk_r}
+        line["value"] = upd * steps / (ms_r * 1e-3)
+        line["ms_per_step"] = ms_r / steps
     if args.workload == "rupture-lsw":
         st = _lib.adg_read_fault(s.ctx, np.empty((nff, 1, s.Bf, 8)))
         line["rupture"] = {"slipping_node_fraction": float(np.mean(st[..., 0] > 1e-3)),
@@ -366,8 +394,10 @@ def main():
                     help="hex columns per side (80: the 1.5 M-tet workload; smaller for profiling)")
     ap.add_argument("--only", default=None, choices=["fp64", "fp32", "3xtf32"],
                     help="profiling aid: run one precision of the coupled workload, print no JSON line")
-    ap.add_argument("--workload", default="coupled", choices=["coupled", "lts", "rupture", "rupture-lsw", "ensemble"],
-                    help="coupled: the headline line; lts / rupture / rupture-lsw / ensemble: the other workloads")
+    ap.add_argument("--workload", default="coupled",
+                    choices=["coupled", "lts", "rupture", "rupture-lsw", "ensemble", "record"],
+                    help="coupled: the headline line; lts / rupture / rupture-lsw / ensemble / record: the other "
+                         "workloads")
     ap.add_argument("--clock-dir", default=None,
                     help="directory for the nvidia-smi clock samples of each timed region (default: the temp dir)")
     args = ap.parse_args()

@@ -205,6 +205,33 @@ int adg_step_noalloc(adg_ctx* ctx, void* d_Q, int n_steps, void* stream);
 int adg_add_receivers(adg_ctx* ctx, int64_t n, const double* xyz);
 int adg_read_receivers(adg_ctx* ctx, double* out);
 
+/* ---- Recording at a cadence (receivers and sea-surface height) --------------
+ * Output streams at fixed cadences while adg_advance / adg_advance_to run,
+ * e.g. receivers every 0.01 s and the sea surface every 0.1 s (Sec. 6).  After
+ * every `every`-th macro step of those calls the library takes a sample on
+ * its stream, into a device ring of `capacity` samples:
+ *   ADG_RECORD_RECEIVERS  the receivers as adg_read_receivers, [n_rec][S][9];
+ *   ADG_RECORD_SSH        eta as adg_read_ssh, [n_gravity_faces][S][Bf].
+ * A second stream copies each sample to a pinned host ring while the next
+ * steps run (an event orders it after the sample, and the slot is not
+ * rewritten before its copy is done).  Samples the caller has not read when
+ * the ring wraps are overwritten and counted as dropped.
+ * adg_record_start: (re)starts one kind with its cadence and capacity (>= 1);
+ *   ADG_E_INVALID if there is nothing of that kind (no receivers, no
+ *   gravitational faces).  Counting starts at the call.
+ * adg_record_read: moves up to max_samples of the oldest unread samples to the
+ *   caller: times t[k] (simulated time after the macro step) and data
+ *   [k][sample]; *n_read = samples moved, *n_dropped = overwritten so far
+ *   (either may be NULL).  Waits only for the copies of those samples.
+ * adg_record_stop: ends one kind and frees its rings.
+ * adg_add_receivers while receivers are being recorded: ADG_E_STATE. */
+#define ADG_RECORD_RECEIVERS 0
+#define ADG_RECORD_SSH 1
+int adg_record_start(adg_ctx* ctx, int kind, int every, int64_t capacity);
+int adg_record_read(adg_ctx* ctx, int kind, int64_t max_samples, double* t, double* data, int64_t* n_read,
+                    int64_t* n_dropped);
+int adg_record_stop(adg_ctx* ctx, int kind);
+
 /* ---- Dynamic rupture (Sec. 3, Eq. bc-dynrup) --------------------------------
  * Faces tagged ADG_TAG_FAULT on both sides (solid-solid).  Each tet pair is one
  * fault face; its minus side is the tet with the lower user index and n is that

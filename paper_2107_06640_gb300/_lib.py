@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(_HERE, "lib", "libadg.so")
 ADG_OK = 0
 ADG_FP64, ADG_FP32, ADG_3XTF32 = 0, 1, 2
 ADG_FRICTION_RS, ADG_FRICTION_LSW = 0, 1
+ADG_RECORD_RECEIVERS, ADG_RECORD_SSH = 0, 1
 ERRORS = {-1: "INVALID", -2: "MESH", -3: "STATE", -4: "CUDA", -5: "NOMEM", -6: "NAN",
           -7: "NEWTON", -8: "TIMEOUT", -9: "NOT_READY"}
 
@@ -52,6 +53,9 @@ _SIGS = {
     "adg_set_dofs": (C.c_int, [_P, _P]),
     "adg_get_dofs": (C.c_int, [_P, _P]),
     "adg_set_dofs_f32": (C.c_int, [_P, _P]),
+    "adg_record_start": (C.c_int, [_P, C.c_int, C.c_int, C.c_int64]),
+    "adg_record_read": (C.c_int, [_P, C.c_int, C.c_int64, _P, _P, _P, _P]),
+    "adg_record_stop": (C.c_int, [_P, C.c_int]),
     "adg_get_dofs_f32": (C.c_int, [_P, _P]),
     "adg_initial_points": (C.c_int, [_P, C.POINTER(C.c_int), _P]),
     "adg_set_initial_values": (C.c_int, [_P, _P]),
@@ -177,6 +181,24 @@ def adg_get_dofs_f32(ctx, out):
     assert out.dtype == np.float32 and out.flags.c_contiguous
     _check(ctx, load().adg_get_dofs_f32(ctx, _ptr(out)))
     return out
+
+
+def adg_record_start(ctx, kind, every, capacity):
+    _check(ctx, load().adg_record_start(ctx, int(kind), int(every), int(capacity)))
+
+
+def adg_record_read(ctx, kind, max_samples, sample):
+    """Up to max_samples unread samples of `sample` doubles each: (t, data[k][sample], dropped)."""
+    t = np.empty(max(int(max_samples), 0))
+    data = np.empty((max(int(max_samples), 0), int(sample)))
+    n, dropped = C.c_int64(0), C.c_int64(0)
+    _check(ctx, load().adg_record_read(ctx, int(kind), int(max_samples), _ptr(t), _ptr(data), C.byref(n),
+                                       C.byref(dropped)))
+    return t[: n.value], data[: n.value], dropped.value
+
+
+def adg_record_stop(ctx, kind):
+    _check(ctx, load().adg_record_stop(ctx, int(kind)))
 
 
 def adg_initial_points(ctx, n_tets):

@@ -2,6 +2,7 @@
 // reordering, host<->device copies and the time-stepping front end.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <exception>
@@ -388,6 +389,7 @@ int adg_advance(adg_ctx* ctx, int n_macro) {
     for (int i = 0; i < n_macro; ++i) {
       c.run_macro(1.0);
       c.tick += 1 << (c.ncl - 1);
+      c.record_after_macro();
     }
     c.check_err();
   });
@@ -404,11 +406,14 @@ int adg_advance_to(adg_ctx* ctx, double t) {
     while (c.time + macro <= t + 1e-12 * macro) {
       c.run_macro(1.0);
       c.tick += 1 << (c.ncl - 1);
+      c.record_after_macro();
     }
     const double rest = t - c.time;
     if (rest > 1e-12 * macro) {
       c.run_macro(rest / macro);
       c.tick += 1 << (c.ncl - 1);
+      c.time = t;
+      c.record_after_macro();
     }
     c.time = t;
     c.check_err();
@@ -508,6 +513,8 @@ int adg_add_receivers(adg_ctx* ctx, int64_t n, const double* xyz) {
   return guard(ctx, [&] {
     Ctx& c = ctx->c;
     need_init(c);
+    if (c.rec[ADG_RECORD_RECEIVERS].every)
+      adg::throw_err(ADG_E_STATE, "receivers are being recorded: adg_record_stop first");
     std::vector<int64_t> elem((size_t)n, -1);
     std::vector<double> phi((size_t)n * c.B);
     for (int64_t r = 0; r < n; ++r) {
@@ -577,6 +584,65 @@ int adg_read_receivers(adg_ctx* ctx, double* out) {
                "receiver download");
     check_cuda(cudaStreamSynchronize(c.stream), "receiver download");
   });
+}
+
+int adg_record_start(adg_ctx* ctx, int kind, int every, int64_t capacity) {
+  if (!ctx || (kind != ADG_RECORD_RECEIVERS && kind != ADG_RECORD_SSH) || every < 1 || capacity < 1)
+    return ADG_E_INVALID;
+  return guard(ctx, [&] {
+    Ctx& c = ctx->c;
+    need_init(c);
+    const size_t sample = kind == ADG_RECORD_RECEIVERS ? (size_t)c.n_rec * c.S * 9 : c.gfaces.size() * (size_t)c.S * c.Bf;
+    if (!sample)
+      adg::throw_err(ADG_E_INVALID, kind == ADG_RECORD_RECEIVERS ? "no receivers to record" : "no sea surface to record");
+    c.record_free(kind);
+    if (!c.rec_stream) check_cuda(cudaStreamCreateWithFlags(&c.rec_stream, cudaStreamNonBlocking), "record stream");
+    Ctx::Recorder& r = c.rec[kind];
+    r.sample = sample;
+    r.cap = capacity;
+    r.t.assign((size_t)capacity, 0.0);
+    r.taken.assign((size_t)capacity, nullptr);
+    r.copied.assign((size_t)capacity, nullptr);
+    for (int64_t k = 0; k < capacity; ++k) {
+      check_cuda(cudaEventCreateWithFlags(&r.taken[k], cudaEventDisableTiming), "record events");
+      check_cuda(cudaEventCreateWithFlags(&r.copied[k], cudaEventDisableTiming), "record events");
+    }
+    const size_t bytes = (size_t)capacity * sample * 8;
+    cudaError_t e = cudaMalloc((void**)&r.dRing, bytes);
+    if (e == cudaSuccess) e = cudaHostAlloc((void**)&r.hRing, bytes, cudaHostAllocDefault);
+    if (e != cudaSuccess) {
+      c.record_free(kind);
+      adg::throw_err(ADG_E_NOMEM, std::string("record rings: ") + cudaGetErrorString(e));
+    }
+    r.every = every;  // last: a failure above leaves the kind off
+  });
+}
+
+int adg_record_read(adg_ctx* ctx, int kind, int64_t max_samples, double* t, double* data, int64_t* n_read,
+                    int64_t* n_dropped) {
+  if (!ctx || (kind != ADG_RECORD_RECEIVERS && kind != ADG_RECORD_SSH) || max_samples < 0 ||
+      (max_samples > 0 && (!t || !data)))
+    return ADG_E_INVALID;
+  return guard(ctx, [&] {
+    Ctx& c = ctx->c;
+    Ctx::Recorder& r = c.rec[kind];
+    if (!r.every) adg::throw_err(ADG_E_STATE, "this kind is not being recorded");
+    const int64_t n = std::min(max_samples, r.count - r.read);
+    for (int64_t i = 0; i < n; ++i) {
+      const int64_t slot = (r.read + i) % r.cap;
+      check_cuda(cudaEventSynchronize(r.copied[slot]), "record copy");
+      std::memcpy(data + i * r.sample, r.hRing + slot * r.sample, r.sample * 8);
+      t[i] = r.t[slot];
+    }
+    r.read += n;
+    if (n_read) *n_read = n;
+    if (n_dropped) *n_dropped = r.dropped;
+  });
+}
+
+int adg_record_stop(adg_ctx* ctx, int kind) {
+  if (!ctx || (kind != ADG_RECORD_RECEIVERS && kind != ADG_RECORD_SSH)) return ADG_E_INVALID;
+  return guard(ctx, [&] { ctx->c.record_free(kind); });
 }
 
 int adg_save_state(adg_ctx* ctx, void* buf, size_t* len) {

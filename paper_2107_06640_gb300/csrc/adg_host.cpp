@@ -797,6 +797,45 @@ void Ctx::run_macro(double scale) {
   time += ticks * dtm;
 }
 
+// Cadence recording: after a macro step of adg_advance / adg_advance_to, take
+// the samples that are due into their device ring slots on the library stream
+// and queue each slot's copy to the pinned host ring on the recording stream.
+void Ctx::record_after_macro() {
+  for (int k = 0; k < 2; ++k) {
+    Recorder& r = rec[k];
+    if (!r.every || ++r.macro % r.every) continue;
+    const int64_t slot = r.count % r.cap;
+    if (r.count - r.read >= r.cap) {  // the oldest unread sample is overwritten
+      r.read++;
+      r.dropped++;
+    }
+    CK(cudaStreamWaitEvent(stream, r.copied[slot], 0));  // the slot's previous copy is done
+    double* d = r.dRing + slot * r.sample;
+    if (k == 0) {
+      const int rc = launch_receivers(fp64, B, dQ, S, n_rec, dRecElem, dRecPhi, d, stream);
+      if (rc) throw Err(ADG_E_CUDA, std::string("receiver kernel: ") + cudaGetErrorString((cudaError_t)rc));
+    } else {
+      CK(cudaMemcpyAsync(d, dEta, r.sample * 8, cudaMemcpyDeviceToDevice, stream));
+    }
+    CK(cudaEventRecord(r.taken[slot], stream));
+    CK(cudaStreamWaitEvent(rec_stream, r.taken[slot], 0));
+    CK(cudaMemcpyAsync(r.hRing + slot * r.sample, d, r.sample * 8, cudaMemcpyDeviceToHost, rec_stream));
+    CK(cudaEventRecord(r.copied[slot], rec_stream));
+    r.t[slot] = time;
+    r.count++;
+  }
+}
+
+void Ctx::record_free(int kind) {
+  Recorder& r = rec[kind];
+  if (rec_stream) cudaStreamSynchronize(rec_stream);
+  if (r.dRing) cudaFree(r.dRing);
+  if (r.hRing) cudaFreeHost(r.hRing);
+  for (cudaEvent_t e : r.taken) cudaEventDestroy(e);
+  for (cudaEvent_t e : r.copied) cudaEventDestroy(e);
+  r = Recorder();
+}
+
 void Ctx::check_err() {
   CK(cudaStreamSynchronize(stream));
   unsigned int h = 0;
@@ -810,6 +849,9 @@ void Ctx::check_err() {
 }
 
 Ctx::~Ctx() {
+  record_free(0);
+  record_free(1);
+  if (rec_stream) cudaStreamDestroy(rec_stream);
   if (graph_exec) cudaGraphExecDestroy(graph_exec);
   for (void* p : owned) cudaFree(p);
   if (hstage) cudaFreeHost(hstage);

@@ -26,9 +26,10 @@ int launch_mlp_grad(const float* P, const float* rows, int64_t row0, int64_t n, 
                     double* loss, void* stream);
 int launch_adam(float* P, const float* g, float* m, float* v, float lr, int step, void* stream);
 
-// receiver readout kernel launcher (readout.cu)
+// dofs reordering between the caller's and the library's element order (dofs_io.cu)
 int launch_permute_dofs(int fp64, int up, const void* in, void* out, const int64_t* order, int64_t nt, int per,
                         int n_sms, void* stream);
+// receiver readout kernel launcher (readout.cu)
 int launch_receivers(int fp64, int B, const void* Q, int S, int64_t n, const int64_t* elem,
                      const double* phi, double* out, void* stream);
 
@@ -105,6 +106,20 @@ struct Ctx {
   int64_t n_rec = 0;
   int64_t* dRecElem = nullptr;
   double *dRecPhi = nullptr, *dRecOut = nullptr;
+  // recording at a cadence (adg_record_*): [0] receivers, [1] sea-surface height
+  struct Recorder {
+    int every = 0;                  // macro steps between samples; 0: off
+    int64_t cap = 0, count = 0, read = 0, dropped = 0, macro = 0;
+    size_t sample = 0;              // doubles per sample
+    double* dRing = nullptr;        // device ring [cap][sample]
+    double* hRing = nullptr;        // pinned host ring [cap][sample]
+    std::vector<double> t;          // [cap] time of the sample in each slot
+    std::vector<cudaEvent_t> taken, copied;  // [cap] sample taken / copied to the host ring
+  };
+  Recorder rec[2];
+  cudaStream_t rec_stream = nullptr;
+  void record_after_macro();
+  void record_free(int kind);
 
   void setup();
   StepArgs base_args() const;

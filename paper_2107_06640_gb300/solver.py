@@ -105,6 +105,28 @@ class Solver:
         out = np.empty((self._nrec, self.S, 9))
         return L.adg_read_receivers(self.ctx, out)
 
+    def record(self, kind, every, capacity):
+        """Start recording receivers (L.ADG_RECORD_RECEIVERS) or the sea surface
+        (L.ADG_RECORD_SSH) every `every` macro steps of advance / advance_to."""
+        L.adg_record_start(self.ctx, kind, every, capacity)
+        self._rec_cap = getattr(self, "_rec_cap", {})
+        self._rec_cap[kind] = int(capacity)
+
+    def read_record(self, kind, max_samples=None):
+        """Unread samples, oldest first (at most max_samples, default the ring
+        capacity): (t[k], samples[k] shaped as read_receivers / read_ssh,
+        dropped so far)."""
+        if kind == L.ADG_RECORD_RECEIVERS:
+            shape = (self._nrec, self.S, 9)
+        else:
+            shape = (int(self.info.n_gravity_faces), self.S, self.Bf)
+        cap = getattr(self, "_rec_cap", {}).get(kind, 0) if max_samples is None else int(max_samples)
+        t, data, dropped = L.adg_record_read(self.ctx, kind, cap, int(np.prod(shape)))
+        return t, data.reshape((len(t),) + shape), dropped
+
+    def stop_record(self, kind):
+        L.adg_record_stop(self.ctx, kind)
+
     def save_state(self):
         return L.adg_save_state(self.ctx)
 
