@@ -70,7 +70,7 @@ typedef struct adg_ctx adg_ctx;
 
 typedef struct adg_config {
   int degree;        /* polynomial degree N in [1, 5]; 5 = order 6 (Sec. 6)       */
-  int precision;     /* ADG_FP64 or ADG_FP32: storage and arithmetic of the dofs;
+  int precision;     /* ADG_FP64, ADG_FP32 or ADG_3XTF32: storage and arithmetic of the dofs;
                         eta/H, LTS buffers and friction stay FP64                 */
   double cfl;        /* C in dt = C/(2N+1) h / c_p, h = insphere diameter (Sec. 4.4) */
   double gravity;    /* g in p = rho g eta; 9.81 in the paper (Sec. 3)            */
@@ -131,6 +131,12 @@ int adg_get_dofs(adg_ctx* ctx, double* Q);
  * array is borrowed for the call; both calls return after their copy. */
 int adg_set_dofs_f32(adg_ctx* ctx, const float* Q);
 int adg_get_dofs_f32(adg_ctx* ctx, float* Q);
+/* The dofs of n listed user tets (indices in [0, nt)), Q[n][S][9][B] double,
+ * gathered on the device: a cheap look at a few elements of a large mesh, at
+ * any point (also inside an LTS macro step, where the elements of a cluster
+ * that has not finished its step hold their mid-step values).
+ * ADG_E_INVALID for an index out of range. */
+int adg_get_dofs_subset(adg_ctx* ctx, int64_t n, const int64_t* tets, double* Q);
 
 /* Initial condition by projection: adg_initial_points returns, for every tet,
  * n_pts physical points (xyz[nt][n_pts][3]); the caller evaluates its field

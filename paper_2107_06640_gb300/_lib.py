@@ -53,6 +53,7 @@ _SIGS = {
     "adg_set_dofs": (C.c_int, [_P, _P]),
     "adg_get_dofs": (C.c_int, [_P, _P]),
     "adg_set_dofs_f32": (C.c_int, [_P, _P]),
+    "adg_get_dofs_subset": (C.c_int, [_P, C.c_int64, _P, _P]),
     "adg_record_start": (C.c_int, [_P, C.c_int, C.c_int, C.c_int64]),
     "adg_record_read": (C.c_int, [_P, C.c_int, C.c_int64, _P, _P, _P, _P]),
     "adg_record_stop": (C.c_int, [_P, C.c_int]),
@@ -199,6 +200,13 @@ def adg_record_read(ctx, kind, max_samples, sample):
 
 def adg_record_stop(ctx, kind):
     _check(ctx, load().adg_record_stop(ctx, int(kind)))
+
+
+def adg_get_dofs_subset(ctx, tets, out):
+    tets = np.ascontiguousarray(tets, dtype=np.int64)
+    assert out.dtype == np.float64 and out.flags.c_contiguous and out.shape[0] == tets.size
+    _check(ctx, load().adg_get_dofs_subset(ctx, tets.size, _ptr(tets), _ptr(out)))
+    return out
 
 
 def adg_initial_points(ctx, n_tets):

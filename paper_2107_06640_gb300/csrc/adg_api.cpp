@@ -281,6 +281,35 @@ int adg_get_dofs_f32(adg_ctx* ctx, float* Q) {
   });
 }
 
+int adg_get_dofs_subset(adg_ctx* ctx, int64_t n, const int64_t* tets, double* Q) {
+  if (!ctx || n < 0 || (n && (!tets || !Q))) return ADG_E_INVALID;
+  return guard(ctx, [&] {
+    Ctx& c = ctx->c;
+    need_init(c);
+    if (!n) return;
+    std::vector<int64_t> idx((size_t)n);
+    for (int64_t k = 0; k < n; ++k) {
+      if (tets[k] < 0 || tets[k] >= c.nt) adg::throw_err(ADG_E_INVALID, "tet index out of range");
+      idx[k] = c.inv[tets[k]];
+    }
+    const int per = c.S * 9 * c.B;
+    const size_t ts = c.fp64 ? 8 : 4;
+    void* d = nullptr;
+    check_cuda(cudaMalloc(&d, (size_t)n * 8 + (size_t)n * per * ts), "dofs subset");
+    int64_t* dIdx = static_cast<int64_t*>(d);
+    void* dOut = static_cast<char*>(d) + (size_t)n * 8;
+    std::vector<char> h((size_t)n * per * ts);
+    cudaError_t e = cudaMemcpyAsync(dIdx, idx.data(), (size_t)n * 8, cudaMemcpyHostToDevice, c.stream);
+    if (e == cudaSuccess) e = (cudaError_t)adg::launch_gather_dofs(c.fp64, c.dQ, dIdx, n, per, dOut, c.stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), dOut, h.size(), cudaMemcpyDeviceToHost, c.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+    cudaFree(d);
+    check_cuda(e, "dofs subset");
+    for (size_t k = 0; k < (size_t)n * per; ++k)
+      Q[k] = c.fp64 ? reinterpret_cast<const double*>(h.data())[k] : (double)reinterpret_cast<const float*>(h.data())[k];
+  });
+}
+
 int adg_initial_points(adg_ctx* ctx, int* n_pts, double* xyz) {
   if (!ctx || !n_pts) return ADG_E_INVALID;
   return guard(ctx, [&] {

@@ -2,7 +2,7 @@
 // the device: upload  out[i] = in[order[i]]  (caller FP32 -> dofs precision T),
 // download out[order[i]] = in[i]  (T -> FP32); rows of `per` values
 // (S x 9 x B per element).  One warp per row, 16-byte chunks where the row
-// length allows.
+// length allows.  Also the gather of listed elements' rows (subset readout).
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -49,7 +49,27 @@ void launch_t(const void* in, void* out, const int64_t* order, int64_t nt, int p
     permute_dofs_kernel<T, kUp, 1><<<grid, 256, 0, st>>>(in, out, order, nt, per);
 }
 
+// out[k] = Q[idx[k]]: rows of `per` values of the listed library elements
+template <typename T>
+__global__ void __launch_bounds__(256) gather_dofs_kernel(const T* __restrict__ Q, const int64_t* __restrict__ idx,
+                                                           int64_t n, int per, T* __restrict__ out) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int64_t k = (int64_t)blockIdx.x * 8 + warp; k < n; k += (int64_t)gridDim.x * 8)
+    for (int c = lane; c < per; c += 32) out[k * per + c] = Q[idx[k] * per + c];
+}
+
 }  // namespace
+
+int launch_gather_dofs(int fp64, const void* Q, const int64_t* idx, int64_t n, int per, void* out, void* stream) {
+  if (n <= 0) return 0;
+  const int64_t want = (n + 7) / 8;
+  const unsigned grid = (unsigned)(want < 4096 ? want : 4096);
+  if (fp64)
+    gather_dofs_kernel<double><<<grid, 256, 0, (cudaStream_t)stream>>>((const double*)Q, idx, n, per, (double*)out);
+  else
+    gather_dofs_kernel<float><<<grid, 256, 0, (cudaStream_t)stream>>>((const float*)Q, idx, n, per, (float*)out);
+  return (int)cudaGetLastError();
+}
 
 int launch_permute_dofs(int fp64, int up, const void* in, void* out, const int64_t* order, int64_t nt, int per,
                         int n_sms, void* stream) {

@@ -55,6 +55,13 @@ class Solver:
         L.adg_get_dofs(self.ctx, out)
         return out[:, 0] if self.S == 1 else out
 
+    def get_dofs_subset(self, tets):
+        """Dofs of the listed tets, [n][S][9][B] (or [n][9][B] when S == 1)."""
+        tets = np.asarray(tets, dtype=np.int64).ravel()
+        out = np.empty((tets.size, self.S, 9, self.B))
+        L.adg_get_dofs_subset(self.ctx, tets, out)
+        return out[:, 0] if self.S == 1 else out
+
     def set_dofs_f32(self, Q):
         """Q: float32 [tet][S][9][B] (or [tet][9][B] when S == 1); at a macro-step boundary."""
         L.adg_set_dofs_f32(self.ctx, Q)

@@ -125,3 +125,61 @@ def test_full_size_megathrust_sampled():
     assert rel_l2(st[idx, :, 0], o.fault["V"]) <= 1e-4
     assert rel_l2(st[idx, :, 1], o.fault["psi"]) <= 1e-4
     assert rel_l2(st[idx, :, 2:5], o.fault["slip"]) <= 1e-4
+
+
+def _mem_available_gb():
+    try:
+        with open("/proc/meminfo") as f:
+            for line in f:
+                if line.startswith("MemAvailable:"):
+                    return int(line.split()[1]) / 2 ** 20
+    except OSError:
+        pass
+    return 0.0
+
+
+def test_full_size_lts_first_tick_sampled():
+    """The LTS workload at its benchmark size (9,360,000 tets graded 32x in x
+    and y under a sinusoidal seafloor, 6 rate-2 clusters, degree 5, 3xTF32).
+    After the first tick, cluster 0 has finished one step of dt_min; in it a
+    coarser neighbour contributes the integral of its Taylor expansion over
+    [0, dt_min], as one global step of dt_min does.  Sampled elements with
+    dt_e < 2 dt_min (cluster 0 whatever their neighbours) against the oracle on
+    their neighbourhood with dt = dt_min, through adg_get_dofs_subset.  The
+    dofs are non-zero only on that neighbourhood, so the full-size FP32 upload
+    is mostly untouched zero pages.  Tolerance as for the other 3xTF32 steps."""
+    if _mem_available_gb() < 40.0:
+        pytest.skip("needs 40 GB of free host memory for the 9.36 M-tet mesh")
+    from oracle.ader import Oracle
+    from paper_2107_06640_gb300 import ADG_3XTF32, Solver
+    from synthetic.workloads import coupled_box
+    L = 100e3
+    bathy = lambda x, y: -2000.0 + 500.0 * np.sin(2 * np.pi * x / L) * np.sin(2 * np.pi * y / L)
+    m, mat = coupled_box(nxy=200, bathy=bathy, grading=32.0)
+    assert m.nt == 9360000
+    rho, lam, mu = mat
+    s = Solver(m.xyz, m.tets, m.face_tag, rho, lam, mu, degree=5, cfl=0.35, precision=ADG_3XTF32, max_clusters=6)
+    assert s.info.n_clusters == 6
+    dtmin = s.info.dt_min
+    rng = np.random.default_rng(41)
+    cand = rng.choice(m.nt, 600, replace=False)
+    sub, smat, keep, pos = submesh(m, mat, cand)
+    oc = Oracle(sub.xyz, sub.tets, sub.face_tag, sub.face_partner, *smat, 5, cfl=0.35)
+    fine = cand[oc.dt_e[pos[cand]] < 2.0 * dtmin * (1.0 - 1e-9)]
+    assert fine.size >= 10
+    pick = fine[:40]
+    sub, smat, keep, pos = submesh(m, mat, pick)
+    Qk = (rng.standard_normal((keep.size, 9, s.B)) * 1e-3).astype(np.float32)
+    Q0 = np.zeros((m.nt, 9, s.B), np.float32)
+    Q0[keep] = Qk
+    s.set_dofs_f32(Q0)
+    del Q0
+    s.step_tick()
+    got = s.get_dofs_subset(pick)
+    o = Oracle(sub.xyz, sub.tets, sub.face_tag, sub.face_partner, *smat, 5, cfl=0.35, dt=dtmin)
+    o.Q = to_oracle_layout(Qk.astype(np.float64))
+    o.step_gts()
+    sel = pos[pick]
+    assert rel_l2(to_oracle_layout(got), o.Q[sel]) <= 1e-5, rel_l2(to_oracle_layout(got), o.Q[sel])
+    # the samples moved (a zero update would pass trivially)
+    assert rel_l2(to_oracle_layout(Qk[sel].astype(np.float64)), o.Q[sel]) > 1e-3

@@ -196,6 +196,8 @@ def test_f32_dofs_transfer(N):
         b.advance(1)
         assert np.array_equal(a.get_dofs(), b.get_dofs())
         assert np.array_equal(a.get_dofs_f32(), b.get_dofs().astype(np.float32))
+        idx = [m.nt - 1, 0, 7, 7]
+        assert np.array_equal(a.get_dofs_subset(idx), a.get_dofs()[idx])
     w = _warped_periodic(4)
     s = Solver(w.xyz, w.tets, w.face_tag, *syn.elastic_uniform(w.nt), face_partner=w.face_partner, degree=3,
                cfl=0.5, max_clusters=3)
@@ -204,6 +206,10 @@ def test_f32_dofs_transfer(N):
     with pytest.raises(AdgError) as ei:
         s.set_dofs_f32(np.zeros((w.nt, 9, s.B), np.float32))
     assert ei.value.code == -3
+    # the subset readout works inside the macro step
+    assert np.array_equal(s.get_dofs_subset([3, 0]), s.get_dofs()[[3, 0]])
+    with pytest.raises(AdgError):
+        s.get_dofs_subset([w.nt])
 
 def test_lts_coupled_graded_fp64():
     m, mat = syn.workloads.coupled_box(nxy=4, n_water=2, n_crust=2, L=8e3, depth=4e3, water=1e3,
