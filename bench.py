@@ -284,7 +284,7 @@ def run_other_workload(args):
                           "lts_update_reduction": gts_upd / upd, "macro_dt": info.macro_dt}
         line["dtype"] = "f32 (3xTF32 tensor-core products)"
     elif args.workload in ("rupture", "rupture-lsw"):
-        r = 3
+        r = args.fault_scale
         m, (rho, lam, mu) = fault_box(nx=32 * r, ny=40 * r, nz=16 * r, dz=1e3 / r, dip_deg=15.0,
                                       ocean_layers=2 * r, water=2e3)
         s = Solver(m.xyz, m.tets, m.face_tag, rho, lam, mu, degree=4, precision=pkg.ADG_FP32, cfl=0.35,
@@ -338,6 +338,8 @@ def run_other_workload(args):
     line["kernel_ms"] = {"local": kms[0], "neighbour": kms[1], "rupture": kms[2],
                          "launches_per_macro": [int(x) for x in kcnt[:3]]}
     line["gpu_launches"] = int(kcnt[:3].sum()) * steps
+    import resource
+    line["host_peak_rss_gb"] = resource.getrusage(resource.RUSAGE_SELF).ru_maxrss / 2 ** 20
     if args.workload == "record":
         # the same steps again while both kinds are recorded every macro step
         R, H = _lib.ADG_RECORD_RECEIVERS, _lib.ADG_RECORD_SSH
@@ -398,6 +400,8 @@ def main():
                     choices=["coupled", "lts", "rupture", "rupture-lsw", "ensemble", "record"],
                     help="coupled: the headline line; lts / rupture / rupture-lsw / ensemble / record: the other "
                          "workloads")
+    ap.add_argument("--fault-scale", type=int, default=5,
+                    help="megathrust refinement r: 32r x 40r x 18r hex columns (3: 3.73 M tets, 5: 17.3 M tets)")
     ap.add_argument("--clock-dir", default=None,
                     help="directory for the nvidia-smi clock samples of each timed region (default: the temp dir)")
     args = ap.parse_args()
