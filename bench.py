@@ -325,10 +325,14 @@ def run_other_workload(args):
         ef, nxyz = s.gravity_faces()
         eta0 = np.stack([f(nxyz[..., 0], nxyz[..., 1]) for f in uplift_scenarios(S, seed=0)], axis=1)
         s.set_eta(eta0)
+        t_hot = time.perf_counter()
+        s.hydrostatic_start()  # the ocean at rest with p' = rho g eta0 under each scenario's surface
+        t_hot = time.perf_counter() - t_hot
         upd = int(s.info.updates_per_macro)
-        line["config"] = {"workload": f"ensemble of {S} seafloor-uplift scenarios (8 Gaussian bumps, 0.1-2 m) "
-                                      f"on a {s.nt}-tet coupled box, degree 5; 64 scenarios = 2 passes of {S}",
-                          "n_tets": s.nt, "ensemble": S}
+        line["config"] = {"workload": f"ensemble of {S} sea-surface uplift scenarios (8 Gaussian bumps, 0.1-2 m) "
+                                      f"with a hydrostatic start of the ocean, on a {s.nt}-tet coupled box, degree 5; "
+                                      f"64 scenarios = 2 passes of {S}",
+                          "n_tets": s.nt, "ensemble": S, "hydrostatic_start_s": t_hot}
         line["dtype"] = "f32 (3xTF32 tensor-core products)"
     t_setup = time.perf_counter() - t_setup
     ms, clk = _timed_advance(s, steps, warm, stream, torch, args.workload)

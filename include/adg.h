@@ -145,6 +145,16 @@ int adg_get_dofs_subset(adg_ctx* ctx, int64_t n, const int64_t* tets, double* Q)
 int adg_initial_points(adg_ctx* ctx, int* n_pts, double* xyz /* may be NULL to query n_pts */);
 int adg_set_initial_values(adg_ctx* ctx, const double* values);
 
+/* Hydrostatic start of the ocean from the current sea-surface height (set by
+ * adg_set_eta): every fluid tet (mu = 0) gets, in every scenario, the
+ * projection of the state at rest with the pressure perturbation
+ * p' = rho g eta(x, y), i.e. s_xx = s_yy = s_zz = -p', shear stresses and
+ * velocity zero; eta(x, y) is the P_N interpolant of the gravitational face
+ * whose horizontal projection contains (x, y).  The dofs of the solid tets
+ * are left as they are.  ADG_E_STATE without gravitational faces, ADG_E_MESH
+ * if a fluid point has no face above it. */
+int adg_hydrostatic_start(adg_ctx* ctx);
+
 /* Gravitational faces (tag 2) in increasing user (tet*4+face) order:
  * elem_face[n_gravity_faces]; node_xyz[n_gravity_faces][Bf][3] or NULL. */
 int adg_gravity_faces(adg_ctx* ctx, int64_t* elem_face, double* node_xyz);

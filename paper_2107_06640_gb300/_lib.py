@@ -54,6 +54,7 @@ _SIGS = {
     "adg_get_dofs": (C.c_int, [_P, _P]),
     "adg_set_dofs_f32": (C.c_int, [_P, _P]),
     "adg_get_dofs_subset": (C.c_int, [_P, C.c_int64, _P, _P]),
+    "adg_hydrostatic_start": (C.c_int, [_P]),
     "adg_record_start": (C.c_int, [_P, C.c_int, C.c_int, C.c_int64]),
     "adg_record_read": (C.c_int, [_P, C.c_int, C.c_int64, _P, _P, _P, _P]),
     "adg_record_stop": (C.c_int, [_P, C.c_int]),
@@ -200,6 +201,10 @@ def adg_record_read(ctx, kind, max_samples, sample):
 
 def adg_record_stop(ctx, kind):
     _check(ctx, load().adg_record_stop(ctx, int(kind)))
+
+
+def adg_hydrostatic_start(ctx):
+    _check(ctx, load().adg_hydrostatic_start(ctx))
 
 
 def adg_get_dofs_subset(ctx, tets, out):

@@ -281,6 +281,157 @@ int adg_get_dofs_f32(adg_ctx* ctx, float* Q) {
   });
 }
 
+int adg_hydrostatic_start(adg_ctx* ctx) {
+  if (!ctx) return ADG_E_INVALID;
+  return guard(ctx, [&] {
+    Ctx& c = ctx->c;
+    need_init(c);
+    const int64_t ngf = (int64_t)c.gfaces.size();
+    if (!ngf) adg::throw_err(ADG_E_STATE, "no gravitational face: no sea surface to start from");
+    const int N = c.N, Bf = c.Bf, B = c.B, S = c.S;
+    // sea-surface height at the face nodes, [ngf][S][Bf]
+    std::vector<double> eta((size_t)ngf * S * Bf);
+    check_cuda(cudaMemcpyAsync(eta.data(), c.dEta, eta.size() * 8, cudaMemcpyDeviceToHost, c.stream), "eta");
+    check_cuda(cudaStreamSynchronize(c.stream), "eta");
+    // the P_N interpolant on a face: eta(chi) = sum_n eta_n L_n(chi) with
+    // L(chi) = m(chi)^T Vinv, m the monomials chi1^a chi2^b (a + b <= N)
+    std::vector<int> ma, mb;
+    for (int a = 0; a <= N; ++a)
+      for (int b = 0; b <= N - a; ++b) { ma.push_back(a); mb.push_back(b); }
+    std::vector<double> V((size_t)Bf * Bf), Vinv((size_t)Bf * Bf, 0.0);
+    for (int n = 0; n < Bf; ++n)
+      for (int j = 0; j < Bf; ++j)
+        V[n * Bf + j] = std::pow(c.ops.node_chi[2 * n], ma[j]) * std::pow(c.ops.node_chi[2 * n + 1], mb[j]);
+    for (int n = 0; n < Bf; ++n) Vinv[n * Bf + n] = 1.0;
+    for (int k = 0; k < Bf; ++k) {  // Gauss-Jordan with partial pivoting: Vinv = V^-1
+      int piv = k;
+      for (int r = k + 1; r < Bf; ++r)
+        if (std::fabs(V[r * Bf + k]) > std::fabs(V[piv * Bf + k])) piv = r;
+      for (int j = 0; j < Bf; ++j) {
+        std::swap(V[k * Bf + j], V[piv * Bf + j]);
+        std::swap(Vinv[k * Bf + j], Vinv[piv * Bf + j]);
+      }
+      const double d = V[k * Bf + k];
+      for (int j = 0; j < Bf; ++j) { V[k * Bf + j] /= d; Vinv[k * Bf + j] /= d; }
+      for (int r = 0; r < Bf; ++r) {
+        if (r == k) continue;
+        const double f = V[r * Bf + k];
+        if (f == 0.0) continue;
+        for (int j = 0; j < Bf; ++j) { V[r * Bf + j] -= f * V[k * Bf + j]; Vinv[r * Bf + j] -= f * Vinv[k * Bf + j]; }
+      }
+    }
+    // the faces seen from above: x(chi) = a + chi1 e1 + chi2 e2 in (x, y), and
+    // a uniform grid of cells listing the faces whose box meets them
+    static const int kFV[4][3] = {{1, 2, 3}, {0, 2, 3}, {0, 1, 3}, {0, 1, 2}};
+    std::vector<double> tri((size_t)ngf * 6);
+    double x0 = 1e300, x1 = -1e300, y0 = 1e300, y1 = -1e300;
+    for (int64_t k = 0; k < ngf; ++k) {
+      const int64_t e = c.gfaces[k] / 4;
+      const int f = (int)(c.gfaces[k] % 4);
+      const double* A = &c.xyz[3 * c.tets[4 * e + kFV[f][0]]];
+      const double* Bv = &c.xyz[3 * c.tets[4 * e + kFV[f][1]]];
+      const double* Cv = &c.xyz[3 * c.tets[4 * e + kFV[f][2]]];
+      double* t = &tri[6 * k];
+      t[0] = A[0]; t[1] = A[1];
+      t[2] = Bv[0] - A[0]; t[3] = Bv[1] - A[1];
+      t[4] = Cv[0] - A[0]; t[5] = Cv[1] - A[1];
+      for (const double* P : {A, Bv, Cv}) {
+        x0 = std::min(x0, P[0]); x1 = std::max(x1, P[0]);
+        y0 = std::min(y0, P[1]); y1 = std::max(y1, P[1]);
+      }
+    }
+    const int G = std::max(1, (int)std::sqrt((double)ngf));
+    const double hx = (x1 - x0) / G + 1e-300, hy = (y1 - y0) / G + 1e-300;
+    auto cell = [&](double v, double lo, double h) { return std::min(G - 1, std::max(0, (int)((v - lo) / h))); };
+    std::vector<std::vector<int64_t>> grid((size_t)G * G);
+    for (int64_t k = 0; k < ngf; ++k) {
+      const double* t = &tri[6 * k];
+      const double bx0 = std::min({t[0], t[0] + t[2], t[0] + t[4]}), bx1 = std::max({t[0], t[0] + t[2], t[0] + t[4]});
+      const double by0 = std::min({t[1], t[1] + t[3], t[1] + t[5]}), by1 = std::max({t[1], t[1] + t[3], t[1] + t[5]});
+      for (int i = cell(bx0, x0, hx); i <= cell(bx1, x0, hx); ++i)
+        for (int j = cell(by0, y0, hy); j <= cell(by1, y0, hy); ++j) grid[(size_t)i * G + j].push_back(k);
+    }
+    // fluid elements, quadrature, projection (sigma_ii = -rho g eta, the rest 0)
+    std::vector<int64_t> fluid;
+    for (int64_t e = 0; e < c.nt; ++e)
+      if (c.mu[e] == 0.0) fluid.push_back(e);
+    if (fluid.empty()) return;
+    std::vector<double> pts, w;
+    adg::tet_rule(2 * N + 4, pts, w);
+    const int nq = (int)w.size();
+    std::vector<double> phi((size_t)nq * B);
+    for (int q = 0; q < nq; ++q) adg::eval_basis(c.ops, &pts[3 * q], &phi[(size_t)q * B]);
+    const int per = S * 9 * B;
+    const int64_t nf = (int64_t)fluid.size();
+    std::vector<double> out((size_t)nf * per, 0.0);
+    int missing = 0;
+#pragma omp parallel for schedule(dynamic, 64) reduction(+ : missing)
+    for (int64_t i = 0; i < nf; ++i) {
+      const int64_t e = fluid[i];
+      const double* P0 = &c.xyz[3 * c.tets[4 * e]];
+      std::vector<double> coef((size_t)S * B, 0.0), L(Bf), m(Bf), es(S);
+      for (int q = 0; q < nq; ++q) {
+        double x[3];
+        for (int d = 0; d < 3; ++d) {
+          x[d] = P0[d];
+          for (int k = 0; k < 3; ++k) x[d] += (c.xyz[3 * c.tets[4 * e + k + 1] + d] - P0[d]) * pts[3 * q + k];
+        }
+        // the face above: largest smallest barycentric coordinate among the cell's faces
+        int64_t best = -1;
+        double bmin = -1e-9, b1 = 0, b2 = 0;
+        for (int64_t k : grid[(size_t)cell(x[0], x0, hx) * G + cell(x[1], y0, hy)]) {
+          const double* t = &tri[6 * k];
+          const double det = t[2] * t[5] - t[3] * t[4];
+          const double px = x[0] - t[0], py = x[1] - t[1];
+          const double c1 = (px * t[5] - py * t[4]) / det, c2 = (t[2] * py - t[3] * px) / det;
+          const double mn = std::min(std::min(c1, c2), 1.0 - c1 - c2);
+          if (mn > bmin) { bmin = mn; best = k; b1 = c1; b2 = c2; }
+        }
+        if (best < 0) { ++missing; continue; }
+        for (int j = 0; j < Bf; ++j) m[j] = std::pow(b1, ma[j]) * std::pow(b2, mb[j]);
+        for (int n = 0; n < Bf; ++n) {
+          double v = 0.0;
+          for (int j = 0; j < Bf; ++j) v += m[j] * Vinv[j * Bf + n];
+          L[n] = v;
+        }
+        for (int s = 0; s < S; ++s) {
+          const double* et = &eta[((size_t)best * S + s) * Bf];
+          double v = 0.0;
+          for (int n = 0; n < Bf; ++n) v += et[n] * L[n];
+          es[s] = w[q] * c.rho[e] * c.cfg.gravity * v;
+        }
+        for (int s = 0; s < S; ++s)
+          for (int l = 0; l < B; ++l) coef[(size_t)s * B + l] += es[s] * phi[(size_t)q * B + l];
+      }
+      for (int s = 0; s < S; ++s)
+        for (int p = 0; p < 3; ++p)
+          for (int l = 0; l < B; ++l) out[(size_t)i * per + ((size_t)s * 9 + p) * B + l] = -coef[(size_t)s * B + l];
+    }
+    if (missing) adg::throw_err(ADG_E_MESH, "hydrostatic start: fluid points outside the sea surface seen from above");
+    // overwrite the fluid elements' dofs on the device
+    const size_t ts = c.fp64 ? 8 : 4;
+    std::vector<int64_t> idx((size_t)nf);
+    for (int64_t i = 0; i < nf; ++i) idx[i] = c.inv[fluid[i]];
+    std::vector<float> out32;
+    const void* src = out.data();
+    if (!c.fp64) {
+      out32.resize(out.size());
+      for (size_t k = 0; k < out.size(); ++k) out32[k] = (float)out[k];
+      src = out32.data();
+    }
+    void* d = nullptr;
+    check_cuda(cudaMalloc(&d, (size_t)nf * 8 + out.size() * ts), "hydrostatic start");
+    int64_t* dIdx = static_cast<int64_t*>(d);
+    void* dIn = static_cast<char*>(d) + (size_t)nf * 8;
+    cudaError_t err = cudaMemcpyAsync(dIdx, idx.data(), (size_t)nf * 8, cudaMemcpyHostToDevice, c.stream);
+    if (err == cudaSuccess) err = cudaMemcpyAsync(dIn, src, out.size() * ts, cudaMemcpyHostToDevice, c.stream);
+    if (err == cudaSuccess) err = (cudaError_t)adg::launch_scatter_dofs(c.fp64, dIn, dIdx, nf, per, c.dQ, c.stream);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(c.stream);
+    cudaFree(d);
+    check_cuda(err, "hydrostatic start");
+  });
+}
+
 int adg_get_dofs_subset(adg_ctx* ctx, int64_t n, const int64_t* tets, double* Q) {
   if (!ctx || n < 0 || (n && (!tets || !Q))) return ADG_E_INVALID;
   return guard(ctx, [&] {

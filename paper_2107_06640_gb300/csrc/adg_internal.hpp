@@ -30,6 +30,7 @@ int launch_adam(float* P, const float* g, float* m, float* v, float lr, int step
 int launch_permute_dofs(int fp64, int up, const void* in, void* out, const int64_t* order, int64_t nt, int per,
                         int n_sms, void* stream);
 int launch_gather_dofs(int fp64, const void* Q, const int64_t* idx, int64_t n, int per, void* out, void* stream);
+int launch_scatter_dofs(int fp64, const void* in, const int64_t* idx, int64_t n, int per, void* Q, void* stream);
 // receiver readout kernel launcher (readout.cu)
 int launch_receivers(int fp64, int B, const void* Q, int S, int64_t n, const int64_t* elem,
                      const double* phi, double* out, void* stream);

@@ -2,7 +2,8 @@
 // the device: upload  out[i] = in[order[i]]  (caller FP32 -> dofs precision T),
 // download out[order[i]] = in[i]  (T -> FP32); rows of `per` values
 // (S x 9 x B per element).  One warp per row, 16-byte chunks where the row
-// length allows.  Also the gather of listed elements' rows (subset readout).
+// length allows.  Also the gather (subset readout) and scatter (subset
+// overwrite) of listed elements' rows.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -58,7 +59,27 @@ __global__ void __launch_bounds__(256) gather_dofs_kernel(const T* __restrict__ 
     for (int c = lane; c < per; c += 32) out[k * per + c] = Q[idx[k] * per + c];
 }
 
+// Q[idx[k]] = in[k]: rows of the listed library elements overwritten
+template <typename T>
+__global__ void __launch_bounds__(256) scatter_dofs_kernel(const T* __restrict__ in, const int64_t* __restrict__ idx,
+                                                            int64_t n, int per, T* __restrict__ Q) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int64_t k = (int64_t)blockIdx.x * 8 + warp; k < n; k += (int64_t)gridDim.x * 8)
+    for (int c = lane; c < per; c += 32) Q[idx[k] * per + c] = in[k * per + c];
+}
+
 }  // namespace
+
+int launch_scatter_dofs(int fp64, const void* in, const int64_t* idx, int64_t n, int per, void* Q, void* stream) {
+  if (n <= 0) return 0;
+  const int64_t want = (n + 7) / 8;
+  const unsigned grid = (unsigned)(want < 4096 ? want : 4096);
+  if (fp64)
+    scatter_dofs_kernel<double><<<grid, 256, 0, (cudaStream_t)stream>>>((const double*)in, idx, n, per, (double*)Q);
+  else
+    scatter_dofs_kernel<float><<<grid, 256, 0, (cudaStream_t)stream>>>((const float*)in, idx, n, per, (float*)Q);
+  return (int)cudaGetLastError();
+}
 
 int launch_gather_dofs(int fp64, const void* Q, const int64_t* idx, int64_t n, int per, void* out, void* stream) {
   if (n <= 0) return 0;

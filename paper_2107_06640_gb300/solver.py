@@ -55,6 +55,10 @@ class Solver:
         L.adg_get_dofs(self.ctx, out)
         return out[:, 0] if self.S == 1 else out
 
+    def hydrostatic_start(self):
+        """Ocean at rest with p' = rho g eta under the current sea surface (after set_eta)."""
+        L.adg_hydrostatic_start(self.ctx)
+
     def get_dofs_subset(self, tets):
         """Dofs of the listed tets, [n][S][9][B] (or [n][9][B] when S == 1)."""
         tets = np.asarray(tets, dtype=np.int64).ravel()

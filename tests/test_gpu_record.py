@@ -105,3 +105,53 @@ def test_record_calls_refuse_what_they_cannot_do():
     assert ei.value.code == -3
     a.stop_record(R)
     a.add_receivers(np.zeros((1, 3)) + m.xyz.mean(0))  # allowed again
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-11), (1, 2e-6)])
+def test_hydrostatic_start_is_exact_for_a_polynomial_sea_surface(precision, tol):
+    """adg_hydrostatic_start: with a sea surface of degree 3 on the flat top of
+    the coupled box, p' = rho g eta(x, y) is a cubic in every water tet, so its
+    projection at degree 3 is exact: receivers in the water read
+    s_xx = s_yy = s_zz = -rho g eta(x, y), zero shear stress and velocity, in
+    both scenarios (each its own surface); the solid keeps its dofs."""
+    from paper_2107_06640_gb300 import AdgError, Solver
+    m, (rho, lam, mu) = small_coupled()
+    s = Solver(m.xyz, m.tets, m.face_tag, rho, lam, mu, degree=3, cfl=0.5, precision=precision, ensemble=2)
+    rng = np.random.default_rng(9)
+    Q0 = rng.standard_normal((m.nt, 2, 9, s.B)) * 1e-3
+    s.set_dofs(Q0)
+    surf = [lambda x, y: 0.3 + 1e-4 * x - 2e-4 * y + 3e-11 * x * x * y,
+            lambda x, y: -0.2 + 5e-8 * x * y - 4e-12 * y ** 3]
+    ef, xyz = s.gravity_faces()
+    s.set_eta(np.stack([f(xyz[..., 0], xyz[..., 1]) for f in surf], axis=1))
+    s.hydrostatic_start()
+    water = np.nonzero(mu == 0.0)[0]
+    solid = np.nonzero(mu > 0.0)[0]
+    assert water.size and solid.size
+    got = s.get_dofs_subset(solid)
+    want = Q0[solid].astype(np.float32).astype(np.float64) if precision == 1 else Q0[solid]
+    assert np.array_equal(got, want)
+    # points inside water tets (random barycentric weights)
+    pick = rng.choice(water, 12, replace=False)
+    lam4 = rng.dirichlet(np.ones(4), size=pick.size)
+    pts = np.einsum("rk,rkd->rd", lam4, m.xyz[m.tets[pick]])
+    s.add_receivers(pts)
+    r = s.read_receivers()  # [n][S][9]
+    g = 9.81
+    for k, f in enumerate(surf):
+        p = rho[pick] * g * f(pts[:, 0], pts[:, 1])
+        scale = np.abs(p).max()
+        for q in range(3):
+            assert np.max(np.abs(r[:, k, q] + p)) <= tol * scale
+        assert np.max(np.abs(r[:, k, 3:])) <= tol * scale
+
+
+def test_hydrostatic_start_needs_a_sea_surface():
+    from paper_2107_06640_gb300 import AdgError, Solver
+    import synthetic as syn
+    m = syn.unit_cube_periodic(2)
+    s = Solver(m.xyz, m.tets, m.face_tag, *syn.materials.elastic_uniform(m.nt), face_partner=m.face_partner,
+               degree=2, cfl=0.5)
+    with pytest.raises(AdgError) as ei:
+        s.hydrostatic_start()
+    assert ei.value.code == -3
