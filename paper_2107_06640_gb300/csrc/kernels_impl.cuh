@@ -15,6 +15,11 @@ namespace adg {
 
 constexpr int kThreads = 128;
 
+// 1/k (k = 1..47; entry 0 unused) and 1/m! (m = 0..5), correctly rounded
+// constants: the gravity-face series multiplies by them instead of dividing
+static __constant__ double kRecipInt[48] = {0.0, 1.0 / 1.0, 1.0 / 2.0, 1.0 / 3.0, 1.0 / 4.0, 1.0 / 5.0, 1.0 / 6.0, 1.0 / 7.0, 1.0 / 8.0, 1.0 / 9.0, 1.0 / 10.0, 1.0 / 11.0, 1.0 / 12.0, 1.0 / 13.0, 1.0 / 14.0, 1.0 / 15.0, 1.0 / 16.0, 1.0 / 17.0, 1.0 / 18.0, 1.0 / 19.0, 1.0 / 20.0, 1.0 / 21.0, 1.0 / 22.0, 1.0 / 23.0, 1.0 / 24.0, 1.0 / 25.0, 1.0 / 26.0, 1.0 / 27.0, 1.0 / 28.0, 1.0 / 29.0, 1.0 / 30.0, 1.0 / 31.0, 1.0 / 32.0, 1.0 / 33.0, 1.0 / 34.0, 1.0 / 35.0, 1.0 / 36.0, 1.0 / 37.0, 1.0 / 38.0, 1.0 / 39.0, 1.0 / 40.0, 1.0 / 41.0, 1.0 / 42.0, 1.0 / 43.0, 1.0 / 44.0, 1.0 / 45.0, 1.0 / 46.0, 1.0 / 47.0};
+static __constant__ double kInvFact[6] = {1.0, 1.0, 1.0 / 2.0, 1.0 / 6.0, 1.0 / 24.0, 1.0 / 120.0};
+
 __host__ __device__ constexpr int doff_rows(int k, int N) {  // first row of D^k in the derivative stack
   int s = 0;
   for (int j = 0; j < k; ++j) s += nb3(N - j);
@@ -317,16 +322,12 @@ __global__ void __launch_bounds__(kThreads) local_kernel(StepArgs a) {
 #pragma unroll
           for (int p = 0; p < 9; ++p) acc[p] += w * d9[p];
         }
-        double val[9];
-#pragma unroll
-        for (int p = 0; p < 9; ++p) val[p] = (double)acc[p];
-        const double nx = gp[0], ny = gp[1], nz = gp[2], Z = gp[3];
-        const double snn = nx * nx * val[0] + ny * ny * val[1] + nz * nz * val[2] +
-                           2.0 * (nx * ny * val[3] + ny * nz * val[4] + nx * nz * val[5]);
-        const double vn = nx * val[6] + ny * val[7] + nz * val[8];
-        double fac = 1.0;
-        for (int j = 2; j <= m; ++j) fac *= j;
-        sF[r] = (vn - snn / Z) / fac;
+        // n.sigma.n and n.v in the dofs precision (the traces are in it)
+        const T nx = (T)gp[0], ny = (T)gp[1], nz = (T)gp[2];
+        const T snn = nx * nx * acc[0] + ny * ny * acc[1] + nz * nz * acc[2] +
+                      T(2) * (nx * ny * acc[3] + ny * nz * acc[4] + nx * nz * acc[5]);
+        const T vn = nx * acc[6] + ny * acc[7] + nz * acc[8];
+        sF[r] = ((double)vn - (double)snn * (1.0 / gp[3])) * kInvFact[m];
       }
       __syncthreads();
       if (tid < Bf) {
@@ -337,11 +338,11 @@ __global__ void __launch_bounds__(kThreads) local_kernel(StepArgs a) {
         double c = eta0, e1 = eta0, H = eta0 * dt, pw = 1.0;
         for (int m = 0; m < N + 40; ++m) {
           const double fm = (m <= N) ? sF[m * Bf + n] : 0.0;
-          c = (fm - kappa * c) / (m + 1);
+          c = (fm - kappa * c) * kRecipInt[m + 1];
           pw *= dt;
           const double term = c * pw;
           e1 += term;
-          H += term * dt / (m + 2);
+          H += term * dt * kRecipInt[m + 2];
           if (m > N && fabs(term) <= 1e-17 * fabs(e1)) break;
         }
         eta[n] = e1;
@@ -350,9 +351,10 @@ __global__ void __launch_bounds__(kThreads) local_kernel(StepArgs a) {
         const double* a7 = gp + 96;
         T* gfl = reinterpret_cast<T*>(a.gflux) + ((int64_t)gs * a.S + s) * 9 * Bf;
         for (int q = 0; q < 9; ++q) {
-          double acc = a1[q] * (-rg * H) + a7[q] * (e1 - eta0);
-          for (int p = 0; p < 9; ++p) acc += Fg[q * 9 + p] * (double)sV[(f * Bf + n) * P + p];
-          gfl[q * Bf + n] = (T)acc;
+          // the own trace's part in the dofs precision, the (eta, H) part in FP64
+          T fv = T(0);
+          for (int p = 0; p < 9; ++p) fv += (T)Fg[q * 9 + p] * sV[(f * Bf + n) * P + p];
+          gfl[q * Bf + n] = (T)(a1[q] * (-rg * H) + a7[q] * (e1 - eta0) + (double)fv);
         }
       }
     }
