@@ -102,6 +102,33 @@ def alu_peak_tflops(fp64, sm_mhz):
 CLOCK_DIR = [tempfile.gettempdir()]
 
 
+class Ranks:
+    """The ranks of one launch (torchrun's RANK / WORLD_SIZE): the barrier
+    around a timed region and the maximum of a host number over the ranks
+    (through `dist` on `device`; a single rank needs neither)."""
+
+    def __init__(self, dist=None, world=1, device="cpu"):
+        self.dist, self.world, self.device = dist, world, device
+
+    def barrier(self):
+        if self.world > 1:
+            self.dist.barrier()
+
+    def max(self, x):
+        if self.world == 1:
+            return float(x)
+        import torch
+        t = torch.tensor([float(x)], dtype=torch.float64, device=self.device)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, seconds):
+    """Units all ranks processed (each the same weak-scaling share) over the
+    slowest rank's time."""
+    return units_per_rank * world / seconds
+
+
 class ClockSampler:
     def __init__(self, path):
         self.path = path
@@ -437,17 +464,13 @@ def main():
     import paper_2107_06640_gb300 as pkg
     from paper_2107_06640_gb300 import Solver
 
+    ranks = Ranks(dist, world, torch.device("cuda", local))
+
     def barrier():
-        if world > 1:
-            dist.barrier()
+        ranks.barrier()
         torch.cuda.synchronize()
 
-    def max_over_ranks(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    max_over_ranks = ranks.max
 
     m, (rho, lam, mu), Q0 = make_workload(seed=rank, nxy=args.nxy)
     stream = torch.cuda.current_stream()
@@ -490,12 +513,12 @@ def main():
             res[prec]["solver"] = None
     r32 = res[HEAD]                # headline: FP32 dofs, reference-matrix products on the tensor cores
     upd = r32["upd"]
-    value = upd * world * r32["steps"] / (r32["ms"] * 1e-3)
+    value = whole_job_rate(upd * r32["steps"], world, r32["ms"] * 1e-3)
     ms_step = r32["ms"] / r32["steps"]
     r64 = res[pkg.ADG_FP64]
-    value64 = upd * world * r64["steps"] / (r64["ms"] * 1e-3)
+    value64 = whole_job_rate(upd * r64["steps"], world, r64["ms"] * 1e-3)
     rcc = res[pkg.ADG_FP32]
-    value_cc = upd * world * rcc["steps"] / (rcc["ms"] * 1e-3)
+    value_cc = whole_job_rate(upd * rcc["steps"], world, rcc["ms"] * 1e-3)
 
     # accuracy of the headline form against FP64 after the same steps from the same input
     s64 = res[pkg.ADG_FP64]["solver"]
@@ -532,7 +555,7 @@ def main():
         s.get_dofs_f32(out32)
     barrier()
     e2e_s = max_over_ranks(time.perf_counter() - t0)
-    e2e_val = upd * world * args.e2e_steps / e2e_s
+    e2e_val = whole_job_rate(upd * args.e2e_steps, world, e2e_s)
     bytes_q = s.nt * 9 * s.B * 4
     # the same through the double-array calls (conversion on the host cores)
     Qh = np.ascontiguousarray(Q0)
@@ -544,7 +567,7 @@ def main():
         s.advance(1)
         pkg._lib.adg_get_dofs(s.ctx, out)
     barrier()
-    e2e64_val = upd * world * args.e2e_steps / max_over_ranks(time.perf_counter() - t0)
+    e2e64_val = whole_job_rate(upd * args.e2e_steps, world, max_over_ranks(time.perf_counter() - t0))
 
     peaks, src = load_peaks()
     fl = flops_per_update(N_DEG)
