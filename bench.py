@@ -308,7 +308,8 @@ def run_other_workload(args):
         gts_upd = s.nt * (1 << (info.n_clusters - 1))
         line["config"] = {"workload": f"LTS-graded coupled box, sin bathymetry +-500 m, x/y grading 32x, "
                                       f"{s.nt} tets, degree 5", "n_tets": s.nt, "clusters": hist,
-                          "lts_update_reduction": gts_upd / upd, "macro_dt": info.macro_dt}
+                          "lts_update_reduction": gts_upd / upd, "macro_dt": info.macro_dt,
+                          "tensor_core_update_fraction": int(info.tensor_core_updates_per_macro) / upd}
         line["dtype"] = "f32 (3xTF32 tensor-core products)"
     elif args.workload in ("rupture", "rupture-lsw"):
         r = args.fault_scale
