@@ -50,11 +50,11 @@ extern "C" {
 
 #define ADG_FP64 0
 #define ADG_FP32 1
-/* FP32 dofs; at degree 5 the predictor, face traces and volume term of the
- * elements without gravitational face, fault face or neighbour in another LTS
- * cluster run on the tensor cores (tcgen05) as 3xTF32 split products with
- * FP32 accumulation, everything else as in ADG_FP32; other degrees behave as
- * ADG_FP32. */
+/* FP32 dofs; at degree 5 the reference-matrix products (predictor, face
+ * traces, volume term, lift) of the elements without gravitational face,
+ * fault face or neighbour in a finer LTS cluster run on the tensor cores
+ * (tcgen05) as 3xTF32 split products with FP32 accumulation, everything else
+ * as in ADG_FP32; other degrees behave as ADG_FP32. */
 #define ADG_3XTF32 2
 
 /* Face tags (per tet and local face). */

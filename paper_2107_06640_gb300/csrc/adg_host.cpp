@@ -375,16 +375,19 @@ void Ctx::setup() {
   }
   ncl = 0;
   for (int64_t e = 0; e < E; ++e) ncl = std::max(ncl, cl[e] + 1);
-  // ---- internal order: by cluster, stable; with the tensor-core local
-  // kernel, the elements of a cluster without gravitational face, fault face
-  // or neighbour in another cluster come first
+  // ---- internal order: by cluster, stable; with the tensor-core kernels,
+  // the elements of a cluster without gravitational face, fault face or
+  // finer neighbour come first (those with a coarser neighbour, which the
+  // tensor-core kernels handle at some extra cost, at the end of that range,
+  // so that they fill few tiles)
   std::vector<char> special(E, 0);
   if (tc)
     for (int64_t e = 0; e < E; ++e)
       for (int f = 0; f < 4; ++f) {
         const int tg = tag[4 * e + f];
         const int64_t e2 = nbr_u[4 * e + f];
-        if (tg == ADG_TAG_GRAVITY || tg == ADG_TAG_FAULT || (e2 >= 0 && cl[e2] != cl[e])) special[e] = 1;
+        if (tg == ADG_TAG_GRAVITY || tg == ADG_TAG_FAULT || (e2 >= 0 && cl[e2] < cl[e])) special[e] = 2;
+        else if (e2 >= 0 && cl[e2] > cl[e] && special[e] == 0) special[e] = 1;
       }
   order.resize(E);
   for (int64_t e = 0; e < E; ++e) order[e] = e;
@@ -397,7 +400,7 @@ void Ctx::setup() {
   cl_plain.assign(ncl, 0);
   for (int64_t i = 0; i < E; ++i) {
     cl_begin[cl[order[i]] + 1]++;
-    if (tc && !special[order[i]]) cl_plain[cl[order[i]]]++;
+    if (tc && special[order[i]] < 2) cl_plain[cl[order[i]]]++;
   }
   for (int c = 0; c < ncl; ++c) cl_begin[c + 1] += cl_begin[c];
   cluster.resize(E);
@@ -501,15 +504,16 @@ void Ctx::setup() {
   n_bslots = nb_slots;
   n_dslots = nd_slots;
   n_gslots = ng;
-  // the tensor-core kernels handle only same-cluster neighbours and linear
-  // boundaries: check that the ordering gave them nothing else
+  // the tensor-core kernels handle same-cluster and coarser neighbours and
+  // linear boundaries: check that the ordering gave them nothing else
   if (tc)
     for (int c = 0; c < ncl; ++c)
       for (int64_t i = cl_begin[c]; i < cl_begin[c] + cl_plain[c]; ++i) {
-        bool ok = bslot[i] < 0;
+        bool ok = true;
         for (int f = 0; f < 4; ++f) {
           const int kind = (ninfo[i * 4 + f] >> 5) & 7;
-          ok = ok && gslot[i * 4 + f] < 0 && dslot[i * 4 + f] < 0 && (kind == NK_SAME || kind == NK_NONE);
+          ok = ok && gslot[i * 4 + f] < 0 && dslot[i * 4 + f] < 0 &&
+               (kind == NK_SAME || kind == NK_NONE || kind == NK_COARSE);
         }
         if (!ok) throw Err(ADG_E_STATE, "internal: element order for the tensor-core kernels is inconsistent");
       }

@@ -71,7 +71,7 @@ struct StepArgs {
 };
 
 // tensor-core (tcgen05, 3xTF32) local kernel, degree 5, FP32 dofs (local_tc.cu),
-// for elements without gravitational faces, fault faces or LTS buffers
+// for elements without gravitational faces, fault faces or finer LTS neighbours
 int launch_local_tc(const StepArgs& a, int64_t n_virtual, int n_sms, void* stream);
 void pack_local_tc(const double* kt, const double* kvol, const double* efc, float* out);
 int local_tc_floats();

@@ -1,7 +1,8 @@
 // Local element kernel on the tensor cores (tcgen05, 3xTF32), degree 5,
 // FP32 dofs: Cauchy-Kovalewski predictor, time integral, face traces and
 // volume term of Sec. 4.1 for elements without gravitational faces, fault
-// faces or LTS buffers (those take the CUDA-core kernel).
+// faces or finer LTS neighbours (those take the CUDA-core kernel); an element
+// with a coarser LTS neighbour also adds its traces to its FP64 LTS buffer.
 //
 // A tile is 12 (virtual) elements x 9 quantities = the 128 rows of the MMAs,
 // one row per TMEM lane: warp w of a warpgroup holds elements 3w..3w+2, the
@@ -180,6 +181,9 @@ struct Lane {
   const float* k4;
   float* sX;          // [128][2] rows 8, 9 of D^3 handed from half 1 to half 0
   float* sT;          // [2][3][kTS] two buffers: one face of this warp's three elements' traces
+  double* btrace;     // LTS buffers of elements with a coarser neighbour (FP64)
+  const int* bslot;   // [E] buffer slot or -1 (null: no buffers)
+  int btrace_mode;    // 0 none, 1 overwrite, 2 accumulate
   uint64_t* mbar;     // this slot's barrier
   int* abort;         // this slot's abort flag
   uint32_t phase;
@@ -323,6 +327,26 @@ __device__ __forceinline__ bool local_tile(Lane& L, int64_t tile) {
     float tv[48];
     tc::ld3x8(trow + cAcc + 8 * H, trow + cAcc + 8 * (H + 2), trow + cAcc + 8 * (H + 4), tv);
     tc::ld3x8(trow + cAcc + 8 * (H + 6), trow + cAcc + 8 * (H + 8), trow + cAcc + 8 * (H == 0 ? 10 : 9), tv + 24);
+    // an element with a coarser neighbour also adds its four face traces to
+    // its LTS buffer, in FP64 (overwrite at the first of the two steps)
+    if (L.btrace_mode && L.bslot && valid) {
+      const int bs = L.bslot[e];
+      if (bs >= 0) {
+        double* bt = L.btrace + ((int64_t)bs * L.S + (v - e * L.S)) * 36 * BF;
+#pragma unroll
+        for (int cj = 0; cj < (H == 0 ? 6 : 5); ++cj) {
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int col = 8 * (H + 2 * cj) + j;
+            if (col < 4 * BF) {
+              const int f = col / BF, n = col - f * BF;
+              double* b = bt + (f * 9 + p) * BF + n;
+              *b = (L.btrace_mode == 1 ? 0.0 : *b) + (double)tv[8 * cj + j];
+            }
+          }
+        }
+      }
+    }
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
       float* sTf = L.sT + (f & 1) * kTB;
@@ -438,6 +462,9 @@ __global__ void __launch_bounds__(kThreadsL, 1) local_tc_kernel(StepArgs a, int6
   L.k4 = sm + LImg::oK4;
   L.sX = sX[slot];
   L.sT = sT[slot][(tid & 127) >> 5];
+  L.btrace = a.btrace;
+  L.bslot = a.bslot;
+  L.btrace_mode = a.btrace_mode;
   L.mbar = &mbar[slot];
   L.abort = &s_abort[slot];
   L.phase = 0;

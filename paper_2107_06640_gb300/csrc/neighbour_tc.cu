@@ -1,7 +1,9 @@
 // Neighbour kernel on the tensor cores (tcgen05, 3xTF32), degree 5, FP32
 // dofs: face fluxes of Sec. 4.2 (Eq. numerical-flux) and their lift for
-// elements whose faces are all interior faces inside their LTS cluster,
-// periodic faces or linear boundaries (the others take the CUDA-core kernel).
+// elements whose faces are interior faces to the same or a coarser LTS
+// cluster, periodic faces or linear boundaries (the others take the CUDA-core
+// kernel); a coarser neighbour's face values are the integral of its Taylor
+// expansion over this element's sub-interval (Sec. 4.4), formed while staging.
 //
 // Same tile as the local tensor-core kernel: 12 (virtual) elements x 9
 // quantities = 128 TMEM lanes (warp w: elements 3w..3w+2, lane 9j+p = element
@@ -84,9 +86,14 @@ __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0
 // Stage face f of a tile (thread u of the slot's 256): own traces and the
 // neighbours' traces of that face, both as stored (one 16-byte aligned face
 // block [quantity][node] per element); the neighbour's node order is applied
-// when the values are read.
+// when the values are read.  nbase: the neighbour's face block in the trace
+// array (>= 0), none (-1), or for a coarser neighbour -2 - the offset of its
+// derivative traces [N+1][9][Bf], integrated here over this element's
+// sub-interval with the coefficients cc (sum_k cc_k D_k, in the order of the
+// CUDA-core kernel).
 __device__ __forceinline__ void stage_face(int f, int u, int64_t v0, int nE, const float* trace,
-                                           const long long* nbase, float* so, float* sn) {
+                                           const long long* nbase, float* so, float* sn, const float* dtrace,
+                                           const float* cc) {
   constexpr int kChunks = kFS / 4;  // 16-byte chunks per face block
 #pragma unroll
   for (int it = 0; it < (TE * kChunks + 255) / 256; ++it) {
@@ -97,7 +104,23 @@ __device__ __forceinline__ void stage_face(int f, int u, int64_t v0, int nE, con
       const long long nb = nbase[f * TE + ei];
       const bool okn = ok && nb >= 0;
       cp16(so + ei * kSS + 4 * ch, trace + ((v0 + (ok ? ei : 0)) * 4 + f) * kFS + 4 * ch, ok);
-      cp16(sn + ei * kSS + 4 * ch, trace + (okn ? nb : 0) + 4 * ch, okn);
+      if (ok && nb <= -2) {
+        const float* dt = dtrace + (-2 - nb);
+        float x[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const int pos = 4 * ch + t;
+          float acc = 0.f;
+          if (pos < 9 * BF) {
+#pragma unroll
+            for (int k = 0; k <= 5; ++k) acc += cc[k] * dt[k * 9 * BF + pos];
+          }
+          x[t] = acc;
+        }
+        *reinterpret_cast<float4*>(sn + ei * kSS + 4 * ch) = make_float4(x[0], x[1], x[2], x[3]);
+      } else {
+        cp16(sn + ei * kSS + 4 * ch, trace + (okn ? nb : 0) + 4 * ch, okn);
+      }
     }
   }
 }
@@ -147,6 +170,10 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
   for (int r = u; r < kG; r += 256) sG[r] = 0.f;  // columns 21..27 stay zero
   const int jj = lane / 9, p = lane - 9 * (lane / 9);
   const int S = kOne ? 1 : a.S;
+  const float* dtrace = reinterpret_cast<const float*>(a.dtrace);
+  float cc[6];  // the coarser neighbours' expansion over this step's sub-interval
+#pragma unroll
+  for (int k = 0; k < 6; ++k) cc[k] = (float)a.ccoef[k];
   auto elem = [&](int64_t vv) -> int64_t { return kOne ? vv : vv / S; };  // element of a virtual element
   const int64_t ntiles = (n_virtual + TE - 1) / TE;
   uint32_t phase = 0;
@@ -177,10 +204,16 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
       const int ei = u - (u / TE) * TE;
       long long nb = -1;
       int pm = 0;
-      if (ei < pnE && ((info >> 5) & 7) == NK_SAME) {
+      const int kind = (info >> 5) & 7;
+      if (ei < pnE && (kind == NK_SAME || kind == NK_COARSE)) {
         const int64_t ve = pv0 + ei, ee = elem(ve);
-        const int64_t vn_e = (int64_t)nbe * S + (ve - ee * S);
-        nb = (vn_e * 4 + (info & 3)) * kFS;
+        if (kind == NK_SAME) {
+          const int64_t vn_e = (int64_t)nbe * S + (ve - ee * S);
+          nb = (vn_e * 4 + (info & 3)) * kFS;
+        } else {
+          const int ds = a.dslot[(int64_t)nbe * 4 + (info & 3)];
+          nb = -2 - ((int64_t)ds * S + (ve - ee * S)) * 6 * 9 * BF;
+        }
         pm = (info >> 2) & 7;
       }
       sNb[u] = nb;
@@ -196,7 +229,7 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
     }
     for (int c = u; c < ne * (PAR / 4); c += 256)
       cp16(sPr + 4 * c, reinterpret_cast<const float*>(a.par) + e0 * PAR + 4 * c);
-    stage_face(0, u, pv0, pnE, trace, sNb, sStage, sStage + kStage);
+    stage_face(0, u, pv0, pnE, trace, sNb, sStage, sStage + kStage, dtrace, cc);
     cp_commit();
   };
 
@@ -222,7 +255,7 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
       // ---- stage face f + 1 while face f is used
       if (f < 3) {
         float* nb_buf = sStage + ((f + 1) & 1) * 2 * kStage;
-        stage_face(f + 1, u, v0, nE, trace, sNb, nb_buf, nb_buf + kStage);
+        stage_face(f + 1, u, v0, nE, trace, sNb, nb_buf, nb_buf + kStage, dtrace, cc);
         cp_commit();
         cp_wait<1>();
       } else {
