@@ -398,9 +398,11 @@ void Ctx::setup() {
   for (int64_t i = 0; i < E; ++i) inv[order[i]] = i;
   cl_begin.assign(ncl + 1, 0);
   cl_plain.assign(ncl, 0);
+  cl_tc_coarse.assign(ncl, 0);
   for (int64_t i = 0; i < E; ++i) {
     cl_begin[cl[order[i]] + 1]++;
     if (tc && special[order[i]] < 2) cl_plain[cl[order[i]]]++;
+    if (tc && special[order[i]] == 1) cl_tc_coarse[cl[order[i]]] = 1;
   }
   for (int c = 0; c < ncl; ++c) cl_begin[c + 1] += cl_begin[c];
   cluster.resize(E);
@@ -626,8 +628,8 @@ void Ctx::setup() {
   // configure kernels once (outside any stream capture)
   StepArgs a0 = base_args();
   int rc = launch_local(fp64, N, a0, 0, stream);
-  if (!rc && tc) rc = launch_local_tc(a0, 0, n_sms, stream);
-  if (!rc && tc) rc = launch_neighbour_tc(a0, 0, n_sms, stream);
+  if (!rc && tc) rc = launch_local_tc(a0, 0, n_sms, stream, false);
+  if (!rc && tc) rc = launch_neighbour_tc(a0, 0, n_sms, stream, false);
   if (rc) throw Err(ADG_E_CUDA, std::string("kernel configuration: ") + cudaGetErrorString((cudaError_t)rc));
   tick = 0;
   time = 0.0;
@@ -678,7 +680,7 @@ void Ctx::launch_tick(int s, double dtm) {
       // plain elements on the tensor cores, the rest on the CUDA cores
       const int64_t np = cl_plain[c];
       ev.launches = (np > 0) + (n > np);
-      if (np > 0) rc = launch_local_tc(a, np * S, n_sms, stream);
+      if (np > 0) rc = launch_local_tc(a, np * S, n_sms, stream, cl_tc_coarse[c] != 0);
       if (prof && np > 0) {  // the tensor-core launch alone
         CK(cudaEventCreate(&ev.m));
         CK(cudaEventRecord(ev.m, stream));
@@ -712,7 +714,7 @@ void Ctx::launch_tick(int s, double dtm) {
     if (tc) {
       const int64_t np = cl_plain[c];
       ev.launches = (np > 0) + (n > np);
-      if (np > 0) rc = launch_neighbour_tc(a, np * S, n_sms, stream);
+      if (np > 0) rc = launch_neighbour_tc(a, np * S, n_sms, stream, cl_tc_coarse[c] != 0);
       if (prof && np > 0) {
         CK(cudaEventCreate(&ev.m));
         CK(cudaEventRecord(ev.m, stream));

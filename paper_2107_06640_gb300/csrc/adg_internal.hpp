@@ -58,6 +58,8 @@ struct Ctx {
   // elements [cl_begin[c], cl_begin[c] + cl_plain[c]) of cluster c have no
   // gravitational face, fault face or LTS buffer (tensor-core local kernel)
   std::vector<int64_t> cl_plain;
+  // cluster c's tensor-core range includes elements with a coarser neighbour
+  std::vector<char> cl_tc_coarse;
   std::vector<int> cluster;
   double dtmin = 0, time = 0;
   int64_t tick = 0;

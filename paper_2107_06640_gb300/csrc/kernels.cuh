@@ -72,12 +72,14 @@ struct StepArgs {
 
 // tensor-core (tcgen05, 3xTF32) local kernel, degree 5, FP32 dofs (local_tc.cu),
 // for elements without gravitational faces, fault faces or finer LTS neighbours
-int launch_local_tc(const StepArgs& a, int64_t n_virtual, int n_sms, void* stream);
+// buffers: the launch's elements include some with an LTS buffer (a coarser neighbour)
+int launch_local_tc(const StepArgs& a, int64_t n_virtual, int n_sms, void* stream, bool buffers);
 void pack_local_tc(const double* kt, const double* kvol, const double* efc, float* out);
 int local_tc_floats();
 // tensor-core (tcgen05, 3xTF32) neighbour kernel, degree 5, FP32 dofs
 // (neighbour_tc.cu), for the same elements
-int launch_neighbour_tc(const StepArgs& a, int64_t n_virtual, int n_sms, void* stream);
+// coarse: the launch's elements include some with a coarser LTS neighbour
+int launch_neighbour_tc(const StepArgs& a, int64_t n_virtual, int n_sms, void* stream, bool coarse);
 void pack_lift_tc(const double* lift, float* out);
 int lift_tc_floats();
 

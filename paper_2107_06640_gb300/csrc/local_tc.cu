@@ -215,7 +215,8 @@ __device__ __forceinline__ bool pair_round(Lane& L, F&& issue_fn) {
 
 // One tile, the share of half H (8-column chunks c with c % 2 == H); false
 // after a timed-out wait.
-template <int H>
+// kBuf: some elements of the launch have an LTS buffer (a coarser neighbour)
+template <int H, bool kBuf>
 __device__ __forceinline__ bool local_tile(Lane& L, int64_t tile) {
   const int64_t v0 = L.v_begin + tile * TE;
   const int64_t nrem = L.n_virtual - tile * TE;
@@ -329,7 +330,7 @@ __device__ __forceinline__ bool local_tile(Lane& L, int64_t tile) {
     tc::ld3x8(trow + cAcc + 8 * (H + 6), trow + cAcc + 8 * (H + 8), trow + cAcc + 8 * (H == 0 ? 10 : 9), tv + 24);
     // an element with a coarser neighbour also adds its four face traces to
     // its LTS buffer, in FP64 (overwrite at the first of the two steps)
-    if (L.btrace_mode && L.bslot && valid) {
+    if (kBuf && L.btrace_mode && L.bslot && valid) {
       const int bs = L.bslot[e];
       if (bs >= 0) {
         double* bt = L.btrace + ((int64_t)bs * L.S + (v - e * L.S)) * 36 * BF;
@@ -415,6 +416,7 @@ __device__ __forceinline__ bool local_tile(Lane& L, int64_t tile) {
   return true;
 }
 
+template <bool kBuf>
 __global__ void __launch_bounds__(kThreadsL, 1) local_tc_kernel(StepArgs a, int64_t n_virtual) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   float* sm = reinterpret_cast<float*>(smem_raw);
@@ -470,7 +472,7 @@ __global__ void __launch_bounds__(kThreadsL, 1) local_tc_kernel(StepArgs a, int6
   L.phase = 0;
   const int64_t ntiles = (n_virtual + TE - 1) / TE;
   for (int64_t tile = (int64_t)blockIdx.x * 2 + slot; tile < ntiles; tile += (int64_t)gridDim.x * 2) {
-    const bool ok = half == 0 ? local_tile<0>(L, tile) : local_tile<1>(L, tile);
+    const bool ok = half == 0 ? local_tile<0, kBuf>(L, tile) : local_tile<1, kBuf>(L, tile);
     if (!ok) break;
   }
   // after a timed-out wait, give this slot's MMAs in flight a bounded chance
@@ -485,10 +487,13 @@ __global__ void __launch_bounds__(kThreadsL, 1) local_tc_kernel(StepArgs a, int6
 
 }  // namespace
 
-int launch_local_tc(const StepArgs& a, int64_t n_virtual, int n_sms, void* stream) {
+int launch_local_tc(const StepArgs& a, int64_t n_virtual, int n_sms, void* stream, bool buffers) {
   static bool configured = false;
   if (!configured) {
-    cudaError_t ce = cudaFuncSetAttribute(local_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, LImg::bytes);
+    cudaError_t ce = cudaFuncSetAttribute(local_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          LImg::bytes);
+    if (ce == cudaSuccess)
+      ce = cudaFuncSetAttribute(local_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, LImg::bytes);
     if (ce != cudaSuccess) return (int)ce;
     configured = true;
   }
@@ -496,7 +501,10 @@ int launch_local_tc(const StepArgs& a, int64_t n_virtual, int n_sms, void* strea
   const int64_t ntiles = (n_virtual + TE - 1) / TE;
   const int64_t want = (ntiles + 1) / 2;
   const unsigned grid = (unsigned)(want < n_sms ? want : n_sms);
-  local_tc_kernel<<<grid, kThreadsL, LImg::bytes, (cudaStream_t)stream>>>(a, n_virtual);
+  if (buffers)
+    local_tc_kernel<true><<<grid, kThreadsL, LImg::bytes, (cudaStream_t)stream>>>(a, n_virtual);
+  else
+    local_tc_kernel<false><<<grid, kThreadsL, LImg::bytes, (cudaStream_t)stream>>>(a, n_virtual);
   return (int)cudaGetLastError();
 }
 

@@ -90,7 +90,8 @@ __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0
 // array (>= 0), none (-1), or for a coarser neighbour -2 - the offset of its
 // derivative traces [N+1][9][Bf], integrated here over this element's
 // sub-interval with the coefficients cc (sum_k cc_k D_k, in the order of the
-// CUDA-core kernel).
+// CUDA-core kernel).  kCoarse: the launch has such faces.
+template <bool kCoarse>
 __device__ __forceinline__ void stage_face(int f, int u, int64_t v0, int nE, const float* trace,
                                            const long long* nbase, float* so, float* sn, const float* dtrace,
                                            const float* cc) {
@@ -104,7 +105,7 @@ __device__ __forceinline__ void stage_face(int f, int u, int64_t v0, int nE, con
       const long long nb = nbase[f * TE + ei];
       const bool okn = ok && nb >= 0;
       cp16(so + ei * kSS + 4 * ch, trace + ((v0 + (ok ? ei : 0)) * 4 + f) * kFS + 4 * ch, ok);
-      if (ok && nb <= -2) {
+      if (kCoarse && ok && nb <= -2) {
         const float* dt = dtrace + (-2 - nb);
         float x[4];
 #pragma unroll
@@ -126,8 +127,9 @@ __device__ __forceinline__ void stage_face(int f, int u, int64_t v0, int nE, con
 }
 
 // kOne: one scenario (S = 1), where a virtual element is its element and the
-// 64-bit divisions by S drop out
-template <bool kOne>
+// 64-bit divisions by S drop out; kCoarse: some faces of the launch have a
+// coarser LTS neighbour (without, their code stays out of the kernel)
+template <bool kOne, bool kCoarse>
 __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, int64_t n_virtual) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   float* sm = reinterpret_cast<float*>(smem_raw);
@@ -205,7 +207,7 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
       long long nb = -1;
       int pm = 0;
       const int kind = (info >> 5) & 7;
-      if (ei < pnE && (kind == NK_SAME || kind == NK_COARSE)) {
+      if (ei < pnE && (kind == NK_SAME || (kCoarse && kind == NK_COARSE))) {
         const int64_t ve = pv0 + ei, ee = elem(ve);
         if (kind == NK_SAME) {
           const int64_t vn_e = (int64_t)nbe * S + (ve - ee * S);
@@ -229,7 +231,7 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
     }
     for (int c = u; c < ne * (PAR / 4); c += 256)
       cp16(sPr + 4 * c, reinterpret_cast<const float*>(a.par) + e0 * PAR + 4 * c);
-    stage_face(0, u, pv0, pnE, trace, sNb, sStage, sStage + kStage, dtrace, cc);
+    stage_face<kCoarse>(0, u, pv0, pnE, trace, sNb, sStage, sStage + kStage, dtrace, cc);
     cp_commit();
   };
 
@@ -255,7 +257,7 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
       // ---- stage face f + 1 while face f is used
       if (f < 3) {
         float* nb_buf = sStage + ((f + 1) & 1) * 2 * kStage;
-        stage_face(f + 1, u, v0, nE, trace, sNb, nb_buf, nb_buf + kStage, dtrace, cc);
+        stage_face<kCoarse>(f + 1, u, v0, nE, trace, sNb, nb_buf, nb_buf + kStage, dtrace, cc);
         cp_commit();
         cp_wait<1>();
       } else {
@@ -411,14 +413,13 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
 
 }  // namespace
 
-int launch_neighbour_tc(const StepArgs& a, int64_t n_virtual, int n_sms, void* stream) {
+int launch_neighbour_tc(const StepArgs& a, int64_t n_virtual, int n_sms, void* stream, bool coarse) {
   static bool configured = false;
   if (!configured) {
-    cudaError_t ce =
-        cudaFuncSetAttribute(neighbour_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, NImg::bytes);
-    if (ce == cudaSuccess)
-      ce = cudaFuncSetAttribute(neighbour_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                NImg::bytes);
+    cudaError_t ce = cudaSuccess;
+    for (auto k : {neighbour_tc_kernel<true, false>, neighbour_tc_kernel<false, false>,
+                   neighbour_tc_kernel<true, true>, neighbour_tc_kernel<false, true>})
+      if (ce == cudaSuccess) ce = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, NImg::bytes);
     if (ce != cudaSuccess) return (int)ce;
     configured = true;
   }
@@ -426,10 +427,9 @@ int launch_neighbour_tc(const StepArgs& a, int64_t n_virtual, int n_sms, void* s
   const int64_t ntiles = (n_virtual + TE - 1) / TE;
   const int64_t want = (ntiles + 1) / 2;
   const unsigned grid = (unsigned)(want < n_sms ? want : n_sms);
-  if (a.S == 1)
-    neighbour_tc_kernel<true><<<grid, kThreadsN, NImg::bytes, (cudaStream_t)stream>>>(a, n_virtual);
-  else
-    neighbour_tc_kernel<false><<<grid, kThreadsN, NImg::bytes, (cudaStream_t)stream>>>(a, n_virtual);
+  auto k = a.S == 1 ? (coarse ? neighbour_tc_kernel<true, true> : neighbour_tc_kernel<true, false>)
+                    : (coarse ? neighbour_tc_kernel<false, true> : neighbour_tc_kernel<false, false>);
+  k<<<grid, kThreadsN, NImg::bytes, (cudaStream_t)stream>>>(a, n_virtual);
   return (int)cudaGetLastError();
 }
 
