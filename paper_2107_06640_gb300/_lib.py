@@ -39,7 +39,8 @@ class adg_info(C.Structure):
                 ("n_clusters", C.c_int), ("cluster_size", C.c_int64 * 16), ("dt_min", C.c_double),
                 ("macro_dt", C.c_double), ("time", C.c_double), ("n_gravity_faces", C.c_int64),
                 ("n_fault_faces", C.c_int64), ("updates_per_macro", C.c_int64),
-                ("device_bytes", C.c_int64), ("tensor_core_updates_per_macro", C.c_int64)]
+                ("device_bytes", C.c_int64), ("tensor_core_updates_per_macro", C.c_int64),
+                ("n_receivers", C.c_int64)]
 
 
 _P = C.c_void_p
@@ -126,6 +127,34 @@ def _f64(a):
     return np.ascontiguousarray(a, dtype=np.float64)
 
 
+# Host arrays cross the ABI as plain pointers: the library reads or writes as
+# many values as the context's sizes say, so every array is checked here.
+_NT = {}  # tets of each context's uploaded mesh (for the material upload)
+
+
+def _dims(ctx):
+    """(n_tets, S, B, Bf, n_gravity_faces, n_fault_faces, n_receivers) of an initialised context."""
+    i = adg_query(ctx)
+    ncl = int(i.n_clusters)
+    w = sum(int(i.cluster_size[c]) << (ncl - 1 - c) for c in range(ncl))
+    S = int(i.updates_per_macro) // w if w else 1
+    return (int(i.n_tets), S, int(i.n_basis), int(i.n_face_nodes), int(i.n_gravity_faces), int(i.n_fault_faces),
+            int(i.n_receivers))
+
+
+def _host(a, dtype, count, what, out=False):
+    """`a` as the library sees it: `count` values of `dtype`, C-contiguous.  An
+    input is converted; an output must already be such an array."""
+    if out:
+        if not (isinstance(a, np.ndarray) and a.dtype == np.dtype(dtype) and a.flags.c_contiguous):
+            raise ValueError(f"{what}: needs a C-contiguous {np.dtype(dtype).name} array")
+    else:
+        a = np.ascontiguousarray(a, dtype=dtype)
+    if a.size != count:
+        raise ValueError(f"{what}: {a.size} values given, the library uses {count}")
+    return a
+
+
 def adg_default_config():
     cfg = adg_config()
     load().adg_default_config(C.byref(cfg))
@@ -141,14 +170,20 @@ def adg_create(cfg):
 def adg_upload_mesh(ctx, xyz, tets, face_tag, face_partner=None):
     xyz = _f64(xyz)
     tets = np.ascontiguousarray(tets, dtype=np.int64)
-    face_tag = np.ascontiguousarray(face_tag, dtype=np.int32)
-    fp = None if face_partner is None else np.ascontiguousarray(face_partner, dtype=np.int64)
-    _check(ctx, load().adg_upload_mesh(ctx, xyz.shape[0], _ptr(xyz), tets.shape[0], _ptr(tets),
-                                       _ptr(face_tag), _ptr(fp)))
+    if xyz.ndim != 2 or xyz.shape[1] != 3 or tets.ndim != 2 or tets.shape[1] != 4:
+        raise ValueError("mesh: xyz [nv][3] and tets [nt][4] expected")
+    nt = tets.shape[0]
+    face_tag = _host(face_tag, np.int32, 4 * nt, "face_tag [nt][4]")
+    fp = None if face_partner is None else _host(face_partner, np.int64, 4 * nt, "face_partner [nt][4]")
+    _check(ctx, load().adg_upload_mesh(ctx, xyz.shape[0], _ptr(xyz), nt, _ptr(tets), _ptr(face_tag), _ptr(fp)))
+    _NT[ctx.value] = nt
 
 
 def adg_upload_material(ctx, rho, lam, mu):
-    rho, lam, mu = _f64(rho), _f64(lam), _f64(mu)
+    nt = _NT.get(ctx.value)
+    if nt is None:
+        raise ValueError("material: upload the mesh first")
+    rho, lam, mu = (_host(a, np.float64, nt, name) for a, name in ((rho, "rho"), (lam, "lambda"), (mu, "mu")))
     _check(ctx, load().adg_upload_material(ctx, _ptr(rho), _ptr(lam), _ptr(mu)))
 
 
@@ -162,25 +197,30 @@ def adg_query(ctx):
     return info
 
 
+def _ndofs(ctx):
+    nt, S, B = _dims(ctx)[:3]
+    return nt * S * 9 * B
+
+
 def adg_set_dofs(ctx, Q):
-    Q = _f64(Q)
+    Q = _host(Q, np.float64, _ndofs(ctx), "dofs [nt][S][9][B]")
     _check(ctx, load().adg_set_dofs(ctx, _ptr(Q)))
 
 
 def adg_get_dofs(ctx, out):
-    assert out.dtype == np.float64 and out.flags.c_contiguous
+    _host(out, np.float64, _ndofs(ctx), "dofs [nt][S][9][B]", out=True)
     _check(ctx, load().adg_get_dofs(ctx, _ptr(out)))
     return out
 
 
 def adg_set_dofs_f32(ctx, Q):
     """Q: float32 [tet][S][9][B] (pinned host memory for full speed)."""
-    Q = np.ascontiguousarray(Q, dtype=np.float32)
+    Q = _host(Q, np.float32, _ndofs(ctx), "dofs [nt][S][9][B]")
     _check(ctx, load().adg_set_dofs_f32(ctx, _ptr(Q)))
 
 
 def adg_get_dofs_f32(ctx, out):
-    assert out.dtype == np.float32 and out.flags.c_contiguous
+    _host(out, np.float32, _ndofs(ctx), "dofs [nt][S][9][B]", out=True)
     _check(ctx, load().adg_get_dofs_f32(ctx, _ptr(out)))
     return out
 
@@ -208,13 +248,16 @@ def adg_hydrostatic_start(ctx):
 
 
 def adg_get_dofs_subset(ctx, tets, out):
-    tets = np.ascontiguousarray(tets, dtype=np.int64)
-    assert out.dtype == np.float64 and out.flags.c_contiguous and out.shape[0] == tets.size
+    tets = np.ascontiguousarray(tets, dtype=np.int64).ravel()
+    nt, S, B = _dims(ctx)[:3]
+    _host(out, np.float64, tets.size * S * 9 * B, "dofs [n][S][9][B]", out=True)
     _check(ctx, load().adg_get_dofs_subset(ctx, tets.size, _ptr(tets), _ptr(out)))
     return out
 
 
 def adg_initial_points(ctx, n_tets):
+    if int(n_tets) != _dims(ctx)[0]:
+        raise ValueError("initial points: n_tets differs from the mesh")
     n = C.c_int()
     _check(ctx, load().adg_initial_points(ctx, C.byref(n), None))
     xyz = np.empty((n_tets, n.value, 3))
@@ -223,11 +266,17 @@ def adg_initial_points(ctx, n_tets):
 
 
 def adg_set_initial_values(ctx, values):
-    values = _f64(values)
+    nt, S = _dims(ctx)[:2]
+    nq = C.c_int()
+    _check(ctx, load().adg_initial_points(ctx, C.byref(nq), None))
+    values = _host(values, np.float64, nt * S * nq.value * 9, "values [nt][S][n_pts][9]")
     _check(ctx, load().adg_set_initial_values(ctx, _ptr(values)))
 
 
 def adg_gravity_faces(ctx, n, Bf):
+    d = _dims(ctx)
+    if int(n) != d[4] or int(Bf) != d[3]:
+        raise ValueError("gravity faces: n or Bf differs from the context")
     ef = np.empty(n, np.int64)
     xyz = np.empty((n, Bf, 3))
     if n:
@@ -235,12 +284,18 @@ def adg_gravity_faces(ctx, n, Bf):
     return ef, xyz
 
 
+def _neta(ctx):
+    nt, S, B, Bf, ngf = _dims(ctx)[:5]
+    return ngf * S * Bf
+
+
 def adg_set_eta(ctx, eta):
-    eta = _f64(eta)
+    eta = _host(eta, np.float64, _neta(ctx), "eta [n_gravity_faces][S][Bf]")
     _check(ctx, load().adg_set_eta(ctx, _ptr(eta)))
 
 
 def adg_read_ssh(ctx, out):
+    _host(out, np.float64, _neta(ctx), "eta [n_gravity_faces][S][Bf]", out=True)
     _check(ctx, load().adg_read_ssh(ctx, _ptr(out)))
     return out
 
@@ -282,6 +337,9 @@ FPAR, FSTATE, MLP_NPARAM, MLP_TRAINABLE = 13, 8, 1327, 1313
 
 
 def adg_fault_faces(ctx, nff, Bf):
+    d = _dims(ctx)
+    if int(nff) != d[5] or int(Bf) != d[3]:
+        raise ValueError("fault faces: nff or Bf differs from the context")
     mf = np.empty(nff, np.int64)
     pf = np.empty(nff, np.int64)
     xyz = np.empty((nff, Bf, 3))
@@ -290,8 +348,13 @@ def adg_fault_faces(ctx, nff, Bf):
     return mf, pf, xyz, nrm
 
 
+def _nfault(ctx):
+    nt, S, B, Bf, ngf, nff = _dims(ctx)[:6]
+    return nff * S * Bf
+
+
 def adg_set_fault(ctx, par):
-    par = _f64(par)
+    par = _host(par, np.float64, _nfault(ctx) * FPAR, "fault parameters [nff][S][Bf][13]")
     _check(ctx, load().adg_set_fault(ctx, _ptr(par)))
 
 
@@ -300,6 +363,7 @@ def adg_set_friction_law(ctx, law):
 
 
 def adg_read_fault(ctx, out):
+    _host(out, np.float64, _nfault(ctx) * FSTATE, "fault state [nff][S][Bf][8]", out=True)
     _check(ctx, load().adg_read_fault(ctx, _ptr(out)))
     return out
 
@@ -325,14 +389,16 @@ def adg_mlp_train(ctx, epochs, batch, lr, seed=0):
 
 def adg_mlp_params(ctx, set_params=None, enable=-1):
     get = np.empty(MLP_NPARAM, np.float32)
-    sp = None if set_params is None else np.ascontiguousarray(set_params, dtype=np.float32)
+    sp = None if set_params is None else _host(set_params, np.float32, MLP_NPARAM, "network parameters")
     _check(ctx, load().adg_mlp_params(ctx, _ptr(sp), _ptr(get), int(enable)))
     return get
 
 
 def adg_mlp_gradient(params, rows):
-    params = np.ascontiguousarray(params, dtype=np.float32)
+    params = _host(params, np.float32, MLP_NPARAM, "network parameters")
     rows = np.ascontiguousarray(rows, dtype=np.float32)
+    if rows.ndim != 2 or rows.shape[1] != 7:
+        raise ValueError("rows: [n][7] expected (6 features, target)")
     grad = np.empty(MLP_TRAINABLE, np.float32)
     loss = np.zeros(1)
     _check(None, load().adg_mlp_gradient(_ptr(params), rows.shape[0], _ptr(rows), _ptr(grad), _ptr(loss)))
@@ -341,10 +407,14 @@ def adg_mlp_gradient(params, rows):
 
 def adg_add_receivers(ctx, xyz):
     xyz = _f64(xyz)
+    if xyz.ndim != 2 or xyz.shape[1] != 3:
+        raise ValueError("receivers: xyz [n][3] expected")
     _check(ctx, load().adg_add_receivers(ctx, xyz.shape[0], _ptr(xyz)))
 
 
 def adg_read_receivers(ctx, out):
+    d = _dims(ctx)
+    _host(out, np.float64, d[6] * d[1] * 9, "receivers [n][S][9]", out=True)
     _check(ctx, load().adg_read_receivers(ctx, _ptr(out)))
     return out
 
@@ -379,4 +449,6 @@ def adg_last_error(ctx):
 
 
 def adg_destroy(ctx):
+    if ctx is not None:
+        _NT.pop(ctx.value, None)
     load().adg_destroy(ctx)

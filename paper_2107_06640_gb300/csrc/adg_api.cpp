@@ -228,6 +228,7 @@ int adg_query(const adg_ctx* ctx, adg_info* out) {
   int64_t utc = 0;
   for (int i = 0; i < c.ncl && i < (int)c.cl_plain.size(); ++i) utc += c.cl_plain[i] * ((int64_t)1 << (c.ncl - 1 - i));
   out->tensor_core_updates_per_macro = utc * c.S;
+  out->n_receivers = c.n_rec;
   return ADG_OK;
 }
 
