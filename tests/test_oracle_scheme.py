@@ -188,3 +188,35 @@ def test_lts_one_cluster_is_bitwise_gts_and_two_clusters_keep_accuracy():
     e_gts = np.linalg.norm(g1.l2_error(plane_wave(g1.t)))
     e_lts = np.linalg.norm(l2.l2_error(plane_wave(l2.t)))
     assert e_lts < 1.5 * e_gts, (e_lts, e_gts)
+
+
+def test_fluid_stress_stays_isotropic():
+    """The acoustic special case of Sec. 4.1 (mu = 0, s_ij = -p delta_ij) is an
+    invariant subspace of the discrete scheme: with mu = 0 every stress
+    update of a fluid element, in the volume term and in the Godunov flux (also
+    across the fluid-solid interface and the gravitational surface), is lambda
+    times a divergence or a normal velocity jump times the identity.  So fluid
+    elements that start with s_xx = s_yy = s_zz and no shear stress keep that
+    form.  The 4-quantity (p, v) ocean is this restriction."""
+    from synthetic.workloads import coupled_box
+    m, (rho, lam, mu) = coupled_box(nxy=2, n_water=1, n_crust=1, L=4e3, depth=2e3, water=1e3)
+    N = 3
+    o = Oracle(m.xyz, m.tets, m.face_tag, m.face_partner, rho, lam, mu, N, cfl=0.5)
+    rng = np.random.default_rng(4)
+    Q = rng.standard_normal(o.Q.shape) * 1e-3
+    fluid = mu == 0.0
+    assert fluid.any() and (~fluid).any()
+    p = rng.standard_normal(Q[fluid].shape[:2]) * 1e-3
+    for i in range(3):
+        Q[fluid, :, i] = -p
+    Q[fluid, :, 3:6] = 0.0
+    o.Q = Q
+    o.eta[:] = rng.standard_normal(o.eta.shape) * 1e-2
+    for _ in range(3):
+        o.step_gts()
+    Qf = o.Q[fluid]
+    scale = np.abs(Qf[..., 0]).max()
+    assert scale > 0
+    assert np.max(np.abs(Qf[..., 1] - Qf[..., 0])) <= 1e-12 * scale
+    assert np.max(np.abs(Qf[..., 2] - Qf[..., 0])) <= 1e-12 * scale
+    assert np.max(np.abs(Qf[..., 3:6])) <= 1e-12 * scale
