@@ -50,13 +50,6 @@ __host__ __device__ __forceinline__ float tf32_trunc(float x) {
 #endif
 }
 
-__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-      "l"(da), "l"(db), "r"(idesc), "r"(acc));
-}
-
 // MMA with the A operand in TMEM (lane = row, one tf32 per column)
 __device__ __forceinline__ void mma_ts(uint32_t d, uint32_t a, uint64_t db, uint32_t idesc, uint32_t acc) {
   asm volatile(
