@@ -6,14 +6,15 @@
 //   local kernel      Sec. 4.1: Cauchy-Kovalewski predictor
 //                       D^{k+1} = -sum_a KT_a D^k A*_a^T,  KT_a[m][l] = int phi_m dphi_l/dxi_a,
 //                     time integral I = sum_k dt^{k+1}/(k+1)! D^k (Eq. taylor),
-//                     volume sum_a K_a I A*_a^T, local Godunov flux with F^-
-//                     (Sec. 4.2, Eq. numerical-flux) lifted from nodal face values,
-//                     gravitational faces (Sec. 4.3): exact (eta, H) Taylor
-//                     recursion in FP64 at the face nodes, flux from
-//                     int w1^b = -rho g H and int w7^b = eta^{n+1} - eta^n;
-//                     writes its own face traces (and LTS buffers/derivatives).
-//   neighbour kernel  gathers the neighbours' face traces (re-oriented by a
-//                     node permutation), applies F^+ and lifts.
+//                     volume sum_a K_a I A*_a^T, its own nodal face traces
+//                     (and LTS buffers / derivative traces); gravitational
+//                     faces (Sec. 4.3): exact (eta, H) Taylor recursion in
+//                     FP64 at the face nodes and that face's time-integrated
+//                     flux from int w1^b = -rho g H and int w7^b = eta^{n+1} - eta^n.
+//   neighbour kernel  Godunov fluxes of all four faces (Sec. 4.2, Eq.
+//                     numerical-flux): F^- on the own traces, F^+ on the
+//                     neighbours' (re-oriented by a node permutation), the
+//                     stored fluxes of gravitational and fault faces; one lift.
 // Dofs layout: Q[v][9][B] (basis fastest); traces [v][4][face_stride(N)], each face
 // block [9][Bf] (node fastest) followed by padding.
 #pragma once
@@ -86,6 +87,7 @@ int lift_tc_floats();
 // ---- dynamic rupture (rupture.cu) ----
 // per-node fault parameters (double, stride FPAR), in this order:
 //   a, b, L, f0, V0, f_w, V_w, sigma_n0, tau0_x, tau0_y, tau0_z, psi_init, V_init
+// (linear slip weakening: mu_s, mu_d, D_c, cohesion in the first four slots)
 constexpr int FPAR = 13;
 // per-node fault state (double, stride FSTATE): |V|, psi, slip_xyz, traction_xyz
 constexpr int FSTATE = 8;
