@@ -159,6 +159,65 @@ def test_free_surface_is_gravity_with_zero_eta():
     assert abs(a[0]) < 1e-15 and abs(a[3]) < 1e-15 and abs(a[5]) < 1e-15
 
 
+def _upwind_plus(A):
+    """A+ = the part of the rotated Jacobian with positive speeds (waves that
+    leave through the face): V diag(max(lambda, 0)) V^-1 where A is
+    diagonalisable; for a fluid (whose zero eigenvalue is defective) the sum
+    over the simple positive eigenvalues of lambda r l^T / (l^T r)."""
+    lam, V = np.linalg.eig(A)
+    if np.linalg.cond(V) < 1e8:
+        return (V @ np.diag(np.maximum(lam.real, 0.0)) @ np.linalg.inv(V)).real
+    lamL, W = np.linalg.eig(A.T)
+    out = np.zeros_like(A)
+    for i in np.nonzero(lam.real > 1e-6 * np.abs(lam).max())[0]:
+        r = V[:, i].real
+        l = W[:, np.argmin(np.abs(lamL - lam[i]))].real
+        out += lam[i].real * np.outer(r, l) / (l @ r)
+    return out
+
+
+@pytest.mark.parametrize("mat", [(2700.0, 3.24e10, 3.24e10), (1.0, 2.0, 1.0), (1000.0, 2.25e9, 0.0)])
+def test_absorbing_flux_is_the_upwind_flux_of_the_interior_state(mat):
+    """Absorbing boundary (ghost q+ = 0 with the interior material): the flux
+    A w^b equals A+ w^-, the classical upwind flux with nothing entering from
+    outside; a transparent ghost (q+ = q-) gives A w^- instead."""
+    rho, lam, mu = mat
+    Zp, Zs = ph.impedances(rho, lam, mu)
+    A = ph.jacobians(rho, lam, mu)[0]
+    Ap = _upwind_plus(A)
+    for _ in range(4):
+        wm = rng.standard_normal(9) * np.array([1e6] * 6 + [1.0] * 3)
+        wb = ph.middle_state(wm, ph.ghost(wm, 3), Zp, Zp, Zs, Zs)
+        got = ph.flux_rotated(wb, rho, lam, mu)
+        assert np.allclose(got, Ap @ wm, rtol=0, atol=1e-10 * np.abs(A @ wm).max())
+        assert not np.allclose(got, A @ wm, rtol=0, atol=1e-3 * np.abs(A @ wm).max())
+
+
+@pytest.mark.parametrize("mat", [(1.0, 2.0, 1.0), (1000.0, 2.25e9, 0.0)])
+@pytest.mark.parametrize("tag", [1, 6])
+def test_wall_middle_states_keep_the_outgoing_waves_and_meet_the_wall_conditions(mat, tag):
+    """Free surface (tag 1): zero traction, w1 = w4 = w6 = 0.  Rigid wall with
+    free slip (tag 6): zero normal velocity and zero shear traction, w7 = w4 =
+    w6 = 0.  In both, the characteristics leaving the element through the face
+    (sigma - Z v on (w1, w7) with Z_p, on (w4, w8) and (w6, w9) with Z_s in a
+    solid) equal the interior's: the wall only sets the incoming ones."""
+    rho, lam, mu = mat
+    Zp, Zs = ph.impedances(rho, lam, mu)
+    for _ in range(4):
+        wm = rng.standard_normal(9) * np.array([1e3] * 6 + [1.0] * 3)
+        wb = ph.middle_state(wm, ph.ghost(wm, tag), Zp, Zp, Zs, Zs)
+        sc = 1e-13 * np.abs(wm).max() * max(Zp, 1.0)
+        assert abs((wb[0] - Zp * wb[6]) - (wm[0] - Zp * wm[6])) <= sc
+        if mu > 0:
+            for ts, tv in ((3, 7), (5, 8)):
+                assert abs((wb[ts] - Zs * wb[tv]) - (wm[ts] - Zs * wm[tv])) <= sc
+        assert wb[3] == pytest.approx(0.0, abs=sc) and wb[5] == pytest.approx(0.0, abs=sc)
+        if tag == 1:
+            assert wb[0] == pytest.approx(0.0, abs=sc)
+        else:
+            assert wb[6] == pytest.approx(0.0, abs=sc / max(Zp, 1.0))
+
+
 def test_gravity_ode_closed_forms():
     dt, kappa = 0.7, 0.3
     # f = 0: eta = eta0 e^{-kappa dt}, H = eta0 (1 - e^{-kappa dt})/kappa
