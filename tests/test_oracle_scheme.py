@@ -190,6 +190,34 @@ def test_lts_one_cluster_is_bitwise_gts_and_two_clusters_keep_accuracy():
     assert e_lts < 1.5 * e_gts, (e_lts, e_gts)
 
 
+@pytest.mark.parametrize("a,n_clusters", [(0.6, 2), (0.95, 3)])
+def test_lts_conserves_the_element_means(a, n_clusters):
+    """In a uniform periodic medium Eq. (elasticity-pde) is in conservation
+    form and the Godunov flux is linear in the two time-integrated traces, so
+    the scheme changes sum_e |J_e| Q_e,0 (the integral of q) by face terms that
+    cancel between neighbours whenever both sides integrate the same states.
+    Rate-2 LTS (Sec. 4.4) gives them the same states: the coarse side takes the
+    fine side's buffer (the sum of its integrals over the coarse step), the
+    fine side the coarse Taylor expansion integrated over each sub-interval,
+    which sum to the coarse integral.  So the integral of q is conserved to
+    rounding with any number of clusters."""
+    m = _warped_periodic(4, a)
+    rho, lam, mu = syn.elastic_uniform(m.nt)
+    o = Oracle(m.xyz, m.tets, m.face_tag, m.face_partner, rho, lam, mu, 3, cfl=0.5, max_clusters=n_clusters)
+    assert np.bincount(o.cluster).size == n_clusters
+    rng = np.random.default_rng(11)
+    W = rng.standard_normal((3, 9))
+    o.Q = o.project(lambda x: 1.0 + np.sin(2 * np.pi * (x @ W)))
+    total = lambda: np.einsum("e,ep->p", o.geo.detJ, o.Q[:, 0, :])
+    t0 = total()
+    scale = np.einsum("e,ep->p", o.geo.detJ, np.abs(o.Q[:, 0, :])).max()
+    for _ in range(3):
+        o.advance_macro()
+    assert np.max(np.abs(total() - t0)) <= 1e-13 * scale
+    # the solution did change
+    assert np.max(np.abs(o.Q[:, 1:, :])) > 0 and not np.allclose(o.Q, o.project(lambda x: 1.0 + np.sin(2 * np.pi * (x @ W))))
+
+
 def test_fluid_stress_stays_isotropic():
     """The acoustic special case of Sec. 4.1 (mu = 0, s_ij = -p delta_ij) is an
     invariant subspace of the discrete scheme: with mu = 0 every stress
