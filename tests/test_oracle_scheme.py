@@ -248,3 +248,30 @@ def test_fluid_stress_stays_isotropic():
     assert np.max(np.abs(Qf[..., 1] - Qf[..., 0])) <= 1e-12 * scale
     assert np.max(np.abs(Qf[..., 2] - Qf[..., 0])) <= 1e-12 * scale
     assert np.max(np.abs(Qf[..., 3:6])) <= 1e-12 * scale
+
+
+@pytest.mark.parametrize("N", [2, 4])
+def test_projection_and_point_evaluation_reproduce_a_polynomial(N):
+    """The receiver readout (Sec. 5 outputs): a field that is a polynomial of
+    degree N in x, y, z lies in every element's space P_N, so its L2
+    projection is exact and evaluating the element polynomial at any point
+    inside the element returns the field, on a warped (non-uniform) mesh
+    where each tet has its own affine map."""
+    m = _warped_periodic(3)
+    rho, lam, mu = syn.elastic_uniform(m.nt)
+    o = Oracle(m.xyz, m.tets, m.face_tag, m.face_partner, rho, lam, mu, N, cfl=0.5)
+    rng = np.random.default_rng(5)
+    terms = [(i, j, k) for i in range(N + 1) for j in range(N + 1 - i) for k in range(N + 1 - i - j)]
+    coef = rng.standard_normal((len(terms), 9))
+
+    def field(x):
+        mono = np.stack([x[..., 0] ** i * x[..., 1] ** j * x[..., 2] ** k for (i, j, k) in terms], axis=-1)
+        return mono @ coef
+
+    o.Q = o.project(field)
+    e = rng.integers(0, o.E, 40)
+    lam4 = rng.dirichlet(np.ones(4), size=e.size)
+    x = np.einsum("rk,rkd->rd", lam4, m.xyz[m.tets[e]])
+    want = field(x)
+    got = o.evaluate(e, x)
+    assert np.max(np.abs(got - want)) <= 1e-11 * np.abs(want).max()
