@@ -103,7 +103,7 @@ def test_solid_fluid_reflection_transmission():
     assert err < 1e-2 and bad > 0.5, (err, bad)
 
 
-def _gravity_case(nx=4, nz=2, N=3, g=1.0, H=1.0, c=2.0, rho=1.0, L=2.0, amp=1e-2):
+def _gravity_case(nx=4, nz=2, N=3, g=1.0, H=1.0, c=2.0, rho=1.0, L=2.0, amp=1e-2, zs=None, max_clusters=1):
     k = 2 * np.pi / L
     om = brentq(lambda w: w * w - g * np.sqrt(k * k - w * w / c / c) * np.tanh(np.sqrt(k * k - w * w / c / c) * H),
                 1e-3, c * k * 0.999)
@@ -123,10 +123,10 @@ def _gravity_case(nx=4, nz=2, N=3, g=1.0, H=1.0, c=2.0, rho=1.0, L=2.0, amp=1e-2
 
     xs = np.linspace(0, L, nx + 1)
     ys = np.linspace(0, L / nx, 2)
-    zs = np.linspace(-H, 0, nz + 1)
+    zs = np.linspace(-H, 0, nz + 1) if zs is None else np.asarray(zs, np.float64) * H
     msh = syn.kuhn_box(xs, ys, zs, tags={"x-": 4, "x+": 4, "y-": 4, "y+": 4, "z-": 6, "z+": 2})
     o = Oracle(msh.xyz, msh.tets, msh.face_tag, msh.face_partner, np.full(msh.nt, rho),
-               np.full(msh.nt, rho * c * c), np.zeros(msh.nt), N, cfl=0.5, g=g)
+               np.full(msh.nt, rho * c * c), np.zeros(msh.nt), N, cfl=0.5, g=g, max_clusters=max_clusters)
     o.Q = o.project(exact(0.0))
     for e, f in np.argwhere(o.geo.face_tag == 2):
         o.eta[e, f] = amp * np.cosh(m_ * H) * np.cos(k * o.face_x[e, f, :, 0]) / (rho * g)
@@ -146,6 +146,33 @@ def test_surface_gravity_wave_dispersion():
     bad = np.linalg.norm(o.l2_error(exact(o.t, om=k * 1.0))) / ref
     assert err < 1e-2 and bad > 0.1, (err, bad)
     assert o.energy() <= E0 * (1 + 1e-12)
+
+
+@pytest.mark.parametrize("zs,top", [([-1, -0.9, -0.45, 0], 1), ([-1, -0.6, -0.2, -0.1, 0], 0)])
+def test_surface_gravity_wave_with_lts(zs, top):
+    """The standing surface-gravity wave under rate-2 LTS (Sec. 4.4) on a grid
+    graded in depth: two clusters, with the gravitational surface in the
+    coarse (top = 1) or the fine (top = 0) cluster, so the (eta, H) ODE runs
+    over that cluster's step from its own Taylor expansion.  The error after
+    half a period stays that of global time stepping on the same grid, and the
+    energy (mechanical plus surface) does not grow."""
+    g_, exact, om, k = _gravity_case(zs=zs, max_clusters=1)
+    o, *_ = _gravity_case(zs=zs, max_clusters=2)
+    assert np.bincount(o.cluster).size == 2
+    assert set(o.cluster[np.argwhere(o.geo.face_tag == 2)[:, 0]]) == {top}
+    T = np.pi / om
+    errs = []
+    for r in (g_, o):
+        macro = r.dtmin * (1 << int(r.cluster.max()))
+        ns = int(np.ceil(T / macro))
+        E0 = r.energy()
+        for _ in range(ns):
+            r.advance_macro(T / ns / macro)
+            assert r.energy() <= E0 * (1 + 1e-12)
+        assert r.t == pytest.approx(T, rel=1e-13)
+        ref = np.linalg.norm(r.l2_error(exact(r.t), Q=0 * r.Q))
+        errs.append(np.linalg.norm(r.l2_error(exact(r.t))) / ref)
+    assert errs[0] < 3e-3 and errs[1] < 1.05 * errs[0], errs
 
 
 def test_energy_does_not_grow_periodic():
