@@ -113,8 +113,9 @@ def test_traction_is_the_strength_while_weakening():
     assert Th - ETA * V[0] == pytest.approx(want, rel=1e-12)
 
 
-@pytest.mark.parametrize("N", [2, 3])
-def test_locked_fault_in_the_scheme_equals_welded_interior_faces(N):
+@pytest.mark.parametrize("N,zs,lts", [(2, (-2e3, -1e3, 0.0), False), (3, (-2e3, -1e3, 0.0), False),
+                                      (3, (-2e3, -1.6e3, 0.0), True)])
+def test_locked_fault_in_the_scheme_equals_welded_interior_faces(N, zs, lts):
     """A fault that cannot slip (cohesion far above any traction, so |V| = 0
     exactly) is a welded interface: the whole scheme with it equals the same
     mesh with those faces interior, to rounding.  This pins the fault path at
@@ -123,7 +124,10 @@ def test_locked_fault_in_the_scheme_equals_welded_interior_faces(N):
     time dependence), the nodal-to-Gauss interpolation and the lift into both
     elements with the area / |J| scaling of each side (Sec. 4.2, Eq.
     bc-dynrup); the elements on either side have different materials and,
-    on a warped grid (so the fault is not planar either), different volumes."""
+    on a warped grid (so the fault is not planar either), different volumes.
+    With rate-2 LTS (Sec. 4.4) the fault faces lie in both clusters and the
+    fault is solved over each cluster's step from the stored expansions; the
+    welded mesh takes the same clusters."""
     from oracle.ader import Oracle
     from synthetic.mesh import kuhn_box
 
@@ -132,16 +136,19 @@ def test_locked_fault_in_the_scheme_equals_welded_interior_faces(N):
         x[:, 2] += 120 * np.sin(x[:, 0] / 900.0)
         return x
 
-    m = kuhn_box(np.linspace(0, 4e3, 5), np.linspace(0, 2e3, 3), np.linspace(-2e3, 0, 3), warp=warp,
+    m = kuhn_box(np.linspace(0, 4e3, 5), np.linspace(0, 2e3, 3), np.array(zs), warp=warp,
                  fault=dict(c=0, jrange=(0, 2), krange=(0, 2)))
     g = np.random.default_rng(3)
     rho = 2700.0 * (1 + 0.2 * g.uniform(-1, 1, m.nt))
     mu = 3.2e10 * (1 + 0.2 * g.uniform(-1, 1, m.nt))
     lam = mu * (1 + 0.3 * g.uniform(0, 1, m.nt))
-    fault = Oracle(m.xyz, m.tets, m.face_tag, m.face_partner, rho, lam, mu, N, cfl=0.5)
+    mc = 2 if lts else 1
+    fault = Oracle(m.xyz, m.tets, m.face_tag, m.face_partner, rho, lam, mu, N, cfl=0.5, max_clusters=mc)
     welded = Oracle(m.xyz, m.tets, np.where(m.face_tag == 5, 0, m.face_tag), m.face_partner, rho, lam, mu, N,
-                    cfl=0.5)
+                    cfl=0.5, max_clusters=mc)
+    welded.cluster = fault.cluster.copy()
     assert fault.nff == 8 and welded.nff == 0
+    assert np.unique(fault.cluster[fault.fm[:, 0]]).size == (2 if lts else 1)
     Bf = (N + 1) * (N + 2) // 2
     par = {k: np.zeros((fault.nff, Bf)) for k in ru.LSW_PARAMS}
     par.update(mu_s=np.full((fault.nff, Bf), 0.6), mu_d=np.full((fault.nff, Bf), 0.4),
@@ -151,8 +158,8 @@ def test_locked_fault_in_the_scheme_equals_welded_interior_faces(N):
     Q0 = g.standard_normal(fault.Q.shape) * np.array([1e6] * 6 + [1.0] * 3)
     fault.Q, welded.Q = Q0.copy(), Q0.copy()
     for _ in range(3):
-        fault.step_gts()
-        welded.step_gts()
+        for o in (fault, welded):
+            o.advance_macro() if lts else o.step_gts()
     assert np.all(fault.fault["V"] == 0) and np.all(fault.fault["slip"] == 0)
     for p in range(9):
         sc = np.abs(welded.Q[..., p]).max()
