@@ -131,3 +131,49 @@ def test_zero_strength_leaves_no_shear_traction():
     assert np.allclose(V, Th / st["eta"], rtol=1e-12)
     *_, tau_tot = ru.middle_traction_velocity(st, V, n)
     assert np.abs(tau_tot).max() < 1e-6
+
+
+def test_step_under_constant_load_converges_to_the_fault_ode():
+    """With both sides at rest the fault sees constant Theta and S, and Eq.
+    bc-dynrup with the slip-law state evolution is the scalar DAE
+    dpsi/dt = -(V/L)(psi - psi_ss(V)),  Theta - eta V = S f(V, psi).
+    Solved independently (scipy's DOP853, the root by Brent's method) it is the
+    limit of the oracle's steps: psi and V converge at first order in dt (each
+    step's tail after the last time point advances the state with the frozen
+    last rate) through a strong weakening (psi 0.6 -> 0.09, V x 20)."""
+    from scipy.integrate import solve_ivp
+    from scipy.optimize import brentq
+    rho, lam, mu = 3000.0, 3.0e10, 3.0e10
+    eta = np.sqrt(rho * mu) / 2.0
+    Th, S, T, N = 30e6, 40e6, 0.2, 3
+    p1 = _par(1, sn0=-S, t0x=Th)
+
+    def V_of(psi):
+        g = lambda lv: Th - eta * np.exp(lv) - S * ru.friction(np.array([np.exp(lv)]), np.array([psi]), p1)[0]
+        return np.exp(brentq(g, -700.0, np.log(Th / eta), xtol=1e-14, rtol=1e-15))
+
+    def rhs(t, y):
+        V = np.array([V_of(y[0])])
+        return -(V / p1["L"]) * (y - ru.psi_ss(V, p1))
+
+    errs = []
+    for steps in (40, 80, 160):
+        dt = T / steps
+        p = dict(p1, V=np.array([V_of(0.6)]))
+        n = np.array([[0.0, 0.0, 1.0]])
+        q = np.zeros((N + 1, 1, 9))
+        mat = tuple(np.full(1, v) for v in (rho, lam, mu))
+        hist = []
+        for _ in range(steps):
+            _, _, psi, V, _, _, _ = ru.solve_step(n, q, q, mat, mat, p, dt, N)
+            p = dict(p, psi=psi, V=V)
+            hist.append((psi[0], V[0]))
+        hist = np.array(hist)
+        t = dt * np.arange(1, steps + 1)
+        ref = solve_ivp(rhs, (0.0, T), [0.6], method="DOP853", rtol=1e-12, atol=1e-14, t_eval=t).y[0]
+        Vref = np.array([V_of(x) for x in ref])
+        errs.append((np.max(np.abs(hist[:, 0] - ref)), np.max(np.abs(hist[:, 1] / Vref - 1))))
+    assert ref[-1] < 0.1 and Vref[-1] > 15 * V_of(0.6)
+    errs = np.array(errs)
+    assert errs[-1, 0] < 2e-4 and errs[-1, 1] < 4e-3, errs
+    assert np.all(errs[:-1] / errs[1:] > 1.8), errs
