@@ -302,3 +302,45 @@ def test_projection_and_point_evaluation_reproduce_a_polynomial(N):
     want = field(x)
     got = o.evaluate(e, x)
     assert np.max(np.abs(got - want)) <= 1e-11 * np.abs(want).max()
+
+
+def test_energy_is_the_integral_of_the_energy_density():
+    """Oracle.energy (used by the non-growth pins) against a direct quadrature:
+    1/2 rho |v|^2 + 1/2 sigma . C^-1 sigma with C the 6 x 6 Voigt stiffness
+    (engineering shear strain) inverted numerically in the solid, p^2 / (2 K)
+    with p = -tr(sigma)/3 in the fluid, plus 1/2 rho g eta^2 on the
+    gravitational surface (Secs. 3, 4.3)."""
+    from oracle import basis as ob
+    from oracle.quadrature import tet_rule, tri_rule
+    from synthetic.workloads import coupled_box
+    m, (rho, lam, mu) = coupled_box(nxy=2, n_water=1, n_crust=1, L=4e3, depth=2e3, water=1e3)
+    N = 2
+    o = Oracle(m.xyz, m.tets, m.face_tag, m.face_partner, rho, lam, mu, N, cfl=0.5)
+    rng = np.random.default_rng(8)
+    o.Q = rng.standard_normal(o.Q.shape) * np.array([1e5] * 6 + [1e-2] * 3)
+    fluid = mu == 0
+    o.Q[fluid, :, 1] = o.Q[fluid, :, 0]
+    o.Q[fluid, :, 2] = o.Q[fluid, :, 0]
+    o.Q[fluid, :, 3:6] = 0.0
+    o.eta[:] = rng.standard_normal(o.eta.shape) * 0.1
+    pts, w = tet_rule(2 * N)
+    phi = ob.eval_basis(N, pts)
+    want = 0.0
+    for e in range(o.E):
+        q = phi @ o.Q[e]                                      # (nq, 9)
+        kin = 0.5 * rho[e] * np.sum(q[:, 6:] ** 2, axis=1)
+        if fluid[e]:
+            p = -q[:, :3].sum(1) / 3
+            pot = p ** 2 / (2 * lam[e])
+        else:
+            C = np.zeros((6, 6))
+            C[:3, :3] = lam[e]
+            C[np.arange(3), np.arange(3)] += 2 * mu[e]
+            C[np.arange(3, 6), np.arange(3, 6)] = mu[e]
+            Sinv = np.linalg.inv(C)
+            pot = 0.5 * np.einsum("qi,ij,qj->q", q[:, :6], Sinv, q[:, :6])
+        want += o.geo.volume[e] * 6 * np.sum(w * (kin + pot))   # |J| = 6 V, sum w = 1/6
+    _, fw = tri_rule(2 * N)
+    for e, f in np.argwhere(o.geo.face_tag == 2):
+        want += o.geo.area[e, f] * 2 * np.sum(fw * 0.5 * rho[e] * o.g * o.eta[e, f] ** 2)
+    assert o.energy() == pytest.approx(want, rel=1e-12)
