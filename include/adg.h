@@ -118,6 +118,20 @@ int adg_upload_material(adg_ctx* ctx, const double* rho, const double* lambda, c
  * per face (Sec. 4.2, Eq. numerical-flux), device allocation.  Dofs start at 0. */
 int adg_init(adg_ctx* ctx);
 
+/* Host-only plan of the uploaded mesh (no device needed): call after
+ * adg_upload_mesh and adg_upload_material, before or after adg_init.  Gives
+ * what adg_init derives from the mesh, in the caller's element order: the CFL
+ * time step of every element, dt_e = cfl/(2N+1) h_e / c_p,e with h_e the
+ * insphere diameter (Sec. 4.4), and its rate-2 cluster c_e (Sec. 4.4): the
+ * largest c with 2^c dt_min <= dt_e, at most max_clusters - 1, face neighbours
+ * at most one cluster apart and both sides of a fault face in one cluster.
+ * The element steps 2^c_e dt_min; a macro step is 2^(n_clusters-1) dt_min.
+ * dt_elem[nt] (seconds), cluster[nt], dt_min[1], n_clusters[1]: caller-owned
+ * outputs, each may be NULL.  Errors: ADG_E_STATE before both uploads;
+ * ADG_E_MESH for an inverted tet, an unmatched interior face or a bad periodic
+ * partner; ADG_E_INVALID for a bad material.  Nothing is written on error. */
+int adg_plan(adg_ctx* ctx, double* dt_elem, int32_t* cluster, double* dt_min, int* n_clusters);
+
 int adg_query(const adg_ctx* ctx, adg_info* out);
 
 /* Dofs in user tet order, layout [nt][S][9][B] (host, double). */

@@ -9,4 +9,4 @@ the C names; `Solver` is a convenience wrapper holding one context.
 
 from . import _lib  # noqa: F401
 from ._lib import AdgError, ADG_FP32, ADG_FP64, ADG_3XTF32, ADG_FRICTION_LSW, ADG_FRICTION_RS  # noqa: F401
-from .solver import Solver  # noqa: F401
+from .solver import Solver, plan  # noqa: F401

@@ -50,6 +50,7 @@ _SIGS = {
     "adg_upload_mesh": (C.c_int, [_P, C.c_int64, _P, C.c_int64, _P, _P, _P]),
     "adg_upload_material": (C.c_int, [_P, _P, _P, _P]),
     "adg_init": (C.c_int, [_P]),
+    "adg_plan": (C.c_int, [_P, _P, _P, C.POINTER(C.c_double), C.POINTER(C.c_int)]),
     "adg_query": (C.c_int, [_P, C.POINTER(adg_info)]),
     "adg_set_dofs": (C.c_int, [_P, _P]),
     "adg_get_dofs": (C.c_int, [_P, _P]),
@@ -189,6 +190,19 @@ def adg_upload_material(ctx, rho, lam, mu):
 
 def adg_init(ctx):
     _check(ctx, load().adg_init(ctx))
+
+
+def adg_plan(ctx):
+    """(dt_elem [nt], cluster [nt], dt_min, n_clusters) of the uploaded mesh,
+    computed on the host (no device needed)."""
+    nt = _NT.get(ctx.value)
+    if nt is None:
+        raise ValueError("plan: upload the mesh first")
+    dt = np.empty(nt, np.float64)
+    cl = np.empty(nt, np.int32)
+    dtmin, ncl = C.c_double(), C.c_int()
+    _check(ctx, load().adg_plan(ctx, _ptr(dt), _ptr(cl), C.byref(dtmin), C.byref(ncl)))
+    return dt, cl, dtmin.value, ncl.value
 
 
 def adg_query(ctx):

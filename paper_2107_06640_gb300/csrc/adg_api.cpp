@@ -206,6 +206,27 @@ int adg_init(adg_ctx* ctx) {
   });
 }
 
+int adg_plan(adg_ctx* ctx, double* dt_elem, int32_t* cluster, double* dt_min, int* n_clusters) {
+  if (!ctx) return ADG_E_INVALID;
+  return guard(ctx, [&] {
+    const Ctx& c = ctx->c;
+    if (!c.has_mesh || !c.has_mat) adg::throw_err(ADG_E_STATE, "upload mesh and material before adg_plan");
+    adg::RefOps local;
+    const adg::RefOps* o = &c.ops;
+    if (!c.inited) {
+      local = adg::make_ref_ops(c.cfg.degree);
+      o = &local;
+    }
+    adg::MeshPlan p;
+    c.plan_mesh(*o, c.cfg.degree, p);
+    if (dt_elem) std::copy(p.dte.begin(), p.dte.end(), dt_elem);
+    if (cluster)
+      for (int64_t e = 0; e < c.nt; ++e) cluster[e] = p.cl[e];
+    if (dt_min) *dt_min = p.dtmin;
+    if (n_clusters) *n_clusters = p.ncl;
+  });
+}
+
 int adg_query(const adg_ctx* ctx, adg_info* out) {
   if (!ctx || !out) return ADG_E_INVALID;
   const Ctx& c = ctx->c;

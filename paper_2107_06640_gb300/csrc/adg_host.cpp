@@ -201,20 +201,15 @@ static void* dalloc(size_t n, std::vector<void*>& owned, int64_t& bytes) {
   return d;
 }
 
-void Ctx::setup() {
-  if (!has_mesh || !has_mat) throw Err(ADG_E_STATE, "upload mesh and material before adg_init");
-  CK(cudaSetDevice(cfg.device));
+// Host-side plan of the mesh in the caller's element order: geometry, face
+// connectivity with node permutations, CFL time steps and rate-2 clusters
+// (Sec. 4.4).  Needs no device; adg_init and adg_plan both use it.
+void Ctx::plan_mesh(const RefOps& o, int N, MeshPlan& plan) const {
   const int64_t E = nt;
-  N = cfg.degree;
-  S = cfg.ensemble;
-  fp64 = cfg.precision == ADG_FP64;
-  tc = cfg.precision == ADG_3XTF32 && cfg.degree == 5;
-  ops = make_ref_ops(N);
-  if (ops.max_orth_err > 1e-12) throw Err(ADG_E_INVALID, "reference basis not orthonormal");
-  B = ops.B; Bf = ops.Bf; B1 = ops.B1;
-
   // ---- geometry (user order)
-  std::vector<double> Jinv(9 * E), detJ(E), area(4 * E), nrm(12 * E), fcen(12 * E), h(E);
+  plan.Jinv.assign(9 * E, 0.0); plan.detJ.assign(E, 0.0); plan.area.assign(4 * E, 0.0); plan.nrm.assign(12 * E, 0.0);
+  plan.fcen.assign(12 * E, 0.0); plan.h.assign(E, 0.0);
+  std::vector<double>&Jinv = plan.Jinv, &detJ = plan.detJ, &area = plan.area, &nrm = plan.nrm, &fcen = plan.fcen, &h = plan.h;
   for (int64_t e = 0; e < E; ++e) {
     const double* P[4];
     for (int k = 0; k < 4; ++k) {
@@ -268,8 +263,9 @@ void Ctx::setup() {
   }
 
   // ---- face connectivity: interior/fault by vertex triples, periodic by partner
-  std::vector<int64_t> nbr_u(4 * E, -1);
-  std::vector<int> nface_u(4 * E, -1), nperm_u(4 * E, -1);
+  plan.nbr.assign(4 * E, -1); plan.nface.assign(4 * E, -1); plan.nperm.assign(4 * E, -1);
+  std::vector<int64_t>& nbr_u = plan.nbr;
+  std::vector<int>&nface_u = plan.nface, &nperm_u = plan.nperm;
   {
     // match interior/fault faces by their sorted vertex triples: sort all
     // triples, then equal neighbours in the sorted list are the two sides
@@ -342,14 +338,16 @@ void Ctx::setup() {
         }
         int pid = -1;
         for (int p = 0; p < 6; ++p)
-          if (ops.vperm[3 * p] == sig[0] && ops.vperm[3 * p + 1] == sig[1] && ops.vperm[3 * p + 2] == sig[2]) pid = p;
+          if (o.vperm[3 * p] == sig[0] && o.vperm[3 * p + 1] == sig[1] && o.vperm[3 * p + 2] == sig[2]) pid = p;
         if (pid < 0) throw Err(ADG_E_MESH, "could not orient a face pair");
         nperm_u[4 * e + f] = pid;
       }
   }
 
   // ---- CFL time steps and rate-2 clusters (Sec. 4.4)
-  std::vector<double> dte(E);
+  plan.dte.assign(E, 0.0);
+  std::vector<double>& dte = plan.dte;
+  double& dtmin = plan.dtmin;
   dtmin = 1e300;
   for (int64_t e = 0; e < E; ++e) {
     double cp = std::sqrt((lam[e] + 2 * mu[e]) / rho[e]);
@@ -357,7 +355,8 @@ void Ctx::setup() {
     dte[e] = cfg.cfl / (2 * N + 1) * h[e] / cp;
     dtmin = std::min(dtmin, dte[e]);
   }
-  std::vector<int> cl(E);
+  plan.cl.assign(E, 0);
+  std::vector<int>& cl = plan.cl;
   const int cmaxcap = std::max(1, std::min(cfg.max_clusters, 16)) - 1;
   for (int64_t e = 0; e < E; ++e) {
     int c = (int)std::floor(std::log2(dte[e] / dtmin) + 1e-12);
@@ -373,8 +372,29 @@ void Ctx::setup() {
         if (cl[e] > lim) { cl[e] = lim; changed = true; }
       }
   }
-  ncl = 0;
-  for (int64_t e = 0; e < E; ++e) ncl = std::max(ncl, cl[e] + 1);
+  plan.ncl = 0;
+  for (int64_t e = 0; e < E; ++e) plan.ncl = std::max(plan.ncl, cl[e] + 1);
+}
+
+void Ctx::setup() {
+  if (!has_mesh || !has_mat) throw Err(ADG_E_STATE, "upload mesh and material before adg_init");
+  CK(cudaSetDevice(cfg.device));
+  const int64_t E = nt;
+  N = cfg.degree;
+  S = cfg.ensemble;
+  fp64 = cfg.precision == ADG_FP64;
+  tc = cfg.precision == ADG_3XTF32 && cfg.degree == 5;
+  ops = make_ref_ops(N);
+  if (ops.max_orth_err > 1e-12) throw Err(ADG_E_INVALID, "reference basis not orthonormal");
+  B = ops.B; Bf = ops.Bf; B1 = ops.B1;
+
+  MeshPlan pl;
+  plan_mesh(ops, N, pl);
+  const std::vector<double>&Jinv = pl.Jinv, &detJ = pl.detJ, &area = pl.area, &nrm = pl.nrm;
+  const std::vector<int64_t>& nbr_u = pl.nbr;
+  const std::vector<int>&nface_u = pl.nface, &nperm_u = pl.nperm, &cl = pl.cl;
+  dtmin = pl.dtmin;
+  ncl = pl.ncl;
   // ---- internal order: by cluster, stable; with the tensor-core kernels,
   // the elements of a cluster without gravitational face, fault face or
   // finer neighbour come first (those with a coarser neighbour, which the

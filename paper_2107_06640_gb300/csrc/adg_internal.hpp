@@ -35,6 +35,16 @@ int launch_scatter_dofs(int fp64, const void* in, const int64_t* idx, int64_t n,
 int launch_receivers(int fp64, int B, const void* Q, int S, int64_t n, const int64_t* elem,
                      const double* phi, double* out, void* stream);
 
+// Host-side plan of a mesh (caller's element order): geometry, face
+// connectivity, CFL time steps and rate-2 clusters (Sec. 4.4)
+struct MeshPlan {
+  std::vector<double> Jinv, detJ, area, nrm, fcen, h, dte;  // [E*9], [E], [E*4], [E*12], [E*12], [E], [E]
+  std::vector<int64_t> nbr;                                // [E*4] neighbour tet or -1
+  std::vector<int> nface, nperm, cl;                       // [E*4] its face, node permutation; [E] cluster
+  double dtmin = 0;
+  int ncl = 1;
+};
+
 struct Ctx {
   adg_config cfg{};
   std::string last_error;
@@ -125,6 +135,7 @@ struct Ctx {
   void record_after_macro();
   void record_free(int kind);
 
+  void plan_mesh(const RefOps& o, int N, MeshPlan& plan) const;
   void setup();
   StepArgs base_args() const;
   void launch_tick(int s, double dtm);

@@ -5,6 +5,23 @@ import numpy as np
 from . import _lib as L
 
 
+def plan(xyz, tets, face_tag, rho, lam, mu, face_partner=None, degree=5, cfl=0.35, max_clusters=1):
+    """The element time steps and rate-2 clusters a Solver on this mesh would
+    use, computed on the host without a device (adg_plan): returns
+    (dt_elem [nt], cluster [nt], dt_min, n_clusters)."""
+    cfg = L.adg_default_config()
+    cfg.degree = degree
+    cfg.cfl = cfl
+    cfg.max_clusters = max_clusters
+    ctx = L.adg_create(cfg)
+    try:
+        L.adg_upload_mesh(ctx, xyz, tets, face_tag, face_partner)
+        L.adg_upload_material(ctx, rho, lam, mu)
+        return L.adg_plan(ctx)
+    finally:
+        L.adg_destroy(ctx)
+
+
 class Solver:
     def __init__(self, xyz, tets, face_tag, rho, lam, mu, face_partner=None, degree=5,
                  precision=L.ADG_FP64, cfl=0.35, gravity=9.81, max_clusters=1, ensemble=1,
@@ -37,6 +54,10 @@ class Solver:
         if getattr(self, "ctx", None) is not None:
             L.adg_destroy(self.ctx)
             self.ctx = None
+
+    def plan(self):
+        """(dt_elem, cluster, dt_min, n_clusters) in the caller's element order."""
+        return L.adg_plan(self.ctx)
 
     def query(self):
         self.info = L.adg_query(self.ctx)

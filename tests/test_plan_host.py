@@ -1,0 +1,116 @@
+"""The library's host-side mesh plan (adg_plan, no device): the CFL time step
+and rate-2 cluster of every element (Sec. 4.4) equal the oracle's, on meshes
+with periodic faces, a fluid layer with a gravitational surface, a fault and
+randomly jittered nodes; cluster indices bit for bit."""
+
+import numpy as np
+import pytest
+
+import synthetic as syn
+from oracle.geometry import Geometry, cfl_dt, clusters
+from synthetic.mesh import kuhn_box
+from synthetic.workloads import coupled_box
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2107_06640_gb300 import build
+    build.build()
+
+
+def _warped_periodic(n, a):
+    phi = lambda u: u - a * np.sin(2 * np.pi * u) / (2 * np.pi)
+    g = np.linspace(0, 1, n + 1)
+    return syn.kuhn_box(g, g, g, tags={s: 4 for s in syn.mesh.SIDES}, warp=lambda x, ijk: phi(x))
+
+
+def _jittered(n, amp, seed):
+    rng = np.random.default_rng(seed)
+    g = np.linspace(0.0, 1.0, n + 1)
+
+    def warp(x, ijk):
+        inner = np.all((ijk > 0) & (ijk < n), axis=1)
+        x[inner] += rng.uniform(-amp, amp, (inner.sum(), 3)) / n
+        return x
+
+    return kuhn_box(g, g, g, warp=warp)
+
+
+def _fault_graded():
+    return kuhn_box(np.linspace(0, 4e3, 5), np.linspace(0, 2e3, 3), np.array([-2e3, -1.6e3, 0.0]),
+                    fault=dict(c=0, jrange=(0, 2), krange=(0, 2)))
+
+
+def _cases():
+    m = _warped_periodic(4, 0.95)
+    yield "periodic-warped", m, syn.elastic_uniform(m.nt), 3, 0.5, 3
+    m, mat = coupled_box(nxy=3, n_water=2, n_crust=3, L=6e3, depth=4e3, water=1.5e3, grading=1.6)
+    yield "ocean-gravity", m, mat, 5, 0.35, 4
+    m = _fault_graded()
+    g = np.random.default_rng(3)
+    mu = 3.2e10 * (1 + 0.2 * g.uniform(-1, 1, m.nt))
+    yield "fault", m, (2700.0 * (1 + 0.2 * g.uniform(-1, 1, m.nt)), mu * 1.1, mu), 4, 0.35, 2
+    for seed in range(2):
+        m = _jittered(4, 0.35, seed)
+        yield f"jittered-{seed}", m, syn.elastic_uniform(m.nt), 2, 0.5, 8
+
+
+@pytest.mark.parametrize("case", list(_cases()), ids=lambda c: c[0])
+def test_plan_equals_the_oracle(case):
+    from paper_2107_06640_gb300 import plan
+    name, m, (rho, lam, mu), N, cfl, mc = case
+    dt, cl, dtmin, ncl = plan(m.xyz, m.tets, m.face_tag, rho, lam, mu, face_partner=m.face_partner, degree=N,
+                              cfl=cfl, max_clusters=mc)
+    geo = Geometry(m.xyz, m.tets, m.face_tag, m.face_partner)
+    want_dt = cfl_dt(geo, rho, lam, mu, N, cfl)
+    want_cl, want_min = clusters(geo, want_dt, mc)
+    assert np.allclose(dt, want_dt, rtol=1e-14, atol=0)
+    assert dtmin == pytest.approx(want_min, rel=1e-14)
+    assert np.array_equal(cl, want_cl)
+    assert ncl == want_cl.max() + 1
+    if name in ("periodic-warped", "ocean-gravity"):
+        assert ncl >= 2
+
+
+def test_jittered_mesh_spans_several_clusters():
+    from paper_2107_06640_gb300 import plan
+    m = _jittered(4, 0.35, 0)
+    _, cl, _, ncl = plan(m.xyz, m.tets, m.face_tag, *syn.elastic_uniform(m.nt), degree=2, cfl=0.5, max_clusters=8)
+    assert ncl >= 3 and np.bincount(cl).min() > 0
+
+
+def test_plan_reports_mesh_and_material_errors():
+    from paper_2107_06640_gb300 import AdgError, _lib as L
+    m = _warped_periodic(2, 0.3)
+    rho, lam, mu = syn.elastic_uniform(m.nt)
+    ctx = L.adg_create(L.adg_default_config())
+    try:
+        L.adg_upload_mesh(ctx, m.xyz, m.tets, m.face_tag, m.face_partner)
+        with pytest.raises(AdgError) as ei:   # no material yet
+            L.adg_plan(ctx)
+        assert ei.value.code == -3
+        bad = mu.copy()
+        bad[5] = -1.0
+        L.adg_upload_material(ctx, rho, lam, bad)
+        with pytest.raises(AdgError) as ei:
+            L.adg_plan(ctx)
+        assert ei.value.code == -1
+    finally:
+        L.adg_destroy(ctx)
+    # an inverted tet, and an interior face without its neighbour
+    for mutate in ("invert", "unmatched"):
+        tets, tag = m.tets.copy(), m.face_tag.copy()
+        if mutate == "invert":
+            tets[7, [1, 2]] = tets[7, [2, 1]]
+            tag[7, [1, 2]] = tag[7, [2, 1]]
+        else:
+            tag = np.where(tag == 4, 0, tag)  # periodic faces declared interior: no matching face
+        ctx = L.adg_create(L.adg_default_config())
+        try:
+            L.adg_upload_mesh(ctx, m.xyz, tets, tag, m.face_partner)
+            L.adg_upload_material(ctx, rho, lam, mu)
+            with pytest.raises(AdgError) as ei:
+                L.adg_plan(ctx)
+            assert ei.value.code == -2, mutate
+        finally:
+            L.adg_destroy(ctx)
