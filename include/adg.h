@@ -107,7 +107,8 @@ int adg_create(const adg_config* cfg, adg_ctx** out);
  * xyz[3*nv] vertex coordinates; tet_v[4*nt] vertex indices;
  * face_tag[4*nt] ADG_TAG_* per local face; face_partner[4*nt] = t*4+f of the
  * paired face for ADG_TAG_PERIODIC faces (ignored otherwise) or NULL when no
- * face is periodic.  Validation (orientation, matching) happens in adg_init. */
+ * face is periodic.  Validation (orientation, matching) happens in adg_init
+ * and adg_plan. */
 int adg_upload_mesh(adg_ctx* ctx, int64_t nv, const double* xyz, int64_t nt,
                     const int64_t* tet_v, const int32_t* face_tag, const int64_t* face_partner);
 
@@ -128,8 +129,11 @@ int adg_init(adg_ctx* ctx);
  * The element steps 2^c_e dt_min; a macro step is 2^(n_clusters-1) dt_min.
  * dt_elem[nt] (seconds), cluster[nt], dt_min[1], n_clusters[1]: caller-owned
  * outputs, each may be NULL.  Errors: ADG_E_STATE before both uploads;
- * ADG_E_MESH for an inverted tet, an unmatched interior face or a bad periodic
- * partner; ADG_E_INVALID for a bad material.  Nothing is written on error. */
+ * ADG_E_MESH for the mesh faults adg_init reports (an inverted tet, a vertex
+ * index or face tag out of range, an interior face without its neighbour, a
+ * fault tagged on one side only, a bad periodic partner); ADG_E_INVALID for a
+ * bad material (rho <= 0, mu < 0, c_p not positive).  Nothing is written on
+ * error. */
 int adg_plan(adg_ctx* ctx, double* dt_elem, int32_t* cluster, double* dt_min, int* n_clusters);
 
 int adg_query(const adg_ctx* ctx, adg_info* out);
