@@ -329,7 +329,12 @@ int adg_mlp_params(adg_ctx* ctx, const float* set, float* get, int enable);
 int adg_mlp_gradient(const float* params, int64_t n, const float* rows, float* grad, double* loss);
 
 /* Checkpoint: dofs, eta, fault state and time at a macro-step boundary.
- * adg_save_state with buf == NULL returns the size in *len. */
+ * adg_save_state with buf == NULL returns the size in *len; a buffer smaller
+ * than that is ADG_E_INVALID, a call inside a macro step ADG_E_STATE.
+ * adg_load_state takes a buffer saved by a context with the same degree,
+ * ensemble, tet count, precision and gravitational faces (else ADG_E_INVALID);
+ * a fault state needs adg_set_fault first (else ADG_E_STATE).  The buffer is
+ * a host array owned by the caller. */
 int adg_save_state(adg_ctx* ctx, void* buf, size_t* len);
 int adg_load_state(adg_ctx* ctx, const void* buf, size_t len);
 
