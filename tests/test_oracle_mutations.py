@@ -1,0 +1,116 @@
+"""The pins catch plausible mistakes: each case plants one mistake in an
+oracle module (a source replacement, executed in a child process on the CPU;
+nothing on disk changes) and runs the pins that cover that part of the
+oracle, which must then fail.  The unmutated pins pass in the rest of the
+suite."""
+
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+# (id, oracle file, original text, planted text, pin tests (file, -k expression))
+CASES = [
+    ("absorbing-transparent", "physics.py",
+     "if tag == 3:      # absorbing: q+ = 0\n        wp[...] = 0.0",
+     "if tag == 3:      # absorbing: q+ = 0\n        wp[...] = wm",
+     ("test_oracle_physics.py", "absorbing")),
+    ("rigid-mirrors-traction", "physics.py",
+     "elif tag == 6:    # rigid wall, free slip\n        wp[..., [6, 3, 5]] *= -1.0",
+     "elif tag == 6:    # rigid wall, free slip\n        wp[..., [0, 3, 5]] *= -1.0",
+     ("test_oracle_physics.py", "wall_middle")),
+    ("free-surface-keeps-shear", "physics.py",
+     "elif tag == 1:    # free surface: traction mirrored\n        wp[..., [0, 3, 5]] *= -1.0",
+     "elif tag == 1:    # free surface: traction mirrored\n        wp[..., [0]] *= -1.0",
+     ("test_oracle_physics.py", "wall_middle")),
+    ("lts-coarse-subinterval-from-start", "ader.py",
+     "ta = t_start - self._t0[nbc]", "ta = 0.0 * self._t0[nbc]",
+     ("test_oracle_scheme.py", "conserves")),
+    ("lts-fine-neighbour-last-integral", "ader.py",
+     "out[fine] = self._buf[nb[fine]]", "out[fine] = self._Iown[nb[fine]]",
+     ("test_oracle_scheme.py", "conserves")),
+    ("lts-buffer-never-reset", "ader.py",
+     "self._buf[idx] = 0.0", "self._buf[idx] = self._buf[idx]",
+     ("test_oracle_scheme.py", "conserves")),
+    ("fault-plus-side-scaled-by-minus-volume", "ader.py",
+     "scale = 2.0 * self.f_area[fi] / self.geo.detJ[e]", "scale = 2.0 * self.f_area[fi] / self.geo.detJ[em[i]]",
+     ("test_oracle_rupture_lsw.py", "locked_fault_in")),
+    ("fault-taylor-factor", "ader.py",
+     "c = t ** k / factorial(k)\n", "c = t ** k / factorial(k + 1)\n",
+     ("test_oracle_rupture_lsw.py", "locked_fault_in")),
+    ("fault-lts-step-length", "ader.py",
+     "for e, d in self.fault_update(sel, self._D, (1 << cl) * dtm, self.fault_guess).items():",
+     "for e, d in self.fault_update(sel, self._D, dtm, self.fault_guess).items():",
+     ("test_oracle_rupture_lsw.py", "locked_fault_in")),
+    ("energy-poisson-term", "ader.py",
+     "pot_s = 0.5 * (sq / (2 * ms) - lam / (2 * ms * (3 * lam + 2 * ms)) * trtr)",
+     "pot_s = 0.5 * (sq / (2 * ms) - lam / (ms * (3 * lam + 2 * ms)) * trtr)",
+     ("test_oracle_scheme.py", "energy_is")),
+    ("energy-surface-term", "ader.py",
+     "E += 0.5 * rho[e] * self.g * 2 * self.geo.area[e, f]", "E += 0.5 * rho[e] * self.g * self.geo.area[e, f]",
+     ("test_oracle_scheme.py", "energy_is")),
+    ("projection-transposed-map", "ader.py",
+     'x = self.geo.x0[:, None, :] + np.einsum("eda,qa->eqd", self.geo.J, pts)\n        vals',
+     'x = self.geo.x0[:, None, :] + np.einsum("ead,qa->eqd", self.geo.J, pts)\n        vals',
+     ("test_oracle_scheme.py", "polynomial")),
+    ("cfl-length-halved", "geometry.py",
+     "self.h = 6.0 * self.volume / self.area.sum(axis=1)", "self.h = 3.0 * self.volume / self.area.sum(axis=1)",
+     ("test_oracle_geometry.py", "")),
+    ("clusters-ignore-faults", "geometry.py",
+     "lim = np.where(tag == 5, cn, cn + 1)", "lim = cn + 1",
+     ("test_oracle_geometry.py", "clusters")),
+    ("clusters-round-up", "geometry.py",
+     "c = np.floor(np.log2(dt / dtmin) + 1e-12).astype(np.int64)",
+     "c = np.ceil(np.log2(dt / dtmin) - 1e-12).astype(np.int64)",
+     ("test_oracle_geometry.py", "clusters")),
+    ("periodic-shift-sign", "geometry.py",
+     "self.shift[e, f] = self.face_centroid[p // 4, p % 4] - self.face_centroid[e, f]",
+     "self.shift[e, f] = self.face_centroid[e, f] - self.face_centroid[p // 4, p % 4]",
+     ("test_oracle_geometry.py", "neighbours")),
+    ("inverse-map-transposed", "geometry.py",
+     'np.einsum("...ad,...d->...a", self.Jinv[e], x - self.x0[e])',
+     'np.einsum("...da,...d->...a", self.Jinv[e], x - self.x0[e])',
+     ("test_oracle_scheme.py", "polynomial")),
+    ("rs-no-tail", "rupture.py",
+     'psi = psi + V * (dt - tprev) if law == "lsw" else psi_relax(psi, V, dt - tprev, par)',
+     'psi = psi + V * (dt - tprev) if law == "lsw" else psi',
+     ("test_oracle_rupture.py", "constant_load")),
+    ("rs-interval-from-step-start", "rupture.py",
+     "        h = tj[j] - tprev\n", "        h = tj[j]\n",
+     ("test_oracle_rupture.py", "constant_load")),
+]
+
+_CHILD = """
+import importlib, sys, traceback
+try:
+    sys.path.insert(0, {root!r})
+    mod = importlib.import_module("oracle." + {stem!r})
+    path = {path!r}
+    src = open(path).read()
+    if src.count({old!r}) != 1:
+        raise RuntimeError("the original text is not unique in " + path)
+    exec(compile(src.replace({old!r}, {new!r}), path, "exec"), mod.__dict__)
+except Exception:
+    traceback.print_exc()
+    sys.exit(3)  # the mistake could not be planted: distinct from a failing pin
+import pytest
+args = ["-q", "-x", "-p", "no:cacheprovider", {test!r}]
+if {sel!r}:
+    args += ["-k", {sel!r}]
+sys.exit(pytest.main(args))
+"""
+
+
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_planted_mistake_fails_its_pins(case):
+    name, fname, old, new, (tfile, sel) = case
+    path = os.path.join(ROOT, "oracle", fname)
+    code = _CHILD.format(root=ROOT, stem=fname[:-3], path=path, old=old, new=new,
+                         test=os.path.join(ROOT, "tests", tfile), sel=sel)
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=600)
+    # pytest exit code 1: tests ran and some failed (not 2/4/5: interrupted, usage error, nothing collected;
+    # 3: the mistake could not be planted)
+    assert r.returncode == 1, f"{name}: pins did not fail (exit {r.returncode})\n{r.stdout[-2000:]}{r.stderr[-2000:]}"
