@@ -81,6 +81,58 @@ CASES = [
     ("rs-interval-from-step-start", "rupture.py",
      "        h = tj[j] - tprev\n", "        h = tj[j]\n",
      ("test_oracle_rupture.py", "constant_load")),
+    ("basis-jacobi-parameter", "basis.py",
+     "f2, f2y, f2t = _G(j, 2 * i + 1, eta, t)", "f2, f2y, f2t = _G(j, 2 * i, eta, t)",
+     ("test_oracle_basis.py", "orthonormal")),
+    ("basis-gradient-sign", "basis.py",
+     "grad[:, l, 1] = -f1s * f2 * f3 + f1 * f2y * f3", "grad[:, l, 1] = f1s * f2 * f3 + f1 * f2y * f3",
+     ("test_oracle_basis.py", "gradient")),
+    ("stiffness-transposed", "basis.py",
+     'return np.einsum("q,qke,ql->ekl", w, g, v)', 'return np.einsum("q,qke,ql->elk", w, g, v)',
+     ("test_oracle_basis.py", "stiffness")),
+    ("face-vertex-list", "basis.py",
+     "FACE_VERTS = ((1, 2, 3), (0, 2, 3), (0, 1, 3), (0, 1, 2))",
+     "FACE_VERTS = ((1, 2, 3), (0, 2, 3), (0, 1, 2), (0, 1, 3))",
+     ("test_oracle_basis.py", "face_maps")),
+    ("tet-rule-collapse-weight", "quadrature.py",
+     "wt = wu * wv * ws * (1 - v) * (1 - s) ** 2", "wt = wu * wv * ws * (1 - v) * (1 - s)",
+     ("test_oracle_basis.py", "quadrature")),
+    ("tet-rule-too-few-points", "quadrature.py",
+     "n = max(1, int(np.ceil((degree + 3) / 2.0)))", "n = max(1, int(np.ceil((degree + 1) / 2.0)))",
+     ("test_oracle_basis.py", "quadrature")),
+    ("jacobian-normal-stress-mu", "physics.py",
+     "M[..., S[(d, d)], 6 + d] -= 2 * mu", "M[..., S[(d, d)], 6 + d] -= mu",
+     ("test_oracle_physics.py", "eigenvalues")),
+    ("middle-state-impedance", "physics.py",
+     "a1 = Zpm * Zpp / (Zpm + Zpp) * ((wm[..., 0:1] - wp[..., 0:1]) / Zpp",
+     "a1 = Zpm * Zpp / (Zpm + Zpp) * ((wm[..., 0:1] - wp[..., 0:1]) / Zpm",
+     ("test_oracle_physics.py", "both_sides")),
+    ("middle-state-shear-impedance", "physics.py",
+     "a = Zsm * Zsp / (Zsm + Zsp) * ((wm[..., ts:ts + 1] - wp[..., ts:ts + 1]) / Zsp",
+     "a = Zsm * Zsp / (Zsm + Zsp) * ((wm[..., ts:ts + 1] - wp[..., ts:ts + 1]) / Zsm",
+     ("test_oracle_physics.py", "both_sides")),
+    ("gravity-ode-H-series", "physics.py",
+     "H = H + term * dt / (m + 2)", "H = H + term * dt / (m + 1)",
+     ("test_oracle_physics.py", "gravity_ode")),
+    ("friction-2V0", "rupture.py",
+     'return a * np.arcsinh(V / (2.0 * p["V0"]) * np.exp(psi / a))',
+     'return a * np.arcsinh(V / p["V0"] * np.exp(psi / a))',
+     ("test_oracle_rupture.py", "steady_state")),
+    ("locked-traction-impedances-swapped", "rupture.py",
+     "theta = eta[..., None] * ((up - um) + taup / Zsp[..., None] + taum / Zsm[..., None])",
+     "theta = eta[..., None] * ((up - um) + taup / Zsm[..., None] + taum / Zsp[..., None])",
+     ("test_oracle_rupture.py", "locked_fault_is")),
+    ("side-velocity-sign", "rupture.py",
+     'ub = st["um"] + (tau_p - st["taum"]) / st["Zsm"][..., None]',
+     'ub = st["um"] - (tau_p - st["taum"]) / st["Zsm"][..., None]',
+     ("test_oracle_rupture.py", "locked_fault_is or slipping")),
+    ("gauss-time-weights", "rupture.py",
+     "return 0.5 * dt * (x + 1.0), 0.5 * dt * w", "return 0.5 * dt * (x + 1.0), dt * w",
+     ("test_oracle_rupture_lsw.py", "locked_fault_in")),
+    ("mlp-tanh-derivative", "mlp.py",
+     "da2 = (dy[:, None] * p[\"w3\"][None, :]) * (1.0 - h2 * h2)",
+     "da2 = (dy[:, None] * p[\"w3\"][None, :]) * (1.0 - h2)",
+     ("test_oracle_mlp.py", "gradient")),
 ]
 
 _CHILD = """

@@ -137,6 +137,43 @@ def test_middle_state_obeys_rankine_hugoniot():
     assert wb[3] == 0 and wb[5] == 0
 
 
+@pytest.mark.parametrize("matp", [(2000.0, 1.2e10, 0.8e10), (1000.0, 2.25e9, 0.0)])
+def test_middle_states_of_both_sides_meet_the_interface_conditions(matp):
+    """The Godunov middle state is the exact Riemann solution at the interface
+    (Sec. 4.2), so the states each side computes for the same face (its own
+    frame, normal n and -n) satisfy the interface conditions: a welded
+    solid-solid contact has one traction sigma.n and one velocity; at a
+    solid-fluid contact the normal traction and normal velocity agree and
+    neither side carries shear traction."""
+    matm = (2700.0, 3.24e10, 3.24e10)
+    Zpm, Zsm = ph.impedances(*matm)
+    Zpp, Zsp = ph.impedances(*matp)
+    fluid = matp[2] == 0.0
+    for _ in range(5):
+        n = _unit(rng.standard_normal(3))
+        qm = rng.standard_normal(9) * np.array([1e6] * 6 + [1.0] * 3)
+        qp = rng.standard_normal(9) * np.array([1e6] * 6 + [1.0] * 3)
+        if fluid:
+            qp[:3] = qp[0]
+            qp[3:6] = 0.0
+        R, Rn = ph.frame(n), ph.frame(-n)
+        bm = ph.rotate_out(ph.middle_state(ph.rotate_in(qm, R), ph.rotate_in(qp, R), Zpm, Zpp, Zsm, Zsp), R)
+        bp = ph.rotate_out(ph.middle_state(ph.rotate_in(qp, Rn), ph.rotate_in(qm, Rn), Zpp, Zpm, Zsp, Zsm), Rn)
+
+        def traction(q):
+            S = np.array([[q[0], q[3], q[5]], [q[3], q[1], q[4]], [q[5], q[4], q[2]]])
+            return S @ n
+
+        tm, tp = traction(bm), traction(bp)
+        ts = 1e-12 * 1e6
+        vs = 1e-12
+        if fluid:
+            assert abs(tm @ n - tp @ n) <= ts and abs(bm[6:] @ n - bp[6:] @ n) <= vs
+            assert np.allclose(tm - (tm @ n) * n, 0.0, atol=ts) and np.allclose(tp - (tp @ n) * n, 0.0, atol=ts)
+        else:
+            assert np.allclose(tm, tp, rtol=0, atol=ts) and np.allclose(bm[6:], bp[6:], rtol=0, atol=vs)
+
+
 def test_gravity_ghost_reproduces_boundary_state():
     # Eq. (free-surface-boundary-state): v_n^b = v_n^- - (rho g eta - p^-)/Z, p^b = rho g eta
     rho, K, g, eta = 1000.0, 2.25e9, 9.81, 0.37
