@@ -133,6 +133,78 @@ CASES = [
      "da2 = (dy[:, None] * p[\"w3\"][None, :]) * (1.0 - h2 * h2)",
      "da2 = (dy[:, None] * p[\"w3\"][None, :]) * (1.0 - h2)",
      ("test_oracle_mlp.py", "gradient")),
+    ('predictor-sign', 'ader.py',
+     'D.append(-np.sum(np.matmul(np.matmul(KT, D[-1][None]), sT), axis=0))',
+     'D.append(np.sum(np.matmul(np.matmul(KT, D[-1][None]), sT), axis=0))',
+     ('test_oracle_scheme.py', 'convergence_order')),
+    ('time-integral-factorial', 'ader.py',
+     'c = (tb ** (k + 1) - ta ** (k + 1)) / factorial(k + 1)',
+     'c = (tb ** (k + 1) - ta ** (k + 1)) / factorial(k)',
+     ('test_oracle_scheme.py', 'convergence_order')),
+    ('volume-operator-transposed', 'ader.py',
+     'return np.sum(np.matmul(np.matmul(self.Kxi[:, None], I[None]), sT), axis=0)',
+     'return np.sum(np.matmul(np.matmul(self.Kxi.transpose(0, 2, 1)[:, None], I[None]), sT), axis=0)',
+     ('test_oracle_scheme.py', 'convergence_order')),
+    ('face-scale-factor-2', 'ader.py',
+     'scale = 2.0 * geo.area[idx, f] / geo.detJ[idx]',
+     'scale = geo.area[idx, f] / geo.detJ[idx]',
+     ('test_oracle_scheme.py', 'convergence_order')),
+    ('periodic-neighbour-shift-sign', 'ader.py',
+     'xs = x[has] + geo.shift[has, f][:, None, :]',
+     'xs = x[has] - geo.shift[has, f][:, None, :]',
+     ('test_oracle_scheme.py', 'convergence_order')),
+    ('gravity-eta-increment', 'ader.py',
+     'wb[..., 6] = eta1 - eta0',
+     'wb[..., 6] = eta1',
+     ('test_oracle_scheme.py', 'surface_gravity_wave_dispersion')),
+    ('gravity-kappa', 'ader.py',
+     'kappa = rho * self.g / Z',
+     'kappa = rho * self.g * Z',
+     ('test_oracle_scheme.py', 'surface_gravity_wave_dispersion')),
+    ('gravity-forcing-sign', 'ader.py',
+     'fc.append((wmm[..., 6] - wmm[..., 0] / Z[:, None]) / factorial(m))',
+     'fc.append((wmm[..., 6] + wmm[..., 0] / Z[:, None]) / factorial(m))',
+     ('test_oracle_scheme.py', 'surface_gravity_wave_dispersion')),
+    ('rotation-transposed', 'physics.py',
+     'Sr = np.einsum("...ji,...jk,...kl->...il", R, S, R, optimize=True)',
+     'Sr = np.einsum("...ij,...jk,...lk->...il", R, S, R, optimize=True)',
+     ('test_oracle_physics.py', 'rotation')),
+    ('flux-wrong-direction', 'physics.py',
+     'A = jacobians(rho, lam, mu)[..., 0, :, :]',
+     'A = jacobians(rho, lam, mu)[..., 1, :, :]',
+     ('test_oracle_scheme.py', 'convergence_order')),
+    ('gravity-ghost-pressure-sign', 'physics.py',
+     'wp[..., 0] = -(2.0 * rho * g * eta - pm)',
+     'wp[..., 0] = (2.0 * rho * g * eta - pm)',
+     ('test_oracle_physics.py', 'gravity_ghost')),
+    ('strength-sign', 'rupture.py',
+     'S=np.maximum(0.0, -(sn0 + sn_b)))',
+     'S=np.maximum(0.0, -(sn0 - sn_b)))',
+     ('test_oracle_rupture_lsw.py', 'normal_stress')),
+    ('lsw-min-max', 'rupture.py',
+     'np.minimum(psi / p["Dc"], 1.0)',
+     'np.maximum(psi / p["Dc"], 1.0)',
+     ('test_oracle_rupture_lsw.py', 'coefficient')),
+    ('state-relaxation-sign', 'rupture.py',
+     'return ss + (psi - ss) * np.exp(-V * h / p["L"])',
+     'return ss + (psi - ss) * np.exp(V * h / p["L"])',
+     ('test_oracle_rupture.py', 'relaxation')),
+    ('basis-norm', 'basis.py',
+     'return 1.0 / np.sqrt(np.einsum("q,ql,ql->l", w, v, v))',
+     'return 1.0 / np.einsum("q,ql,ql->l", w, v, v)',
+     ('test_oracle_basis.py', 'orthonormal')),
+    ('tri-rule-weight', 'quadrature.py',
+     'wt = wu * wv * (1 - v)\n',
+     'wt = wu * wv\n',
+     ('test_oracle_basis.py', '')),
+    ('inverse-map-transposed-matrix', 'geometry.py',
+     'self.Jinv = np.linalg.inv(self.J)',
+     'self.Jinv = np.linalg.inv(self.J).transpose(0, 2, 1)',
+     ('test_oracle_scheme.py', 'polynomial')),
+    ('normal-orientation', 'geometry.py',
+     'sgn = np.sign(np.einsum("ij,ij->i", n, a - opp))',
+     'sgn = np.ones(n.shape[0])',
+     ('test_oracle_geometry.py', '')),
 ]
 
 _CHILD = """

@@ -165,3 +165,32 @@ def test_locked_fault_in_the_scheme_equals_welded_interior_faces(N, zs, lts):
         sc = np.abs(welded.Q[..., p]).max()
         assert np.max(np.abs(fault.Q[..., p] - welded.Q[..., p])) <= 1e-11 * sc, p
     assert not np.allclose(welded.Q, Q0)
+
+
+@pytest.mark.parametrize("dP", [5e6, -5e6])
+def test_normal_stress_change_moves_the_strength(dP):
+    """The strength acts on the total normal stress (Eq. bc-dynrup: S from the
+    background sigma_n0 plus the dynamic normal stress of the middle state).
+    Both sides carry an extra isotropic stress -dP I, which puts no shear on
+    the fault (Theta = |tau0| stays 27 MPa) and makes the welded normal stress
+    -dP: extra compression (dP > 0) raises the static strength
+    C + mu_s (40 MPa + dP) above Theta and the fault stays locked; extra
+    tension lowers it and the fault slides with the traction at the strength
+    C + f(psi) (40 MPa + dP)."""
+    Th, S0, C = 27e6, 40e6, 2e6
+    N, dt = 3, 2e-3
+    n = np.tile([0.0, 0.0, 1.0], (1, 1))
+    q = np.zeros((N + 1, 1, 9))
+    q[..., :3] = -dP
+    mat = tuple(np.full(1, v) for v in (RHO, LAM, MU))
+    par = _par(1, C=C, sn0=-S0, tau=Th)
+    Gm, Gp, psi, V, dslip, iters, tau = ru.solve_step(n, q, q, mat, mat, par, dt, N, law="lsw")
+    S = S0 + dP
+    if dP > 0:
+        assert V[0] == 0 and psi[0] == 0 and np.allclose(tau[0], [Th, 0, 0], rtol=1e-15)
+    else:
+        assert V[0] > 0 and psi[0] > 0
+        tj, _ = ru.time_points(N, dt)
+        psi_last = psi[0] - V[0] * (dt - tj[-1])
+        want = C + ru.lsw_friction(np.array([psi_last]), dict(mu_s=0.6, mu_d=0.4, Dc=0.5))[0] * S
+        assert np.linalg.norm(tau[0]) == pytest.approx(want, rel=1e-12)
