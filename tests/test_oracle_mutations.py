@@ -256,13 +256,28 @@ sys.exit(pytest.main(args))
 """
 
 
-@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
-def test_planted_mistake_fails_its_pins(case):
+def _run(case):
     name, fname, old, new, (tfile, sel) = case
     path = os.path.join(ROOT, "oracle", fname)
     code = _CHILD.format(root=ROOT, stem=fname[:-3], path=path, old=old, new=new,
                          test=os.path.join(ROOT, "tests", tfile), sel=sel)
-    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=600)
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    return subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=900,
+                          env=env)
+
+
+@pytest.fixture(scope="module")
+def results():
+    """All children at once (independent processes, single-threaded BLAS)."""
+    from concurrent.futures import ThreadPoolExecutor
+    with ThreadPoolExecutor(max_workers=max(1, min(8, os.cpu_count() or 1))) as ex:
+        return dict(zip((c[0] for c in CASES), ex.map(_run, CASES)))
+
+
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_planted_mistake_fails_its_pins(case, results):
+    name = case[0]
+    r = results[name]
     # pytest exit code 1: tests ran and some failed (not 2/4/5: interrupted, usage error, nothing collected;
     # 3: the mistake could not be planted)
     assert r.returncode == 1, f"{name}: pins did not fail (exit {r.returncode})\n{r.stdout[-2000:]}{r.stderr[-2000:]}"
