@@ -233,6 +233,26 @@ CASES = [
      'self._buf[idx] += Iown',
      'self._buf[idx] = Iown',
      ('test_oracle_scheme.py', 'conserves')),
+    ('subinterval-integral-of-difference', 'ader.py',
+     'c = (tb ** (k + 1) - ta ** (k + 1)) / factorial(k + 1)',
+     'c = (tb - ta) ** (k + 1) / factorial(k + 1)',
+     ('test_oracle_scheme.py', 'conserves')),
+    ('lts-predictor-start-time', 'ader.py',
+     'self._t0[idx] = tick_t',
+     'self._t0[idx] = 0.0',
+     ('test_oracle_scheme.py', 'conserves')),
+    ('lts-buffer-reset-every-step', 'ader.py',
+     'if s % (1 << (cl + 1)) == 0:',
+     'if s % (1 << cl) == 0:',
+     ('test_oracle_scheme.py', 'conserves')),
+    ('macro-scale-ignored', 'ader.py',
+     'dtm = self.dtmin * scale',
+     'dtm = self.dtmin',
+     ('test_oracle_scheme.py', 'gravity_wave_with_lts')),
+    ('neighbour-basis-through-own-map', 'ader.py',
+     'xin = np.einsum("ead,eqd->eqa", geo.Jinv[nb[has]], xs - geo.x0[nb[has]][:, None, :])',
+     'xin = np.einsum("ead,eqd->eqa", geo.Jinv[has], xs - geo.x0[has][:, None, :])',
+     ('test_oracle_scheme.py', 'convergence_order')),
 ]
 
 _CHILD = """
