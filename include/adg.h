@@ -136,6 +136,19 @@ int adg_init(adg_ctx* ctx);
  * error. */
 int adg_plan(adg_ctx* ctx, double* dt_elem, int32_t* cluster, double* dt_min, int* n_clusters);
 
+/* Host-only: the Godunov flux matrices adg_init builds for local face `face`
+ * of user tet `tet` (Sec. 4.2, Eq. numerical-flux), global frame, row-major
+ * 9x9, caller-owned Fm[81], Fp[81] (either may be NULL).  The flux T A^- w^b
+ * through the face is Fm q^- + Fp q^+ for interior and periodic faces (q^+ the
+ * neighbour's state at the same point) and Fm q^- for free-surface, rigid-wall
+ * and absorbing faces (Fp zero); both are zero for gravitational and fault
+ * faces, whose fluxes come from the (eta, H) ODE and the friction solve.  The
+ * element update subtracts 2|S_f|/|J| times the face integral of the flux
+ * against the basis.  No device needed; call after both uploads.  It plans
+ * the mesh on every call (meant for inspection and tests).  Errors:
+ * ADG_E_INVALID for tet or face out of range; otherwise as adg_plan. */
+int adg_face_flux(adg_ctx* ctx, int64_t tet, int face, double* Fm, double* Fp);
+
 int adg_query(const adg_ctx* ctx, adg_info* out);
 
 /* Dofs in user tet order, layout [nt][S][9][B] (host, double). */

@@ -51,6 +51,7 @@ _SIGS = {
     "adg_upload_material": (C.c_int, [_P, _P, _P, _P]),
     "adg_init": (C.c_int, [_P]),
     "adg_plan": (C.c_int, [_P, _P, _P, C.POINTER(C.c_double), C.POINTER(C.c_int)]),
+    "adg_face_flux": (C.c_int, [_P, C.c_int64, C.c_int, _P, _P]),
     "adg_query": (C.c_int, [_P, C.POINTER(adg_info)]),
     "adg_set_dofs": (C.c_int, [_P, _P]),
     "adg_get_dofs": (C.c_int, [_P, _P]),
@@ -203,6 +204,14 @@ def adg_plan(ctx):
     dtmin, ncl = C.c_double(), C.c_int()
     _check(ctx, load().adg_plan(ctx, _ptr(dt), _ptr(cl), C.byref(dtmin), C.byref(ncl)))
     return dt, cl, dtmin.value, ncl.value
+
+
+def adg_face_flux(ctx, tet, face):
+    """(Fm, Fp), each [9][9], of local face `face` of user tet `tet` (host only)."""
+    Fm = np.empty((9, 9), np.float64)
+    Fp = np.empty((9, 9), np.float64)
+    _check(ctx, load().adg_face_flux(ctx, int(tet), int(face), _ptr(Fm), _ptr(Fp)))
+    return Fm, Fp
 
 
 def adg_query(ctx):

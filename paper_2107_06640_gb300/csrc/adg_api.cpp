@@ -227,6 +227,24 @@ int adg_plan(adg_ctx* ctx, double* dt_elem, int32_t* cluster, double* dt_min, in
   });
 }
 
+int adg_face_flux(adg_ctx* ctx, int64_t tet, int face, double* Fm, double* Fp) {
+  if (!ctx) return ADG_E_INVALID;
+  return guard(ctx, [&] {
+    const Ctx& c = ctx->c;
+    if (!c.has_mesh || !c.has_mat) adg::throw_err(ADG_E_STATE, "upload mesh and material before adg_face_flux");
+    if (tet < 0 || tet >= c.nt || face < 0 || face > 3) adg::throw_err(ADG_E_INVALID, "tet or face out of range");
+    adg::RefOps local;
+    const adg::RefOps* o = &c.ops;
+    if (!c.inited) {
+      local = adg::make_ref_ops(c.cfg.degree);
+      o = &local;
+    }
+    adg::MeshPlan p;
+    c.plan_mesh(*o, c.cfg.degree, p);
+    c.face_flux(p, tet, face, Fm, Fp);
+  });
+}
+
 int adg_query(const adg_ctx* ctx, adg_info* out) {
   if (!ctx || !out) return ADG_E_INVALID;
   const Ctx& c = ctx->c;

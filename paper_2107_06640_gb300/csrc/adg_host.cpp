@@ -144,6 +144,28 @@ M9 diag9(std::initializer_list<double> d) {
   return r;
 }
 
+// Godunov flux matrices of a face in the global frame (Sec. 4.2, Eq.
+// numerical-flux): with TA = T A^- and Ti = T^-1 for the face's normal, the
+// flux T A^- w^b, w^b = Mm T^-1 q^- + Mp T^-1 q^+, is Fm q^- + Fp q^+.
+void godunov_pair(const M9& TA, const M9& Ti, double Zpm, double Zpp, double Zsm, double Zsp, M9& Fm, M9& Fp) {
+  M9 Mm, Mp;
+  middle_state(Zpm, Zpp, Zsm, Zsp, Mm, Mp);
+  Fm = mm(mm(TA, Mm), Ti);
+  Fp = mm(mm(TA, Mp), Ti);
+}
+
+// Linear boundaries (Sec. 4.3): the ghost state w^+ = G w^- (free surface:
+// traction w1, w4, w6 mirrored; rigid wall: w7, w4, w6 mirrored; absorbing:
+// G = 0) with the minus material folds into Fm = T A^- (Mm + Mp G) T^-1.
+M9 boundary_matrix(const M9& TA, const M9& Ti, double Zp, double Zs, int tag) {
+  M9 Mm, Mp;
+  middle_state(Zp, Zp, Zs, Zs, Mm, Mp);
+  M9 G{};
+  if (tag == ADG_TAG_FREE) G = diag9({-1, 1, 1, -1, 1, -1, 1, 1, 1});
+  else if (tag == ADG_TAG_RIGID) G = diag9({1, 1, 1, -1, 1, -1, -1, 1, 1});
+  return mm(mm(TA, madd(Mm, mm(Mp, G))), Ti);
+}
+
 // ---------------- Gauss-Legendre on [0,1] (Newton on P_n) ----------------
 void gauss01(int n, std::vector<double>& x, std::vector<double>& w) {
   x.resize(n);
@@ -376,6 +398,28 @@ void Ctx::plan_mesh(const RefOps& o, int N, MeshPlan& plan) const {
   for (int64_t e = 0; e < E; ++e) plan.ncl = std::max(plan.ncl, cl[e] + 1);
 }
 
+// The flux matrices setup() builds for face f of user tet eu (global frame,
+// row-major): interior and periodic faces Fm, Fp; free, rigid and absorbing
+// faces Fm (Fp zero); gravitational and fault faces zero (their fluxes come
+// from the (eta, H) ODE and the friction solve).
+void Ctx::face_flux(const MeshPlan& pl, int64_t eu, int f, double* Fm, double* Fp) const {
+  M9 FmM{}, FpM{};
+  const int tg = tag[4 * eu + f];
+  const double Zpm = std::sqrt(rho[eu] * (lam[eu] + 2 * mu[eu])), Zsm = std::sqrt(rho[eu] * mu[eu]);
+  M9 T, Ti;
+  rot_mats(&pl.nrm[12 * eu + 3 * f], T, Ti);
+  const M9 TA = mm(T, jac_x(rho[eu], lam[eu], mu[eu]));
+  if (tg == ADG_TAG_INTERIOR || tg == ADG_TAG_PERIODIC) {
+    const int64_t e2u = pl.nbr[4 * eu + f];
+    const double Zpp = std::sqrt(rho[e2u] * (lam[e2u] + 2 * mu[e2u])), Zsp = std::sqrt(rho[e2u] * mu[e2u]);
+    godunov_pair(TA, Ti, Zpm, Zpp, Zsm, Zsp, FmM, FpM);
+  } else if (tg == ADG_TAG_FREE || tg == ADG_TAG_RIGID || tg == ADG_TAG_ABSORB) {
+    FmM = boundary_matrix(TA, Ti, Zpm, Zsm, tg);
+  }
+  if (Fm) std::copy(FmM.begin(), FmM.end(), Fm);
+  if (Fp) std::copy(FpM.begin(), FpM.end(), Fp);
+}
+
 void Ctx::setup() {
   if (!has_mesh || !has_mat) throw Err(ADG_E_STATE, "upload mesh and material before adg_init");
   CK(cudaSetDevice(cfg.device));
@@ -469,9 +513,7 @@ void Ctx::setup() {
       if (tg == ADG_TAG_INTERIOR || tg == ADG_TAG_PERIODIC) {
         const int64_t e2u = nbr_u[4 * eu + f];
         const double Zpp = std::sqrt(rho[e2u] * (lam[e2u] + 2 * mu[e2u])), Zsp = std::sqrt(rho[e2u] * mu[e2u]);
-        middle_state(Zpm, Zpp, Zsm, Zsp, Mm, Mp);
-        FmM = mm(mm(TA, Mm), Ti);
-        FpM = mm(mm(TA, Mp), Ti);
+        godunov_pair(TA, Ti, Zpm, Zpp, Zsm, Zsp, FmM, FpM);
         const int64_t e2 = inv[e2u];
         nbr[i * 4 + f] = (int)e2;
         const int c1 = cluster[i], c2 = cluster[e2];
@@ -504,12 +546,7 @@ void Ctx::setup() {
         nbr[i * 4 + f] = (int)inv[nbr_u[4 * eu + f]];
         ninfo[i * 4 + f] = nface_u[4 * eu + f] | (nperm_u[4 * eu + f] << 2) | (kind << 5);
       } else {
-        middle_state(Zpm, Zpm, Zsm, Zsm, Mm, Mp);
-        M9 G{};
-        if (tg == ADG_TAG_FREE) G = diag9({-1, 1, 1, -1, 1, -1, 1, 1, 1});
-        else if (tg == ADG_TAG_RIGID) G = diag9({1, 1, 1, -1, 1, -1, -1, 1, 1});
-        // absorbing: G = 0
-        FmM = mm(mm(TA, madd(Mm, mm(Mp, G))), Ti);
+        FmM = boundary_matrix(TA, Ti, Zpm, Zsm, tg);  // free, rigid, absorbing
       }
       for (int k = 0; k < 81; ++k) {
         Fm[(i * 4 + f) * 81 + k] = FmM[k];

@@ -114,3 +114,86 @@ def test_plan_reports_mesh_and_material_errors():
             assert ei.value.code == -2, mutate
         finally:
             L.adg_destroy(ctx)
+
+
+def _flux_case(m, mat, N=2):
+    from paper_2107_06640_gb300 import _lib as L
+    cfg = L.adg_default_config()
+    cfg.degree = N
+    ctx = L.adg_create(cfg)
+    L.adg_upload_mesh(ctx, m.xyz, m.tets, m.face_tag, m.face_partner)
+    L.adg_upload_material(ctx, *mat)
+    return L, ctx
+
+
+def _oracle_flux(n, tag, qm, qp, matm, matp):
+    """The oracle's Godunov flux T A^- w^b through a face with outward normal n."""
+    from oracle import physics as ph
+    R = ph.frame(n)
+    wm = ph.rotate_in(qm, R)
+    Zpm, Zsm = ph.impedances(*matm)
+    if tag in (0, 4):
+        Zpp, Zsp = ph.impedances(*matp)
+        wb = ph.middle_state(wm, ph.rotate_in(qp, R), Zpm, Zpp, Zsm, Zsp)
+    else:
+        wb = ph.middle_state(wm, ph.ghost(wm, tag), Zpm, Zpm, Zsm, Zsm)
+    return ph.rotate_out(ph.flux_rotated(wb, *matm), R)
+
+
+def test_face_flux_matrices_equal_the_oracle_flux():
+    """adg_face_flux returns the 9 x 9 matrices the kernels apply; with random
+    states on both sides they give the oracle's Godunov flux (Sec. 4.2) on
+    solid-solid (two materials), solid-fluid, fluid-fluid, periodic, free,
+    rigid and absorbing faces, and zero on gravitational and fault faces."""
+    rng = np.random.default_rng(12)
+    scale = np.array([1e6] * 6 + [1.0] * 3)
+    # ocean over crust with a gravitational top and absorbing sides; a second
+    # box with periodic x, free y and rigid z sides and a fault
+    m1, (rho, lam, mu) = coupled_box(nxy=2, n_water=1, n_crust=2, L=4e3, depth=3e3, water=1e3)
+    rho = rho * (1 + 0.1 * rng.uniform(-1, 1, m1.nt))
+    m2 = kuhn_box(np.linspace(0, 4e3, 5), np.linspace(0, 2e3, 3), np.linspace(-2e3, 0, 3),
+                  tags={"x-": 4, "x+": 4, "y-": 1, "y+": 1, "z-": 6, "z+": 6},
+                  fault=dict(c=0, jrange=(0, 2), krange=(0, 2)))
+    mu2 = 3.2e10 * (1 + 0.2 * rng.uniform(-1, 1, m2.nt))
+    cases = [(m1, (rho, lam, mu)), (m2, (2700.0 * (1 + 0.2 * rng.uniform(-1, 1, m2.nt)), 1.1 * mu2, mu2))]
+    seen = set()
+    for m, mat in cases:
+        L, ctx = _flux_case(m, mat)
+        geo = Geometry(m.xyz, m.tets, m.face_tag, m.face_partner)
+        try:
+            for e in range(m.nt):
+                for f in range(4):
+                    tag = int(m.face_tag[e, f])
+                    nb = geo.nbr[e, f]
+                    fluid_pair = (mat[2][e] == 0, nb >= 0 and mat[2][nb] == 0)
+                    key = (tag, fluid_pair)
+                    if key in seen and rng.uniform() > 0.05:
+                        continue
+                    seen.add(key)
+                    Fm, Fp = L.adg_face_flux(ctx, e, f)
+                    if tag in (2, 5):
+                        assert not Fm.any() and not Fp.any()
+                        continue
+                    qm = rng.standard_normal(9) * scale
+                    qp = rng.standard_normal(9) * scale
+                    matm = tuple(a[e] for a in mat)
+                    matp = tuple(a[nb] for a in mat) if nb >= 0 else matm
+                    want = _oracle_flux(geo.normal[e, f], tag, qm, qp, matm, matp)
+                    got = Fm @ qm + Fp @ qp
+                    sc = np.abs(want).max()
+                    assert np.max(np.abs(got - want)) <= 1e-12 * sc, (tag, fluid_pair)
+                    if tag not in (0, 4):
+                        assert not Fp.any()
+        finally:
+            L.adg_destroy(ctx)
+    tags = {k[0] for k in seen}
+    assert tags == {0, 1, 2, 3, 4, 5, 6}
+    assert (0, (True, False)) in seen and (0, (False, True)) in seen and (0, (True, True)) in seen
+    from paper_2107_06640_gb300 import AdgError
+    L, ctx = _flux_case(m2, cases[1][1])
+    try:
+        with pytest.raises(AdgError) as ei:
+            L.adg_face_flux(ctx, m2.nt, 0)
+        assert ei.value.code == -1
+    finally:
+        L.adg_destroy(ctx)
