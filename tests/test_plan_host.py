@@ -1,7 +1,8 @@
-"""The library's host-side mesh plan (adg_plan, no device): the CFL time step
-and rate-2 cluster of every element (Sec. 4.4) equal the oracle's, on meshes
-with periodic faces, a fluid layer with a gravitational surface, a fault and
-randomly jittered nodes; cluster indices bit for bit."""
+"""The library's host-side set-up, checked on the CPU (no device) against the
+oracle.  adg_plan: the CFL time step and rate-2 cluster of every element
+(Sec. 4.4) on meshes with periodic faces, a fluid layer with a gravitational
+surface, a fault and randomly jittered nodes; cluster indices bit for bit.
+adg_face_flux: the Godunov flux matrices of every face kind (Sec. 4.2)."""
 
 import numpy as np
 import pytest
