@@ -226,7 +226,7 @@ static void* dalloc(size_t n, std::vector<void*>& owned, int64_t& bytes) {
 // Host-side plan of the mesh in the caller's element order: geometry, face
 // connectivity with node permutations, CFL time steps and rate-2 clusters
 // (Sec. 4.4).  Needs no device; adg_init and adg_plan both use it.
-void Ctx::plan_mesh(const RefOps& o, int N, MeshPlan& plan) const {
+void Ctx::plan_mesh(const RefOps& o, int degree, MeshPlan& plan) const {
   const int64_t E = nt;
   // ---- geometry (user order)
   plan.Jinv.assign(9 * E, 0.0); plan.detJ.assign(E, 0.0); plan.area.assign(4 * E, 0.0); plan.nrm.assign(12 * E, 0.0);
@@ -369,19 +369,19 @@ void Ctx::plan_mesh(const RefOps& o, int N, MeshPlan& plan) const {
   // ---- CFL time steps and rate-2 clusters (Sec. 4.4)
   plan.dte.assign(E, 0.0);
   std::vector<double>& dte = plan.dte;
-  double& dtmin = plan.dtmin;
-  dtmin = 1e300;
+  double& dt_min = plan.dtmin;
+  dt_min = 1e300;
   for (int64_t e = 0; e < E; ++e) {
     double cp = std::sqrt((lam[e] + 2 * mu[e]) / rho[e]);
     if (!(cp > 0) || !(rho[e] > 0) || mu[e] < 0) throw Err(ADG_E_INVALID, "bad material");
-    dte[e] = cfg.cfl / (2 * N + 1) * h[e] / cp;
-    dtmin = std::min(dtmin, dte[e]);
+    dte[e] = cfg.cfl / (2 * degree + 1) * h[e] / cp;
+    dt_min = std::min(dt_min, dte[e]);
   }
   plan.cl.assign(E, 0);
   std::vector<int>& cl = plan.cl;
   const int cmaxcap = std::max(1, std::min(cfg.max_clusters, 16)) - 1;
   for (int64_t e = 0; e < E; ++e) {
-    int c = (int)std::floor(std::log2(dte[e] / dtmin) + 1e-12);
+    int c = (int)std::floor(std::log2(dte[e] / dt_min) + 1e-12);
     cl[e] = std::max(0, std::min(c, cmaxcap));
   }
   for (bool changed = true; changed;) {

@@ -135,7 +135,7 @@ struct Ctx {
   void record_after_macro();
   void record_free(int kind);
 
-  void plan_mesh(const RefOps& o, int N, MeshPlan& plan) const;
+  void plan_mesh(const RefOps& o, int degree, MeshPlan& plan) const;
   void face_flux(const MeshPlan& pl, int64_t eu, int f, double* Fm, double* Fp) const;
   void setup();
   StepArgs base_args() const;
