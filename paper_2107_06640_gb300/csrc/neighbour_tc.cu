@@ -225,9 +225,9 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
     const int64_t e0 = elem(pv0);
     const int ne = (int)(elem(pv0 + pnE - 1) - e0 + 1);
     // F-, F+ rows of elements e0 .. e0 + ne - 1: ne x 1296 bytes each, 16-byte aligned
-    for (int cc = u; cc < ne * 81; cc += 256) {
-      cp16(sFm + 4 * cc, reinterpret_cast<const float*>(a.Fm) + e0 * 324 + 4 * cc);
-      cp16(sFm + TE * 324 + 4 * cc, reinterpret_cast<const float*>(a.Fp) + e0 * 324 + 4 * cc);
+    for (int i4 = u; i4 < ne * 81; i4 += 256) {
+      cp16(sFm + 4 * i4, reinterpret_cast<const float*>(a.Fm) + e0 * 324 + 4 * i4);
+      cp16(sFm + TE * 324 + 4 * i4, reinterpret_cast<const float*>(a.Fp) + e0 * 324 + 4 * i4);
     }
     for (int c = u; c < ne * (PAR / 4); c += 256)
       cp16(sPr + 4 * c, reinterpret_cast<const float*>(a.par) + e0 * PAR + 4 * c);
