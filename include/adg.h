@@ -133,7 +133,9 @@ int adg_init(adg_ctx* ctx);
  * index or face tag out of range, an interior face without its neighbour, a
  * fault tagged on one side only, a bad periodic partner); ADG_E_INVALID for a
  * bad material (rho <= 0, mu < 0, c_p not positive).  Nothing is written on
- * error. */
+ * error.  The plan (and, before adg_init, the reference operators) is kept
+ * in the context for adg_face_flux and adg_face_neighbour until the next
+ * upload. */
 int adg_plan(adg_ctx* ctx, double* dt_elem, int32_t* cluster, double* dt_min, int* n_clusters);
 
 /* Host-only: the Godunov flux matrices adg_init builds for local face `face`
@@ -144,10 +146,21 @@ int adg_plan(adg_ctx* ctx, double* dt_elem, int32_t* cluster, double* dt_min, in
  * and absorbing faces (Fp zero); both are zero for gravitational and fault
  * faces, whose fluxes come from the (eta, H) ODE and the friction solve.  The
  * element update subtracts 2|S_f|/|J| times the face integral of the flux
- * against the basis.  No device needed; call after both uploads.  It plans
- * the mesh on every call (meant for inspection and tests).  Errors:
+ * against the basis.  No device needed; call after both uploads.  Errors:
  * ADG_E_INVALID for tet or face out of range; otherwise as adg_plan. */
 int adg_face_flux(adg_ctx* ctx, int64_t tet, int face, double* Fm, double* Fp);
+
+/* Host-only: local face `face` of user tet `tet` as its neighbour sees it
+ * (interior, periodic and fault faces): *nb_tet, *nb_face = the neighbour tet
+ * and its local face (-1, -1 for a face without neighbour), and
+ * node_map[Bf] = for each face node n (equispaced, see above) the
+ * neighbour's face node at the same physical point (for periodic faces:
+ * after the translation between the two faces).  This is the re-orientation
+ * the neighbour flux applies to the neighbour's trace (Sec. 4.2).  Outputs
+ * caller-owned, each may be NULL; node_map is left untouched without a
+ * neighbour.  No device needed.  Errors as adg_face_flux. */
+int adg_face_neighbour(adg_ctx* ctx, int64_t tet, int face, int64_t* nb_tet, int* nb_face,
+                       int32_t* node_map);
 
 int adg_query(const adg_ctx* ctx, adg_info* out);
 

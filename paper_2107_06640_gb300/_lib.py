@@ -52,6 +52,7 @@ _SIGS = {
     "adg_init": (C.c_int, [_P]),
     "adg_plan": (C.c_int, [_P, _P, _P, C.POINTER(C.c_double), C.POINTER(C.c_int)]),
     "adg_face_flux": (C.c_int, [_P, C.c_int64, C.c_int, _P, _P]),
+    "adg_face_neighbour": (C.c_int, [_P, C.c_int64, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int), _P]),
     "adg_query": (C.c_int, [_P, C.POINTER(adg_info)]),
     "adg_set_dofs": (C.c_int, [_P, _P]),
     "adg_get_dofs": (C.c_int, [_P, _P]),
@@ -212,6 +213,15 @@ def adg_face_flux(ctx, tet, face):
     Fp = np.empty((9, 9), np.float64)
     _check(ctx, load().adg_face_flux(ctx, int(tet), int(face), _ptr(Fm), _ptr(Fp)))
     return Fm, Fp
+
+
+def adg_face_neighbour(ctx, tet, face, n_face_nodes):
+    """(neighbour tet, its local face, node_map [Bf]) of local face `face` of
+    user tet `tet` (host only); (-1, -1, None) without a neighbour."""
+    nb, nf = C.c_int64(), C.c_int()
+    node_map = np.full(int(n_face_nodes), -1, np.int32)
+    _check(ctx, load().adg_face_neighbour(ctx, int(tet), int(face), C.byref(nb), C.byref(nf), _ptr(node_map)))
+    return (nb.value, nf.value, node_map) if nb.value >= 0 else (-1, -1, None)
 
 
 def adg_query(ctx):

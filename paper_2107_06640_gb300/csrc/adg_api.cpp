@@ -133,6 +133,20 @@ void run_ticks_to_boundary(Ctx& c) {
   }
 }
 
+// The host plan of the uploaded mesh, built on first use and kept until the
+// next upload; *o receives the reference operators it was built with.
+const adg::MeshPlan& host_plan(Ctx& c, const adg::RefOps** o) {
+  if (!c.has_mesh || !c.has_mat) adg::throw_err(ADG_E_STATE, "upload mesh and material first");
+  if (!c.inited && c.host_ops.N != c.cfg.degree) c.host_ops = adg::make_ref_ops(c.cfg.degree);
+  *o = c.inited ? &c.ops : &c.host_ops;
+  if (!c.host_plan) {
+    auto p = std::make_unique<adg::MeshPlan>();
+    c.plan_mesh(**o, c.cfg.degree, *p);
+    c.host_plan = std::move(p);
+  }
+  return *c.host_plan;
+}
+
 }  // namespace
 
 extern "C" {
@@ -181,6 +195,7 @@ int adg_upload_mesh(adg_ctx* ctx, int64_t nv, const double* xyz, int64_t nt, con
     if (face_partner) c.partner.assign(face_partner, face_partner + 4 * nt);
     else c.partner.clear();
     c.has_mesh = true;
+    c.host_plan.reset();
   });
 }
 
@@ -195,6 +210,7 @@ int adg_upload_material(adg_ctx* ctx, const double* rho, const double* lambda, c
     c.lam.assign(lambda, lambda + c.nt);
     c.mu.assign(mu, mu + c.nt);
     c.has_mat = true;
+    c.host_plan.reset();
   });
 }
 
@@ -209,16 +225,9 @@ int adg_init(adg_ctx* ctx) {
 int adg_plan(adg_ctx* ctx, double* dt_elem, int32_t* cluster, double* dt_min, int* n_clusters) {
   if (!ctx) return ADG_E_INVALID;
   return guard(ctx, [&] {
-    const Ctx& c = ctx->c;
-    if (!c.has_mesh || !c.has_mat) adg::throw_err(ADG_E_STATE, "upload mesh and material before adg_plan");
-    adg::RefOps local;
-    const adg::RefOps* o = &c.ops;
-    if (!c.inited) {
-      local = adg::make_ref_ops(c.cfg.degree);
-      o = &local;
-    }
-    adg::MeshPlan p;
-    c.plan_mesh(*o, c.cfg.degree, p);
+    Ctx& c = ctx->c;
+    const adg::RefOps* o;
+    const adg::MeshPlan& p = host_plan(c, &o);
     if (dt_elem) std::copy(p.dte.begin(), p.dte.end(), dt_elem);
     if (cluster)
       for (int64_t e = 0; e < c.nt; ++e) cluster[e] = p.cl[e];
@@ -230,18 +239,21 @@ int adg_plan(adg_ctx* ctx, double* dt_elem, int32_t* cluster, double* dt_min, in
 int adg_face_flux(adg_ctx* ctx, int64_t tet, int face, double* Fm, double* Fp) {
   if (!ctx) return ADG_E_INVALID;
   return guard(ctx, [&] {
-    const Ctx& c = ctx->c;
-    if (!c.has_mesh || !c.has_mat) adg::throw_err(ADG_E_STATE, "upload mesh and material before adg_face_flux");
+    Ctx& c = ctx->c;
     if (tet < 0 || tet >= c.nt || face < 0 || face > 3) adg::throw_err(ADG_E_INVALID, "tet or face out of range");
-    adg::RefOps local;
-    const adg::RefOps* o = &c.ops;
-    if (!c.inited) {
-      local = adg::make_ref_ops(c.cfg.degree);
-      o = &local;
-    }
-    adg::MeshPlan p;
-    c.plan_mesh(*o, c.cfg.degree, p);
-    c.face_flux(p, tet, face, Fm, Fp);
+    const adg::RefOps* o;
+    c.face_flux(host_plan(c, &o), tet, face, Fm, Fp);
+  });
+}
+
+int adg_face_neighbour(adg_ctx* ctx, int64_t tet, int face, int64_t* nb_tet, int* nb_face, int32_t* node_map) {
+  if (!ctx) return ADG_E_INVALID;
+  return guard(ctx, [&] {
+    Ctx& c = ctx->c;
+    if (tet < 0 || tet >= c.nt || face < 0 || face > 3) adg::throw_err(ADG_E_INVALID, "tet or face out of range");
+    const adg::RefOps* o;
+    const adg::MeshPlan& p = host_plan(c, &o);
+    c.face_neighbour(p, *o, tet, face, nb_tet, nb_face, node_map);
   });
 }
 

@@ -420,6 +420,20 @@ void Ctx::face_flux(const MeshPlan& pl, int64_t eu, int f, double* Fm, double* F
   if (Fp) std::copy(FpM.begin(), FpM.end(), Fp);
 }
 
+// Face f of user tet eu seen from its neighbour (interior, periodic and fault
+// faces): the neighbour tet and local face, and node_map[n] = the neighbour's
+// face node at the place of my face node n (the permutation the neighbour
+// kernel applies to the neighbour's trace); nb = -1 for faces without one.
+void Ctx::face_neighbour(const MeshPlan& pl, const RefOps& o, int64_t eu, int f, int64_t* nb, int* nf,
+                         int32_t* node_map) const {
+  const int64_t e2 = pl.nbr[4 * eu + f];
+  if (nb) *nb = e2;
+  if (nf) *nf = e2 < 0 ? -1 : pl.nface[4 * eu + f];
+  if (e2 < 0 || !node_map) return;
+  const int pid = pl.nperm[4 * eu + f];
+  for (int n = 0; n < o.Bf; ++n) node_map[n] = o.perm[(size_t)pid * o.Bf + n];
+}
+
 void Ctx::setup() {
   if (!has_mesh || !has_mat) throw Err(ADG_E_STATE, "upload mesh and material before adg_init");
   CK(cudaSetDevice(cfg.device));

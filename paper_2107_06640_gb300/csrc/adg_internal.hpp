@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <memory>
 #include <stdexcept>
 #include <string>
 #include <vector>
@@ -55,6 +56,10 @@ struct Ctx {
   std::vector<int32_t> tag;
   std::vector<double> rho, lam, mu;
   bool has_mesh = false, has_mat = false, inited = false;
+  // host plan for adg_plan / adg_face_flux / adg_face_neighbour, kept until the
+  // next mesh or material upload (adg_init builds its own)
+  std::unique_ptr<struct MeshPlan> host_plan;
+  RefOps host_ops;
   // discretisation
   int N = 0, B = 0, Bf = 0, B1 = 0, S = 1;
   bool fp64 = true;
@@ -137,6 +142,8 @@ struct Ctx {
 
   void plan_mesh(const RefOps& o, int degree, MeshPlan& plan) const;
   void face_flux(const MeshPlan& pl, int64_t eu, int f, double* Fm, double* Fp) const;
+  void face_neighbour(const MeshPlan& pl, const RefOps& o, int64_t eu, int f, int64_t* nb, int* nf,
+                      int32_t* node_map) const;
   void setup();
   StepArgs base_args() const;
   void launch_tick(int s, double dtm);

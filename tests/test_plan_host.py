@@ -8,6 +8,7 @@ import numpy as np
 import pytest
 
 import synthetic as syn
+from oracle.basis import FACE_VERTS
 from oracle.geometry import Geometry, cfl_dt, clusters
 from synthetic.mesh import kuhn_box
 from synthetic.workloads import coupled_box
@@ -196,5 +197,76 @@ def test_face_flux_matrices_equal_the_oracle_flux():
         with pytest.raises(AdgError) as ei:
             L.adg_face_flux(ctx, m2.nt, 0)
         assert ei.value.code == -1
+    finally:
+        L.adg_destroy(ctx)
+
+
+def _face_nodes(xyz, tet, f, N):
+    """Physical points of the equispaced face nodes chi = (i1/N, i2/N), i2 outer,
+    i1 inner, on local face f (opposite local vertex f; vertices a < b < c)."""
+    a, b, c = (xyz[tet[v]] for v in FACE_VERTS[f])
+    chi = np.array([(i1 / N, i2 / N) for i2 in range(N + 1) for i1 in range(N + 1 - i2)])
+    return a + chi[:, :1] * (b - a) + chi[:, 1:] * (c - a)
+
+
+@pytest.mark.parametrize("N", [3, 5])
+def test_face_node_maps_match_physical_points(N):
+    """adg_face_neighbour: for every interior, periodic and fault face the
+    neighbour and its face are the oracle's, and node_map (the permutation the
+    neighbour flux applies to the neighbour's trace, Sec. 4.2) carries each face
+    node onto the neighbour's node at the same physical point, on a warped
+    periodic box, a warped fault box and a jittered box."""
+    from paper_2107_06640_gb300 import _lib as L
+
+    def warp(x, ijk):
+        x[:, 0] += 150 * np.sin(x[:, 2] / 700.0) + 90 * np.cos(x[:, 1] / 500.0)
+        x[:, 2] += 120 * np.sin(x[:, 0] / 900.0)
+        return x
+
+    meshes = [_warped_periodic(3, 0.6),
+              kuhn_box(np.linspace(0, 4e3, 5), np.linspace(0, 2e3, 3), np.linspace(-2e3, 0, 3), warp=warp,
+                       fault=dict(c=0, jrange=(0, 2), krange=(0, 2))),
+              _jittered(3, 0.3, 4)]
+    Bf = (N + 1) * (N + 2) // 2
+    kinds = set()
+    for m in meshes:
+        geo = Geometry(m.xyz, m.tets, m.face_tag, m.face_partner)
+        mat = syn.elastic_uniform(m.nt)
+        L_, ctx = _flux_case(m, mat, N=N)
+        try:
+            for e in range(m.nt):
+                for f in range(4):
+                    nb, nf, node_map = L.adg_face_neighbour(ctx, e, f, Bf)
+                    assert nb == geo.nbr[e, f] and (nb < 0 or nf == geo.nbr_face[e, f])
+                    if nb < 0:
+                        continue
+                    kinds.add(int(m.face_tag[e, f]))
+                    assert sorted(node_map) == list(range(Bf))
+                    mine = _face_nodes(m.xyz, m.tets[e], f, N) + geo.shift[e, f]
+                    theirs = _face_nodes(m.xyz, m.tets[nb], nf, N)
+                    scale = np.abs(m.xyz).max()
+                    assert np.max(np.abs(theirs[node_map] - mine)) <= 1e-12 * scale, (e, f)
+        finally:
+            L.adg_destroy(ctx)
+    assert kinds == {0, 4, 5}
+
+
+def test_a_new_upload_replaces_the_kept_plan():
+    from paper_2107_06640_gb300 import _lib as L
+    m = _warped_periodic(2, 0.3)
+    rho, lam, mu = syn.elastic_uniform(m.nt)
+    ctx = L.adg_create(L.adg_default_config())
+    try:
+        L.adg_upload_mesh(ctx, m.xyz, m.tets, m.face_tag, m.face_partner)
+        L.adg_upload_material(ctx, rho, lam, mu)
+        dt1 = L.adg_plan(ctx)[0]
+        L.adg_upload_material(ctx, rho, 4.0 * lam + 6.0 * mu, mu)  # c_p doubled: half the time steps
+        dt2 = L.adg_plan(ctx)[0]
+        assert np.allclose(dt2, dt1 / 2, rtol=1e-14)
+        Fm, _ = L.adg_face_flux(ctx, 0, 0)
+        want = _oracle_flux(Geometry(m.xyz, m.tets, m.face_tag, m.face_partner).normal[0, 0], int(m.face_tag[0, 0]),
+                            np.eye(9)[6], np.zeros(9), (rho[0], 4 * lam[0] + 6 * mu[0], mu[0]),
+                            (rho[0], 4 * lam[0] + 6 * mu[0], mu[0]))
+        assert np.allclose(Fm[:, 6], want, rtol=1e-12, atol=1e-12 * np.abs(want).max())
     finally:
         L.adg_destroy(ctx)
