@@ -247,8 +247,16 @@ int adg_profile(adg_ctx* ctx, int n_macro, double* ms, int64_t* launches);
  *  - d_Q: DEVICE pointer to the caller's dofs in the context's precision,
  *    layout [tet][9][B] in user tet order (for such contexts the internal
  *    order is the user order), updated in place.  Owned by the caller.
- *  - stream: cudaStream_t to launch on, or NULL for the context's stream;
- *    the call only enqueues work (no synchronisation).
+ *  - stream: cudaStream_t to launch on; NULL is CUDA's default (legacy)
+ *    stream, as in any CUDA call, so work the caller enqueued on it (torch's
+ *    default stream, handle 0) is ordered before these kernels.  The call
+ *    only enqueues work (no synchronisation).
+ *  - Arithmetic: the CUDA-core kernels in the context's precision.  In an
+ *    ADG_3XTF32 context those are the FP32 kernels of ADG_FP32 (the
+ *    tensor-core kernels stage through shared memory the library allocates
+ *    with the context), so the result is the ADG_FP32 one: within 2e-5
+ *    relative L2 of the FP64 solution after a few steps, not bit-equal to
+ *    adg_advance of that context.
  *  - Meshes whose traces need more than the fixed maximum
  *    (n_tets * 4 * S_f * sizeof(precision) > 32 MiB, S_f = 9 Bf rounded up
  *    to a multiple of 4) are rejected with
@@ -260,6 +268,18 @@ int adg_profile(adg_ctx* ctx, int n_macro, double* ms, int64_t* launches);
  *    on the GPU race on it.  Non-finite dofs are reported by the next
  *    adg_sync() on the context. */
 int adg_step_noalloc(adg_ctx* ctx, void* d_Q, int n_steps, void* stream);
+
+/* Peak-rate probe of a GPU (a measurement aid for the roofline denominators;
+ * the paper has no counterpart).  kind 0: tcgen05.mma kind::tf32 with FP32
+ * accumulation (M = 128, N = 256, A in TMEM, B in shared memory, one CTA per
+ * SM); kind 1: FP32 fused multiply-add on the CUDA cores; kind 2: FP64 fused
+ * multiply-add.  Runs one untimed launch, then `reps` timed launches on a
+ * stream of its own; *flops = floating-point operations of the timed
+ * launches, *ms = their duration (CUDA events).  Allocates and frees a few
+ * bytes of device memory.  ADG_E_INVALID for a bad kind, device or reps,
+ * ADG_E_TIMEOUT if a bounded wait of the MMA loop ran out, ADG_E_CUDA on a
+ * CUDA error. */
+int adg_measure_peak(int kind, int device, int reps, double* flops, double* ms);
 
 /* Receivers: physical points; readout of q at the current time (whole ticks
  * synchronised: at macro-step boundaries), out[n][S][9] (host, double). */

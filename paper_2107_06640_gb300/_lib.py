@@ -75,6 +75,7 @@ _SIGS = {
     "adg_sync": (C.c_int, [_P]),
     "adg_profile": (C.c_int, [_P, C.c_int, _P, _P]),
     "adg_step_noalloc": (C.c_int, [_P, _P, C.c_int, _P]),
+    "adg_measure_peak": (C.c_int, [C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "adg_fault_faces": (C.c_int, [_P, _P, _P, _P, _P]),
     "adg_set_fault": (C.c_int, [_P, _P]),
     "adg_set_friction_law": (C.c_int, [_P, C.c_int]),
@@ -364,6 +365,14 @@ def adg_step_noalloc(ctx, d_Q_ptr, n_steps, stream_ptr=None):
     """d_Q_ptr: integer device address of the caller's dofs (see include/adg.h)."""
     _check(ctx, load().adg_step_noalloc(ctx, C.c_void_p(d_Q_ptr), int(n_steps),
                                         None if stream_ptr is None else C.c_void_p(stream_ptr)))
+
+
+def adg_measure_peak(kind, device=0, reps=20):
+    """(flops, ms) of `reps` timed launches of peak probe `kind` (0: tcgen05
+    kind::tf32 MMA, 1: FP32 FMA, 2: FP64 FMA) on `device`."""
+    f, ms = C.c_double(), C.c_double()
+    _check(None, load().adg_measure_peak(int(kind), int(device), int(reps), C.byref(f), C.byref(ms)))
+    return f.value, ms.value
 
 
 FPAR, FSTATE, MLP_NPARAM, MLP_TRAINABLE = 13, 8, 1327, 1313

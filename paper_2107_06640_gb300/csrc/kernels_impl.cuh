@@ -9,6 +9,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include "func_attr.hpp"
 #include "kernels.cuh"
 
 namespace adg {
@@ -500,12 +501,10 @@ __global__ void __launch_bounds__(kThreads) neighbour_kernel(StepArgs a) {
 template <typename T, int N>
 int launch_local_t(const StepArgs& a, int64_t nblocks, cudaStream_t st) {
   constexpr int bytes = Smem<T, N>::bytes;
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t ce = cudaFuncSetAttribute(local_kernel<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (ce != cudaSuccess) return (int)ce;
-    configured = true;
-  }
+  const int rc = configure_on_device((const void*)local_kernel<T, N>, [] {
+    return cudaFuncSetAttribute(local_kernel<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  });
+  if (rc) return rc;
   if (nblocks <= 0) return 0;
   local_kernel<T, N><<<(unsigned)nblocks, kThreads, bytes, st>>>(a);
   return (int)cudaGetLastError();

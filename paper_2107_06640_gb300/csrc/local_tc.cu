@@ -31,6 +31,7 @@
 
 #include <cstdint>
 
+#include "func_attr.hpp"
 #include "kernels.cuh"
 #include "tc_common.cuh"
 
@@ -488,15 +489,14 @@ __global__ void __launch_bounds__(kThreadsL, 1) local_tc_kernel(StepArgs a, int6
 }  // namespace
 
 int launch_local_tc(const StepArgs& a, int64_t n_virtual, int n_sms, void* stream, bool buffers) {
-  static bool configured = false;
-  if (!configured) {
+  const int rc = configure_on_device((const void*)local_tc_kernel<false>, [] {
     cudaError_t ce = cudaFuncSetAttribute(local_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           LImg::bytes);
     if (ce == cudaSuccess)
       ce = cudaFuncSetAttribute(local_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, LImg::bytes);
-    if (ce != cudaSuccess) return (int)ce;
-    configured = true;
-  }
+    return ce;
+  });
+  if (rc) return rc;
   if (n_virtual <= 0) return 0;
   const int64_t ntiles = (n_virtual + TE - 1) / TE;
   const int64_t want = (ntiles + 1) / 2;

@@ -29,6 +29,7 @@
 
 #include <cstdint>
 
+#include "func_attr.hpp"
 #include "kernels.cuh"
 #include "tc_common.cuh"
 
@@ -414,15 +415,14 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
 }  // namespace
 
 int launch_neighbour_tc(const StepArgs& a, int64_t n_virtual, int n_sms, void* stream, bool coarse) {
-  static bool configured = false;
-  if (!configured) {
+  const int rc = configure_on_device((const void*)neighbour_tc_kernel<true, false>, [] {
     cudaError_t ce = cudaSuccess;
     for (auto k : {neighbour_tc_kernel<true, false>, neighbour_tc_kernel<false, false>,
                    neighbour_tc_kernel<true, true>, neighbour_tc_kernel<false, true>})
       if (ce == cudaSuccess) ce = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, NImg::bytes);
-    if (ce != cudaSuccess) return (int)ce;
-    configured = true;
-  }
+    return ce;
+  });
+  if (rc) return rc;
   if (n_virtual <= 0) return 0;
   const int64_t ntiles = (n_virtual + TE - 1) / TE;
   const int64_t want = (ntiles + 1) / 2;

@@ -73,7 +73,10 @@ extern "C" int adg_step_noalloc(adg_ctx* ctx, void* d_Q, int n_steps, void* stre
     }
     scratch = g_scratch_addr[dev];
   }
-  cudaStream_t st = stream ? (cudaStream_t)stream : c.stream;
+  // NULL is CUDA's default stream (the legacy one), as for any CUDA call: a
+  // caller that wrote d_Q there, torch's default stream included, is ordered
+  // before these kernels
+  cudaStream_t st = stream ? (cudaStream_t)stream : cudaStreamLegacy;
   adg::StepArgs a = c.base_args();
   a.Q = d_Q;
   a.trace = scratch;

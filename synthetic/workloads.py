@@ -191,11 +191,17 @@ def lsw_fault_params(node_xyz, normal, seed=0, patch_center=None, patch_radius=3
 
 
 def random_dofs(shape, seed, decay=0.5, N=None):
-    """Seeded random modal coefficients (any basis layout); optional decay by
-    basis index keeps higher modes smaller."""
+    """Seeded standard-normal modal coefficients.  With N given, the axis of
+    length B_N = (N+1)(N+2)(N+3)/6 is the basis axis (either dofs layout,
+    [..., B, 9] or [..., 9, B]; the last such axis if several match) and mode l
+    is scaled by (1 + l)^-decay, so that higher modes are smaller."""
     rng = np.random.default_rng(seed)
     Q = rng.standard_normal(shape)
     if N is not None and decay:
-        B = shape[-1]
-        Q *= (1.0 + np.arange(B)) ** (-decay)
+        B = (N + 1) * (N + 2) * (N + 3) // 6
+        axes = [i for i, n in enumerate(shape) if n == B]
+        if not axes:
+            raise ValueError(f"random_dofs: no axis of length B = {B} in {shape}")
+        w = (1.0 + np.arange(B)) ** (-decay)
+        Q *= w.reshape([-1 if i == axes[-1] else 1 for i in range(len(shape))])
     return Q
