@@ -60,19 +60,19 @@ def bytes_per_update(N, w):
     reads and writes the dofs and writes 4 face traces; the neighbour kernel
     reads the own and the neighbours' traces and reads and writes the dofs.
     The tensor-core forms count what they move: face blocks padded to a
-    multiple of 4 floats, the element parameters, and (neighbour) the F-/F+
-    matrices."""
+    multiple of 4 floats, the element parameters, and (neighbour) the four
+    32-byte face records (normal, neighbour impedances, face code)."""
     B, Bf = (N + 1) * (N + 2) * (N + 3) // 6, (N + 1) * (N + 2) // 2
     FS = (9 * Bf + 3) // 4 * 4
     return {"local_kernel": (2 * 9 * B + 4 * 9 * Bf) * w, "neighbour_kernel": (2 * 9 * B + 8 * 9 * Bf) * w,
             "local_tc_kernel": (2 * 9 * B + 4 * FS + 16) * w,
-            "neighbour_tc_kernel": (2 * 9 * B + 8 * FS + 2 * 4 * 81 + 16) * w}
+            "neighbour_tc_kernel": (2 * 9 * B + 8 * FS + 16) * w + 4 * 32}
 
 
 # DRAM bytes (read + write) per element of the tensor-core kernels, from the
 # full ncu capture of the 374,400-tet box (profiles/tensor_core_kernels_box40.md);
 # a launch's traffic is scaled from it by the number of elements
-TC_DRAM_BYTES_PER_ELEMENT = {"local_tc_kernel": 7012.7, "neighbour_tc_kernel": 10538.1}
+TC_DRAM_BYTES_PER_ELEMENT = {"local_tc_kernel": 7012.7}
 
 
 def load_peaks():
@@ -83,19 +83,34 @@ def load_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-def tf32x3_peak_tflops(peaks):
-    """Effective 3xTF32 peak: the measured sustained bf16 dense rate scaled by
-    the nominal tf32/bf16 ratio (1.1 / 2.25 PFLOP/s) and divided by the three
-    tf32 products of every split product."""
-    return peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"]) * (1.1 / 2.25) / 3.0
+def unit_peaks():
+    """The TF32 tensor, FP32 and FP64 rates this project measured on the GPU
+    (profiles/peaks.md, written by `python -m paper_2107_06640_gb300.peaks`),
+    or None."""
+    from paper_2107_06640_gb300 import peaks as pk
+    return pk.load()
 
 
-def alu_peak_tflops(fp64, sm_mhz):
-    """CUDA-core peak: 152 SMs x 128 FP32 lanes x 2 flop/FMA x clock; FP64 from
-    the 1.25 TFLOP/s nominal at the 2070 MHz maximum, scaled to the clock."""
+def tf32x3_peak_tflops(peaks, units=None):
+    """(peak, source) of a 3xTF32 split product: a third of the measured dense
+    TF32 tcgen05 rate (a burst rate: the tensor-core launches are timed alone);
+    without that measurement, the measured burst bf16 rate times the nominal
+    tf32/bf16 ratio 1.1/2.25, divided by 3."""
+    if units and units.get("tf32_tensor_tflops"):
+        return units["tf32_tensor_tflops"] / 3.0, "measured tcgen05 kind::tf32 rate / 3 (profiles/peaks.md)"
+    return peaks["bf16_tflops"] * (1.1 / 2.25) / 3.0, "measured burst bf16 x nominal 1.1/2.25 / 3"
+
+
+def alu_peak_tflops(fp64, sm_mhz, units=None, sm_count=None):
+    """(peak, source) of the CUDA-core kernels: the measured FP64 or FP32 FMA
+    rate; without it, SMs x 128 FP32 lanes x 2 x clock, or the nominal
+    1.25 TFLOP/s FP64 scaled to the clock."""
+    key = "fp64_fma_tflops" if fp64 else "fp32_fma_tflops"
+    if units and units.get(key):
+        return units[key], f"measured {key} (profiles/peaks.md)"
     if fp64:
-        return 1.25 * sm_mhz / 2070.0
-    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+        return 1.25 * sm_mhz / 2070.0, "nominal 1.25 TFLOP/s FP64 at the sampled clock"
+    return (sm_count or 152) * 128 * 2 * sm_mhz * 1e6 / 1e12, "derived: SMs x 128 FP32 lanes x 2 x clock"
 
 
 # where the nvidia-smi clock samples of each timed region are written (--clock-dir)
@@ -584,28 +599,30 @@ def main():
     kname = ["local_tc_kernel", "neighbour_tc_kernel"][dom] if tc_form else ["local_kernel", "neighbour_kernel"][dom]
     clk = r32["clocks"]
     sm_mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    alu_peak = alu_peak_tflops(False, peaks.get("sm_max_mhz", 2070.0))
+    units = unit_peaks()
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    alu_peak, alu_src = alu_peak_tflops(False, peaks.get("sm_max_mhz", 2070.0), units, n_sm)
     achieved_flops = fl[kname.replace("_tc", "")] * n_k / (t_k[dom] * 1e-3) / 1e12
     achieved_bytes = by[kname] * n_k / (t_k[dom] * 1e-3) / 1e9
     frac_alu = achieved_flops / alu_peak
     frac_hbm = achieved_bytes / peaks["hbm_gbs"]
-    tc_peak = tf32x3_peak_tflops(peaks)
+    tc_peak, tc_src = tf32x3_peak_tflops(peaks, units)
     achieved_tc = fl["local_tensor"] * n_k / (t_k[0] * 1e-3) / 1e12 if tc_form else None
     if kname == "local_tc_kernel":
         roof = {"bound": "tensor", "achieved": achieved_tc, "peak": tc_peak, "unit": "TFLOP/s",
                 "frac": achieved_tc / tc_peak, "traffic": None, "kernel": kname,
-                "peak_source": f"{src} sustained bf16 x 1.1/2.25 (tf32) / 3 (3xTF32 products)",
+                "peak_source": tc_src,
                 "flops_counted": "reference-matrix products only (predictor levels 0-2, volume, traces)"}
     elif kname == "neighbour_tc_kernel":
         # the lift runs on the tensor cores and the fluxes are ~27 kflop per update:
         # HBM (traces, flux matrices, dofs) is the roof
         roof = {"bound": "hbm", "achieved": achieved_bytes, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": frac_hbm, "traffic": None, "kernel": kname, "peak_source": src,
-                "bytes_counted": f"{by[kname]} B per update: own and neighbour face blocks, F-/F+, dofs read+write"}
+                "bytes_counted": f"{by[kname]} B per update: own and neighbour face blocks, face records, dofs read+write"}
     elif frac_alu >= frac_hbm:
         roof = {"bound": "alu", "achieved": achieved_flops, "peak": alu_peak, "unit": "TFLOP/s",
                 "frac": frac_alu, "traffic": None, "kernel": kname,
-                "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2070 MHz"}
+                "peak_source": alu_src}
     else:
         roof = {"bound": "hbm", "achieved": achieved_bytes, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": frac_hbm, "traffic": None, "kernel": kname, "peak_source": src}
@@ -624,6 +641,7 @@ def main():
                      / peaks["hbm_gbs"]})
     r64k = r64["kms"]
     fp64_alu = fl["local_kernel"] * s.nt / (r64k[0] * 1e-3) / 1e12
+    fp64_peak, fp64_src = alu_peak_tflops(True, r64["clocks"].get("sm_mhz") or 2070.0, units, n_sm)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": r32["steps"],
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -637,7 +655,8 @@ def main():
                             "note": "every product on FP32 CUDA cores",
                             "kernel_ms": {"local": rcc["kms"][0], "neighbour": rcc["kms"][1]}},
         "fp64": {"value": value64, "unit": UNIT, "steps": r64["steps"], "ms_per_step": r64["ms"] / r64["steps"],
-                 "local_kernel_tflops": fp64_alu, "fp64_peak_tflops_nominal": 1.25,
+                 "local_kernel_tflops": fp64_alu, "fp64_peak_tflops": fp64_peak, "fp64_peak_source": fp64_src,
+                 "local_kernel_frac": fp64_alu / fp64_peak,
                  "kernel_ms": {"local": r64k[0], "neighbour": r64k[1]}, "clocks": r64["clocks"]},
         "roofline": roof,
         "accuracy": accuracy,

@@ -488,6 +488,7 @@ void Ctx::setup() {
 
   // ---- per-element / per-face device data (internal order)
   std::vector<double> par((size_t)E * PAR), Fm((size_t)E * 324, 0.0), Fp((size_t)E * 324, 0.0);
+  std::vector<float> frec(tc ? (size_t)E * 4 * FREC : 0, 0.f);
   std::vector<int> nbr((size_t)E * 4, -1), ninfo((size_t)E * 4, 0), gslot((size_t)E * 4, -1),
       bslot(E, -1), dslot((size_t)E * 4, -1);
   std::vector<double> gpar;
@@ -524,9 +525,20 @@ void Ctx::setup() {
       const int tg = tag[4 * eu + f];
       M9 Mm, Mp, FmM{}, FpM{};
       int kind = NK_NONE;
+      float* rec = tc ? &frec[((size_t)i * 4 + f) * FREC] : nullptr;
+      if (rec) {
+        for (int d = 0; d < 3; ++d) rec[d] = (float)n[d];
+        rec[5] = (float)(tg == ADG_TAG_FREE ? FACE_FREE
+                         : tg == ADG_TAG_RIGID ? FACE_RIGID
+                         : tg == ADG_TAG_ABSORB ? FACE_ABSORB : FACE_NEIGHBOUR);
+      }
       if (tg == ADG_TAG_INTERIOR || tg == ADG_TAG_PERIODIC) {
         const int64_t e2u = nbr_u[4 * eu + f];
         const double Zpp = std::sqrt(rho[e2u] * (lam[e2u] + 2 * mu[e2u])), Zsp = std::sqrt(rho[e2u] * mu[e2u]);
+        if (rec) {
+          rec[3] = (float)Zpp;
+          rec[4] = (float)Zsp;
+        }
         godunov_pair(TA, Ti, Zpm, Zpp, Zsm, Zsp, FmM, FpM);
         const int64_t e2 = inv[e2u];
         nbr[i * 4 + f] = (int)e2;
@@ -683,6 +695,7 @@ void Ctx::setup() {
     std::vector<float> tf(lift_tc_floats());
     pack_lift_tc(ops.lift.data(), tf.data());
     dTcLift = upload_raw<float>(tf, owned, dev_bytes);
+    dFrec = upload_raw<float>(frec, owned, dev_bytes);
   }
   dErr = (unsigned int*)dalloc(sizeof(unsigned int), owned, dev_bytes);
   if (nff) {
@@ -715,6 +728,7 @@ StepArgs Ctx::base_args() const {
   a.ktT = dKt; a.kvolT = dKvol; a.efcT = dEfc; a.liftT = dLift; a.perm = dPerm; a.gpar = dGpar;
   a.S = S; a.err = dErr;
   a.fslot = dFslot; a.drout = dDrout; a.gflux = dGflux; a.tc_local = dTcLocal; a.tc_lift = dTcLift;
+  a.frec = dFrec;
   return a;
 }
 

@@ -89,6 +89,7 @@ struct Ctx {
   int64_t* dOrder = nullptr;  // order on the device: the caller's element of library element i
   double *dBtrace = nullptr, *dEta = nullptr, *dGpar = nullptr;
   void *dPar = nullptr, *dFm = nullptr, *dFp = nullptr;
+  float* dFrec = nullptr;  // face records of the tensor-core neighbour kernel
   void *dKt = nullptr, *dKvol = nullptr, *dEfc = nullptr, *dLift = nullptr;
   int *dNbr = nullptr, *dNinfo = nullptr, *dGslot = nullptr, *dBslot = nullptr, *dDslot = nullptr,
       *dPerm = nullptr;

@@ -69,7 +69,15 @@ struct StepArgs {
   void* gflux;          // T [ngslot*S][9][Bf] time-integrated flux of gravitational faces
   const float* tc_local; // tensor-core operands of the local kernel (hi/lo, canonical layout), degree 5
   const float* tc_lift;  // tensor-core lift operand of the neighbour kernel (hi/lo, canonical layout), degree 5
+  const float* frec;     // [E][4][FREC] face records of the tensor-core neighbour kernel (FP32 dofs)
 };
+
+// Face record of the tensor-core neighbour kernel (floats): the outward unit
+// normal n[3], the plus side's impedances Zp+, Zs+ (interior and periodic
+// faces), the face code (FACE_* below), two zeros.  The kernel forms the
+// Godunov flux of Sec. 4.2 from it and the element's own material.
+constexpr int FREC = 8;
+enum { FACE_NEIGHBOUR = 0, FACE_FREE = 1, FACE_RIGID = 2, FACE_ABSORB = 3 };
 
 // tensor-core (tcgen05, 3xTF32) local kernel, degree 5, FP32 dofs (local_tc.cu),
 // for elements without gravitational faces, fault faces or finer LTS neighbours

@@ -13,17 +13,20 @@
 //      copied asynchronously (cp.async, double-buffered over the faces) into
 //      shared memory as they are stored, [element][quantity][node] (element
 //      stride padded against bank conflicts);
-//   2. work item (element, node triplet, group of 3 output rows p), one per
-//      thread of the tile, forms for its three nodes and rows
-//        G[p][n] = s_f (sum_q F-[p][q] V_own[q][n] + sum_q F+[p][q] V_nbr[q][perm n])
-//      (s_f = 2|S_f|/|J|, F rows broadcast from the staged F-/F+ of the tile)
-//      and writes the 9 values to a transposition buffer [element][p][28];
+//   2. work item (element, node), one per thread of the tile, forms the
+//      scaled Godunov flux G[.][n] = s_f (F- V_own[.][n] + F+ V_nbr[.][perm n])
+//      (s_f = 2|S_f|/|J|) in the face frame: both states rotated to (n, s, t),
+//      the middle state of Eq. (boundary-state) (a linear boundary's ghost
+//      folded into it), A- applied and the result rotated back, with the
+//      face's coefficients formed once per tile from a 32-byte face record
+//      and the element's material; it writes the 9 values to a transposition
+//      buffer [element][p][28];
 //   3. the thread of row (element, p) takes its 24 columns, splits them into
 //      tf32 hi + lo and writes them to TMEM columns 24 f + n.
 // One MMA chain then lifts all four faces:
 //   Q[(element, p)][m] -= sum_{f,n} G[p][24 f + n] lift_f[m][n],
 // A = G in TMEM (K = 96), B = the lift matrices resident in shared memory.
-// The next tile's F matrices, parameters and face 0 are requested before
+// The next tile's face records, parameters and face 0 are requested before
 // this tile's lift.
 #include <cuda_runtime.h>
 
@@ -50,8 +53,8 @@ constexpr int kStage = TE * kSS;      // floats per staged face array
 constexpr int kGrow = 28;             // transposed flux row: 21 nodes + 7 zero; 28 floats put the 8
                                       // rows of a quarter warp's 16-byte reads on distinct banks
 constexpr int kG = TE * 9 * kGrow;    // floats per transposition buffer
-constexpr int kTrip = 7;              // node triplets (n, n + 7, n + 14) per element face
-constexpr int kItems = TE * kTrip * 3;  // work items per face: element x node triplet x 3 output rows
+constexpr int kItems = TE * BF;       // work items per face: element x node
+constexpr int kCoef = 32;             // per (face, element): frame n, s, t; middle-state and A- coefficients
 
 struct NImg {
   static constexpr int oL = 0, sL = kN * kK;                  // lift hi, lo
@@ -59,9 +62,11 @@ struct NImg {
   static constexpr int oMeta = oPerm + 128;                   // per tile slot: [face][element] int64 + int
   static constexpr int sMeta = 4 * TE * 3;
   static constexpr int oStage = oMeta + 2 * sMeta;            // per tile slot: 2 buffers x (own, nbr)
-  static constexpr int oF = oStage + 2 * 4 * kStage;          // per tile slot: F- then F+ of the tile
-  static constexpr int sF = 2 * TE * 324;
-  static constexpr int oPar = oF + 2 * sF;                    // per tile slot: element parameters
+  static constexpr int oRec = oStage + 2 * 4 * kStage;        // per tile slot: face records [element][face]
+  static constexpr int sRec = TE * 4 * FREC;
+  static constexpr int oCoef = oRec + 2 * sRec;               // per tile slot: [face][element][kCoef]
+  static constexpr int sCoef = 4 * TE * kCoef;
+  static constexpr int oPar = oCoef + 2 * sCoef;              // per tile slot: element parameters
   static constexpr int sPar = TE * PAR;
   static constexpr int oG = oPar + 2 * sPar;                  // per tile slot: transposition buffer
   static constexpr int floats = oG + 2 * kG;
@@ -127,6 +132,111 @@ __device__ __forceinline__ void stage_face(int f, int u, int64_t v0, int nE, con
   }
 }
 
+// Coefficients of face f of the tile's element el (el < ne; others untouched)
+// from its face record and parameters: the frame (n, s, t) with n the outward
+// normal and s, t any orthonormal tangents (the flux does not depend on
+// them); the middle state w^b = Mm w- + Mp w+ of the rotated states on the
+// components the x-Jacobian reads (Sec. 4.2, Eq. boundary-state; normal pair
+// (0, 6) with the P impedances, shear pairs (3, 7) and (5, 8) with the S
+// impedances, welded when both sides are solid, else zero shear traction);
+// for a linear boundary the ghost w+ = G w- (free surface: traction
+// mirrored; rigid wall: normal velocity mirrored; absorbing: G = 0) is folded
+// into Mm; and the x-Jacobian entries of the element's material times the
+// face scale s_f = 2|S_f|/|J|.
+__device__ __forceinline__ void face_coefficients(int f, int el, int ne, const float* sRec, const float* sPr,
+                                                  float* sCo) {
+  if (el >= ne) return;
+  const float* rec = sRec + (el * 4 + f) * FREC;
+  const float* pr = sPr + el * PAR;
+  float* co = sCo + (f * TE + el) * kCoef;
+  const float nx = rec[0], ny = rec[1], nz = rec[2];
+  // tangent from the coordinate axis along which n is smallest
+  const float ax = fabsf(nx), ay = fabsf(ny), az = fabsf(nz);
+  const int k = (ay < ax) ? ((az < ay) ? 2 : 1) : ((az < ax) ? 2 : 0);
+  const float dot = k == 0 ? nx : (k == 1 ? ny : nz);
+  float sx = (k == 0 ? 1.f : 0.f) - dot * nx, sy = (k == 1 ? 1.f : 0.f) - dot * ny,
+        sz = (k == 2 ? 1.f : 0.f) - dot * nz;
+  const float is = rsqrtf(sx * sx + sy * sy + sz * sz);
+  sx *= is; sy *= is; sz *= is;
+  const float tx = ny * sz - nz * sy, ty = nz * sx - nx * sz, tz = nx * sy - ny * sx;
+  const float rho = pr[9], lam = pr[10], mu = pr[11], sf = pr[12 + f];
+  const float Zpm = sqrtf(rho * (lam + 2.f * mu)), Zsm = sqrtf(rho * mu);
+  const int code = (int)rec[5];
+  const float Zpp = code == FACE_NEIGHBOUR ? rec[3] : Zpm, Zsp = code == FACE_NEIGHBOUR ? rec[4] : Zsm;
+  const float c = Zpm * Zpp / (Zpm + Zpp);
+  float a00 = 1.f - c / Zpp, a06 = -c, b00 = c / Zpp, b06 = c;
+  float a60 = -c / (Zpp * Zpm), a66 = 1.f - c / Zpm, b60 = c / (Zpp * Zpm), b66 = c / Zpm;
+  float stt, stv, svt, svv, ttt, ttv, tvt, tvv;
+  if (Zsm > 0.f && Zsp > 0.f) {
+    const float cs = Zsm * Zsp / (Zsm + Zsp);
+    stt = 1.f - cs / Zsp; stv = -cs; ttt = cs / Zsp; ttv = cs;
+    svt = -cs / (Zsp * Zsm); svv = 1.f - cs / Zsm; tvt = cs / (Zsp * Zsm); tvv = cs / Zsm;
+  } else {
+    stt = stv = ttt = ttv = tvt = tvv = 0.f;
+    svv = 1.f;
+    svt = Zsm > 0.f ? -1.f / Zsm : 0.f;
+  }
+  if (code != FACE_NEIGHBOUR) {
+    // ghost multipliers of the rotated components: traction (0), shear traction
+    // (3, 5), normal velocity (6), tangential velocities (7, 8)
+    const float G0 = code == FACE_FREE ? -1.f : (code == FACE_RIGID ? 1.f : 0.f);
+    const float G3 = code == FACE_ABSORB ? 0.f : -1.f;
+    const float G6 = code == FACE_FREE ? 1.f : (code == FACE_RIGID ? -1.f : 0.f);
+    const float G7 = code == FACE_ABSORB ? 0.f : 1.f;
+    a00 += b00 * G0; a06 += b06 * G6; a60 += b60 * G0; a66 += b66 * G6;
+    stt += ttt * G3; stv += ttv * G7; svt += tvt * G3; svv += tvv * G7;
+    b00 = b06 = b60 = b66 = ttt = ttv = tvt = tvv = 0.f;
+  }
+  const float v[29] = {nx, ny, nz, sx, sy, sz, tx, ty, tz, a00, a06, a60, a66, b00, b06, b60, b66,
+                       stt, stv, svt, svv, ttt, ttv, tvt, tvv,
+                       -(lam + 2.f * mu) * sf, -lam * sf, -mu * sf, -sf / rho};
+#pragma unroll
+  for (int i = 0; i < 29; ++i) co[i] = v[i];
+}
+
+// Scaled Godunov flux of one face node: qm, qp the minus and plus traces
+// (global frame, quantities sxx syy szz sxy syz sxz vx vy vz); g = s_f (F- qm +
+// F+ qp) = s_f T A- (Mm T^-1 qm + Mp T^-1 qp).
+__device__ __forceinline__ void face_flux(const float* co, const float qm[9], const float qp[9], float g[9]) {
+  const float nx = co[0], ny = co[1], nz = co[2], sx = co[3], sy = co[4], sz = co[5], tx = co[6], ty = co[7],
+              tz = co[8];
+  float w[2][6];  // rotated components 0, 3, 5, 6, 7, 8 of each state
+#pragma unroll
+  for (int side = 0; side < 2; ++side) {
+    const float* q = side == 0 ? qm : qp;
+    const float snx = q[0] * nx + q[3] * ny + q[5] * nz;
+    const float sny = q[3] * nx + q[1] * ny + q[4] * nz;
+    const float snz = q[5] * nx + q[4] * ny + q[2] * nz;
+    w[side][0] = nx * snx + ny * sny + nz * snz;
+    w[side][1] = sx * snx + sy * sny + sz * snz;
+    w[side][2] = tx * snx + ty * sny + tz * snz;
+    w[side][3] = nx * q[6] + ny * q[7] + nz * q[8];
+    w[side][4] = sx * q[6] + sy * q[7] + sz * q[8];
+    w[side][5] = tx * q[6] + ty * q[7] + tz * q[8];
+  }
+  const float b0 = co[9] * w[0][0] + co[10] * w[0][3] + co[13] * w[1][0] + co[14] * w[1][3];
+  const float b6 = co[11] * w[0][0] + co[12] * w[0][3] + co[15] * w[1][0] + co[16] * w[1][3];
+  const float b3 = co[17] * w[0][1] + co[18] * w[0][4] + co[21] * w[1][1] + co[22] * w[1][4];
+  const float b7 = co[19] * w[0][1] + co[20] * w[0][4] + co[23] * w[1][1] + co[24] * w[1][4];
+  const float b5 = co[17] * w[0][2] + co[18] * w[0][5] + co[21] * w[1][2] + co[22] * w[1][5];
+  const float b8 = co[19] * w[0][2] + co[20] * w[0][5] + co[23] * w[1][2] + co[24] * w[1][5];
+  // x-Jacobian of the minus material (times s_f) on the middle state
+  const float f0 = co[25] * b6, f1 = co[26] * b6, f3 = co[27] * b7, f5 = co[27] * b8;
+  const float f6 = co[28] * b0, f7 = co[28] * b3, f8 = co[28] * b5;
+  // back to the global frame: stress f1 I + n u^T + u n^T, velocity f6 n + f7 s + f8 t
+  const float h = 0.5f * (f0 - f1);
+  const float ux = h * nx + f3 * sx + f5 * tx, uy = h * ny + f3 * sy + f5 * ty, uz = h * nz + f3 * sz + f5 * tz;
+  g[0] = f1 + 2.f * nx * ux;
+  g[1] = f1 + 2.f * ny * uy;
+  g[2] = f1 + 2.f * nz * uz;
+  g[3] = nx * uy + ux * ny;
+  g[4] = ny * uz + uy * nz;
+  g[5] = nx * uz + ux * nz;
+  g[6] = f6 * nx + f7 * sx + f8 * tx;
+  g[7] = f6 * ny + f7 * sy + f8 * ty;
+  g[8] = f6 * nz + f7 * sz + f8 * tz;
+}
+
 // kOne: one scenario (S = 1), where a virtual element is its element and the
 // 64-bit divisions by S drop out; kCoarse: some faces of the launch have a
 // coarser LTS neighbour (without, their code stays out of the kernel)
@@ -165,7 +275,8 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
   long long* sNb = reinterpret_cast<long long*>(sm + NImg::oMeta + slot * NImg::sMeta);
   int* sPm = reinterpret_cast<int*>(sNb + 4 * TE);
   const float* trace = reinterpret_cast<const float*>(a.trace);
-  float* sFm = sm + NImg::oF + slot * NImg::sF;  // [element - e0][face][81], F+ at + TE * 324
+  float* sRec = sm + NImg::oRec + slot * NImg::sRec;   // [element - e0][face][FREC]
+  float* sCo = sm + NImg::oCoef + slot * NImg::sCoef;  // [face][element - e0][kCoef]
   float* sPr = sm + NImg::oPar + slot * NImg::sPar;
   // [element][p][28]; one buffer: face f + 1's items start after the barrier
   // that every thread reaches only when its rows of face f are done
@@ -183,7 +294,7 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
   float bad = 0.f;  // stays 0 while every updated dof is finite (x * 0 is NaN for x = inf, NaN)
 
   // Neighbour trace blocks of a tile's faces, then one cp.async group per
-  // thread with the tile's F-/F+ matrices, element parameters and face 0
+  // thread with the tile's face records, element parameters and face 0
   // (staging buffer 0).  Thread u < 48 owns (face u / 12, element u % 12) of
   // a tile: its neighbour information, loaded early (meta_load) and made the
   // tile's trace-block table later (prefetch).
@@ -225,11 +336,8 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
     slot_bar(slot);
     const int64_t e0 = elem(pv0);
     const int ne = (int)(elem(pv0 + pnE - 1) - e0 + 1);
-    // F-, F+ rows of elements e0 .. e0 + ne - 1: ne x 1296 bytes each, 16-byte aligned
-    for (int i4 = u; i4 < ne * 81; i4 += 256) {
-      cp16(sFm + 4 * i4, reinterpret_cast<const float*>(a.Fm) + e0 * 324 + 4 * i4);
-      cp16(sFm + TE * 324 + 4 * i4, reinterpret_cast<const float*>(a.Fp) + e0 * 324 + 4 * i4);
-    }
+    // face records of elements e0 .. e0 + ne - 1: ne x 128 bytes, 16-byte aligned
+    for (int i4 = u; i4 < ne * FREC; i4 += 256) cp16(sRec + 4 * i4, a.frec + e0 * 4 * FREC + 4 * i4);
     for (int c = u; c < ne * (PAR / 4); c += 256)
       cp16(sPr + 4 * c, reinterpret_cast<const float*>(a.par) + e0 * PAR + 4 * c);
     stage_face<kCoarse>(0, u, pv0, pnE, trace, sNb, sStage, sStage + kStage, dtrace, cc);
@@ -253,6 +361,7 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
     const bool valid = lane < 27 && i < nE;
     const int64_t v = v0 + (valid ? i : 0);
     const int r0 = kOne ? 0 : (int)(v0 - elem(v0) * S);  // scenario of the tile's first virtual element
+    const int ne = (int)(elem(v0 + nE - 1) - elem(v0) + 1);  // elements of the tile
 #pragma unroll 1
     for (int f = 0; f < 4; ++f) {
       // ---- stage face f + 1 while face f is used
@@ -273,47 +382,32 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
         tc::fence_after();
         tc::mma3_ts<kN, 48>(tbase + cAcc, tbase + cGh, tbase + cGl, sL, sL + 4 * NImg::sL, false);
       }
+      if (f == 0) {  // the face coefficients of the tile (records and parameters arrived with face 0)
+        if (u < 4 * TE) face_coefficients(u / TE, u % TE, ne, sRec, sPr, sCo);
+        slot_bar(slot);
+      }
       const float* sVo = sStage + (f & 1) * 2 * kStage;
       const float* sVn = sVo + kStage;
-      // ---- work item (element, node triplet, three output rows) of thread u: scaled flux
+      // ---- work item (element, node) of thread u: scaled Godunov flux in the face frame
       if (u < kItems) {
-        const int item = u;
-        const int ei = item / (3 * kTrip), rem = item - ei * (3 * kTrip);
-        const int k = rem / 3, pg = rem - 3 * k;  // node triplet, group of output rows
+        const int ei = u / BF, n = u - ei * BF;
         const int el = kOne ? ei : (r0 + ei) / S;  // element of item's virtual element, from the tile's first
-        const float* Fm = sFm + (el * 4 + f) * 81 + 27 * pg;
-        const float* Fp = Fm + TE * 324;
-        const float sc = ei < nE ? sPr[el * PAR + 12 + f] : 0.f;
-        const int* perm = sPerm + sPm[f * TE + ei] * BF;
-        int nd[3], pn[3];
-#pragma unroll
-        for (int uu = 0; uu < 3; ++uu) {
-          nd[uu] = k + kTrip * uu;
-          pn[uu] = perm[nd[uu]];
-        }
-        float vo[3][9], vn[3][9];
-#pragma unroll
-        for (int qq = 0; qq < 9; ++qq) {
-          const float* o = sVo + ei * kSS + qq * BF;
-          const float* nn = sVn + ei * kSS + qq * BF;
-#pragma unroll
-          for (int uu = 0; uu < 3; ++uu) {
-            vo[uu][qq] = o[nd[uu]];
-            vn[uu][qq] = nn[pn[uu]];
-          }
-        }
-        float* gout = sG + (ei * 9 + 3 * pg) * kGrow;
-#pragma unroll
-        for (int pp = 0; pp < 3; ++pp) {
-          float g[3] = {0.f, 0.f, 0.f};
+        float* gout = sG + ei * 9 * kGrow + n;
+        if (ei < nE) {
+          const int pn = sPerm[sPm[f * TE + ei] * BF + n];
+          float qo[9], qn[9];
 #pragma unroll
           for (int qq = 0; qq < 9; ++qq) {
-            const float fm = Fm[pp * 9 + qq], fp = Fp[pp * 9 + qq];
-#pragma unroll
-            for (int uu = 0; uu < 3; ++uu) g[uu] += fm * vo[uu][qq] + fp * vn[uu][qq];
+            qo[qq] = sVo[ei * kSS + qq * BF + n];
+            qn[qq] = sVn[ei * kSS + qq * BF + pn];
           }
+          float g[9];
+          face_flux(sCo + (f * TE + el) * kCoef, qo, qn, g);
 #pragma unroll
-          for (int uu = 0; uu < 3; ++uu) gout[pp * kGrow + nd[uu]] = sc * g[uu];
+          for (int pp = 0; pp < 9; ++pp) gout[pp * kGrow] = g[pp];
+        } else {
+#pragma unroll
+          for (int pp = 0; pp < 9; ++pp) gout[pp * kGrow] = 0.f;
         }
       }
       slot_bar(slot);
@@ -360,8 +454,7 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
       tc::prefetch_l2(reinterpret_cast<const float*>(a.Q) + q0 * 9 * B, n2 * 9 * B * 4);
       tc::prefetch_l2(trace + q0 * 4 * kFS, n2 * 4 * kFS * 4);
       const int64_t e0 = elem(q0), ne = elem(q0 + n2 - 1) - e0 + 1;
-      tc::prefetch_l2(reinterpret_cast<const float*>(a.Fm) + e0 * 324, (uint32_t)(ne * 324 * 4));
-      tc::prefetch_l2(reinterpret_cast<const float*>(a.Fp) + e0 * 324, (uint32_t)(ne * 324 * 4));
+      tc::prefetch_l2(a.frec + e0 * 4 * FREC, (uint32_t)(ne * 4 * FREC * 4));
     }
     // ---- lift of faces 2 and 3 on the tensor cores (faces 0 and 1 were issued above)
     asm volatile("tcgen05.wait::st.sync.aligned;");

@@ -34,14 +34,24 @@ def test_byte_counts_are_the_arrays_moved():
     assert b["neighbour_kernel"] == dofs + 2 * traces
     padded = 4 * 192 * 4  # face blocks padded to a multiple of 4 floats
     assert b["local_tc_kernel"] == dofs + padded + 16 * 4
-    assert b["neighbour_tc_kernel"] == dofs + 2 * padded + 2 * 4 * 81 * 4 + 16 * 4
+    assert b["neighbour_tc_kernel"] == dofs + 2 * padded + 4 * 32 + 16 * 4
 
 
 def test_peak_arithmetic():
-    assert bench.tf32x3_peak_tflops({"bf16_tflops": 1.0, "bf16_tflops_sustained": 2250.0}) == pytest.approx(
-        2250.0 * 1.1 / 2.25 / 3.0)
-    assert bench.alu_peak_tflops(False, 2070.0) == pytest.approx(152 * 128 * 2 * 2.07e9 / 1e12)
-    assert bench.alu_peak_tflops(True, 2070.0) == pytest.approx(1.25)
+    units = {"tf32_tensor_tflops": 1200.0, "fp32_fma_tflops": 76.0, "fp64_fma_tflops": 1.2}
+    # measured rates: a 3xTF32 product costs three TF32 MMAs
+    assert bench.tf32x3_peak_tflops({"bf16_tflops": 1.0}, units)[0] == pytest.approx(400.0)
+    assert bench.alu_peak_tflops(False, 2070.0, units)[0] == pytest.approx(76.0)
+    assert bench.alu_peak_tflops(True, 2070.0, units)[0] == pytest.approx(1.2)
+    # without them: the burst bf16 rate times the nominal tf32 ratio; lanes x clock; nominal FP64
+    assert bench.tf32x3_peak_tflops({"bf16_tflops": 2250.0})[0] == pytest.approx(2250.0 * 1.1 / 2.25 / 3.0)
+    assert bench.alu_peak_tflops(False, 2070.0, None, 148)[0] == pytest.approx(148 * 128 * 2 * 2.07e9 / 1e12)
+    assert bench.alu_peak_tflops(True, 2070.0)[0] == pytest.approx(1.25)
+
+
+def test_measured_peaks_file_is_read():
+    u = bench.unit_peaks()
+    assert u is not None and u["tf32_tensor_tflops"] > 0 and u["fp32_fma_tflops"] > 0 and u["fp64_fma_tflops"] > 0
 
 
 def test_reference_arm_prints_one_json_line():

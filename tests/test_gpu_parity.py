@@ -149,6 +149,24 @@ def test_free_surface_and_rigid_wall_fp64():
     assert rel_l2(to_oracle_layout(s.get_dofs()), o.Q) <= FP64_TOL
 
 
+def test_free_surface_rigid_wall_absorbing_on_the_tensor_cores():
+    """Free-surface top, rigid-wall bottom and absorbing sides at N=5 in the
+    3xTF32 form: with no gravitational face every element takes both
+    tensor-core kernels, whose neighbour kernel forms each face's Godunov flux
+    (ghost states of the linear boundaries included) in the face frame."""
+    m, mat = small_coupled(rigid_bottom=True)
+    m.face_tag[m.face_tag == syn.TAG_GRAVITY] = syn.TAG_FREE
+    o, s = make_pair(m, mat, 5, precision=2, cfl=0.5)
+    assert int(s.info.tensor_core_updates_per_macro) == m.nt
+    Q0 = random_dofs((m.nt, s.B, 9), 8, N=5)
+    o.Q = Q0.copy()
+    s.set_dofs(to_gpu_layout(Q0))
+    for _ in range(3):
+        o.step_gts()
+    s.advance(3)
+    assert rel_l2(to_oracle_layout(s.get_dofs()), o.Q) <= 2e-5
+
+
 def _warped_periodic(n, a=0.6):
     phi = lambda u: u - a * np.sin(2 * np.pi * u) / (2 * np.pi)
     g = np.linspace(0, 1, n + 1)
