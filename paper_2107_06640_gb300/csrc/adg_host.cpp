@@ -711,9 +711,10 @@ void Ctx::setup() {
   }
   // configure kernels once (outside any stream capture)
   StepArgs a0 = base_args();
-  int rc = launch_local(fp64, N, a0, 0, stream);
-  if (!rc && tc) rc = launch_local_tc(a0, 0, n_sms, stream, false);
-  if (!rc && tc) rc = launch_neighbour_tc(a0, 0, n_sms, stream, false);
+  const Segs none = make_segs(nullptr, 0, 1);
+  int rc = launch_local(fp64, N, a0, none, stream);
+  if (!rc && tc) rc = launch_local_tc(a0, none, n_sms, stream, false);
+  if (!rc && tc) rc = launch_neighbour_tc(a0, none, n_sms, stream, false);
   if (rc) throw Err(ADG_E_CUDA, std::string("kernel configuration: ") + cudaGetErrorString((cudaError_t)rc));
   tick = 0;
   time = 0.0;
@@ -742,75 +743,74 @@ static void taylor_int(int N, double ta, double tb, double* out) {
   }
 }
 
-// Launch the work of tick s of the rate-2 schedule with fine step dtm.
+// Launch the work of tick s of the rate-2 schedule with fine step dtm (Sec.
+// 4.4): first the local phase of every cluster that starts a step at this
+// tick, then the friction solves and the neighbour phase of every cluster
+// that ends one.  Each phase is one launch per kernel kind covering all its
+// clusters (a segment per cluster with that cluster's step and coefficients):
+// the tensor-core kernels take the plain elements, the CUDA-core kernels the
+// rest (all elements without the tensor-core form).
 void Ctx::launch_tick(int s, double dtm) {
   StepArgs a = base_args();
-  for (int c = 0; c < ncl; ++c) {
-    if (s % (1 << c)) continue;
-    const int64_t n = cl_begin[c + 1] - cl_begin[c];
-    if (!n) continue;
-    const double dt = (double)(1 << c) * dtm;
-    a.v_begin = cl_begin[c] * S;
-    a.dt = dt;
-    taylor_int(N, 0.0, dt, a.tcoef);
-    a.btrace_mode = (s % (1 << (c + 1)) == 0) ? 1 : 2;
-    ProfEv ev{0, nullptr, nullptr, 1};
+  for (int phase = 0; phase < 2; ++phase) {
+    Seg tcs[kMaxSeg], ccs[kMaxSeg];
+    int ntc = 0, ncc = 0;
+    bool coarse = false;
+    for (int c = 0; c < ncl; ++c) {
+      const bool active = phase == 0 ? s % (1 << c) == 0 : (s + 1) % (1 << c) == 0;
+      const int64_t n = cl_begin[c + 1] - cl_begin[c];
+      if (!active || !n) continue;
+      const double dt = (double)(1 << c) * dtm;
+      Seg sg{};
+      sg.dt = dt;
+      if (phase == 0) {
+        taylor_int(N, 0.0, dt, sg.tcoef);
+        sg.btrace_mode = (s % (1 << (c + 1)) == 0) ? 1 : 2;
+      } else {
+        // position of this step inside the coarser neighbour's (2x longer) step
+        const int half = ((s + 1) / (1 << c) - 1) % 2;
+        taylor_int(N, half * dt, (half + 1) * dt, sg.ccoef);
+        if (fcl_begin.size() > (size_t)c + 1 && fcl_begin[c + 1] > fcl_begin[c]) launch_rupture_cluster(c, dt);
+      }
+      const int64_t np = tc ? cl_plain[c] : 0;
+      if (np > 0) {
+        Seg t = sg;
+        t.v_begin = cl_begin[c] * S;
+        t.n = np * S;
+        tcs[ntc++] = t;
+        coarse = coarse || cl_tc_coarse[c] != 0;
+      }
+      if (n > np) {
+        Seg t = sg;
+        t.v_begin = (cl_begin[c] + np) * S;
+        t.n = (n - np) * S;
+        ccs[ncc++] = t;
+      }
+    }
+    if (!ntc && !ncc) continue;
+    ProfEv ev{phase, nullptr, nullptr, (ntc > 0) + (ncc > 0)};
     if (prof) {
       CK(cudaEventCreate(&ev.a));
       CK(cudaEventCreate(&ev.b));
       CK(cudaEventRecord(ev.a, stream));
     }
     int rc = 0;
-    if (tc) {
-      // plain elements on the tensor cores, the rest on the CUDA cores
-      const int64_t np = cl_plain[c];
-      ev.launches = (np > 0) + (n > np);
-      if (np > 0) rc = launch_local_tc(a, np * S, n_sms, stream, cl_tc_coarse[c] != 0);
-      if (prof && np > 0) {  // the tensor-core launch alone
+    if (ntc) {
+      const Segs g = make_segs(tcs, ntc, kTileElems);
+      rc = phase == 0 ? launch_local_tc(a, g, n_sms, stream, coarse) : launch_neighbour_tc(a, g, n_sms, stream, coarse);
+      if (prof) {  // the tensor-core launch alone
         CK(cudaEventCreate(&ev.m));
         CK(cudaEventRecord(ev.m, stream));
       }
-      a.v_begin = (cl_begin[c] + np) * S;
-      if (!rc && n > np) rc = launch_local(fp64, N, a, (n - np) * S, stream);
-    } else {
-      rc = launch_local(fp64, N, a, n * S, stream);
+    }
+    if (!rc && ncc) {
+      const Segs g = make_segs(ccs, ncc, 1);
+      rc = phase == 0 ? launch_local(fp64, N, a, g, stream) : launch_neighbour(fp64, N, a, g, stream);
     }
     if (prof) { CK(cudaEventRecord(ev.b, stream)); prof->push_back(ev); }
-    if (rc) throw Err(ADG_E_CUDA, std::string("local kernel: ") + cudaGetErrorString((cudaError_t)rc));
-  }
-  for (int c = 0; c < ncl; ++c) {
-    if ((s + 1) % (1 << c)) continue;
-    const int64_t n = cl_begin[c + 1] - cl_begin[c];
-    if (!n) continue;
-    const double dt = (double)(1 << c) * dtm;
-    // position of this step inside the coarser neighbour's (2x longer) step
-    const int half = ((s + 1) / (1 << c) - 1) % 2;
-    a.v_begin = cl_begin[c] * S;
-    a.dt = dt;
-    taylor_int(N, half * dt, (half + 1) * dt, a.ccoef);
-    if (fcl_begin.size() > (size_t)c + 1 && fcl_begin[c + 1] > fcl_begin[c]) launch_rupture_cluster(c, dt);
-    ProfEv ev{1, nullptr, nullptr, 1};
-    if (prof) {
-      CK(cudaEventCreate(&ev.a));
-      CK(cudaEventCreate(&ev.b));
-      CK(cudaEventRecord(ev.a, stream));
-    }
-    int rc = 0;
-    if (tc) {
-      const int64_t np = cl_plain[c];
-      ev.launches = (np > 0) + (n > np);
-      if (np > 0) rc = launch_neighbour_tc(a, np * S, n_sms, stream, cl_tc_coarse[c] != 0);
-      if (prof && np > 0) {
-        CK(cudaEventCreate(&ev.m));
-        CK(cudaEventRecord(ev.m, stream));
-      }
-      a.v_begin = (cl_begin[c] + np) * S;
-      if (!rc && n > np) rc = launch_neighbour(fp64, N, a, (n - np) * S, stream);
-    } else {
-      rc = launch_neighbour(fp64, N, a, n * S, stream);
-    }
-    if (prof) { CK(cudaEventRecord(ev.b, stream)); prof->push_back(ev); }
-    if (rc) throw Err(ADG_E_CUDA, std::string("neighbour kernel: ") + cudaGetErrorString((cudaError_t)rc));
+    if (rc)
+      throw Err(ADG_E_CUDA, std::string(phase == 0 ? "local kernel: " : "neighbour kernel: ") +
+                                cudaGetErrorString((cudaError_t)rc));
   }
 }
 
@@ -849,17 +849,17 @@ int64_t Ctx::launches_per_macro() const {
   int64_t L = 0;
   const int ticks = 1 << (ncl - 1);
   for (int s = 0; s < ticks; ++s)
-    for (int c = 0; c < ncl; ++c) {
-      if (cl_begin[c + 1] == cl_begin[c]) continue;
-      if (s % (1 << c) == 0) {
+    for (int phase = 0; phase < 2; ++phase) {
+      bool tcl = false, ccl = false;
+      for (int c = 0; c < ncl; ++c) {
         const int64_t n = cl_begin[c + 1] - cl_begin[c];
-        L += tc ? (cl_plain[c] > 0) + (n > cl_plain[c]) : 1;
+        if (!n || (phase == 0 ? s % (1 << c) : (s + 1) % (1 << c))) continue;
+        if (phase == 1 && fcl_begin[c + 1] > fcl_begin[c]) L += 1;  // friction solve per cluster
+        const int64_t np = tc ? cl_plain[c] : 0;
+        tcl = tcl || np > 0;
+        ccl = ccl || n > np;
       }
-      if ((s + 1) % (1 << c) == 0) {
-        const int64_t n = cl_begin[c + 1] - cl_begin[c];
-        L += (fcl_begin[c + 1] > fcl_begin[c]) ? 1 : 0;
-        L += tc ? (cl_plain[c] > 0) + (n > cl_plain[c]) : 1;
-      }
+      L += tcl + ccl;
     }
   return L;
 }

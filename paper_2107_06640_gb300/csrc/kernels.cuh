@@ -57,12 +57,7 @@ struct StepArgs {
   const void* liftT;    // T [4][Bf(n)][B(m)]  lift[f][m][n] stored n-major
   const int* perm;      // [6][Bf]
   const double* gpar;   // [ngslot][GPAR]
-  int64_t v_begin;      // first virtual element of the launch
   int S;                // ensemble size
-  int btrace_mode;      // 0 none, 1 overwrite, 2 accumulate
-  double tcoef[8];      // dt^{k+1}/(k+1)!, k = 0..N (own step)
-  double ccoef[8];      // (tb^{k+1}-ta^{k+1})/(k+1)! on a coarser neighbour's expansion
-  double dt;            // own step (gravity ODE)
   unsigned int* err;    // device error word
   const int* fslot;     // [E][4] 2*fault + side for fault faces, else -1
   const void* drout;    // T [nff*S][2][9][Bf] time-integrated fault flux per side
@@ -79,16 +74,52 @@ struct StepArgs {
 constexpr int FREC = 8;
 enum { FACE_NEIGHBOUR = 0, FACE_FREE = 1, FACE_RIGID = 2, FACE_ABSORB = 3 };
 
+// The clusters of one LTS phase (Sec. 4.4) in a single launch: segment i
+// covers the virtual elements [v_begin, v_begin + n) of one cluster with that
+// cluster's time coefficients, and the launch's work units (tiles of the
+// tensor-core kernels, blocks of the CUDA-core kernels) [first[i], first[i+1]).
+// The launch takes the table by value (kernel parameter space), so a CUDA
+// graph keeps it and no device buffer is involved.
+constexpr int kMaxSeg = 16;
+// virtual elements per tile of the tensor-core kernels (12 x 9 quantities =
+// the 128 rows of one MMA)
+constexpr int kTileElems = 12;
+struct Seg {
+  int64_t v_begin, n;
+  double tcoef[8];   // dt^{k+1}/(k+1)!, k = 0..N (the cluster's own step)
+  double ccoef[8];   // (tb^{k+1}-ta^{k+1})/(k+1)! on a coarser neighbour's expansion
+  double dt;         // the cluster's step (gravity ODE)
+  int btrace_mode;   // 0 none, 1 overwrite, 2 accumulate (LTS buffers)
+};
+struct Segs {
+  int n;                        // segments
+  int64_t first[kMaxSeg + 1];   // first work unit of each segment; first[n] = all units
+  Seg s[kMaxSeg];
+};
+// segment of work unit u (segments are few: a linear scan)
+__host__ __device__ inline int seg_find(const Segs& g, int64_t u) {
+  int i = 0;
+  while (i + 1 < g.n && u >= g.first[i + 1]) ++i;
+  return i;
+}
+// segment of work unit u in a launch that may have several (kMulti) or has one
+template <bool kMulti>
+__host__ __device__ inline int seg_of(const Segs& g, int64_t u) {
+  return kMulti ? seg_find(g, u) : 0;
+}
+// Segs of the given segments with `unit` virtual elements per work unit
+Segs make_segs(const Seg* s, int n, int unit);
+
 // tensor-core (tcgen05, 3xTF32) local kernel, degree 5, FP32 dofs (local_tc.cu),
 // for elements without gravitational faces, fault faces or finer LTS neighbours
 // buffers: the launch's elements include some with an LTS buffer (a coarser neighbour)
-int launch_local_tc(const StepArgs& a, int64_t n_virtual, int n_sms, void* stream, bool buffers);
+int launch_local_tc(const StepArgs& a, const Segs& g, int n_sms, void* stream, bool buffers);
 void pack_local_tc(const double* kt, const double* kvol, const double* efc, float* out);
 int local_tc_floats();
 // tensor-core (tcgen05, 3xTF32) neighbour kernel, degree 5, FP32 dofs
 // (neighbour_tc.cu), for the same elements
 // coarse: the launch's elements include some with a coarser LTS neighbour
-int launch_neighbour_tc(const StepArgs& a, int64_t n_virtual, int n_sms, void* stream, bool coarse);
+int launch_neighbour_tc(const StepArgs& a, const Segs& g, int n_sms, void* stream, bool coarse);
 void pack_lift_tc(const double* lift, float* out);
 int lift_tc_floats();
 
@@ -134,8 +165,8 @@ int launch_rupture(int fp64, int N, const DRArgs& a, void* stream);
 enum { ERR_NAN = 1u, ERR_TIMEOUT = 2u, ERR_NEWTON = 4u };
 
 // host-side launchers (kernels_f64.cu / kernels_f32.cu); return cudaError_t as int
-int launch_local(int fp64, int N, const StepArgs& a, int64_t nblocks, void* stream);
-int launch_neighbour(int fp64, int N, const StepArgs& a, int64_t nblocks, void* stream);
+int launch_local(int fp64, int N, const StepArgs& a, const Segs& g, void* stream);
+int launch_neighbour(int fp64, int N, const StepArgs& a, const Segs& g, void* stream);
 int local_smem_bytes(int fp64, int N);
 
 }  // namespace adg

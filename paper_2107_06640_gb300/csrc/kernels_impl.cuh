@@ -111,7 +111,7 @@ struct Smem {
 };
 
 template <typename T, int N>
-__global__ void __launch_bounds__(kThreads) local_kernel(StepArgs a) {
+__global__ void __launch_bounds__(kThreads) local_kernel(StepArgs a, const __grid_constant__ Segs segs) {
   using S = Smem<T, N>;
   constexpr int P = S::P, B = S::B, Bf = S::Bf, B1 = S::B1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -125,7 +125,8 @@ __global__ void __launch_bounds__(kThreads) local_kernel(StepArgs a) {
   double* sF = reinterpret_cast<double*>(smem_raw + ((S::oEnd * (int)sizeof(T) + 15) / 16) * 16);
 
   const int tid = threadIdx.x, nth = blockDim.x;
-  const int64_t v = a.v_begin + blockIdx.x;
+  const Seg& sg = segs.s[seg_find(segs, blockIdx.x)];
+  const int64_t v = sg.v_begin + ((int64_t)blockIdx.x - segs.first[&sg - segs.s]);
   const int64_t e = v / a.S;
   const int s = (int)(v - e * a.S);
   T* Q = reinterpret_cast<T*>(a.Q) + v * 9 * B;
@@ -195,7 +196,7 @@ __global__ void __launch_bounds__(kThreads) local_kernel(StepArgs a) {
       if (l < nb3(N - k)) {
         T d9[9];
         load9(sD + (doff_rows(k, N) + l) * P, d9);
-        const T c = T(a.tcoef[k]);
+        const T c = T(sg.tcoef[k]);
 #pragma unroll
         for (int p = 0; p < 9; ++p) acc[p] += c * d9[p];
       }
@@ -248,7 +249,7 @@ __global__ void __launch_bounds__(kThreads) local_kernel(StepArgs a) {
   constexpr int FS = face_stride(N);
   T* trace = reinterpret_cast<T*>(a.trace) + v * 4 * FS;
   double* bt = nullptr;
-  if (a.btrace_mode && a.bslot) {
+  if (sg.btrace_mode && a.bslot) {
     const int bs = a.bslot[e];
     if (bs >= 0) bt = a.btrace + ((int64_t)bs * a.S + s) * 36 * Bf;
   }
@@ -272,7 +273,7 @@ __global__ void __launch_bounds__(kThreads) local_kernel(StepArgs a) {
 #pragma unroll
       for (int p = 0; p < 9; ++p) {
         double* b = bt + (f * 9 + p) * Bf + n;
-        *b = (a.btrace_mode == 1 ? 0.0 : *b) + (double)acc[p];
+        *b = (sg.btrace_mode == 1 ? 0.0 : *b) + (double)acc[p];
       }
     }
   }
@@ -334,7 +335,7 @@ __global__ void __launch_bounds__(kThreads) local_kernel(StepArgs a) {
       if (tid < Bf) {
         const int n = tid;
         double* eta = a.eta + ((int64_t)gs * a.S + s) * Bf;
-        const double kappa = gp[4], rg = gp[5], dt = a.dt;
+        const double kappa = gp[4], rg = gp[5], dt = sg.dt;
         const double eta0 = eta[n];
         double c = eta0, e1 = eta0, H = eta0 * dt, pw = 1.0;
         for (int m = 0; m < N + 40; ++m) {
@@ -369,7 +370,7 @@ struct SmemN {
 };
 
 template <typename T, int N>
-__global__ void __launch_bounds__(kThreads) neighbour_kernel(StepArgs a) {
+__global__ void __launch_bounds__(kThreads) neighbour_kernel(StepArgs a, const __grid_constant__ Segs segs) {
   constexpr int P = Pad<T>::P, B = nb3(N), Bf = nb2(N);
   __shared__ __align__(16) T sVo[4 * Bf * P];  // own traces [f][n][p]
   __shared__ __align__(16) T sVn[4 * Bf * P];  // neighbours' traces in this face's node order
@@ -380,7 +381,8 @@ __global__ void __launch_bounds__(kThreads) neighbour_kernel(StepArgs a) {
   __shared__ int sKind[4];
   __shared__ int sGrav[4];
   const int tid = threadIdx.x, nth = blockDim.x;
-  const int64_t v = a.v_begin + blockIdx.x;
+  const Seg& sg = segs.s[seg_find(segs, blockIdx.x)];
+  const int64_t v = sg.v_begin + ((int64_t)blockIdx.x - segs.first[&sg - segs.s]);
   const int64_t e = v / a.S;
   const int s = (int)(v - e * a.S);
   const T* liftT = reinterpret_cast<const T*>(a.liftT);
@@ -420,7 +422,7 @@ __global__ void __launch_bounds__(kThreads) neighbour_kernel(StepArgs a) {
         const T* dt = reinterpret_cast<const T*>(a.dtrace) + ((int64_t)ds * a.S + s) * (N + 1) * 9 * Bf;
         T acc = T(0);
 #pragma unroll
-        for (int k = 0; k <= N; ++k) acc += T(a.ccoef[k]) * dt[(k * 9 + p) * Bf + src];
+        for (int k = 0; k <= N; ++k) acc += T(sg.ccoef[k]) * dt[(k * 9 + p) * Bf + src];
         val = acc;
       }
     }
@@ -499,26 +501,28 @@ __global__ void __launch_bounds__(kThreads) neighbour_kernel(StepArgs a) {
 }
 
 template <typename T, int N>
-int launch_local_t(const StepArgs& a, int64_t nblocks, cudaStream_t st) {
+int launch_local_t(const StepArgs& a, const Segs& g, cudaStream_t st) {
+  const int64_t nblocks = g.n ? g.first[g.n] : 0;
   constexpr int bytes = Smem<T, N>::bytes;
   const int rc = configure_on_device((const void*)local_kernel<T, N>, [] {
     return cudaFuncSetAttribute(local_kernel<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   });
   if (rc) return rc;
   if (nblocks <= 0) return 0;
-  local_kernel<T, N><<<(unsigned)nblocks, kThreads, bytes, st>>>(a);
+  local_kernel<T, N><<<(unsigned)nblocks, kThreads, bytes, st>>>(a, g);
   return (int)cudaGetLastError();
 }
 
 template <typename T, int N>
-int launch_neighbour_t(const StepArgs& a, int64_t nblocks, cudaStream_t st) {
+int launch_neighbour_t(const StepArgs& a, const Segs& g, cudaStream_t st) {
+  const int64_t nblocks = g.n ? g.first[g.n] : 0;
   if (nblocks <= 0) return 0;
-  neighbour_kernel<T, N><<<(unsigned)nblocks, kThreads, 0, st>>>(a);
+  neighbour_kernel<T, N><<<(unsigned)nblocks, kThreads, 0, st>>>(a, g);
   return (int)cudaGetLastError();
 }
 
 template <typename T>
-int dispatch_local(int N, const StepArgs& a, int64_t nb, cudaStream_t st) {
+int dispatch_local(int N, const StepArgs& a, const Segs& nb, cudaStream_t st) {
   switch (N) {
     case 1: return launch_local_t<T, 1>(a, nb, st);
     case 2: return launch_local_t<T, 2>(a, nb, st);
@@ -529,7 +533,7 @@ int dispatch_local(int N, const StepArgs& a, int64_t nb, cudaStream_t st) {
   return (int)cudaErrorInvalidValue;
 }
 template <typename T>
-int dispatch_neighbour(int N, const StepArgs& a, int64_t nb, cudaStream_t st) {
+int dispatch_neighbour(int N, const StepArgs& a, const Segs& nb, cudaStream_t st) {
   switch (N) {
     case 1: return launch_neighbour_t<T, 1>(a, nb, st);
     case 2: return launch_neighbour_t<T, 2>(a, nb, st);

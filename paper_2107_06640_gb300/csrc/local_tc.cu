@@ -41,7 +41,7 @@ namespace {
 
 constexpr int B = 56, B1 = 35, BF = 21;
 constexpr int FS = face_stride(5);  // 192 floats per face block of the trace array
-constexpr int TE = 12;          // elements per tile
+constexpr int TE = kTileElems;  // elements per tile
 constexpr int kThreadsL = 512;  // two tiles in flight, two warpgroups (halves) per tile
 constexpr int kWaitIters = 1 << 24;
 // trace staging: one face of a warp pair's three elements, element blocks of
@@ -72,6 +72,15 @@ struct LImg {
 };
 static_assert(LImg::bytes + 2 * (2 * 128 + 4 * 2 * kTB) * 4 + 64 <= 232448,
               "operands exceed the shared memory of one CTA");
+
+// the kernel's shared memory besides the operand image (dynamic): per slot the
+// MMA barrier, abort flag, rows 8, 9 of D^3 handed from half 1 to half 0, and
+// per warp pair two trace staging buffers
+__shared__ __align__(8) uint64_t s_mbar[2];
+__shared__ int s_abort[2];
+__shared__ float s_X[2][2 * 128];
+__shared__ __align__(16) float s_T[2][4][2 * kTB];
+extern __shared__ __align__(1024) unsigned char smem_raw[];
 
 // per-warpgroup TMEM columns: A hi [0, 64), A lo [64, 128), accumulators [128, 256)
 constexpr uint32_t cAh = 0, cAl = 64, cAcc = 128;
@@ -168,47 +177,34 @@ __device__ __forceinline__ void warp_pair_bar(int slot, int w) {
 }
 
 // Everything one thread needs to work on the tiles of its slot.
+// (Arrays and sizes come from the launch's StepArgs, read where they are used.)
 struct Lane {
-  float* Q;
-  float* trace;
-  const float* par;
-  unsigned int* err;
-  int64_t v_begin, n_virtual;
-  int S;
-  float tcf[6];       // dt^{k+1}/(k+1)!, k = 0..5
+  float tcf[6];       // dt^{k+1}/(k+1)!, k = 0..5, of the tile's cluster
   int slot, t, w, lane;
   uint32_t tbase, trow, sbase;
-  const float* k3;
-  const float* k4;
-  float* sX;          // [128][2] rows 8, 9 of D^3 handed from half 1 to half 0
-  float* sT;          // [2][3][kTS] two buffers: one face of this warp's three elements' traces
-  double* btrace;     // LTS buffers of elements with a coarser neighbour (FP64)
-  const int* bslot;   // [E] buffer slot or -1 (null: no buffers)
-  int btrace_mode;    // 0 none, 1 overwrite, 2 accumulate
-  uint64_t* mbar;     // this slot's barrier
-  int* abort;         // this slot's abort flag
+  int btrace_mode;    // of the tile's cluster: 0 none, 1 overwrite, 2 accumulate (LTS buffers)
   uint32_t phase;
 };
 
 // One tensor-core round of a slot: both halves' A stores made visible, MMAs
 // issued by thread 0 of half 0, bounded wait for their completion.
 template <int H, class F>
-__device__ __forceinline__ bool pair_round(Lane& L, F&& issue_fn) {
+__device__ __forceinline__ bool pair_round(Lane& L, unsigned int* err, F&& issue_fn) {
   asm volatile("tcgen05.wait::st.sync.aligned;");
   tc::fence_before();
   pair_bar(L.slot);
   tc::fence_after();
   if (H == 0 && L.t == 0) {
     issue_fn();
-    tc::commit(L.mbar);
-    if (!tc::mbar_wait(L.mbar, L.phase, kWaitIters)) {
-      atomicOr(L.err, ERR_TIMEOUT);
-      *L.abort = 1;
+    tc::commit(&s_mbar[L.slot]);
+    if (!tc::mbar_wait(&s_mbar[L.slot], L.phase, kWaitIters)) {
+      atomicOr(err, ERR_TIMEOUT);
+      s_abort[L.slot] = 1;
     }
   }
   pair_bar(L.slot);
-  const bool ok = !*(volatile int*)L.abort;
-  if (ok) tc::mbar_wait(L.mbar, L.phase, 1 << 20);  // observe the completed phase in every thread
+  const bool ok = !*(volatile int*)&s_abort[L.slot];
+  if (ok) tc::mbar_wait(&s_mbar[L.slot], L.phase, 1 << 20);  // observe the completed phase in every thread
   L.phase ^= 1u;
   tc::fence_after();
   return ok;
@@ -217,30 +213,35 @@ __device__ __forceinline__ bool pair_round(Lane& L, F&& issue_fn) {
 // One tile, the share of half H (8-column chunks c with c % 2 == H); false
 // after a timed-out wait.
 // kBuf: some elements of the launch have an LTS buffer (a coarser neighbour)
-template <int H, bool kBuf>
-__device__ __forceinline__ bool local_tile(Lane& L, int64_t tile) {
-  const int64_t v0 = L.v_begin + tile * TE;
-  const int64_t nrem = L.n_virtual - tile * TE;
+// tile: index within its segment; gtile: index among all tiles of the launch
+// (kMulti: the launch has several segments)
+template <int H, bool kBuf, bool kMulti>
+__device__ __forceinline__ bool local_tile(Lane& L, const StepArgs& a, const Segs& g, int64_t gtile, int64_t v_begin,
+                                           int64_t n_virtual, int64_t tile) {
+  float* const Q = reinterpret_cast<float*>(a.Q);
+  const int64_t v0 = v_begin + tile * TE;
+  const int64_t nrem = n_virtual - tile * TE;
   const int nE = (int)(nrem < TE ? nrem : TE);
   const int jj = L.lane / 9, p = L.lane - 9 * (L.lane / 9);
   const int i = 3 * L.w + jj;
   const bool valid = L.lane < 27 && i < nE;
   const int64_t v = v0 + (valid ? i : 0);
-  const int64_t e = v / L.S;
+  const int64_t e = v / a.S;
   Star st;
-  star_setup(L.lane, valid, L.par + e * PAR, st);
+  star_setup(L.lane, valid, reinterpret_cast<const float*>(a.par) + e * PAR, st);
   const uint32_t trow = L.trow, tbase = L.tbase, sbase = L.sbase;
 
-  // the next tile of this slot into L2 while this one is worked on
+  // the tile after the next of this slot into L2 while this one is worked on
   if (H == 0 && L.t == 0) {
-    const int64_t nt = tile + (int64_t)gridDim.x * 4;
-    if (nt * TE < L.n_virtual) {
-      const int64_t nrem2 = L.n_virtual - nt * TE;
-      tc::prefetch_l2(L.Q + (L.v_begin + nt * TE) * 9 * B, (uint32_t)((nrem2 < TE ? nrem2 : TE) * 9 * B * 4));
+    const int64_t t2 = gtile + (int64_t)gridDim.x * 4;
+    if (t2 < g.first[g.n]) {
+      const int i2 = seg_of<kMulti>(g, t2);
+      const int64_t l2 = t2 - g.first[i2], rem2 = g.s[i2].n - l2 * TE;
+      tc::prefetch_l2(Q + (g.s[i2].v_begin + l2 * TE) * 9 * B, (uint32_t)((rem2 < TE ? rem2 : TE) * 9 * B * 4));
     }
   }
   // ---- D^0 = Q row: I = dt Q, A = Q
-  float* Qrow = L.Q + (v * 9 + p) * B;
+  float* Qrow = Q + (v * 9 + p) * B;
   float I[B];
 #pragma unroll
   for (int c = H; c < B / 8; c += 2) {
@@ -257,19 +258,19 @@ __device__ __forceinline__ bool local_tile(Lane& L, int64_t tile) {
     tc::st_split8(trow + cAh + 8 * c, trow + cAl + 8 * c, x);
   }
   // ---- levels 0, 1, 2 on the tensor cores
-  if (!pair_round<H>(L, [&] {
+  if (!pair_round<H>(L, a.err, [&] {
         tc::mma3_ts<kN0, kK0>(tbase + cAcc, tbase + cAh, tbase + cAl, sbase + 4 * LImg::oP0,
                               sbase + 4 * (LImg::oP0 + LImg::sP0), false);
       }))
     return false;
   level_epilogue<H, kM0, kM0p, true>(trow + cAcc, trow + cAh, trow + cAl, st, L.tcf[1], I, nullptr);
-  if (!pair_round<H>(L, [&] {
+  if (!pair_round<H>(L, a.err, [&] {
         tc::mma3_ts<kN1, kK1>(tbase + cAcc, tbase + cAh, tbase + cAl, sbase + 4 * LImg::oP1,
                               sbase + 4 * (LImg::oP1 + LImg::sP1), false);
       }))
     return false;
   level_epilogue<H, kM1, kM1p, true>(trow + cAcc, trow + cAh, trow + cAl, st, L.tcf[2], I, nullptr);
-  if (!pair_round<H>(L, [&] {
+  if (!pair_round<H>(L, a.err, [&] {
         tc::mma3_ts<kN2, kK2>(tbase + cAcc, tbase + cAh, tbase + cAl, sbase + 4 * LImg::oP2,
                               sbase + 4 * (LImg::oP2 + LImg::sP2), false);
       }))
@@ -278,15 +279,15 @@ __device__ __forceinline__ bool local_tile(Lane& L, int64_t tile) {
   level_epilogue<H, kM2, kM2p, false>(trow + cAcc, trow + cAh, trow + cAl, st, L.tcf[3], I, d3);
   // ---- levels 3 and 4 (half 0, with rows 8 and 9 of D^3 from half 1)
   if (H == 1) {
-    L.sX[2 * L.t] = d3[8];
-    L.sX[2 * L.t + 1] = d3[9];
+    s_X[L.slot][2 * L.t] = d3[8];
+    s_X[L.slot][2 * L.t + 1] = d3[9];
   }
   pair_bar(L.slot);
   if (H == 0) {
-    d3[8] = L.sX[2 * L.t];
-    d3[9] = L.sX[2 * L.t + 1];
-    const float* k3 = L.k3;
-    const float* k4 = L.k4;
+    d3[8] = s_X[L.slot][2 * L.t];
+    d3[9] = s_X[L.slot][2 * L.t + 1];
+    const float* k3 = reinterpret_cast<const float*>(smem_raw) + LImg::oK3;
+    const float* k4 = reinterpret_cast<const float*>(smem_raw) + LImg::oK4;
     float d4[4];
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
@@ -313,7 +314,7 @@ __device__ __forceinline__ bool local_tile(Lane& L, int64_t tile) {
   // ---- face traces: T = I E^T (N = 4 x 21)
 #pragma unroll
   for (int c = H; c < B / 8; c += 2) tc::st_split8(trow + cAh + 8 * c, trow + cAl + 8 * c, I + 8 * c);
-  if (!pair_round<H>(L, [&] {
+  if (!pair_round<H>(L, a.err, [&] {
         tc::mma3_ts<kNT, kK0>(tbase + cAcc, tbase + cAh, tbase + cAl, sbase + 4 * LImg::oT,
                               sbase + 4 * (LImg::oT + LImg::sT), false);
       }))
@@ -331,10 +332,10 @@ __device__ __forceinline__ bool local_tile(Lane& L, int64_t tile) {
     tc::ld3x8(trow + cAcc + 8 * (H + 6), trow + cAcc + 8 * (H + 8), trow + cAcc + 8 * (H == 0 ? 10 : 9), tv + 24);
     // an element with a coarser neighbour also adds its four face traces to
     // its LTS buffer, in FP64 (overwrite at the first of the two steps)
-    if (kBuf && L.btrace_mode && L.bslot && valid) {
-      const int bs = L.bslot[e];
+    if (kBuf && L.btrace_mode && a.bslot && valid) {
+      const int bs = a.bslot[e];
       if (bs >= 0) {
-        double* bt = L.btrace + ((int64_t)bs * L.S + (v - e * L.S)) * 36 * BF;
+        double* bt = a.btrace + ((int64_t)bs * a.S + (v - e * a.S)) * 36 * BF;
 #pragma unroll
         for (int cj = 0; cj < (H == 0 ? 6 : 5); ++cj) {
 #pragma unroll
@@ -351,7 +352,7 @@ __device__ __forceinline__ bool local_tile(Lane& L, int64_t tile) {
     }
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
-      float* sTf = L.sT + (f & 1) * kTB;
+      float* sTf = s_T[L.slot][L.w] + (f & 1) * kTB;
 #pragma unroll
       for (int cj = 0; cj < (H == 0 ? 6 : 5); ++cj) {
         const int c = H + 2 * cj;
@@ -369,7 +370,8 @@ __device__ __forceinline__ bool local_tile(Lane& L, int64_t tile) {
       warp_pair_bar(L.slot, L.w);
       if (copier) {
         for (int ej = 0; ej < nmine; ++ej)
-          tc::bulk_store(L.trace + ((v0 + 3 * L.w + ej) * 4 + f) * FS, sTf + ej * kTS, FS * 4);
+          tc::bulk_store(reinterpret_cast<float*>(a.trace) + ((v0 + 3 * L.w + ej) * 4 + f) * FS, sTf + ej * kTS,
+                         FS * 4);
         tc::bulk_commit();
       }
     }
@@ -391,7 +393,7 @@ __device__ __forceinline__ bool local_tile(Lane& L, int64_t tile) {
     }
   }
   constexpr uint32_t cV = 80;  // volume accumulator: axis a, basis m at column 80 + 56 a + m
-  if (!pair_round<H>(L, [&] {
+  if (!pair_round<H>(L, a.err, [&] {
         tc::mma3_ts<kNV, 40>(tbase + cV, tbase + 0, tbase + 40, sbase + 4 * LImg::oV,
                              sbase + 4 * (LImg::oV + LImg::sV), false);
       }))
@@ -417,15 +419,12 @@ __device__ __forceinline__ bool local_tile(Lane& L, int64_t tile) {
   return true;
 }
 
-template <bool kBuf>
-__global__ void __launch_bounds__(kThreadsL, 1) local_tc_kernel(StepArgs a, int64_t n_virtual) {
-  extern __shared__ __align__(1024) unsigned char smem_raw[];
+template <bool kBuf, bool kMulti>
+__global__ void __launch_bounds__(kThreadsL, 1) local_tc_kernel(StepArgs a, const __grid_constant__ Segs g) {
   float* sm = reinterpret_cast<float*>(smem_raw);
   __shared__ uint32_t tmem_base;
-  __shared__ __align__(8) uint64_t mbar[2];
-  __shared__ int s_abort[2];
-  __shared__ float sX[2][2 * 128];
-  __shared__ __align__(16) float sT[2][4][2 * kTB];
+  uint64_t* mbar = s_mbar;
+  float (*sT)[4][2 * kTB] = s_T;
 
   const int tid = threadIdx.x, slot = tid >> 8, half = (tid >> 7) & 1;
   {
@@ -445,15 +444,6 @@ __global__ void __launch_bounds__(kThreadsL, 1) local_tc_kernel(StepArgs a, int6
   tc::fence_after();
 
   Lane L;
-  L.Q = reinterpret_cast<float*>(a.Q);
-  L.trace = reinterpret_cast<float*>(a.trace);
-  L.par = reinterpret_cast<const float*>(a.par);
-  L.err = a.err;
-  L.v_begin = a.v_begin;
-  L.S = a.S;
-#pragma unroll
-  for (int k = 0; k < 6; ++k) L.tcf[k] = (float)a.tcoef[k];
-  L.n_virtual = n_virtual;
   L.slot = slot;
   L.t = tid & 127;
   L.w = L.t >> 5;
@@ -461,19 +451,20 @@ __global__ void __launch_bounds__(kThreadsL, 1) local_tc_kernel(StepArgs a, int6
   L.tbase = tmem_base + (uint32_t)slot * 256u;
   L.trow = L.tbase + ((uint32_t)(32 * L.w) << 16);
   L.sbase = tc::smem_u32(sm);
-  L.k3 = sm + LImg::oK3;
-  L.k4 = sm + LImg::oK4;
-  L.sX = sX[slot];
-  L.sT = sT[slot][(tid & 127) >> 5];
-  L.btrace = a.btrace;
-  L.bslot = a.bslot;
-  L.btrace_mode = a.btrace_mode;
-  L.mbar = &mbar[slot];
-  L.abort = &s_abort[slot];
+
+
+
   L.phase = 0;
-  const int64_t ntiles = (n_virtual + TE - 1) / TE;
+  // tiles of all segments (the clusters of this phase) in one sequence
+  const int64_t ntiles = g.first[g.n];
   for (int64_t tile = (int64_t)blockIdx.x * 2 + slot; tile < ntiles; tile += (int64_t)gridDim.x * 2) {
-    const bool ok = half == 0 ? local_tile<0, kBuf>(L, tile) : local_tile<1, kBuf>(L, tile);
+    const Seg& sg = g.s[seg_of<kMulti>(g, tile)];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) L.tcf[k] = (float)sg.tcoef[k];
+    L.btrace_mode = sg.btrace_mode;
+    const int64_t lt = tile - g.first[&sg - g.s];
+    const bool ok = half == 0 ? local_tile<0, kBuf, kMulti>(L, a, g, tile, sg.v_begin, sg.n, lt)
+                              : local_tile<1, kBuf, kMulti>(L, a, g, tile, sg.v_begin, sg.n, lt);
     if (!ok) break;
   }
   // after a timed-out wait, give this slot's MMAs in flight a bounded chance
@@ -488,23 +479,22 @@ __global__ void __launch_bounds__(kThreadsL, 1) local_tc_kernel(StepArgs a, int6
 
 }  // namespace
 
-int launch_local_tc(const StepArgs& a, int64_t n_virtual, int n_sms, void* stream, bool buffers) {
-  const int rc = configure_on_device((const void*)local_tc_kernel<false>, [] {
-    cudaError_t ce = cudaFuncSetAttribute(local_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          LImg::bytes);
-    if (ce == cudaSuccess)
-      ce = cudaFuncSetAttribute(local_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, LImg::bytes);
+int launch_local_tc(const StepArgs& a, const Segs& g, int n_sms, void* stream, bool buffers) {
+  const int rc = configure_on_device((const void*)local_tc_kernel<false, false>, [] {
+    cudaError_t ce = cudaSuccess;
+    for (auto k : {local_tc_kernel<false, false>, local_tc_kernel<true, false>, local_tc_kernel<false, true>,
+                   local_tc_kernel<true, true>})
+      if (ce == cudaSuccess) ce = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, LImg::bytes);
     return ce;
   });
   if (rc) return rc;
-  if (n_virtual <= 0) return 0;
-  const int64_t ntiles = (n_virtual + TE - 1) / TE;
+  const int64_t ntiles = g.n ? g.first[g.n] : 0;
+  if (ntiles <= 0) return 0;
   const int64_t want = (ntiles + 1) / 2;
   const unsigned grid = (unsigned)(want < n_sms ? want : n_sms);
-  if (buffers)
-    local_tc_kernel<true><<<grid, kThreadsL, LImg::bytes, (cudaStream_t)stream>>>(a, n_virtual);
-  else
-    local_tc_kernel<false><<<grid, kThreadsL, LImg::bytes, (cudaStream_t)stream>>>(a, n_virtual);
+  auto k = g.n > 1 ? (buffers ? local_tc_kernel<true, true> : local_tc_kernel<false, true>)
+                   : (buffers ? local_tc_kernel<true, false> : local_tc_kernel<false, false>);
+  k<<<grid, kThreadsL, LImg::bytes, (cudaStream_t)stream>>>(a, g);
   return (int)cudaGetLastError();
 }
 

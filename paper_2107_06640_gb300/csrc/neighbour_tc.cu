@@ -41,7 +41,7 @@ namespace adg {
 namespace {
 
 constexpr int B = 56, BF = 21;
-constexpr int TE = 12;
+constexpr int TE = kTileElems;
 constexpr int kThreadsN = 512;  // two tiles in flight, two warpgroups (halves) per tile
 constexpr int kWaitIters = 1 << 24;
 constexpr int kK = 96;          // 4 faces x 24 columns (21 nodes + 3 zero)
@@ -240,8 +240,8 @@ __device__ __forceinline__ void face_flux(const float* co, const float qm[9], co
 // kOne: one scenario (S = 1), where a virtual element is its element and the
 // 64-bit divisions by S drop out; kCoarse: some faces of the launch have a
 // coarser LTS neighbour (without, their code stays out of the kernel)
-template <bool kOne, bool kCoarse>
-__global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, int64_t n_virtual) {
+template <bool kOne, bool kCoarse, bool kMulti>
+__global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, const __grid_constant__ Segs g) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   float* sm = reinterpret_cast<float*>(smem_raw);
   int* sPerm = reinterpret_cast<int*>(sm + NImg::oPerm);
@@ -285,11 +285,22 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
   const int jj = lane / 9, p = lane - 9 * (lane / 9);
   const int S = kOne ? 1 : a.S;
   const float* dtrace = reinterpret_cast<const float*>(a.dtrace);
-  float cc[6];  // the coarser neighbours' expansion over this step's sub-interval
-#pragma unroll
-  for (int k = 0; k < 6; ++k) cc[k] = (float)a.ccoef[k];
   auto elem = [&](int64_t vv) -> int64_t { return kOne ? vv : vv / S; };  // element of a virtual element
-  const int64_t ntiles = (n_virtual + TE - 1) / TE;
+  // tiles of all segments (the clusters of this phase) in one sequence: tile
+  // tl starts at virtual element pv0 with prem virtual elements left in its
+  // segment, whose coarser neighbours' expansion over this step's
+  // sub-interval has the coefficients cc
+  const int64_t ntiles = g.first[g.n];
+  auto tile_at = [&](int64_t tl, int64_t& pv0, int64_t& prem, float* cc) {
+    const Seg& sg = g.s[seg_of<kMulti>(g, tl)];
+    const int64_t lt = tl - g.first[&sg - g.s];
+    pv0 = sg.v_begin + lt * TE;
+    prem = sg.n - lt * TE;
+    if (cc) {
+#pragma unroll
+      for (int k = 0; k < 6; ++k) cc[k] = (float)sg.ccoef[k];
+    }
+  };
   uint32_t phase = 0;
   float bad = 0.f;  // stays 0 while every updated dof is finite (x * 0 is NaN for x = inf, NaN)
 
@@ -301,7 +312,8 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
   auto meta_load = [&](int64_t tl, int& info, int& nbe) {
     info = 0;
     nbe = 0;
-    const int64_t pv0 = a.v_begin + tl * TE, prem = n_virtual - tl * TE;
+    int64_t pv0, prem;
+    tile_at(tl, pv0, prem, nullptr);
     if (u < 4 * TE) {
       const int f = u / TE, ei = u - f * TE;
       if (ei < prem) {
@@ -312,7 +324,9 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
     }
   };
   auto prefetch = [&](int64_t tl, int info, int nbe) {
-    const int64_t pv0 = a.v_begin + tl * TE, prem = n_virtual - tl * TE;
+    int64_t pv0, prem;
+    float cc[6];
+    tile_at(tl, pv0, prem, kCoarse ? cc : nullptr);
     const int pnE = (int)(prem < TE ? prem : TE);
     if (u < 4 * TE) {
       const int ei = u - (u / TE) * TE;
@@ -354,8 +368,9 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
     const int64_t next = tile + (int64_t)gridDim.x * 2;
     int info_n = 0, nbe_n = 0;  // the next tile's neighbour information, needed after the faces
     if (next < ntiles) meta_load(next, info_n, nbe_n);
-    const int64_t v0 = a.v_begin + tile * TE;
-    const int64_t nrem = n_virtual - tile * TE;
+    int64_t v0, nrem;
+    float cc[6];
+    tile_at(tile, v0, nrem, kCoarse ? cc : nullptr);
     const int nE = (int)(nrem < TE ? nrem : TE);
     const int i = 3 * w + jj;
     const bool valid = lane < 27 && i < nE;
@@ -449,7 +464,8 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
     // and the tile after it into L2
     const int64_t next2 = next + (int64_t)gridDim.x * 2;
     if (u == 0 && next2 < ntiles) {
-      const int64_t q0 = a.v_begin + next2 * TE, rem2 = n_virtual - next2 * TE;
+      int64_t q0, rem2;
+      tile_at(next2, q0, rem2, nullptr);
       const uint32_t n2 = (uint32_t)(rem2 < TE ? rem2 : TE);
       tc::prefetch_l2(reinterpret_cast<const float*>(a.Q) + q0 * 9 * B, n2 * 9 * B * 4);
       tc::prefetch_l2(trace + q0 * 4 * kFS, n2 * 4 * kFS * 4);
@@ -507,22 +523,26 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
 
 }  // namespace
 
-int launch_neighbour_tc(const StepArgs& a, int64_t n_virtual, int n_sms, void* stream, bool coarse) {
-  const int rc = configure_on_device((const void*)neighbour_tc_kernel<true, false>, [] {
+int launch_neighbour_tc(const StepArgs& a, const Segs& g, int n_sms, void* stream, bool coarse) {
+  const int rc = configure_on_device((const void*)neighbour_tc_kernel<true, false, false>, [] {
     cudaError_t ce = cudaSuccess;
-    for (auto k : {neighbour_tc_kernel<true, false>, neighbour_tc_kernel<false, false>,
-                   neighbour_tc_kernel<true, true>, neighbour_tc_kernel<false, true>})
+    for (auto k : {neighbour_tc_kernel<true, false, false>, neighbour_tc_kernel<false, false, false>,
+                   neighbour_tc_kernel<true, true, false>, neighbour_tc_kernel<false, true, false>,
+                   neighbour_tc_kernel<true, false, true>, neighbour_tc_kernel<false, false, true>,
+                   neighbour_tc_kernel<true, true, true>, neighbour_tc_kernel<false, true, true>})
       if (ce == cudaSuccess) ce = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, NImg::bytes);
     return ce;
   });
   if (rc) return rc;
-  if (n_virtual <= 0) return 0;
-  const int64_t ntiles = (n_virtual + TE - 1) / TE;
+  const int64_t ntiles = g.n ? g.first[g.n] : 0;
+  if (ntiles <= 0) return 0;
   const int64_t want = (ntiles + 1) / 2;
   const unsigned grid = (unsigned)(want < n_sms ? want : n_sms);
-  auto k = a.S == 1 ? (coarse ? neighbour_tc_kernel<true, true> : neighbour_tc_kernel<true, false>)
-                    : (coarse ? neighbour_tc_kernel<false, true> : neighbour_tc_kernel<false, false>);
-  k<<<grid, kThreadsN, NImg::bytes, (cudaStream_t)stream>>>(a, n_virtual);
+  auto k = g.n > 1 ? (a.S == 1 ? (coarse ? neighbour_tc_kernel<true, true, true> : neighbour_tc_kernel<true, false, true>)
+                              : (coarse ? neighbour_tc_kernel<false, true, true> : neighbour_tc_kernel<false, false, true>))
+                   : (a.S == 1 ? (coarse ? neighbour_tc_kernel<true, true, false> : neighbour_tc_kernel<true, false, false>)
+                              : (coarse ? neighbour_tc_kernel<false, true, false> : neighbour_tc_kernel<false, false, false>));
+  k<<<grid, kThreadsN, NImg::bytes, (cudaStream_t)stream>>>(a, g);
   return (int)cudaGetLastError();
 }
 

@@ -80,18 +80,20 @@ extern "C" int adg_step_noalloc(adg_ctx* ctx, void* d_Q, int n_steps, void* stre
   adg::StepArgs a = c.base_args();
   a.Q = d_Q;
   a.trace = scratch;
-  a.v_begin = 0;
-  a.btrace_mode = 0;
-  a.dt = c.dtmin;
+  adg::Seg sg{};  // the whole mesh, one global step of dt_min
+  sg.v_begin = 0;
+  sg.n = c.nt;
+  sg.dt = c.dtmin;
   double fa = 0.0, fb = c.dtmin, fac = 1.0;
   for (int k = 0; k <= c.N; ++k) {
     fac *= (k + 1);
-    a.tcoef[k] = (fb - fa) / fac;
+    sg.tcoef[k] = (fb - fa) / fac;
     fb *= c.dtmin;
   }
+  const adg::Segs g = adg::make_segs(&sg, 1, 1);
   for (int i = 0; i < n_steps; ++i) {
-    int rc = adg::launch_local(c.fp64, c.N, a, c.nt, st);
-    if (!rc) rc = adg::launch_neighbour(c.fp64, c.N, a, c.nt, st);
+    int rc = adg::launch_local(c.fp64, c.N, a, g, st);
+    if (!rc) rc = adg::launch_neighbour(c.fp64, c.N, a, g, st);
     if (rc) {
       c.last_error = std::string("adg_step_noalloc: launch failed: ") + cudaGetErrorString((cudaError_t)rc);
       return ADG_E_CUDA;
