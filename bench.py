@@ -378,6 +378,8 @@ def run_other_workload(args):
                           "n_tets": s.nt, "ensemble": S, "hydrostatic_start_s": t_hot}
         line["dtype"] = "f32 (3xTF32 tensor-core products)"
     t_setup = time.perf_counter() - t_setup
+    ch, tms = _lib.adg_autotune(s.ctx, reps=1)
+    line["autotune"] = {"choice": [int(x) for x in ch], "ms_per_candidate": tms.round(3).tolist()}
     ms, clk = _timed_advance(s, steps, warm, stream, torch, args.workload)
     line.update({"value": upd * steps / (ms * 1e-3), "steps": steps, "ms_per_step": ms / steps, "clocks": clk,
                  "setup_s": t_setup})
@@ -510,6 +512,13 @@ def main():
         s.set_dofs(Q0)
         s.set_eta(np.zeros((int(s.info.n_gravity_faces), 1, s.Bf)))
         upd = int(s.info.updates_per_macro)
+        tune = None
+        if prec != pkg.ADG_FP64:  # launch shapes by the library's autotuner (FP64 keeps the defaults)
+            ch, tms = pkg._lib.adg_autotune(s.ctx, reps=2)
+            tune = {"choice": {"cc_local_threads": int(ch[0]), "cc_neighbour_threads": int(ch[1]),
+                               "tc_local_tiles_per_sweep": int(ch[2]), "tc_neighbour_tiles_per_sweep": int(ch[3])},
+                    "ms_per_candidate": tms.round(4).tolist(),
+                    "candidates": [[64, 128, 256], [64, 128, 256], [1, 2, 4], [1, 2, 4]]}
         s.advance(warm)
         barrier()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -521,7 +530,7 @@ def main():
         ms = max_over_ranks(ev0.elapsed_time(ev1))
         # per-kernel durations (CUDA events on the library stream)
         kms, kcnt = pkg._lib.adg_profile(s.ctx, 2)
-        res[prec] = dict(solver=s, ms=ms, steps=steps, upd=upd, kms=kms, kcnt=kcnt,
+        res[prec] = dict(solver=s, ms=ms, steps=steps, upd=upd, kms=kms, kcnt=kcnt, tune=tune,
                          clocks=cs.summary(local), launches=int(kcnt[:3].sum() // 2),
                          advanced=warm + steps + 2)
         if prec not in (HEAD, pkg.ADG_FP64):
@@ -667,6 +676,7 @@ def main():
                 "host_double_arrays": {"value": e2e64_val, "unit": UNIT,
                                        "note": "adg_set_dofs + adg_advance(1) + adg_get_dofs, conversion on the host"}},
         "gpu_launches": r32["launches"] * r32["steps"],
+        "autotune": r32["tune"],
     }
     if rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline()

@@ -269,6 +269,29 @@ int adg_profile(adg_ctx* ctx, int n_macro, double* ms, int64_t* launches);
  *    adg_sync() on the context. */
 int adg_step_noalloc(adg_ctx* ctx, void* d_Q, int n_steps, void* stream);
 
+/* Autotuner of the launch shapes (the paper has no counterpart; a service
+ * of this library).  The work of a step is fixed by the scheme; how it is cut
+ * into launches is chosen per kernel kind by timing the candidates on this
+ * context's own clusters with CUDA events (whole macro steps, per-phase
+ * events as in adg_profile, after one untimed macro step):
+ *   choice[0] / [1]: threads per element block of the CUDA-core local /
+ *                    neighbour kernels, of {64, 128, 256};
+ *   choice[2] / [3]: consecutive 12-element tiles one CTA slot of the
+ *                    tensor-core local / neighbour kernel takes per sweep
+ *                    (elements per CTA before it strides on), of {1, 2, 4};
+ *   0 for a kernel kind this context does not launch.
+ * ms (optional, [4][3]): mean milliseconds per macro step of that kernel kind
+ * for each candidate (-1 where not timed).  reps >= 1 timed macro steps per
+ * candidate.  The state the steps change (dofs, sea surface, fault state and
+ * counters, error word, time) is copied aside on the device and restored, so
+ * the solution is unchanged; the call allocates that copy.  Choices are
+ * cached for the process by (degree, precision, ensemble, tet count rounded
+ * to a power of two, clusters) and reused unless force != 0.  Call at a
+ * macro-step boundary after adg_init (else ADG_E_STATE); results of later
+ * steps are bit-identical for every choice.  ADG_E_INVALID for bad
+ * arguments, ADG_E_CUDA / ADG_E_NOMEM on device errors. */
+int adg_autotune(adg_ctx* ctx, int reps, int force, int* choice, double* ms);
+
 /* Peak-rate probe of a GPU (a measurement aid for the roofline denominators;
  * the paper has no counterpart).  kind 0: tcgen05.mma kind::tf32 with FP32
  * accumulation (M = 128, N = 256, A in TMEM, B in shared memory, one CTA per

@@ -75,6 +75,7 @@ _SIGS = {
     "adg_sync": (C.c_int, [_P]),
     "adg_profile": (C.c_int, [_P, C.c_int, _P, _P]),
     "adg_step_noalloc": (C.c_int, [_P, _P, C.c_int, _P]),
+    "adg_autotune": (C.c_int, [_P, C.c_int, C.c_int, _P, _P]),
     "adg_measure_peak": (C.c_int, [C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "adg_fault_faces": (C.c_int, [_P, _P, _P, _P, _P]),
     "adg_set_fault": (C.c_int, [_P, _P]),
@@ -365,6 +366,16 @@ def adg_step_noalloc(ctx, d_Q_ptr, n_steps, stream_ptr=None):
     """d_Q_ptr: integer device address of the caller's dofs (see include/adg.h)."""
     _check(ctx, load().adg_step_noalloc(ctx, C.c_void_p(d_Q_ptr), int(n_steps),
                                         None if stream_ptr is None else C.c_void_p(stream_ptr)))
+
+
+def adg_autotune(ctx, reps=2, force=False):
+    """Launch shapes chosen by the library's autotuner: (choice [4] =
+    CUDA-core local / neighbour threads per block, tensor-core local /
+    neighbour tiles per CTA sweep; ms [4][3] per candidate)."""
+    choice = np.zeros(4, np.int32)
+    ms = np.zeros((4, 3))
+    _check(ctx, load().adg_autotune(ctx, int(reps), int(bool(force)), _ptr(choice), _ptr(ms)))
+    return choice, ms
 
 
 def adg_measure_peak(kind, device=0, reps=20):

@@ -796,7 +796,7 @@ void Ctx::launch_tick(int s, double dtm) {
     }
     int rc = 0;
     if (ntc) {
-      const Segs g = make_segs(tcs, ntc, kTileElems);
+      const Segs g = make_segs(tcs, ntc, kTileElems, tc_chunk[phase]);
       rc = phase == 0 ? launch_local_tc(a, g, n_sms, stream, coarse) : launch_neighbour_tc(a, g, n_sms, stream, coarse);
       if (prof) {  // the tensor-core launch alone
         CK(cudaEventCreate(&ev.m));
@@ -805,7 +805,8 @@ void Ctx::launch_tick(int s, double dtm) {
     }
     if (!rc && ncc) {
       const Segs g = make_segs(ccs, ncc, 1);
-      rc = phase == 0 ? launch_local(fp64, N, a, g, stream) : launch_neighbour(fp64, N, a, g, stream);
+      rc = phase == 0 ? launch_local(fp64, N, a, g, stream, cc_threads[0])
+                      : launch_neighbour(fp64, N, a, g, stream, cc_threads[1]);
     }
     if (prof) { CK(cudaEventRecord(ev.b, stream)); prof->push_back(ev); }
     if (rc)

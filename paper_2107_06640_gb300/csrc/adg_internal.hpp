@@ -96,6 +96,11 @@ struct Ctx {
   unsigned int* dErr = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
   bool use_graph = true;
+  // launch shapes (adg_autotune; phase 0 local, 1 neighbour): threads per
+  // element block of the CUDA-core kernels, consecutive tiles per CTA-slot
+  // sweep of the tensor-core kernels
+  int cc_threads[2] = {128, 128};
+  int tc_chunk[2] = {1, 1};
   // dynamic rupture: fault faces in internal (cluster) order
   int64_t nff = 0;
   std::vector<int> fface;                 // [nff][5] minus elem, face, plus elem, face, perm
@@ -150,6 +155,7 @@ struct Ctx {
   void launch_tick(int s, double dtm);
   void run_macro(double scale);
   int64_t launches_per_macro() const;
+  void autotune(int reps, bool force, int* choice, double* ms);
   void check_err();
   ~Ctx();
 };

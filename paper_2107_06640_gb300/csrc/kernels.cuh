@@ -93,9 +93,17 @@ struct Seg {
 };
 struct Segs {
   int n;                        // segments
+  int chunk;                    // tensor-core kernels: consecutive tiles a CTA slot takes per sweep
   int64_t first[kMaxSeg + 1];   // first work unit of each segment; first[n] = all units
   Seg s[kMaxSeg];
 };
+// Tensor-core kernels: the i-th tile of slot `slot` (of `slots`, over all CTAs)
+// when every slot takes `chunk` consecutive tiles per sweep; increasing in i.
+// (Tile counts stay below 2^31.)
+__host__ __device__ inline int slot_tile(int i, int slot, int slots, int chunk) {
+  const int q = i / chunk;
+  return (q * slots + slot) * chunk + (i - q * chunk);
+}
 // segment of work unit u (segments are few: a linear scan)
 __host__ __device__ inline int seg_find(const Segs& g, int64_t u) {
   int i = 0;
@@ -108,7 +116,7 @@ __host__ __device__ inline int seg_of(const Segs& g, int64_t u) {
   return kMulti ? seg_find(g, u) : 0;
 }
 // Segs of the given segments with `unit` virtual elements per work unit
-Segs make_segs(const Seg* s, int n, int unit);
+Segs make_segs(const Seg* s, int n, int unit, int chunk = 1);
 
 // tensor-core (tcgen05, 3xTF32) local kernel, degree 5, FP32 dofs (local_tc.cu),
 // for elements without gravitational faces, fault faces or finer LTS neighbours
@@ -165,8 +173,9 @@ int launch_rupture(int fp64, int N, const DRArgs& a, void* stream);
 enum { ERR_NAN = 1u, ERR_TIMEOUT = 2u, ERR_NEWTON = 4u };
 
 // host-side launchers (kernels_f64.cu / kernels_f32.cu); return cudaError_t as int
-int launch_local(int fp64, int N, const StepArgs& a, const Segs& g, void* stream);
-int launch_neighbour(int fp64, int N, const StepArgs& a, const Segs& g, void* stream);
+// (threads: per element block, a multiple of 32 up to 256)
+int launch_local(int fp64, int N, const StepArgs& a, const Segs& g, void* stream, int threads = 128);
+int launch_neighbour(int fp64, int N, const StepArgs& a, const Segs& g, void* stream, int threads = 128);
 int local_smem_bytes(int fp64, int N);
 
 }  // namespace adg

@@ -14,7 +14,8 @@
 
 namespace adg {
 
-constexpr int kThreads = 128;
+// threads per element block: a launch-time choice (the autotuner's), up to this
+constexpr int kMaxThreads = 256;
 
 // 1/k (k = 1..47; entry 0 unused) and 1/m! (m = 0..5), correctly rounded
 // constants: the gravity-face series multiplies by them instead of dividing
@@ -111,7 +112,7 @@ struct Smem {
 };
 
 template <typename T, int N>
-__global__ void __launch_bounds__(kThreads) local_kernel(StepArgs a, const __grid_constant__ Segs segs) {
+__global__ void __launch_bounds__(kMaxThreads) local_kernel(StepArgs a, const __grid_constant__ Segs segs) {
   using S = Smem<T, N>;
   constexpr int P = S::P, B = S::B, Bf = S::Bf, B1 = S::B1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -370,7 +371,7 @@ struct SmemN {
 };
 
 template <typename T, int N>
-__global__ void __launch_bounds__(kThreads) neighbour_kernel(StepArgs a, const __grid_constant__ Segs segs) {
+__global__ void __launch_bounds__(kMaxThreads) neighbour_kernel(StepArgs a, const __grid_constant__ Segs segs) {
   constexpr int P = Pad<T>::P, B = nb3(N), Bf = nb2(N);
   __shared__ __align__(16) T sVo[4 * Bf * P];  // own traces [f][n][p]
   __shared__ __align__(16) T sVn[4 * Bf * P];  // neighbours' traces in this face's node order
@@ -501,7 +502,7 @@ __global__ void __launch_bounds__(kThreads) neighbour_kernel(StepArgs a, const _
 }
 
 template <typename T, int N>
-int launch_local_t(const StepArgs& a, const Segs& g, cudaStream_t st) {
+int launch_local_t(const StepArgs& a, const Segs& g, int threads, cudaStream_t st) {
   const int64_t nblocks = g.n ? g.first[g.n] : 0;
   constexpr int bytes = Smem<T, N>::bytes;
   const int rc = configure_on_device((const void*)local_kernel<T, N>, [] {
@@ -509,37 +510,39 @@ int launch_local_t(const StepArgs& a, const Segs& g, cudaStream_t st) {
   });
   if (rc) return rc;
   if (nblocks <= 0) return 0;
-  local_kernel<T, N><<<(unsigned)nblocks, kThreads, bytes, st>>>(a, g);
+  if (threads < 32 || threads > kMaxThreads || threads % 32) return (int)cudaErrorInvalidValue;
+  local_kernel<T, N><<<(unsigned)nblocks, threads, bytes, st>>>(a, g);
   return (int)cudaGetLastError();
 }
 
 template <typename T, int N>
-int launch_neighbour_t(const StepArgs& a, const Segs& g, cudaStream_t st) {
+int launch_neighbour_t(const StepArgs& a, const Segs& g, int threads, cudaStream_t st) {
   const int64_t nblocks = g.n ? g.first[g.n] : 0;
   if (nblocks <= 0) return 0;
-  neighbour_kernel<T, N><<<(unsigned)nblocks, kThreads, 0, st>>>(a, g);
+  if (threads < 32 || threads > kMaxThreads || threads % 32) return (int)cudaErrorInvalidValue;
+  neighbour_kernel<T, N><<<(unsigned)nblocks, threads, 0, st>>>(a, g);
   return (int)cudaGetLastError();
 }
 
 template <typename T>
-int dispatch_local(int N, const StepArgs& a, const Segs& nb, cudaStream_t st) {
+int dispatch_local(int N, const StepArgs& a, const Segs& nb, int th, cudaStream_t st) {
   switch (N) {
-    case 1: return launch_local_t<T, 1>(a, nb, st);
-    case 2: return launch_local_t<T, 2>(a, nb, st);
-    case 3: return launch_local_t<T, 3>(a, nb, st);
-    case 4: return launch_local_t<T, 4>(a, nb, st);
-    case 5: return launch_local_t<T, 5>(a, nb, st);
+    case 1: return launch_local_t<T, 1>(a, nb, th, st);
+    case 2: return launch_local_t<T, 2>(a, nb, th, st);
+    case 3: return launch_local_t<T, 3>(a, nb, th, st);
+    case 4: return launch_local_t<T, 4>(a, nb, th, st);
+    case 5: return launch_local_t<T, 5>(a, nb, th, st);
   }
   return (int)cudaErrorInvalidValue;
 }
 template <typename T>
-int dispatch_neighbour(int N, const StepArgs& a, const Segs& nb, cudaStream_t st) {
+int dispatch_neighbour(int N, const StepArgs& a, const Segs& nb, int th, cudaStream_t st) {
   switch (N) {
-    case 1: return launch_neighbour_t<T, 1>(a, nb, st);
-    case 2: return launch_neighbour_t<T, 2>(a, nb, st);
-    case 3: return launch_neighbour_t<T, 3>(a, nb, st);
-    case 4: return launch_neighbour_t<T, 4>(a, nb, st);
-    case 5: return launch_neighbour_t<T, 5>(a, nb, st);
+    case 1: return launch_neighbour_t<T, 1>(a, nb, th, st);
+    case 2: return launch_neighbour_t<T, 2>(a, nb, th, st);
+    case 3: return launch_neighbour_t<T, 3>(a, nb, th, st);
+    case 4: return launch_neighbour_t<T, 4>(a, nb, th, st);
+    case 5: return launch_neighbour_t<T, 5>(a, nb, th, st);
   }
   return (int)cudaErrorInvalidValue;
 }

@@ -213,10 +213,10 @@ __device__ __forceinline__ bool pair_round(Lane& L, unsigned int* err, F&& issue
 // One tile, the share of half H (8-column chunks c with c % 2 == H); false
 // after a timed-out wait.
 // kBuf: some elements of the launch have an LTS buffer (a coarser neighbour)
-// tile: index within its segment; gtile: index among all tiles of the launch
-// (kMulti: the launch has several segments)
+// tile: index within its segment; t2: this slot's tile after the next among
+// all tiles of the launch (kMulti: the launch has several segments)
 template <int H, bool kBuf, bool kMulti>
-__device__ __forceinline__ bool local_tile(Lane& L, const StepArgs& a, const Segs& g, int64_t gtile, int64_t v_begin,
+__device__ __forceinline__ bool local_tile(Lane& L, const StepArgs& a, const Segs& g, int64_t t2, int64_t v_begin,
                                            int64_t n_virtual, int64_t tile) {
   float* const Q = reinterpret_cast<float*>(a.Q);
   const int64_t v0 = v_begin + tile * TE;
@@ -233,7 +233,6 @@ __device__ __forceinline__ bool local_tile(Lane& L, const StepArgs& a, const Seg
 
   // the tile after the next of this slot into L2 while this one is worked on
   if (H == 0 && L.t == 0) {
-    const int64_t t2 = gtile + (int64_t)gridDim.x * 4;
     if (t2 < g.first[g.n]) {
       const int i2 = seg_of<kMulti>(g, t2);
       const int64_t l2 = t2 - g.first[i2], rem2 = g.s[i2].n - l2 * TE;
@@ -419,7 +418,8 @@ __device__ __forceinline__ bool local_tile(Lane& L, const StepArgs& a, const Seg
   return true;
 }
 
-template <bool kBuf, bool kMulti>
+// kChunk: consecutive tiles a slot takes per sweep (a compile-time launch shape)
+template <bool kBuf, bool kMulti, int kChunk>
 __global__ void __launch_bounds__(kThreadsL, 1) local_tc_kernel(StepArgs a, const __grid_constant__ Segs g) {
   float* sm = reinterpret_cast<float*>(smem_raw);
   __shared__ uint32_t tmem_base;
@@ -451,21 +451,28 @@ __global__ void __launch_bounds__(kThreadsL, 1) local_tc_kernel(StepArgs a, cons
   L.tbase = tmem_base + (uint32_t)slot * 256u;
   L.trow = L.tbase + ((uint32_t)(32 * L.w) << 16);
   L.sbase = tc::smem_u32(sm);
-
-
-
   L.phase = 0;
-  // tiles of all segments (the clusters of this phase) in one sequence
+  // tiles of all segments (the clusters of this phase) in one sequence; slot
+  // `me` of all `slots` takes kChunk consecutive tiles per sweep
   const int64_t ntiles = g.first[g.n];
-  for (int64_t tile = (int64_t)blockIdx.x * 2 + slot; tile < ntiles; tile += (int64_t)gridDim.x * 2) {
+  const int slots = (int)gridDim.x * 2, me = (int)blockIdx.x * 2 + slot;
+  auto work = [&](int64_t tile, int64_t t2) {
     const Seg& sg = g.s[seg_of<kMulti>(g, tile)];
 #pragma unroll
     for (int k = 0; k < 6; ++k) L.tcf[k] = (float)sg.tcoef[k];
     L.btrace_mode = sg.btrace_mode;
     const int64_t lt = tile - g.first[&sg - g.s];
-    const bool ok = half == 0 ? local_tile<0, kBuf, kMulti>(L, a, g, tile, sg.v_begin, sg.n, lt)
-                              : local_tile<1, kBuf, kMulti>(L, a, g, tile, sg.v_begin, sg.n, lt);
-    if (!ok) break;
+    return half == 0 ? local_tile<0, kBuf, kMulti>(L, a, g, t2, sg.v_begin, sg.n, lt)
+                     : local_tile<1, kBuf, kMulti>(L, a, g, t2, sg.v_begin, sg.n, lt);
+  };
+  if constexpr (kChunk == 1) {
+    for (int64_t tile = me; tile < ntiles; tile += slots)
+      if (!work(tile, tile + 2 * (int64_t)slots)) break;
+  } else {
+    for (int it = 0;; ++it) {
+      const int64_t tile = slot_tile(it, me, slots, kChunk);
+      if (tile >= ntiles || !work(tile, slot_tile(it + 2, me, slots, kChunk))) break;
+    }
   }
   // after a timed-out wait, give this slot's MMAs in flight a bounded chance
   // to finish before the columns are freed
@@ -480,21 +487,28 @@ __global__ void __launch_bounds__(kThreadsL, 1) local_tc_kernel(StepArgs a, cons
 }  // namespace
 
 int launch_local_tc(const StepArgs& a, const Segs& g, int n_sms, void* stream, bool buffers) {
-  const int rc = configure_on_device((const void*)local_tc_kernel<false, false>, [] {
+  using K = void (*)(StepArgs, Segs);
+  // [kBuf][kMulti][chunk 1, 2, 4]
+  static const K kern[2][2][3] = {
+      {{local_tc_kernel<false, false, 1>, local_tc_kernel<false, false, 2>, local_tc_kernel<false, false, 4>},
+       {local_tc_kernel<false, true, 1>, local_tc_kernel<false, true, 2>, local_tc_kernel<false, true, 4>}},
+      {{local_tc_kernel<true, false, 1>, local_tc_kernel<true, false, 2>, local_tc_kernel<true, false, 4>},
+       {local_tc_kernel<true, true, 1>, local_tc_kernel<true, true, 2>, local_tc_kernel<true, true, 4>}}};
+  const int rc = configure_on_device((const void*)kern[0][0][0], [] {
     cudaError_t ce = cudaSuccess;
-    for (auto k : {local_tc_kernel<false, false>, local_tc_kernel<true, false>, local_tc_kernel<false, true>,
-                   local_tc_kernel<true, true>})
-      if (ce == cudaSuccess) ce = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, LImg::bytes);
+    for (int i = 0; i < 12; ++i)
+      if (ce == cudaSuccess)
+        ce = cudaFuncSetAttribute((const void*)kern[i / 6][(i / 3) % 2][i % 3], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  LImg::bytes);
     return ce;
   });
   if (rc) return rc;
   const int64_t ntiles = g.n ? g.first[g.n] : 0;
   if (ntiles <= 0) return 0;
+  const int ci = g.chunk >= 4 ? 2 : (g.chunk >= 2 ? 1 : 0);
   const int64_t want = (ntiles + 1) / 2;
   const unsigned grid = (unsigned)(want < n_sms ? want : n_sms);
-  auto k = g.n > 1 ? (buffers ? local_tc_kernel<true, true> : local_tc_kernel<false, true>)
-                   : (buffers ? local_tc_kernel<true, false> : local_tc_kernel<false, false>);
-  k<<<grid, kThreadsL, LImg::bytes, (cudaStream_t)stream>>>(a, g);
+  kern[buffers ? 1 : 0][g.n > 1 ? 1 : 0][ci]<<<grid, kThreadsL, LImg::bytes, (cudaStream_t)stream>>>(a, g);
   return (int)cudaGetLastError();
 }
 

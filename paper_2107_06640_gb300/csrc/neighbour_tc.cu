@@ -240,7 +240,8 @@ __device__ __forceinline__ void face_flux(const float* co, const float qm[9], co
 // kOne: one scenario (S = 1), where a virtual element is its element and the
 // 64-bit divisions by S drop out; kCoarse: some faces of the launch have a
 // coarser LTS neighbour (without, their code stays out of the kernel)
-template <bool kOne, bool kCoarse, bool kMulti>
+// kChunk: consecutive tiles a slot takes per sweep (a compile-time launch shape)
+template <bool kOne, bool kCoarse, bool kMulti, int kChunk>
 __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, const __grid_constant__ Segs g) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   float* sm = reinterpret_cast<float*>(smem_raw);
@@ -358,14 +359,16 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
     cp_commit();
   };
 
-  int64_t tile = (int64_t)blockIdx.x * 2 + slot;
+  const int slots = (int)gridDim.x * 2, me = (int)blockIdx.x * 2 + slot;
+  int it = 0;
+  int64_t tile = slot_tile(0, me, slots, kChunk);
   if (tile < ntiles) {
     int info0, nbe0;
     meta_load(tile, info0, nbe0);
     prefetch(tile, info0, nbe0);
   }
-  for (; tile < ntiles; tile += (int64_t)gridDim.x * 2) {
-    const int64_t next = tile + (int64_t)gridDim.x * 2;
+  for (; tile < ntiles; tile = slot_tile(++it, me, slots, kChunk)) {
+    const int64_t next = slot_tile(it + 1, me, slots, kChunk);
     int info_n = 0, nbe_n = 0;  // the next tile's neighbour information, needed after the faces
     if (next < ntiles) meta_load(next, info_n, nbe_n);
     int64_t v0, nrem;
@@ -462,7 +465,7 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
     // ---- the next tile's loads overlap this tile's lift and dofs update
     if (next < ntiles) prefetch(next, info_n, nbe_n);
     // and the tile after it into L2
-    const int64_t next2 = next + (int64_t)gridDim.x * 2;
+    const int64_t next2 = slot_tile(it + 2, me, slots, kChunk);
     if (u == 0 && next2 < ntiles) {
       int64_t q0, rem2;
       tile_at(next2, q0, rem2, nullptr);
@@ -524,25 +527,31 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
 }  // namespace
 
 int launch_neighbour_tc(const StepArgs& a, const Segs& g, int n_sms, void* stream, bool coarse) {
-  const int rc = configure_on_device((const void*)neighbour_tc_kernel<true, false, false>, [] {
+  using K = void (*)(StepArgs, Segs);
+#define ADG_NK(one, coarse, multi) \
+  { neighbour_tc_kernel<one, coarse, multi, 1>, neighbour_tc_kernel<one, coarse, multi, 2>, \
+    neighbour_tc_kernel<one, coarse, multi, 4> }
+  // [S == 1][coarse][multi][chunk 1, 2, 4]
+  static const K kern[2][2][2][3] = {{{ADG_NK(false, false, false), ADG_NK(false, false, true)},
+                                      {ADG_NK(false, true, false), ADG_NK(false, true, true)}},
+                                     {{ADG_NK(true, false, false), ADG_NK(true, false, true)},
+                                      {ADG_NK(true, true, false), ADG_NK(true, true, true)}}};
+#undef ADG_NK
+  const int rc = configure_on_device((const void*)kern[0][0][0][0], [] {
     cudaError_t ce = cudaSuccess;
-    for (auto k : {neighbour_tc_kernel<true, false, false>, neighbour_tc_kernel<false, false, false>,
-                   neighbour_tc_kernel<true, true, false>, neighbour_tc_kernel<false, true, false>,
-                   neighbour_tc_kernel<true, false, true>, neighbour_tc_kernel<false, false, true>,
-                   neighbour_tc_kernel<true, true, true>, neighbour_tc_kernel<false, true, true>})
-      if (ce == cudaSuccess) ce = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, NImg::bytes);
+    for (int i = 0; i < 24; ++i)
+      if (ce == cudaSuccess)
+        ce = cudaFuncSetAttribute((const void*)kern[i / 12][(i / 6) % 2][(i / 3) % 2][i % 3],
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, NImg::bytes);
     return ce;
   });
   if (rc) return rc;
   const int64_t ntiles = g.n ? g.first[g.n] : 0;
   if (ntiles <= 0) return 0;
+  const int ci = g.chunk >= 4 ? 2 : (g.chunk >= 2 ? 1 : 0);
   const int64_t want = (ntiles + 1) / 2;
   const unsigned grid = (unsigned)(want < n_sms ? want : n_sms);
-  auto k = g.n > 1 ? (a.S == 1 ? (coarse ? neighbour_tc_kernel<true, true, true> : neighbour_tc_kernel<true, false, true>)
-                              : (coarse ? neighbour_tc_kernel<false, true, true> : neighbour_tc_kernel<false, false, true>))
-                   : (a.S == 1 ? (coarse ? neighbour_tc_kernel<true, true, false> : neighbour_tc_kernel<true, false, false>)
-                              : (coarse ? neighbour_tc_kernel<false, true, false> : neighbour_tc_kernel<false, false, false>));
-  k<<<grid, kThreadsN, NImg::bytes, (cudaStream_t)stream>>>(a, g);
+  kern[a.S == 1 ? 1 : 0][coarse ? 1 : 0][g.n > 1 ? 1 : 0][ci]<<<grid, kThreadsN, NImg::bytes, (cudaStream_t)stream>>>(a, g);
   return (int)cudaGetLastError();
 }
 
