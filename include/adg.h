@@ -117,6 +117,24 @@ int adg_upload_material(adg_ctx* ctx, const double* rho, const double* lambda, c
 
 /* Geometry, CFL time steps, rate-2 clustering, Godunov flux matrices F-/F+
  * per face (Sec. 4.2, Eq. numerical-flux), device allocation.  Dofs start at 0. */
+/* The ocean as the acoustic system (Sec. 4.1: the fluid is the elastic
+ * system with mu = 0, its stress -p I).  Call before adg_init (else
+ * ADG_E_STATE); enable = 0 restores the default.  With it:
+ *  - the stress of every fluid element (mu = 0) is kept isotropic: each dofs
+ *    upload (adg_set_dofs, adg_set_dofs_f32, adg_set_initial_values,
+ *    adg_load_state) replaces it by sigma_xx = sigma_yy = sigma_zz = their mean,
+ *    with no shear stress; the scheme keeps that form (the acoustic subspace
+ *    is invariant), so the results equal those of the 9-quantity system on
+ *    such data;
+ *  - with the tensor-core kernels (ADG_3XTF32, degree 5), the fluid elements
+ *    without gravitational face, fault face or LTS neighbour in another
+ *    cluster take a 4-quantity (p, v) local kernel: 32 elements per 128-row
+ *    tile, the acoustic star product, 4 of the 9 dofs rows read; their face
+ *    traces are written in the usual 9-quantity layout.
+ * Without it the fluid carries whatever stress the caller uploads (a
+ * deviatoric part stays constant in a fluid but drives velocities). */
+int adg_set_acoustic_ocean(adg_ctx* ctx, int enable);
+
 int adg_init(adg_ctx* ctx);
 
 /* Host-only plan of the uploaded mesh (no device needed): call after

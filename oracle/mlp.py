@@ -124,13 +124,21 @@ class LearnedStart:
     """Start guess for the first-pass Newton of the friction solve (the
     `guess` argument of the oracle's rupture step).  With P None it returns
     the plain warm start; with capture=True it records [features, ln V* - x_a]
-    rows of the first-pass solves (via `solved`)."""
+    rows of the first-pass solves (via `solved`).
+
+    Rule (the learned part is not in the paper): at time point j the network
+    is evaluated only at points whose first-pass Newton at point j - 1 needed
+    more than one iteration (the state is changing there; where the warm
+    start already converges, the network cannot help).  Where it was also
+    evaluated at j - 1, the start is the warm start moved by the change of the
+    predicted ln V*; everywhere else it is the warm start."""
 
     def __init__(self, P=None, capture=False):
         self.P = P
         self.capture = capture
         self.rows = []
         self.prev = None
+        self.busy = None
 
     def __call__(self, j, Th, st, psi, V, par):
         S, eta = st["S"], st["eta"]
@@ -141,16 +149,20 @@ class LearnedStart:
         self._f, self._xa, self._solve = f, xa, solve
         if self.P is None:
             return V
-        xhat = np.where(solve, predict(self.P, f), np.nan)
-        xw = f[..., 3]
         if j == 0 or self.prev is None:
-            self.prev = np.full_like(xhat, np.nan)
-        use = solve & np.isfinite(self.prev)
+            self.prev = np.full(solve.shape, np.nan)
+            self.busy = np.zeros(solve.shape, bool)
+        ev = solve & self.busy
+        xhat = np.where(ev, predict(self.P, f), np.nan)
+        xw = f[..., 3]
+        use = ev & np.isfinite(self.prev)
         x0 = np.where(use, xw + (xhat - np.where(use, self.prev, 0.0)), xw)
         self.prev = xhat
         return np.where(solve, np.exp(np.clip(x0, X_FLOOR, f[..., 2])), V)
 
-    def solved(self, j, V):
+    def solved(self, j, V, iters=None):
+        if iters is not None:
+            self.busy = self._solve & (np.asarray(iters) > 1)
         if self.capture:
             s = self._solve
             z = np.log(np.maximum(V[s], 1e-300)) - self._xa[s]

@@ -266,7 +266,7 @@ def solve_step(n, qm_t, qp_t, matm, matp, par, dt, N, guess=None, tol=1e-10, max
             if not np.all(ok):
                 raise RuntimeError("friction Newton did not converge")
             if ps == 0 and hasattr(guess, "solved"):
-                guess.solved(j, Vcur)
+                guess.solved(j, Vcur, it)
             iters[j, ps] = it
         psi, V = psi_new, Vcur
         t_b, vb, vc, Vvec, tau_tot = middle_traction_velocity(st, V, n)

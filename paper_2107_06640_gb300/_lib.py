@@ -50,6 +50,7 @@ _SIGS = {
     "adg_upload_mesh": (C.c_int, [_P, C.c_int64, _P, C.c_int64, _P, _P, _P]),
     "adg_upload_material": (C.c_int, [_P, _P, _P, _P]),
     "adg_init": (C.c_int, [_P]),
+    "adg_set_acoustic_ocean": (C.c_int, [_P, C.c_int]),
     "adg_plan": (C.c_int, [_P, _P, _P, C.POINTER(C.c_double), C.POINTER(C.c_int)]),
     "adg_face_flux": (C.c_int, [_P, C.c_int64, C.c_int, _P, _P]),
     "adg_face_neighbour": (C.c_int, [_P, C.c_int64, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int), _P]),
@@ -194,6 +195,10 @@ def adg_upload_material(ctx, rho, lam, mu):
 
 def adg_init(ctx):
     _check(ctx, load().adg_init(ctx))
+
+
+def adg_set_acoustic_ocean(ctx, enable=True):
+    _check(ctx, load().adg_set_acoustic_ocean(ctx, int(bool(enable))))
 
 
 def adg_plan(ctx):

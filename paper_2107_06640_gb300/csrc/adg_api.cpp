@@ -214,6 +214,14 @@ int adg_upload_material(adg_ctx* ctx, const double* rho, const double* lambda, c
   });
 }
 
+int adg_set_acoustic_ocean(adg_ctx* ctx, int enable) {
+  if (!ctx) return ADG_E_INVALID;
+  return guard(ctx, [&] {
+    if (ctx->c.inited) adg::throw_err(ADG_E_STATE, "the ocean model is fixed at adg_init");
+    ctx->c.acoustic = enable != 0;
+  });
+}
+
 int adg_init(adg_ctx* ctx) {
   if (!ctx) return ADG_E_INVALID;
   return guard(ctx, [&] {
@@ -289,6 +297,7 @@ int adg_set_dofs(adg_ctx* ctx, const double* Q) {
     need_init(ctx->c);
     if (ctx->c.fp64) put_dofs<double>(ctx->c, Q);
     else put_dofs<float>(ctx->c, Q);
+    ctx->c.project_fluid();
   });
 }
 
@@ -314,6 +323,7 @@ int adg_set_dofs_f32(adg_ctx* ctx, const float* Q) {
                                                       c.stream),
                "dofs upload");
     check_cuda(cudaStreamSynchronize(c.stream), "dofs upload");
+    c.project_fluid();
   });
 }
 
@@ -559,6 +569,7 @@ int adg_set_initial_values(adg_ctx* ctx, const double* values) {
       }
     if (c.fp64) put_dofs<double>(c, Q.data());
     else put_dofs<float>(c, Q.data());
+    c.project_fluid();
   });
 }
 
@@ -922,6 +933,7 @@ int adg_load_state(adg_ctx* ctx, const void* buf, size_t len) {
     const char* body = p + kStateHeader;
     check_cuda(cudaStreamSynchronize(c.stream), "load");
     check_cuda(cudaMemcpy(c.dQ, body, qb, cudaMemcpyHostToDevice), "load dofs");
+    c.project_fluid();
     if (eb) check_cuda(cudaMemcpy(c.dEta, body + qb, eb, cudaMemcpyHostToDevice), "load eta");
     if (fb) {
       if (!c.fault_set) adg::throw_err(ADG_E_STATE, "set the fault parameters before loading a fault state");

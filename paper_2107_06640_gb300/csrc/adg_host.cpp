@@ -467,20 +467,30 @@ void Ctx::setup() {
         if (tg == ADG_TAG_GRAVITY || tg == ADG_TAG_FAULT || (e2 >= 0 && cl[e2] < cl[e])) special[e] = 2;
         else if (e2 >= 0 && cl[e2] > cl[e] && special[e] == 0) special[e] = 1;
       }
+  // order key within a cluster: 0 plain elastic, 1 plain fluid on the
+  // acoustic local kernel, 2 with a coarser neighbour, 3 the CUDA-core rest
+  std::vector<char> key(E, 0);
+  for (int64_t e = 0; e < E; ++e)
+    key[e] = special[e] ? (char)(special[e] + 1) : (char)(tc && acoustic && mu[e] == 0.0 ? 1 : 0);
   order.resize(E);
   for (int64_t e = 0; e < E; ++e) order[e] = e;
   std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) {
-    return cl[a] != cl[b] ? cl[a] < cl[b] : special[a] < special[b];
+    return cl[a] != cl[b] ? cl[a] < cl[b] : key[a] < key[b];
   });
   inv.assign(E, 0);
   for (int64_t i = 0; i < E; ++i) inv[order[i]] = i;
   cl_begin.assign(ncl + 1, 0);
   cl_plain.assign(ncl, 0);
+  cl_elastic.assign(ncl, 0);
+  cl_fluid.assign(ncl, 0);
   cl_tc_coarse.assign(ncl, 0);
   for (int64_t i = 0; i < E; ++i) {
-    cl_begin[cl[order[i]] + 1]++;
-    if (tc && special[order[i]] < 2) cl_plain[cl[order[i]]]++;
-    if (tc && special[order[i]] == 1) cl_tc_coarse[cl[order[i]]] = 1;
+    const int k = key[order[i]], c = cl[order[i]];
+    cl_begin[c + 1]++;
+    if (tc && k < 3) cl_plain[c]++;
+    if (tc && k == 0) cl_elastic[c]++;
+    if (tc && k == 1) cl_fluid[c]++;
+    if (tc && k == 2) cl_tc_coarse[c] = 1;
   }
   for (int c = 0; c < ncl; ++c) cl_begin[c + 1] += cl_begin[c];
   cluster.resize(E);
@@ -698,6 +708,13 @@ void Ctx::setup() {
     dFrec = upload_raw<float>(frec, owned, dev_bytes);
   }
   dErr = (unsigned int*)dalloc(sizeof(unsigned int), owned, dev_bytes);
+  if (acoustic) {
+    std::vector<int64_t> fl;
+    for (int64_t i = 0; i < E; ++i)
+      if (mu[order[i]] == 0.0) fl.push_back(i);
+    n_fluid = (int64_t)fl.size();
+    dFluid = n_fluid ? upload_raw<int64_t>(fl, owned, dev_bytes) : nullptr;
+  }
   if (nff) {
     dFface = upload_raw<int>(fface, owned, dev_bytes);
     dFslot = upload_raw<int>(fslot, owned, dev_bytes);
@@ -753,8 +770,9 @@ static void taylor_int(int N, double ta, double tb, double* out) {
 void Ctx::launch_tick(int s, double dtm) {
   StepArgs a = base_args();
   for (int phase = 0; phase < 2; ++phase) {
-    Seg tcs[kMaxSeg], ccs[kMaxSeg];
-    int ntc = 0, ncc = 0;
+    // per kernel kind the clusters' segments: tensor-core elastic, tensor-core
+    // acoustic (local phase only), CUDA-core
+    std::vector<Seg> tcs, fls, ccs;
     bool coarse = false;
     for (int c = 0; c < ncl; ++c) {
       const bool active = phase == 0 ? s % (1 << c) == 0 : (s + 1) % (1 << c) == 0;
@@ -772,42 +790,55 @@ void Ctx::launch_tick(int s, double dtm) {
         taylor_int(N, half * dt, (half + 1) * dt, sg.ccoef);
         if (fcl_begin.size() > (size_t)c + 1 && fcl_begin[c + 1] > fcl_begin[c]) launch_rupture_cluster(c, dt);
       }
+      auto seg = [&](int64_t first, int64_t count) {
+        Seg t = sg;
+        t.v_begin = first * S;
+        t.n = count * S;
+        return t;
+      };
       const int64_t np = tc ? cl_plain[c] : 0;
       if (np > 0) {
-        Seg t = sg;
-        t.v_begin = cl_begin[c] * S;
-        t.n = np * S;
-        tcs[ntc++] = t;
         coarse = coarse || cl_tc_coarse[c] != 0;
+        const int64_t n0 = cl_elastic[c], n1 = cl_fluid[c];
+        if (phase == 0 && n1 > 0) {
+          // elastic elements around the acoustic range, which takes its own kernel
+          if (n0 > 0) tcs.push_back(seg(cl_begin[c], n0));
+          fls.push_back(seg(cl_begin[c] + n0, n1));
+          if (np > n0 + n1) tcs.push_back(seg(cl_begin[c] + n0 + n1, np - n0 - n1));
+        } else {
+          tcs.push_back(seg(cl_begin[c], np));
+        }
       }
-      if (n > np) {
-        Seg t = sg;
-        t.v_begin = (cl_begin[c] + np) * S;
-        t.n = (n - np) * S;
-        ccs[ncc++] = t;
-      }
+      if (n > np) ccs.push_back(seg(cl_begin[c] + np, n - np));
     }
-    if (!ntc && !ncc) continue;
-    ProfEv ev{phase, nullptr, nullptr, (ntc > 0) + (ncc > 0)};
+    if (tcs.empty() && fls.empty() && ccs.empty()) continue;
+    ProfEv ev{phase, nullptr, nullptr, 0};
     if (prof) {
       CK(cudaEventCreate(&ev.a));
       CK(cudaEventCreate(&ev.b));
       CK(cudaEventRecord(ev.a, stream));
     }
     int rc = 0;
-    if (ntc) {
-      const Segs g = make_segs(tcs, ntc, kTileElems, tc_chunk[phase]);
-      rc = phase == 0 ? launch_local_tc(a, g, n_sms, stream, coarse) : launch_neighbour_tc(a, g, n_sms, stream, coarse);
-      if (prof) {  // the tensor-core launch alone
-        CK(cudaEventCreate(&ev.m));
-        CK(cudaEventRecord(ev.m, stream));
+    // one launch per kind and at most kMaxSeg segments
+    auto launch = [&](const std::vector<Seg>& v, int unit, auto&& fn) {
+      for (size_t i = 0; i < v.size() && !rc; i += kMaxSeg) {
+        const int k = (int)std::min<size_t>(kMaxSeg, v.size() - i);
+        rc = fn(make_segs(v.data() + i, k, unit, unit == 1 ? 1 : tc_chunk[phase]));
+        ev.launches++;
       }
+    };
+    launch(tcs, kTileElems, [&](const Segs& g) {
+      return phase == 0 ? launch_local_tc(a, g, n_sms, stream, coarse) : launch_neighbour_tc(a, g, n_sms, stream, coarse);
+    });
+    launch(fls, kTileElemsFluid, [&](const Segs& g) { return launch_local_tc(a, g, n_sms, stream, false, true); });
+    if (prof && (!tcs.empty() || !fls.empty())) {  // the tensor-core launches alone
+      CK(cudaEventCreate(&ev.m));
+      CK(cudaEventRecord(ev.m, stream));
     }
-    if (!rc && ncc) {
-      const Segs g = make_segs(ccs, ncc, 1);
-      rc = phase == 0 ? launch_local(fp64, N, a, g, stream, cc_threads[0])
-                      : launch_neighbour(fp64, N, a, g, stream, cc_threads[1]);
-    }
+    launch(ccs, 1, [&](const Segs& g) {
+      return phase == 0 ? launch_local(fp64, N, a, g, stream, cc_threads[0])
+                        : launch_neighbour(fp64, N, a, g, stream, cc_threads[1]);
+    });
     if (prof) { CK(cudaEventRecord(ev.b, stream)); prof->push_back(ev); }
     if (rc)
       throw Err(ADG_E_CUDA, std::string(phase == 0 ? "local kernel: " : "neighbour kernel: ") +
@@ -851,18 +882,26 @@ int64_t Ctx::launches_per_macro() const {
   const int ticks = 1 << (ncl - 1);
   for (int s = 0; s < ticks; ++s)
     for (int phase = 0; phase < 2; ++phase) {
-      bool tcl = false, ccl = false;
+      bool tcl = false, fll = false, ccl = false;
       for (int c = 0; c < ncl; ++c) {
         const int64_t n = cl_begin[c + 1] - cl_begin[c];
         if (!n || (phase == 0 ? s % (1 << c) : (s + 1) % (1 << c))) continue;
         if (phase == 1 && fcl_begin[c + 1] > fcl_begin[c]) L += 1;  // friction solve per cluster
-        const int64_t np = tc ? cl_plain[c] : 0;
-        tcl = tcl || np > 0;
+        const int64_t np = tc ? cl_plain[c] : 0, nf = (tc && phase == 0) ? cl_fluid[c] : 0;
+        tcl = tcl || np > nf;
+        fll = fll || nf > 0;
         ccl = ccl || n > np;
       }
-      L += tcl + ccl;
+      L += tcl + fll + ccl;
     }
   return L;
+}
+
+void Ctx::project_fluid() {
+  if (!acoustic || !n_fluid) return;
+  const int rc = launch_isotropic_fluid(fp64, dQ, dFluid, n_fluid, S * B, B, stream);
+  if (rc) throw Err(ADG_E_CUDA, std::string("fluid projection: ") + cudaGetErrorString((cudaError_t)rc));
+  CK(cudaStreamSynchronize(stream));
 }
 
 void Ctx::run_macro(double scale) {

@@ -32,6 +32,10 @@ int launch_permute_dofs(int fp64, int up, const void* in, void* out, const int64
                         int n_sms, void* stream);
 int launch_gather_dofs(int fp64, const void* Q, const int64_t* idx, int64_t n, int per, void* out, void* stream);
 int launch_scatter_dofs(int fp64, const void* in, const int64_t* idx, int64_t n, int per, void* Q, void* stream);
+// the stress of the listed elements' dofs replaced by its isotropic part:
+// sigma_xx = sigma_yy = sigma_zz = their mean, no shear (rows [9][B] per
+// virtual element, `sb` = S x B columns of basis functions per element)
+int launch_isotropic_fluid(int fp64, void* Q, const int64_t* elems, int64_t n, int sb, int B, void* stream);
 // receiver readout kernel launcher (readout.cu)
 int launch_receivers(int fp64, int B, const void* Q, int S, int64_t n, const int64_t* elem,
                      const double* phi, double* out, void* stream);
@@ -75,6 +79,14 @@ struct Ctx {
   std::vector<int64_t> cl_plain;
   // cluster c's tensor-core range includes elements with a coarser neighbour
   std::vector<char> cl_tc_coarse;
+  // acoustic ocean (adg_set_acoustic_ocean): the plain fluid elements of
+  // cluster c, [cl_begin[c] + cl_elastic[c], + cl_fluid[c]), take the
+  // 4-quantity local kernel; the library keeps fluid stress isotropic
+  bool acoustic = false;
+  std::vector<int64_t> cl_elastic, cl_fluid;
+  int64_t* dFluid = nullptr;  // library indices of all fluid elements (projection at upload)
+  int64_t n_fluid = 0;
+  void project_fluid();       // fluid stress -> its isotropic part, on the device
   std::vector<int> cluster;
   double dtmin = 0, time = 0;
   int64_t tick = 0;

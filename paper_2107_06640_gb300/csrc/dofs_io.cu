@@ -108,4 +108,34 @@ int launch_permute_dofs(int fp64, int up, const void* in, void* out, const int64
   return (int)cudaGetLastError();
 }
 
+namespace {
+template <typename T>
+__global__ void __launch_bounds__(256) isotropic_fluid_kernel(T* __restrict__ Q, const int64_t* __restrict__ elems,
+                                                               int64_t n, int sb, int B) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n * sb) return;
+  const int64_t e = elems[k / sb];
+  const int r = (int)(k % sb), s = r / B, l = r - s * B;
+  T* q = Q + ((e * (sb / B) + s) * 9) * B + l;  // row p of virtual element (e, s) at q[p * B]
+  const T m = (q[0] + q[B] + q[2 * B]) / T(3);
+  q[0] = m;
+  q[B] = m;
+  q[2 * B] = m;
+  q[3 * B] = T(0);
+  q[4 * B] = T(0);
+  q[5 * B] = T(0);
+}
+}  // namespace
+
+int launch_isotropic_fluid(int fp64, void* Q, const int64_t* elems, int64_t n, int sb, int B, void* stream) {
+  if (n <= 0) return 0;
+  const int64_t total = n * sb;
+  const unsigned blocks = (unsigned)((total + 255) / 256);
+  if (fp64)
+    isotropic_fluid_kernel<double><<<blocks, 256, 0, (cudaStream_t)stream>>>((double*)Q, elems, n, sb, B);
+  else
+    isotropic_fluid_kernel<float><<<blocks, 256, 0, (cudaStream_t)stream>>>((float*)Q, elems, n, sb, B);
+  return (int)cudaGetLastError();
+}
+
 }  // namespace adg

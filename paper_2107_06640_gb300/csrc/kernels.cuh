@@ -84,6 +84,8 @@ constexpr int kMaxSeg = 16;
 // virtual elements per tile of the tensor-core kernels (12 x 9 quantities =
 // the 128 rows of one MMA)
 constexpr int kTileElems = 12;
+// ... and of the acoustic (4-quantity, ocean) instantiation of the local one
+constexpr int kTileElemsFluid = 32;
 struct Seg {
   int64_t v_begin, n;
   double tcoef[8];   // dt^{k+1}/(k+1)!, k = 0..N (the cluster's own step)
@@ -121,7 +123,9 @@ Segs make_segs(const Seg* s, int n, int unit, int chunk = 1);
 // tensor-core (tcgen05, 3xTF32) local kernel, degree 5, FP32 dofs (local_tc.cu),
 // for elements without gravitational faces, fault faces or finer LTS neighbours
 // buffers: the launch's elements include some with an LTS buffer (a coarser neighbour)
-int launch_local_tc(const StepArgs& a, const Segs& g, int n_sms, void* stream, bool buffers);
+// acoustic: the launch's elements are fluid (mu = 0) without LTS buffer, on the
+// 4-quantity (p, v) instantiation; their stress must be isotropic (-p I)
+int launch_local_tc(const StepArgs& a, const Segs& g, int n_sms, void* stream, bool buffers, bool acoustic = false);
 void pack_local_tc(const double* kt, const double* kvol, const double* efc, float* out);
 int local_tc_floats();
 // tensor-core (tcgen05, 3xTF32) neighbour kernel, degree 5, FP32 dofs

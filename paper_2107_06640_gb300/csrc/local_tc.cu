@@ -27,6 +27,16 @@
 // worked on by two warpgroups that split every stage by 8-column chunks (even
 // chunks: first half, odd chunks: second half); one thread per tile issues
 // its MMAs and waits for their completion with a bounded mbarrier wait.
+//
+// Acoustic ocean (Sec. 4.1: the fluid is the elastic system with mu = 0;
+// stress -p I): the fluid instantiation works on the 4 quantities (p, v) only,
+// stored as the sigma_xx row (sigma_yy = sigma_zz = sigma_xx, no shear) and
+// the velocity rows.  A tile is then 32 elements x 4 quantities (warp w:
+// elements 8w..8w+7, lane 4j+p), all 128 rows in use; the star product is the
+// acoustic one, dsigma/dt = lambda div v and dv/dt = grad(sigma_xx) / rho in
+// the same Jacobian form; the element's face blocks are written in the full
+// 9-quantity layout (three equal normal-stress rows, zero shear), so
+// neighbours and the neighbour kernel see ordinary traces.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -41,8 +51,21 @@ namespace {
 
 constexpr int B = 56, B1 = 35, BF = 21;
 constexpr int FS = face_stride(5);  // 192 floats per face block of the trace array
-constexpr int TE = kTileElems;  // elements per tile
 constexpr int kThreadsL = 512;  // two tiles in flight, two warpgroups (halves) per tile
+
+// The medium of an instantiation: quantities per element (rows of the tile),
+// elements per warp and per tile, and the dofs row of quantity p.
+struct Elastic {
+  static constexpr bool fluid = false;
+  static constexpr int Q = 9, EW = 3, TE = kTileElems;
+  static __device__ __forceinline__ int row(int p) { return p; }
+};
+struct Acoustic {
+  static constexpr bool fluid = true;
+  static constexpr int Q = 4, EW = 8, TE = kTileElemsFluid;
+  static __device__ __forceinline__ int row(int p) { return p == 0 ? 0 : 5 + p; }  // sigma_xx, v_x, v_y, v_z
+};
+static_assert(Elastic::TE == 4 * Elastic::EW && Acoustic::TE == 4 * Acoustic::EW, "tile of 4 warps");
 constexpr int kWaitIters = 1 << 24;
 // trace staging: one face of a warp pair's three elements, element blocks of
 // kTS floats (16-byte aligned, the face block's 189 values then zeros); two
@@ -132,6 +155,29 @@ __device__ __forceinline__ void star_setup(int lane, bool valid, const float* pa
   s.src[2] = (lane >= 27 ? lane : base + q2);
 }
 
+// The acoustic star data of lane 4j + p (p = 0: sigma_xx = -p_pressure,
+// p = 1..3: v_x, v_y, v_z): the normal stress reads the three velocities with
+// lambda (mu = 0), velocity component d reads the normal stress in direction
+// d with 1/rho, the other two directions nothing.
+__device__ __forceinline__ void star_setup_acoustic(int lane, bool valid, const float* par, Star& s) {
+  const int p = lane & 3, base = lane & ~3;
+  float lam = 0.f, irho = 0.f;
+  if (valid) {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) s.g[k] = par[k];
+    irho = 1.f / par[9];
+    lam = par[10];
+  } else {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) s.g[k] = 0.f;
+  }
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    s.c[d] = p == 0 ? lam : (p == d + 1 ? irho : 0.f);
+    s.src[d] = p == 0 ? base + 1 + d : (p == d + 1 ? base : lane);
+  }
+}
+
 // one output of the star product from the three axis values of this lane
 __device__ __forceinline__ float star_apply(const Star& s, float y0, float y1, float y2) {
   const float X0 = s.g[0] * y0 + s.g[3] * y1 + s.g[6] * y2;
@@ -215,20 +261,24 @@ __device__ __forceinline__ bool pair_round(Lane& L, unsigned int* err, F&& issue
 // kBuf: some elements of the launch have an LTS buffer (a coarser neighbour)
 // tile: index within its segment; t2: this slot's tile after the next among
 // all tiles of the launch (kMulti: the launch has several segments)
-template <int H, bool kBuf, bool kMulti>
+template <class M, int H, bool kBuf, bool kMulti>
 __device__ __forceinline__ bool local_tile(Lane& L, const StepArgs& a, const Segs& g, int64_t t2, int64_t v_begin,
                                            int64_t n_virtual, int64_t tile) {
+  constexpr int TE = M::TE;
   float* const Q = reinterpret_cast<float*>(a.Q);
   const int64_t v0 = v_begin + tile * TE;
   const int64_t nrem = n_virtual - tile * TE;
   const int nE = (int)(nrem < TE ? nrem : TE);
-  const int jj = L.lane / 9, p = L.lane - 9 * (L.lane / 9);
-  const int i = 3 * L.w + jj;
-  const bool valid = L.lane < 27 && i < nE;
+  const int jj = L.lane / M::Q, p = L.lane - M::Q * (L.lane / M::Q);
+  const int i = M::EW * L.w + jj;
+  const bool valid = L.lane < M::EW * M::Q && i < nE;
   const int64_t v = v0 + (valid ? i : 0);
   const int64_t e = v / a.S;
   Star st;
-  star_setup(L.lane, valid, reinterpret_cast<const float*>(a.par) + e * PAR, st);
+  if constexpr (M::fluid)
+    star_setup_acoustic(L.lane, valid, reinterpret_cast<const float*>(a.par) + e * PAR, st);
+  else
+    star_setup(L.lane, valid, reinterpret_cast<const float*>(a.par) + e * PAR, st);
   const uint32_t trow = L.trow, tbase = L.tbase, sbase = L.sbase;
 
   // the tile after the next of this slot into L2 while this one is worked on
@@ -240,7 +290,7 @@ __device__ __forceinline__ bool local_tile(Lane& L, const StepArgs& a, const Seg
     }
   }
   // ---- D^0 = Q row: I = dt Q, A = Q
-  float* Qrow = Q + (v * 9 + p) * B;
+  float* Qrow = Q + (v * 9 + M::row(p)) * B;
   float I[B];
 #pragma unroll
   for (int c = H; c < B / 8; c += 2) {
@@ -323,7 +373,7 @@ __device__ __forceinline__ bool local_tile(Lane& L, const StepArgs& a, const Seg
   // copies each element's block with a bulk copy; two buffers alternate, the
   // copier waits until the copy before the last has read its buffer
   {
-    const int nmine = nE - 3 * L.w < 3 ? nE - 3 * L.w : 3;  // elements of this warp (may be <= 0)
+    const int nmine = nE - M::EW * L.w < M::EW ? nE - M::EW * L.w : M::EW;  // elements of this warp (may be <= 0)
     const bool copier = H == 0 && L.lane == 0;
     // this half's chunks c = H, H + 2, ... of the 88 trace columns, read once
     float tv[48];
@@ -331,7 +381,7 @@ __device__ __forceinline__ bool local_tile(Lane& L, const StepArgs& a, const Seg
     tc::ld3x8(trow + cAcc + 8 * (H + 6), trow + cAcc + 8 * (H + 8), trow + cAcc + 8 * (H == 0 ? 10 : 9), tv + 24);
     // an element with a coarser neighbour also adds its four face traces to
     // its LTS buffer, in FP64 (overwrite at the first of the two steps)
-    if (kBuf && L.btrace_mode && a.bslot && valid) {
+    if (kBuf && !M::fluid && L.btrace_mode && a.bslot && valid) {
       const int bs = a.bslot[e];
       if (bs >= 0) {
         double* bt = a.btrace + ((int64_t)bs * a.S + (v - e * a.S)) * 36 * BF;
@@ -349,29 +399,65 @@ __device__ __forceinline__ bool local_tile(Lane& L, const StepArgs& a, const Seg
         }
       }
     }
+    if constexpr (M::fluid) {
+      // acoustic: this face's (p, v) rows of the warp's eight elements in a
+      // compact buffer [element][4][21], then the warp pair writes each
+      // element's full face block (sigma_xx three times, zero shear, v,
+      // padding zeros) with 16-byte stores
+      float* sC = s_T[L.slot][L.w];
 #pragma unroll
-    for (int f = 0; f < 4; ++f) {
-      float* sTf = s_T[L.slot][L.w] + (f & 1) * kTB;
+      for (int f = 0; f < 4; ++f) {
 #pragma unroll
-      for (int cj = 0; cj < (H == 0 ? 6 : 5); ++cj) {
-        const int c = H + 2 * cj;
-        if (8 * c + 7 < BF * f || 8 * c >= BF * (f + 1)) continue;  // chunk outside face f
-        if (valid) {
+        for (int cj = 0; cj < (H == 0 ? 6 : 5); ++cj) {
+          const int c = H + 2 * cj;
+          if (8 * c + 7 < BF * f || 8 * c >= BF * (f + 1)) continue;  // chunk outside face f
+          if (valid) {
 #pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            const int col = 8 * c + j;
-            if (col >= BF * f && col < BF * (f + 1)) sTf[jj * kTS + p * BF + col - BF * f] = tv[8 * cj + j];
+            for (int j = 0; j < 8; ++j) {
+              const int col = 8 * c + j;
+              if (col >= BF * f && col < BF * (f + 1)) sC[(jj * 4 + p) * BF + col - BF * f] = tv[8 * cj + j];
+            }
           }
         }
+        warp_pair_bar(L.slot, L.w);
+        for (int k = L.lane + 32 * H; k < nmine * (FS / 4); k += 64) {
+          const int ej = k / (FS / 4), c4 = k - ej * (FS / 4);
+          float x[4];
+#pragma unroll
+          for (int t = 0; t < 4; ++t) {
+            const int idx = 4 * c4 + t, r = idx / BF, n = idx - BF * (idx / BF);
+            x[t] = (idx >= 9 * BF || (r >= 3 && r < 6)) ? 0.f : sC[(ej * 4 + (r < 3 ? 0 : r - 5)) * BF + n];
+          }
+          reinterpret_cast<float4*>(reinterpret_cast<float*>(a.trace) +
+                                    ((v0 + M::EW * L.w + ej) * 4 + f) * FS)[c4] = make_float4(x[0], x[1], x[2], x[3]);
+        }
+        warp_pair_bar(L.slot, L.w);  // the next face refills the buffer
       }
-      tc::fence_async_smem();
-      if (copier) tc::bulk_wait_read();  // the other buffer is free for face f + 1
-      warp_pair_bar(L.slot, L.w);
-      if (copier) {
-        for (int ej = 0; ej < nmine; ++ej)
-          tc::bulk_store(reinterpret_cast<float*>(a.trace) + ((v0 + 3 * L.w + ej) * 4 + f) * FS, sTf + ej * kTS,
-                         FS * 4);
-        tc::bulk_commit();
+    } else {
+#pragma unroll
+      for (int f = 0; f < 4; ++f) {
+        float* sTf = s_T[L.slot][L.w] + (f & 1) * kTB;
+#pragma unroll
+        for (int cj = 0; cj < (H == 0 ? 6 : 5); ++cj) {
+          const int c = H + 2 * cj;
+          if (8 * c + 7 < BF * f || 8 * c >= BF * (f + 1)) continue;  // chunk outside face f
+          if (valid) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              const int col = 8 * c + j;
+              if (col >= BF * f && col < BF * (f + 1)) sTf[jj * kTS + p * BF + col - BF * f] = tv[8 * cj + j];
+            }
+          }
+        }
+        tc::fence_async_smem();
+        if (copier) tc::bulk_wait_read();  // the other buffer is free for face f + 1
+        warp_pair_bar(L.slot, L.w);
+        if (copier) {
+          for (int ej = 0; ej < nmine; ++ej)
+            tc::bulk_store(reinterpret_cast<float*>(a.trace) + ((v0 + M::EW * L.w + ej) * 4 + f) * FS,
+                           sTf + ej * kTS, FS * 4);
+          tc::bulk_commit();
+        }
       }
     }
   }
@@ -406,10 +492,16 @@ __device__ __forceinline__ bool local_tile(Lane& L, const StepArgs& a, const Seg
 #pragma unroll
     for (int j = 0; j < 8; ++j) x[j] = -star_apply(st, y[j], y[8 + j], y[16 + j]);
     if (valid) {
-      float4* dst = reinterpret_cast<float4*>(Qrow + 8 * c);
       const float4 q0 = qv[c - H], q1 = qv[c - H + 1];
-      dst[0] = make_float4(q0.x + x[0], q0.y + x[1], q0.z + x[2], q0.w + x[3]);
-      dst[1] = make_float4(q1.x + x[4], q1.y + x[5], q1.z + x[6], q1.w + x[7]);
+      const float4 n0 = make_float4(q0.x + x[0], q0.y + x[1], q0.z + x[2], q0.w + x[3]);
+      const float4 n1 = make_float4(q1.x + x[4], q1.y + x[5], q1.z + x[6], q1.w + x[7]);
+      // (acoustic: the normal-stress row is written as sigma_xx, sigma_yy and sigma_zz)
+#pragma unroll
+      for (int r = 0; r < (M::fluid && p == 0 ? 3 : 1); ++r) {
+        float4* dst = reinterpret_cast<float4*>(Qrow + r * B + 8 * c);
+        dst[0] = n0;
+        dst[1] = n1;
+      }
     }
   }
   // the next tile's first MMA overwrites these columns only after the
@@ -418,8 +510,9 @@ __device__ __forceinline__ bool local_tile(Lane& L, const StepArgs& a, const Seg
   return true;
 }
 
-// kChunk: consecutive tiles a slot takes per sweep (a compile-time launch shape)
-template <bool kBuf, bool kMulti, int kChunk>
+// M: the medium (Elastic or Acoustic); kChunk: consecutive tiles a slot takes
+// per sweep (a compile-time launch shape)
+template <class M, bool kBuf, bool kMulti, int kChunk>
 __global__ void __launch_bounds__(kThreadsL, 1) local_tc_kernel(StepArgs a, const __grid_constant__ Segs g) {
   float* sm = reinterpret_cast<float*>(smem_raw);
   __shared__ uint32_t tmem_base;
@@ -462,8 +555,8 @@ __global__ void __launch_bounds__(kThreadsL, 1) local_tc_kernel(StepArgs a, cons
     for (int k = 0; k < 6; ++k) L.tcf[k] = (float)sg.tcoef[k];
     L.btrace_mode = sg.btrace_mode;
     const int64_t lt = tile - g.first[&sg - g.s];
-    return half == 0 ? local_tile<0, kBuf, kMulti>(L, a, g, t2, sg.v_begin, sg.n, lt)
-                     : local_tile<1, kBuf, kMulti>(L, a, g, t2, sg.v_begin, sg.n, lt);
+    return half == 0 ? local_tile<M, 0, kBuf, kMulti>(L, a, g, t2, sg.v_begin, sg.n, lt)
+                     : local_tile<M, 1, kBuf, kMulti>(L, a, g, t2, sg.v_begin, sg.n, lt);
   };
   if constexpr (kChunk == 1) {
     for (int64_t tile = me; tile < ntiles; tile += slots)
@@ -486,29 +579,40 @@ __global__ void __launch_bounds__(kThreadsL, 1) local_tc_kernel(StepArgs a, cons
 
 }  // namespace
 
-int launch_local_tc(const StepArgs& a, const Segs& g, int n_sms, void* stream, bool buffers) {
+int launch_local_tc(const StepArgs& a, const Segs& g, int n_sms, void* stream, bool buffers, bool acoustic) {
   using K = void (*)(StepArgs, Segs);
-  // [kBuf][kMulti][chunk 1, 2, 4]
+  // elastic [kBuf][kMulti][chunk 1, 2, 4]; acoustic [kMulti][chunk] (its elements have no LTS buffer)
   static const K kern[2][2][3] = {
-      {{local_tc_kernel<false, false, 1>, local_tc_kernel<false, false, 2>, local_tc_kernel<false, false, 4>},
-       {local_tc_kernel<false, true, 1>, local_tc_kernel<false, true, 2>, local_tc_kernel<false, true, 4>}},
-      {{local_tc_kernel<true, false, 1>, local_tc_kernel<true, false, 2>, local_tc_kernel<true, false, 4>},
-       {local_tc_kernel<true, true, 1>, local_tc_kernel<true, true, 2>, local_tc_kernel<true, true, 4>}}};
+      {{local_tc_kernel<Elastic, false, false, 1>, local_tc_kernel<Elastic, false, false, 2>,
+        local_tc_kernel<Elastic, false, false, 4>},
+       {local_tc_kernel<Elastic, false, true, 1>, local_tc_kernel<Elastic, false, true, 2>,
+        local_tc_kernel<Elastic, false, true, 4>}},
+      {{local_tc_kernel<Elastic, true, false, 1>, local_tc_kernel<Elastic, true, false, 2>,
+        local_tc_kernel<Elastic, true, false, 4>},
+       {local_tc_kernel<Elastic, true, true, 1>, local_tc_kernel<Elastic, true, true, 2>,
+        local_tc_kernel<Elastic, true, true, 4>}}};
+  static const K kfl[2][3] = {
+      {local_tc_kernel<Acoustic, false, false, 1>, local_tc_kernel<Acoustic, false, false, 2>,
+       local_tc_kernel<Acoustic, false, false, 4>},
+      {local_tc_kernel<Acoustic, false, true, 1>, local_tc_kernel<Acoustic, false, true, 2>,
+       local_tc_kernel<Acoustic, false, true, 4>}};
   const int rc = configure_on_device((const void*)kern[0][0][0], [] {
     cudaError_t ce = cudaSuccess;
-    for (int i = 0; i < 12; ++i)
-      if (ce == cudaSuccess)
-        ce = cudaFuncSetAttribute((const void*)kern[i / 6][(i / 3) % 2][i % 3], cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  LImg::bytes);
+    for (int i = 0; i < 18; ++i) {
+      const K k = i < 12 ? kern[i / 6][(i / 3) % 2][i % 3] : kfl[(i - 12) / 3][(i - 12) % 3];
+      if (ce == cudaSuccess) ce = cudaFuncSetAttribute((const void*)k, cudaFuncAttributeMaxDynamicSharedMemorySize, LImg::bytes);
+    }
     return ce;
   });
   if (rc) return rc;
   const int64_t ntiles = g.n ? g.first[g.n] : 0;
   if (ntiles <= 0) return 0;
+  if (acoustic && buffers) return (int)cudaErrorInvalidValue;
   const int ci = g.chunk >= 4 ? 2 : (g.chunk >= 2 ? 1 : 0);
   const int64_t want = (ntiles + 1) / 2;
   const unsigned grid = (unsigned)(want < n_sms ? want : n_sms);
-  kern[buffers ? 1 : 0][g.n > 1 ? 1 : 0][ci]<<<grid, kThreadsL, LImg::bytes, (cudaStream_t)stream>>>(a, g);
+  const K k = acoustic ? kfl[g.n > 1 ? 1 : 0][ci] : kern[buffers ? 1 : 0][g.n > 1 ? 1 : 0][ci];
+  k<<<grid, kThreadsL, LImg::bytes, (cudaStream_t)stream>>>(a, g);
   return (int)cudaGetLastError();
 }
 

@@ -112,7 +112,14 @@ __device__ void traction(const double q[9], const double n[3], double t[3]) {
   t[2] = q[5] * n[0] + q[4] * n[1] + q[2] * n[2];
 }
 
-// friction-guess network (FP32): features -> predicted ln V* - x_a
+__device__ __forceinline__ float tanh_hw(float x) {  // the hardware tanh approximation (MUFU)
+  float y;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// friction-guess network (FP32, weights W in shared memory, 16-byte aligned
+// rows): features -> predicted ln V* - x_a
 __device__ float mlp_eval(const float* W, const float f[MLP_IN]) {
   const float* W1 = W;
   const float* b1 = W1 + MLP_IN * MLP_H;
@@ -126,17 +133,24 @@ __device__ float mlp_eval(const float* W, const float f[MLP_IN]) {
   float x[MLP_IN], h1[MLP_H];
 #pragma unroll
   for (int i = 0; i < MLP_IN; ++i) x[i] = (f[i] - mu[i]) / sd[i];
+#pragma unroll
   for (int j = 0; j < MLP_H; ++j) {
     float s = b1[j];
 #pragma unroll
     for (int i = 0; i < MLP_IN; ++i) s += W1[j * MLP_IN + i] * x[i];
-    h1[j] = tanhf(s);
+    h1[j] = tanh_hw(s);
   }
   float y = b3[0];
+#pragma unroll 4
   for (int j = 0; j < MLP_H; ++j) {
+    const float4* w = reinterpret_cast<const float4*>(W2 + j * MLP_H);
     float s = b2[j];
-    for (int i = 0; i < MLP_H; ++i) s += W2[j * MLP_H + i] * h1[i];
-    y += w3[j] * tanhf(s);
+#pragma unroll
+    for (int i = 0; i < MLP_H / 4; ++i) {
+      const float4 q = w[i];
+      s += q.x * h1[4 * i] + q.y * h1[4 * i + 1] + q.z * h1[4 * i + 2] + q.w * h1[4 * i + 3];
+    }
+    y += w3[j] * tanh_hw(s);
   }
   return osc[0] + osc[1] * y;
 }
@@ -144,6 +158,11 @@ __device__ float mlp_eval(const float* W, const float f[MLP_IN]) {
 template <typename T, int N>
 __global__ void __launch_bounds__(128) rupture_kernel(DRArgs a) {
   constexpr int Bf = nb2(N);
+  __shared__ __align__(16) float sW[(MLP_NPARAM + 3) / 4 * 4];  // the network's weights, once per block
+  if (a.mlp) {
+    for (int i = threadIdx.x; i < MLP_NPARAM; i += blockDim.x) sW[i] = a.mlp[i];
+  }
+  __syncthreads();
   const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t total = a.n_faces * a.S * Bf;
   if (id >= total) return;
@@ -178,6 +197,10 @@ __global__ void __launch_bounds__(128) rupture_kernel(DRArgs a) {
   double tprev = 0.0;
   double xhat_prev = 0.0;  // the network's ln V* at the previous time point
   bool have_prev = false;
+  // the first-pass Newton at the previous time point needed more than one
+  // iteration: the state is changing here, and only then is the network
+  // evaluated (where the warm start already converges it cannot help)
+  bool busy = false;
   unsigned long long n_solves = 0, n_iters = 0;
   bool all_ok = true;
   for (int j = 0; j <= N; ++j) {
@@ -235,16 +258,19 @@ __global__ void __launch_bounds__(128) rupture_kernel(DRArgs a) {
       feat[3] = (float)xwc;
       feat[4] = (float)fmin(fmax(log(eta / (S * p.a)), -50.0), 50.0);
       feat[5] = (float)xa;
-      if (a.mlp) {
-        // predicted ln V* = x_a + network; from the second time point on, the
-        // start is the warm start moved by the change of that prediction
-        const double xhat = xa + (double)mlp_eval(a.mlp, feat);
+      if (a.mlp && busy) {
+        // predicted ln V* = x_a + network; when it was also evaluated at the
+        // previous time point, the start is the warm start moved by the change
+        // of that prediction
+        const double xhat = xa + (double)mlp_eval(sW, feat);
         if (have_prev) {
           x0 = fmin(fmax(xwc + (xhat - xhat_prev), kXFloor), xhi);
           learned = true;
         }
         xhat_prev = xhat;
         have_prev = true;
+      } else {
+        have_prev = false;
       }
     } else {
       have_prev = false;
@@ -281,6 +307,7 @@ __global__ void __launch_bounds__(128) rupture_kernel(DRArgs a) {
         n_solves++;
         n_iters += it;
       }
+      if (pass == 0) busy = solve && it > 1;
       if (pass == 0 && solve && a.capture) {
         const unsigned long long k = atomicAdd(a.cap_count, 1ull);
         if ((int64_t)k < a.cap_capacity) {

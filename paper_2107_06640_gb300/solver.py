@@ -25,7 +25,7 @@ def plan(xyz, tets, face_tag, rho, lam, mu, face_partner=None, degree=5, cfl=0.3
 class Solver:
     def __init__(self, xyz, tets, face_tag, rho, lam, mu, face_partner=None, degree=5,
                  precision=L.ADG_FP64, cfl=0.35, gravity=9.81, max_clusters=1, ensemble=1,
-                 device=0, stream=None):
+                 device=0, stream=None, acoustic_ocean=False):
         cfg = L.adg_default_config()
         cfg.degree = degree
         cfg.precision = precision
@@ -39,6 +39,8 @@ class Solver:
         try:
             L.adg_upload_mesh(self.ctx, xyz, tets, face_tag, face_partner)
             L.adg_upload_material(self.ctx, rho, lam, mu)
+            if acoustic_ocean:
+                L.adg_set_acoustic_ocean(self.ctx, True)
             L.adg_init(self.ctx)
         except Exception:
             L.adg_destroy(self.ctx)

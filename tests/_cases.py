@@ -21,14 +21,14 @@ def rel_l2(a, b):
     return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
 
 
-def make_pair(mesh, mat, N, precision=0, cfl=0.5, g=9.81, max_clusters=1, ensemble=1):
+def make_pair(mesh, mat, N, precision=0, cfl=0.5, g=9.81, max_clusters=1, ensemble=1, acoustic_ocean=False):
     from paper_2107_06640_gb300 import Solver
     rho, lam, mu = mat
     o = Oracle(mesh.xyz, mesh.tets, mesh.face_tag, mesh.face_partner, rho, lam, mu, N, cfl=cfl, g=g,
                max_clusters=max_clusters)
     s = Solver(mesh.xyz, mesh.tets, mesh.face_tag, rho, lam, mu, face_partner=mesh.face_partner,
                degree=N, precision=precision, cfl=cfl, gravity=g, max_clusters=max_clusters,
-               ensemble=ensemble)
+               ensemble=ensemble, acoustic_ocean=acoustic_ocean)
     return o, s
 
 
