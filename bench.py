@@ -32,7 +32,8 @@ sys.path.insert(0, ROOT)
 N_DEG = 5
 METRIC = "ADER-DG element-updates/s at order 6, FP32/batched vs FP64; % of roofline"
 UNIT = "element-updates/s"
-WORKLOAD = "coupled ocean-crust box 100x100x40 km, 1,497,600 tets, degree 5, gravitational surface"
+WORKLOAD = ("coupled ocean-crust box 100x100x40 km, 1,497,600 tets, degree 5, gravitational surface, "
+            "acoustic ocean")
 
 
 def flops_per_update(N):
@@ -66,13 +67,15 @@ def bytes_per_update(N, w):
     FS = (9 * Bf + 3) // 4 * 4
     return {"local_kernel": (2 * 9 * B + 4 * 9 * Bf) * w, "neighbour_kernel": (2 * 9 * B + 8 * 9 * Bf) * w,
             "local_tc_kernel": (2 * 9 * B + 4 * FS + 16) * w,
+            # acoustic element: reads its 4 (p, v) rows, writes the three normal-stress rows and v
+            "local_tc_kernel_acoustic": ((4 + 6) * B + 4 * FS + 16) * w,
             "neighbour_tc_kernel": (2 * 9 * B + 8 * FS + 16) * w + 4 * 32}
 
 
 # DRAM bytes (read + write) per element of the tensor-core kernels, from the
 # full ncu capture of the 374,400-tet box (profiles/tensor_core_kernels_box40.md);
 # a launch's traffic is scaled from it by the number of elements
-TC_DRAM_BYTES_PER_ELEMENT = {"local_tc_kernel": 7012.7}
+TC_DRAM_BYTES_PER_ELEMENT = {}
 
 
 def load_peaks():
@@ -302,7 +305,8 @@ def run_other_workload(args):
     __graft_entry__.build()
     import paper_2107_06640_gb300 as pkg
     from paper_2107_06640_gb300 import Solver, _lib
-    from synthetic.workloads import coupled_box, fault_box, lsw_fault_params, rs_fault_params, uplift_scenarios
+    from synthetic.workloads import (coupled_box, fault_box, lsw_fault_params, random_dofs, rs_fault_params,
+                                     uplift_scenarios)
     torch.cuda.set_device(0)
     stream = torch.cuda.current_stream()
     steps, warm = args.steps, args.warmup
@@ -314,7 +318,7 @@ def run_other_workload(args):
         bathy = lambda x, y: -2000.0 + 500.0 * np.sin(2 * np.pi * x / L) * np.sin(2 * np.pi * y / L)
         m, (rho, lam, mu) = coupled_box(nxy=200, bathy=bathy, grading=32.0)
         s = Solver(m.xyz, m.tets, m.face_tag, rho, lam, mu, degree=N_DEG, precision=pkg.ADG_3XTF32, cfl=0.35,
-                   max_clusters=6, stream=stream.cuda_stream)
+                   max_clusters=6, stream=stream.cuda_stream, acoustic_ocean=True)
         ef, nxyz = s.gravity_faces()
         s.set_eta(np.exp(-((nxyz[..., 0] - L / 2) ** 2 + (nxyz[..., 1] - L / 2) ** 2) / (2 * 8e3 ** 2))[:, None, :])
         info = s.info
@@ -348,10 +352,26 @@ def run_other_workload(args):
                                       f"{law}, {s.nt} tets, degree 4",
                           "n_tets": s.nt, "fault_faces": nff, "fault_nodes": nff * s.Bf}
         line["dtype"] = "f32 (friction f64)"
+    elif args.workload == "ocean":
+        # ocean-dominated coupled box (34 of 39 layers water, like the ocean share of the paper's mesh L),
+        # acoustic ocean; the same box on the 9-quantity local kernel is timed below for comparison
+        m, (rho, lam, mu) = coupled_box(nxy=80, n_water=34, n_crust=5, water=34e3)
+        Q0 = random_dofs((m.nt, 9, 56), 0, N=N_DEG) * 1e-4
+        mk = lambda ac: Solver(m.xyz, m.tets, m.face_tag, rho, lam, mu, degree=N_DEG, precision=pkg.ADG_3XTF32,
+                               cfl=0.35, stream=stream.cuda_stream, acoustic_ocean=ac)
+        s = mk(True)
+        s.set_dofs(Q0)
+        s.set_eta(np.zeros((int(s.info.n_gravity_faces), 1, s.Bf)))
+        upd = int(s.info.updates_per_macro)
+        line["config"] = {"workload": f"ocean-dominated coupled box 100x100x40 km, 34 km water over 6 km crust, "
+                                      f"{s.nt} tets ({int((mu == 0).sum())} fluid), degree 5, acoustic ocean",
+                          "n_tets": s.nt, "fluid_tets": int((mu == 0).sum()),
+                          "acoustic_kernel_updates": int(s.info.acoustic_updates_per_macro)}
+        line["dtype"] = "f32 (3xTF32 tensor-core products)"
     elif args.workload == "record":
         m, (rho, lam, mu), Q0 = make_workload(seed=0, nxy=args.nxy)
         s = Solver(m.xyz, m.tets, m.face_tag, rho, lam, mu, degree=N_DEG, precision=pkg.ADG_3XTF32, cfl=0.35,
-                   stream=stream.cuda_stream)
+                   stream=stream.cuda_stream, acoustic_ocean=True)
         s.set_dofs(Q0)
         s.set_eta(np.zeros((int(s.info.n_gravity_faces), 1, s.Bf)))
         pick = np.random.default_rng(0).choice(m.nt, 1000, replace=False)
@@ -364,7 +384,7 @@ def run_other_workload(args):
         S = 32
         m, (rho, lam, mu) = coupled_box(nxy=66)
         s = Solver(m.xyz, m.tets, m.face_tag, rho, lam, mu, degree=N_DEG, precision=pkg.ADG_3XTF32, cfl=0.35,
-                   ensemble=S, stream=stream.cuda_stream)
+                   ensemble=S, stream=stream.cuda_stream, acoustic_ocean=True)
         ef, nxyz = s.gravity_faces()
         eta0 = np.stack([f(nxyz[..., 0], nxyz[..., 1]) for f in uplift_scenarios(S, seed=0)], axis=1)
         s.set_eta(eta0)
@@ -405,6 +425,17 @@ def run_other_workload(args):
                              "clocks_with": clk_r}
         line["value"] = upd * steps / (ms_r * 1e-3)
         line["ms_per_step"] = ms_r / steps
+    if args.workload == "ocean":
+        # the same box, its fluid on the 9-quantity kernels (the ocean embedded in the elastic system)
+        del s
+        s9 = mk(False)
+        s9.set_dofs(Q0)
+        s9.set_eta(np.zeros((int(s9.info.n_gravity_faces), 1, s9.Bf)))
+        _lib.adg_autotune(s9.ctx, reps=1)
+        ms9, clk9 = _timed_advance(s9, steps, warm, stream, torch, "ocean9")
+        kms9, _ = _lib.adg_profile(s9.ctx, 1)
+        line["nine_quantity_ocean"] = {"value": upd * steps / (ms9 * 1e-3), "ms_per_step": ms9 / steps,
+                                       "kernel_ms": {"local": kms9[0], "neighbour": kms9[1]}, "clocks": clk9}
     if args.workload == "rupture-lsw":
         st = _lib.adg_read_fault(s.ctx, np.empty((nff, 1, s.Bf, 8)))
         line["rupture"] = {"slipping_node_fraction": float(np.mean(st[..., 0] > 1e-3)),
@@ -446,9 +477,9 @@ def main():
     ap.add_argument("--only", default=None, choices=["fp64", "fp32", "3xtf32"],
                     help="profiling aid: run one precision of the coupled workload, print no JSON line")
     ap.add_argument("--workload", default="coupled",
-                    choices=["coupled", "lts", "rupture", "rupture-lsw", "ensemble", "record"],
-                    help="coupled: the headline line; lts / rupture / rupture-lsw / ensemble / record: the other "
-                         "workloads")
+                    choices=["coupled", "lts", "rupture", "rupture-lsw", "ensemble", "record", "ocean"],
+                    help="coupled: the headline line; lts / rupture / rupture-lsw / ensemble / record / ocean: the "
+                         "other workloads")
     ap.add_argument("--fault-scale", type=int, default=5,
                     help="megathrust refinement r: 32r x 40r x 18r hex columns (3: 3.73 M tets, 5: 17.3 M tets)")
     ap.add_argument("--clock-dir", default=None,
@@ -500,7 +531,7 @@ def main():
         # profiling aid: one precision, a short run, no JSON line
         prec = {"fp64": pkg.ADG_FP64, "fp32": pkg.ADG_FP32, "3xtf32": pkg.ADG_3XTF32}[args.only]
         s = Solver(m.xyz, m.tets, m.face_tag, rho, lam, mu, degree=N_DEG, precision=prec, cfl=0.35,
-                   device=local, stream=stream.cuda_stream)
+                   device=local, stream=stream.cuda_stream, acoustic_ocean=True)
         s.set_dofs(Q0)
         s.advance(args.warmup + args.steps)
         s.sync()
@@ -508,7 +539,7 @@ def main():
         return
     for prec, steps, warm in runs:
         s = Solver(m.xyz, m.tets, m.face_tag, rho, lam, mu, degree=N_DEG, precision=prec, cfl=0.35,
-                   device=local, stream=stream.cuda_stream)
+                   device=local, stream=stream.cuda_stream, acoustic_ocean=True)
         s.set_dofs(Q0)
         s.set_eta(np.zeros((int(s.info.n_gravity_faces), 1, s.Bf)))
         upd = int(s.info.updates_per_macro)
@@ -549,7 +580,7 @@ def main():
     s64 = res[pkg.ADG_FP64]["solver"]
     n64 = res[pkg.ADG_FP64]["advanced"]
     sa = Solver(m.xyz, m.tets, m.face_tag, rho, lam, mu, degree=N_DEG, precision=HEAD, cfl=0.35,
-                device=local, stream=stream.cuda_stream)
+                device=local, stream=stream.cuda_stream, acoustic_ocean=True)
     sa.set_dofs(Q0)
     sa.set_eta(np.zeros((int(sa.info.n_gravity_faces), 1, sa.Bf)))
     sa.advance(n64)
@@ -601,6 +632,7 @@ def main():
     # elements of one launch of the dominant kernel and that launch's own duration:
     # with the tensor-core form the tensor-core launches are timed alone (kms[3], kms[4])
     n_tc = int(s.info.tensor_core_updates_per_macro)
+    n_ac = int(s.info.acoustic_updates_per_macro)  # of those, on the 4-quantity local kernel
     tc_form = HEAD == pkg.ADG_3XTF32 and n_tc > 0
     t_k = [kms[3], kms[4]] if tc_form else [kms[0], kms[1]]
     n_k = n_tc if tc_form else s.nt
@@ -612,16 +644,22 @@ def main():
     n_sm = torch.cuda.get_device_properties(local).multi_processor_count
     alu_peak, alu_src = alu_peak_tflops(False, peaks.get("sm_max_mhz", 2070.0), units, n_sm)
     achieved_flops = fl[kname.replace("_tc", "")] * n_k / (t_k[dom] * 1e-3) / 1e12
-    achieved_bytes = by[kname] * n_k / (t_k[dom] * 1e-3) / 1e9
+    # an acoustic element's reference-matrix products act on 4 of the 9 quantity rows
+    local_bytes = by["local_tc_kernel"] * (n_k - n_ac) + by["local_tc_kernel_acoustic"] * n_ac
+    launch_bytes = local_bytes if kname == "local_tc_kernel" else by[kname] * n_k
+    achieved_bytes = launch_bytes / (t_k[dom] * 1e-3) / 1e9
     frac_alu = achieved_flops / alu_peak
     frac_hbm = achieved_bytes / peaks["hbm_gbs"]
     tc_peak, tc_src = tf32x3_peak_tflops(peaks, units)
-    achieved_tc = fl["local_tensor"] * n_k / (t_k[0] * 1e-3) / 1e12 if tc_form else None
+    tensor_flops = fl["local_tensor"] * ((n_k - n_ac) + n_ac * 4.0 / 9.0)
+    achieved_tc = tensor_flops / (t_k[0] * 1e-3) / 1e12 if tc_form else None
     if kname == "local_tc_kernel":
         roof = {"bound": "tensor", "achieved": achieved_tc, "peak": tc_peak, "unit": "TFLOP/s",
                 "frac": achieved_tc / tc_peak, "traffic": None, "kernel": kname,
                 "peak_source": tc_src,
-                "flops_counted": "reference-matrix products only (predictor levels 0-2, volume, traces)"}
+                "flops_counted": "reference-matrix products only (predictor levels 0-2, volume, traces); "
+                                 "an acoustic element's count 4/9 of an elastic one's",
+                "elements": {"elastic": n_k - n_ac, "acoustic": n_ac}}
     elif kname == "neighbour_tc_kernel":
         # the lift runs on the tensor cores and the fluxes are ~27 kflop per update:
         # HBM (traces, flux matrices, dofs) is the roof
@@ -645,7 +683,7 @@ def main():
     if tc_form:
         roof.update({"tc_kernel_ms": {"local_tc": kms[3], "neighbour_tc": kms[4]},
                      "local_tc_tensor_frac": achieved_tc / tc_peak,
-                     "local_tc_hbm_frac": by["local_tc_kernel"] * n_k / (kms[3] * 1e-3) / 1e9 / peaks["hbm_gbs"],
+                     "local_tc_hbm_frac": local_bytes / (kms[3] * 1e-3) / 1e9 / peaks["hbm_gbs"],
                      "neighbour_tc_hbm_frac": by["neighbour_tc_kernel"] * n_k / (kms[4] * 1e-3) / 1e9
                      / peaks["hbm_gbs"]})
     r64k = r64["kms"]

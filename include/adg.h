@@ -95,6 +95,8 @@ typedef struct adg_info {
   int64_t device_bytes;
   int64_t tensor_core_updates_per_macro; /* of those, by the tensor-core kernels (ADG_3XTF32, degree 5) */
   int64_t n_receivers;       /* from the last adg_add_receivers */
+  int64_t acoustic_updates_per_macro; /* of the tensor-core ones, on the 4-quantity local kernel
+                                         (adg_set_acoustic_ocean) */
 } adg_info;
 
 /* Default configuration: N=5, FP64, cfl 0.35 (Sec. 6), g 9.81, GTS, S=1. */

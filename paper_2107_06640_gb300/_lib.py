@@ -40,7 +40,7 @@ class adg_info(C.Structure):
                 ("macro_dt", C.c_double), ("time", C.c_double), ("n_gravity_faces", C.c_int64),
                 ("n_fault_faces", C.c_int64), ("updates_per_macro", C.c_int64),
                 ("device_bytes", C.c_int64), ("tensor_core_updates_per_macro", C.c_int64),
-                ("n_receivers", C.c_int64)]
+                ("n_receivers", C.c_int64), ("acoustic_updates_per_macro", C.c_int64)]
 
 
 _P = C.c_void_p

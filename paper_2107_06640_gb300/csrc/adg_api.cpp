@@ -288,6 +288,9 @@ int adg_query(const adg_ctx* ctx, adg_info* out) {
   for (int i = 0; i < c.ncl && i < (int)c.cl_plain.size(); ++i) utc += c.cl_plain[i] * ((int64_t)1 << (c.ncl - 1 - i));
   out->tensor_core_updates_per_macro = utc * c.S;
   out->n_receivers = c.n_rec;
+  int64_t ua = 0;
+  for (int i = 0; i < c.ncl && i < (int)c.cl_fluid.size(); ++i) ua += c.cl_fluid[i] * ((int64_t)1 << (c.ncl - 1 - i));
+  out->acoustic_updates_per_macro = ua * c.S;
   return ADG_OK;
 }
 
