@@ -72,10 +72,12 @@ def bytes_per_update(N, w):
             "neighbour_tc_kernel": (2 * 9 * B + 8 * FS + 16) * w + 4 * 32}
 
 
-# DRAM bytes (read + write) per element of the tensor-core kernels, from the
-# full ncu capture of the 374,400-tet box (profiles/tensor_core_kernels_box40.md);
-# a launch's traffic is scaled from it by the number of elements
-TC_DRAM_BYTES_PER_ELEMENT = {}
+# DRAM bytes (read + write) per element of the tensor-core kernels (elastic and
+# acoustic local, neighbour), from the one-kernel ncu captures of the
+# 374,400-tet box (profiles/tensor_core_kernels_box40.md); a launch's traffic
+# is scaled from them by its elements of each kind
+TC_DRAM_BYTES_PER_ELEMENT = {"local_tc_kernel": 6996.9, "local_tc_kernel_acoustic": 5618.0,
+                             "neighbour_tc_kernel": 7561.5}
 
 
 def load_peaks():
@@ -674,7 +676,9 @@ def main():
         roof = {"bound": "hbm", "achieved": achieved_bytes, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": frac_hbm, "traffic": None, "kernel": kname, "peak_source": src}
     if kname in TC_DRAM_BYTES_PER_ELEMENT:
-        roof["traffic"] = TC_DRAM_BYTES_PER_ELEMENT[kname] * n_k
+        roof["traffic"] = (TC_DRAM_BYTES_PER_ELEMENT[kname] * (n_k - n_ac) +
+                           TC_DRAM_BYTES_PER_ELEMENT["local_tc_kernel_acoustic"] * n_ac
+                           if kname == "local_tc_kernel" else TC_DRAM_BYTES_PER_ELEMENT[kname] * n_k)
         roof["traffic_note"] = "DRAM bytes per launch, ncu on the 374,400-tet box scaled by elements"
     roof.update({"ms_per_launch": t_k[dom], "elements_per_launch": n_k, "hbm_frac": frac_hbm,
                  # the CUDA-core ALU fraction of a tensor-core kernel's whole flop count means nothing
