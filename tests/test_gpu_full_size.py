@@ -196,3 +196,137 @@ def test_full_size_lts_first_tick_sampled():
     assert rel_l2(to_oracle_layout(got), o.Q[sel]) <= 1e-5, rel_l2(to_oracle_layout(got), o.Q[sel])
     # the samples moved (a zero update would pass trivially)
     assert rel_l2(to_oracle_layout(Qk[sel].astype(np.float64)), o.Q[sel]) > 1e-3
+
+
+def _face_neighbours(tets):
+    """[nt][4] face neighbour of each tet face (-1 on the boundary), by
+    matching the sorted vertex triples of all faces."""
+    fv = np.array([[1, 2, 3], [0, 2, 3], [0, 1, 3], [0, 1, 2]])
+    tri = np.sort(tets[:, fv], axis=2)
+    nv = int(tets.max()) + 1
+    key = ((tri[..., 0] * nv + tri[..., 1]) * nv + tri[..., 2]).ravel()
+    order = np.argsort(key, kind="stable")
+    sk = key[order]
+    same = np.nonzero(sk[1:] == sk[:-1])[0]
+    a, b = order[same], order[same + 1]
+    nbr = np.full(key.size, -1, np.int64)
+    nbr[a] = b // 4
+    nbr[b] = a // 4
+    return nbr.reshape(-1, 4)
+
+
+def _lts_support(nbr, cl, patch, cmax):
+    """A superset of the elements whose dofs can be non-zero after one rate-2
+    LTS macro step (Sec. 4.4) that starts from dofs non-zero only on `patch`:
+    at every tick s, in cluster order, each cluster c with (s+1) % 2^c == 0
+    ends a step, and an element of it joins when a face neighbour is already
+    in (a prediction, an LTS buffer or a Taylor integral of a neighbour only
+    carries data the neighbour had by then)."""
+    supp = np.zeros(cl.size, bool)
+    supp[patch] = True
+    idx = np.array(patch, np.int64)
+    for s in range(1 << cmax):
+        for c in range(cmax + 1):
+            if (s + 1) % (1 << c):
+                continue
+            cand = np.unique(nbr[idx].ravel())
+            cand = cand[cand >= 0]
+            cand = cand[(cl[cand] == c) & ~supp[cand]]
+            supp[cand] = True
+            idx = np.concatenate([idx, cand])
+    return np.sort(idx)
+
+
+def test_full_size_lts_whole_macro_step_sampled():
+    """The LTS workload at its benchmark size and launch configuration
+    (9,360,000 tets graded 32x, 6 rate-2 clusters, degree 5, 3xTF32, acoustic
+    ocean) over one whole macro step of 32 ticks.  The dofs start non-zero on
+    three patches only, each a tet and its face neighbours at a cluster border
+    (1|0, 2|3 and 4|5), chosen with a seeded search for small supports, so
+    that between them every cluster steps with data, takes LTS buffers from a
+    finer neighbour and Taylor integrals from a coarser one.  Every element outside
+    the patches' support (a superset of where data can arrive within the
+    macro step) must still be exactly zero; the support, as a small mesh with
+    the library's clusters and dt_min, is stepped by the oracle's LTS macro
+    step and compared element by element.  Tolerance as for the other 3xTF32
+    macro steps."""
+    if _mem_available_gb() < 48.0:
+        pytest.skip("needs 48 GB of free host memory for the 9.36 M-tet mesh")
+    from oracle.ader import Oracle
+    from paper_2107_06640_gb300 import ADG_3XTF32, Solver
+    from synthetic.workloads import coupled_box
+    L = 100e3
+    bathy = lambda x, y: -2000.0 + 500.0 * np.sin(2 * np.pi * x / L) * np.sin(2 * np.pi * y / L)
+    m, mat = coupled_box(nxy=200, bathy=bathy, grading=32.0)
+    assert m.nt == 9360000
+    s = Solver(m.xyz, m.tets, m.face_tag, *mat, degree=5, cfl=0.35, precision=ADG_3XTF32, max_clusters=6,
+               acoustic_ocean=True)
+    _, cl, dtmin, ncl = s.plan()
+    assert ncl == 6
+    cmax = ncl - 1
+    nbr = _face_neighbours(m.tets)
+    rng = np.random.default_rng(43)
+    taken = np.zeros(m.nt, bool)
+    patches, supports = [], []
+    for a, b in ((1, 0), (2, 3), (4, 5)):
+        inner = np.nonzero(cl == a)[0]
+        nb = nbr[inner]
+        border = np.zeros(inner.size, bool)
+        for f in range(4):
+            v = nb[:, f] >= 0
+            border[v] |= cl[nb[v, f]] == b
+        best = None
+        for e in rng.choice(inner[border], 24, replace=False):
+            p = np.unique(np.concatenate([[e], nbr[e][nbr[e] >= 0]]))
+            F = _lts_support(nbr, cl, p, cmax)
+            ring = nbr[F].ravel()
+            if taken[F].any() or taken[ring[ring >= 0]].any():
+                continue
+            work = int(sum(np.count_nonzero(cl[F] == c) << (cmax - c) for c in range(ncl)))
+            if best is None or work < best[0]:
+                best = (work, p, F)
+        assert best is not None
+        patches.append(best[1])
+        supports.append(best[2])
+        taken[best[2]] = True
+    F = np.unique(np.concatenate(supports))
+    P = np.concatenate(patches)
+    sub, smat, keep, pos = submesh(m, mat, F)
+    o = Oracle(sub.xyz, sub.tets, sub.face_tag, sub.face_partner, *smat, 5, cfl=0.35, max_clusters=ncl)
+    o.cluster = cl[keep].astype(np.int64)
+    o.dtmin = dtmin
+    assert set(np.unique(cl[F])) == set(range(ncl))
+    Qp = rng.standard_normal((P.size, s.B, 9)) * 1e-3
+    fluid = mat[2][P] == 0.0
+    mean = Qp[fluid, :, 0:3].mean(axis=2)
+    Qp[fluid, :, 0] = Qp[fluid, :, 1] = Qp[fluid, :, 2] = mean    # fluid stress -p I
+    Qp[fluid, :, 3:6] = 0.0
+    Qp = Qp.astype(np.float32).astype(np.float64)
+    o.Q[pos[P]] = Qp
+    Qbig = np.zeros((m.nt, 9, s.B), np.float32)
+    Qbig[P] = np.swapaxes(Qp, 1, 2)
+    s.set_dofs_f32(Qbig)
+    s.advance(1)
+    s.get_dofs_f32(out=Qbig)
+    inside = np.zeros(m.nt, bool)
+    inside[F] = True
+    step = 1 << 19
+    for lo in range(0, m.nt, step):
+        rows = np.any(Qbig[lo:lo + step].reshape(-1, 9 * s.B) != 0.0, axis=1)
+        stray = np.nonzero(rows & ~inside[lo:lo + step])[0]
+        assert stray.size == 0, ("data outside the support", lo + stray[:8])
+    got = to_oracle_layout(Qbig[F].astype(np.float64))
+    del Qbig
+    o.advance_macro()
+    want = o.Q[pos[F]]
+    assert rel_l2(got, want) <= 2e-5, rel_l2(got, want)
+    start = 0
+    for p, Fi in zip(patches, supports):
+        sel = np.searchsorted(F, Fi)
+        assert rel_l2(got[sel], want[sel]) <= 2e-5, (rel_l2(got[sel], want[sel]), np.bincount(cl[Fi], minlength=ncl))
+        # the patch moved (a zero update would pass trivially)
+        assert rel_l2(Qp[start:start + p.size], want[np.searchsorted(F, p)]) > 1e-3
+        start += p.size
+    # the data travelled: every cluster holds non-zero dofs after the step
+    for c in range(ncl):
+        assert np.abs(want[cl[F] == c]).max() > 0.0, c
