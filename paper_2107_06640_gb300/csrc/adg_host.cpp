@@ -441,7 +441,7 @@ void Ctx::setup() {
   N = cfg.degree;
   S = cfg.ensemble;
   fp64 = cfg.precision == ADG_FP64;
-  tc = cfg.precision == ADG_3XTF32 && cfg.degree == 5;
+  tc = cfg.precision == ADG_3XTF32 && (cfg.degree == 5 || cfg.degree == 4);
   ops = make_ref_ops(N);
   if (ops.max_orth_err > 1e-12) throw Err(ADG_E_INVALID, "reference basis not orthonormal");
   B = ops.B; Bf = ops.Bf; B1 = ops.B1;
@@ -699,11 +699,11 @@ void Ctx::setup() {
   dPerm = upload_raw<int>(ops.perm, owned, dev_bytes);
   CK(cudaDeviceGetAttribute(&n_sms, cudaDevAttrMultiProcessorCount, cfg.device));
   if (tc) {
-    std::vector<float> tl(local_tc_floats());
-    pack_local_tc(ops.kt.data(), ops.kvol.data(), ops.efc.data(), tl.data());
+    std::vector<float> tl(local_tc_floats(N));
+    pack_local_tc(N, ops.kt.data(), ops.kvol.data(), ops.efc.data(), tl.data());
     dTcLocal = upload_raw<float>(tl, owned, dev_bytes);
-    std::vector<float> tf(lift_tc_floats());
-    pack_lift_tc(ops.lift.data(), tf.data());
+    std::vector<float> tf(lift_tc_floats(N));
+    pack_lift_tc(N, ops.lift.data(), tf.data());
     dTcLift = upload_raw<float>(tf, owned, dev_bytes);
     dFrec = upload_raw<float>(frec, owned, dev_bytes);
   }
@@ -730,8 +730,8 @@ void Ctx::setup() {
   StepArgs a0 = base_args();
   const Segs none = make_segs(nullptr, 0, 1);
   int rc = launch_local(fp64, N, a0, none, stream);
-  if (!rc && tc) rc = launch_local_tc(a0, none, n_sms, stream, false);
-  if (!rc && tc) rc = launch_neighbour_tc(a0, none, n_sms, stream, false);
+  if (!rc && tc) rc = launch_local_tc(N, a0, none, n_sms, stream, false);
+  if (!rc && tc) rc = launch_neighbour_tc(N, a0, none, n_sms, stream, false);
   if (rc) throw Err(ADG_E_CUDA, std::string("kernel configuration: ") + cudaGetErrorString((cudaError_t)rc));
   tick = 0;
   time = 0.0;
@@ -828,9 +828,10 @@ void Ctx::launch_tick(int s, double dtm) {
       }
     };
     launch(tcs, kTileElems, [&](const Segs& g) {
-      return phase == 0 ? launch_local_tc(a, g, n_sms, stream, coarse) : launch_neighbour_tc(a, g, n_sms, stream, coarse);
+      return phase == 0 ? launch_local_tc(N, a, g, n_sms, stream, coarse)
+                        : launch_neighbour_tc(N, a, g, n_sms, stream, coarse);
     });
-    launch(fls, kTileElemsFluid, [&](const Segs& g) { return launch_local_tc(a, g, n_sms, stream, false, true); });
+    launch(fls, kTileElemsFluid, [&](const Segs& g) { return launch_local_tc(N, a, g, n_sms, stream, false, true); });
     if (prof && (!tcs.empty() || !fls.empty())) {  // the tensor-core launches alone
       CK(cudaEventCreate(&ev.m));
       CK(cudaEventRecord(ev.m, stream));

@@ -62,8 +62,8 @@ struct StepArgs {
   const int* fslot;     // [E][4] 2*fault + side for fault faces, else -1
   const void* drout;    // T [nff*S][2][9][Bf] time-integrated fault flux per side
   void* gflux;          // T [ngslot*S][9][Bf] time-integrated flux of gravitational faces
-  const float* tc_local; // tensor-core operands of the local kernel (hi/lo, canonical layout), degree 5
-  const float* tc_lift;  // tensor-core lift operand of the neighbour kernel (hi/lo, canonical layout), degree 5
+  const float* tc_local; // tensor-core operands of the local kernel (hi/lo, canonical layout), degree 5 or 4
+  const float* tc_lift;  // tensor-core lift operand of the neighbour kernel (hi/lo, canonical layout), degree 5 or 4
   const float* frec;     // [E][4][FREC] face records of the tensor-core neighbour kernel (FP32 dofs)
 };
 
@@ -120,20 +120,23 @@ __host__ __device__ inline int seg_of(const Segs& g, int64_t u) {
 // Segs of the given segments with `unit` virtual elements per work unit
 Segs make_segs(const Seg* s, int n, int unit, int chunk = 1);
 
-// tensor-core (tcgen05, 3xTF32) local kernel, degree 5, FP32 dofs (local_tc.cu),
-// for elements without gravitational faces, fault faces or finer LTS neighbours
+// tensor-core (tcgen05, 3xTF32) local kernel, degree 5 or 4, FP32 dofs
+// (local_tc.cuh; one translation unit per degree), for elements without
+// gravitational faces, fault faces or finer LTS neighbours
 // buffers: the launch's elements include some with an LTS buffer (a coarser neighbour)
 // acoustic: the launch's elements are fluid (mu = 0) without LTS buffer, on the
 // 4-quantity (p, v) instantiation; their stress must be isotropic (-p I)
-int launch_local_tc(const StepArgs& a, const Segs& g, int n_sms, void* stream, bool buffers, bool acoustic = false);
-void pack_local_tc(const double* kt, const double* kvol, const double* efc, float* out);
-int local_tc_floats();
-// tensor-core (tcgen05, 3xTF32) neighbour kernel, degree 5, FP32 dofs
-// (neighbour_tc.cu), for the same elements
+// (other degrees: cudaErrorInvalidValue)
+int launch_local_tc(int degree, const StepArgs& a, const Segs& g, int n_sms, void* stream, bool buffers,
+                    bool acoustic = false);
+void pack_local_tc(int degree, const double* kt, const double* kvol, const double* efc, float* out);
+int local_tc_floats(int degree);
+// tensor-core (tcgen05, 3xTF32) neighbour kernel, degree 5 or 4, FP32 dofs
+// (neighbour_tc.cuh), for the same elements
 // coarse: the launch's elements include some with a coarser LTS neighbour
-int launch_neighbour_tc(const StepArgs& a, const Segs& g, int n_sms, void* stream, bool coarse);
-void pack_lift_tc(const double* lift, float* out);
-int lift_tc_floats();
+int launch_neighbour_tc(int degree, const StepArgs& a, const Segs& g, int n_sms, void* stream, bool coarse);
+void pack_lift_tc(int degree, const double* lift, float* out);
+int lift_tc_floats(int degree);
 
 // ---- dynamic rupture (rupture.cu) ----
 // per-node fault parameters (double, stride FPAR), in this order:

@@ -1,5 +1,5 @@
-// Local element kernel on the tensor cores (tcgen05, 3xTF32), degree 5,
-// FP32 dofs: Cauchy-Kovalewski predictor, time integral, face traces and
+// Local element kernel on the tensor cores (tcgen05, 3xTF32), degrees 5 and
+// 4, FP32 dofs: Cauchy-Kovalewski predictor, time integral, face traces and
 // volume term of Sec. 4.1 for elements without gravitational faces, fault
 // faces or finer LTS neighbours (those take the CUDA-core kernel); an element
 // with a coarser LTS neighbour also adds its traces to its FP64 LTS buffer.
@@ -13,11 +13,11 @@
 // the threads that own the rows) and the reference matrices as B operands,
 // resident in shared memory in the canonical K-major layout (hi and lo);
 // A_hi B_hi + A_hi B_lo + A_lo B_hi accumulate in fp32 in TMEM.  Per tile:
-//   levels k = 0, 1, 2:  Y = D^k [KT_0; KT_1; KT_2]^T on the tensor cores,
+//   levels k < N - 2:  Y = D^k [KT_0; KT_1; KT_2]^T on the tensor cores,
 //     then X_d = sum_a (dxi_a/dx_d) Y_a and D^{k+1} = -sum_d A_d X_d on the CUDA
 //     cores (Jacobian form of the star product; the quantities of an element
 //     are exchanged with warp shuffles);
-//   levels 3, 4 (4 and 1 rows) on the CUDA cores from registers;
+//   the last two levels (4 and 1 rows) on the CUDA cores from registers;
 //   I = sum_k dt^{k+1}/(k+1)! D^k in registers (Eq. taylor);
 //   traces V_f = E_f I on the tensor cores, staged per face in shared memory
 //     and written to the trace array with bulk copies (cp.async.bulk);
@@ -37,6 +37,15 @@
 // the same Jacobian form; the element's face blocks are written in the full
 // 9-quantity layout (three equal normal-stress rows, zero shear), so
 // neighbours and the neighbour kernel see ordinary traces.
+//
+// Degree 4 (35 basis functions): a dofs row is 140 bytes, not a multiple of 16,
+// so the tile's rows are staged in shared memory with coalesced loads at the
+// start of the tile (its rows are consecutive in memory) and written back the
+// same way after the volume update.
+//
+// This header holds the kernel for both degrees; local_tc.cu and local_tc4.cu
+// instantiate it (one degree per translation unit, compiled in parallel).
+#pragma once
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -49,8 +58,6 @@ namespace adg {
 
 namespace {
 
-constexpr int B = 56, B1 = 35, BF = 21;
-constexpr int FS = face_stride(5);  // 192 floats per face block of the trace array
 constexpr int kThreadsL = 512;  // two tiles in flight, two warpgroups (halves) per tile
 
 // The medium of an instantiation: quantities per element (rows of the tile),
@@ -67,33 +74,65 @@ struct Acoustic {
 };
 static_assert(Elastic::TE == 4 * Elastic::EW && Acoustic::TE == 4 * Acoustic::EW, "tile of 4 warps");
 constexpr int kWaitIters = 1 << 24;
-// trace staging: one face of a warp pair's three elements, element blocks of
-// kTS floats (16-byte aligned, the face block's 189 values then zeros); two
-// buffers alternate over the faces
-constexpr int kTS = 196;
-constexpr int kTB = 3 * kTS;
 
-// tensor-core predictor levels: K (rows of D^k, padded to 8), rows of D^{k+1}
-// per axis (padded to 8), N = 3 axes (padded to 16)
-constexpr int kK0 = 56, kM0 = 35, kM0p = 40, kN0 = 128;
-constexpr int kK1 = 40, kM1 = 20, kM1p = 24, kN1 = 80;
-constexpr int kK2 = 24, kM2 = 10, kM2p = 16, kN2 = 48;
-constexpr int kNT = 96;  // traces: 4 faces x 21 nodes, padded
-constexpr int kNV = 176;  // volume: 3 axes x 56 basis functions, padded; K = 40 (35 used)
+constexpr int r8(int x) { return (x + 7) / 8 * 8; }
+constexpr int r16(int x) { return (x + 15) / 16 * 16; }
 
-// shared-memory image of the operands (floats), hi block then lo block each
-struct LImg {
-  static constexpr int oP0 = 0, sP0 = kN0 * kK0;
-  static constexpr int oP1 = oP0 + 2 * sP0, sP1 = kN1 * kK1;
-  static constexpr int oP2 = oP1 + 2 * sP1, sP2 = kN2 * kK2;
-  static constexpr int oV = oP2 + 2 * sP2, sV = kNV * 40;
-  static constexpr int oT = oV + 2 * sV, sT = kNT * kK0;
-  static constexpr int oK3 = oT + 2 * sT;                  // kt[a][m][l], m < 4, l < 10
-  static constexpr int oK4 = oK3 + 120;                    // kt[a][0][l], l < 4
-  static constexpr int floats = ((oK4 + 12 + 3) / 4) * 4;
-  static constexpr int bytes = floats * 4;
+// Shapes of degree N.  Predictor level l on the tensor cores multiplies D^l
+// (KU[l] rows used, K[l] padded to 8) by the three stacked KT_a, keeping the
+// M[l] rows of D^{l+1} per axis (padded to MP[l]; N = NN[l] = 3 MP[l] padded
+// to 16); the last tensor-core level leaves the 10 rows of D^{N-2}, and the
+// CUDA cores take D^{N-1} (4 rows) and D^N (1 row).  TS: floats per element in
+// the trace staging buffer (the face block, then zeros; 16-byte multiple).
+template <int N>
+struct LDeg;
+template <>
+struct LDeg<5> {
+  static constexpr int B = 56, B1 = 35, BF = 21, NL = 3, TS = 196;
+  static constexpr int K[3] = {56, 40, 24}, KU[3] = {56, 35, 20}, M[3] = {35, 20, 10}, MP[3] = {40, 24, 16},
+                       NN[3] = {128, 80, 48};
 };
-static_assert(LImg::bytes + 2 * (2 * 128 + 4 * 2 * kTB) * 4 + 64 <= 232448,
+template <>
+struct LDeg<4> {
+  static constexpr int B = 35, B1 = 20, BF = 15, NL = 2, TS = 140;
+  static constexpr int K[3] = {40, 24, 0}, KU[3] = {35, 20, 0}, M[3] = {20, 10, 0}, MP[3] = {24, 16, 0},
+                       NN[3] = {80, 48, 0};
+};
+
+// derived shapes and the shared-memory image of the operands (floats), hi
+// block then lo block each
+template <int N>
+struct LImg : LDeg<N> {
+  using D = LDeg<N>;
+  static constexpr int B = D::B, B1 = D::B1, BF = D::BF, NL = D::NL;
+  static constexpr int BP = r8(B);            // a row padded to whole 8-column chunks
+  static constexpr int NCH = BP / 8;          // 8-column chunks of a row
+  static constexpr int FS = face_stride(N);   // floats per face block of the trace array
+  static constexpr int NT = r16(4 * BF);      // traces: 4 faces x BF nodes, padded; K = BP
+  static constexpr int NTCH = (4 * BF + 7) / 8;  // 8-column chunks holding traces
+  static constexpr int KV = r8(B1);           // volume: K = the B1 rows of I that K_a reads
+  static constexpr int NV = r16(3 * BP);      // volume: axis a, basis m at column BP a + m
+  static constexpr bool kAligned = B % 4 == 0;  // dofs rows 16-byte aligned (float4 access)
+  static constexpr int oP0 = 0, sP0 = D::NN[0] * D::K[0];
+  static constexpr int oP1 = oP0 + 2 * sP0, sP1 = D::NN[1] * D::K[1];
+  static constexpr int oP2 = oP1 + 2 * sP1, sP2 = D::NN[2] * D::K[2];
+  static constexpr int oV = oP2 + 2 * sP2, sV = NV * KV;
+  static constexpr int oT = oV + 2 * sV, sT = NT * BP;
+  static constexpr int oK3 = oT + 2 * sT;     // kt[a][m][l], m < 4, l < 10
+  static constexpr int oK4 = oK3 + 120;       // kt[a][0][l], l < 4
+  static constexpr int floats = ((oK4 + 12 + 3) / 4) * 4;
+  // degree 4: per slot, the tile's dofs rows [row][B] (32 x 4 acoustic rows at most)
+  static constexpr int oQ = floats, sQ = kAligned ? 0 : 128 * B;
+  static constexpr int bytes = (floats + 2 * sQ) * 4;
+  // A hi at [0, 64), lo at [64, 128), accumulators from 128; volume: A at [0, 2 KV), accumulators after
+  static_assert(BP <= 64 && D::NN[0] <= 128 && NT <= 128 && 2 * KV + NV <= 256, "TMEM columns of a slot");
+};
+
+// trace staging: per warp pair one face of its elements, two buffers
+// alternating over the faces (sized for degree 5, the larger)
+constexpr int kTB = 3 * LDeg<5>::TS;
+static_assert(LImg<5>::bytes + 2 * (2 * 128 + 4 * 2 * kTB) * 4 + 64 <= 232448 &&
+                  LImg<4>::bytes + 2 * (2 * 128 + 4 * 2 * kTB) * 4 + 64 <= 232448,
               "operands exceed the shared memory of one CTA");
 
 // the kernel's shared memory besides the operand image (dynamic): per slot the
@@ -193,9 +232,9 @@ __device__ __forceinline__ float star_apply(const Star& s, float y0, float y1, f
 // mc % 2 == H: Y (3 axes x MP columns at tacc) -> D^{k+1} (M rows),
 // I += ck * D^{k+1}; D^{k+1} goes to the A columns of the next level (TO_A)
 // or to registers dn.
-template <int H, int M, int MP, bool TO_A>
+template <int H, int M, int MP, bool TO_A, int BP>
 __device__ __forceinline__ void level_epilogue(uint32_t tacc, uint32_t tah, uint32_t tal, const Star& s, float ck,
-                                               float (&I)[B], float* dn) {
+                                               float (&I)[BP], float* dn) {
 #pragma unroll
   for (int mc = H; mc < MP / 8; mc += 2) {
     float y[24];
@@ -256,14 +295,54 @@ __device__ __forceinline__ bool pair_round(Lane& L, unsigned int* err, F&& issue
   return ok;
 }
 
+// Degree 4: the tile's dofs rows in shared memory.  The 256 threads of the
+// slot (u) copy the rows of the tile's elements [v0, v0 + nE) with coalesced
+// loads (a tile's rows are consecutive in memory; an acoustic tile takes rows
+// 0 and 6..8 of each element); tile row (element ei, quantity qi) sits at
+// (ei * M::Q + qi) * B.
+template <class M, int B>
+__device__ __forceinline__ void rows_load(float* sQ, const float* Q, int64_t v0, int nE, int u) {
+  const int n = nE * M::Q * B;
+  for (int i = u; i < n; i += 256) {
+    int64_t src;
+    if constexpr (M::fluid) {
+      const int ej = i / (4 * B), r = i - ej * 4 * B;
+      src = (v0 + ej) * 9 * B + (r < B ? r : 5 * B + r);
+    } else {
+      src = v0 * 9 * B + i;
+    }
+    sQ[i] = Q[src];
+  }
+}
+// ... and back (acoustic: the normal-stress row as sigma_xx, sigma_yy and
+// sigma_zz, then the velocity rows; the shear rows stay zero)
+template <class M, int B>
+__device__ __forceinline__ void rows_store(const float* sQ, float* Q, int64_t v0, int nE, int u) {
+  if constexpr (M::fluid) {
+    const int n = nE * 6 * B;
+    for (int i = u; i < n; i += 256) {
+      const int ej = i / (6 * B), r = i - ej * 6 * B;
+      const int qi = r < 3 * B ? 0 : 1 + (r - 3 * B) / B;
+      const int k = r < 3 * B ? r % B : (r - 3 * B) % B;
+      Q[(v0 + ej) * 9 * B + (r < 3 * B ? r : 3 * B + r)] = sQ[(ej * 4 + qi) * B + k];
+    }
+  } else {
+    const int n = nE * 9 * B;
+    for (int i = u; i < n; i += 256) Q[v0 * 9 * B + i] = sQ[i];
+  }
+}
+
 // One tile, the share of half H (8-column chunks c with c % 2 == H); false
 // after a timed-out wait.
 // kBuf: some elements of the launch have an LTS buffer (a coarser neighbour)
 // tile: index within its segment; t2: this slot's tile after the next among
 // all tiles of the launch (kMulti: the launch has several segments)
-template <class M, int H, bool kBuf, bool kMulti>
+template <int N, class M, int H, bool kBuf, bool kMulti>
 __device__ __forceinline__ bool local_tile(Lane& L, const StepArgs& a, const Segs& g, int64_t t2, int64_t v_begin,
                                            int64_t n_virtual, int64_t tile) {
+  using D = LDeg<N>;
+  using I_ = LImg<N>;
+  constexpr int B = I_::B, BF = I_::BF, BP = I_::BP, NCH = I_::NCH, FS = I_::FS, TS = D::TS, NL = D::NL;
   constexpr int TE = M::TE;
   float* const Q = reinterpret_cast<float*>(a.Q);
   const int64_t v0 = v_begin + tile * TE;
@@ -286,69 +365,90 @@ __device__ __forceinline__ bool local_tile(Lane& L, const StepArgs& a, const Seg
     if (t2 < g.first[g.n]) {
       const int i2 = seg_of<kMulti>(g, t2);
       const int64_t l2 = t2 - g.first[i2], rem2 = g.s[i2].n - l2 * TE;
-      tc::prefetch_l2(Q + (g.s[i2].v_begin + l2 * TE) * 9 * B, (uint32_t)((rem2 < TE ? rem2 : TE) * 9 * B * 4));
+      tc::prefetch_l2_inner(Q + (g.s[i2].v_begin + l2 * TE) * 9 * B, (uint32_t)((rem2 < TE ? rem2 : TE) * 9 * B * 4));
     }
   }
   // ---- D^0 = Q row: I = dt Q, A = Q
   float* Qrow = Q + (v * 9 + M::row(p)) * B;
-  float I[B];
+  float* sQ = nullptr;   // degree 4: the slot's staged rows
+  float* srow = nullptr; // ... and this thread's
+  if constexpr (!I_::kAligned) {
+    sQ = reinterpret_cast<float*>(smem_raw) + I_::oQ + L.slot * I_::sQ;
+    srow = sQ + (i * M::Q + p) * B;
+    pair_bar(L.slot);  // the previous tile's rows have been written back
+    rows_load<M, B>(sQ, Q, v0, nE, L.t + 128 * H);
+    pair_bar(L.slot);
+  }
+  float I[BP];
 #pragma unroll
-  for (int c = H; c < B / 8; c += 2) {
+  for (int c = H; c < NCH; c += 2) {
     float x[8];
-    float4 x0 = make_float4(0.f, 0.f, 0.f, 0.f), x1 = x0;
-    if (valid) {
-      x0 = *reinterpret_cast<const float4*>(Qrow + 8 * c);
-      x1 = *reinterpret_cast<const float4*>(Qrow + 8 * c + 4);
+    if constexpr (I_::kAligned) {
+      float4 x0 = make_float4(0.f, 0.f, 0.f, 0.f), x1 = x0;
+      if (valid) {
+        x0 = *reinterpret_cast<const float4*>(Qrow + 8 * c);
+        x1 = *reinterpret_cast<const float4*>(Qrow + 8 * c + 4);
+      }
+      x[0] = x0.x; x[1] = x0.y; x[2] = x0.z; x[3] = x0.w;
+      x[4] = x1.x; x[5] = x1.y; x[6] = x1.z; x[7] = x1.w;
+    } else {
+#pragma unroll
+      for (int j = 0; j < 8; ++j) x[j] = (valid && 8 * c + j < B) ? srow[8 * c + j] : 0.f;
     }
-    x[0] = x0.x; x[1] = x0.y; x[2] = x0.z; x[3] = x0.w;
-    x[4] = x1.x; x[5] = x1.y; x[6] = x1.z; x[7] = x1.w;
 #pragma unroll
     for (int j = 0; j < 8; ++j) I[8 * c + j] = L.tcf[0] * x[j];
     tc::st_split8(trow + cAh + 8 * c, trow + cAl + 8 * c, x);
   }
-  // ---- levels 0, 1, 2 on the tensor cores
+  // ---- predictor levels on the tensor cores: all but the last feed the next
+  // level's A operand, the last leaves the 10 rows of D^NL in registers
+  if constexpr (NL == 3) {
+    if (!pair_round<H>(L, a.err, [&] {
+          tc::mma3_ts<D::NN[0], D::K[0]>(tbase + cAcc, tbase + cAh, tbase + cAl, sbase + 4 * I_::oP0,
+                                         sbase + 4 * (I_::oP0 + I_::sP0), false);
+        }))
+      return false;
+    level_epilogue<H, D::M[0], D::MP[0], true>(trow + cAcc, trow + cAh, trow + cAl, st, L.tcf[1], I, nullptr);
+  }
+  constexpr int l1 = NL - 2, l2 = NL - 1;
+  constexpr int o1 = l1 == 0 ? I_::oP0 : I_::oP1, s1 = l1 == 0 ? I_::sP0 : I_::sP1;
+  constexpr int o2 = l2 == 1 ? I_::oP1 : I_::oP2, s2 = l2 == 1 ? I_::sP1 : I_::sP2;
   if (!pair_round<H>(L, a.err, [&] {
-        tc::mma3_ts<kN0, kK0>(tbase + cAcc, tbase + cAh, tbase + cAl, sbase + 4 * LImg::oP0,
-                              sbase + 4 * (LImg::oP0 + LImg::sP0), false);
+        tc::mma3_ts<D::NN[l1], D::K[l1]>(tbase + cAcc, tbase + cAh, tbase + cAl, sbase + 4 * o1,
+                                         sbase + 4 * (o1 + s1), false);
       }))
     return false;
-  level_epilogue<H, kM0, kM0p, true>(trow + cAcc, trow + cAh, trow + cAl, st, L.tcf[1], I, nullptr);
+  level_epilogue<H, D::M[l1], D::MP[l1], true>(trow + cAcc, trow + cAh, trow + cAl, st, L.tcf[l1 + 1], I, nullptr);
   if (!pair_round<H>(L, a.err, [&] {
-        tc::mma3_ts<kN1, kK1>(tbase + cAcc, tbase + cAh, tbase + cAl, sbase + 4 * LImg::oP1,
-                              sbase + 4 * (LImg::oP1 + LImg::sP1), false);
+        tc::mma3_ts<D::NN[l2], D::K[l2]>(tbase + cAcc, tbase + cAh, tbase + cAl, sbase + 4 * o2,
+                                         sbase + 4 * (o2 + s2), false);
       }))
     return false;
-  level_epilogue<H, kM1, kM1p, true>(trow + cAcc, trow + cAh, trow + cAl, st, L.tcf[2], I, nullptr);
-  if (!pair_round<H>(L, a.err, [&] {
-        tc::mma3_ts<kN2, kK2>(tbase + cAcc, tbase + cAh, tbase + cAl, sbase + 4 * LImg::oP2,
-                              sbase + 4 * (LImg::oP2 + LImg::sP2), false);
-      }))
-    return false;
-  float d3[kM2p];
-  level_epilogue<H, kM2, kM2p, false>(trow + cAcc, trow + cAh, trow + cAl, st, L.tcf[3], I, d3);
-  // ---- levels 3 and 4 (half 0, with rows 8 and 9 of D^3 from half 1)
+  static_assert(D::M[l2] == 10 && D::MP[l2] == 16, "the last tensor-core level leaves 10 rows");
+  float dl[16];
+  level_epilogue<H, D::M[l2], D::MP[l2], false>(trow + cAcc, trow + cAh, trow + cAl, st, L.tcf[NL], I, dl);
+  // ---- the last two levels (half 0, with rows 8 and 9 of D^NL from half 1)
   if (H == 1) {
-    s_X[L.slot][2 * L.t] = d3[8];
-    s_X[L.slot][2 * L.t + 1] = d3[9];
+    s_X[L.slot][2 * L.t] = dl[8];
+    s_X[L.slot][2 * L.t + 1] = dl[9];
   }
   pair_bar(L.slot);
   if (H == 0) {
-    d3[8] = s_X[L.slot][2 * L.t];
-    d3[9] = s_X[L.slot][2 * L.t + 1];
-    const float* k3 = reinterpret_cast<const float*>(smem_raw) + LImg::oK3;
-    const float* k4 = reinterpret_cast<const float*>(smem_raw) + LImg::oK4;
+    dl[8] = s_X[L.slot][2 * L.t];
+    dl[9] = s_X[L.slot][2 * L.t + 1];
+    const float* k3 = reinterpret_cast<const float*>(smem_raw) + I_::oK3;
+    const float* k4 = reinterpret_cast<const float*>(smem_raw) + I_::oK4;
     float d4[4];
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
       float y0 = 0.f, y1 = 0.f, y2 = 0.f;
 #pragma unroll
-      for (int l = 0; l < kM2; ++l) {
-        y0 += k3[(0 * 4 + m) * 10 + l] * d3[l];
-        y1 += k3[(1 * 4 + m) * 10 + l] * d3[l];
-        y2 += k3[(2 * 4 + m) * 10 + l] * d3[l];
+      for (int l = 0; l < 10; ++l) {
+        y0 += k3[(0 * 4 + m) * 10 + l] * dl[l];
+        y1 += k3[(1 * 4 + m) * 10 + l] * dl[l];
+        y2 += k3[(2 * 4 + m) * 10 + l] * dl[l];
       }
       d4[m] = star_apply(st, y0, y1, y2);
-      I[m] += L.tcf[4] * d4[m];
+      I[m] += L.tcf[NL + 1] * d4[m];
     }
     float y0 = 0.f, y1 = 0.f, y2 = 0.f;
 #pragma unroll
@@ -357,15 +457,15 @@ __device__ __forceinline__ bool local_tile(Lane& L, const StepArgs& a, const Seg
       y1 += k4[1 * 4 + l] * d4[l];
       y2 += k4[2 * 4 + l] * d4[l];
     }
-    I[0] += L.tcf[5] * star_apply(st, y0, y1, y2);
+    I[0] += L.tcf[NL + 2] * star_apply(st, y0, y1, y2);
   }
 
-  // ---- face traces: T = I E^T (N = 4 x 21)
+  // ---- face traces: T = I E^T (N = 4 x BF)
 #pragma unroll
-  for (int c = H; c < B / 8; c += 2) tc::st_split8(trow + cAh + 8 * c, trow + cAl + 8 * c, I + 8 * c);
+  for (int c = H; c < NCH; c += 2) tc::st_split8(trow + cAh + 8 * c, trow + cAl + 8 * c, I + 8 * c);
   if (!pair_round<H>(L, a.err, [&] {
-        tc::mma3_ts<kNT, kK0>(tbase + cAcc, tbase + cAh, tbase + cAl, sbase + 4 * LImg::oT,
-                              sbase + 4 * (LImg::oT + LImg::sT), false);
+        tc::mma3_ts<I_::NT, BP>(tbase + cAcc, tbase + cAh, tbase + cAl, sbase + 4 * I_::oT,
+                                sbase + 4 * (I_::oT + I_::sT), false);
       }))
     return false;
   // traces leave face by face: the rows go to a shared buffer laid out like
@@ -373,12 +473,19 @@ __device__ __forceinline__ bool local_tile(Lane& L, const StepArgs& a, const Seg
   // copies each element's block with a bulk copy; two buffers alternate, the
   // copier waits until the copy before the last has read its buffer
   {
+    constexpr int NTH = H == 0 ? (I_::NTCH + 1) / 2 : I_::NTCH / 2;  // this half's trace chunks
     const int nmine = nE - M::EW * L.w < M::EW ? nE - M::EW * L.w : M::EW;  // elements of this warp (may be <= 0)
     const bool copier = H == 0 && L.lane == 0;
-    // this half's chunks c = H, H + 2, ... of the 88 trace columns, read once
+    // this half's chunks c = H, H + 2, ... of the trace columns, read once
     float tv[48];
-    tc::ld3x8(trow + cAcc + 8 * H, trow + cAcc + 8 * (H + 2), trow + cAcc + 8 * (H + 4), tv);
-    tc::ld3x8(trow + cAcc + 8 * (H + 6), trow + cAcc + 8 * (H + 8), trow + cAcc + 8 * (H == 0 ? 10 : 9), tv + 24);
+    if constexpr (N == 5) {
+      tc::ld3x8(trow + cAcc + 8 * H, trow + cAcc + 8 * (H + 2), trow + cAcc + 8 * (H + 4), tv);
+      tc::ld3x8(trow + cAcc + 8 * (H + 6), trow + cAcc + 8 * (H + 8), trow + cAcc + 8 * (H == 0 ? 10 : 9), tv + 24);
+    } else {
+      static_assert(N == 4 && I_::NTCH == 8, "trace chunks of degree 4");
+      tc::ld3x8(trow + cAcc + 8 * H, trow + cAcc + 8 * (H + 2), trow + cAcc + 8 * (H + 4), tv);
+      tc::ld8(trow + cAcc + 8 * (H + 6), tv + 24);
+    }
     // an element with a coarser neighbour also adds its four face traces to
     // its LTS buffer, in FP64 (overwrite at the first of the two steps)
     if (kBuf && !M::fluid && L.btrace_mode && a.bslot && valid) {
@@ -386,7 +493,7 @@ __device__ __forceinline__ bool local_tile(Lane& L, const StepArgs& a, const Seg
       if (bs >= 0) {
         double* bt = a.btrace + ((int64_t)bs * a.S + (v - e * a.S)) * 36 * BF;
 #pragma unroll
-        for (int cj = 0; cj < (H == 0 ? 6 : 5); ++cj) {
+        for (int cj = 0; cj < NTH; ++cj) {
 #pragma unroll
           for (int j = 0; j < 8; ++j) {
             const int col = 8 * (H + 2 * cj) + j;
@@ -401,14 +508,14 @@ __device__ __forceinline__ bool local_tile(Lane& L, const StepArgs& a, const Seg
     }
     if constexpr (M::fluid) {
       // acoustic: this face's (p, v) rows of the warp's eight elements in a
-      // compact buffer [element][4][21], then the warp pair writes each
+      // compact buffer [element][4][BF], then the warp pair writes each
       // element's full face block (sigma_xx three times, zero shear, v,
       // padding zeros) with 16-byte stores
       float* sC = s_T[L.slot][L.w];
 #pragma unroll
       for (int f = 0; f < 4; ++f) {
 #pragma unroll
-        for (int cj = 0; cj < (H == 0 ? 6 : 5); ++cj) {
+        for (int cj = 0; cj < NTH; ++cj) {
           const int c = H + 2 * cj;
           if (8 * c + 7 < BF * f || 8 * c >= BF * (f + 1)) continue;  // chunk outside face f
           if (valid) {
@@ -438,14 +545,14 @@ __device__ __forceinline__ bool local_tile(Lane& L, const StepArgs& a, const Seg
       for (int f = 0; f < 4; ++f) {
         float* sTf = s_T[L.slot][L.w] + (f & 1) * kTB;
 #pragma unroll
-        for (int cj = 0; cj < (H == 0 ? 6 : 5); ++cj) {
+        for (int cj = 0; cj < NTH; ++cj) {
           const int c = H + 2 * cj;
           if (8 * c + 7 < BF * f || 8 * c >= BF * (f + 1)) continue;  // chunk outside face f
           if (valid) {
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
               const int col = 8 * c + j;
-              if (col >= BF * f && col < BF * (f + 1)) sTf[jj * kTS + p * BF + col - BF * f] = tv[8 * cj + j];
+              if (col >= BF * f && col < BF * (f + 1)) sTf[jj * TS + p * BF + col - BF * f] = tv[8 * cj + j];
             }
           }
         }
@@ -455,54 +562,70 @@ __device__ __forceinline__ bool local_tile(Lane& L, const StepArgs& a, const Seg
         if (copier) {
           for (int ej = 0; ej < nmine; ++ej)
             tc::bulk_store(reinterpret_cast<float*>(a.trace) + ((v0 + M::EW * L.w + ej) * 4 + f) * FS,
-                           sTf + ej * kTS, FS * 4);
+                           sTf + ej * TS, FS * 4);
           tc::bulk_commit();
         }
       }
     }
   }
 
-  // ---- volume: W_a = K_a I (l < 35) for the three axes in one product,
+  // ---- volume: W_a = K_a I (l < B1) for the three axes in one product,
   // then Q += sum_a A*_a W_a = -sum_d c_d X_d[src_d] (Jacobian form)
+  constexpr int KV = I_::KV;
 #pragma unroll
-  for (int c = H; c < 5; c += 2) tc::st_split8(trow + 8 * c, trow + 40 + 8 * c, I + 8 * c);
-  // the dofs rows for the update are requested before the round
+  for (int c = H; c < KV / 8; c += 2) tc::st_split8(trow + 8 * c, trow + KV + 8 * c, I + 8 * c);
+  // the dofs rows for the update are requested before the round (degree 5;
+  // degree 4 updates its staged rows)
   float4 qv[8];
+  if constexpr (I_::kAligned) {
 #pragma unroll
-  for (int c = H; c < B / 8; c += 2) {
-    qv[c - H] = make_float4(0.f, 0.f, 0.f, 0.f);
-    qv[c - H + 1] = qv[c - H];
-    if (valid) {
-      qv[c - H] = reinterpret_cast<const float4*>(Qrow + 8 * c)[0];
-      qv[c - H + 1] = reinterpret_cast<const float4*>(Qrow + 8 * c)[1];
+    for (int c = H; c < NCH; c += 2) {
+      qv[c - H] = make_float4(0.f, 0.f, 0.f, 0.f);
+      qv[c - H + 1] = qv[c - H];
+      if (valid) {
+        qv[c - H] = reinterpret_cast<const float4*>(Qrow + 8 * c)[0];
+        qv[c - H + 1] = reinterpret_cast<const float4*>(Qrow + 8 * c)[1];
+      }
     }
   }
-  constexpr uint32_t cV = 80;  // volume accumulator: axis a, basis m at column 80 + 56 a + m
+  constexpr uint32_t cV = 2 * KV;  // volume accumulator: axis a, basis m at column cV + BP a + m
   if (!pair_round<H>(L, a.err, [&] {
-        tc::mma3_ts<kNV, 40>(tbase + cV, tbase + 0, tbase + 40, sbase + 4 * LImg::oV,
-                             sbase + 4 * (LImg::oV + LImg::sV), false);
+        tc::mma3_ts<I_::NV, KV>(tbase + cV, tbase + 0, tbase + KV, sbase + 4 * I_::oV,
+                                sbase + 4 * (I_::oV + I_::sV), false);
       }))
     return false;
   // ---- Q += volume term (face terms follow in the neighbour kernel)
 #pragma unroll
-  for (int c = H; c < B / 8; c += 2) {
+  for (int c = H; c < NCH; c += 2) {
     float y[24];
-    tc::ld3x8(trow + cV + 8 * c, trow + cV + B + 8 * c, trow + cV + 2 * B + 8 * c, y);
+    tc::ld3x8(trow + cV + 8 * c, trow + cV + BP + 8 * c, trow + cV + 2 * BP + 8 * c, y);
     float x[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) x[j] = -star_apply(st, y[j], y[8 + j], y[16 + j]);
-    if (valid) {
-      const float4 q0 = qv[c - H], q1 = qv[c - H + 1];
-      const float4 n0 = make_float4(q0.x + x[0], q0.y + x[1], q0.z + x[2], q0.w + x[3]);
-      const float4 n1 = make_float4(q1.x + x[4], q1.y + x[5], q1.z + x[6], q1.w + x[7]);
-      // (acoustic: the normal-stress row is written as sigma_xx, sigma_yy and sigma_zz)
+    if constexpr (I_::kAligned) {
+      if (valid) {
+        const float4 q0 = qv[c - H], q1 = qv[c - H + 1];
+        const float4 n0 = make_float4(q0.x + x[0], q0.y + x[1], q0.z + x[2], q0.w + x[3]);
+        const float4 n1 = make_float4(q1.x + x[4], q1.y + x[5], q1.z + x[6], q1.w + x[7]);
+        // (acoustic: the normal-stress row is written as sigma_xx, sigma_yy and sigma_zz)
 #pragma unroll
-      for (int r = 0; r < (M::fluid && p == 0 ? 3 : 1); ++r) {
-        float4* dst = reinterpret_cast<float4*>(Qrow + r * B + 8 * c);
-        dst[0] = n0;
-        dst[1] = n1;
+        for (int r = 0; r < (M::fluid && p == 0 ? 3 : 1); ++r) {
+          float4* dst = reinterpret_cast<float4*>(Qrow + r * B + 8 * c);
+          dst[0] = n0;
+          dst[1] = n1;
+        }
+      }
+    } else {
+      if (valid) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          if (8 * c + j < B) srow[8 * c + j] += x[j];
       }
     }
+  }
+  if constexpr (!I_::kAligned) {
+    pair_bar(L.slot);
+    rows_store<M, B>(sQ, Q, v0, nE, L.t + 128 * H);
   }
   // the next tile's first MMA overwrites these columns only after the
   // barrier at the start of its round
@@ -510,9 +633,9 @@ __device__ __forceinline__ bool local_tile(Lane& L, const StepArgs& a, const Seg
   return true;
 }
 
-// M: the medium (Elastic or Acoustic); kChunk: consecutive tiles a slot takes
-// per sweep (a compile-time launch shape)
-template <class M, bool kBuf, bool kMulti, int kChunk>
+// N: degree; M: the medium (Elastic or Acoustic); kChunk: consecutive tiles a
+// slot takes per sweep (a compile-time launch shape)
+template <int N, class M, bool kBuf, bool kMulti, int kChunk>
 __global__ void __launch_bounds__(kThreadsL, 1) local_tc_kernel(StepArgs a, const __grid_constant__ Segs g) {
   float* sm = reinterpret_cast<float*>(smem_raw);
   __shared__ uint32_t tmem_base;
@@ -523,7 +646,7 @@ __global__ void __launch_bounds__(kThreadsL, 1) local_tc_kernel(StepArgs a, cons
   {
     const float4* src = reinterpret_cast<const float4*>(a.tc_local);
     float4* dst = reinterpret_cast<float4*>(sm);
-    for (int r = tid; r < LImg::floats / 4; r += kThreadsL) dst[r] = src[r];
+    for (int r = tid; r < LImg<N>::floats / 4; r += kThreadsL) dst[r] = src[r];
   }
   for (int r = tid; r < 2 * 4 * 2 * kTB; r += kThreadsL) (&sT[0][0][0])[r] = 0.f;
   if (tid < 2) {
@@ -552,11 +675,11 @@ __global__ void __launch_bounds__(kThreadsL, 1) local_tc_kernel(StepArgs a, cons
   auto work = [&](int64_t tile, int64_t t2) {
     const Seg& sg = g.s[seg_of<kMulti>(g, tile)];
 #pragma unroll
-    for (int k = 0; k < 6; ++k) L.tcf[k] = (float)sg.tcoef[k];
+    for (int k = 0; k <= N; ++k) L.tcf[k] = (float)sg.tcoef[k];
     L.btrace_mode = sg.btrace_mode;
     const int64_t lt = tile - g.first[&sg - g.s];
-    return half == 0 ? local_tile<M, 0, kBuf, kMulti>(L, a, g, t2, sg.v_begin, sg.n, lt)
-                     : local_tile<M, 1, kBuf, kMulti>(L, a, g, t2, sg.v_begin, sg.n, lt);
+    return half == 0 ? local_tile<N, M, 0, kBuf, kMulti>(L, a, g, t2, sg.v_begin, sg.n, lt)
+                     : local_tile<N, M, 1, kBuf, kMulti>(L, a, g, t2, sg.v_begin, sg.n, lt);
   };
   if constexpr (kChunk == 1) {
     for (int64_t tile = me; tile < ntiles; tile += slots)
@@ -579,28 +702,31 @@ __global__ void __launch_bounds__(kThreadsL, 1) local_tc_kernel(StepArgs a, cons
 
 }  // namespace
 
-int launch_local_tc(const StepArgs& a, const Segs& g, int n_sms, void* stream, bool buffers, bool acoustic) {
+// The launcher of degree N (the kernel table of that degree's translation unit).
+template <int N>
+int launch_local_tc_deg(const StepArgs& a, const Segs& g, int n_sms, void* stream, bool buffers, bool acoustic) {
   using K = void (*)(StepArgs, Segs);
   // elastic [kBuf][kMulti][chunk 1, 2, 4]; acoustic [kMulti][chunk] (its elements have no LTS buffer)
   static const K kern[2][2][3] = {
-      {{local_tc_kernel<Elastic, false, false, 1>, local_tc_kernel<Elastic, false, false, 2>,
-        local_tc_kernel<Elastic, false, false, 4>},
-       {local_tc_kernel<Elastic, false, true, 1>, local_tc_kernel<Elastic, false, true, 2>,
-        local_tc_kernel<Elastic, false, true, 4>}},
-      {{local_tc_kernel<Elastic, true, false, 1>, local_tc_kernel<Elastic, true, false, 2>,
-        local_tc_kernel<Elastic, true, false, 4>},
-       {local_tc_kernel<Elastic, true, true, 1>, local_tc_kernel<Elastic, true, true, 2>,
-        local_tc_kernel<Elastic, true, true, 4>}}};
+      {{local_tc_kernel<N, Elastic, false, false, 1>, local_tc_kernel<N, Elastic, false, false, 2>,
+        local_tc_kernel<N, Elastic, false, false, 4>},
+       {local_tc_kernel<N, Elastic, false, true, 1>, local_tc_kernel<N, Elastic, false, true, 2>,
+        local_tc_kernel<N, Elastic, false, true, 4>}},
+      {{local_tc_kernel<N, Elastic, true, false, 1>, local_tc_kernel<N, Elastic, true, false, 2>,
+        local_tc_kernel<N, Elastic, true, false, 4>},
+       {local_tc_kernel<N, Elastic, true, true, 1>, local_tc_kernel<N, Elastic, true, true, 2>,
+        local_tc_kernel<N, Elastic, true, true, 4>}}};
   static const K kfl[2][3] = {
-      {local_tc_kernel<Acoustic, false, false, 1>, local_tc_kernel<Acoustic, false, false, 2>,
-       local_tc_kernel<Acoustic, false, false, 4>},
-      {local_tc_kernel<Acoustic, false, true, 1>, local_tc_kernel<Acoustic, false, true, 2>,
-       local_tc_kernel<Acoustic, false, true, 4>}};
+      {local_tc_kernel<N, Acoustic, false, false, 1>, local_tc_kernel<N, Acoustic, false, false, 2>,
+       local_tc_kernel<N, Acoustic, false, false, 4>},
+      {local_tc_kernel<N, Acoustic, false, true, 1>, local_tc_kernel<N, Acoustic, false, true, 2>,
+       local_tc_kernel<N, Acoustic, false, true, 4>}};
   const int rc = configure_on_device((const void*)kern[0][0][0], [] {
     cudaError_t ce = cudaSuccess;
     for (int i = 0; i < 18; ++i) {
       const K k = i < 12 ? kern[i / 6][(i / 3) % 2][i % 3] : kfl[(i - 12) / 3][(i - 12) % 3];
-      if (ce == cudaSuccess) ce = cudaFuncSetAttribute((const void*)k, cudaFuncAttributeMaxDynamicSharedMemorySize, LImg::bytes);
+      if (ce == cudaSuccess)
+        ce = cudaFuncSetAttribute((const void*)k, cudaFuncAttributeMaxDynamicSharedMemorySize, LImg<N>::bytes);
     }
     return ce;
   });
@@ -612,15 +738,19 @@ int launch_local_tc(const StepArgs& a, const Segs& g, int n_sms, void* stream, b
   const int64_t want = (ntiles + 1) / 2;
   const unsigned grid = (unsigned)(want < n_sms ? want : n_sms);
   const K k = acoustic ? kfl[g.n > 1 ? 1 : 0][ci] : kern[buffers ? 1 : 0][g.n > 1 ? 1 : 0][ci];
-  k<<<grid, kThreadsL, LImg::bytes, (cudaStream_t)stream>>>(a, g);
+  k<<<grid, kThreadsL, LImg<N>::bytes, (cudaStream_t)stream>>>(a, g);
   return (int)cudaGetLastError();
 }
 
-// Host-side image of the operands: kt[a][m][l], kvol[a][m][l] (l < 35) and
-// efc[f][n][l] of the degree-5 basis, split into tf32 hi / lo and laid out as
-// the canonical K-major B operands of local_tc_kernel.
-void pack_local_tc(const double* kt, const double* kvol, const double* efc, float* out) {
-  for (int i = 0; i < LImg::floats; ++i) out[i] = 0.f;
+// Host-side image of the operands of degree N: kt[a][m][l], kvol[a][m][l]
+// (l < B1) and efc[f][n][l] of that degree's basis, split into tf32 hi / lo
+// and laid out as the canonical K-major B operands of local_tc_kernel.
+template <int N>
+void pack_local_tc_deg(const double* kt, const double* kvol, const double* efc, float* out) {
+  using D = LDeg<N>;
+  using I_ = LImg<N>;
+  constexpr int B = I_::B, B1 = I_::B1, BF = I_::BF, BP = I_::BP;
+  for (int i = 0; i < I_::floats; ++i) out[i] = 0.f;
   auto put = [&](int off, int size, int R, int n, int k, double x) {
     const float xf = (float)x;
     const float hi = tc::tf32_trunc(xf);
@@ -628,28 +758,24 @@ void pack_local_tc(const double* kt, const double* kvol, const double* efc, floa
     out[off + o] = hi;
     out[off + size + o] = xf - hi;
   };
-  const int Mk[3] = {kM0, kM1, kM2}, Mp[3] = {kM0p, kM1p, kM2p}, Kk[3] = {B, B1, 20};
-  const int offk[3] = {LImg::oP0, LImg::oP1, LImg::oP2}, sizek[3] = {LImg::sP0, LImg::sP1, LImg::sP2};
-  const int Nk[3] = {kN0, kN1, kN2};
-  for (int lev = 0; lev < 3; ++lev)
+  const int offk[3] = {I_::oP0, I_::oP1, I_::oP2}, sizek[3] = {I_::sP0, I_::sP1, I_::sP2};
+  for (int lev = 0; lev < D::NL; ++lev)
     for (int ax = 0; ax < 3; ++ax)
-      for (int m = 0; m < Mk[lev]; ++m)
-        for (int l = 0; l < Kk[lev]; ++l)
-          put(offk[lev], sizek[lev], Nk[lev], ax * Mp[lev] + m, l, kt[((size_t)ax * B + m) * B + l]);
+      for (int m = 0; m < D::M[lev]; ++m)
+        for (int l = 0; l < D::KU[lev]; ++l)
+          put(offk[lev], sizek[lev], D::NN[lev], ax * D::MP[lev] + m, l, kt[((size_t)ax * B + m) * B + l]);
   for (int ax = 0; ax < 3; ++ax)
     for (int m = 0; m < B; ++m)
       for (int l = 0; l < B1; ++l)
-        put(LImg::oV, LImg::sV, kNV, ax * B + m, l, kvol[((size_t)ax * B + m) * B1 + l]);
+        put(I_::oV, I_::sV, I_::NV, ax * BP + m, l, kvol[((size_t)ax * B + m) * B1 + l]);
   for (int f = 0; f < 4; ++f)
     for (int n = 0; n < BF; ++n)
-      for (int l = 0; l < B; ++l) put(LImg::oT, LImg::sT, kNT, f * BF + n, l, efc[((size_t)f * BF + n) * B + l]);
+      for (int l = 0; l < B; ++l) put(I_::oT, I_::sT, I_::NT, f * BF + n, l, efc[((size_t)f * BF + n) * B + l]);
   for (int ax = 0; ax < 3; ++ax)
     for (int m = 0; m < 4; ++m)
-      for (int l = 0; l < 10; ++l) out[LImg::oK3 + (ax * 4 + m) * 10 + l] = (float)kt[((size_t)ax * B + m) * B + l];
+      for (int l = 0; l < 10; ++l) out[I_::oK3 + (ax * 4 + m) * 10 + l] = (float)kt[((size_t)ax * B + m) * B + l];
   for (int ax = 0; ax < 3; ++ax)
-    for (int l = 0; l < 4; ++l) out[LImg::oK4 + ax * 4 + l] = (float)kt[((size_t)ax * B + 0) * B + l];
+    for (int l = 0; l < 4; ++l) out[I_::oK4 + ax * 4 + l] = (float)kt[((size_t)ax * B + 0) * B + l];
 }
-
-int local_tc_floats() { return LImg::floats; }
 
 }  // namespace adg

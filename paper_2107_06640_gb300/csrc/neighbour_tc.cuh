@@ -1,5 +1,5 @@
-// Neighbour kernel on the tensor cores (tcgen05, 3xTF32), degree 5, FP32
-// dofs: face fluxes of Sec. 4.2 (Eq. numerical-flux) and their lift for
+// Neighbour kernel on the tensor cores (tcgen05, 3xTF32), degrees 5 and 4,
+// FP32 dofs: face fluxes of Sec. 4.2 (Eq. numerical-flux) and their lift for
 // elements whose faces are interior faces to the same or a coarser LTS
 // cluster, periodic faces or linear boundaries (the others take the CUDA-core
 // kernel); a coarser neighbour's face values are the integral of its Taylor
@@ -21,13 +21,20 @@
 //      face's coefficients formed once per tile from a 32-byte face record
 //      and the element's material; it writes the 9 values to a transposition
 //      buffer [element][p][28];
-//   3. the thread of row (element, p) takes its 24 columns, splits them into
-//      tf32 hi + lo and writes them to TMEM columns 24 f + n.
+//   3. the thread of row (element, p) takes its CW columns (the face's nodes
+//      padded to 8: 24 at degree 5, 16 at degree 4), splits them into tf32
+//      hi + lo and writes them to TMEM columns CW f + n.
 // One MMA chain then lifts all four faces:
-//   Q[(element, p)][m] -= sum_{f,n} G[p][24 f + n] lift_f[m][n],
-// A = G in TMEM (K = 96), B = the lift matrices resident in shared memory.
+//   Q[(element, p)][m] -= sum_{f,n} G[p][CW f + n] lift_f[m][n],
+// A = G in TMEM (K = 4 CW), B = the lift matrices resident in shared memory.
 // The next tile's face records, parameters and face 0 are requested before
-// this tile's lift.
+// this tile's lift.  At degree 4 a dofs row (140 bytes) is not 16-byte
+// aligned: the tile's rows are staged in shared memory with coalesced loads
+// and written back the same way.
+//
+// This header holds the kernel for both degrees; neighbour_tc.cu and
+// neighbour_tc4.cu instantiate it, one degree per translation unit.
+#pragma once
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -40,25 +47,40 @@ namespace adg {
 
 namespace {
 
-constexpr int B = 56, BF = 21;
 constexpr int TE = kTileElems;
 constexpr int kThreadsN = 512;  // two tiles in flight, two warpgroups (halves) per tile
 constexpr int kWaitIters = 1 << 24;
-constexpr int kK = 96;          // 4 faces x 24 columns (21 nodes + 3 zero)
-constexpr int kN = 64;          // 56 basis functions, padded
-constexpr int kFS = face_stride(5);   // floats per face block in the trace array (192)
-constexpr int kSS = kFS + 8;          // staged floats per element face: the 8 extra put the two
-                                      // elements a warp's work items span on different banks
-constexpr int kStage = TE * kSS;      // floats per staged face array
-constexpr int kGrow = 28;             // transposed flux row: 21 nodes + 7 zero; 28 floats put the 8
-                                      // rows of a quarter warp's 16-byte reads on distinct banks
-constexpr int kG = TE * 9 * kGrow;    // floats per transposition buffer
-constexpr int kItems = TE * BF;       // work items per face: element x node
-constexpr int kCoef = 32;             // per (face, element): frame n, s, t; middle-state and A- coefficients
+constexpr int kCoef = 32;       // per (face, element): frame n, s, t; middle-state and A- coefficients
 
-struct NImg {
+// Shapes of degree N: CW TMEM columns per face (BF nodes, zero padded), the
+// lift's N (the basis, padded to 16) and the transposed flux row kGrow
+// (CW floats, padded so that the 8 rows of a quarter warp's 16-byte reads
+// fall on distinct banks).
+template <int N>
+struct NDeg;
+template <>
+struct NDeg<5> {
+  static constexpr int B = 56, BF = 21, CW = 24, kN = 64, kGrow = 28;
+};
+template <>
+struct NDeg<4> {
+  static constexpr int B = 35, BF = 15, CW = 16, kN = 48, kGrow = 20;
+};
+
+template <int N>
+struct NImg : NDeg<N> {
+  using D = NDeg<N>;
+  static constexpr int B = D::B, BF = D::BF, CW = D::CW, kN = D::kN, kGrow = D::kGrow;
+  static constexpr int kK = 4 * CW;               // lift: K = 4 faces x CW columns
+  static constexpr int kFS = face_stride(N);      // floats per face block in the trace array
+  static constexpr int kSS = kFS + 8;             // staged floats per element face: the 8 extra put the
+                                                  // elements a warp's work items span on different banks
+  static constexpr int kStage = TE * kSS;         // floats per staged face array
+  static constexpr int kG = TE * 9 * kGrow;       // floats per transposition buffer
+  static constexpr int kItems = TE * BF;          // work items per face: element x node
+  static constexpr bool kAligned = B % 4 == 0;    // dofs rows 16-byte aligned (float4 access)
   static constexpr int oL = 0, sL = kN * kK;                  // lift hi, lo
-  static constexpr int oPerm = oL + 2 * sL;                   // 6 x 21 ints
+  static constexpr int oPerm = oL + 2 * sL;                   // 6 x BF ints
   static constexpr int oMeta = oPerm + 128;                   // per tile slot: [face][element] int64 + int
   static constexpr int sMeta = 4 * TE * 3;
   static constexpr int oStage = oMeta + 2 * sMeta;            // per tile slot: 2 buffers x (own, nbr)
@@ -69,13 +91,15 @@ struct NImg {
   static constexpr int oPar = oCoef + 2 * sCoef;              // per tile slot: element parameters
   static constexpr int sPar = TE * PAR;
   static constexpr int oG = oPar + 2 * sPar;                  // per tile slot: transposition buffer
-  static constexpr int floats = oG + 2 * kG;
+  static constexpr int oQ = oG + 2 * kG;                      // per tile slot (degree 4): the tile's dofs rows
+  static constexpr int sQ = kAligned ? 0 : TE * 9 * B;
+  static constexpr int floats = oQ + 2 * sQ;
   static constexpr int bytes = floats * 4;
+  static_assert(kItems <= 256 && 6 * BF <= 128 && kK <= 96 && 2 * kK + kN <= 256, "shapes of one tile slot");
+  static_assert(bytes + 64 <= 232448, "neighbour tensor-core kernel exceeds the shared memory of one CTA");
 };
-static_assert(NImg::bytes + 64 <= 232448, "neighbour tensor-core kernel exceeds the shared memory of one CTA");
 
-// per-slot TMEM columns: G hi [0, 96), G lo [96, 192), accumulator [192, 256)
-constexpr uint32_t cGh = 0, cGl = 96, cAcc = 192;
+// per-slot TMEM columns: G hi [0, kK), G lo [kK, 2 kK), accumulator [2 kK, 2 kK + kN)
 
 // the 256 threads (two warpgroups) of a tile slot
 __device__ __forceinline__ void slot_bar(int slot) { asm volatile("bar.sync %0, 256;" ::"r"(slot + 1)); }
@@ -97,10 +121,12 @@ __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0
 // derivative traces [N+1][9][Bf], integrated here over this element's
 // sub-interval with the coefficients cc (sum_k cc_k D_k, in the order of the
 // CUDA-core kernel).  kCoarse: the launch has such faces.
-template <bool kCoarse>
+template <int N, bool kCoarse>
 __device__ __forceinline__ void stage_face(int f, int u, int64_t v0, int nE, const float* trace,
                                            const long long* nbase, float* so, float* sn, const float* dtrace,
                                            const float* cc) {
+  using I_ = NImg<N>;
+  constexpr int kFS = I_::kFS, kSS = I_::kSS, BF = I_::BF;
   constexpr int kChunks = kFS / 4;  // 16-byte chunks per face block
 #pragma unroll
   for (int it = 0; it < (TE * kChunks + 255) / 256; ++it) {
@@ -120,7 +146,7 @@ __device__ __forceinline__ void stage_face(int f, int u, int64_t v0, int nE, con
           float acc = 0.f;
           if (pos < 9 * BF) {
 #pragma unroll
-            for (int k = 0; k <= 5; ++k) acc += cc[k] * dt[k * 9 * BF + pos];
+            for (int k = 0; k <= N; ++k) acc += cc[k] * dt[k * 9 * BF + pos];
           }
           x[t] = acc;
         }
@@ -241,11 +267,16 @@ __device__ __forceinline__ void face_flux(const float* co, const float qm[9], co
 // 64-bit divisions by S drop out; kCoarse: some faces of the launch have a
 // coarser LTS neighbour (without, their code stays out of the kernel)
 // kChunk: consecutive tiles a slot takes per sweep (a compile-time launch shape)
-template <bool kOne, bool kCoarse, bool kMulti, int kChunk>
+template <int N, bool kOne, bool kCoarse, bool kMulti, int kChunk>
 __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, const __grid_constant__ Segs g) {
+  using NI = NImg<N>;
+  constexpr int B = NI::B, BF = NI::BF, CW = NI::CW, kN = NI::kN, kK = NI::kK, kGrow = NI::kGrow;
+  constexpr int kFS = NI::kFS, kSS = NI::kSS, kStage = NI::kStage, kG = NI::kG, kItems = NI::kItems;
+  constexpr uint32_t cGh = 0, cGl = kK, cAcc = 2 * kK;
+  constexpr int NCH = (B + 7) / 8;  // 8-column chunks of a dofs row
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   float* sm = reinterpret_cast<float*>(smem_raw);
-  int* sPerm = reinterpret_cast<int*>(sm + NImg::oPerm);
+  int* sPerm = reinterpret_cast<int*>(sm + NI::oPerm);
   __shared__ uint32_t tmem_base;
   __shared__ __align__(8) uint64_t mbar[2];
   __shared__ int s_abort[2];
@@ -255,8 +286,8 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
   const int u = tid & 255, t = tid & 127, w = t >> 5, lane = tid & 31;
   {
     const float4* src = reinterpret_cast<const float4*>(a.tc_lift);
-    float4* dst = reinterpret_cast<float4*>(sm + NImg::oL);
-    for (int r = tid; r < 2 * NImg::sL / 4; r += kThreadsN) dst[r] = src[r];
+    float4* dst = reinterpret_cast<float4*>(sm + NI::oL);
+    for (int r = tid; r < 2 * NI::sL / 4; r += kThreadsN) dst[r] = src[r];
     for (int r = tid; r < 6 * BF; r += kThreadsN) sPerm[r] = a.perm[r];
   }
   if (tid < 2) {
@@ -271,17 +302,17 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
 
   const uint32_t tbase = tmem_base + (uint32_t)slot * 256u;
   const uint32_t trow = tbase + ((uint32_t)(32 * w) << 16);
-  const uint32_t sL = tc::smem_u32(sm + NImg::oL);
-  float* sStage = sm + NImg::oStage + slot * 4 * kStage;  // buffer b: own at 2b, nbr at 2b + 1
-  long long* sNb = reinterpret_cast<long long*>(sm + NImg::oMeta + slot * NImg::sMeta);
+  const uint32_t sL = tc::smem_u32(sm + NI::oL);
+  float* sStage = sm + NI::oStage + slot * 4 * kStage;  // buffer b: own at 2b, nbr at 2b + 1
+  long long* sNb = reinterpret_cast<long long*>(sm + NI::oMeta + slot * NI::sMeta);
   int* sPm = reinterpret_cast<int*>(sNb + 4 * TE);
   const float* trace = reinterpret_cast<const float*>(a.trace);
-  float* sRec = sm + NImg::oRec + slot * NImg::sRec;   // [element - e0][face][FREC]
-  float* sCo = sm + NImg::oCoef + slot * NImg::sCoef;  // [face][element - e0][kCoef]
-  float* sPr = sm + NImg::oPar + slot * NImg::sPar;
+  float* sRec = sm + NI::oRec + slot * NI::sRec;   // [element - e0][face][FREC]
+  float* sCo = sm + NI::oCoef + slot * NI::sCoef;  // [face][element - e0][kCoef]
+  float* sPr = sm + NI::oPar + slot * NI::sPar;
   // [element][p][28]; one buffer: face f + 1's items start after the barrier
   // that every thread reaches only when its rows of face f are done
-  float* sG = sm + NImg::oG + slot * kG;
+  float* sG = sm + NI::oG + slot * kG;
   for (int r = u; r < kG; r += 256) sG[r] = 0.f;  // columns 21..27 stay zero
   const int jj = lane / 9, p = lane - 9 * (lane / 9);
   const int S = kOne ? 1 : a.S;
@@ -299,7 +330,7 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
     prem = sg.n - lt * TE;
     if (cc) {
 #pragma unroll
-      for (int k = 0; k < 6; ++k) cc[k] = (float)sg.ccoef[k];
+      for (int k = 0; k <= N; ++k) cc[k] = (float)sg.ccoef[k];
     }
   };
   uint32_t phase = 0;
@@ -326,7 +357,7 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
   };
   auto prefetch = [&](int64_t tl, int info, int nbe) {
     int64_t pv0, prem;
-    float cc[6];
+    float cc[N + 1];
     tile_at(tl, pv0, prem, kCoarse ? cc : nullptr);
     const int pnE = (int)(prem < TE ? prem : TE);
     if (u < 4 * TE) {
@@ -341,7 +372,7 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
           nb = (vn_e * 4 + (info & 3)) * kFS;
         } else {
           const int ds = a.dslot[(int64_t)nbe * 4 + (info & 3)];
-          nb = -2 - ((int64_t)ds * S + (ve - ee * S)) * 6 * 9 * BF;
+          nb = -2 - ((int64_t)ds * S + (ve - ee * S)) * (N + 1) * 9 * BF;
         }
         pm = (info >> 2) & 7;
       }
@@ -355,7 +386,7 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
     for (int i4 = u; i4 < ne * FREC; i4 += 256) cp16(sRec + 4 * i4, a.frec + e0 * 4 * FREC + 4 * i4);
     for (int c = u; c < ne * (PAR / 4); c += 256)
       cp16(sPr + 4 * c, reinterpret_cast<const float*>(a.par) + e0 * PAR + 4 * c);
-    stage_face<kCoarse>(0, u, pv0, pnE, trace, sNb, sStage, sStage + kStage, dtrace, cc);
+    stage_face<N, kCoarse>(0, u, pv0, pnE, trace, sNb, sStage, sStage + kStage, dtrace, cc);
     cp_commit();
   };
 
@@ -372,7 +403,7 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
     int info_n = 0, nbe_n = 0;  // the next tile's neighbour information, needed after the faces
     if (next < ntiles) meta_load(next, info_n, nbe_n);
     int64_t v0, nrem;
-    float cc[6];
+    float cc[N + 1];
     tile_at(tile, v0, nrem, kCoarse ? cc : nullptr);
     const int nE = (int)(nrem < TE ? nrem : TE);
     const int i = 3 * w + jj;
@@ -385,7 +416,7 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
       // ---- stage face f + 1 while face f is used
       if (f < 3) {
         float* nb_buf = sStage + ((f + 1) & 1) * 2 * kStage;
-        stage_face<kCoarse>(f + 1, u, v0, nE, trace, sNb, nb_buf, nb_buf + kStage, dtrace, cc);
+        stage_face<N, kCoarse>(f + 1, u, v0, nE, trace, sNb, nb_buf, nb_buf + kStage, dtrace, cc);
         cp_commit();
         cp_wait<1>();
       } else {
@@ -398,7 +429,7 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
       slot_bar(slot);
       if (f == 2 && u == 0) {
         tc::fence_after();
-        tc::mma3_ts<kN, 48>(tbase + cAcc, tbase + cGh, tbase + cGl, sL, sL + 4 * NImg::sL, false);
+        tc::mma3_ts<kN, 2 * CW>(tbase + cAcc, tbase + cGh, tbase + cGl, sL, sL + 4 * NI::sL, false);
       }
       if (f == 0) {  // the face coefficients of the tile (records and parameters arrived with face 0)
         if (u < 4 * TE) face_coefficients(u / TE, u % TE, ne, sRec, sPr, sCo);
@@ -429,12 +460,12 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
         }
       }
       slot_bar(slot);
-      // ---- this row's 24 columns of face f -> TMEM (hi, lo): 8-column chunk c
+      // ---- this row's CW columns of face f -> TMEM (hi, lo): 8-column chunk c
       // by the half (c + f) % 2
       {
         const float4* g4 = reinterpret_cast<const float4*>(sG + ((i < TE ? i : 0) * 9 + p) * kGrow);
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
+        for (int c = 0; c < CW / 8; ++c) {
           if (((c + f) & 1) != half) continue;
           const float4 x0 = g4[2 * c], x1 = g4[2 * c + 1];
           float g[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
@@ -442,25 +473,32 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
 #pragma unroll
             for (int jn = 0; jn < 8; ++jn) g[jn] = 0.f;
           }
-          tc::st_split8(trow + cGh + 24 * f + 8 * c, trow + cGl + 24 * f + 8 * c, g);
+          tc::st_split8(trow + cGh + CW * f + 8 * c, trow + cGl + CW * f + 8 * c, g);
         }
       }
     }
     // this half's chunks (c % 2 == half) of the dofs row (in L2 from the
     // prefetch two tiles back), loaded while the next tile's copies are issued
-    // and the lift runs
+    // and the lift runs; degree 4: the tile's rows, staged in shared memory by
+    // the slot's 256 threads with coalesced loads
     float* Qrow = reinterpret_cast<float*>(a.Q) + (v * 9 + p) * B;
     float q[32];
+    float* sQ = sm + NI::oQ + slot * NI::sQ;
+    if constexpr (NI::kAligned) {
 #pragma unroll
-    for (int cj = 0; cj < 4; ++cj) {
-      const int c = half + 2 * cj;
-      float4 x0 = make_float4(0.f, 0.f, 0.f, 0.f), x1 = x0;
-      if (c < B / 8 && valid) {
-        x0 = reinterpret_cast<const float4*>(Qrow + 8 * c)[0];
-        x1 = reinterpret_cast<const float4*>(Qrow + 8 * c)[1];
+      for (int cj = 0; cj < 4; ++cj) {
+        const int c = half + 2 * cj;
+        float4 x0 = make_float4(0.f, 0.f, 0.f, 0.f), x1 = x0;
+        if (c < B / 8 && valid) {
+          x0 = reinterpret_cast<const float4*>(Qrow + 8 * c)[0];
+          x1 = reinterpret_cast<const float4*>(Qrow + 8 * c)[1];
+        }
+        q[8 * cj] = x0.x; q[8 * cj + 1] = x0.y; q[8 * cj + 2] = x0.z; q[8 * cj + 3] = x0.w;
+        q[8 * cj + 4] = x1.x; q[8 * cj + 5] = x1.y; q[8 * cj + 6] = x1.z; q[8 * cj + 7] = x1.w;
       }
-      q[8 * cj] = x0.x; q[8 * cj + 1] = x0.y; q[8 * cj + 2] = x0.z; q[8 * cj + 3] = x0.w;
-      q[8 * cj + 4] = x1.x; q[8 * cj + 5] = x1.y; q[8 * cj + 6] = x1.z; q[8 * cj + 7] = x1.w;
+    } else {
+      const float* Qt = reinterpret_cast<const float*>(a.Q) + v0 * 9 * B;
+      for (int r = u; r < nE * 9 * B; r += 256) sQ[r] = Qt[r];
     }
     // ---- the next tile's loads overlap this tile's lift and dofs update
     if (next < ntiles) prefetch(next, info_n, nbe_n);
@@ -470,7 +508,7 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
       int64_t q0, rem2;
       tile_at(next2, q0, rem2, nullptr);
       const uint32_t n2 = (uint32_t)(rem2 < TE ? rem2 : TE);
-      tc::prefetch_l2(reinterpret_cast<const float*>(a.Q) + q0 * 9 * B, n2 * 9 * B * 4);
+      tc::prefetch_l2_inner(reinterpret_cast<const float*>(a.Q) + q0 * 9 * B, n2 * 9 * B * 4);
       tc::prefetch_l2(trace + q0 * 4 * kFS, n2 * 4 * kFS * 4);
       const int64_t e0 = elem(q0), ne = elem(q0 + n2 - 1) - e0 + 1;
       tc::prefetch_l2(a.frec + e0 * 4 * FREC, (uint32_t)(ne * 4 * FREC * 4));
@@ -481,7 +519,7 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
     slot_bar(slot);
     tc::fence_after();
     if (u == 0) {
-      tc::mma3_ts<kN, kK, 48>(tbase + cAcc, tbase + cGh, tbase + cGl, sL, sL + 4 * NImg::sL, true);
+      tc::mma3_ts<kN, kK, 2 * CW>(tbase + cAcc, tbase + cGh, tbase + cGl, sL, sL + 4 * NI::sL, true);
       tc::commit(&mbar[slot]);
       if (!tc::mbar_wait(&mbar[slot], phase, kWaitIters)) {
         atomicOr(a.err, ERR_TIMEOUT);
@@ -497,21 +535,45 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
     {
       float x[32];
       tc::ld3x8(trow + cAcc + 8 * half, trow + cAcc + 8 * (half + 2), trow + cAcc + 8 * (half + 4), x);
-      if (half == 0) tc::ld8(trow + cAcc + 48, x + 24);
+      if constexpr (NCH > 6) {
+        if (half == 0) tc::ld8(trow + cAcc + 48, x + 24);
+      }
+      if constexpr (NI::kAligned) {
 #pragma unroll
-      for (int cj = 0; cj < 4; ++cj) {
-        const int c = half + 2 * cj;
-        if (c < B / 8 && valid) {
-          float nq[8];
+        for (int cj = 0; cj < 4; ++cj) {
+          const int c = half + 2 * cj;
+          if (c < B / 8 && valid) {
+            float nq[8];
 #pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            nq[j] = q[8 * cj + j] - x[8 * cj + j];
-            bad = fmaf(nq[j], 0.f, bad);
+            for (int j = 0; j < 8; ++j) {
+              nq[j] = q[8 * cj + j] - x[8 * cj + j];
+              bad = fmaf(nq[j], 0.f, bad);
+            }
+            float4* dst = reinterpret_cast<float4*>(Qrow + 8 * c);
+            dst[0] = make_float4(nq[0], nq[1], nq[2], nq[3]);
+            dst[1] = make_float4(nq[4], nq[5], nq[6], nq[7]);
           }
-          float4* dst = reinterpret_cast<float4*>(Qrow + 8 * c);
-          dst[0] = make_float4(nq[0], nq[1], nq[2], nq[3]);
-          dst[1] = make_float4(nq[4], nq[5], nq[6], nq[7]);
         }
+      } else {
+        static_assert(NCH <= 6, "three chunks per half");
+        float* srow = sQ + (i * 9 + p) * B;
+#pragma unroll
+        for (int cj = 0; cj < 3; ++cj) {
+          const int c = half + 2 * cj;
+          if (c < NCH && valid) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              if (8 * c + j < B) {
+                const float nq = srow[8 * c + j] - x[8 * cj + j];
+                bad = fmaf(nq, 0.f, bad);
+                srow[8 * c + j] = nq;
+              }
+            }
+          }
+        }
+        slot_bar(slot);
+        float* Qt = reinterpret_cast<float*>(a.Q) + v0 * 9 * B;
+        for (int r = u; r < nE * 9 * B; r += 256) Qt[r] = sQ[r];
       }
     }
     tc::fence_before();
@@ -526,11 +588,13 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
 
 }  // namespace
 
-int launch_neighbour_tc(const StepArgs& a, const Segs& g, int n_sms, void* stream, bool coarse) {
+// The launcher of degree N (the kernel table of that degree's translation unit).
+template <int N>
+int launch_neighbour_tc_deg(const StepArgs& a, const Segs& g, int n_sms, void* stream, bool coarse) {
   using K = void (*)(StepArgs, Segs);
 #define ADG_NK(one, coarse, multi) \
-  { neighbour_tc_kernel<one, coarse, multi, 1>, neighbour_tc_kernel<one, coarse, multi, 2>, \
-    neighbour_tc_kernel<one, coarse, multi, 4> }
+  { neighbour_tc_kernel<N, one, coarse, multi, 1>, neighbour_tc_kernel<N, one, coarse, multi, 2>, \
+    neighbour_tc_kernel<N, one, coarse, multi, 4> }
   // [S == 1][coarse][multi][chunk 1, 2, 4]
   static const K kern[2][2][2][3] = {{{ADG_NK(false, false, false), ADG_NK(false, false, true)},
                                       {ADG_NK(false, true, false), ADG_NK(false, true, true)}},
@@ -542,7 +606,7 @@ int launch_neighbour_tc(const StepArgs& a, const Segs& g, int n_sms, void* strea
     for (int i = 0; i < 24; ++i)
       if (ce == cudaSuccess)
         ce = cudaFuncSetAttribute((const void*)kern[i / 12][(i / 6) % 2][(i / 3) % 2][i % 3],
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, NImg::bytes);
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, NImg<N>::bytes);
     return ce;
   });
   if (rc) return rc;
@@ -551,25 +615,28 @@ int launch_neighbour_tc(const StepArgs& a, const Segs& g, int n_sms, void* strea
   const int ci = g.chunk >= 4 ? 2 : (g.chunk >= 2 ? 1 : 0);
   const int64_t want = (ntiles + 1) / 2;
   const unsigned grid = (unsigned)(want < n_sms ? want : n_sms);
-  kern[a.S == 1 ? 1 : 0][coarse ? 1 : 0][g.n > 1 ? 1 : 0][ci]<<<grid, kThreadsN, NImg::bytes, (cudaStream_t)stream>>>(a, g);
+  kern[a.S == 1 ? 1 : 0][coarse ? 1 : 0][g.n > 1 ? 1 : 0][ci]<<<grid, kThreadsN, NImg<N>::bytes,
+                                                               (cudaStream_t)stream>>>(a, g);
   return (int)cudaGetLastError();
 }
 
-// Host-side B operand of the lift: lift[f][m][n] of the degree-5 basis at
-// row m, column 24 f + n, split into tf32 hi / lo, canonical K-major layout.
-void pack_lift_tc(const double* lift, float* out) {
-  for (int i = 0; i < 2 * NImg::sL; ++i) out[i] = 0.f;
+// Host-side B operand of the lift of degree N: lift[f][m][n] of that
+// degree's basis at row m, column CW f + n, split into tf32 hi / lo,
+// canonical K-major layout.
+template <int N>
+void pack_lift_tc_deg(const double* lift, float* out) {
+  using NI = NImg<N>;
+  constexpr int B = NI::B, BF = NI::BF;
+  for (int i = 0; i < 2 * NI::sL; ++i) out[i] = 0.f;
   for (int f = 0; f < 4; ++f)
     for (int m = 0; m < B; ++m)
       for (int n = 0; n < BF; ++n) {
         const float xf = (float)lift[((size_t)f * B + m) * BF + n];
         const float hi = tc::tf32_trunc(xf);
-        const int o = tc::canon(m, 24 * f + n, kN);
+        const int o = tc::canon(m, NI::CW * f + n, NI::kN);
         out[o] = hi;
-        out[NImg::sL + o] = xf - hi;
+        out[NI::sL + o] = xf - hi;
       }
 }
-
-int lift_tc_floats() { return 2 * NImg::sL; }
 
 }  // namespace adg

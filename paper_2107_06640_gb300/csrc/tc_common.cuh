@@ -110,6 +110,14 @@ __device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
   }
 }
 
+// the same for any span: only its 16-byte aligned interior (a hint; the
+// bytes at either end that share a 16-byte unit with the span's neighbours
+// are left out)
+__device__ __forceinline__ void prefetch_l2_inner(const void* p, uint32_t bytes) {
+  const uintptr_t a0 = ((uintptr_t)p + 15) & ~(uintptr_t)15, a1 = ((uintptr_t)p + bytes) & ~(uintptr_t)15;
+  if (a1 > a0) prefetch_l2(reinterpret_cast<const void*>(a0), (uint32_t)(a1 - a0));
+}
+
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;"); }

@@ -54,14 +54,15 @@ def _run(m, mat, N, precision, steps=3, seed=41, macro=False, **kw):
     return o, s, eq, ee
 
 
-def test_acoustic_local_kernel_matches_the_oracle_3xtf32():
+@pytest.mark.parametrize("N", [5, 4])
+def test_acoustic_local_kernel_matches_the_oracle_3xtf32(N):
     """Ocean (two water layers) over crust, gravitational top, absorbing
     sides: the second water layer's 54 elements take the 4-quantity kernel
     (two tiles of 32, the second ragged), the crust the elastic one, the
     sea-surface layer the CUDA-core kernel; three steps."""
     from paper_2107_06640_gb300 import _lib
     m, mat = small_coupled()
-    o, s, eq, ee = _run(m, mat, 5, 2)
+    o, s, eq, ee = _run(m, mat, N, 2)
     assert eq <= 2e-5 and ee <= 1e-6, (eq, ee)
     _, launches = _lib.adg_profile(s.ctx, 1)
     assert launches[0] == 3  # local phase: elastic and acoustic tensor-core launches, CUDA-core rest
@@ -69,9 +70,10 @@ def test_acoustic_local_kernel_matches_the_oracle_3xtf32():
     assert int(s.info.tensor_core_updates_per_macro) == plain
 
 
-def test_acoustic_ocean_under_lts_3xtf32():
+@pytest.mark.parametrize("N", [5, 4])
+def test_acoustic_ocean_under_lts_3xtf32(N):
     m, mat = syn.workloads.coupled_box(nxy=4, n_water=3, n_crust=2, L=8e3, depth=4e3, water=1.5e3, grading=4.0)
-    o, s, eq, ee = _run(m, mat, 5, 2, steps=1, macro=True, max_clusters=4)
+    o, s, eq, ee = _run(m, mat, N, 2, steps=1, macro=True, max_clusters=4)
     assert s.info.n_clusters >= 2
     assert eq <= 2e-5 and ee <= 1e-6, (eq, ee)
 
@@ -97,16 +99,18 @@ def test_upload_keeps_only_the_isotropic_fluid_stress():
     assert np.allclose(got, want, rtol=0, atol=1e-15 * np.abs(want).max())
 
 
-def test_acoustic_kernel_equals_the_nine_quantity_kernel():
+@pytest.mark.parametrize("N", [5, 4])
+def test_acoustic_kernel_equals_the_nine_quantity_kernel(N):
     """On isotropic fluid data the 4-quantity local kernel gives the
     9-quantity tensor-core result to FP32 rounding."""
     from paper_2107_06640_gb300 import Solver
     m, mat = small_coupled()
     rho, lam, mu = mat
-    Q0 = to_gpu_layout(_isotropic(random_dofs((m.nt, 56, 9), 43, N=5), mu == 0.0))
+    B = (N + 1) * (N + 2) * (N + 3) // 6
+    Q0 = to_gpu_layout(_isotropic(random_dofs((m.nt, B, 9), 43, N=N), mu == 0.0))
     out = []
     for ac in (False, True):
-        s = Solver(m.xyz, m.tets, m.face_tag, rho, lam, mu, degree=5, cfl=0.5, precision=2, acoustic_ocean=ac)
+        s = Solver(m.xyz, m.tets, m.face_tag, rho, lam, mu, degree=N, cfl=0.5, precision=2, acoustic_ocean=ac)
         s.set_dofs(Q0)
         s.advance(3)
         out.append(s.get_dofs())

@@ -65,20 +65,21 @@ def test_coupled_random_dofs_fp64(N):
     assert eq <= FP64_TOL and ee <= FP64_TOL, (eq, ee)
 
 
-@pytest.mark.parametrize("precision", [1, 2])
-def test_coupled_random_dofs_fp32(precision):
-    # FP32 dofs (1: CUDA-core products, 2: tensor-core 3xTF32 products; FP64
-    # eta): per-output tolerance after 3 steps at N=5
-    eq, ee = _coupled_run(5, precision)
+@pytest.mark.parametrize("precision,N", [(1, 5), (2, 5), (2, 4)])
+def test_coupled_random_dofs_fp32(precision, N):
+    # FP32 dofs (1: CUDA-core products, 2: tensor-core 3xTF32 products at
+    # degrees 5 and 4; FP64 eta): per-output tolerance after 3 steps
+    eq, ee = _coupled_run(N, precision)
     assert eq <= 2e-5 and ee <= 1e-6, (eq, ee)
 
 
-def test_lts_coupled_graded_3xtf32():
+@pytest.mark.parametrize("N", [5, 4])
+def test_lts_coupled_graded_3xtf32(N):
     m, mat = syn.workloads.coupled_box(nxy=4, n_water=2, n_crust=2, L=8e3, depth=4e3, water=1e3,
                                        grading=4.0)
-    o, s = make_pair(m, mat, 5, precision=2, cfl=0.5, max_clusters=4)
+    o, s = make_pair(m, mat, N, precision=2, cfl=0.5, max_clusters=4)
     assert s.info.n_clusters >= 2
-    Q0 = random_dofs((m.nt, s.B, 9), 3, N=5)
+    Q0 = random_dofs((m.nt, s.B, 9), 3, N=N)
     o.Q = Q0.copy()
     s.set_dofs(to_gpu_layout(Q0))
     o.advance_macro()
@@ -86,14 +87,16 @@ def test_lts_coupled_graded_3xtf32():
     assert rel_l2(to_oracle_layout(s.get_dofs()), o.Q) <= 2e-5
 
 
-def test_periodic_cube_tensor_core_local_kernel():
+@pytest.mark.parametrize("N", [5, 4])
+def test_periodic_cube_tensor_core_local_kernel(N):
     """Every element of a periodic cube takes the tensor-core local kernel
     (no gravitational, fault or LTS-boundary faces); 384 elements = 32 tiles
-    of 12, ragged against the 2 x 152 tiles in flight."""
+    of 12, ragged against the 2 x 152 tiles in flight.  Degree 4 stages its
+    140-byte dofs rows through shared memory."""
     m, mat = syn.unit_cube_periodic(4), syn.materials.elastic_uniform(384)
-    o, s = make_pair(m, mat, 5, precision=2, cfl=0.5)
+    o, s = make_pair(m, mat, N, precision=2, cfl=0.5)
     from paper_2107_06640_gb300 import _lib
-    Q0 = random_dofs((m.nt, s.B, 9), 5, N=5)
+    Q0 = random_dofs((m.nt, s.B, 9), 5, N=N)
     o.Q = Q0.copy()
     s.set_dofs(to_gpu_layout(Q0))
     for _ in range(3):
@@ -105,10 +108,11 @@ def test_periodic_cube_tensor_core_local_kernel():
     assert int(s.info.tensor_core_updates_per_macro) == m.nt
 
 
-def test_coupled_box_uses_both_kernel_forms_3xtf32():
+@pytest.mark.parametrize("N", [5, 4])
+def test_coupled_box_uses_both_kernel_forms_3xtf32(N):
     m, mat = small_coupled()
     from paper_2107_06640_gb300 import _lib
-    s = make_pair(m, mat, 5, precision=2, cfl=0.5)[1]
+    s = make_pair(m, mat, N, precision=2, cfl=0.5)[1]
     ms, launches = _lib.adg_profile(s.ctx, 1)
     # tensor cores for the interior, CUDA cores for the gravity-face layer
     assert launches[0] == 2 and launches[1] == 2
@@ -118,14 +122,15 @@ def test_coupled_box_uses_both_kernel_forms_3xtf32():
     assert int(s.info.tensor_core_updates_per_macro) == plain < m.nt
 
 
-def test_ensemble_equals_independent_runs_3xtf32():
+@pytest.mark.parametrize("N", [5, 4])
+def test_ensemble_equals_independent_runs_3xtf32(N):
     m, mat = small_coupled(nxy=2)
     S = 5
     from paper_2107_06640_gb300 import ADG_3XTF32, Solver
     rho, lam, mu = mat
-    kw = dict(degree=5, cfl=0.5, precision=ADG_3XTF32)
+    kw = dict(degree=N, cfl=0.5, precision=ADG_3XTF32)
     ens = Solver(m.xyz, m.tets, m.face_tag, rho, lam, mu, ensemble=S, **kw)
-    Qs = np.stack([to_gpu_layout(random_dofs((m.nt, ens.B, 9), 20 + k, N=5)) for k in range(S)], axis=1)
+    Qs = np.stack([to_gpu_layout(random_dofs((m.nt, ens.B, 9), 20 + k, N=N)) for k in range(S)], axis=1)
     ens.set_dofs(Qs.astype(np.float32))
     ens.advance(2)
     out = ens.get_dofs()
@@ -149,16 +154,17 @@ def test_free_surface_and_rigid_wall_fp64():
     assert rel_l2(to_oracle_layout(s.get_dofs()), o.Q) <= FP64_TOL
 
 
-def test_free_surface_rigid_wall_absorbing_on_the_tensor_cores():
-    """Free-surface top, rigid-wall bottom and absorbing sides at N=5 in the
-    3xTF32 form: with no gravitational face every element takes both
-    tensor-core kernels, whose neighbour kernel forms each face's Godunov flux
-    (ghost states of the linear boundaries included) in the face frame."""
+@pytest.mark.parametrize("N", [5, 4])
+def test_free_surface_rigid_wall_absorbing_on_the_tensor_cores(N):
+    """Free-surface top, rigid-wall bottom and absorbing sides in the 3xTF32
+    form: with no gravitational face every element takes both tensor-core
+    kernels, whose neighbour kernel forms each face's Godunov flux (ghost
+    states of the linear boundaries included) in the face frame."""
     m, mat = small_coupled(rigid_bottom=True)
     m.face_tag[m.face_tag == syn.TAG_GRAVITY] = syn.TAG_FREE
-    o, s = make_pair(m, mat, 5, precision=2, cfl=0.5)
+    o, s = make_pair(m, mat, N, precision=2, cfl=0.5)
     assert int(s.info.tensor_core_updates_per_macro) == m.nt
-    Q0 = random_dofs((m.nt, s.B, 9), 8, N=5)
+    Q0 = random_dofs((m.nt, s.B, 9), 8, N=N)
     o.Q = Q0.copy()
     s.set_dofs(to_gpu_layout(Q0))
     for _ in range(3):

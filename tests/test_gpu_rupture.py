@@ -107,6 +107,32 @@ def test_slip_weakening_under_ocean_with_lts_fp64():
     _compare(o, s, nff)
 
 
+def test_rupture_degree4_on_the_tensor_cores_under_ocean():
+    """Degree 4 in the 3xTF32 form, the megathrust's configuration: elements
+    with a fault or gravitational face take the FP32 CUDA-core kernels, the
+    others both tensor-core kernels; the friction solve stays FP64 on FP32
+    traces.  Against the FP64 oracle after 4 steps: dofs within 2e-5 as the
+    other 3xTF32 steps; the fault state within 1e-3, because a relative error
+    d in the traction moves ln V by about d Th / (a S) (Th / (a S) ~ 50 here)."""
+    from paper_2107_06640_gb300 import _lib
+    m, o, s, nff = _fault_pair(N=4, ocean_layers=1, precision=2)
+    assert 0 < int(s.info.tensor_core_updates_per_macro) < m.nt
+    Q0 = random_dofs((m.nt, s.B, 9), 4, N=4) * 1e3
+    o.Q = Q0.copy()
+    s.set_dofs(to_gpu_layout(Q0))
+    for _ in range(4):
+        o.step_gts()
+    s.advance(4)
+    assert rel_l2(to_oracle_layout(s.get_dofs()), o.Q) <= 2e-5, rel_l2(to_oracle_layout(s.get_dofs()), o.Q)
+    st = _read_fault(s, nff)
+    errs = [rel_l2(st[..., 0], o.fault["V"]), rel_l2(st[..., 1], o.fault["psi"]),
+            rel_l2(st[..., 2:5], o.fault["slip"]), rel_l2(st[..., 5:8], o.fault["traction"])]
+    assert max(errs) <= 1e-3, errs
+    assert st[..., 0].max() > 0.1          # the nucleation patch ruptured
+    _, launches = _lib.adg_profile(s.ctx, 1)
+    assert launches[0] >= 2 and launches[1] >= 2   # tensor-core and CUDA-core launches in both phases
+
+
 def test_friction_law_switch_needs_new_parameters():
     from paper_2107_06640_gb300 import AdgError, _lib
     m, o, s, nff = _fault_pair(law="lsw")
