@@ -50,8 +50,8 @@ extern "C" {
 
 #define ADG_FP64 0
 #define ADG_FP32 1
-/* FP32 dofs; at degree 5 the reference-matrix products (predictor, face
- * traces, volume term, lift) of the elements without gravitational face,
+/* FP32 dofs; at degrees 5 and 4 the reference-matrix products (predictor,
+ * face traces, volume term, lift) of the elements without gravitational face,
  * fault face or neighbour in a finer LTS cluster run on the tensor cores
  * (tcgen05) as 3xTF32 split products with FP32 accumulation, everything else
  * as in ADG_FP32; other degrees behave as ADG_FP32. */
@@ -93,7 +93,7 @@ typedef struct adg_info {
   int64_t n_fault_faces;
   int64_t updates_per_macro; /* element updates (x ensemble) per macro step */
   int64_t device_bytes;
-  int64_t tensor_core_updates_per_macro; /* of those, by the tensor-core kernels (ADG_3XTF32, degree 5) */
+  int64_t tensor_core_updates_per_macro; /* of those, by the tensor-core kernels (ADG_3XTF32, degree 5 or 4) */
   int64_t n_receivers;       /* from the last adg_add_receivers */
   int64_t acoustic_updates_per_macro; /* of the tensor-core ones, on the 4-quantity local kernel
                                          (adg_set_acoustic_ocean) */
@@ -128,7 +128,7 @@ int adg_upload_material(adg_ctx* ctx, const double* rho, const double* lambda, c
  *    with no shear stress; the scheme keeps that form (the acoustic subspace
  *    is invariant), so the results equal those of the 9-quantity system on
  *    such data;
- *  - with the tensor-core kernels (ADG_3XTF32, degree 5), the fluid elements
+ *  - with the tensor-core kernels (ADG_3XTF32, degree 5 or 4), the fluid elements
  *    without gravitational face, fault face or LTS neighbour in another
  *    cluster take a 4-quantity (p, v) local kernel: 32 elements per 128-row
  *    tile, the acoustic star product, 4 of the 9 dofs rows read; their face
@@ -248,7 +248,7 @@ int adg_sync(adg_ctx* ctx);
  * kernel kind of a cluster on the library stream.  ms[k] = mean duration of
  * one such phase of kind k, launches[k] = number of kernel launches (arrays
  * of 5), k = 0 local (predictor, volume, traces; with ADG_3XTF32 at degree 5
- * one tensor-core and one CUDA-core launch per cluster), 1 neighbour flux,
+ * or 4 tensor-core and CUDA-core launches), 1 neighbour flux,
  * 2 fault friction solve, 3 and 4 the tensor-core launch of the local and
  * of the neighbour phase alone (0 without one).  Advances the simulation
  * like adg_advance. */
