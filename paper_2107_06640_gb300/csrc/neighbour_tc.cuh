@@ -81,16 +81,18 @@ struct NImg : NDeg<N> {
   static constexpr bool kAligned = B % 4 == 0;    // dofs rows 16-byte aligned (float4 access)
   static constexpr int oL = 0, sL = kN * kK;                  // lift hi, lo
   static constexpr int oPerm = oL + 2 * sL;                   // 6 x BF ints
-  static constexpr int oMeta = oPerm + 128;                   // per tile slot: [face][element] int64 + int
+  // per tile slot and tile parity: [face][element] int64 + int
+  static constexpr int oMeta = oPerm + 128;
   static constexpr int sMeta = 4 * TE * 3;
-  static constexpr int oStage = oMeta + 2 * sMeta;            // per tile slot: 2 buffers x (own, nbr)
-  static constexpr int oRec = oStage + 2 * 4 * kStage;        // per tile slot: face records [element][face]
-  static constexpr int sRec = TE * 4 * FREC;
-  static constexpr int oCoef = oRec + 2 * sRec;               // per tile slot: [face][element][kCoef]
+  static constexpr int kBufs = 3;                             // staged faces: the one in use and two ahead
+  static constexpr int oStage = oMeta + 2 * 2 * sMeta;        // per tile slot: kBufs buffers x (own, nbr)
+  static constexpr int oRec = oStage + 2 * kBufs * 2 * kStage;  // per slot and tile parity: face records
+  static constexpr int sRec = TE * 4 * FREC;                  // [element][face][FREC]
+  static constexpr int oCoef = oRec + 2 * 2 * sRec;           // per tile slot: [face][element][kCoef]
   static constexpr int sCoef = 4 * TE * kCoef;
-  static constexpr int oPar = oCoef + 2 * sCoef;              // per tile slot: element parameters
+  static constexpr int oPar = oCoef + 2 * sCoef;              // per slot and tile parity: element parameters
   static constexpr int sPar = TE * PAR;
-  static constexpr int oG = oPar + 2 * sPar;                  // per tile slot: transposition buffer
+  static constexpr int oG = oPar + 2 * 2 * sPar;              // per tile slot: transposition buffer
   static constexpr int oQ = oG + 2 * kG;                      // per tile slot (degree 4): the tile's dofs rows
   static constexpr int sQ = kAligned ? 0 : TE * 9 * B;
   static constexpr int floats = oQ + 2 * sQ;
@@ -303,13 +305,18 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
   const uint32_t tbase = tmem_base + (uint32_t)slot * 256u;
   const uint32_t trow = tbase + ((uint32_t)(32 * w) << 16);
   const uint32_t sL = tc::smem_u32(sm + NI::oL);
-  float* sStage = sm + NI::oStage + slot * 4 * kStage;  // buffer b: own at 2b, nbr at 2b + 1
-  long long* sNb = reinterpret_cast<long long*>(sm + NI::oMeta + slot * NI::sMeta);
-  int* sPm = reinterpret_cast<int*>(sNb + 4 * TE);
+  // staged face g (counted over the slot's tiles, 4 per tile) in buffer g % 3:
+  // own traces at 2 b, the neighbours' at 2 b + 1
+  float* sStage = sm + NI::oStage + slot * NI::kBufs * 2 * kStage;
+  auto stage_buf = [&](int gface) { return sStage + (gface % NI::kBufs) * 2 * kStage; };
+  // per tile parity: the trace-block table and node permutations of a tile's
+  // faces, its face records and element parameters
+  auto sNb = [&](int par) { return reinterpret_cast<long long*>(sm + NI::oMeta + (slot * 2 + par) * NI::sMeta); };
+  auto sPm = [&](int par) { return reinterpret_cast<int*>(sNb(par) + 4 * TE); };
+  auto sRec = [&](int par) { return sm + NI::oRec + (slot * 2 + par) * NI::sRec; };  // [element - e0][face][FREC]
+  auto sPr = [&](int par) { return sm + NI::oPar + (slot * 2 + par) * NI::sPar; };
   const float* trace = reinterpret_cast<const float*>(a.trace);
-  float* sRec = sm + NI::oRec + slot * NI::sRec;   // [element - e0][face][FREC]
   float* sCo = sm + NI::oCoef + slot * NI::sCoef;  // [face][element - e0][kCoef]
-  float* sPr = sm + NI::oPar + slot * NI::sPar;
   // [element][p][28]; one buffer: face f + 1's items start after the barrier
   // that every thread reaches only when its rows of face f are done
   float* sG = sm + NI::oG + slot * kG;
@@ -337,10 +344,10 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
   float bad = 0.f;  // stays 0 while every updated dof is finite (x * 0 is NaN for x = inf, NaN)
 
   // Neighbour trace blocks of a tile's faces, then one cp.async group per
-  // thread with the tile's face records, element parameters and face 0
-  // (staging buffer 0).  Thread u < 48 owns (face u / 12, element u % 12) of
-  // a tile: its neighbour information, loaded early (meta_load) and made the
-  // tile's trace-block table later (prefetch).
+  // thread with the tile's face records, element parameters and face 0, all
+  // into the buffers of the tile's parity.  Thread u < 48 owns (face u / 12,
+  // element u % 12) of a tile: its neighbour information, loaded early
+  // (meta_load) and made the tile's trace-block table later (prefetch).
   auto meta_load = [&](int64_t tl, int& info, int& nbe) {
     info = 0;
     nbe = 0;
@@ -355,7 +362,7 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
       }
     }
   };
-  auto prefetch = [&](int64_t tl, int info, int nbe) {
+  auto prefetch = [&](int64_t tl, int par, int info, int nbe) {
     int64_t pv0, prem;
     float cc[N + 1];
     tile_at(tl, pv0, prem, kCoarse ? cc : nullptr);
@@ -376,31 +383,49 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
         }
         pm = (info >> 2) & 7;
       }
-      sNb[u] = nb;
-      sPm[u] = pm;
+      sNb(par)[u] = nb;
+      sPm(par)[u] = pm;
     }
     slot_bar(slot);
     const int64_t e0 = elem(pv0);
     const int ne = (int)(elem(pv0 + pnE - 1) - e0 + 1);
     // face records of elements e0 .. e0 + ne - 1: ne x 128 bytes, 16-byte aligned
-    for (int i4 = u; i4 < ne * FREC; i4 += 256) cp16(sRec + 4 * i4, a.frec + e0 * 4 * FREC + 4 * i4);
+    for (int i4 = u; i4 < ne * FREC; i4 += 256) cp16(sRec(par) + 4 * i4, a.frec + e0 * 4 * FREC + 4 * i4);
     for (int c = u; c < ne * (PAR / 4); c += 256)
-      cp16(sPr + 4 * c, reinterpret_cast<const float*>(a.par) + e0 * PAR + 4 * c);
-    stage_face<N, kCoarse>(0, u, pv0, pnE, trace, sNb, sStage, sStage + kStage, dtrace, cc);
+      cp16(sPr(par) + 4 * c, reinterpret_cast<const float*>(a.par) + e0 * PAR + 4 * c);
+    // (committed with the tile's face 0)
+  };
+  // face f of the tile with slot counter itl: staged (one cp.async group) into buffer (4 itl + f) % 3
+  auto stage = [&](int64_t tl, int itl, int f) {
+    int64_t pv0, prem;
+    float cc[N + 1];
+    tile_at(tl, pv0, prem, kCoarse ? cc : nullptr);
+    const int pnE = (int)(prem < TE ? prem : TE);
+    float* buf = stage_buf(4 * itl + f);
+    stage_face<N, kCoarse>(f, u, pv0, pnE, trace, sNb(itl & 1), buf, buf + kStage, dtrace, cc);
     cp_commit();
   };
 
+  // Faces are staged two ahead of their use (three buffers): at face f of a
+  // tile, face f + 2 of the same tile (f < 2) or face f - 2 of the next tile
+  // (f >= 2; with face 0 come the next tile's records and parameters) is
+  // requested, then the oldest group, face f, is waited for.  Every step
+  // commits one group (an empty one past the last tile), so cp.async.wait_group 2
+  // always leaves exactly the two younger faces in flight.
   const int slots = (int)gridDim.x * 2, me = (int)blockIdx.x * 2 + slot;
   int it = 0;
   int64_t tile = slot_tile(0, me, slots, kChunk);
   if (tile < ntiles) {
     int info0, nbe0;
     meta_load(tile, info0, nbe0);
-    prefetch(tile, info0, nbe0);
+    prefetch(tile, 0, info0, nbe0);
+    stage(tile, 0, 0);
+    stage(tile, 0, 1);
   }
   for (; tile < ntiles; tile = slot_tile(++it, me, slots, kChunk)) {
     const int64_t next = slot_tile(it + 1, me, slots, kChunk);
-    int info_n = 0, nbe_n = 0;  // the next tile's neighbour information, needed after the faces
+    const int par = it & 1;
+    int info_n = 0, nbe_n = 0;  // the next tile's neighbour information, needed at face 2
     if (next < ntiles) meta_load(next, info_n, nbe_n);
     int64_t v0, nrem;
     float cc[N + 1];
@@ -413,15 +438,16 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
     const int ne = (int)(elem(v0 + nE - 1) - elem(v0) + 1);  // elements of the tile
 #pragma unroll 1
     for (int f = 0; f < 4; ++f) {
-      // ---- stage face f + 1 while face f is used
-      if (f < 3) {
-        float* nb_buf = sStage + ((f + 1) & 1) * 2 * kStage;
-        stage_face<N, kCoarse>(f + 1, u, v0, nE, trace, sNb, nb_buf, nb_buf + kStage, dtrace, cc);
-        cp_commit();
-        cp_wait<1>();
+      // ---- request the face two ahead, wait for face f
+      if (f < 2) {
+        stage(tile, it, f + 2);
+      } else if (next < ntiles) {
+        if (f == 2) prefetch(next, par ^ 1, info_n, nbe_n);
+        stage(next, it + 1, f - 2);
       } else {
-        cp_wait<0>();
+        cp_commit();
       }
+      cp_wait<2>();
       if (f == 2) {  // the rows of faces 0 and 1 are in TMEM: their lift starts now
         asm volatile("tcgen05.wait::st.sync.aligned;");
         tc::fence_before();
@@ -432,10 +458,10 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
         tc::mma3_ts<kN, 2 * CW>(tbase + cAcc, tbase + cGh, tbase + cGl, sL, sL + 4 * NI::sL, false);
       }
       if (f == 0) {  // the face coefficients of the tile (records and parameters arrived with face 0)
-        if (u < 4 * TE) face_coefficients(u / TE, u % TE, ne, sRec, sPr, sCo);
+        if (u < 4 * TE) face_coefficients(u / TE, u % TE, ne, sRec(par), sPr(par), sCo);
         slot_bar(slot);
       }
-      const float* sVo = sStage + (f & 1) * 2 * kStage;
+      const float* sVo = stage_buf(4 * it + f);
       const float* sVn = sVo + kStage;
       // ---- work item (element, node) of thread u: scaled Godunov flux in the face frame
       if (u < kItems) {
@@ -443,7 +469,7 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
         const int el = kOne ? ei : (r0 + ei) / S;  // element of item's virtual element, from the tile's first
         float* gout = sG + ei * 9 * kGrow + n;
         if (ei < nE) {
-          const int pn = sPerm[sPm[f * TE + ei] * BF + n];
+          const int pn = sPerm[sPm(par)[f * TE + ei] * BF + n];
           float qo[9], qn[9];
 #pragma unroll
           for (int qq = 0; qq < 9; ++qq) {
@@ -500,9 +526,7 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
       const float* Qt = reinterpret_cast<const float*>(a.Q) + v0 * 9 * B;
       for (int r = u; r < nE * 9 * B; r += 256) sQ[r] = Qt[r];
     }
-    // ---- the next tile's loads overlap this tile's lift and dofs update
-    if (next < ntiles) prefetch(next, info_n, nbe_n);
-    // and the tile after it into L2
+    // ---- the tile after the next into L2
     const int64_t next2 = slot_tile(it + 2, me, slots, kChunk);
     if (u == 0 && next2 < ntiles) {
       int64_t q0, rem2;
@@ -579,6 +603,7 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
     tc::fence_before();
   }
   if (__any_sync(0xffffffffu, bad != 0.f) && lane == 0) atomicOr(a.err, ERR_NAN);
+  cp_wait<0>();  // no copy into shared memory outlives the loop (an aborted slot may leave some)
   if (u == 0 && s_abort[slot]) tc::mbar_wait(&mbar[slot], phase ^ 1u, kWaitIters);
   tc::fence_before();
   __syncthreads();
