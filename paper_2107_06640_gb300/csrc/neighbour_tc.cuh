@@ -88,9 +88,9 @@ struct NImg : NDeg<N> {
   static constexpr int oStage = oMeta + 2 * 2 * sMeta;        // per tile slot: kBufs buffers x (own, nbr)
   static constexpr int oRec = oStage + 2 * kBufs * 2 * kStage;  // per slot and tile parity: face records
   static constexpr int sRec = TE * 4 * FREC;                  // [element][face][FREC]
-  static constexpr int oCoef = oRec + 2 * 2 * sRec;           // per tile slot: [face][element][kCoef]
+  static constexpr int oCoef = oRec + 2 * 2 * sRec;           // per slot and tile parity: [face][element][kCoef]
   static constexpr int sCoef = 4 * TE * kCoef;
-  static constexpr int oPar = oCoef + 2 * sCoef;              // per slot and tile parity: element parameters
+  static constexpr int oPar = oCoef + 2 * 2 * sCoef;          // per slot and tile parity: element parameters
   static constexpr int sPar = TE * PAR;
   static constexpr int oG = oPar + 2 * 2 * sPar;              // per tile slot: transposition buffer
   static constexpr int oQ = oG + 2 * kG;                      // per tile slot (degree 4): the tile's dofs rows
@@ -225,7 +225,14 @@ __device__ __forceinline__ void face_coefficients(int f, int el, int ne, const f
 // Scaled Godunov flux of one face node: qm, qp the minus and plus traces
 // (global frame, quantities sxx syy szz sxy syz sxz vx vy vz); g = s_f (F- qm +
 // F+ qp) = s_f T A- (Mm T^-1 qm + Mp T^-1 qp).
-__device__ __forceinline__ void face_flux(const float* co, const float qm[9], const float qp[9], float g[9]) {
+__device__ __forceinline__ void face_flux(const float* cop, const float qm[9], const float qp[9], float g[9]) {
+  // the 29 coefficients in eight 16-byte loads (a (face, element) record is 32 floats, 16-byte aligned)
+  float co[32];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const float4 x = reinterpret_cast<const float4*>(cop)[i];
+    co[4 * i] = x.x; co[4 * i + 1] = x.y; co[4 * i + 2] = x.z; co[4 * i + 3] = x.w;
+  }
   const float nx = co[0], ny = co[1], nz = co[2], sx = co[3], sy = co[4], sz = co[5], tx = co[6], ty = co[7],
               tz = co[8];
   float w[2][6];  // rotated components 0, 3, 5, 6, 7, 8 of each state
@@ -316,7 +323,7 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
   auto sRec = [&](int par) { return sm + NI::oRec + (slot * 2 + par) * NI::sRec; };  // [element - e0][face][FREC]
   auto sPr = [&](int par) { return sm + NI::oPar + (slot * 2 + par) * NI::sPar; };
   const float* trace = reinterpret_cast<const float*>(a.trace);
-  float* sCo = sm + NI::oCoef + slot * NI::sCoef;  // [face][element - e0][kCoef]
+  auto sCo = [&](int par) { return sm + NI::oCoef + (slot * 2 + par) * NI::sCoef; };  // [face][element - e0][kCoef]
   // [element][p][28]; one buffer: face f + 1's items start after the barrier
   // that every thread reaches only when its rows of face f are done
   float* sG = sm + NI::oG + slot * kG;
@@ -457,8 +464,8 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
         tc::fence_after();
         tc::mma3_ts<kN, 2 * CW>(tbase + cAcc, tbase + cGh, tbase + cGl, sL, sL + 4 * NI::sL, false);
       }
-      if (f == 0) {  // the face coefficients of the tile (records and parameters arrived with face 0)
-        if (u < 4 * TE) face_coefficients(u / TE, u % TE, ne, sRec(par), sPr(par), sCo);
+      if (f == 0 && it == 0) {  // the first tile's face coefficients (later tiles': during the lift before)
+        if (u < 4 * TE) face_coefficients(u / TE, u % TE, ne, sRec(par), sPr(par), sCo(par));
         slot_bar(slot);
       }
       const float* sVo = stage_buf(4 * it + f);
@@ -477,7 +484,7 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
             qn[qq] = sVn[ei * kSS + qq * BF + pn];
           }
           float g[9];
-          face_flux(sCo + (f * TE + el) * kCoef, qo, qn, g);
+          face_flux(sCo(par) + (f * TE + el) * kCoef, qo, qn, g);
 #pragma unroll
           for (int pp = 0; pp < 9; ++pp) gout[pp * kGrow] = g[pp];
         } else {
@@ -537,11 +544,22 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
       const int64_t e0 = elem(q0), ne = elem(q0 + n2 - 1) - e0 + 1;
       tc::prefetch_l2(a.frec + e0 * 4 * FREC, (uint32_t)(ne * 4 * FREC * 4));
     }
-    // ---- lift of faces 2 and 3 on the tensor cores (faces 0 and 1 were issued above)
+    // ---- lift of faces 2 and 3 on the tensor cores (faces 0 and 1 were issued above);
+    // meanwhile threads 64..111 form the next tile's face coefficients (its
+    // records and parameters came with its face 0, the older of the two groups
+    // in flight)
+    if (next < ntiles) cp_wait<1>();
     asm volatile("tcgen05.wait::st.sync.aligned;");
     tc::fence_before();
     slot_bar(slot);
     tc::fence_after();
+    if (next < ntiles && u >= 64 && u < 64 + 4 * TE) {
+      int64_t pv0, prem;
+      tile_at(next, pv0, prem, nullptr);
+      const int pnE = (int)(prem < TE ? prem : TE);
+      const int ne_n = (int)(elem(pv0 + pnE - 1) - elem(pv0) + 1);
+      face_coefficients((u - 64) / TE, (u - 64) % TE, ne_n, sRec(par ^ 1), sPr(par ^ 1), sCo(par ^ 1));
+    }
     if (u == 0) {
       tc::mma3_ts<kN, kK, 2 * CW>(tbase + cAcc, tbase + cGh, tbase + cGl, sL, sL + 4 * NI::sL, true);
       tc::commit(&mbar[slot]);
