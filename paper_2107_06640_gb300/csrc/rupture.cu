@@ -155,11 +155,13 @@ __device__ float mlp_eval(const float* W, const float f[MLP_IN]) {
   return osc[0] + osc[1] * y;
 }
 
-template <typename T, int N>
+// kNet: the launch evaluates the friction-guess network or captures training
+// samples (without, that code stays out of the kernel)
+template <typename T, int N, bool kNet>
 __global__ void __launch_bounds__(128) rupture_kernel(DRArgs a) {
   constexpr int Bf = nb2(N);
   __shared__ __align__(16) float sW[(MLP_NPARAM + 3) / 4 * 4];  // the network's weights, once per block
-  if (a.mlp) {
+  if (kNet && a.mlp) {
     for (int i = threadIdx.x; i < MLP_NPARAM; i += blockDim.x) sW[i] = a.mlp[i];
   }
   __syncthreads();
@@ -203,17 +205,22 @@ __global__ void __launch_bounds__(128) rupture_kernel(DRArgs a) {
   bool busy = false;
   unsigned long long n_solves = 0, n_iters = 0;
   bool all_ok = true;
+#pragma unroll 1
   for (int j = 0; j <= N; ++j) {
     const double t = a.tp[j];
+    // Taylor weights t^k / k!, formed once per time point
+    double tk[N + 1];
+    tk[0] = 1.0;
+#pragma unroll
+    for (int k = 1; k <= N; ++k) tk[k] = tk[k - 1] * t / (double)k;
     double qm[9], qp[9];
 #pragma unroll
     for (int c = 0; c < 9; ++c) {
-      double am = 0, ap = 0, tk = 1.0, fac = 1.0;
+      double am = 0, ap = 0;
+#pragma unroll
       for (int k = 0; k <= N; ++k) {
-        am += tk / fac * (double)dm[(k * 9 + c) * Bf + n];
-        ap += tk / fac * (double)dp[(k * 9 + c) * Bf + np_];
-        tk *= t;
-        fac *= (k + 1);
+        am += tk[k] * (double)dm[(k * 9 + c) * Bf + n];
+        ap += tk[k] * (double)dp[(k * 9 + c) * Bf + np_];
       }
       qm[c] = am;
       qp[c] = ap;
@@ -246,25 +253,29 @@ __global__ void __launch_bounds__(128) rupture_kernel(DRArgs a) {
     const bool lsw = a.law == FRIC_LSW;
     const bool solve = (Th > 0) && (S > 0) && !lsw;
     bool learned = false;
-    if (solve && (a.mlp || a.capture)) {
-      const double lc = psi / p.a - log(2.0 * p.V0);
-      const double xhi = log(Th / eta);
-      const double r = fmin(Th / (S * p.a), 700.0);
-      const double xwc = fmin(fmax(xw, kXFloor), xhi);
-      xa = fmin(fmax(r - lc - 0.6931471805599453, kXFloor), xhi);
-      feat[0] = (float)r;
-      feat[1] = (float)lc;
-      feat[2] = (float)xhi;
-      feat[3] = (float)xwc;
-      feat[4] = (float)fmin(fmax(log(eta / (S * p.a)), -50.0), 50.0);
-      feat[5] = (float)xa;
+    // the features only where the network runs or a training sample is
+    // captured, in FP32 (they only seed Newton; the solve itself stays FP64)
+    if (kNet && solve && ((a.mlp && busy) || a.capture)) {
+      const float Sa = (float)(S * p.a), Thf = (float)Th, etaf = (float)eta;
+      const float lc = (float)(psi / p.a) - logf(2.f * (float)p.V0);
+      const float xhi = logf(Thf / etaf);
+      const float r = fminf(Thf / Sa, 700.f);
+      const float xwc = fminf(fmaxf((float)xw, (float)kXFloor), xhi);
+      const float xaf = fminf(fmaxf(r - lc - 0.6931472f, (float)kXFloor), xhi);
+      xa = (double)xaf;
+      feat[0] = r;
+      feat[1] = lc;
+      feat[2] = xhi;
+      feat[3] = xwc;
+      feat[4] = fminf(fmaxf(logf(etaf / Sa), -50.f), 50.f);
+      feat[5] = xaf;
       if (a.mlp && busy) {
         // predicted ln V* = x_a + network; when it was also evaluated at the
         // previous time point, the start is the warm start moved by the change
         // of that prediction
         const double xhat = xa + (double)mlp_eval(sW, feat);
         if (have_prev) {
-          x0 = fmin(fmax(xwc + (xhat - xhat_prev), kXFloor), xhi);
+          x0 = fmin(fmax((double)xwc + (xhat - xhat_prev), kXFloor), (double)xhi);
           learned = true;
         }
         xhat_prev = xhat;
@@ -308,7 +319,7 @@ __global__ void __launch_bounds__(128) rupture_kernel(DRArgs a) {
         n_iters += it;
       }
       if (pass == 0) busy = solve && it > 1;
-      if (pass == 0 && solve && a.capture) {
+      if (kNet && pass == 0 && solve && a.capture) {
         const unsigned long long k = atomicAdd(a.cap_count, 1ull);
         if ((int64_t)k < a.cap_capacity) {
           float* row = a.capture + k * (MLP_IN + 1);
@@ -357,14 +368,17 @@ int dispatch(int N, const DRArgs& a, cudaStream_t st) {
   const int64_t total = a.n_faces * a.S * nb2(N);
   if (total <= 0) return 0;
   const unsigned grid = (unsigned)((total + 127) / 128);
+  const bool net = a.mlp || a.capture;
+#define ADG_RK(n) (net ? rupture_kernel<T, n, true> : rupture_kernel<T, n, false>)<<<grid, 128, 0, st>>>(a)
   switch (N) {
-    case 1: rupture_kernel<T, 1><<<grid, 128, 0, st>>>(a); break;
-    case 2: rupture_kernel<T, 2><<<grid, 128, 0, st>>>(a); break;
-    case 3: rupture_kernel<T, 3><<<grid, 128, 0, st>>>(a); break;
-    case 4: rupture_kernel<T, 4><<<grid, 128, 0, st>>>(a); break;
-    case 5: rupture_kernel<T, 5><<<grid, 128, 0, st>>>(a); break;
+    case 1: ADG_RK(1); break;
+    case 2: ADG_RK(2); break;
+    case 3: ADG_RK(3); break;
+    case 4: ADG_RK(4); break;
+    case 5: ADG_RK(5); break;
     default: return (int)cudaErrorInvalidValue;
   }
+#undef ADG_RK
   return (int)cudaGetLastError();
 }
 
