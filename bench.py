@@ -480,6 +480,8 @@ def main():
                     help="hex columns per side (80: the 1.5 M-tet workload; smaller for profiling)")
     ap.add_argument("--only", default=None, choices=["fp64", "fp32", "3xtf32"],
                     help="profiling aid: run one precision of the coupled workload, print no JSON line")
+    ap.add_argument("--degree", type=int, default=N_DEG,
+                    help="profiling aid (with --only): the polynomial degree of that run")
     ap.add_argument("--workload", default="coupled",
                     choices=["coupled", "lts", "rupture", "rupture-lsw", "ensemble", "record", "ocean"],
                     help="coupled: the headline line; lts / rupture / rupture-lsw / ensemble / record / ocean: the "
@@ -534,12 +536,12 @@ def main():
     if args.only:
         # profiling aid: one precision, a short run, no JSON line
         prec = {"fp64": pkg.ADG_FP64, "fp32": pkg.ADG_FP32, "3xtf32": pkg.ADG_3XTF32}[args.only]
-        s = Solver(m.xyz, m.tets, m.face_tag, rho, lam, mu, degree=N_DEG, precision=prec, cfl=0.35,
+        s = Solver(m.xyz, m.tets, m.face_tag, rho, lam, mu, degree=args.degree, precision=prec, cfl=0.35,
                    device=local, stream=stream.cuda_stream, acoustic_ocean=True)
-        s.set_dofs(Q0)
+        s.set_dofs(np.ascontiguousarray(Q0[:, :, :s.B]))  # (the hierarchical basis: a lower degree's leading modes)
         s.advance(args.warmup + args.steps)
         s.sync()
-        print(f"profiling run: {args.only}, {args.warmup + args.steps} steps", flush=True)
+        print(f"profiling run: {args.only}, degree {args.degree}, {args.warmup + args.steps} steps", flush=True)
         return
     for prec, steps, warm in runs:
         s = Solver(m.xyz, m.tets, m.face_tag, rho, lam, mu, degree=N_DEG, precision=prec, cfl=0.35,

@@ -121,9 +121,9 @@ struct LImg : LDeg<N> {
   static constexpr int oK3 = oT + 2 * sT;     // kt[a][m][l], m < 4, l < 10
   static constexpr int oK4 = oK3 + 120;       // kt[a][0][l], l < 4
   static constexpr int floats = ((oK4 + 12 + 3) / 4) * 4;
-  // degree 4: per slot, the tile's dofs rows [row][B] (32 x 4 acoustic rows at most)
+  // degree 4: per slot, two buffers of a tile's dofs rows [row][B] (32 x 4 acoustic rows at most)
   static constexpr int oQ = floats, sQ = kAligned ? 0 : 128 * B;
-  static constexpr int bytes = (floats + 2 * sQ) * 4;
+  static constexpr int bytes = (floats + 2 * 2 * sQ) * 4;
   // A hi at [0, 64), lo at [64, 128), accumulators from 128; volume: A at [0, 2 KV), accumulators after
   static_assert(BP <= 64 && D::NN[0] <= 128 && NT <= 128 && 2 * KV + NV <= 256, "TMEM columns of a slot");
 };
@@ -269,6 +269,7 @@ struct Lane {
   uint32_t tbase, trow, sbase;
   int btrace_mode;    // of the tile's cluster: 0 none, 1 overwrite, 2 accumulate (LTS buffers)
   uint32_t phase;
+  int it;             // tiles this slot has begun (degree 4: the staged-rows buffer of a tile is it % 2)
 };
 
 // One tensor-core round of a slot: both halves' A stores made visible, MMAs
@@ -300,6 +301,7 @@ __device__ __forceinline__ bool pair_round(Lane& L, unsigned int* err, F&& issue
 // loads (a tile's rows are consecutive in memory; an acoustic tile takes rows
 // 0 and 6..8 of each element); tile row (element ei, quantity qi) sits at
 // (ei * M::Q + qi) * B.
+// (asynchronous: cp.async of 4 bytes each, committed by the caller)
 template <class M, int B>
 __device__ __forceinline__ void rows_load(float* sQ, const float* Q, int64_t v0, int nE, int u) {
   const int n = nE * M::Q * B;
@@ -311,7 +313,7 @@ __device__ __forceinline__ void rows_load(float* sQ, const float* Q, int64_t v0,
     } else {
       src = v0 * 9 * B + i;
     }
-    sQ[i] = Q[src];
+    tc::cp_async4(sQ + i, Q + src);
   }
 }
 // ... and back (acoustic: the normal-stress row as sigma_xx, sigma_yy and
@@ -338,8 +340,8 @@ __device__ __forceinline__ void rows_store(const float* sQ, float* Q, int64_t v0
 // tile: index within its segment; t2: this slot's tile after the next among
 // all tiles of the launch (kMulti: the launch has several segments)
 template <int N, class M, int H, bool kBuf, bool kMulti>
-__device__ __forceinline__ bool local_tile(Lane& L, const StepArgs& a, const Segs& g, int64_t t2, int64_t v_begin,
-                                           int64_t n_virtual, int64_t tile) {
+__device__ __forceinline__ bool local_tile(Lane& L, const StepArgs& a, const Segs& g, int64_t t1, int64_t t2,
+                                           int64_t v_begin, int64_t n_virtual, int64_t tile) {
   using D = LDeg<N>;
   using I_ = LImg<N>;
   constexpr int B = I_::B, BF = I_::BF, BP = I_::BP, NCH = I_::NCH, FS = I_::FS, TS = D::TS, NL = D::NL;
@@ -373,10 +375,24 @@ __device__ __forceinline__ bool local_tile(Lane& L, const StepArgs& a, const Seg
   float* sQ = nullptr;   // degree 4: the slot's staged rows
   float* srow = nullptr; // ... and this thread's
   if constexpr (!I_::kAligned) {
-    sQ = reinterpret_cast<float*>(smem_raw) + I_::oQ + L.slot * I_::sQ;
+    // two buffers per slot: this tile's rows were requested during the
+    // previous tile (the first tile's here), the next tile's are requested now
+    float* const sQb = reinterpret_cast<float*>(smem_raw) + I_::oQ + L.slot * 2 * I_::sQ;
+    sQ = sQb + (L.it & 1) * I_::sQ;
     srow = sQ + (i * M::Q + p) * B;
-    pair_bar(L.slot);  // the previous tile's rows have been written back
-    rows_load<M, B>(sQ, Q, v0, nE, L.t + 128 * H);
+    pair_bar(L.slot);  // the previous tile's rows have been written back from the other buffer
+    if (L.it == 0) {
+      rows_load<M, B>(sQ, Q, v0, nE, L.t + 128 * H);
+      tc::cp_async_commit();
+    }
+    if (t1 < g.first[g.n]) {
+      const int i1 = seg_of<kMulti>(g, t1);
+      const int64_t l1 = t1 - g.first[i1], rem1 = g.s[i1].n - l1 * TE;
+      rows_load<M, B>(sQb + ((L.it + 1) & 1) * I_::sQ, Q, g.s[i1].v_begin + l1 * TE, (int)(rem1 < TE ? rem1 : TE),
+                      L.t + 128 * H);
+    }
+    tc::cp_async_commit();
+    tc::cp_async_wait<1>();  // this tile's rows
     pair_bar(L.slot);
   }
   float I[BP];
@@ -672,24 +688,30 @@ __global__ void __launch_bounds__(kThreadsL, 1) local_tc_kernel(StepArgs a, cons
   // `me` of all `slots` takes kChunk consecutive tiles per sweep
   const int64_t ntiles = g.first[g.n];
   const int slots = (int)gridDim.x * 2, me = (int)blockIdx.x * 2 + slot;
-  auto work = [&](int64_t tile, int64_t t2) {
+  auto work = [&](int64_t tile, int64_t t1, int64_t t2) {
     const Seg& sg = g.s[seg_of<kMulti>(g, tile)];
 #pragma unroll
     for (int k = 0; k <= N; ++k) L.tcf[k] = (float)sg.tcoef[k];
     L.btrace_mode = sg.btrace_mode;
     const int64_t lt = tile - g.first[&sg - g.s];
-    return half == 0 ? local_tile<N, M, 0, kBuf, kMulti>(L, a, g, t2, sg.v_begin, sg.n, lt)
-                     : local_tile<N, M, 1, kBuf, kMulti>(L, a, g, t2, sg.v_begin, sg.n, lt);
+    const bool ok = half == 0 ? local_tile<N, M, 0, kBuf, kMulti>(L, a, g, t1, t2, sg.v_begin, sg.n, lt)
+                              : local_tile<N, M, 1, kBuf, kMulti>(L, a, g, t1, t2, sg.v_begin, sg.n, lt);
+    L.it++;
+    return ok;
   };
+  L.it = 0;
   if constexpr (kChunk == 1) {
     for (int64_t tile = me; tile < ntiles; tile += slots)
-      if (!work(tile, tile + 2 * (int64_t)slots)) break;
+      if (!work(tile, tile + (int64_t)slots, tile + 2 * (int64_t)slots)) break;
   } else {
     for (int it = 0;; ++it) {
       const int64_t tile = slot_tile(it, me, slots, kChunk);
-      if (tile >= ntiles || !work(tile, slot_tile(it + 2, me, slots, kChunk))) break;
+      if (tile >= ntiles ||
+          !work(tile, slot_tile(it + 1, me, slots, kChunk), slot_tile(it + 2, me, slots, kChunk)))
+        break;
     }
   }
+  tc::cp_async_wait<0>();  // (degree 4) no copy into shared memory outlives the loop
   // after a timed-out wait, give this slot's MMAs in flight a bounded chance
   // to finish before the columns are freed
   if (half == 0 && L.t == 0 && s_abort[slot]) tc::mbar_wait(&mbar[slot], L.phase ^ 1u, kWaitIters);

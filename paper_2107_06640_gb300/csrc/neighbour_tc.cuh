@@ -530,8 +530,10 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
         q[8 * cj + 4] = x1.x; q[8 * cj + 5] = x1.y; q[8 * cj + 6] = x1.z; q[8 * cj + 7] = x1.w;
       }
     } else {
+      // (one cp.async group, the youngest: waited for before the update)
       const float* Qt = reinterpret_cast<const float*>(a.Q) + v0 * 9 * B;
-      for (int r = u; r < nE * 9 * B; r += 256) sQ[r] = Qt[r];
+      for (int r = u; r < nE * 9 * B; r += 256) tc::cp_async4(sQ + r, Qt + r);
+      cp_commit();
     }
     // ---- the tile after the next into L2
     const int64_t next2 = slot_tile(it + 2, me, slots, kChunk);
@@ -548,7 +550,12 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
     // meanwhile threads 64..111 form the next tile's face coefficients (its
     // records and parameters came with its face 0, the older of the two groups
     // in flight)
-    if (next < ntiles) cp_wait<1>();
+    if (next < ntiles) {
+      if constexpr (NI::kAligned)
+        cp_wait<1>();
+      else
+        cp_wait<2>();  // the staged dofs rows are younger
+    }
     asm volatile("tcgen05.wait::st.sync.aligned;");
     tc::fence_before();
     slot_bar(slot);
@@ -568,6 +575,7 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
         s_abort[slot] = 1;
       }
     }
+    if constexpr (!NI::kAligned) cp_wait<0>();  // the tile's staged dofs rows
     slot_bar(slot);
     if (s_abort[slot]) break;
     tc::mbar_wait(&mbar[slot], phase, 1 << 20);

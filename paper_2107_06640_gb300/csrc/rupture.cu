@@ -254,28 +254,28 @@ __global__ void __launch_bounds__(128) rupture_kernel(DRArgs a) {
     const bool solve = (Th > 0) && (S > 0) && !lsw;
     bool learned = false;
     // the features only where the network runs or a training sample is
-    // captured, in FP32 (they only seed Newton; the solve itself stays FP64)
+    // captured, in FP64: the start moves the warm start by the change of the
+    // prediction between time points, which rounding noise in the features
+    // would swamp
     if (kNet && solve && ((a.mlp && busy) || a.capture)) {
-      const float Sa = (float)(S * p.a), Thf = (float)Th, etaf = (float)eta;
-      const float lc = (float)(psi / p.a) - logf(2.f * (float)p.V0);
-      const float xhi = logf(Thf / etaf);
-      const float r = fminf(Thf / Sa, 700.f);
-      const float xwc = fminf(fmaxf((float)xw, (float)kXFloor), xhi);
-      const float xaf = fminf(fmaxf(r - lc - 0.6931472f, (float)kXFloor), xhi);
-      xa = (double)xaf;
-      feat[0] = r;
-      feat[1] = lc;
-      feat[2] = xhi;
-      feat[3] = xwc;
-      feat[4] = fminf(fmaxf(logf(etaf / Sa), -50.f), 50.f);
-      feat[5] = xaf;
+      const double lc = psi / p.a - log(2.0 * p.V0);
+      const double xhi = log(Th / eta);
+      const double r = fmin(Th / (S * p.a), 700.0);
+      const double xwc = fmin(fmax(xw, kXFloor), xhi);
+      xa = fmin(fmax(r - lc - 0.6931471805599453, kXFloor), xhi);
+      feat[0] = (float)r;
+      feat[1] = (float)lc;
+      feat[2] = (float)xhi;
+      feat[3] = (float)xwc;
+      feat[4] = (float)fmin(fmax(log(eta / (S * p.a)), -50.0), 50.0);
+      feat[5] = (float)xa;
       if (a.mlp && busy) {
         // predicted ln V* = x_a + network; when it was also evaluated at the
         // previous time point, the start is the warm start moved by the change
         // of that prediction
         const double xhat = xa + (double)mlp_eval(sW, feat);
         if (have_prev) {
-          x0 = fmin(fmax((double)xwc + (xhat - xhat_prev), kXFloor), (double)xhi);
+          x0 = fmin(fmax(xwc + (xhat - xhat_prev), kXFloor), xhi);
           learned = true;
         }
         xhat_prev = xhat;

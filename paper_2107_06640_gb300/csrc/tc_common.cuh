@@ -110,6 +110,15 @@ __device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
   }
 }
 
+// asynchronous 4-byte copy global -> shared (cp.async; committed and waited
+// for with cp.async.commit_group / cp.async.wait_group)
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int NPEND>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(NPEND) : "memory"); }
+
 // the same for any span: only its 16-byte aligned interior (a hint; the
 // bytes at either end that share a 16-byte unit with the span's neighbours
 // are left out)
