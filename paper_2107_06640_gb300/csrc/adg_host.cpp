@@ -458,20 +458,30 @@ void Ctx::setup() {
   // finer neighbour come first (those with a coarser neighbour, which the
   // tensor-core kernels handle at some extra cost, at the end of that range,
   // so that they fill few tiles)
+  // (special: 1 a coarser neighbour, 3 one gravitational face (both on the
+  // tensor-core kernels), 2 the CUDA-core kernels: a fault face, a finer
+  // neighbour or more than one gravitational face)
   std::vector<char> special(E, 0);
   if (tc)
-    for (int64_t e = 0; e < E; ++e)
+    for (int64_t e = 0; e < E; ++e) {
+      int ng_e = 0;
+      bool cc = false, coarser = false;
       for (int f = 0; f < 4; ++f) {
         const int tg = tag[4 * e + f];
         const int64_t e2 = nbr_u[4 * e + f];
-        if (tg == ADG_TAG_GRAVITY || tg == ADG_TAG_FAULT || (e2 >= 0 && cl[e2] < cl[e])) special[e] = 2;
-        else if (e2 >= 0 && cl[e2] > cl[e] && special[e] == 0) special[e] = 1;
+        ng_e += tg == ADG_TAG_GRAVITY;
+        cc = cc || tg == ADG_TAG_FAULT || (e2 >= 0 && cl[e2] < cl[e]);
+        coarser = coarser || (e2 >= 0 && cl[e2] > cl[e]);
       }
+      special[e] = (cc || ng_e > 1) ? 2 : (ng_e == 1 ? 3 : (coarser ? 1 : 0));
+    }
   // order key within a cluster: 0 plain elastic, 1 plain fluid on the
-  // acoustic local kernel, 2 with a coarser neighbour, 3 the CUDA-core rest
+  // acoustic local kernel, 2 with a coarser neighbour, 3 with a gravitational
+  // face (all four on the tensor-core kernels), 4 the CUDA-core rest
   std::vector<char> key(E, 0);
   for (int64_t e = 0; e < E; ++e)
-    key[e] = special[e] ? (char)(special[e] + 1) : (char)(tc && acoustic && mu[e] == 0.0 ? 1 : 0);
+    key[e] = special[e] == 1 ? 2 : special[e] == 3 ? 3 : special[e] == 2 ? 4
+                                 : (char)(tc && acoustic && mu[e] == 0.0 ? 1 : 0);
   order.resize(E);
   for (int64_t e = 0; e < E; ++e) order[e] = e;
   std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) {
@@ -483,13 +493,15 @@ void Ctx::setup() {
   cl_plain.assign(ncl, 0);
   cl_elastic.assign(ncl, 0);
   cl_fluid.assign(ncl, 0);
+  cl_grav.assign(ncl, 0);
   cl_tc_coarse.assign(ncl, 0);
   for (int64_t i = 0; i < E; ++i) {
     const int k = key[order[i]], c = cl[order[i]];
     cl_begin[c + 1]++;
-    if (tc && k < 3) cl_plain[c]++;
+    if (tc && k < 4) cl_plain[c]++;
     if (tc && k == 0) cl_elastic[c]++;
     if (tc && k == 1) cl_fluid[c]++;
+    if (tc && k == 3) cl_grav[c]++;
     if (tc && k == 2) cl_tc_coarse[c] = 1;
   }
   for (int c = 0; c < ncl; ++c) cl_begin[c + 1] += cl_begin[c];
@@ -558,6 +570,11 @@ void Ctx::setup() {
         if (kind == NK_FINE) dslot[i * 4 + f] = 1;
         ninfo[i * 4 + f] = nface_u[4 * eu + f] | (nperm_u[4 * eu + f] << 2) | (kind << 5);
       } else if (tg == ADG_TAG_GRAVITY) {
+        if (rec) {
+          const int g = gslot[i * 4 + f];
+          rec[5] = (float)FACE_GRAVITY;
+          std::memcpy(&rec[6], &g, sizeof(int));
+        }
         middle_state(Zpm, Zpm, Zsm, Zsm, Mm, Mp);
         // time-integrated middle state: w1 = -rho g H, w7 = eta^{n+1}-eta^n, w4 = w6 = 0,
         // w8/w9 = w8/w9 - w4/w6 / Z_s (solid) ; Fg applies the shear part to int q^-
@@ -604,12 +621,16 @@ void Ctx::setup() {
   if (tc)
     for (int c = 0; c < ncl; ++c)
       for (int64_t i = cl_begin[c]; i < cl_begin[c] + cl_plain[c]; ++i) {
+        // (the last cl_grav[c] of them have exactly one gravitational face)
+        const bool grav = i >= cl_begin[c] + cl_plain[c] - cl_grav[c];
         bool ok = true;
+        int ngf = 0;
         for (int f = 0; f < 4; ++f) {
           const int kind = (ninfo[i * 4 + f] >> 5) & 7;
-          ok = ok && gslot[i * 4 + f] < 0 && dslot[i * 4 + f] < 0 &&
-               (kind == NK_SAME || kind == NK_NONE || kind == NK_COARSE);
+          ngf += gslot[i * 4 + f] >= 0;
+          ok = ok && dslot[i * 4 + f] < 0 && (kind == NK_SAME || kind == NK_NONE || kind == NK_COARSE);
         }
+        ok = ok && ngf == (grav ? 1 : 0);
         if (!ok) throw Err(ADG_E_STATE, "internal: element order for the tensor-core kernels is inconsistent");
       }
   // ---- fault faces: one entry per tet pair, minus side = lower user tet index,
@@ -706,6 +727,10 @@ void Ctx::setup() {
     pack_lift_tc(N, ops.lift.data(), tf.data());
     dTcLift = upload_raw<float>(tf, owned, dev_bytes);
     dFrec = upload_raw<float>(frec, owned, dev_bytes);
+    int64_t ngrav = 0;
+    for (int c = 0; c < ncl; ++c) ngrav += cl_grav[c];
+    if (ngrav > 0)
+      dGscr = (float*)dalloc((size_t)n_gslots * S * gscr_floats(N) * sizeof(float), owned, dev_bytes);
   }
   dErr = (unsigned int*)dalloc(sizeof(unsigned int), owned, dev_bytes);
   if (acoustic) {
@@ -746,7 +771,7 @@ StepArgs Ctx::base_args() const {
   a.ktT = dKt; a.kvolT = dKvol; a.efcT = dEfc; a.liftT = dLift; a.perm = dPerm; a.gpar = dGpar;
   a.S = S; a.err = dErr;
   a.fslot = dFslot; a.drout = dDrout; a.gflux = dGflux; a.tc_local = dTcLocal; a.tc_lift = dTcLift;
-  a.frec = dFrec;
+  a.frec = dFrec; a.gscr = dGscr;
   return a;
 }
 
@@ -771,8 +796,8 @@ void Ctx::launch_tick(int s, double dtm) {
   StepArgs a = base_args();
   for (int phase = 0; phase < 2; ++phase) {
     // per kernel kind the clusters' segments: tensor-core elastic, tensor-core
-    // acoustic (local phase only), CUDA-core
-    std::vector<Seg> tcs, fls, ccs;
+    // acoustic and gravitational-face (local phase only), CUDA-core
+    std::vector<Seg> tcs, fls, grs, ccs;
     bool coarse = false;
     for (int c = 0; c < ncl; ++c) {
       const bool active = phase == 0 ? s % (1 << c) == 0 : (s + 1) % (1 << c) == 0;
@@ -799,19 +824,25 @@ void Ctx::launch_tick(int s, double dtm) {
       const int64_t np = tc ? cl_plain[c] : 0;
       if (np > 0) {
         coarse = coarse || cl_tc_coarse[c] != 0;
-        const int64_t n0 = cl_elastic[c], n1 = cl_fluid[c];
-        if (phase == 0 && n1 > 0) {
-          // elastic elements around the acoustic range, which takes its own kernel
-          if (n0 > 0) tcs.push_back(seg(cl_begin[c], n0));
-          fls.push_back(seg(cl_begin[c] + n0, n1));
-          if (np > n0 + n1) tcs.push_back(seg(cl_begin[c] + n0 + n1, np - n0 - n1));
+        const int64_t n0 = cl_elastic[c], n1 = cl_fluid[c], ng_c = cl_grav[c];
+        if (phase == 0) {
+          // elastic elements around the acoustic range, then the gravitational-face
+          // range; the last two take their own kernels
+          if (n1 > 0) {
+            if (n0 > 0) tcs.push_back(seg(cl_begin[c], n0));
+            fls.push_back(seg(cl_begin[c] + n0, n1));
+            if (np - ng_c > n0 + n1) tcs.push_back(seg(cl_begin[c] + n0 + n1, np - ng_c - n0 - n1));
+          } else if (np > ng_c) {
+            tcs.push_back(seg(cl_begin[c], np - ng_c));
+          }
+          if (ng_c > 0) grs.push_back(seg(cl_begin[c] + np - ng_c, ng_c));
         } else {
           tcs.push_back(seg(cl_begin[c], np));
         }
       }
       if (n > np) ccs.push_back(seg(cl_begin[c] + np, n - np));
     }
-    if (tcs.empty() && fls.empty() && ccs.empty()) continue;
+    if (tcs.empty() && fls.empty() && grs.empty() && ccs.empty()) continue;
     ProfEv ev{phase, nullptr, nullptr, 0};
     if (prof) {
       CK(cudaEventCreate(&ev.a));
@@ -832,7 +863,9 @@ void Ctx::launch_tick(int s, double dtm) {
                         : launch_neighbour_tc(N, a, g, n_sms, stream, coarse);
     });
     launch(fls, kTileElemsFluid, [&](const Segs& g) { return launch_local_tc(N, a, g, n_sms, stream, false, true); });
-    if (prof && (!tcs.empty() || !fls.empty())) {  // the tensor-core launches alone
+    launch(grs, kTileElems,
+           [&](const Segs& g) { return launch_local_tc(N, a, g, n_sms, stream, coarse, false, true); });
+    if (prof && (!tcs.empty() || !fls.empty() || !grs.empty())) {  // the tensor-core launches alone
       CK(cudaEventCreate(&ev.m));
       CK(cudaEventRecord(ev.m, stream));
     }
@@ -883,17 +916,19 @@ int64_t Ctx::launches_per_macro() const {
   const int ticks = 1 << (ncl - 1);
   for (int s = 0; s < ticks; ++s)
     for (int phase = 0; phase < 2; ++phase) {
-      bool tcl = false, fll = false, ccl = false;
+      bool tcl = false, fll = false, grl = false, ccl = false;
       for (int c = 0; c < ncl; ++c) {
         const int64_t n = cl_begin[c + 1] - cl_begin[c];
         if (!n || (phase == 0 ? s % (1 << c) : (s + 1) % (1 << c))) continue;
         if (phase == 1 && fcl_begin[c + 1] > fcl_begin[c]) L += 1;  // friction solve per cluster
-        const int64_t np = tc ? cl_plain[c] : 0, nf = (tc && phase == 0) ? cl_fluid[c] : 0;
-        tcl = tcl || np > nf;
+        const int64_t np = tc ? cl_plain[c] : 0, nf = (tc && phase == 0) ? cl_fluid[c] : 0,
+                      ngr = (tc && phase == 0) ? cl_grav[c] : 0;
+        tcl = tcl || np > nf + ngr;
         fll = fll || nf > 0;
+        grl = grl || ngr > 0;
         ccl = ccl || n > np;
       }
-      L += tcl + fll + ccl;
+      L += tcl + fll + grl + ccl;
     }
   return L;
 }

@@ -84,6 +84,10 @@ struct Ctx {
   // 4-quantity local kernel; the library keeps fluid stress isotropic
   bool acoustic = false;
   std::vector<int64_t> cl_elastic, cl_fluid;
+  // the last cl_grav[c] elements of cluster c's tensor-core range have one
+  // gravitational face (their own local launch; dGscr: its scratch)
+  std::vector<int64_t> cl_grav;
+  float* dGscr = nullptr;
   int64_t* dFluid = nullptr;  // library indices of all fluid elements (projection at upload)
   int64_t n_fluid = 0;
   void project_fluid();       // fluid stress -> its isotropic part, on the device

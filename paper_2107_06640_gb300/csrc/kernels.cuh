@@ -65,14 +65,24 @@ struct StepArgs {
   const float* tc_local; // tensor-core operands of the local kernel (hi/lo, canonical layout), degree 5 or 4
   const float* tc_lift;  // tensor-core lift operand of the neighbour kernel (hi/lo, canonical layout), degree 5 or 4
   const float* frec;     // [E][4][FREC] face records of the tensor-core neighbour kernel (FP32 dofs)
+  float* gscr;           // [ngslot*S][gscr_floats(N)] scratch of the tensor-core local kernel's gravity faces
 };
+// Per gravity slot and scenario, the tensor-core local kernel's scratch: the
+// normal-projected derivative rows g_m[l] = sum_p w_p D^m[p][l] (m = 0..N,
+// l < B(N - m); w: v_n - sigma_nn / Z), then the own-trace flux part
+// sum_p Fg[q][p] V[p][n] (q < 9, n < Bf).
+__host__ __device__ constexpr int gscr_off(int n, int m) { return m <= 0 ? 0 : gscr_off(n, m - 1) + nb3(n - m + 1); }
+__host__ __device__ constexpr int gscr_floats(int n) { return gscr_off(n, n + 1) + 9 * nb2(n); }
 
 // Face record of the tensor-core neighbour kernel (floats): the outward unit
 // normal n[3], the plus side's impedances Zp+, Zs+ (interior and periodic
 // faces), the face code (FACE_* below), two zeros.  The kernel forms the
 // Godunov flux of Sec. 4.2 from it and the element's own material.
 constexpr int FREC = 8;
-enum { FACE_NEIGHBOUR = 0, FACE_FREE = 1, FACE_RIGID = 2, FACE_ABSORB = 3 };
+// (FACE_GRAVITY: a gravitational free surface; the record's seventh float
+// holds the bits of its gravity slot, and the kernel lifts the flux the local
+// kernel stored for it)
+enum { FACE_NEIGHBOUR = 0, FACE_FREE = 1, FACE_RIGID = 2, FACE_ABSORB = 3, FACE_GRAVITY = 4 };
 
 // The clusters of one LTS phase (Sec. 4.4) in a single launch: segment i
 // covers the virtual elements [v_begin, v_begin + n) of one cluster with that
@@ -127,8 +137,11 @@ Segs make_segs(const Seg* s, int n, int unit, int chunk = 1);
 // acoustic: the launch's elements are fluid (mu = 0) without LTS buffer, on the
 // 4-quantity (p, v) instantiation; their stress must be isotropic (-p I)
 // (other degrees: cudaErrorInvalidValue)
+// grav: the launch's elements each have one gravitational face (elastic
+// instantiation; derivative traces of that face and the FP64 (eta, H) update
+// on the element's tile)
 int launch_local_tc(int degree, const StepArgs& a, const Segs& g, int n_sms, void* stream, bool buffers,
-                    bool acoustic = false);
+                    bool acoustic = false, bool grav = false);
 void pack_local_tc(int degree, const double* kt, const double* kvol, const double* efc, float* out);
 int local_tc_floats(int degree);
 // tensor-core (tcgen05, 3xTF32) neighbour kernel, degree 5 or 4, FP32 dofs

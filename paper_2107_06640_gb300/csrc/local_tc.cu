@@ -4,13 +4,14 @@
 
 namespace adg {
 
-int launch_local_tc4(const StepArgs& a, const Segs& g, int n_sms, void* stream, bool buffers, bool acoustic);
+int launch_local_tc4(const StepArgs& a, const Segs& g, int n_sms, void* stream, bool buffers, bool acoustic,
+                     bool grav);
 
 int launch_local_tc(int degree, const StepArgs& a, const Segs& g, int n_sms, void* stream, bool buffers,
-                    bool acoustic) {
-  if (degree == 4) return launch_local_tc4(a, g, n_sms, stream, buffers, acoustic);
+                    bool acoustic, bool grav) {
+  if (degree == 4) return launch_local_tc4(a, g, n_sms, stream, buffers, acoustic, grav);
   if (degree != 5) return (int)cudaErrorInvalidValue;
-  return launch_local_tc_deg<5>(a, g, n_sms, stream, buffers, acoustic);
+  return launch_local_tc_deg<5>(a, g, n_sms, stream, buffers, acoustic, grav);
 }
 
 void pack_local_tc(int degree, const double* kt, const double* kvol, const double* efc, float* out) {

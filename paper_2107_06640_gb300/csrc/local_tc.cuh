@@ -232,9 +232,36 @@ __device__ __forceinline__ float star_apply(const Star& s, float y0, float y1, f
 // mc % 2 == H: Y (3 axes x MP columns at tacc) -> D^{k+1} (M rows),
 // I += ck * D^{k+1}; D^{k+1} goes to the A columns of the next level (TO_A)
 // or to registers dn.
-template <int H, int M, int MP, bool TO_A, int BP>
+// Gravitational free surface (Sec. 4.3) on the tensor-core kernel, for an
+// element with one gravitational face: per thread (row p of its element) the
+// weight w_p of that row in v_n - sigma_nn / Z at the face (normal n, P
+// impedance Z), the element's scratch (null on other rows than p = 0 and on
+// lanes without such an element) and the first lane of its element.
+struct Grav {
+  float w = 0.f;
+  float* dst = nullptr;
+  int base = 0;
+};
+// 1/k and 1/k! for the gravitational face's Taylor series (products, not FP64 divisions)
+__constant__ double kRcp[48] = {0.0, 1.0 / 1, 1.0 / 2, 1.0 / 3, 1.0 / 4, 1.0 / 5, 1.0 / 6, 1.0 / 7, 1.0 / 8,
+                                1.0 / 9, 1.0 / 10, 1.0 / 11, 1.0 / 12, 1.0 / 13, 1.0 / 14, 1.0 / 15, 1.0 / 16,
+                                1.0 / 17, 1.0 / 18, 1.0 / 19, 1.0 / 20, 1.0 / 21, 1.0 / 22, 1.0 / 23, 1.0 / 24,
+                                1.0 / 25, 1.0 / 26, 1.0 / 27, 1.0 / 28, 1.0 / 29, 1.0 / 30, 1.0 / 31, 1.0 / 32,
+                                1.0 / 33, 1.0 / 34, 1.0 / 35, 1.0 / 36, 1.0 / 37, 1.0 / 38, 1.0 / 39, 1.0 / 40,
+                                1.0 / 41, 1.0 / 42, 1.0 / 43, 1.0 / 44, 1.0 / 45, 1.0 / 46, 1.0 / 47};
+__constant__ double kRcpFact[6] = {1.0, 1.0, 1.0 / 2, 1.0 / 6, 1.0 / 24, 1.0 / 120};
+
+// sum over the 9 rows of this lane's element of w_p x_p (every lane of the warp takes part)
+__device__ __forceinline__ float elem_sum9(float v, int base) {
+  float s = 0.f;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) s += __shfl_sync(0xffffffffu, v, (base + k) & 31);
+  return s;
+}
+
+template <int H, int M, int MP, bool TO_A, bool kG, int BP>
 __device__ __forceinline__ void level_epilogue(uint32_t tacc, uint32_t tah, uint32_t tal, const Star& s, float ck,
-                                               float (&I)[BP], float* dn) {
+                                               float (&I)[BP], float* dn, const Grav& gv, int goff) {
 #pragma unroll
   for (int mc = H; mc < MP / 8; mc += 2) {
     float y[24];
@@ -249,6 +276,10 @@ __device__ __forceinline__ void level_epilogue(uint32_t tacc, uint32_t tah, uint
         if (!TO_A) dn[m] = d[j];
       } else {
         d[j] = 0.f;
+      }
+      if constexpr (kG) {  // the gravitational face's projected row of this level
+        const float g = elem_sum9(gv.w * d[j], gv.base);
+        if (gv.dst && m < M) gv.dst[goff + m] = g;
       }
     }
     if (TO_A) tc::st_split8(tah + 8 * mc, tal + 8 * mc, d);
@@ -270,6 +301,7 @@ struct Lane {
   int btrace_mode;    // of the tile's cluster: 0 none, 1 overwrite, 2 accumulate (LTS buffers)
   uint32_t phase;
   int it;             // tiles this slot has begun (degree 4: the staged-rows buffer of a tile is it % 2)
+  double dt;          // the tile's cluster step (gravitational faces)
 };
 
 // One tensor-core round of a slot: both halves' A stores made visible, MMAs
@@ -339,7 +371,8 @@ __device__ __forceinline__ void rows_store(const float* sQ, float* Q, int64_t v0
 // kBuf: some elements of the launch have an LTS buffer (a coarser neighbour)
 // tile: index within its segment; t2: this slot's tile after the next among
 // all tiles of the launch (kMulti: the launch has several segments)
-template <int N, class M, int H, bool kBuf, bool kMulti>
+// kGrav: every element of the launch has one gravitational face (elastic)
+template <int N, class M, int H, bool kBuf, bool kMulti, bool kGrav>
 __device__ __forceinline__ bool local_tile(Lane& L, const StepArgs& a, const Segs& g, int64_t t1, int64_t t2,
                                            int64_t v_begin, int64_t n_virtual, int64_t tile) {
   using D = LDeg<N>;
@@ -361,6 +394,28 @@ __device__ __forceinline__ bool local_tile(Lane& L, const StepArgs& a, const Seg
   else
     star_setup(L.lane, valid, reinterpret_cast<const float*>(a.par) + e * PAR, st);
   const uint32_t trow = L.trow, tbase = L.tbase, sbase = L.sbase;
+  // gravitational face of this row's element
+  Grav gv;
+  int gface = -1, gsl = -1;
+  if constexpr (kGrav) {
+    static_assert(!M::fluid, "gravitational faces take the elastic instantiation");
+    gv.base = 9 * jj;
+    if (valid) {
+#pragma unroll
+      for (int f = 0; f < 4; ++f) {
+        const int gs = a.gslot[e * 4 + f];
+        if (gs >= 0) { gface = f; gsl = gs; }
+      }
+    }
+    if (gsl >= 0) {
+      const double* gp = a.gpar + (int64_t)gsl * GPAR;
+      const float nx = (float)gp[0], ny = (float)gp[1], nz = (float)gp[2], iz = (float)(1.0 / gp[3]);
+      const float w[9] = {-nx * nx * iz, -ny * ny * iz, -nz * nz * iz, -2.f * nx * ny * iz, -2.f * ny * nz * iz,
+                          -2.f * nx * nz * iz, nx, ny, nz};
+      gv.w = w[p];
+      if (p == 0) gv.dst = a.gscr + ((int64_t)gsl * a.S + (v - e * a.S)) * gscr_floats(N);
+    }
+  }
 
   // the tile after the next of this slot into L2 while this one is worked on
   if (H == 0 && L.t == 0) {
@@ -413,6 +468,13 @@ __device__ __forceinline__ bool local_tile(Lane& L, const StepArgs& a, const Seg
     }
 #pragma unroll
     for (int j = 0; j < 8; ++j) I[8 * c + j] = L.tcf[0] * x[j];
+    if constexpr (kGrav) {
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const float gsum = elem_sum9(gv.w * x[j], gv.base);
+        if (gv.dst && 8 * c + j < B) gv.dst[gscr_off(N, 0) + 8 * c + j] = gsum;
+      }
+    }
     tc::st_split8(trow + cAh + 8 * c, trow + cAl + 8 * c, x);
   }
   // ---- predictor levels on the tensor cores: all but the last feed the next
@@ -423,7 +485,8 @@ __device__ __forceinline__ bool local_tile(Lane& L, const StepArgs& a, const Seg
                                          sbase + 4 * (I_::oP0 + I_::sP0), false);
         }))
       return false;
-    level_epilogue<H, D::M[0], D::MP[0], true>(trow + cAcc, trow + cAh, trow + cAl, st, L.tcf[1], I, nullptr);
+    level_epilogue<H, D::M[0], D::MP[0], true, kGrav>(trow + cAcc, trow + cAh, trow + cAl, st, L.tcf[1], I, nullptr,
+                                                      gv, gscr_off(N, 1));
   }
   constexpr int l1 = NL - 2, l2 = NL - 1;
   constexpr int o1 = l1 == 0 ? I_::oP0 : I_::oP1, s1 = l1 == 0 ? I_::sP0 : I_::sP1;
@@ -433,7 +496,8 @@ __device__ __forceinline__ bool local_tile(Lane& L, const StepArgs& a, const Seg
                                          sbase + 4 * (o1 + s1), false);
       }))
     return false;
-  level_epilogue<H, D::M[l1], D::MP[l1], true>(trow + cAcc, trow + cAh, trow + cAl, st, L.tcf[l1 + 1], I, nullptr);
+  level_epilogue<H, D::M[l1], D::MP[l1], true, kGrav>(trow + cAcc, trow + cAh, trow + cAl, st, L.tcf[l1 + 1], I,
+                                                     nullptr, gv, gscr_off(N, l1 + 1));
   if (!pair_round<H>(L, a.err, [&] {
         tc::mma3_ts<D::NN[l2], D::K[l2]>(tbase + cAcc, tbase + cAh, tbase + cAl, sbase + 4 * o2,
                                          sbase + 4 * (o2 + s2), false);
@@ -441,7 +505,8 @@ __device__ __forceinline__ bool local_tile(Lane& L, const StepArgs& a, const Seg
     return false;
   static_assert(D::M[l2] == 10 && D::MP[l2] == 16, "the last tensor-core level leaves 10 rows");
   float dl[16];
-  level_epilogue<H, D::M[l2], D::MP[l2], false>(trow + cAcc, trow + cAh, trow + cAl, st, L.tcf[NL], I, dl);
+  level_epilogue<H, D::M[l2], D::MP[l2], false, kGrav>(trow + cAcc, trow + cAh, trow + cAl, st, L.tcf[NL], I, dl, gv,
+                                                      gscr_off(N, l2 + 1));
   // ---- the last two levels (half 0, with rows 8 and 9 of D^NL from half 1)
   if (H == 1) {
     s_X[L.slot][2 * L.t] = dl[8];
@@ -465,6 +530,10 @@ __device__ __forceinline__ bool local_tile(Lane& L, const StepArgs& a, const Seg
       }
       d4[m] = star_apply(st, y0, y1, y2);
       I[m] += L.tcf[NL + 1] * d4[m];
+      if constexpr (kGrav) {
+        const float gsum = elem_sum9(gv.w * d4[m], gv.base);
+        if (gv.dst) gv.dst[gscr_off(N, NL + 1) + m] = gsum;
+      }
     }
     float y0 = 0.f, y1 = 0.f, y2 = 0.f;
 #pragma unroll
@@ -473,7 +542,12 @@ __device__ __forceinline__ bool local_tile(Lane& L, const StepArgs& a, const Seg
       y1 += k4[1 * 4 + l] * d4[l];
       y2 += k4[2 * 4 + l] * d4[l];
     }
-    I[0] += L.tcf[NL + 2] * star_apply(st, y0, y1, y2);
+    const float d5 = star_apply(st, y0, y1, y2);
+    I[0] += L.tcf[NL + 2] * d5;
+    if constexpr (kGrav) {
+      const float gsum = elem_sum9(gv.w * d5, gv.base);
+      if (gv.dst) gv.dst[gscr_off(N, NL + 2)] = gsum;
+    }
   }
 
   // ---- face traces: T = I E^T (N = 4 x BF)
@@ -581,6 +655,90 @@ __device__ __forceinline__ bool local_tile(Lane& L, const StepArgs& a, const Seg
                            sTf + ej * TS, FS * 4);
           tc::bulk_commit();
         }
+        if constexpr (kGrav) {
+          // the own-trace part of the gravitational face's flux, sum_p Fg[q][p] V[p][n],
+          // from this face's staged block, for the warp pair's elements whose gravitational face is f
+          int gfe[M::EW], gse[M::EW];
+#pragma unroll
+          for (int ej = 0; ej < M::EW; ++ej) {
+            gfe[ej] = __shfl_sync(0xffffffffu, gface, 9 * ej);
+            gse[ej] = __shfl_sync(0xffffffffu, gsl, 9 * ej);
+          }
+          for (int k = L.lane + 32 * H; k < nmine * 9 * BF; k += 64) {
+            const int ej = k / (9 * BF), r = k - ej * 9 * BF, q = r / BF, n = r - q * BF;
+            int gf = -1, gs = -1;
+#pragma unroll
+            for (int jx = 0; jx < M::EW; ++jx)
+              if (jx == ej) { gf = gfe[jx]; gs = gse[jx]; }
+            if (gf != f || gs < 0) continue;
+            const double* Fg = a.gpar + (int64_t)gs * GPAR + 6 + q * 9;
+            float acc = 0.f;
+#pragma unroll
+            for (int pp = 0; pp < 9; ++pp) acc += (float)Fg[pp] * sTf[ej * TS + pp * BF + n];
+            const int64_t ve = v0 + M::EW * L.w + ej;
+            a.gscr[((int64_t)gs * a.S + (ve - (ve / a.S) * a.S)) * gscr_floats(N) + gscr_off(N, N + 1) + q * BF + n] =
+                acc;
+          }
+        }
+      }
+    }
+  }
+
+  // ---- gravitational faces: the face's normal-projected derivative traces
+  // f_m = E g_m, the (eta, H) ODE of Sec. 4.3 in FP64 over the step (its
+  // Taylor series, as in the CUDA-core kernel) and the face's time-integrated
+  // flux; one (element, node) per thread of the slot
+  if constexpr (kGrav) {
+    pair_bar(L.slot);  // the slot's scratch rows are written
+    const int u = L.t + 128 * H;
+    const int ei = u / BF, n = u - (u / BF) * BF;
+    if (u < TE * BF && ei < nE) {
+      const int64_t ve = v0 + ei, ee = ve / a.S;
+      const int sc = (int)(ve - ee * a.S);
+      int gf = -1, gs = -1;
+#pragma unroll
+      for (int f = 0; f < 4; ++f) {
+        const int x = a.gslot[ee * 4 + f];
+        if (x >= 0) { gf = f; gs = x; }
+      }
+      if (gs >= 0) {
+        const float* gsrc = a.gscr + ((int64_t)gs * a.S + sc) * gscr_floats(N);
+        const float* img = reinterpret_cast<const float*>(smem_raw);
+        double fm[N + 1];
+#pragma unroll
+        for (int m = 0; m <= N; ++m) {
+          const int Bm = nb3(N - m);
+          float acc = 0.f;
+          for (int l = 0; l < Bm; ++l) {
+            const int o = tc::canon(gf * BF + n, l, I_::NT);
+            acc += (img[I_::oT + o] + img[I_::oT + I_::sT + o]) * gsrc[gscr_off(N, m) + l];
+          }
+          fm[m] = (double)acc * kRcpFact[m];
+        }
+        const double* gp = a.gpar + (int64_t)gs * GPAR;
+        double* eta = a.eta + ((int64_t)gs * a.S + sc) * BF;
+        const double kappa = gp[4], rg = gp[5], dt = L.dt;
+        const double eta0 = eta[n];
+        double c = eta0, e1 = eta0, Hint = eta0 * dt, pw = 1.0;
+#pragma unroll 1
+        for (int m = 0; m < N + 40; ++m) {
+          double fv = 0.0;
+#pragma unroll
+          for (int k = 0; k <= N; ++k)
+            if (k == m) fv = fm[k];
+          c = (fv - kappa * c) * kRcp[m + 1];
+          pw *= dt;
+          const double term = c * pw;
+          e1 += term;
+          Hint += term * dt * kRcp[m + 2];
+          if (m > N && fabs(term) <= 1e-17 * fabs(e1)) break;
+        }
+        eta[n] = e1;
+        float* gfl = reinterpret_cast<float*>(a.gflux) + ((int64_t)gs * a.S + sc) * 9 * BF;
+#pragma unroll
+        for (int q = 0; q < 9; ++q)
+          gfl[q * BF + n] = (float)(gp[87 + q] * (-rg * Hint) + gp[96 + q] * (e1 - eta0) +
+                                    (double)gsrc[gscr_off(N, N + 1) + q * BF + n]);
       }
     }
   }
@@ -651,7 +809,7 @@ __device__ __forceinline__ bool local_tile(Lane& L, const StepArgs& a, const Seg
 
 // N: degree; M: the medium (Elastic or Acoustic); kChunk: consecutive tiles a
 // slot takes per sweep (a compile-time launch shape)
-template <int N, class M, bool kBuf, bool kMulti, int kChunk>
+template <int N, class M, bool kBuf, bool kMulti, int kChunk, bool kGrav = false>
 __global__ void __launch_bounds__(kThreadsL, 1) local_tc_kernel(StepArgs a, const __grid_constant__ Segs g) {
   float* sm = reinterpret_cast<float*>(smem_raw);
   __shared__ uint32_t tmem_base;
@@ -693,9 +851,10 @@ __global__ void __launch_bounds__(kThreadsL, 1) local_tc_kernel(StepArgs a, cons
 #pragma unroll
     for (int k = 0; k <= N; ++k) L.tcf[k] = (float)sg.tcoef[k];
     L.btrace_mode = sg.btrace_mode;
+    L.dt = sg.dt;
     const int64_t lt = tile - g.first[&sg - g.s];
-    const bool ok = half == 0 ? local_tile<N, M, 0, kBuf, kMulti>(L, a, g, t1, t2, sg.v_begin, sg.n, lt)
-                              : local_tile<N, M, 1, kBuf, kMulti>(L, a, g, t1, t2, sg.v_begin, sg.n, lt);
+    const bool ok = half == 0 ? local_tile<N, M, 0, kBuf, kMulti, kGrav>(L, a, g, t1, t2, sg.v_begin, sg.n, lt)
+                              : local_tile<N, M, 1, kBuf, kMulti, kGrav>(L, a, g, t1, t2, sg.v_begin, sg.n, lt);
     L.it++;
     return ok;
   };
@@ -726,7 +885,8 @@ __global__ void __launch_bounds__(kThreadsL, 1) local_tc_kernel(StepArgs a, cons
 
 // The launcher of degree N (the kernel table of that degree's translation unit).
 template <int N>
-int launch_local_tc_deg(const StepArgs& a, const Segs& g, int n_sms, void* stream, bool buffers, bool acoustic) {
+int launch_local_tc_deg(const StepArgs& a, const Segs& g, int n_sms, void* stream, bool buffers, bool acoustic,
+                        bool grav) {
   using K = void (*)(StepArgs, Segs);
   // elastic [kBuf][kMulti][chunk 1, 2, 4]; acoustic [kMulti][chunk] (its elements have no LTS buffer)
   static const K kern[2][2][3] = {
@@ -743,10 +903,13 @@ int launch_local_tc_deg(const StepArgs& a, const Segs& g, int n_sms, void* strea
        local_tc_kernel<N, Acoustic, false, false, 4>},
       {local_tc_kernel<N, Acoustic, false, true, 1>, local_tc_kernel<N, Acoustic, false, true, 2>,
        local_tc_kernel<N, Acoustic, false, true, 4>}};
+  // gravitational-face elements: [kMulti], one tile per sweep, LTS buffers allowed
+  static const K kgr[2] = {local_tc_kernel<N, Elastic, true, false, 1, true>,
+                           local_tc_kernel<N, Elastic, true, true, 1, true>};
   const int rc = configure_on_device((const void*)kern[0][0][0], [] {
     cudaError_t ce = cudaSuccess;
-    for (int i = 0; i < 18; ++i) {
-      const K k = i < 12 ? kern[i / 6][(i / 3) % 2][i % 3] : kfl[(i - 12) / 3][(i - 12) % 3];
+    for (int i = 0; i < 20; ++i) {
+      const K k = i < 12 ? kern[i / 6][(i / 3) % 2][i % 3] : i < 18 ? kfl[(i - 12) / 3][(i - 12) % 3] : kgr[i - 18];
       if (ce == cudaSuccess)
         ce = cudaFuncSetAttribute((const void*)k, cudaFuncAttributeMaxDynamicSharedMemorySize, LImg<N>::bytes);
     }
@@ -755,11 +918,12 @@ int launch_local_tc_deg(const StepArgs& a, const Segs& g, int n_sms, void* strea
   if (rc) return rc;
   const int64_t ntiles = g.n ? g.first[g.n] : 0;
   if (ntiles <= 0) return 0;
-  if (acoustic && buffers) return (int)cudaErrorInvalidValue;
+  if (acoustic && (buffers || grav)) return (int)cudaErrorInvalidValue;
   const int ci = g.chunk >= 4 ? 2 : (g.chunk >= 2 ? 1 : 0);
   const int64_t want = (ntiles + 1) / 2;
   const unsigned grid = (unsigned)(want < n_sms ? want : n_sms);
-  const K k = acoustic ? kfl[g.n > 1 ? 1 : 0][ci] : kern[buffers ? 1 : 0][g.n > 1 ? 1 : 0][ci];
+  const K k = grav ? kgr[g.n > 1 ? 1 : 0]
+                   : acoustic ? kfl[g.n > 1 ? 1 : 0][ci] : kern[buffers ? 1 : 0][g.n > 1 ? 1 : 0][ci];
   k<<<grid, kThreadsL, LImg<N>::bytes, (cudaStream_t)stream>>>(a, g);
   return (int)cudaGetLastError();
 }

@@ -220,6 +220,9 @@ __device__ __forceinline__ void face_coefficients(int f, int el, int ne, const f
                        -(lam + 2.f * mu) * sf, -lam * sf, -mu * sf, -sf / rho};
 #pragma unroll
   for (int i = 0; i < 29; ++i) co[i] = v[i];
+  // a gravitational face lifts the flux the local kernel stored: its slot and s_f
+  co[29] = code == FACE_GRAVITY ? rec[6] : __int_as_float(-1);
+  co[30] = sf;
 }
 
 // Scaled Godunov flux of one face node: qm, qp the minus and plus traces
@@ -484,7 +487,18 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
             qn[qq] = sVn[ei * kSS + qq * BF + pn];
           }
           float g[9];
-          face_flux(sCo(par) + (f * TE + el) * kCoef, qo, qn, g);
+          const float* cof = sCo(par) + (f * TE + el) * kCoef;
+          const int gs = __float_as_int(cof[29]);
+          if (gs >= 0) {
+            // gravitational face: s_f times the time-integrated flux of the local kernel
+            const int sc = kOne ? 0 : (r0 + ei) % S;
+            const float* src = reinterpret_cast<const float*>(a.gflux) + ((int64_t)gs * S + sc) * 9 * BF + n;
+            const float sf = cof[30];
+#pragma unroll
+            for (int pp = 0; pp < 9; ++pp) g[pp] = sf * src[pp * BF];
+          } else {
+            face_flux(cof, qo, qn, g);
+          }
 #pragma unroll
           for (int pp = 0; pp < 9; ++pp) gout[pp * kGrow] = g[pp];
         } else {

@@ -59,15 +59,17 @@ def test_acoustic_local_kernel_matches_the_oracle_3xtf32(N):
     """Ocean (two water layers) over crust, gravitational top, absorbing
     sides: the second water layer's 54 elements take the 4-quantity kernel
     (two tiles of 32, the second ragged), the crust the elastic one, the
-    sea-surface layer the CUDA-core kernel; three steps."""
+    sea-surface layer the elastic one with its gravitational-face path;
+    three steps."""
     from paper_2107_06640_gb300 import _lib
     m, mat = small_coupled()
     o, s, eq, ee = _run(m, mat, N, 2)
     assert eq <= 2e-5 and ee <= 1e-6, (eq, ee)
     _, launches = _lib.adg_profile(s.ctx, 1)
-    assert launches[0] == 3  # local phase: elastic and acoustic tensor-core launches, CUDA-core rest
-    plain = int(np.sum(~np.any(m.face_tag == syn.TAG_GRAVITY, axis=1)))
-    assert int(s.info.tensor_core_updates_per_macro) == plain
+    assert launches[0] == 3  # local phase: elastic, acoustic and gravitational-face tensor-core launches
+    assert int(s.info.tensor_core_updates_per_macro) == m.nt
+    fluid_plain = int(np.sum((mat[2] == 0) & ~np.any(m.face_tag == syn.TAG_GRAVITY, axis=1)))
+    assert int(s.info.acoustic_updates_per_macro) == fluid_plain
 
 
 @pytest.mark.parametrize("N", [5, 4])

@@ -109,17 +109,22 @@ def test_periodic_cube_tensor_core_local_kernel(N):
 
 
 @pytest.mark.parametrize("N", [5, 4])
-def test_coupled_box_uses_both_kernel_forms_3xtf32(N):
+def test_coupled_box_gravity_elements_on_the_tensor_cores(N):
+    """Ocean over crust with a gravitational top: every element takes the
+    tensor-core kernels, those with a sea-surface face on their own local
+    launch (derivative traces of that face and the FP64 (eta, H) update on the
+    tile), which the neighbour kernel's stored-flux path lifts.  Parity
+    against the oracle (dofs and sea surface) is _coupled_run's."""
     m, mat = small_coupled()
     from paper_2107_06640_gb300 import _lib
     s = make_pair(m, mat, N, precision=2, cfl=0.5)[1]
     ms, launches = _lib.adg_profile(s.ctx, 1)
-    # tensor cores for the interior, CUDA cores for the gravity-face layer
-    assert launches[0] == 2 and launches[1] == 2
-    assert launches[3] == 1 and launches[4] == 1
-    assert 0 < ms[3] <= ms[0] and 0 < ms[4] <= ms[1]  # the tensor-core launches timed alone
-    plain = int(np.sum(~np.any(m.face_tag == syn.TAG_GRAVITY, axis=1)))
-    assert int(s.info.tensor_core_updates_per_macro) == plain < m.nt
+    assert launches[0] == 2 and launches[1] == 1   # local: elastic + gravitational-face launches; neighbour: one
+    assert launches[3] == 1 and launches[4] == 1   # (phases with a tensor-core part)
+    assert 0 < ms[3] <= ms[0] and 0 < ms[4] <= ms[1]
+    assert int(s.info.tensor_core_updates_per_macro) == m.nt
+    eq, ee = _coupled_run(N, 2, seed=9)
+    assert eq <= 2e-5 and ee <= 1e-6, (eq, ee)
 
 
 @pytest.mark.parametrize("N", [5, 4])
