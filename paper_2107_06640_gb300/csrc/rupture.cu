@@ -46,32 +46,42 @@ struct FricPar {
   double a, b, L, f0, V0, fw, Vw;
 };
 
-__device__ double f_ss(double V, const FricPar& p) {
-  const double fLV = p.f0 - (p.b - p.a) * log(V / p.V0);
+// (lnV = ln V, l2v0 = ln(2 V0): shared with the caller's other uses)
+__device__ double f_ss(double V, double lnV, double l2v0, const FricPar& p) {
+  const double fLV = p.f0 - (p.b - p.a) * (lnV - (l2v0 - 0.6931471805599453));
   const double r = V / p.Vw;
   const double r2 = r * r, r4 = r2 * r2, r8 = r4 * r4;
-  return p.fw + (fLV - p.fw) / pow(1.0 + r8, 0.125);
+  // (1 + r8 rounds to 1 below 2^-53: the power is then exactly 1)
+  return p.fw + (fLV - p.fw) / (r8 < 1e-17 ? 1.0 : pow(1.0 + r8, 0.125));
 }
 
-__device__ double psi_relax(double psi, double V, double h, const FricPar& p) {
+__device__ double psi_relax(double psi, double V, double h, double l2v0, const FricPar& p) {
   // exact solution of dpsi/dt = -(V/L)(psi - psi_ss(V)) for frozen V over h
   // (V floored at 1e-300: for V -> 0 the state does not change)
   V = fmax(V, 1e-300);
-  const double x = f_ss(V, p) / p.a;
-  const double lsinh = x + log1p(-exp(-2.0 * x)) - 0.6931471805599453;  // ln sinh(x)
-  const double ss = p.a * (log(2.0 * p.V0 / V) + lsinh);
+  const double lnV = log(V);
+  const double x = f_ss(V, lnV, l2v0, p) / p.a;
+  // ln sinh(x) = x + ln(1 - e^{-2x}) - ln 2; above x = 20 the middle term is below
+  // half an ulp of x and the sum is x - ln 2 exactly
+  const double lsinh = (x > 20.0 ? x : x + log1p(-exp(-2.0 * x))) - 0.6931471805599453;
+  const double ss = p.a * ((l2v0 - lnV) + lsinh);
   return ss + (psi - ss) * exp(-V * h / p.L);
 }
 
-// Newton on x = ln V for Theta - eta V - S a asinh(c V) = 0 (decreasing, concave in x)
-__device__ double newton_v(double Th, double S, double eta, double psi, const FricPar& p, double x0,
-                           int* iters, bool* ok) {
+// Newton on x = ln V for Theta - eta V - S a asinh(c V) = 0 (decreasing, concave in x);
+// lc = ln c = psi / a - ln(2 V0) and hi = ln(Theta / eta) (the root's upper
+// bound) come from the caller, which shares them between the two passes and
+// the network's features; *xout = the final x (ln V)
+__device__ double newton_v(double Th, double S, double eta, double lc, double hi, const FricPar& p, double x0,
+                           int* iters, bool* ok, double* xout) {
   *iters = 0;
   *ok = true;
+  *xout = kXFloor;
   if (!(Th > 0)) return 0.0;
-  if (S == 0.0) return Th / eta;
-  const double lc = psi / p.a - log(2.0 * p.V0);
-  const double hi = log(Th / eta);
+  if (S == 0.0) {
+    *xout = hi;
+    return Th / eta;
+  }
   double x = fmin(fmax(x0, kXFloor), hi);
   for (int it = 0; it < kMaxIter; ++it) {
     const double V = exp(x);
@@ -83,11 +93,13 @@ __device__ double newton_v(double Th, double S, double eta, double psi, const Fr
     x = xn;
     if (step <= kTol) {
       *iters = it + 1;
+      *xout = x;
       return exp(x);
     }
   }
   *iters = kMaxIter;
   *ok = false;
+  *xout = x;
   return exp(x);
 }
 
@@ -193,6 +205,7 @@ __global__ void __launch_bounds__(128) rupture_kernel(DRArgs a) {
     for (int i = 0; i < 3; ++i) t0s[i] -= t0n * nrm[i];
   }
   double V = st[0], psi = st[1];
+  const double l2v0 = log(2.0 * p.V0);  // (ln c = psi / a - ln(2 V0))
   double slip[3] = {st[2], st[3], st[4]};
   double tau_tot[3] = {st[5], st[6], st[7]};
   double Gm[9] = {0}, Gp[9] = {0};
@@ -247,6 +260,7 @@ __global__ void __launch_bounds__(128) rupture_kernel(DRArgs a) {
     const double h = t - tprev;
     const double Vold = V;
     const double xw = log(fmax(V, 1e-300));  // warm start: the previous ln|V|
+    const double hi = Th > 0 ? log(Th / eta) : 0.0;  // the root's upper bound ln(Theta / eta)
     double x0 = xw;
     double xa = 0.0;  // asinh asymptote: the base of the network's prediction
     float feat[MLP_IN];
@@ -258,8 +272,8 @@ __global__ void __launch_bounds__(128) rupture_kernel(DRArgs a) {
     // prediction between time points, which rounding noise in the features
     // would swamp
     if (kNet && solve && ((a.mlp && busy) || a.capture)) {
-      const double lc = psi / p.a - log(2.0 * p.V0);
-      const double xhi = log(Th / eta);
+      const double lc = psi / p.a - l2v0;
+      const double xhi = hi;
       const double r = fmin(Th / (S * p.a), 700.0);
       const double xwc = fmin(fmax(xw, kXFloor), xhi);
       xa = fmin(fmax(r - lc - 0.6931471805599453, kXFloor), xhi);
@@ -286,8 +300,8 @@ __global__ void __launch_bounds__(128) rupture_kernel(DRArgs a) {
     } else {
       have_prev = false;
     }
-    double Vcur = exp(x0);
-    if (!(Vcur > 0)) Vcur = 0.0;
+    double Vcur = 0.0;
+    double xs = x0;  // the Newton start (ln V): pass 0 from x0, pass 1 from pass 0's root
     double psi_new = psi;
     if (lsw) {
       // mu_s, mu_d, D_c, C in the slots a, b, L, f0
@@ -303,16 +317,19 @@ __global__ void __launch_bounds__(128) rupture_kernel(DRArgs a) {
       // the start guess only seeds Newton; pass 0 relaxes psi with the previous
       // slip rate, pass 1 with the mid-point of the previous and pass-0 rates
       const double Vmid = pass == 0 ? Vold : 0.5 * (Vold + Vcur);
-      psi_new = psi_relax(psi, Vmid, h, p);
+      psi_new = psi_relax(psi, Vmid, h, l2v0, p);
+      const double lcn = psi_new / p.a - l2v0;
       int it;
       bool ok;
-      Vcur = newton_v(Th, S, eta, psi_new, p, log(fmax(Vcur, 1e-300)), &it, &ok);
+      double xo;
+      Vcur = newton_v(Th, S, eta, lcn, hi, p, xs, &it, &ok, &xo);
       if (pass == 0 && learned && !ok) {
         // fallback: rerun from the warm start
         int it_w;
-        Vcur = newton_v(Th, S, eta, psi_new, p, xw, &it_w, &ok);
+        Vcur = newton_v(Th, S, eta, lcn, hi, p, xw, &it_w, &ok, &xo);
         it += it_w;
       }
+      xs = xo;
       all_ok &= ok;
       if (solve) {
         n_solves++;
@@ -324,7 +341,7 @@ __global__ void __launch_bounds__(128) rupture_kernel(DRArgs a) {
         if ((int64_t)k < a.cap_capacity) {
           float* row = a.capture + k * (MLP_IN + 1);
           for (int i = 0; i < MLP_IN; ++i) row[i] = feat[i];
-          row[MLP_IN] = (float)(log(fmax(Vcur, 1e-300)) - xa);
+          row[MLP_IN] = (float)(xs - xa);
         }
       }
     }
@@ -346,7 +363,7 @@ __global__ void __launch_bounds__(128) rupture_kernel(DRArgs a) {
     ahat(nrm, tb, vc, rhop, lamp, mup, -1.0, a.tw[j], Gp);
     tprev = t;
   }
-  psi = a.law == FRIC_LSW ? psi + V * (a.dt - tprev) : psi_relax(psi, V, a.dt - tprev, p);
+  psi = a.law == FRIC_LSW ? psi + V * (a.dt - tprev) : psi_relax(psi, V, a.dt - tprev, l2v0, p);
   st[0] = V;
   st[1] = psi;
   for (int i = 0; i < 3; ++i) {
