@@ -458,26 +458,29 @@ void Ctx::setup() {
   // finer neighbour come first (those with a coarser neighbour, which the
   // tensor-core kernels handle at some extra cost, at the end of that range,
   // so that they fill few tiles)
-  // (special: 1 a coarser neighbour, 3 one gravitational face (both on the
-  // tensor-core kernels), 2 the CUDA-core kernels: a fault face, a finer
-  // neighbour or more than one gravitational face)
+  // (special: 1 a coarser neighbour, 3 one gravitational face or a finer
+  // neighbour (both on the tensor-core kernels, 3 on their special local
+  // instantiation), 2 the CUDA-core kernels: a fault face or more than one
+  // gravitational face)
   std::vector<char> special(E, 0);
   if (tc)
     for (int64_t e = 0; e < E; ++e) {
       int ng_e = 0;
-      bool cc = false, coarser = false;
+      bool cc = false, coarser = false, finer = false;
       for (int f = 0; f < 4; ++f) {
         const int tg = tag[4 * e + f];
         const int64_t e2 = nbr_u[4 * e + f];
         ng_e += tg == ADG_TAG_GRAVITY;
-        cc = cc || tg == ADG_TAG_FAULT || (e2 >= 0 && cl[e2] < cl[e]);
+        cc = cc || tg == ADG_TAG_FAULT;
         coarser = coarser || (e2 >= 0 && cl[e2] > cl[e]);
+        finer = finer || (e2 >= 0 && cl[e2] < cl[e]);
       }
-      special[e] = (cc || ng_e > 1) ? 2 : (ng_e == 1 ? 3 : (coarser ? 1 : 0));
+      special[e] = (cc || ng_e > 1) ? 2 : ((ng_e == 1 || finer) ? 3 : (coarser ? 1 : 0));
     }
   // order key within a cluster: 0 plain elastic, 1 plain fluid on the
   // acoustic local kernel, 2 with a coarser neighbour, 3 with a gravitational
-  // face (all four on the tensor-core kernels), 4 the CUDA-core rest
+  // face or a finer neighbour (all four on the tensor-core kernels), 4 the
+  // CUDA-core rest
   std::vector<char> key(E, 0);
   for (int64_t e = 0; e < E; ++e)
     key[e] = special[e] == 1 ? 2 : special[e] == 3 ? 3 : special[e] == 2 ? 4
@@ -502,7 +505,7 @@ void Ctx::setup() {
     if (tc && k == 0) cl_elastic[c]++;
     if (tc && k == 1) cl_fluid[c]++;
     if (tc && k == 3) cl_grav[c]++;
-    if (tc && k == 2) cl_tc_coarse[c] = 1;
+    if (tc && (k == 2 || k == 3)) cl_tc_coarse[c] = 1;  // (the neighbour kernel's LTS-face code)
   }
   for (int c = 0; c < ncl; ++c) cl_begin[c + 1] += cl_begin[c];
   cluster.resize(E);
@@ -621,16 +624,18 @@ void Ctx::setup() {
   if (tc)
     for (int c = 0; c < ncl; ++c)
       for (int64_t i = cl_begin[c]; i < cl_begin[c] + cl_plain[c]; ++i) {
-        // (the last cl_grav[c] of them have exactly one gravitational face)
-        const bool grav = i >= cl_begin[c] + cl_plain[c] - cl_grav[c];
+        // (the last cl_grav[c] of them may have one gravitational face and faces
+        // with a finer neighbour)
+        const bool spec = i >= cl_begin[c] + cl_plain[c] - cl_grav[c];
         bool ok = true;
         int ngf = 0;
         for (int f = 0; f < 4; ++f) {
           const int kind = (ninfo[i * 4 + f] >> 5) & 7;
           ngf += gslot[i * 4 + f] >= 0;
-          ok = ok && dslot[i * 4 + f] < 0 && (kind == NK_SAME || kind == NK_NONE || kind == NK_COARSE);
+          ok = ok && (kind == NK_SAME || kind == NK_NONE || kind == NK_COARSE || (spec && kind == NK_FINE)) &&
+               (dslot[i * 4 + f] < 0 || (spec && kind == NK_FINE));
         }
-        ok = ok && ngf == (grav ? 1 : 0);
+        ok = ok && ngf <= (spec ? 1 : 0);
         if (!ok) throw Err(ADG_E_STATE, "internal: element order for the tensor-core kernels is inconsistent");
       }
   // ---- fault faces: one entry per tet pair, minus side = lower user tet index,
@@ -729,7 +734,7 @@ void Ctx::setup() {
     dFrec = upload_raw<float>(frec, owned, dev_bytes);
     int64_t ngrav = 0;
     for (int c = 0; c < ncl; ++c) ngrav += cl_grav[c];
-    if (ngrav > 0)
+    if (ngrav > 0 && n_gslots > 0)
       dGscr = (float*)dalloc((size_t)n_gslots * S * gscr_floats(N) * sizeof(float), owned, dev_bytes);
   }
   dErr = (unsigned int*)dalloc(sizeof(unsigned int), owned, dev_bytes);

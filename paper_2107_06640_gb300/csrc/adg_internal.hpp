@@ -85,7 +85,8 @@ struct Ctx {
   bool acoustic = false;
   std::vector<int64_t> cl_elastic, cl_fluid;
   // the last cl_grav[c] elements of cluster c's tensor-core range have one
-  // gravitational face (their own local launch; dGscr: its scratch)
+  // gravitational face or a finer neighbour (their own local launch; dGscr:
+  // the gravitational faces' scratch)
   std::vector<int64_t> cl_grav;
   float* dGscr = nullptr;
   int64_t* dFluid = nullptr;  // library indices of all fluid elements (projection at upload)

@@ -137,9 +137,9 @@ Segs make_segs(const Seg* s, int n, int unit, int chunk = 1);
 // acoustic: the launch's elements are fluid (mu = 0) without LTS buffer, on the
 // 4-quantity (p, v) instantiation; their stress must be isotropic (-p I)
 // (other degrees: cudaErrorInvalidValue)
-// grav: the launch's elements each have one gravitational face (elastic
-// instantiation; derivative traces of that face and the FP64 (eta, H) update
-// on the element's tile)
+// grav: the launch's elements have one gravitational face or a finer LTS
+// neighbour (elastic instantiation; the face's (eta, H) update in FP64 and
+// the derivative traces of every level on faces with a finer neighbour)
 int launch_local_tc(int degree, const StepArgs& a, const Segs& g, int n_sms, void* stream, bool buffers,
                     bool acoustic = false, bool grav = false);
 void pack_local_tc(int degree, const double* kt, const double* kvol, const double* efc, float* out);

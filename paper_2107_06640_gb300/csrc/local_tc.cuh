@@ -1,8 +1,11 @@
 // Local element kernel on the tensor cores (tcgen05, 3xTF32), degrees 5 and
 // 4, FP32 dofs: Cauchy-Kovalewski predictor, time integral, face traces and
-// volume term of Sec. 4.1 for elements without gravitational faces, fault
-// faces or finer LTS neighbours (those take the CUDA-core kernel); an element
-// with a coarser LTS neighbour also adds its traces to its FP64 LTS buffer.
+// volume term of Sec. 4.1 for elements without fault faces (those take the
+// CUDA-core kernel); an element with a coarser LTS neighbour also adds its
+// traces to its FP64 LTS buffer; elements with one gravitational face or a
+// finer LTS neighbour take a special instantiation that also forms the
+// gravitational face's (eta, H) update and the derivative traces of every
+// level on faces with a finer neighbour.
 //
 // A tile is 12 (virtual) elements x 9 quantities = the 128 rows of the MMAs,
 // one row per TMEM lane: warp w of a warpgroup holds elements 3w..3w+2, the
@@ -371,8 +374,47 @@ __device__ __forceinline__ void rows_store(const float* sQ, float* Q, int64_t v0
 // kBuf: some elements of the launch have an LTS buffer (a coarser neighbour)
 // tile: index within its segment; t2: this slot's tile after the next among
 // all tiles of the launch (kMulti: the launch has several segments)
-// kGrav: every element of the launch has one gravitational face (elastic)
-template <int N, class M, int H, bool kBuf, bool kMulti, bool kGrav>
+// Derivative traces of level m (Sec. 4.4: a finer neighbour integrates this
+// element's Taylor expansion over its sub-steps) on this row's faces with a
+// finer neighbour: one tensor-core round T = D^m E^T with D^m the A operand
+// in TMEM (K = KM), then this half's trace chunks to dtr[f] (null: no finer
+// neighbour on face f; [N+1][9][Bf] per face, this row's quantity already
+// offset).  False after a timed-out wait.
+template <int N, int H, int KM>
+__device__ __forceinline__ bool dtrace_round(Lane& L, const StepArgs& a, float* const (&dtr)[4], int m) {
+  using I_ = LImg<N>;
+  constexpr int BF = I_::BF, NTH = H == 0 ? (I_::NTCH + 1) / 2 : I_::NTCH / 2;
+  if (!pair_round<H>(L, a.err, [&] {
+        tc::mma3_ts<I_::NT, KM>(L.tbase + cAcc, L.tbase + cAh, L.tbase + cAl, L.sbase + 4 * I_::oT,
+                                L.sbase + 4 * (I_::oT + I_::sT), false);
+      }))
+    return false;
+  const uint32_t trow = L.trow;
+  float tv[48];
+  if constexpr (N == 5) {
+    tc::ld3x8(trow + cAcc + 8 * H, trow + cAcc + 8 * (H + 2), trow + cAcc + 8 * (H + 4), tv);
+    tc::ld3x8(trow + cAcc + 8 * (H + 6), trow + cAcc + 8 * (H + 8), trow + cAcc + 8 * (H == 0 ? 10 : 9), tv + 24);
+  } else {
+    tc::ld3x8(trow + cAcc + 8 * H, trow + cAcc + 8 * (H + 2), trow + cAcc + 8 * (H + 4), tv);
+    tc::ld8(trow + cAcc + 8 * (H + 6), tv + 24);
+  }
+#pragma unroll
+  for (int cj = 0; cj < NTH; ++cj) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int col = 8 * (H + 2 * cj) + j;
+      if (col < 4 * BF) {
+        const int f = col / BF, n = col - f * BF;
+        if (dtr[f]) dtr[f][m * 9 * BF + n] = tv[8 * cj + j];
+      }
+    }
+  }
+  return true;
+}
+
+// kSpec: the launch's elements may have one gravitational face and faces with
+// a finer LTS neighbour (elastic instantiation)
+template <int N, class M, int H, bool kBuf, bool kMulti, bool kSpec>
 __device__ __forceinline__ bool local_tile(Lane& L, const StepArgs& a, const Segs& g, int64_t t1, int64_t t2,
                                            int64_t v_begin, int64_t n_virtual, int64_t tile) {
   using D = LDeg<N>;
@@ -397,10 +439,10 @@ __device__ __forceinline__ bool local_tile(Lane& L, const StepArgs& a, const Seg
   // gravitational face of this row's element
   Grav gv;
   int gface = -1, gsl = -1;
-  if constexpr (kGrav) {
+  if constexpr (kSpec) {
     static_assert(!M::fluid, "gravitational faces take the elastic instantiation");
     gv.base = 9 * jj;
-    if (valid) {
+    if (valid && a.gslot) {
 #pragma unroll
       for (int f = 0; f < 4; ++f) {
         const int gs = a.gslot[e * 4 + f];
@@ -414,6 +456,18 @@ __device__ __forceinline__ bool local_tile(Lane& L, const StepArgs& a, const Seg
                           -2.f * nx * nz * iz, nx, ny, nz};
       gv.w = w[p];
       if (p == 0) gv.dst = a.gscr + ((int64_t)gsl * a.S + (v - e * a.S)) * gscr_floats(N);
+    }
+  }
+  // faces with a finer neighbour: this row's derivative traces there
+  float* dtr[4] = {nullptr, nullptr, nullptr, nullptr};
+  if constexpr (kSpec) {
+    if (valid && a.dslot) {
+#pragma unroll
+      for (int f = 0; f < 4; ++f) {
+        const int ds = a.dslot[e * 4 + f];
+        if (ds >= 0)
+          dtr[f] = reinterpret_cast<float*>(a.dtrace) + ((int64_t)ds * a.S + (v - e * a.S)) * (N + 1) * 9 * BF + p * BF;
+      }
     }
   }
 
@@ -468,7 +522,7 @@ __device__ __forceinline__ bool local_tile(Lane& L, const StepArgs& a, const Seg
     }
 #pragma unroll
     for (int j = 0; j < 8; ++j) I[8 * c + j] = L.tcf[0] * x[j];
-    if constexpr (kGrav) {
+    if constexpr (kSpec) {
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
         const float gsum = elem_sum9(gv.w * x[j], gv.base);
@@ -480,24 +534,33 @@ __device__ __forceinline__ bool local_tile(Lane& L, const StepArgs& a, const Seg
   // ---- predictor levels on the tensor cores: all but the last feed the next
   // level's A operand, the last leaves the 10 rows of D^NL in registers
   if constexpr (NL == 3) {
+    if constexpr (kSpec) {
+      if (!dtrace_round<N, H, D::K[0]>(L, a, dtr, 0)) return false;
+    }
     if (!pair_round<H>(L, a.err, [&] {
           tc::mma3_ts<D::NN[0], D::K[0]>(tbase + cAcc, tbase + cAh, tbase + cAl, sbase + 4 * I_::oP0,
                                          sbase + 4 * (I_::oP0 + I_::sP0), false);
         }))
       return false;
-    level_epilogue<H, D::M[0], D::MP[0], true, kGrav>(trow + cAcc, trow + cAh, trow + cAl, st, L.tcf[1], I, nullptr,
+    level_epilogue<H, D::M[0], D::MP[0], true, kSpec>(trow + cAcc, trow + cAh, trow + cAl, st, L.tcf[1], I, nullptr,
                                                       gv, gscr_off(N, 1));
   }
   constexpr int l1 = NL - 2, l2 = NL - 1;
   constexpr int o1 = l1 == 0 ? I_::oP0 : I_::oP1, s1 = l1 == 0 ? I_::sP0 : I_::sP1;
   constexpr int o2 = l2 == 1 ? I_::oP1 : I_::oP2, s2 = l2 == 1 ? I_::sP1 : I_::sP2;
+  if constexpr (kSpec) {
+    if (!dtrace_round<N, H, D::K[l1]>(L, a, dtr, l1)) return false;
+  }
   if (!pair_round<H>(L, a.err, [&] {
         tc::mma3_ts<D::NN[l1], D::K[l1]>(tbase + cAcc, tbase + cAh, tbase + cAl, sbase + 4 * o1,
                                          sbase + 4 * (o1 + s1), false);
       }))
     return false;
-  level_epilogue<H, D::M[l1], D::MP[l1], true, kGrav>(trow + cAcc, trow + cAh, trow + cAl, st, L.tcf[l1 + 1], I,
+  level_epilogue<H, D::M[l1], D::MP[l1], true, kSpec>(trow + cAcc, trow + cAh, trow + cAl, st, L.tcf[l1 + 1], I,
                                                      nullptr, gv, gscr_off(N, l1 + 1));
+  if constexpr (kSpec) {
+    if (!dtrace_round<N, H, D::K[l2]>(L, a, dtr, l2)) return false;
+  }
   if (!pair_round<H>(L, a.err, [&] {
         tc::mma3_ts<D::NN[l2], D::K[l2]>(tbase + cAcc, tbase + cAh, tbase + cAl, sbase + 4 * o2,
                                          sbase + 4 * (o2 + s2), false);
@@ -505,7 +568,7 @@ __device__ __forceinline__ bool local_tile(Lane& L, const StepArgs& a, const Seg
     return false;
   static_assert(D::M[l2] == 10 && D::MP[l2] == 16, "the last tensor-core level leaves 10 rows");
   float dl[16];
-  level_epilogue<H, D::M[l2], D::MP[l2], false, kGrav>(trow + cAcc, trow + cAh, trow + cAl, st, L.tcf[NL], I, dl, gv,
+  level_epilogue<H, D::M[l2], D::MP[l2], false, kSpec>(trow + cAcc, trow + cAh, trow + cAl, st, L.tcf[NL], I, dl, gv,
                                                       gscr_off(N, l2 + 1));
   // ---- the last two levels (half 0, with rows 8 and 9 of D^NL from half 1)
   if (H == 1) {
@@ -530,7 +593,7 @@ __device__ __forceinline__ bool local_tile(Lane& L, const StepArgs& a, const Seg
       }
       d4[m] = star_apply(st, y0, y1, y2);
       I[m] += L.tcf[NL + 1] * d4[m];
-      if constexpr (kGrav) {
+      if constexpr (kSpec) {
         const float gsum = elem_sum9(gv.w * d4[m], gv.base);
         if (gv.dst) gv.dst[gscr_off(N, NL + 1) + m] = gsum;
       }
@@ -544,9 +607,31 @@ __device__ __forceinline__ bool local_tile(Lane& L, const StepArgs& a, const Seg
     }
     const float d5 = star_apply(st, y0, y1, y2);
     I[0] += L.tcf[NL + 2] * d5;
-    if constexpr (kGrav) {
+    if constexpr (kSpec) {
       const float gsum = elem_sum9(gv.w * d5, gv.base);
       if (gv.dst) gv.dst[gscr_off(N, NL + 2)] = gsum;
+      // derivative traces of the last three levels (10, 4 and 1 rows) on the
+      // faces with a finer neighbour, on the CUDA cores (E: hi + lo of the image)
+      const float* img = reinterpret_cast<const float*>(smem_raw);
+#pragma unroll 1
+      for (int f = 0; f < 4; ++f) {
+        if (!dtr[f]) continue;
+#pragma unroll 1
+        for (int n = 0; n < BF; ++n) {
+          float t3 = 0.f, t4 = 0.f;
+#pragma unroll
+          for (int l = 0; l < 10; ++l) {
+            const int o = tc::canon(f * BF + n, l, I_::NT);
+            const float E = img[I_::oT + o] + img[I_::oT + I_::sT + o];
+            t3 += E * dl[l];
+            if (l < 4) t4 += E * d4[l];
+          }
+          const int o0 = tc::canon(f * BF + n, 0, I_::NT);
+          dtr[f][NL * 9 * BF + n] = t3;
+          dtr[f][(NL + 1) * 9 * BF + n] = t4;
+          dtr[f][(NL + 2) * 9 * BF + n] = (img[I_::oT + o0] + img[I_::oT + I_::sT + o0]) * d5;
+        }
+      }
     }
   }
 
@@ -655,7 +740,7 @@ __device__ __forceinline__ bool local_tile(Lane& L, const StepArgs& a, const Seg
                            sTf + ej * TS, FS * 4);
           tc::bulk_commit();
         }
-        if constexpr (kGrav) {
+        if constexpr (kSpec) {
           // the own-trace part of the gravitational face's flux, sum_p Fg[q][p] V[p][n],
           // from this face's staged block, for the warp pair's elements whose gravitational face is f
           int gfe[M::EW], gse[M::EW];
@@ -688,11 +773,11 @@ __device__ __forceinline__ bool local_tile(Lane& L, const StepArgs& a, const Seg
   // f_m = E g_m, the (eta, H) ODE of Sec. 4.3 in FP64 over the step (its
   // Taylor series, as in the CUDA-core kernel) and the face's time-integrated
   // flux; one (element, node) per thread of the slot
-  if constexpr (kGrav) {
+  if constexpr (kSpec) {
     pair_bar(L.slot);  // the slot's scratch rows are written
     const int u = L.t + 128 * H;
     const int ei = u / BF, n = u - (u / BF) * BF;
-    if (u < TE * BF && ei < nE) {
+    if (u < TE * BF && ei < nE && a.gslot) {
       const int64_t ve = v0 + ei, ee = ve / a.S;
       const int sc = (int)(ve - ee * a.S);
       int gf = -1, gs = -1;
@@ -809,7 +894,7 @@ __device__ __forceinline__ bool local_tile(Lane& L, const StepArgs& a, const Seg
 
 // N: degree; M: the medium (Elastic or Acoustic); kChunk: consecutive tiles a
 // slot takes per sweep (a compile-time launch shape)
-template <int N, class M, bool kBuf, bool kMulti, int kChunk, bool kGrav = false>
+template <int N, class M, bool kBuf, bool kMulti, int kChunk, bool kSpec = false>
 __global__ void __launch_bounds__(kThreadsL, 1) local_tc_kernel(StepArgs a, const __grid_constant__ Segs g) {
   float* sm = reinterpret_cast<float*>(smem_raw);
   __shared__ uint32_t tmem_base;
@@ -853,8 +938,8 @@ __global__ void __launch_bounds__(kThreadsL, 1) local_tc_kernel(StepArgs a, cons
     L.btrace_mode = sg.btrace_mode;
     L.dt = sg.dt;
     const int64_t lt = tile - g.first[&sg - g.s];
-    const bool ok = half == 0 ? local_tile<N, M, 0, kBuf, kMulti, kGrav>(L, a, g, t1, t2, sg.v_begin, sg.n, lt)
-                              : local_tile<N, M, 1, kBuf, kMulti, kGrav>(L, a, g, t1, t2, sg.v_begin, sg.n, lt);
+    const bool ok = half == 0 ? local_tile<N, M, 0, kBuf, kMulti, kSpec>(L, a, g, t1, t2, sg.v_begin, sg.n, lt)
+                              : local_tile<N, M, 1, kBuf, kMulti, kSpec>(L, a, g, t1, t2, sg.v_begin, sg.n, lt);
     L.it++;
     return ok;
   };
@@ -903,7 +988,7 @@ int launch_local_tc_deg(const StepArgs& a, const Segs& g, int n_sms, void* strea
        local_tc_kernel<N, Acoustic, false, false, 4>},
       {local_tc_kernel<N, Acoustic, false, true, 1>, local_tc_kernel<N, Acoustic, false, true, 2>,
        local_tc_kernel<N, Acoustic, false, true, 4>}};
-  // gravitational-face elements: [kMulti], one tile per sweep, LTS buffers allowed
+  // elements with a gravitational face or a finer neighbour: [kMulti], one tile per sweep, LTS buffers allowed
   static const K kgr[2] = {local_tc_kernel<N, Elastic, true, false, 1, true>,
                            local_tc_kernel<N, Elastic, true, true, 1, true>};
   const int rc = configure_on_device((const void*)kern[0][0][0], [] {

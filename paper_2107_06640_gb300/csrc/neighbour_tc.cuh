@@ -119,14 +119,17 @@ __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0
 // neighbours' traces of that face, both as stored (one 16-byte aligned face
 // block [quantity][node] per element); the neighbour's node order is applied
 // when the values are read.  nbase: the neighbour's face block in the trace
-// array (>= 0), none (-1), or for a coarser neighbour -2 - the offset of its
+// array (>= 0), none (-1), for a coarser neighbour -2 - the offset of its
 // derivative traces [N+1][9][Bf], integrated here over this element's
 // sub-interval with the coefficients cc (sum_k cc_k D_k, in the order of the
-// CUDA-core kernel).  kCoarse: the launch has such faces.
+// CUDA-core kernel), for a finer neighbour kFineTag - the offset of its FP64
+// LTS buffer [9][Bf] (the integral of its face traces over this element's
+// step).  kCoarse: the launch has such faces (coarser or finer).
+constexpr long long kFineTag = -(1LL << 50);
 template <int N, bool kCoarse>
 __device__ __forceinline__ void stage_face(int f, int u, int64_t v0, int nE, const float* trace,
                                            const long long* nbase, float* so, float* sn, const float* dtrace,
-                                           const float* cc) {
+                                           const float* cc, const double* btrace) {
   using I_ = NImg<N>;
   constexpr int kFS = I_::kFS, kSS = I_::kSS, BF = I_::BF;
   constexpr int kChunks = kFS / 4;  // 16-byte chunks per face block
@@ -139,7 +142,16 @@ __device__ __forceinline__ void stage_face(int f, int u, int64_t v0, int nE, con
       const long long nb = nbase[f * TE + ei];
       const bool okn = ok && nb >= 0;
       cp16(so + ei * kSS + 4 * ch, trace + ((v0 + (ok ? ei : 0)) * 4 + f) * kFS + 4 * ch, ok);
-      if (kCoarse && ok && nb <= -2) {
+      if (kCoarse && ok && nb <= kFineTag) {
+        const double* bt = btrace + (kFineTag - nb);
+        float x[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const int pos = 4 * ch + t;
+          x[t] = pos < 9 * BF ? (float)bt[pos] : 0.f;
+        }
+        *reinterpret_cast<float4*>(sn + ei * kSS + 4 * ch) = make_float4(x[0], x[1], x[2], x[3]);
+      } else if (kCoarse && ok && nb <= -2) {
         const float* dt = dtrace + (-2 - nb);
         float x[4];
 #pragma unroll
@@ -277,7 +289,7 @@ __device__ __forceinline__ void face_flux(const float* cop, const float qm[9], c
 
 // kOne: one scenario (S = 1), where a virtual element is its element and the
 // 64-bit divisions by S drop out; kCoarse: some faces of the launch have a
-// coarser LTS neighbour (without, their code stays out of the kernel)
+// coarser or finer LTS neighbour (without, their code stays out of the kernel)
 // kChunk: consecutive tiles a slot takes per sweep (a compile-time launch shape)
 template <int N, bool kOne, bool kCoarse, bool kMulti, int kChunk>
 __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, const __grid_constant__ Segs g) {
@@ -382,14 +394,17 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
       long long nb = -1;
       int pm = 0;
       const int kind = (info >> 5) & 7;
-      if (ei < pnE && (kind == NK_SAME || (kCoarse && kind == NK_COARSE))) {
+      if (ei < pnE && (kind == NK_SAME || (kCoarse && (kind == NK_COARSE || kind == NK_FINE)))) {
         const int64_t ve = pv0 + ei, ee = elem(ve);
         if (kind == NK_SAME) {
           const int64_t vn_e = (int64_t)nbe * S + (ve - ee * S);
           nb = (vn_e * 4 + (info & 3)) * kFS;
-        } else {
+        } else if (kind == NK_COARSE) {
           const int ds = a.dslot[(int64_t)nbe * 4 + (info & 3)];
           nb = -2 - ((int64_t)ds * S + (ve - ee * S)) * (N + 1) * 9 * BF;
+        } else {
+          const int bs = a.bslot[nbe];
+          nb = kFineTag - (((int64_t)bs * S + (ve - ee * S)) * 4 + (info & 3)) * 9 * BF;
         }
         pm = (info >> 2) & 7;
       }
@@ -412,7 +427,7 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
     tile_at(tl, pv0, prem, kCoarse ? cc : nullptr);
     const int pnE = (int)(prem < TE ? prem : TE);
     float* buf = stage_buf(4 * itl + f);
-    stage_face<N, kCoarse>(f, u, pv0, pnE, trace, sNb(itl & 1), buf, buf + kStage, dtrace, cc);
+    stage_face<N, kCoarse>(f, u, pv0, pnE, trace, sNb(itl & 1), buf, buf + kStage, dtrace, cc, a.btrace);
     cp_commit();
   };
 
