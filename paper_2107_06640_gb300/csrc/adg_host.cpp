@@ -462,7 +462,7 @@ void Ctx::setup() {
   // neighbour (both on the tensor-core kernels, 3 on their special local
   // instantiation), 2 the CUDA-core kernels: a fault face or more than one
   // gravitational face)
-  std::vector<char> special(E, 0);
+  std::vector<char> special(E, 0), lts_face(E, 0);
   if (tc)
     for (int64_t e = 0; e < E; ++e) {
       int ng_e = 0;
@@ -476,6 +476,7 @@ void Ctx::setup() {
         finer = finer || (e2 >= 0 && cl[e2] < cl[e]);
       }
       special[e] = (cc || ng_e > 1) ? 2 : ((ng_e == 1 || finer) ? 3 : (coarser ? 1 : 0));
+      lts_face[e] = coarser || finer;
     }
   // order key within a cluster: 0 plain elastic, 1 plain fluid on the
   // acoustic local kernel, 2 with a coarser neighbour, 3 with a gravitational
@@ -498,6 +499,7 @@ void Ctx::setup() {
   cl_fluid.assign(ncl, 0);
   cl_grav.assign(ncl, 0);
   cl_tc_coarse.assign(ncl, 0);
+  cl_tc_lts.assign(ncl, 0);
   for (int64_t i = 0; i < E; ++i) {
     const int k = key[order[i]], c = cl[order[i]];
     cl_begin[c + 1]++;
@@ -505,7 +507,8 @@ void Ctx::setup() {
     if (tc && k == 0) cl_elastic[c]++;
     if (tc && k == 1) cl_fluid[c]++;
     if (tc && k == 3) cl_grav[c]++;
-    if (tc && (k == 2 || k == 3)) cl_tc_coarse[c] = 1;  // (the neighbour kernel's LTS-face code)
+    if (tc && k == 2) cl_tc_coarse[c] = 1;                                  // (the local kernel's buffer code)
+    if (tc && (k == 2 || k == 3) && lts_face[order[i]]) cl_tc_lts[c] = 1;  // (the neighbour kernel's LTS-face code)
   }
   for (int c = 0; c < ncl; ++c) cl_begin[c + 1] += cl_begin[c];
   cluster.resize(E);
@@ -803,7 +806,7 @@ void Ctx::launch_tick(int s, double dtm) {
     // per kernel kind the clusters' segments: tensor-core elastic, tensor-core
     // acoustic and gravitational-face (local phase only), CUDA-core
     std::vector<Seg> tcs, fls, grs, ccs;
-    bool coarse = false;
+    bool coarse = false, ltsf = false;
     for (int c = 0; c < ncl; ++c) {
       const bool active = phase == 0 ? s % (1 << c) == 0 : (s + 1) % (1 << c) == 0;
       const int64_t n = cl_begin[c + 1] - cl_begin[c];
@@ -829,6 +832,7 @@ void Ctx::launch_tick(int s, double dtm) {
       const int64_t np = tc ? cl_plain[c] : 0;
       if (np > 0) {
         coarse = coarse || cl_tc_coarse[c] != 0;
+        ltsf = ltsf || cl_tc_lts[c] != 0;
         const int64_t n0 = cl_elastic[c], n1 = cl_fluid[c], ng_c = cl_grav[c];
         if (phase == 0) {
           // elastic elements around the acoustic range, then the gravitational-face
@@ -865,7 +869,7 @@ void Ctx::launch_tick(int s, double dtm) {
     };
     launch(tcs, kTileElems, [&](const Segs& g) {
       return phase == 0 ? launch_local_tc(N, a, g, n_sms, stream, coarse)
-                        : launch_neighbour_tc(N, a, g, n_sms, stream, coarse);
+                        : launch_neighbour_tc(N, a, g, n_sms, stream, ltsf);
     });
     launch(fls, kTileElemsFluid, [&](const Segs& g) { return launch_local_tc(N, a, g, n_sms, stream, false, true); });
     launch(grs, kTileElems,

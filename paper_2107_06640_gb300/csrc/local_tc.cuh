@@ -458,9 +458,13 @@ __device__ __forceinline__ bool local_tile(Lane& L, const StepArgs& a, const Seg
       if (p == 0) gv.dst = a.gscr + ((int64_t)gsl * a.S + (v - e * a.S)) * gscr_floats(N);
     }
   }
-  // faces with a finer neighbour: this row's derivative traces there
+  // faces with a finer neighbour: this row's derivative traces there; tile_fine:
+  // some element of the tile has one (the same answer in every thread of the slot)
   float* dtr[4] = {nullptr, nullptr, nullptr, nullptr};
+  bool tile_fine = false;
   if constexpr (kSpec) {
+    if (a.dslot)
+      for (int k = 0; k < 4 * nE; ++k) tile_fine |= a.dslot[((v0 + (k >> 2)) / a.S) * 4 + (k & 3)] >= 0;
     if (valid && a.dslot) {
 #pragma unroll
       for (int f = 0; f < 4; ++f) {
@@ -535,7 +539,7 @@ __device__ __forceinline__ bool local_tile(Lane& L, const StepArgs& a, const Seg
   // level's A operand, the last leaves the 10 rows of D^NL in registers
   if constexpr (NL == 3) {
     if constexpr (kSpec) {
-      if (!dtrace_round<N, H, D::K[0]>(L, a, dtr, 0)) return false;
+      if (tile_fine && !dtrace_round<N, H, D::K[0]>(L, a, dtr, 0)) return false;
     }
     if (!pair_round<H>(L, a.err, [&] {
           tc::mma3_ts<D::NN[0], D::K[0]>(tbase + cAcc, tbase + cAh, tbase + cAl, sbase + 4 * I_::oP0,
@@ -549,7 +553,7 @@ __device__ __forceinline__ bool local_tile(Lane& L, const StepArgs& a, const Seg
   constexpr int o1 = l1 == 0 ? I_::oP0 : I_::oP1, s1 = l1 == 0 ? I_::sP0 : I_::sP1;
   constexpr int o2 = l2 == 1 ? I_::oP1 : I_::oP2, s2 = l2 == 1 ? I_::sP1 : I_::sP2;
   if constexpr (kSpec) {
-    if (!dtrace_round<N, H, D::K[l1]>(L, a, dtr, l1)) return false;
+    if (tile_fine && !dtrace_round<N, H, D::K[l1]>(L, a, dtr, l1)) return false;
   }
   if (!pair_round<H>(L, a.err, [&] {
         tc::mma3_ts<D::NN[l1], D::K[l1]>(tbase + cAcc, tbase + cAh, tbase + cAl, sbase + 4 * o1,
@@ -559,7 +563,7 @@ __device__ __forceinline__ bool local_tile(Lane& L, const StepArgs& a, const Seg
   level_epilogue<H, D::M[l1], D::MP[l1], true, kSpec>(trow + cAcc, trow + cAh, trow + cAl, st, L.tcf[l1 + 1], I,
                                                      nullptr, gv, gscr_off(N, l1 + 1));
   if constexpr (kSpec) {
-    if (!dtrace_round<N, H, D::K[l2]>(L, a, dtr, l2)) return false;
+    if (tile_fine && !dtrace_round<N, H, D::K[l2]>(L, a, dtr, l2)) return false;
   }
   if (!pair_round<H>(L, a.err, [&] {
         tc::mma3_ts<D::NN[l2], D::K[l2]>(tbase + cAcc, tbase + cAh, tbase + cAl, sbase + 4 * o2,
