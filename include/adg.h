@@ -51,10 +51,12 @@ extern "C" {
 #define ADG_FP64 0
 #define ADG_FP32 1
 /* FP32 dofs; at degrees 5 and 4 the reference-matrix products (predictor,
- * face traces, volume term, lift) of the elements without gravitational face,
- * fault face or neighbour in a finer LTS cluster run on the tensor cores
- * (tcgen05) as 3xTF32 split products with FP32 accumulation, everything else
- * as in ADG_FP32; other degrees behave as ADG_FP32. */
+ * face traces, volume term, lift) of every element without a fault face or
+ * two or more gravitational faces run on the tensor cores (tcgen05) as 3xTF32
+ * split products with FP32 accumulation (elements at LTS cluster borders and
+ * with one gravitational face included), everything else as in ADG_FP32;
+ * the sea-surface series, LTS buffers and friction stay FP64; other degrees
+ * behave as ADG_FP32. */
 #define ADG_3XTF32 2
 
 /* Face tags (per tet and local face). */
@@ -130,7 +132,8 @@ int adg_upload_material(adg_ctx* ctx, const double* rho, const double* lambda, c
  *    such data;
  *  - with the tensor-core kernels (ADG_3XTF32, degree 5 or 4), the fluid elements
  *    without gravitational face, fault face or LTS neighbour in another
- *    cluster take a 4-quantity (p, v) local kernel: 32 elements per 128-row
+ *    cluster take a 4-quantity (p, v) local kernel (the others the 9-quantity
+ *    ones): 32 elements per 128-row
  *    tile, the acoustic star product, 4 of the 9 dofs rows read; their face
  *    traces are written in the usual 9-quantity layout.
  * Without it the fluid carries whatever stress the caller uploads (a
