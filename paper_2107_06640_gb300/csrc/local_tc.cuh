@@ -905,11 +905,13 @@ __global__ void __launch_bounds__(kThreadsL, 1) local_tc_kernel(StepArgs a, cons
   uint64_t* mbar = s_mbar;
   float (*sT)[4][2 * kTB] = s_T;
 
+  __shared__ __align__(8) uint64_t s_img;  // completion of the operand image's bulk copies
   const int tid = threadIdx.x, slot = tid >> 8, half = (tid >> 7) & 1;
-  {
-    const float4* src = reinterpret_cast<const float4*>(a.tc_local);
-    float4* dst = reinterpret_cast<float4*>(sm);
-    for (int r = tid; r < LImg<N>::floats / 4; r += kThreadsL) dst[r] = src[r];
+  // the operand image (the reference matrices' B operands) into shared memory
+  // by the TMA engine, while the threads set up the rest
+  if (tid == 0) {
+    tc::mbar_init(&s_img, 1);
+    tc::bulk_load_all(sm, a.tc_local, LImg<N>::floats * 4, &s_img);
   }
   for (int r = tid; r < 2 * 4 * 2 * kTB; r += kThreadsL) (&sT[0][0][0])[r] = 0.f;
   if (tid < 2) {
@@ -917,10 +919,25 @@ __global__ void __launch_bounds__(kThreadsL, 1) local_tc_kernel(StepArgs a, cons
     s_abort[tid] = 0;
   }
   if (tid < 32) tc::tmem_alloc<512>(&tmem_base);
+  __syncthreads();  // (the image barrier is initialised)
+  const bool img_ok = tc::mbar_wait(&s_img, 0, kWaitIters);
   tc::fence_async_smem();
   tc::fence_before();
-  __syncthreads();
+  const bool all_ok = __syncthreads_and(img_ok);
   tc::fence_after();
+  if (!all_ok) {
+    // the image did not arrive within the bound: report, give the copies a
+    // bounded chance to finish, free the columns and leave
+    if (tid == 0) {
+      atomicOr(a.err, ERR_TIMEOUT);
+      tc::mbar_wait(&s_img, 0, kWaitIters);
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    if (tid < 32) tc::tmem_dealloc<512>(tmem_base);
+    return;
+  }
 
   Lane L;
   L.slot = slot;

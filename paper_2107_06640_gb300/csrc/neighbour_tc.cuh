@@ -308,21 +308,37 @@ __global__ void __launch_bounds__(kThreadsN, 1) neighbour_tc_kernel(StepArgs a, 
   // slot: tile in flight; half: warpgroup within the slot; u: thread within the slot
   const int tid = threadIdx.x, slot = tid >> 8, half = (tid >> 7) & 1;
   const int u = tid & 255, t = tid & 127, w = t >> 5, lane = tid & 31;
-  {
-    const float4* src = reinterpret_cast<const float4*>(a.tc_lift);
-    float4* dst = reinterpret_cast<float4*>(sm + NI::oL);
-    for (int r = tid; r < 2 * NI::sL / 4; r += kThreadsN) dst[r] = src[r];
-    for (int r = tid; r < 6 * BF; r += kThreadsN) sPerm[r] = a.perm[r];
+  __shared__ __align__(8) uint64_t s_img;  // completion of the lift operand's bulk copies
+  // the lift operand into shared memory by the TMA engine, while the threads set up the rest
+  if (tid == 0) {
+    tc::mbar_init(&s_img, 1);
+    tc::bulk_load_all(sm + NI::oL, a.tc_lift, 2 * NI::sL * 4, &s_img);
   }
+  for (int r = tid; r < 6 * BF; r += kThreadsN) sPerm[r] = a.perm[r];
   if (tid < 2) {
     tc::mbar_init(&mbar[tid], 1);
     s_abort[tid] = 0;
   }
   if (tid < 32) tc::tmem_alloc<512>(&tmem_base);
+  __syncthreads();  // (the image barrier is initialised)
+  const bool img_ok = tc::mbar_wait(&s_img, 0, kWaitIters);
   tc::fence_async_smem();
   tc::fence_before();
-  __syncthreads();
+  const bool all_ok = __syncthreads_and(img_ok);
   tc::fence_after();
+  if (!all_ok) {
+    // the operand did not arrive within the bound: report, give the copies a
+    // bounded chance to finish, free the columns and leave
+    if (tid == 0) {
+      atomicOr(a.err, ERR_TIMEOUT);
+      tc::mbar_wait(&s_img, 0, kWaitIters);
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    if (tid < 32) tc::tmem_dealloc<512>(tmem_base);
+    return;
+  }
 
   const uint32_t tbase = tmem_base + (uint32_t)slot * 256u;
   const uint32_t trow = tbase + ((uint32_t)(32 * w) << 16);

@@ -87,6 +87,28 @@ __device__ __forceinline__ void mbar_init(uint64_t* mbar, int count) {
   asm volatile("fence.mbarrier_init.release.cluster;");
 }
 
+// one thread's arrival on the mbarrier, announcing `bytes` of asynchronous copies
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)), "r"(bytes)
+               : "memory");
+}
+// bulk copy (TMA engine, non-tensor) global -> this CTA's shared memory, both
+// 16-byte aligned, bytes a multiple of 16; completes on the mbarrier
+__device__ __forceinline__ void bulk_load(void* sm, const void* g, uint32_t bytes, uint64_t* mbar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(sm)),
+               "l"(g), "r"(bytes), "r"(smem_u32(mbar))
+               : "memory");
+}
+// thread 0 of the CTA: `bytes` from global to shared memory in bulk copies of
+// at most 32 KB, all completing on `mbar` (initialised, phase 0)
+__device__ __forceinline__ void bulk_load_all(void* sm, const void* g, uint32_t bytes, uint64_t* mbar) {
+  mbar_expect_tx(mbar, bytes);
+  for (uint32_t o = 0; o < bytes; o += 32768u)
+    bulk_load(static_cast<char*>(sm) + o, static_cast<const char*>(g) + o, bytes - o < 32768u ? bytes - o : 32768u,
+              mbar);
+}
+
 // wait for phase `parity` of the mbarrier; false if the bound ran out
 __device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, int max_iter) {
   for (int it = 0; it < max_iter; ++it) {
