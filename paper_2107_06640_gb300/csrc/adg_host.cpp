@@ -498,7 +498,6 @@ void Ctx::setup() {
   cl_elastic.assign(ncl, 0);
   cl_fluid.assign(ncl, 0);
   cl_grav.assign(ncl, 0);
-  cl_tc_coarse.assign(ncl, 0);
   cl_tc_lts.assign(ncl, 0);
   for (int64_t i = 0; i < E; ++i) {
     const int k = key[order[i]], c = cl[order[i]];
@@ -507,7 +506,6 @@ void Ctx::setup() {
     if (tc && k == 0) cl_elastic[c]++;
     if (tc && k == 1) cl_fluid[c]++;
     if (tc && k == 3) cl_grav[c]++;
-    if (tc && k == 2) cl_tc_coarse[c] = 1;                                  // (the local kernel's buffer code)
     if (tc && (k == 2 || k == 3) && lts_face[order[i]]) cl_tc_lts[c] = 1;  // (the neighbour kernel's LTS-face code)
   }
   for (int c = 0; c < ncl; ++c) cl_begin[c + 1] += cl_begin[c];
@@ -805,8 +803,10 @@ void Ctx::launch_tick(int s, double dtm) {
   for (int phase = 0; phase < 2; ++phase) {
     // per kernel kind the clusters' segments: tensor-core elastic, tensor-core
     // acoustic and gravitational-face (local phase only), CUDA-core
-    std::vector<Seg> tcs, fls, grs, ccs;
-    bool coarse = false, ltsf = false;
+    // (tcb: the local phase's elements with a coarser neighbour outside the
+    // special range, on the instantiation with the LTS-buffer code)
+    std::vector<Seg> tcs, tcb, fls, grs, ccs;
+    bool ltsf = false;
     for (int c = 0; c < ncl; ++c) {
       const bool active = phase == 0 ? s % (1 << c) == 0 : (s + 1) % (1 << c) == 0;
       const int64_t n = cl_begin[c + 1] - cl_begin[c];
@@ -831,19 +831,14 @@ void Ctx::launch_tick(int s, double dtm) {
       };
       const int64_t np = tc ? cl_plain[c] : 0;
       if (np > 0) {
-        coarse = coarse || cl_tc_coarse[c] != 0;
         ltsf = ltsf || cl_tc_lts[c] != 0;
-        const int64_t n0 = cl_elastic[c], n1 = cl_fluid[c], ng_c = cl_grav[c];
+        const int64_t n0 = cl_elastic[c], n1 = cl_fluid[c], ng_c = cl_grav[c], n2 = np - ng_c - n0 - n1;
         if (phase == 0) {
-          // elastic elements around the acoustic range, then the gravitational-face
-          // range; the last two take their own kernels
-          if (n1 > 0) {
-            if (n0 > 0) tcs.push_back(seg(cl_begin[c], n0));
-            fls.push_back(seg(cl_begin[c] + n0, n1));
-            if (np - ng_c > n0 + n1) tcs.push_back(seg(cl_begin[c] + n0 + n1, np - ng_c - n0 - n1));
-          } else if (np > ng_c) {
-            tcs.push_back(seg(cl_begin[c], np - ng_c));
-          }
+          // plain elastic, acoustic, coarser-neighbour and special ranges, each on
+          // its own kernel
+          if (n0 > 0) tcs.push_back(seg(cl_begin[c], n0));
+          if (n1 > 0) fls.push_back(seg(cl_begin[c] + n0, n1));
+          if (n2 > 0) tcb.push_back(seg(cl_begin[c] + n0 + n1, n2));
           if (ng_c > 0) grs.push_back(seg(cl_begin[c] + np - ng_c, ng_c));
         } else {
           tcs.push_back(seg(cl_begin[c], np));
@@ -851,7 +846,7 @@ void Ctx::launch_tick(int s, double dtm) {
       }
       if (n > np) ccs.push_back(seg(cl_begin[c] + np, n - np));
     }
-    if (tcs.empty() && fls.empty() && grs.empty() && ccs.empty()) continue;
+    if (tcs.empty() && tcb.empty() && fls.empty() && grs.empty() && ccs.empty()) continue;
     ProfEv ev{phase, nullptr, nullptr, 0};
     if (prof) {
       CK(cudaEventCreate(&ev.a));
@@ -868,13 +863,14 @@ void Ctx::launch_tick(int s, double dtm) {
       }
     };
     launch(tcs, kTileElems, [&](const Segs& g) {
-      return phase == 0 ? launch_local_tc(N, a, g, n_sms, stream, coarse)
+      return phase == 0 ? launch_local_tc(N, a, g, n_sms, stream, false)
                         : launch_neighbour_tc(N, a, g, n_sms, stream, ltsf);
     });
+    launch(tcb, kTileElems, [&](const Segs& g) { return launch_local_tc(N, a, g, n_sms, stream, true); });
     launch(fls, kTileElemsFluid, [&](const Segs& g) { return launch_local_tc(N, a, g, n_sms, stream, false, true); });
     launch(grs, kTileElems,
-           [&](const Segs& g) { return launch_local_tc(N, a, g, n_sms, stream, coarse, false, true); });
-    if (prof && (!tcs.empty() || !fls.empty() || !grs.empty())) {  // the tensor-core launches alone
+           [&](const Segs& g) { return launch_local_tc(N, a, g, n_sms, stream, true, false, true); });
+    if (prof && (!tcs.empty() || !tcb.empty() || !fls.empty() || !grs.empty())) {  // the tensor-core launches alone
       CK(cudaEventCreate(&ev.m));
       CK(cudaEventRecord(ev.m, stream));
     }
@@ -925,19 +921,24 @@ int64_t Ctx::launches_per_macro() const {
   const int ticks = 1 << (ncl - 1);
   for (int s = 0; s < ticks; ++s)
     for (int phase = 0; phase < 2; ++phase) {
-      bool tcl = false, fll = false, grl = false, ccl = false;
+      bool tcl = false, tbl = false, fll = false, grl = false, ccl = false;
       for (int c = 0; c < ncl; ++c) {
         const int64_t n = cl_begin[c + 1] - cl_begin[c];
         if (!n || (phase == 0 ? s % (1 << c) : (s + 1) % (1 << c))) continue;
         if (phase == 1 && fcl_begin[c + 1] > fcl_begin[c]) L += 1;  // friction solve per cluster
-        const int64_t np = tc ? cl_plain[c] : 0, nf = (tc && phase == 0) ? cl_fluid[c] : 0,
-                      ngr = (tc && phase == 0) ? cl_grav[c] : 0;
-        tcl = tcl || np > nf + ngr;
-        fll = fll || nf > 0;
-        grl = grl || ngr > 0;
+        const int64_t np = tc ? cl_plain[c] : 0;
+        if (phase == 0 && np > 0) {
+          const int64_t n0 = cl_elastic[c], nf = cl_fluid[c], ngr = cl_grav[c];
+          tcl = tcl || n0 > 0;
+          fll = fll || nf > 0;
+          tbl = tbl || np - ngr - n0 - nf > 0;
+          grl = grl || ngr > 0;
+        } else {
+          tcl = tcl || np > 0;
+        }
         ccl = ccl || n > np;
       }
-      L += tcl + fll + grl + ccl;
+      L += tcl + tbl + fll + grl + ccl;
     }
   return L;
 }

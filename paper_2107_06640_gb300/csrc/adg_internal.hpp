@@ -77,10 +77,9 @@ struct Ctx {
   // elements [cl_begin[c], cl_begin[c] + cl_plain[c]) of cluster c have no
   // gravitational face, fault face or LTS buffer (tensor-core local kernel)
   std::vector<int64_t> cl_plain;
-  // cluster c's tensor-core range includes elements with a coarser neighbour
-  // outside the special range (local kernel: LTS buffers), elements with a
-  // coarser or finer neighbour (neighbour kernel: LTS faces)
-  std::vector<char> cl_tc_coarse, cl_tc_lts;
+  // cluster c's tensor-core range includes elements with a coarser or finer
+  // neighbour (the neighbour kernel's LTS-face code)
+  std::vector<char> cl_tc_lts;
   // acoustic ocean (adg_set_acoustic_ocean): the plain fluid elements of
   // cluster c, [cl_begin[c] + cl_elastic[c], + cl_fluid[c]), take the
   // 4-quantity local kernel; the library keeps fluid stress isotropic
