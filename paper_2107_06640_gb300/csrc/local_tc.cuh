@@ -1,7 +1,8 @@
 // Local element kernel on the tensor cores (tcgen05, 3xTF32), degrees 5 and
 // 4, FP32 dofs: Cauchy-Kovalewski predictor, time integral, face traces and
-// volume term of Sec. 4.1 for elements without fault faces (those take the
-// CUDA-core kernel); an element with a coarser LTS neighbour also adds its
+// volume term of Sec. 4.1 for elements without fault faces or two or more
+// gravitational faces (those take the CUDA-core kernel); an element with a
+// coarser LTS neighbour also adds its
 // traces to its FP64 LTS buffer; elements with one gravitational face or a
 // finer LTS neighbour take a special instantiation that also forms the
 // gravitational face's (eta, H) update and the derivative traces of every
@@ -26,6 +27,7 @@
 //     and written to the trace array with bulk copies (cp.async.bulk);
 //   volume: W_a = K_a I for the three axes on the tensor cores, then
 //     Q += sum_a A*_a W_a on the CUDA cores (Jacobian form, shuffles).
+// The operand image reaches shared memory once per CTA by TMA bulk copies.
 // A CTA keeps two tiles in flight (TMEM columns [0, 256) and [256, 512)), each
 // worked on by two warpgroups that split every stage by 8-column chunks (even
 // chunks: first half, odd chunks: second half); one thread per tile issues
