@@ -76,8 +76,8 @@ def bytes_per_update(N, w):
 # acoustic local, neighbour), from the one-kernel ncu captures of the
 # 374,400-tet box (profiles/tensor_core_kernels_box40.md); a launch's traffic
 # is scaled from them by its elements of each kind
-TC_DRAM_BYTES_PER_ELEMENT = {"local_tc_kernel": 6996.9, "local_tc_kernel_acoustic": 5618.0,
-                             "neighbour_tc_kernel": 7694.3}
+TC_DRAM_BYTES_PER_ELEMENT = {"local_tc_kernel": 6996.4, "local_tc_kernel_acoustic": 5649.0,
+                             "neighbour_tc_kernel": 7701.7}
 
 
 def load_peaks():
