@@ -199,6 +199,32 @@ int adg_get_dofs(adg_ctx* ctx, double* Q);
  * array is borrowed for the call; both calls return after their copy. */
 int adg_set_dofs_f32(adg_ctx* ctx, const float* Q);
 int adg_get_dofs_f32(adg_ctx* ctx, float* Q);
+/* Pipelined forms of the three calls above: each enqueues its work and
+ * returns without waiting, so that the host copies of one step overlap the
+ * compute of another.  Q, layout and precision as in adg_set_dofs_f32 /
+ * adg_get_dofs_f32 (pinned host memory for an asynchronous copy).
+ * - adg_set_dofs_f32_async: the host array is copied on the context's
+ *   upload stream into a device staging buffer of its own, then reordered
+ *   into the dofs on the library stream (after everything enqueued there
+ *   before, before everything enqueued after).  The array is borrowed until
+ *   adg_sync returns: the caller neither frees nor changes it before.
+ * - adg_get_dofs_f32_async: the dofs as they stand after the work enqueued
+ *   before are reordered into a second staging buffer on the library stream
+ *   and copied to the host array on the download stream.  The array holds
+ *   them once adg_sync has returned.
+ * - adg_advance_async: adg_advance without waiting for the steps: device
+ *   errors (ADG_E_NAN, ADG_E_NEWTON, ADG_E_TIMEOUT) are reported by the next
+ *   adg_sync or synchronous call instead.
+ * - adg_sync (declared below) waits for all of the context's enqueued work
+ *   and copies, then reports device errors as adg_advance does.
+ * The staging buffers (2 x nt x S x 9 x B floats of device memory) and the
+ * two copy streams are created by the first pipelined call and released by
+ * adg_destroy.  Any call needs no macro-step boundary (the staging is not the
+ * trace array).  Errors: ADG_E_INVALID for a NULL argument or n_macro < 0,
+ * ADG_E_STATE before adg_init, ADG_E_CUDA for a failed enqueue or allocation. */
+int adg_set_dofs_f32_async(adg_ctx* ctx, const float* Q);
+int adg_get_dofs_f32_async(adg_ctx* ctx, float* Q);
+int adg_advance_async(adg_ctx* ctx, int n_macro);
 /* The dofs of n listed user tets (indices in [0, nt)), Q[n][S][9][B] double,
  * gathered on the device: a cheap look at a few elements of a large mesh, at
  * any point (also inside an LTS macro step, where the elements of a cluster
@@ -243,7 +269,8 @@ int adg_advance_to(adg_ctx* ctx, double t);
 int adg_step_tick(adg_ctx* ctx);
 /* Run ticks until cluster c completes one more step. */
 int adg_step_cluster(adg_ctx* ctx, int c);
-/* Block until queued work is done; reports device-side errors (NaN...). */
+/* Block until queued work is done, the copies of the pipelined transfers
+ * included; reports device-side errors (NaN...). */
 int adg_sync(adg_ctx* ctx);
 
 /* Per-kernel timing for roofline reports: runs n_macro macro steps with

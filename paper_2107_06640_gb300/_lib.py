@@ -64,6 +64,9 @@ _SIGS = {
     "adg_record_read": (C.c_int, [_P, C.c_int, C.c_int64, _P, _P, _P, _P]),
     "adg_record_stop": (C.c_int, [_P, C.c_int]),
     "adg_get_dofs_f32": (C.c_int, [_P, _P]),
+    "adg_set_dofs_f32_async": (C.c_int, [_P, _P]),
+    "adg_get_dofs_f32_async": (C.c_int, [_P, _P]),
+    "adg_advance_async": (C.c_int, [_P, C.c_int]),
     "adg_initial_points": (C.c_int, [_P, C.POINTER(C.c_int), _P]),
     "adg_set_initial_values": (C.c_int, [_P, _P]),
     "adg_gravity_faces": (C.c_int, [_P, _P, _P]),
@@ -263,6 +266,25 @@ def adg_get_dofs_f32(ctx, out):
     _host(out, np.float32, _ndofs(ctx), "dofs [nt][S][9][B]", out=True)
     _check(ctx, load().adg_get_dofs_f32(ctx, _ptr(out)))
     return out
+
+
+def adg_set_dofs_f32_async(ctx, Q):
+    """Enqueue the upload of Q (C-contiguous float32 [tet][S][9][B], pinned host
+    memory; never a converted copy, since Q is borrowed until adg_sync returns)."""
+    _host(Q, np.float32, _ndofs(ctx), "dofs [nt][S][9][B]", out=True)
+    _check(ctx, load().adg_set_dofs_f32_async(ctx, _ptr(Q)))
+    return Q
+
+
+def adg_get_dofs_f32_async(ctx, out):
+    """Enqueue the download into out (float32, pinned); complete after adg_sync."""
+    _host(out, np.float32, _ndofs(ctx), "dofs [nt][S][9][B]", out=True)
+    _check(ctx, load().adg_get_dofs_f32_async(ctx, _ptr(out)))
+    return out
+
+
+def adg_advance_async(ctx, n):
+    _check(ctx, load().adg_advance_async(ctx, int(n)))
 
 
 def adg_record_start(ctx, kind, every, capacity):

@@ -346,6 +346,65 @@ int adg_get_dofs_f32(adg_ctx* ctx, float* Q) {
   });
 }
 
+// Pipelined transfers: the upload's host copy runs on its own stream into its
+// own staging buffer and is reordered into the dofs on the library stream; the
+// download is reordered on the library stream and copied to the host on a
+// second stream.  Events keep each staging buffer from being overwritten
+// before its last reader is done, so a step's compute overlaps the next
+// step's upload and the previous step's download.
+int adg_set_dofs_f32_async(adg_ctx* ctx, const float* Q) {
+  if (!ctx || !Q) return ADG_E_INVALID;
+  return guard(ctx, [&] {
+    Ctx& c = ctx->c;
+    need_init(c);
+    c.aio_setup();
+    const int per = c.S * 9 * c.B;
+    const size_t bytes = (size_t)c.nt * per * sizeof(float);
+    check_cuda(cudaStreamWaitEvent(c.aio.in, c.aio.in_used, 0), "dofs upload");
+    check_cuda(cudaMemcpyAsync(c.aio.dIn, Q, bytes, cudaMemcpyHostToDevice, c.aio.in), "dofs upload");
+    check_cuda(cudaEventRecord(c.aio.in_copied, c.aio.in), "dofs upload");
+    check_cuda(cudaStreamWaitEvent(c.stream, c.aio.in_copied, 0), "dofs upload");
+    check_cuda((cudaError_t)adg::launch_permute_dofs(c.fp64, 1, c.aio.dIn, c.dQ, c.dOrder, c.nt, per, c.n_sms,
+                                                      c.stream),
+               "dofs upload");
+    check_cuda(cudaEventRecord(c.aio.in_used, c.stream), "dofs upload");
+    c.project_fluid(false);
+  });
+}
+
+int adg_get_dofs_f32_async(adg_ctx* ctx, float* Q) {
+  if (!ctx || !Q) return ADG_E_INVALID;
+  return guard(ctx, [&] {
+    Ctx& c = ctx->c;
+    need_init(c);
+    c.aio_setup();
+    const int per = c.S * 9 * c.B;
+    const size_t bytes = (size_t)c.nt * per * sizeof(float);
+    check_cuda(cudaStreamWaitEvent(c.stream, c.aio.out_copied, 0), "dofs download");
+    check_cuda((cudaError_t)adg::launch_permute_dofs(c.fp64, 0, c.dQ, c.aio.dOut, c.dOrder, c.nt, per, c.n_sms,
+                                                      c.stream),
+               "dofs download");
+    check_cuda(cudaEventRecord(c.aio.out_made, c.stream), "dofs download");
+    check_cuda(cudaStreamWaitEvent(c.aio.out, c.aio.out_made, 0), "dofs download");
+    check_cuda(cudaMemcpyAsync(Q, c.aio.dOut, bytes, cudaMemcpyDeviceToHost, c.aio.out), "dofs download");
+    check_cuda(cudaEventRecord(c.aio.out_copied, c.aio.out), "dofs download");
+  });
+}
+
+int adg_advance_async(adg_ctx* ctx, int n_macro) {
+  if (!ctx || n_macro < 0) return ADG_E_INVALID;
+  return guard(ctx, [&] {
+    Ctx& c = ctx->c;
+    need_init(c);
+    run_ticks_to_boundary(c);
+    for (int i = 0; i < n_macro; ++i) {
+      c.run_macro(1.0);
+      c.tick += 1 << (c.ncl - 1);
+      c.record_after_macro();
+    }
+  });
+}
+
 int adg_hydrostatic_start(adg_ctx* ctx) {
   if (!ctx) return ADG_E_INVALID;
   return guard(ctx, [&] {
@@ -750,6 +809,7 @@ int adg_sync(adg_ctx* ctx) {
   if (!ctx) return ADG_E_INVALID;
   return guard(ctx, [&] {
     need_init(ctx->c);
+    ctx->c.aio_sync();  // the pipelined copies (their streams wait on the library stream where needed)
     ctx->c.check_err();
   });
 }

@@ -943,11 +943,38 @@ int64_t Ctx::launches_per_macro() const {
   return L;
 }
 
-void Ctx::project_fluid() {
+void Ctx::project_fluid(bool sync) {
   if (!acoustic || !n_fluid) return;
   const int rc = launch_isotropic_fluid(fp64, dQ, dFluid, n_fluid, S * B, B, stream);
   if (rc) throw Err(ADG_E_CUDA, std::string("fluid projection: ") + cudaGetErrorString((cudaError_t)rc));
-  CK(cudaStreamSynchronize(stream));
+  if (sync) CK(cudaStreamSynchronize(stream));
+}
+
+void Ctx::aio_setup() {
+  if (aio.in) return;  // (created last: everything else is in place)
+  const size_t bytes = (size_t)nt * S * 9 * B * sizeof(float);
+  if (!aio.dIn) aio.dIn = static_cast<float*>(dalloc(bytes, owned, dev_bytes));
+  if (!aio.dOut) aio.dOut = static_cast<float*>(dalloc(bytes, owned, dev_bytes));
+  for (cudaEvent_t* e : {&aio.in_copied, &aio.in_used, &aio.out_made, &aio.out_copied})
+    if (!*e) CK(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+  if (!aio.out) CK(cudaStreamCreateWithFlags(&aio.out, cudaStreamNonBlocking));
+  CK(cudaStreamCreateWithFlags(&aio.in, cudaStreamNonBlocking));
+}
+
+void Ctx::aio_sync() {
+  if (aio.in) CK(cudaStreamSynchronize(aio.in));
+  if (aio.out) CK(cudaStreamSynchronize(aio.out));
+}
+
+void Ctx::aio_free() {
+  for (cudaStream_t st : {aio.in, aio.out})
+    if (st) {
+      cudaStreamSynchronize(st);
+      cudaStreamDestroy(st);
+    }
+  for (cudaEvent_t e : {aio.in_copied, aio.in_used, aio.out_made, aio.out_copied})
+    if (e) cudaEventDestroy(e);
+  aio = AsyncIo{};  // (the staging buffers are among the owned allocations)
 }
 
 void Ctx::run_macro(double scale) {
@@ -1028,6 +1055,7 @@ void Ctx::check_err() {
 Ctx::~Ctx() {
   record_free(0);
   record_free(1);
+  aio_free();
   if (rec_stream) cudaStreamDestroy(rec_stream);
   if (graph_exec) cudaGraphExecDestroy(graph_exec);
   for (void* p : owned) cudaFree(p);

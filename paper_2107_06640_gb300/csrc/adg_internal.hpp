@@ -92,7 +92,7 @@ struct Ctx {
   float* dGscr = nullptr;
   int64_t* dFluid = nullptr;  // library indices of all fluid elements (projection at upload)
   int64_t n_fluid = 0;
-  void project_fluid();       // fluid stress -> its isotropic part, on the device
+  void project_fluid(bool sync = true);  // fluid stress -> its isotropic part, on the device
   std::vector<int> cluster;
   double dtmin = 0, time = 0;
   int64_t tick = 0;
@@ -145,6 +145,21 @@ struct Ctx {
   // pinned host staging buffer for dofs upload / download (allocated on first use)
   void* hstage = nullptr;
   size_t hstage_bytes = 0;
+  // pipelined FP32 dofs transfers (adg_set_dofs_f32_async / adg_get_dofs_f32_async):
+  // device staging of one upload and one download, a copy stream for each
+  // direction, and the events that order them with the library stream
+  // (created on first use)
+  struct AsyncIo {
+    cudaStream_t in = nullptr, out = nullptr;
+    float *dIn = nullptr, *dOut = nullptr;
+    cudaEvent_t in_copied = nullptr;   // the upload's host copy has landed in dIn
+    cudaEvent_t in_used = nullptr;     // the library stream has reordered dIn into the dofs
+    cudaEvent_t out_made = nullptr;    // the library stream has written the download into dOut
+    cudaEvent_t out_copied = nullptr;  // dOut has been copied to the host
+  } aio;
+  void aio_setup();
+  void aio_sync();
+  void aio_free();
   // receivers
   int64_t n_rec = 0;
   int64_t* dRecElem = nullptr;

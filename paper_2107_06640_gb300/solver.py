@@ -100,6 +100,20 @@ class Solver:
         L.adg_get_dofs_f32(self.ctx, out)
         return out
 
+    def set_dofs_f32_async(self, Q):
+        """Enqueue the upload of Q (C-contiguous float32 [tet][S][9][B], pinned);
+        Q stays borrowed until sync() returns."""
+        L.adg_set_dofs_f32_async(self.ctx, Q)
+
+    def get_dofs_f32_async(self, out):
+        """Enqueue the download of the dofs into out (float32, pinned); complete after sync()."""
+        L.adg_get_dofs_f32_async(self.ctx, out)
+        return out
+
+    def advance_async(self, n=1):
+        """Enqueue n macro steps; device errors surface at the next sync()."""
+        L.adg_advance_async(self.ctx, n)
+
     def initial_points(self):
         return L.adg_initial_points(self.ctx, self.nt)
 

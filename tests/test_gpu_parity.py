@@ -240,6 +240,45 @@ def test_f32_dofs_transfer(N):
     with pytest.raises(AdgError):
         s.get_dofs_subset([w.nt])
 
+@pytest.mark.parametrize("prec_name,S,N,acoustic", [("ADG_3XTF32", 1, 5, True), ("ADG_FP64", 2, 3, False)])
+def test_f32_dofs_pipelined_transfers(prec_name, S, N, acoustic):
+    """adg_set_dofs_f32_async / adg_advance_async / adg_get_dofs_f32_async then
+    adg_sync: four steps enqueued back to back, each from its own upload and
+    into its own download, give bit for bit the results of the synchronous
+    calls (the uploads' fluid stress projected as there), the context ends at
+    the same time, a synchronous call after the pipeline sees the last state,
+    and an input that would need converting is refused before anything is
+    enqueued."""
+    import torch
+    import paper_2107_06640_gb300 as pkg
+    from paper_2107_06640_gb300 import Solver
+    m, (rho, lam, mu) = small_coupled()
+    kw = dict(degree=N, cfl=0.5, precision=getattr(pkg, prec_name), ensemble=S, acoustic_ocean=acoustic)
+    a = Solver(m.xyz, m.tets, m.face_tag, rho, lam, mu, **kw)
+    b = Solver(m.xyz, m.tets, m.face_tag, rho, lam, mu, **kw)
+    shape = (m.nt, S, 9, a.B)
+    rng = np.random.default_rng(11)
+    K = 4
+    ins = [torch.empty(shape, dtype=torch.float32, pin_memory=True).numpy() for _ in range(K)]
+    outs = [torch.empty(shape, dtype=torch.float32, pin_memory=True).numpy() for _ in range(K)]
+    for x in ins:
+        x[...] = (rng.standard_normal(shape) * 1e-2).astype(np.float32)
+    for k in range(K):
+        a.set_dofs_f32_async(ins[k])
+        a.advance_async(1)
+        a.get_dofs_f32_async(outs[k])
+    a.sync()
+    for k in range(K):
+        b.set_dofs_f32(ins[k])
+        b.advance(1)
+        assert np.array_equal(outs[k], b.get_dofs_f32()), k
+    assert a.info.time == b.info.time
+    assert np.array_equal(a.get_dofs_f32(), outs[-1])
+    with pytest.raises(ValueError):
+        a.set_dofs_f32_async(ins[0].astype(np.float64))
+    with pytest.raises(ValueError):
+        a.get_dofs_f32_async(np.empty(shape, np.float64))
+
 def test_lts_coupled_graded_fp64():
     m, mat = syn.workloads.coupled_box(nxy=4, n_water=2, n_crust=2, L=8e3, depth=4e3, water=1e3,
                                        grading=4.0)
