@@ -136,6 +136,16 @@ int main(void) {
   dtmin = -1.0;
   CHECK(adg_plan(ctx, NULL, NULL, &dtmin, NULL) == ADG_E_INVALID && dtmin == -1.0);
 
+  /* the pipelined calls: argument checks, then the state check before adg_init */
+  float qf = 0.f;
+  CHECK(adg_set_dofs_f32_async(NULL, &qf) == ADG_E_INVALID);
+  CHECK(adg_get_dofs_f32_async(ctx, NULL) == ADG_E_INVALID);
+  CHECK(adg_advance_async(ctx, -1) == ADG_E_INVALID);
+  CHECK(adg_set_dofs_f32_async(ctx, &qf) == ADG_E_STATE);
+  CHECK(adg_get_dofs_f32_async(ctx, &qf) == ADG_E_STATE);
+  CHECK(adg_advance_async(ctx, 1) == ADG_E_STATE);
+  CHECK(adg_sync(ctx) == ADG_E_STATE);
+
   adg_destroy(ctx);
   printf("ok %lld %d %.17g\n", (long long)nt, ncl, dt_planned);
   free(xyz); free(tets); free(tag); free(rho); free(lam); free(mu); free(dt); free(cl); free(kt);
