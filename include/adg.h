@@ -217,9 +217,9 @@ int adg_get_dofs_f32(adg_ctx* ctx, float* Q);
  *   adg_sync or synchronous call instead.
  * - adg_sync (declared below) waits for all of the context's enqueued work
  *   and copies, then reports device errors as adg_advance does.
- * The staging buffers (2 x nt x S x 9 x B floats of device memory) and the
- * two copy streams are created by the first pipelined call and released by
- * adg_destroy.  Any call needs no macro-step boundary (the staging is not the
+ * The staging buffers (two per direction, transfer j using buffer j % 2:
+ * 4 x nt x S x 9 x B floats of device memory) and the two copy streams are
+ * created by the first pipelined call and released by adg_destroy.  Any call needs no macro-step boundary (the staging is not the
  * trace array).  Errors: ADG_E_INVALID for a NULL argument or n_macro < 0,
  * ADG_E_STATE before adg_init, ADG_E_CUDA for a failed enqueue or allocation. */
 int adg_set_dofs_f32_async(adg_ctx* ctx, const float* Q);

@@ -360,14 +360,17 @@ int adg_set_dofs_f32_async(adg_ctx* ctx, const float* Q) {
     c.aio_setup();
     const int per = c.S * 9 * c.B;
     const size_t bytes = (size_t)c.nt * per * sizeof(float);
-    check_cuda(cudaStreamWaitEvent(c.aio.in, c.aio.in_used, 0), "dofs upload");
-    check_cuda(cudaMemcpyAsync(c.aio.dIn, Q, bytes, cudaMemcpyHostToDevice, c.aio.in), "dofs upload");
-    check_cuda(cudaEventRecord(c.aio.in_copied, c.aio.in), "dofs upload");
-    check_cuda(cudaStreamWaitEvent(c.stream, c.aio.in_copied, 0), "dofs upload");
-    check_cuda((cudaError_t)adg::launch_permute_dofs(c.fp64, 1, c.aio.dIn, c.dQ, c.dOrder, c.nt, per, c.n_sms,
+    const int b = (int)(c.aio.n_in & 1);
+    // buffer b was last read by the reordering of the upload before the previous one
+    check_cuda(cudaStreamWaitEvent(c.aio.in, c.aio.in_used[b], 0), "dofs upload");
+    check_cuda(cudaMemcpyAsync(c.aio.dIn[b], Q, bytes, cudaMemcpyHostToDevice, c.aio.in), "dofs upload");
+    check_cuda(cudaEventRecord(c.aio.in_copied[b], c.aio.in), "dofs upload");
+    check_cuda(cudaStreamWaitEvent(c.stream, c.aio.in_copied[b], 0), "dofs upload");
+    check_cuda((cudaError_t)adg::launch_permute_dofs(c.fp64, 1, c.aio.dIn[b], c.dQ, c.dOrder, c.nt, per, c.n_sms,
                                                       c.stream),
                "dofs upload");
-    check_cuda(cudaEventRecord(c.aio.in_used, c.stream), "dofs upload");
+    check_cuda(cudaEventRecord(c.aio.in_used[b], c.stream), "dofs upload");
+    c.aio.n_in++;
     c.project_fluid(false);
   });
 }
@@ -380,14 +383,17 @@ int adg_get_dofs_f32_async(adg_ctx* ctx, float* Q) {
     c.aio_setup();
     const int per = c.S * 9 * c.B;
     const size_t bytes = (size_t)c.nt * per * sizeof(float);
-    check_cuda(cudaStreamWaitEvent(c.stream, c.aio.out_copied, 0), "dofs download");
-    check_cuda((cudaError_t)adg::launch_permute_dofs(c.fp64, 0, c.dQ, c.aio.dOut, c.dOrder, c.nt, per, c.n_sms,
+    const int b = (int)(c.aio.n_out & 1);
+    // buffer b was last read by the host copy of the download before the previous one
+    check_cuda(cudaStreamWaitEvent(c.stream, c.aio.out_copied[b], 0), "dofs download");
+    check_cuda((cudaError_t)adg::launch_permute_dofs(c.fp64, 0, c.dQ, c.aio.dOut[b], c.dOrder, c.nt, per, c.n_sms,
                                                       c.stream),
                "dofs download");
-    check_cuda(cudaEventRecord(c.aio.out_made, c.stream), "dofs download");
-    check_cuda(cudaStreamWaitEvent(c.aio.out, c.aio.out_made, 0), "dofs download");
-    check_cuda(cudaMemcpyAsync(Q, c.aio.dOut, bytes, cudaMemcpyDeviceToHost, c.aio.out), "dofs download");
-    check_cuda(cudaEventRecord(c.aio.out_copied, c.aio.out), "dofs download");
+    check_cuda(cudaEventRecord(c.aio.out_made[b], c.stream), "dofs download");
+    check_cuda(cudaStreamWaitEvent(c.aio.out, c.aio.out_made[b], 0), "dofs download");
+    check_cuda(cudaMemcpyAsync(Q, c.aio.dOut[b], bytes, cudaMemcpyDeviceToHost, c.aio.out), "dofs download");
+    check_cuda(cudaEventRecord(c.aio.out_copied[b], c.aio.out), "dofs download");
+    c.aio.n_out++;
   });
 }
 

@@ -953,10 +953,12 @@ void Ctx::project_fluid(bool sync) {
 void Ctx::aio_setup() {
   if (aio.in) return;  // (created last: everything else is in place)
   const size_t bytes = (size_t)nt * S * 9 * B * sizeof(float);
-  if (!aio.dIn) aio.dIn = static_cast<float*>(dalloc(bytes, owned, dev_bytes));
-  if (!aio.dOut) aio.dOut = static_cast<float*>(dalloc(bytes, owned, dev_bytes));
-  for (cudaEvent_t* e : {&aio.in_copied, &aio.in_used, &aio.out_made, &aio.out_copied})
-    if (!*e) CK(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+  for (int b = 0; b < 2; ++b) {
+    if (!aio.dIn[b]) aio.dIn[b] = static_cast<float*>(dalloc(bytes, owned, dev_bytes));
+    if (!aio.dOut[b]) aio.dOut[b] = static_cast<float*>(dalloc(bytes, owned, dev_bytes));
+    for (cudaEvent_t* e : {&aio.in_copied[b], &aio.in_used[b], &aio.out_made[b], &aio.out_copied[b]})
+      if (!*e) CK(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+  }
   if (!aio.out) CK(cudaStreamCreateWithFlags(&aio.out, cudaStreamNonBlocking));
   CK(cudaStreamCreateWithFlags(&aio.in, cudaStreamNonBlocking));
 }
@@ -972,8 +974,9 @@ void Ctx::aio_free() {
       cudaStreamSynchronize(st);
       cudaStreamDestroy(st);
     }
-  for (cudaEvent_t e : {aio.in_copied, aio.in_used, aio.out_made, aio.out_copied})
-    if (e) cudaEventDestroy(e);
+  for (int b = 0; b < 2; ++b)
+    for (cudaEvent_t e : {aio.in_copied[b], aio.in_used[b], aio.out_made[b], aio.out_copied[b]})
+      if (e) cudaEventDestroy(e);
   aio = AsyncIo{};  // (the staging buffers are among the owned allocations)
 }
 

@@ -146,16 +146,18 @@ struct Ctx {
   void* hstage = nullptr;
   size_t hstage_bytes = 0;
   // pipelined FP32 dofs transfers (adg_set_dofs_f32_async / adg_get_dofs_f32_async):
-  // device staging of one upload and one download, a copy stream for each
-  // direction, and the events that order them with the library stream
-  // (created on first use)
+  // two device staging buffers for uploads and two for downloads (transfer j
+  // uses buffer j % 2, so a copy never waits for the reordering of the
+  // transfer just before it), a copy stream for each direction, and the
+  // events that order them with the library stream (created on first use)
   struct AsyncIo {
     cudaStream_t in = nullptr, out = nullptr;
-    float *dIn = nullptr, *dOut = nullptr;
-    cudaEvent_t in_copied = nullptr;   // the upload's host copy has landed in dIn
-    cudaEvent_t in_used = nullptr;     // the library stream has reordered dIn into the dofs
-    cudaEvent_t out_made = nullptr;    // the library stream has written the download into dOut
-    cudaEvent_t out_copied = nullptr;  // dOut has been copied to the host
+    float *dIn[2] = {nullptr, nullptr}, *dOut[2] = {nullptr, nullptr};
+    cudaEvent_t in_copied[2] = {nullptr, nullptr};   // an upload's host copy has landed in dIn[b]
+    cudaEvent_t in_used[2] = {nullptr, nullptr};     // the library stream has reordered dIn[b] into the dofs
+    cudaEvent_t out_made[2] = {nullptr, nullptr};    // the library stream has written a download into dOut[b]
+    cudaEvent_t out_copied[2] = {nullptr, nullptr};  // dOut[b] has been copied to the host
+    int64_t n_in = 0, n_out = 0;                     // uploads and downloads enqueued so far
   } aio;
   void aio_setup();
   void aio_sync();
