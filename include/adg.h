@@ -199,9 +199,9 @@ int adg_get_dofs(adg_ctx* ctx, double* Q);
  * array is borrowed for the call; both calls return after their copy. */
 int adg_set_dofs_f32(adg_ctx* ctx, const float* Q);
 int adg_get_dofs_f32(adg_ctx* ctx, float* Q);
-/* Pipelined forms of the three calls above: each enqueues its work and
- * returns without waiting, so that the host copies of one step overlap the
- * compute of another.  Q, layout and precision as in adg_set_dofs_f32 /
+/* Pipelined forms of the three calls above (host-transfer plumbing; the paper
+ * has no counterpart): each enqueues its work and returns without waiting, so
+ * that the host copies of one step overlap the compute of another.  Q, layout and precision as in adg_set_dofs_f32 /
  * adg_get_dofs_f32 (pinned host memory for an asynchronous copy).
  * - adg_set_dofs_f32_async: the host array is copied on the context's
  *   upload stream into a device staging buffer of its own, then reordered
