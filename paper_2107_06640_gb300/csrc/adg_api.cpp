@@ -346,12 +346,13 @@ int adg_get_dofs_f32(adg_ctx* ctx, float* Q) {
   });
 }
 
-// Pipelined transfers: the upload's host copy runs on its own stream into its
-// own staging buffer and is reordered into the dofs on the library stream; the
-// download is reordered on the library stream and copied to the host on a
-// second stream.  Events keep each staging buffer from being overwritten
-// before its last reader is done, so a step's compute overlaps the next
-// step's upload and the previous step's download.
+// Pipelined transfers: an upload's host copy runs on its own stream into one
+// of two staging buffers and is reordered into the dofs on the library
+// stream; a download is reordered on the library stream into one of two
+// other staging buffers and copied to the host on a second stream.  Events
+// keep each staging buffer from being overwritten before its last reader is
+// done, so a step's compute overlaps the later uploads and the earlier
+// downloads, and neither copy stream waits for the reordering in between.
 int adg_set_dofs_f32_async(adg_ctx* ctx, const float* Q) {
   if (!ctx || !Q) return ADG_E_INVALID;
   return guard(ctx, [&] {
